@@ -1,0 +1,200 @@
+"""HHL as the paper's procedure, step by step, in FP64 -- test infrastructure only.
+
+Follows the "Practical HHL procedures" box of Sec. III-A (steps 1-4), the HHL decomposition
+|x> = sum_i lambda_i^-1 b_i |v_i> of Sec. III-A, the circuit structure of Fig. 5 (state
+preparation, quantum phase estimation, eigenvalue-inversion rotation on an ancilla, inverse
+phase estimation) and the resource formula of Sec. III-B.
+
+Readings of points the paper leaves open (the same list is kept with the design notes):
+  * qubit order little-endian; data qubits 0..nb-1, clock qubit j is nb+j (bit j of the clock
+    value), the ancilla is qubit nb+m;
+  * evolution U = exp(+iAt); clock qubit j controls U^(2^j); an eigenvalue lambda lands on clock
+    value k = lambda t 2^m / (2 pi); the inverse QFT includes the final qubit-reversal swaps;
+  * default t = 2 pi (2^m - 1) / (2^m lambda_max) (lambda_max on the top grid value);
+    grid value of clock k: lt_k = 2 pi k / (t 2^m); default C = the largest grid value not above
+    lambda_min (at least one grid step); theta_k = 2 asin(C / lt_k), clamped to pi where
+    C / lt_k > 1, and theta_0 = 0;
+  * padding to 2^nb: block-diag(A, lambda_max I), b padded with zeros;
+  * readout: P = P(ancilla = 1); P0 = P(ancilla = 1 and clock = 0); |x> is the
+    (ancilla = 1, clock = 0) slice divided by sqrt(P0); ||x|| = sqrt(P) / C (the printed
+    ||x|| = |lambda_0| sqrt(P) holds when C = |lambda_0|); x = ||x|| ||b|| |x>;
+  * n_total counts the ancilla, and Table I's n_QPE column includes the sign qubit n_negval.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import core
+
+# ---------------------------------------------------------------- textbook gate matrices
+SQRT1_2 = 1.0 / math.sqrt(2.0)
+H = np.array([[SQRT1_2, SQRT1_2], [SQRT1_2, -SQRT1_2]], dtype=np.complex128)
+SWAP = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=np.complex128)
+
+
+def RY(theta: float) -> np.ndarray:
+    c, s = math.cos(theta / 2), math.sin(theta / 2)
+    return np.array([[c, -s], [s, c]], dtype=np.complex128)
+
+
+def CP(phi: float) -> np.ndarray:
+    """Controlled phase on two qubits: diag(1, 1, 1, e^{i phi})."""
+    return np.diag([1, 1, 1, np.exp(1j * phi)]).astype(np.complex128)
+
+
+# A gate of the unfused list: ("u", targets, U, controls, ctrl_vals) or
+# ("ucry", target, controls, thetas).
+
+
+def qft_gates(qubits, inverse: bool):
+    """QFT |x> = 2^{-m/2} sum_k exp(2 pi i x k / 2^m) |k> on `qubits` (qubits[j] = bit j).
+
+    Textbook circuit (Nielsen & Chuang Sec. 5.1) for the most significant qubit first: H on a
+    qubit, then controlled phases 2 pi / 2^(d+1) from each lower qubit at distance d, and the
+    bit-reversal swaps at the end.  The inverse is the reversed sequence with conjugate phases.
+    """
+    m = len(qubits)
+    seq = []
+    for j in range(m - 1, -1, -1):
+        seq.append(("u", [qubits[j]], H, [], []))
+        for l in range(j - 1, -1, -1):
+            seq.append(("u", [qubits[l], qubits[j]], CP(2 * math.pi / 2 ** (j - l + 1)), [], []))
+    for j in range(m // 2):
+        seq.append(("u", [qubits[j], qubits[m - 1 - j]], SWAP, [], []))
+    if not inverse:
+        return seq
+    out = []
+    for g in reversed(seq):
+        out.append(("u", g[1], g[2].conj().T, [], []))
+    return out
+
+
+def resource_counts(n_rows: int, kappa: float, has_negative: bool):
+    """Sec. III-B qubit count, with Table I's conventions (ancilla counted, sign qubit in n_QPE).
+
+    Returns (n_total, n_data, n_qpe_table)."""
+    n_data = int(math.ceil(math.log2(n_rows))) if n_rows > 1 else 1
+    n_qpe = max(n_data + 1, int(math.ceil(math.log2(kappa + 1))))
+    n_neg = 1 if has_negative else 0
+    return n_data + n_qpe + n_neg + 1, n_data, n_qpe + n_neg
+
+
+def check_problem(A: np.ndarray, b: np.ndarray):
+    A = np.asarray(A, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128).ravel()
+    N = A.shape[0]
+    if A.shape != (N, N) or b.size != N or N < 1:
+        raise ValueError("shape")
+    if not (np.all(np.isfinite(A)) and np.all(np.isfinite(b))):
+        raise ValueError("non-finite input")
+    scale = max(1.0, float(np.max(np.abs(A))))
+    if np.max(np.abs(A - A.conj().T)) > 1e-12 * scale:
+        raise ValueError("A is not Hermitian")
+    if np.linalg.norm(b) == 0:
+        raise ValueError("b = 0")
+    return A, b
+
+
+def build(A, b, m: int, t: float = 0.0, C: float = 0.0):
+    """Step 1 and 2 of the procedure: normalize b, pad, and emit the unfused HHL gate list."""
+    A, b = check_problem(A, b)
+    N = A.shape[0]
+    bnorm = float(np.linalg.norm(b))
+    bhat = b / bnorm
+    nb = max(1, int(math.ceil(math.log2(N))))
+    lam_A = np.linalg.eigvalsh(A)
+    if lam_A[0] <= 0:
+        raise ValueError("A must be positive definite")
+    lam_max = float(lam_A[-1])
+    D = 1 << nb
+    Ap = np.zeros((D, D), dtype=np.complex128)
+    Ap[:N, :N] = A
+    for i in range(N, D):
+        Ap[i, i] = lam_max
+    bp = np.zeros(D, dtype=np.complex128)
+    bp[:N] = bhat
+    lam, V = np.linalg.eigh(Ap)
+    if m <= 0:
+        kappa = float(lam_A[-1] / lam_A[0])
+        m = resource_counts(N, kappa, False)[2]
+    M = 1 << m
+    if t <= 0:
+        t = 2 * math.pi * (M - 1) / (M * lam_max)
+    step = 2 * math.pi / (t * M)              # grid value of clock k is k * step
+    lam_min = float(lam[0])
+    if C <= 0:
+        C = max(1.0, math.floor(lam_min / step * (1 + 1e-9))) * step
+    elif C > lam_min * (1 + 1e-9):
+        raise ValueError("C above the smallest eigenvalue")
+    k = np.arange(M, dtype=np.float64)
+    theta = np.zeros(M)
+    with np.errstate(divide="ignore"):
+        r = np.where(k > 0, C / np.where(k > 0, k * step, 1.0), 0.0)
+    theta[1:] = 2.0 * np.arcsin(np.minimum(r[1:], 1.0))
+
+    data = list(range(nb))
+    clock = [nb + j for j in range(m)]
+    anc = nb + m
+    gates = []
+    qpe = []
+    for q in clock:
+        qpe.append(("u", [q], H, [], []))
+    for j in range(m):
+        Uj = (V * np.exp(1j * lam * t * 2 ** j)) @ V.conj().T
+        qpe.append(("u", data, Uj, [clock[j]], [1]))
+    qpe += qft_gates(clock, inverse=True)
+    gates += qpe
+    gates.append(("ucry", anc, clock, theta))
+    for g in reversed(qpe):
+        gates.append(("u", g[1], g[2].conj().T, g[3], g[4]))
+    return dict(N=N, nb=nb, m=m, n=nb + m + 1, t=t, C=C, bnorm=bnorm, b_pad=bp, gates=gates,
+                theta=theta, lam=lam)
+
+
+def initial_state(h) -> np.ndarray:
+    """|0>_anc |0>_clock |b>: the normalized, padded b in the lowest 2^nb amplitudes."""
+    psi = np.zeros(1 << h["n"], dtype=np.complex128)
+    psi[: 1 << h["nb"]] = h["b_pad"]
+    return psi
+
+
+def run(h, psi: np.ndarray | None = None) -> np.ndarray:
+    """Apply every gate of the unfused list in order (step 2), from the initial state."""
+    if psi is None:
+        psi = initial_state(h)
+    for g in h["gates"]:
+        if g[0] == "u":
+            core.apply_gate(psi, g[1], g[2], g[3], g[4])
+        else:
+            core.apply_ucry(psi, g[1], g[2], g[3])
+    return psi
+
+
+def readout(h, psi: np.ndarray):
+    """Steps 3-4: read |x>, P(ancilla = 1) and the solution x from the final state."""
+    nb, m = h["nb"], h["m"]
+    anc_bit = 1 << (nb + m)
+    clock_mask = ((1 << m) - 1) << nb
+    norm2 = core.masked_norm2(psi, 0, 0)
+    P = core.masked_norm2(psi, anc_bit, anc_bit)
+    P0 = core.masked_norm2(psi, anc_bit | clock_mask, anc_bit)
+    sl = psi[anc_bit: anc_bit + (1 << nb)].copy()
+    x_state = sl / math.sqrt(P0)
+    norm_x = math.sqrt(P) / h["C"]
+    x = norm_x * h["bnorm"] * x_state[: h["N"]]
+    return dict(x=x, x_state=x_state, P=P, P0=P0, leakage=P - P0, norm2=norm2, norm_x=norm_x)
+
+
+def solve(A, b, m: int, t: float = 0.0, C: float = 0.0):
+    h = build(A, b, m, t, C)
+    psi = run(h)
+    r = readout(h, psi)
+    r["psi"] = psi
+    r["circuit"] = h
+    return r
+
+
+def classical_solution(A, b) -> np.ndarray:
+    return np.linalg.solve(np.asarray(A, dtype=np.complex128), np.asarray(b, dtype=np.complex128))

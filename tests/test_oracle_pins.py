@@ -1,0 +1,258 @@
+"""Pins of the FP64 oracle against things other than itself (no GPU needed).
+
+  * gate rule          -> brute-force full 2^n x 2^n operator built from Kronecker products
+  * UCRY               -> brute-force block-diagonal operator
+  * QFT / inverse QFT  -> numpy's FFT (the DFT up to normalisation)
+  * QPE                -> an eigenvector whose phase lies on the clock grid lands on exactly |k>
+  * HHL (exact grid)   -> the postselected slice equals A^-1 b / ||A^-1 b||, P = C^2 ||A^-1 b||^2,
+                          no leakage, and x = A^-1 b (Sec. III-A)
+  * resource formula   -> the qubit counts printed in Table I (tests/golden)
+  * compensated sums   -> math.fsum (exactly rounded)
+Two mutation tests plant a plausible mistake in the oracle and check that a pin catches it.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import core, hhl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def full_operator(n, targets, U, controls=(), vals=()):
+    """2^n x 2^n operator of U on `targets` controlled on `controls` == `vals`, built as
+    I (x) G in a basis where the gate's qubits are the lowest bits, then permuted back."""
+    k, c = len(targets), len(controls)
+    dk = 1 << k
+    if c:
+        pv = sum(int(v) << j for j, v in enumerate(vals))
+        P = np.zeros((1 << c, 1 << c))
+        P[pv, pv] = 1.0
+        G = np.kron(P, U) + np.kron(np.eye(1 << c) - P, np.eye(dk))
+    else:
+        G = U
+    Fp = np.kron(np.eye(1 << (n - k - c)), G)
+    order = list(targets) + list(controls) + [q for q in range(n) if q not in targets and q not in controls]
+    idx = np.arange(1 << n)
+    pi = np.zeros(1 << n, dtype=np.int64)
+    for j, q in enumerate(order):
+        pi |= ((idx >> q) & 1) << j
+    return Fp[np.ix_(pi, pi)]
+
+
+def rand_state(rng, n):
+    v = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    return v / np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_gate_rule_matches_bruteforce(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(3, 9))
+    for _ in range(8):
+        k = int(rng.integers(1, min(4, n) + 1))
+        c = int(rng.integers(0, min(2, n - k) + 1))
+        qs = [int(q) for q in rng.choice(n, size=k + c, replace=False)]
+        t, ctl = qs[:k], qs[k:]
+        vals = [int(v) for v in rng.integers(0, 2, size=c)]
+        U = synth.haar_unitary(rng, 1 << k)
+        psi = rand_state(rng, n)
+        ref = full_operator(n, t, U, ctl, vals) @ psi
+        out = psi.copy()
+        core.apply_gate(out, t, U, ctl, vals)
+        assert np.max(np.abs(out - ref)) < 1e-13
+
+
+def test_ucry_matches_bruteforce():
+    rng = np.random.default_rng(11)
+    n, target, ctl = 6, 5, [1, 2, 4]
+    theta = rng.uniform(-np.pi, np.pi, size=8)
+    F = np.eye(1 << n, dtype=np.complex128)
+    for v in range(8):  # the eight controlled rotations act on disjoint subspaces
+        vals = [(v >> j) & 1 for j in range(3)]
+        F = full_operator(n, [target], hhl.RY(theta[v]), ctl, vals) @ F
+    psi = rand_state(rng, n)
+    out = psi.copy()
+    core.apply_ucry(out, target, ctl, theta)
+    assert np.max(np.abs(out - F @ psi)) < 1e-13
+
+
+def test_norm_preserved_by_random_circuit():
+    rng = np.random.default_rng(5)
+    n = 11
+    psi = rand_state(rng, n)
+    gates = 60
+    for _ in range(gates):
+        k = int(rng.integers(1, 5))
+        t = synth.random_targets(rng, n, k)
+        core.apply_gate(psi, t, synth.haar_unitary(rng, 1 << k))
+    assert abs(np.vdot(psi, psi).real - 1.0) < 1e-13 * gates
+
+
+def test_haar_unitary():
+    rng = np.random.default_rng(2)
+    for k in range(1, 7):
+        U = synth.haar_unitary(rng, 1 << k)
+        assert np.max(np.abs(U.conj().T @ U - np.eye(1 << k))) < 1e-13
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 7])
+def test_qft_matches_fft(m):
+    rng = np.random.default_rng(m)
+    psi = rand_state(rng, m)
+    fwd = psi.copy()
+    for g in hhl.qft_gates(list(range(m)), inverse=False):
+        core.apply_gate(fwd, g[1], g[2])
+    N = 1 << m
+    assert np.max(np.abs(fwd - np.fft.ifft(psi) * math.sqrt(N))) < 1e-13
+    inv = psi.copy()
+    for g in hhl.qft_gates(list(range(m)), inverse=True):
+        core.apply_gate(inv, g[1], g[2])
+    assert np.max(np.abs(inv - np.fft.fft(psi) / math.sqrt(N))) < 1e-13
+
+
+def test_qft_on_embedded_register():
+    # register on qubits 2,4,5 of a 6-qubit state, others spectators
+    rng = np.random.default_rng(9)
+    reg = [2, 4, 5]
+    psi = rand_state(rng, 6)
+    out = psi.copy()
+    for g in hhl.qft_gates(reg, inverse=True):
+        core.apply_gate(out, g[1], g[2])
+    # reference: reshape so the register value is an axis, FFT along it
+    idx = np.arange(64)
+    val = sum(((idx >> q) & 1) << j for j, q in enumerate(reg))
+    rest = idx & ~sum(1 << q for q in reg)
+    ref = np.zeros_like(psi)
+    for r in np.unique(rest):
+        sel = np.where(rest == r)[0]
+        order = sel[np.argsort(val[sel])]
+        ref[order] = np.fft.fft(psi[order]) / math.sqrt(8)
+    assert np.max(np.abs(out - ref)) < 1e-13
+
+
+def _grid_problem(seed, N, m, complex_vectors=False):
+    rng = np.random.default_rng(seed)
+    top = 2 ** m - 1
+    k = np.sort(rng.integers(1, top + 1, size=N)).astype(float)
+    k[-1] = top
+    if complex_vectors:
+        V = synth.haar_unitary(rng, N)
+    else:
+        V, _ = np.linalg.qr(rng.standard_normal((N, N)))
+    A = (V * k) @ V.conj().T
+    A = 0.5 * (A + A.conj().T)
+    b = rng.standard_normal(N) + (1j * rng.standard_normal(N) if complex_vectors else 0)
+    return A, b, k, V
+
+
+def test_qpe_exact_on_grid_eigenvector():
+    m, N = 5, 4
+    A, _, k, V = _grid_problem(3, N, m)
+    for i in range(N):
+        h = hhl.build(A, V[:, i], m, t=2 * math.pi / 2 ** m)
+        qpe = []
+        for g in h["gates"]:
+            if g[0] == "ucry":
+                break
+            qpe.append(g)
+        psi = hhl.initial_state(h)
+        for g in qpe:
+            core.apply_gate(psi, g[1], g[2], g[3], g[4])
+        nb = h["nb"]
+        clock_val = int(round(k[i]))
+        sl = psi[clock_val << nb: (clock_val << nb) + (1 << nb)]
+        assert abs(np.linalg.norm(sl) - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("m,N,cplx,seed", [(3, 2, False, 0), (4, 4, False, 1), (5, 3, False, 2),
+                                           (6, 5, True, 3), (7, 8, True, 4), (8, 4, False, 5)])
+def test_hhl_exact_grid(m, N, cplx, seed):
+    A, b, k, V = _grid_problem(seed, N, m, cplx)
+    r = hhl.solve(A, b, m, t=2 * math.pi / 2 ** m)
+    xt = np.linalg.solve(A, b)
+    bh = b / np.linalg.norm(b)
+    y = np.linalg.solve(A, bh)
+    C = r["circuit"]["C"]
+    assert abs(C - k[0]) < 1e-9
+    assert np.max(np.abs(r["x_state"][:N] - y / np.linalg.norm(y))) < 1e-12
+    assert abs(r["P"] - C ** 2 * np.vdot(y, y).real) < 1e-12
+    assert abs(r["leakage"]) < 1e-14
+    assert abs(r["norm_x"] - np.linalg.norm(y)) < 1e-12 * np.linalg.norm(y)
+    assert np.max(np.abs(r["x"] - xt)) < 1e-11 * np.linalg.norm(xt)
+    assert abs(r["norm2"] - 1.0) < 1e-12
+
+
+def test_hhl_padding_gives_zero_tail():
+    A, b, _, _ = _grid_problem(7, 3, 5)
+    r = hhl.solve(A, b, 5, t=2 * math.pi / 32)
+    assert r["circuit"]["nb"] == 2
+    assert abs(r["x_state"][3]) < 1e-13
+    assert np.max(np.abs(r["x"] - np.linalg.solve(A, b))) < 1e-11
+
+
+def test_hhl7_problem_exact():
+    p = synth.hhl7_problem()
+    r = hhl.solve(p["A"], p["b"], p["m"], p["t"], p["C"])
+    xt = np.linalg.solve(p["A"], p["b"])
+    assert np.max(np.abs(r["x"] - xt)) < 1e-12 * np.linalg.norm(xt)
+    assert r["circuit"]["n"] == 7
+
+
+def test_resource_formula_matches_table1():
+    rows = []
+    with open(os.path.join(GOLDEN, "table1_resources.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append(line.split())
+    assert len(rows) == 3
+    for name, nrows, kappa, neg, n_total, n_data, n_qpe in rows:
+        got = hhl.resource_counts(int(nrows), float(kappa), bool(int(neg)))
+        assert got == (int(n_total), int(n_data), int(n_qpe)), name
+
+
+def test_compensated_sum_vs_fsum():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(10000) * 1e8, rng.standard_normal(10000),
+                        -rng.standard_normal(10000) * 1e8])
+    rng.shuffle(x)
+    assert abs(core.compensated_sum(x) - math.fsum(x)) <= 1e-16 * np.sum(np.abs(x))
+    psi = rand_state(rng, 10)
+    sq = np.concatenate([psi.real ** 2, psi.imag ** 2])
+    assert abs(core.masked_norm2(psi, 0, 0) - math.fsum(sq)) < 1e-15
+
+
+# ---------------------------------------------------------------- planted mistakes
+def test_planted_missing_swaps_is_caught(monkeypatch):
+    orig = hhl.qft_gates
+
+    def no_swaps(qubits, inverse):
+        return [g for g in orig(qubits, inverse) if not (len(g[1]) == 2 and np.allclose(g[2], hhl.SWAP))]
+
+    monkeypatch.setattr(hhl, "qft_gates", no_swaps)
+    psi = rand_state(np.random.default_rng(1), 4)
+    out = psi.copy()
+    for g in hhl.qft_gates(list(range(4)), inverse=False):
+        core.apply_gate(out, g[1], g[2])
+    assert np.max(np.abs(out - np.fft.ifft(psi) * 4.0)) > 1e-3
+
+
+def test_planted_wrong_evolution_sign_is_caught(monkeypatch):
+    A, b, _, _ = _grid_problem(1, 4, 4)
+    orig_build = hhl.build
+
+    def conj_build(*args, **kw):
+        h = orig_build(*args, **kw)
+        # plant: controlled evolutions become exp(-iAt) (complex conjugate for real A)
+        h["gates"] = [("u", g[1], g[2].conj(), g[3], g[4]) if g[0] == "u" and g[3] else g
+                      for g in h["gates"]]
+        return h
+
+    monkeypatch.setattr(hhl, "build", conj_build)
+    r = hhl.solve(A, b, 4, t=2 * math.pi / 16)
+    y = np.linalg.solve(A, b / np.linalg.norm(b))
+    err = np.max(np.abs(r["x_state"][:4] - y / np.linalg.norm(y))) if r["P0"] > 1e-30 else 1.0
+    assert err > 1e-3 or abs(r["leakage"]) > 1e-3
