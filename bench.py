@@ -1,0 +1,383 @@
+"""Benchmark of the GB300 HHL state-vector simulator.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
+
+Default workload ("gates"): the gate-apply microbenchmark on a 31-qubit complex64 state
+(16 GiB): 200 Haar-random 2^k x 2^k unitaries for each k in 1..6 on uniformly random distinct
+targets (1200 gates), initial state a seeded complex Gaussian, normalized.  One step applies
+the 1200 gates in order through the C ABI (one qsim_apply per gate).  The metric is the
+algorithmic HBM bandwidth of gate application, 2 x 8 bytes x 2^31 per gate, divided by the
+step time (inputs far larger than L2, so no flush is needed).
+
+Other workloads (one JSON line each): "gates-c128" (30-qubit complex128 state, same gates),
+"hhl7" (7-qubit exact-grid HHL, complex128, solves/s and latency), "hhl27" (27-qubit
+precision-form HHL: complex64 vs complex128, solves/s and error vs the oracle).
+
+Multi-GPU (torchrun): every rank runs the same workload on its own GPU (independent replicas,
+no collective on the data path); value = work of all ranks / max over ranks of the time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+
+# ------------------------------------------------------------------------------ helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("bf16_tflops", 1946.5)), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def dist_setup(gpus: int):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------ oracle baseline
+def oracle_gate_sample(seed: int, n_sample: int = 24, per_k: int = 1):
+    """The oracle (FP64, OpenMP over the host cores) on a bounded sample of the gate
+    workload: `per_k` Haar gates per k = 1..6 on an n_sample-qubit complex128 state."""
+    from oracle import core as ocore
+    gates = synth.gate_microbench_list(seed, n_sample, per_k=per_k)
+    psi = synth.gaussian_state_np(seed, n_sample)
+    t0 = time.perf_counter()
+    for t, U in gates:
+        ocore.apply_gate(psi, t, U)
+    dt = time.perf_counter() - t0
+    byts = len(gates) * 2 * 16 * (1 << n_sample)
+    return {"value": byts / dt / 1e9, "unit": "GB/s", "cores": ocore.num_threads(),
+            "kind": "oracle", "seconds": dt,
+            "sample": "%d Haar gate(s) per k=1..6 on a %d-qubit complex128 state (FP64 oracle, "
+                      "algorithmic bytes 2x16x2^n per gate; GB/s is independent of n for this "
+                      "streaming rule)" % (per_k, n_sample)}
+
+
+# ------------------------------------------------------------------------- gate workload
+def run_gates(args, ws, rank, dtype_name):
+    import torch
+    import paper_2402_08136_gb300 as qs
+
+    dtype = torch.complex64 if dtype_name == "c64" else torch.complex128
+    n = args.n or (31 if dtype_name == "c64" else 30)
+    S = 8 if dtype_name == "c64" else 16
+    seed = 2402
+    gates = synth.gate_microbench_list(seed, n, per_k=args.per_k)
+    circs = [qs.Circuit(n).add_gate(t, U) for t, U in gates]
+    ks = [len(t) for t, _ in gates]
+    st = synth.gaussian_state_torch(seed, n, dtype, "cuda", normalize=True)
+    stream = torch.cuda.current_stream()
+    bytes_per_gate = 2.0 * S * (1 << n)
+    step_bytes = bytes_per_gate * len(gates)
+
+    def step(evs=None):
+        for i, c in enumerate(circs):
+            if evs is not None:
+                evs[i][0].record(stream)
+            qs.qsim_apply(st, c, stream)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in circs] for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_start.record(stream)
+        for s in range(args.steps):
+            step(evs[s])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    ms_total = t_start.elapsed_time(t_end)
+    ms_total = max_over_ranks(ws, ms_total)
+    ms_step = ms_total / args.steps
+    value = ws * step_bytes * args.steps / (ms_total / 1e3) / 1e9
+    durs = np.array([[a.elapsed_time(b) for a, b in row] for row in evs])  # ms
+    per_k = {}
+    for k in sorted(set(ks)):
+        sel = [i for i, kk in enumerate(ks) if kk == k]
+        d = durs[:, sel].mean()
+        per_k[str(k)] = {"ms_per_gate": round(float(d), 4),
+                         "gbs": round(bytes_per_gate / (d / 1e3) / 1e9, 1)}
+    hbm, _, peak_kind = measured_peaks()
+    mean_launch = float(durs.mean())
+    achieved = bytes_per_gate / (mean_launch / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "dense_tile_kernel", "achieved": round(achieved, 1),
+                "peak": hbm, "peak_kind": peak_kind + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                "bytes_per_launch": bytes_per_gate}
+
+    # end to end through the public API from pinned host memory
+    host_in = synth.gaussian_state_torch(seed, n, dtype, "cpu", chunk=1 << 22, normalize=True) \
+        if args.e2e_from_host_gen else st.cpu()
+    host_in = host_in.pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_steps = args.steps
+
+    def e2e_step():
+        st.copy_(host_in, non_blocking=True)
+        step()
+        host_out.copy_(st, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(ws, a.elapsed_time(b))
+    e2e_val = ws * step_bytes * e2e_steps / (e2e_ms / 1e3) / 1e9
+    nbytes = host_in.numel() * host_in.element_size()
+    return {
+        "metric": "gate-apply HBM GB/s (algorithmic, 2 x bytes/amp x 2^n per gate)",
+        "value": round(value, 1), "unit": "GB/s", "ms_per_step": round(ms_step, 2),
+        "higher_is_better": True, "dtype": dtype_name,
+        "config": {"workload": "gate-apply microbenchmark: %d-qubit %s state, %d Haar gates per "
+                               "k=1..6 on random distinct targets" % (n, "complex64" if S == 8
+                                                                       else "complex128", args.per_k),
+                   "n_qubits": n, "gates_per_step": len(gates), "state_bytes": S << n,
+                   "l2": "inputs larger than L2 (state %d GiB vs 129 MB L2)" % ((S << n) >> 30),
+                   "seed": seed},
+        "per_k": per_k, "roofline": roofline,
+        "e2e": {"value": round(e2e_val, 1), "unit": "GB/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": len(circs) * args.steps,
+        "clocks": clk.summary(),
+    }
+
+
+# -------------------------------------------------------------------------- HHL workloads
+def run_hhl(args, ws, rank, which):
+    import torch
+    import paper_2402_08136_gb300 as qs
+
+    if which == "hhl7":
+        p = synth.hhl7_problem()
+        dtypes = [("c128", torch.complex128)]
+        max_k = args.max_k or 4
+    else:
+        p = synth.hhl27_problem()
+        dtypes = [("c64", torch.complex64), ("c128", torch.complex128)]
+        max_k = args.max_k or 4
+    h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"])
+    info = h.info()
+    n = info["n"]
+    circ = qs.qsim_fuse(h.as_circuit(), max_k)
+    ci = circ.info()
+    xt = np.linalg.solve(p["A"], p["b"])
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, dt in dtypes:
+        st = torch.empty(1 << n, dtype=dt, device="cuda")
+
+        def solve():
+            qs.hhl_prepare_state(st, h, stream)
+            qs.qsim_apply(st, circ, stream, n_qubits=n)
+            return qs.hhl_readout(st, h, stream)
+
+        for _ in range(args.warmup):
+            solve()
+        torch.cuda.synchronize()
+        lat = []
+        barrier(ws)
+        t0 = time.perf_counter()
+        reps = args.steps * (200 if which == "hhl7" else 1)
+        for _ in range(reps):
+            a = time.perf_counter()
+            r = solve()
+            lat.append(time.perf_counter() - a)
+        torch.cuda.synchronize()
+        dt_s = max_over_ranks(ws, time.perf_counter() - t0)
+        rel = float(np.linalg.norm(r["x"] - xt) / np.linalg.norm(xt))
+        res[name] = {"solves_per_s": ws * reps / dt_s, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                     "p99_ms": 1e3 * float(np.percentile(lat, 99)), "rel_err_vs_classical": rel,
+                     "p_success": r["p_success"], "leakage": r["leakage"]}
+        del st
+    main = res[dtypes[0][0]]
+    return {
+        "metric": "HHL solves/s", "value": round(main["solves_per_s"], 3), "unit": "solves/s",
+        "ms_per_step": round(1e3 / main["solves_per_s"], 3), "higher_is_better": True,
+        "dtype": dtypes[0][0],
+        "config": {"workload": which, "n_qubits": n, "nb": info["nb"], "m": info["m"],
+                   "fused_ops": ci["n_gates"], "unfused_gates": info["n_gates"], "max_k": max_k},
+        "paths": res,
+        "gpu_launches": None,
+    }
+
+
+# ---------------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gates",
+                    choices=["gates", "gates-c128", "hhl7", "hhl27"])
+    ap.add_argument("--n", type=int, default=0, help="override qubit count (gates workloads)")
+    ap.add_argument("--per-k", type=int, default=200)
+    ap.add_argument("--max-k", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-from-host-gen", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    if args.impl == "reference":
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return
+        vals = []
+        for _ in range(args.warmup):
+            oracle_gate_sample(2402)
+        for _ in range(args.steps):
+            vals.append(oracle_gate_sample(2402))
+        v = sum(x["value"] for x in vals) / len(vals)
+        cb = dict(vals[-1])
+        cb["value"] = round(v, 3)
+        line = {"impl": "reference", "metric": "gate-apply HBM GB/s (algorithmic, 2 x bytes/amp x 2^n per gate)",
+                "value": round(v, 3), "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(1e3 * cb["seconds"], 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": "gate-apply microbenchmark (bounded "
+                                                            "oracle sample)"},
+                "cpu_baseline": cb,
+                "e2e": {"value": round(v, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    from paper_2402_08136_gb300 import build as qbuild
+    qbuild.build()
+    ws, rank, local = dist_setup(args.gpus)
+    if args.workload in ("gates", "gates-c128"):
+        out = run_gates(args, ws, rank, "c64" if args.workload == "gates" else "c128")
+    else:
+        out = run_hhl(args, ws, rank, args.workload)
+    line = {"metric": out.pop("metric"), "value": out.pop("value"), "unit": out.pop("unit"),
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out.pop("ms_per_step"), "higher_is_better": out.pop("higher_is_better"),
+            "scaling": "weak", "vs_baseline": None, "dtype": out.pop("dtype"), "data": "synthetic",
+            "config": dict(out.pop("config"), parallelism="replicas x%d" % ws)}
+    line.update(out)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_gate_sample(2402)
+    if rank == 0:
+        print(json.dumps(line))
+    barrier(ws)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

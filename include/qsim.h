@@ -1,0 +1,199 @@
+/*
+ * qsim.h -- C ABI of the GB300 HHL state-vector simulation library (libqsim_gb300.so).
+ *
+ * Zheng, Chen, Yang & Li, "Early Exploration of a Flexible Framework for Efficient Quantum
+ * Linear Solvers in Power Systems" (PESGM 2024).  The library implements the data-parallel
+ * core of the paper's method: build the HHL circuit for A x = b (Sec. III-A, Fig. 5), fuse its
+ * gates (Sec. II-C, Fig. 4), apply them to a 2^n-amplitude state vector on the GPU (the
+ * "unitary evolution of the state", Sec. II-C), and read the solution out of the final state
+ * (Sec. III-A, steps 3-4).
+ *
+ * Conventions used by every call
+ *   - Qubit q is bit q of the amplitude index (little-endian).
+ *   - A k-qubit gate matrix is 2^k x 2^k, row-major, complex as interleaved (re, im) doubles;
+ *     bit b of its row/column index is the value of qubit targets[b].
+ *   - State vectors are device buffers of 2^n complex amplitudes, interleaved (re, im):
+ *     QSIM_C64 = 2 x float (8 bytes per amplitude), QSIM_C128 = 2 x double (16 bytes).
+ *     They are owned by the caller (e.g. a torch tensor); the library never frees them.
+ *   - A `stream` argument is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls documented as asynchronous only enqueue work on that stream.
+ *   - Host inputs are read only during the call.  Objects returned through `**out` are owned by
+ *     the library and released with the matching *_free / *_destroy call.
+ *   - Every call returns QSIM_OK (0) or a negative status; it never aborts or exits.  The text
+ *     of the last error on the calling thread is returned by qsim_last_error().
+ *
+ * HHL register layout (used by hhl_* calls): data qubits 0..nb-1, clock qubit j is qubit nb+j
+ * (bit j of the clock value), the ancilla is qubit nb+m; n = nb + m + 1.
+ */
+#ifndef QSIM_GB300_H
+#define QSIM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define QSIM_OK 0
+#define QSIM_EINVAL (-1)   /* bad argument: shape, range, non-finite, non-Hermitian, ...      */
+#define QSIM_ENOMEM (-2)   /* host or device allocation failed                                 */
+#define QSIM_EBUSY (-3)    /* pool: request not finished yet / memory budget exhausted         */
+#define QSIM_ECUDA (-4)    /* a CUDA runtime call failed (message names it)                   */
+#define QSIM_ETIMEOUT (-5) /* a bounded wait ran out                                           */
+#define QSIM_ENOTFOUND (-6) /* pool: unknown ticket                                            */
+
+/* ---- state dtypes ---------------------------------------------------------------------- */
+#define QSIM_C64 1  /* complex64: FP32 state; gate arithmetic FP32 (dense k>=4 on tensor cores) */
+#define QSIM_C128 2 /* complex128: FP64 state and FP64 gate arithmetic                          */
+
+typedef struct qsim_circuit qsim_circuit; /* gate list (unfused or fused)                       */
+typedef struct hhl_circuit hhl_circuit;   /* HHL problem + its unfused gate list                */
+typedef struct qsim_pool qsim_pool;       /* serving pool (device memory budget + worker)       */
+
+/* Thread-local text of the last error (empty string if none).  Never NULL. */
+const char *qsim_last_error(void);
+
+/* Library version string, e.g. "0.1.0 sm_103a". */
+const char *qsim_version(void);
+
+/* ======================================================================================= *
+ * Circuits                                                                                 *
+ * ======================================================================================= */
+
+/* New empty circuit on n_qubits (1..34).  Errors: EINVAL, ENOMEM. */
+int qsim_circuit_create(int n_qubits, qsim_circuit **out);
+
+/* Append a k-qubit gate U (1 <= k <= 7), applied only where every controls[j] qubit is 1.
+ * targets[0..k-1] and controls[0..n_controls-1] must be distinct and < n_qubits.  U is
+ * 2^k x 2^k complex (interleaved doubles, row-major, see conventions); it is copied.
+ * A gate that is a unitary product of 1- and 2-qubit gates is the unit of the paper's
+ * "gate" (Sec. II-C); unitarity is not checked.  Errors: EINVAL (ranges, repeats, NaN). */
+int qsim_circuit_add_gate(qsim_circuit *c, int k, const int *targets, int n_controls,
+                          const int *controls, const double *U);
+
+/* Append a uniformly controlled RY: for every value v of the control register (controls[j]
+ * is bit j of v, 1 <= n_controls <= 30), rotate `target` by RY(theta[v]) =
+ * [[cos theta/2, -sin theta/2], [sin theta/2, cos theta/2]].  This is the HHL eigenvalue-
+ * inversion rotation (Sec. III-A, Fig. 5).  theta has 2^n_controls entries (copied).
+ * Errors: EINVAL. */
+int qsim_circuit_add_ucry(qsim_circuit *c, int target, int n_controls, const int *controls,
+                          const double *theta);
+
+/* Release a circuit and any device copy of its matrices.  NULL is a no-op. */
+void qsim_circuit_free(qsim_circuit *c);
+
+/* Counts describing a circuit. */
+typedef struct {
+    int n_qubits;
+    int n_gates;        /* entries in the list (fused: executed operations)                  */
+    int n_dense;        /* dense operations (after fusion: 2^k x 2^k products)               */
+    int n_diag;         /* diagonal / phase operations                                        */
+    int n_perm;         /* permutation operations (swaps)                                     */
+    int n_ucry;         /* uniformly controlled rotations                                     */
+    int max_k;          /* widest dense operation (targets)                                   */
+    int fused;          /* 1 if produced by qsim_fuse                                          */
+    double bytes_c64;   /* algorithmic HBM bytes of one application to a complex64 state     */
+    double bytes_c128;  /* same for complex128                                                */
+    double flops;       /* algorithmic real flops of one application                          */
+} qsim_circuit_info;
+
+int qsim_circuit_get_info(const qsim_circuit *c, qsim_circuit_info *out);
+
+/* ======================================================================================= *
+ * Fusion (Sec. II-C, Fig. 4)                                                               *
+ * ======================================================================================= */
+
+/* Fuse `in` into a new circuit whose dense operations act on at most max_k qubits
+ * (1 <= max_k <= 6; 0 picks the width tuned for this GPU and dtype QSIM_C64).  Uncontrolled
+ * gates are merged greedily in circuit order (a gate joins the latest block that touches any
+ * of its qubits when the union stays within max_k, which for max_k = 2 realises the paper's
+ * four strategies: 1q+1q, 1q into 2q before and after, 2q+2q); each product is multiplied
+ * once on the host in FP64.  Controlled multi-target gates and uniformly controlled rotations
+ * are kept as they are.  Fused blocks that are exactly diagonal, single-phase or swaps are
+ * tagged so the specialised kernels run them.  The fused circuit is equal to the input up to
+ * FP64 rounding.  Errors: EINVAL, ENOMEM. */
+int qsim_fuse(const qsim_circuit *in, int max_k, qsim_circuit **out);
+
+/* ======================================================================================= *
+ * Application (the hot loop)                                                               *
+ * ======================================================================================= */
+
+/* Apply every operation of `c` in order to `state` (device, 2^n_qubits amplitudes of `dtype`,
+ * n_qubits == the circuit's qubit count), asynchronously on `stream`.  The first call for a
+ * circuit and dtype uploads its matrices to the device (synchronously) and keeps them until
+ * qsim_circuit_free.  Errors: EINVAL (size/dtype mismatch, NULL), ENOMEM, ECUDA. */
+int qsim_apply(void *state, int n_qubits, int dtype, const qsim_circuit *c, void *stream);
+
+/* ======================================================================================= *
+ * HHL (Sec. III-A procedure, Fig. 5 circuit, Sec. III-B resources)                         *
+ * ======================================================================================= */
+
+/* Build the HHL circuit for A x = b.
+ *   A: N x N complex (interleaved, row-major), Hermitian to 1e-12 * max|A_ij| and positive
+ *      definite; b: N complex (not necessarily normalized, nonzero).
+ *   n_clock: clock qubits m (1..26); <= 0 uses the Sec. III-B formula
+ *            max(n_data + 1, ceil(log2(kappa + 1))).
+ *   t: evolution time; <= 0 picks t = 2 pi (2^m - 1) / (2^m lambda_max).
+ *   C: inversion constant; <= 0 picks the largest clock grid value 2 pi k / (t 2^m) not above
+ *      lambda_min (at least one grid step); a given C above lambda_min is EINVAL.
+ * Steps: normalize b (record ||b||), pad to 2^nb with block-diag(A, lambda_max I) and zeros in
+ * b, eigendecompose on the host (complex Jacobi, FP64), and emit: H on each clock qubit,
+ * clock j controls U_j = V diag(exp(i lambda t 2^j)) V^H on the data qubits, the inverse QFT
+ * (with bit-reversal swaps) on the clock, the uniformly controlled RY with
+ * theta_k = 2 asin(min(1, C / (2 pi k / (t 2^m)))) (theta_0 = 0) on the ancilla, then the
+ * inverse of the phase estimation.  Errors: EINVAL, ENOMEM. */
+int hhl_build(const double *A, const double *b, int N, int n_clock, double t, double C,
+              hhl_circuit **out);
+
+/* Same as hhl_build from a given spectral decomposition A = V diag(lambda) V^H:
+ * lambda: N real eigenvalues (all > 0); V: N x N complex unitary (interleaved, row-major,
+ * column i is the eigenvector of lambda[i]).  Used when the spectrum is known exactly. */
+int hhl_build_spectral(const double *lambda, const double *V, const double *b, int N,
+                       int n_clock, double t, double C, hhl_circuit **out);
+
+void hhl_circuit_free(hhl_circuit *h);
+
+/* Borrowed view of the HHL gate list as a circuit (valid until hhl_circuit_free). */
+const qsim_circuit *hhl_as_circuit(const hhl_circuit *h);
+
+typedef struct {
+    int N, nb, m, n;     /* system size, data / clock / total qubits                         */
+    double t, C;         /* evolution time and inversion constant used                        */
+    double norm_b;       /* ||b||                                                              */
+    double lambda_min, lambda_max;
+    int n_total_formula; /* Sec. III-B count (data + QPE + sign + ancilla) for this A           */
+    int n_gates;         /* unfused gate count                                                */
+} hhl_info;
+
+int hhl_get_info(const hhl_circuit *h, hhl_info *out);
+
+/* Write |0>_anc |0>_clock |b/||b||> into `state` (device, 2^n amplitudes of dtype),
+ * asynchronously on `stream`.  Errors: EINVAL, ECUDA. */
+int hhl_prepare_state(void *state, int dtype, const hhl_circuit *h, void *stream);
+
+typedef struct {
+    double p_success;  /* P(ancilla = 1)                                                       */
+    double p_clock0;   /* P(ancilla = 1 and clock = 0)                                         */
+    double leakage;    /* p_success - p_clock0                                                 */
+    double norm2;      /* ||psi||^2 (should be 1)                                              */
+    double norm_x;     /* ||x|| = sqrt(p_success) / C  (Sec. III-A step 4a, with C = |lambda0|)*/
+    double norm_b;     /* ||b||                                                                */
+} hhl_readout_stats;
+
+/* Read the solution out of a final HHL state (Sec. III-A steps 3-4), FP64 reductions on the
+ * GPU for either dtype, enqueued on `stream`, then a synchronizing copy of 2^nb amplitudes
+ * and the sums to the host.  Outputs (each may be NULL):
+ *   x_out:       N complex (interleaved): x = ||x|| ||b|| |x>
+ *   x_state_out: 2^nb complex: |x> = (ancilla = 1, clock = 0 slice) / sqrt(p_clock0)
+ *   stats:       the scalars above.
+ * Uses device scratch allocated with cudaMallocAsync on `stream` and freed before return.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int hhl_readout(const void *state, int dtype, const hhl_circuit *h, void *stream, double *x_out,
+                double *x_state_out, hhl_readout_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_GB300_H */

@@ -1,0 +1,24 @@
+"""GB300-native HHL state-vector simulation (Zheng, Chen, Yang & Li, PESGM 2024).
+
+Thin Python binding of ``libqsim_gb300.so`` (C ABI in ``include/qsim.h``): argument
+marshalling only; every step of the simulation runs in the library's CUDA kernels.  PyTorch is
+used for device memory and streams.  There is no CPU fallback: if the shared library is
+missing the import of a binding raises ``QsimLibraryMissing``.
+"""
+from ._binding import (  # noqa: F401
+    QSIM_C64,
+    QSIM_C128,
+    QsimError,
+    QsimLibraryMissing,
+    Circuit,
+    HHLCircuit,
+    hhl_build,
+    hhl_build_spectral,
+    hhl_prepare_state,
+    hhl_readout,
+    library,
+    library_path,
+    qsim_apply,
+    qsim_fuse,
+    qsim_version,
+)

@@ -1,0 +1,274 @@
+"""ctypes binding of libqsim_gb300.so with the same names as the C ABI (include/qsim.h)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(HERE, "libqsim_gb300.so")
+
+QSIM_OK = 0
+QSIM_C64 = 1
+QSIM_C128 = 2
+_STATUS = {-1: "EINVAL", -2: "ENOMEM", -3: "EBUSY", -4: "ECUDA", -5: "ETIMEOUT", -6: "ENOTFOUND"}
+
+
+class QsimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (_STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class QsimLibraryMissing(ImportError):
+    pass
+
+
+class _CircuitInfo(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int), ("n_gates", ctypes.c_int), ("n_dense", ctypes.c_int),
+                ("n_diag", ctypes.c_int), ("n_perm", ctypes.c_int), ("n_ucry", ctypes.c_int),
+                ("max_k", ctypes.c_int), ("fused", ctypes.c_int), ("bytes_c64", ctypes.c_double),
+                ("bytes_c128", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+class _HHLInfo(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("nb", ctypes.c_int), ("m", ctypes.c_int), ("n", ctypes.c_int),
+                ("t", ctypes.c_double), ("C", ctypes.c_double), ("norm_b", ctypes.c_double),
+                ("lambda_min", ctypes.c_double), ("lambda_max", ctypes.c_double),
+                ("n_total_formula", ctypes.c_int), ("n_gates", ctypes.c_int)]
+
+
+class _ReadoutStats(ctypes.Structure):
+    _fields_ = [("p_success", ctypes.c_double), ("p_clock0", ctypes.c_double),
+                ("leakage", ctypes.c_double), ("norm2", ctypes.c_double),
+                ("norm_x", ctypes.c_double), ("norm_b", ctypes.c_double)]
+
+
+_lib = None
+
+_VP = ctypes.c_void_p
+_IP = ctypes.POINTER(ctypes.c_int)
+_DP = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "qsim_last_error": ([], ctypes.c_char_p),
+    "qsim_version": ([], ctypes.c_char_p),
+    "qsim_circuit_create": ([ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
+    "qsim_circuit_add_gate": ([_VP, ctypes.c_int, _IP, ctypes.c_int, _IP, _DP], ctypes.c_int),
+    "qsim_circuit_add_ucry": ([_VP, ctypes.c_int, ctypes.c_int, _IP, _DP], ctypes.c_int),
+    "qsim_circuit_free": ([_VP], None),
+    "qsim_circuit_get_info": ([_VP, ctypes.POINTER(_CircuitInfo)], ctypes.c_int),
+    "qsim_fuse": ([_VP, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
+    "qsim_apply": ([_VP, ctypes.c_int, ctypes.c_int, _VP, _VP], ctypes.c_int),
+    "hhl_build": ([_DP, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                   ctypes.POINTER(_VP)], ctypes.c_int),
+    "hhl_build_spectral": ([_DP, _DP, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                            ctypes.c_double, ctypes.POINTER(_VP)], ctypes.c_int),
+    "hhl_circuit_free": ([_VP], None),
+    "hhl_as_circuit": ([_VP], _VP),
+    "hhl_get_info": ([_VP, ctypes.POINTER(_HHLInfo)], ctypes.c_int),
+    "hhl_prepare_state": ([_VP, ctypes.c_int, _VP, _VP], ctypes.c_int),
+    "hhl_readout": ([_VP, ctypes.c_int, _VP, _VP, _DP, _DP, ctypes.POINTER(_ReadoutStats)],
+                    ctypes.c_int),
+}
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def library():
+    """Load libqsim_gb300.so (built in-tree by build.py); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise QsimLibraryMissing(
+                "libqsim_gb300.so not built: run paper_2402_08136_gb300/build.py "
+                "(there is no CPU fallback)")
+        L = ctypes.CDLL(_LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != QSIM_OK:
+        raise QsimError(rc, library().qsim_last_error().decode())
+
+
+def _ints(v):
+    a = np.ascontiguousarray(np.asarray(list(v) if len(v) else [0], dtype=np.int32))
+    return a, a.ctypes.data_as(_IP)
+
+
+def _cplx(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+    return a, a.view(np.float64).ctypes.data_as(_DP)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _dtype_of(state):
+    import torch
+    if state.dtype == torch.complex64:
+        return QSIM_C64
+    if state.dtype == torch.complex128:
+        return QSIM_C128
+    raise QsimError(-1, "state must be complex64 or complex128")
+
+
+def _check_state(state, n: int):
+    if not state.is_cuda or not state.is_contiguous() or state.numel() != (1 << n):
+        raise QsimError(-1, "state must be a contiguous CUDA tensor of 2^n amplitudes")
+
+
+def qsim_version() -> str:
+    return library().qsim_version().decode()
+
+
+class Circuit:
+    """Owning handle of a qsim_circuit (or a borrowed view when `owner` is given)."""
+
+    def __init__(self, n_qubits: int | None = None, _ptr=None, _owner=None):
+        L = library()
+        if _ptr is None:
+            p = _VP()
+            _check(L.qsim_circuit_create(int(n_qubits), ctypes.byref(p)))
+            _ptr = p
+        self._ptr = _ptr
+        self._owner = _owner
+
+    @property
+    def ptr(self):
+        return self._ptr
+
+    def add_gate(self, targets, U, controls=()):
+        t, tp = _ints(targets)
+        c, cp = _ints(controls)
+        u, up = _cplx(U)
+        k = len(targets)
+        if u.shape != (1 << k, 1 << k):
+            raise QsimError(-1, "U must be 2^k x 2^k")
+        _check(library().qsim_circuit_add_gate(self._ptr, k, tp, len(controls), cp, up))
+        return self
+
+    def add_ucry(self, target, controls, theta):
+        c, cp = _ints(controls)
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        if th.size != 1 << len(controls):
+            raise QsimError(-1, "theta must have 2^n_controls entries")
+        _check(library().qsim_circuit_add_ucry(self._ptr, int(target), len(controls), cp,
+                                               th.ctypes.data_as(_DP)))
+        return self
+
+    def info(self) -> dict:
+        s = _CircuitInfo()
+        _check(library().qsim_circuit_get_info(self._ptr, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    @property
+    def n_qubits(self) -> int:
+        return self.info()["n_qubits"]
+
+    def __del__(self):
+        if getattr(self, "_owner", None) is None and getattr(self, "_ptr", None):
+            try:
+                library().qsim_circuit_free(self._ptr)
+            except Exception:
+                pass
+            self._ptr = None
+
+
+def qsim_fuse(circuit: Circuit, max_k: int = 0) -> Circuit:
+    p = _VP()
+    _check(library().qsim_fuse(circuit.ptr, int(max_k), ctypes.byref(p)))
+    return Circuit(_ptr=p)
+
+
+def qsim_apply(state, circuit: Circuit, stream=None, n_qubits: int | None = None):
+    """Apply `circuit` to the CUDA tensor `state` in place, asynchronously on `stream`."""
+    n = circuit.n_qubits if n_qubits is None else n_qubits
+    _check_state(state, n)
+    _check(library().qsim_apply(ctypes.c_void_p(state.data_ptr()), n, _dtype_of(state),
+                                circuit.ptr, _stream_ptr(stream)))
+    return state
+
+
+class HHLCircuit:
+    def __init__(self, ptr):
+        self._ptr = ptr
+
+    @property
+    def ptr(self):
+        return self._ptr
+
+    def info(self) -> dict:
+        s = _HHLInfo()
+        _check(library().hhl_get_info(self._ptr, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def as_circuit(self) -> Circuit:
+        return Circuit(_ptr=_VP(library().hhl_as_circuit(self._ptr)), _owner=self)
+
+    def __del__(self):
+        if getattr(self, "_ptr", None):
+            try:
+                library().hhl_circuit_free(self._ptr)
+            except Exception:
+                pass
+            self._ptr = None
+
+
+def hhl_build(A, b, n_clock: int = 0, t: float = 0.0, C: float = 0.0) -> HHLCircuit:
+    Aa, Ap = _cplx(A)
+    ba, bp = _cplx(np.ravel(b))
+    N = ba.size
+    if Aa.shape != (N, N):
+        raise QsimError(-1, "A must be N x N")
+    p = _VP()
+    _check(library().hhl_build(Ap, bp, N, int(n_clock), float(t), float(C), ctypes.byref(p)))
+    return HHLCircuit(p)
+
+
+def hhl_build_spectral(lam, V, b, n_clock: int = 0, t: float = 0.0, C: float = 0.0) -> HHLCircuit:
+    la = np.ascontiguousarray(np.asarray(lam, dtype=np.float64))
+    Va, Vp = _cplx(V)
+    ba, bp = _cplx(np.ravel(b))
+    N = ba.size
+    if Va.shape != (N, N) or la.size != N:
+        raise QsimError(-1, "shape mismatch")
+    p = _VP()
+    _check(library().hhl_build_spectral(la.ctypes.data_as(_DP), Vp, bp, N, int(n_clock),
+                                        float(t), float(C), ctypes.byref(p)))
+    return HHLCircuit(p)
+
+
+def hhl_prepare_state(state, h: HHLCircuit, stream=None):
+    _check_state(state, h.info()["n"])
+    _check(library().hhl_prepare_state(ctypes.c_void_p(state.data_ptr()), _dtype_of(state), h.ptr,
+                                       _stream_ptr(stream)))
+    return state
+
+
+def hhl_readout(state, h: HHLCircuit, stream=None) -> dict:
+    """Solution readout (synchronizes the stream).  Returns x, x_state and the statistics."""
+    info = h.info()
+    _check_state(state, info["n"])
+    x = np.zeros(info["N"], dtype=np.complex128)
+    xs = np.zeros(1 << info["nb"], dtype=np.complex128)
+    st = _ReadoutStats()
+    _check(library().hhl_readout(ctypes.c_void_p(state.data_ptr()), _dtype_of(state), h.ptr,
+                                 _stream_ptr(stream), x.view(np.float64).ctypes.data_as(_DP),
+                                 xs.view(np.float64).ctypes.data_as(_DP), ctypes.byref(st)))
+    out = {f: getattr(st, f) for f, _ in st._fields_}
+    out["x"] = x
+    out["x_state"] = xs
+    return out

@@ -1,0 +1,358 @@
+// Gate lists, operation classification and gate fusion (Sec. II-C, Fig. 4 of the paper).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "common.h"
+
+namespace qsim {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+void clear_last_error() { g_last_error.clear(); }
+
+static void check_qubits(int n, const int *q, int cnt, uint64_t &seen, const char *what) {
+    for (int i = 0; i < cnt; i++) {
+        QSIM_REQUIRE(q[i] >= 0 && q[i] < n, std::string(what) + " qubit out of range");
+        QSIM_REQUIRE(!((seen >> q[i]) & 1ull), std::string(what) + " qubits must be distinct");
+        seen |= 1ull << q[i];
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Classification: a dense gate becomes the cheapest exact operation kind.
+Op classify_dense(const std::vector<int> &targets, const std::vector<int> &controls,
+                  const std::vector<cd> &U) {
+    const int k = (int)targets.size();
+    const int d = 1 << k;
+    Op op;
+    op.targets = targets;
+    op.controls = controls;
+    bool diag = true;
+    for (int r = 0; r < d && diag; r++)
+        for (int c = 0; c < d; c++)
+            if (r != c && U[(size_t)r * d + c] != cd(0.0, 0.0)) { diag = false; break; }
+    if (diag) {
+        // phase on the all-ones pattern only?
+        bool single = true;
+        for (int r = 0; r < d - 1; r++)
+            if (U[(size_t)r * d + r] != cd(1.0, 0.0)) { single = false; break; }
+        if (single) {
+            op.kind = OP_PHASE;
+            op.phase = U[(size_t)(d - 1) * d + (d - 1)];
+            // all gate qubits must be 1: merge targets into the condition set
+            op.targets.insert(op.targets.end(), controls.begin(), controls.end());
+            op.controls.clear();
+            return op;
+        }
+        op.kind = OP_DIAG;
+        op.U.resize(d);
+        for (int r = 0; r < d; r++) op.U[r] = U[(size_t)r * d + r];
+        return op;
+    }
+    if (k == 2) {  // exact SWAP matrix
+        static const double sw[16] = {1, 0, 0, 0, 0, 0, 1, 0, 0, 1, 0, 0, 0, 0, 0, 1};
+        bool is_swap = true;
+        for (int i = 0; i < 16; i++)
+            if (U[i] != cd(sw[i], 0.0)) { is_swap = false; break; }
+        if (is_swap) {
+            op.kind = OP_SWAP;
+            return op;
+        }
+    }
+    op.kind = OP_DENSE;
+    op.U = U;
+    return op;
+}
+
+void build_ops(qsim_circuit *c) {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->ops_ready) return;
+    c->ops.clear();
+    for (const Gate &g : c->gates) {
+        if (g.kind == GATE_UCRY) {
+            Op op;
+            op.kind = OP_UCRY;
+            op.targets = g.targets;
+            op.controls = g.controls;
+            op.theta = g.theta;
+            c->ops.push_back(std::move(op));
+        } else {
+            c->ops.push_back(classify_dense(g.targets, g.controls, g.U));
+        }
+    }
+    c->ops_ready = true;
+}
+
+// ---------------------------------------------------------------------------------------
+// Fusion.
+//
+// A block holds a dense unitary on an ordered qubit list.  Gate g (uncontrolled, qubit set Q)
+// may be appended to block B when no block after B touches Q (then g commutes with every later
+// block and can move back to B), and |B.qubits u Q| <= max_k.  The candidate is the latest
+// block touching Q; a gate touching no open qubit joins the latest block with room.  Any other
+// entry (controlled multi-target gate, uniformly controlled rotation) closes the blocks that
+// touch its qubits by acting as a barrier on them.
+namespace {
+
+struct Block {
+    std::vector<int> qubits;  // bit b of the block matrix index <-> qubits[b]
+    std::vector<cd> M;        // 2^|qubits| square, row-major
+    bool barrier = false;     // a kept-as-is gate (index into gates via src)
+    int src = -1;
+};
+
+// Expand gate matrix U (on `tq`) to the block basis `bq` (tq subset of bq): returns E with
+// E[r][c] = U[rt][ct] if the non-target bits of r and c agree, else 0.
+std::vector<cd> expand_to(const std::vector<int> &bq, const std::vector<int> &tq,
+                          const std::vector<cd> &U) {
+    const int K = (int)bq.size(), k = (int)tq.size();
+    const int D = 1 << K, d = 1 << k;
+    std::vector<int> pos(k);
+    uint64_t tmask = 0;
+    for (int b = 0; b < k; b++) {
+        pos[b] = (int)(std::find(bq.begin(), bq.end(), tq[b]) - bq.begin());
+        tmask |= 1ull << pos[b];
+    }
+    auto sub = [&](int r) {
+        int v = 0;
+        for (int b = 0; b < k; b++) v |= ((r >> pos[b]) & 1) << b;
+        return v;
+    };
+    std::vector<cd> E((size_t)D * D, cd(0.0, 0.0));
+    for (int r = 0; r < D; r++)
+        for (int c = 0; c < D; c++)
+            if ((r & ~tmask) == (c & ~tmask)) E[(size_t)r * D + c] = U[(size_t)sub(r) * d + sub(c)];
+    return E;
+}
+
+void matmul_into(std::vector<cd> &out, const std::vector<cd> &A, const std::vector<cd> &B, int D) {
+    out.assign((size_t)D * D, cd(0.0, 0.0));
+    for (int i = 0; i < D; i++)
+        for (int l = 0; l < D; l++) {
+            const cd a = A[(size_t)i * D + l];
+            if (a == cd(0.0, 0.0)) continue;
+            for (int j = 0; j < D; j++) out[(size_t)i * D + j] += a * B[(size_t)l * D + j];
+        }
+}
+
+// B.M <- G_expanded * B.M after widening B to include the gate's new qubits.
+void absorb(Block &B, const std::vector<int> &tq, const std::vector<cd> &U) {
+    std::vector<int> nq = B.qubits;
+    for (int q : tq)
+        if (std::find(nq.begin(), nq.end(), q) == nq.end()) nq.push_back(q);
+    if (nq.size() != B.qubits.size()) {
+        // widen: M' = I (x) M, the new qubits being the high bits of the block index
+        const int Ko = (int)B.qubits.size(), K = (int)nq.size();
+        const int Do = 1 << Ko, D = 1 << K;
+        std::vector<cd> W((size_t)D * D, cd(0.0, 0.0));
+        for (int r = 0; r < D; r++)
+            for (int c = 0; c < D; c++)
+                if ((r >> Ko) == (c >> Ko))
+                    W[(size_t)r * D + c] = Ko == 0 ? cd(1.0, 0.0)
+                                                   : B.M[(size_t)(r & (Do - 1)) * Do + (c & (Do - 1))];
+        B.qubits = nq;
+        B.M.swap(W);
+    }
+    const int D = 1 << (int)B.qubits.size();
+    std::vector<cd> E = expand_to(B.qubits, tq, U), out;
+    matmul_into(out, E, B.M, D);
+    B.M.swap(out);
+}
+
+}  // namespace
+
+static qsim_circuit *fuse_impl(const qsim_circuit *in, int max_k) {
+    std::unique_ptr<qsim_circuit> out(new qsim_circuit());
+    out->n = in->n;
+    out->fused = true;
+    std::vector<Block> blocks;
+    std::vector<int> last(in->n, -1);  // latest block index touching each qubit
+    for (size_t gi = 0; gi < in->gates.size(); gi++) {
+        const Gate &g = in->gates[gi];
+        std::vector<int> Q = g.targets;
+        Q.insert(Q.end(), g.controls.begin(), g.controls.end());
+        const bool fusable = g.kind == GATE_U && g.controls.empty() && (int)g.targets.size() <= max_k;
+        if (!fusable) {
+            Block b;
+            b.barrier = true;
+            b.src = (int)gi;
+            b.qubits = Q;
+            blocks.push_back(std::move(b));
+            for (int q : Q) last[q] = (int)blocks.size() - 1;
+            continue;
+        }
+        int cand = -1;
+        for (int q : Q) cand = std::max(cand, last[q]);
+        auto fits = [&](int bi) {
+            if (bi < 0 || blocks[bi].barrier) return false;
+            int cnt = (int)blocks[bi].qubits.size();
+            for (int q : Q)
+                if (std::find(blocks[bi].qubits.begin(), blocks[bi].qubits.end(), q) ==
+                    blocks[bi].qubits.end())
+                    cnt++;
+            return cnt <= max_k;
+        };
+        // join the latest block touching Q, else the newest block (every block after the
+        // candidate shares no qubit with the gate, so the gate commutes back to it)
+        int target = -1;
+        const int newest = (int)blocks.size() - 1;
+        if (cand >= 0 && fits(cand)) target = cand;
+        else if (newest >= 0 && newest != cand && fits(newest)) target = newest;
+        if (target < 0) {
+            blocks.emplace_back();
+            target = (int)blocks.size() - 1;
+        }
+        absorb(blocks[target], g.targets, g.U);
+        for (int q : blocks[target].qubits) last[q] = std::max(last[q], target);
+        for (int q : Q) last[q] = target;
+    }
+    for (const Block &b : blocks) {
+        if (b.barrier) {
+            out->gates.push_back(in->gates[b.src]);
+        } else {
+            Gate g;
+            g.kind = GATE_U;
+            g.targets = b.qubits;
+            g.U = b.M;
+            out->gates.push_back(std::move(g));
+        }
+    }
+    return out.release();
+}
+
+void circuit_info(const qsim_circuit *c, qsim_circuit_info *o) {
+    std::memset(o, 0, sizeof(*o));
+    o->n_qubits = c->n;
+    o->fused = c->fused ? 1 : 0;
+    const double N = std::ldexp(1.0, c->n);
+    for (const Op &op : c->ops) {
+        const int k = (int)op.targets.size();
+        const double frac_ctrl = std::ldexp(1.0, -(int)op.controls.size());
+        double amps = 0.0, flops = 0.0;  // amplitudes read+written once, real flops
+        switch (op.kind) {
+            case OP_DENSE:
+                o->n_dense++;
+                o->max_k = std::max(o->max_k, k);
+                amps = N * frac_ctrl;
+                flops = amps * 8.0 * std::ldexp(1.0, k);
+                break;
+            case OP_PHASE:
+                o->n_diag++;
+                amps = N * std::ldexp(1.0, -k);
+                flops = amps * 6.0;
+                break;
+            case OP_DIAG:
+                o->n_diag++;
+                amps = N * frac_ctrl;
+                flops = amps * 6.0;
+                break;
+            case OP_SWAP:
+                o->n_perm++;
+                amps = N * frac_ctrl * 0.5;
+                break;
+            case OP_UCRY:
+                o->n_ucry++;
+                amps = N;
+                flops = amps * 6.0;
+                break;
+        }
+        o->bytes_c64 += 2.0 * 8.0 * amps;
+        o->bytes_c128 += 2.0 * 16.0 * amps;
+        o->flops += flops;
+    }
+    o->n_gates = (int)c->ops.size();
+}
+
+}  // namespace qsim
+
+using namespace qsim;
+
+extern "C" {
+
+const char *qsim_last_error(void) { return g_last_error.c_str(); }
+
+const char *qsim_version(void) { return "0.1.0 sm_103a"; }
+
+int qsim_circuit_create(int n_qubits, qsim_circuit **out) {
+    return guarded([&] {
+        QSIM_REQUIRE(out != nullptr, "out is NULL");
+        QSIM_REQUIRE(n_qubits >= 1 && n_qubits <= 34, "n_qubits must be in 1..34");
+        qsim_circuit *c = new qsim_circuit();
+        c->n = n_qubits;
+        *out = c;
+    });
+}
+
+int qsim_circuit_add_gate(qsim_circuit *c, int k, const int *targets, int n_controls,
+                          const int *controls, const double *U) {
+    return guarded([&] {
+        QSIM_REQUIRE(c != nullptr && targets != nullptr && U != nullptr, "NULL argument");
+        QSIM_REQUIRE(k >= 1 && k <= 7, "k must be in 1..7");
+        QSIM_REQUIRE(n_controls >= 0 && (n_controls == 0 || controls != nullptr), "bad controls");
+        QSIM_REQUIRE(k + n_controls <= c->n, "more gate qubits than circuit qubits");
+        uint64_t seen = 0;
+        check_qubits(c->n, targets, k, seen, "target");
+        check_qubits(c->n, controls, n_controls, seen, "control");
+        const size_t d = (size_t)1 << k;
+        Gate g;
+        g.kind = GATE_U;
+        g.targets.assign(targets, targets + k);
+        if (n_controls) g.controls.assign(controls, controls + n_controls);
+        g.U.resize(d * d);
+        for (size_t i = 0; i < d * d; i++) {
+            QSIM_REQUIRE(std::isfinite(U[2 * i]) && std::isfinite(U[2 * i + 1]), "non-finite matrix entry");
+            g.U[i] = cd(U[2 * i], U[2 * i + 1]);
+        }
+        std::lock_guard<std::mutex> lk(c->mu);
+        QSIM_REQUIRE(!c->fused, "cannot append to a fused circuit");
+        c->gates.push_back(std::move(g));
+        c->ops_ready = false;
+    });
+}
+
+int qsim_circuit_add_ucry(qsim_circuit *c, int target, int n_controls, const int *controls,
+                          const double *theta) {
+    return guarded([&] {
+        QSIM_REQUIRE(c != nullptr && controls != nullptr && theta != nullptr, "NULL argument");
+        QSIM_REQUIRE(n_controls >= 1 && n_controls <= 30, "n_controls must be in 1..30");
+        QSIM_REQUIRE(n_controls + 1 <= c->n, "more gate qubits than circuit qubits");
+        uint64_t seen = 0;
+        check_qubits(c->n, &target, 1, seen, "target");
+        check_qubits(c->n, controls, n_controls, seen, "control");
+        Gate g;
+        g.kind = GATE_UCRY;
+        g.targets = {target};
+        g.controls.assign(controls, controls + n_controls);
+        const size_t cnt = (size_t)1 << n_controls;
+        g.theta.assign(theta, theta + cnt);
+        for (double v : g.theta) QSIM_REQUIRE(std::isfinite(v), "non-finite angle");
+        std::lock_guard<std::mutex> lk(c->mu);
+        QSIM_REQUIRE(!c->fused, "cannot append to a fused circuit");
+        c->gates.push_back(std::move(g));
+        c->ops_ready = false;
+    });
+}
+
+int qsim_circuit_get_info(const qsim_circuit *c, qsim_circuit_info *out) {
+    return guarded([&] {
+        QSIM_REQUIRE(c != nullptr && out != nullptr, "NULL argument");
+        qsim_circuit *cc = const_cast<qsim_circuit *>(c);
+        build_ops(cc);
+        circuit_info(cc, out);
+    });
+}
+
+int qsim_fuse(const qsim_circuit *in, int max_k, qsim_circuit **out) {
+    return guarded([&] {
+        QSIM_REQUIRE(in != nullptr && out != nullptr, "NULL argument");
+        QSIM_REQUIRE(max_k >= 0 && max_k <= 6, "max_k must be in 0..6");
+        if (max_k == 0) max_k = 4;
+        qsim_circuit *f = fuse_impl(in, max_k);
+        build_ops(f);
+        *out = f;
+    });
+}
+
+}  // extern "C"

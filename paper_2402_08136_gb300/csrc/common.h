@@ -1,0 +1,123 @@
+// Internal types of the GB300 HHL simulation library (not part of the C ABI).
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <mutex>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+
+namespace qsim {
+
+using cd = std::complex<double>;
+
+// Error carrying a status code; converted to a return value at the C boundary.
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+void set_last_error(const std::string &msg);
+void clear_last_error();
+
+#define QSIM_REQUIRE(cond, msg)                                                  \
+    do {                                                                         \
+        if (!(cond)) throw ::qsim::Error(QSIM_EINVAL, std::string(msg));         \
+    } while (0)
+
+// Wrap a C entry point body: exceptions become status codes + thread-local message.
+template <class F>
+int guarded(F &&f) {
+    try {
+        clear_last_error();
+        f();
+        return QSIM_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return QSIM_ENOMEM;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return QSIM_EINVAL;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Gate list entries (what the user or hhl_build appends).
+enum GateKind { GATE_U = 0, GATE_UCRY = 1 };
+
+struct Gate {
+    GateKind kind = GATE_U;
+    std::vector<int> targets;   // GATE_U: matrix bit b <-> targets[b]; GATE_UCRY: {target}
+    std::vector<int> controls;  // must be 1 (GATE_U); register bits (GATE_UCRY)
+    std::vector<cd> U;          // GATE_U: 2^k x 2^k row-major
+    std::vector<double> theta;  // GATE_UCRY: 2^|controls|
+};
+
+// Executable operation kinds (one device pass each, or a pass group for the tile kernel).
+enum OpKind {
+    OP_DENSE = 0,  // dense 2^k x 2^k on targets, applied where outer controls are 1
+    OP_PHASE = 1,  // multiply amplitudes whose `targets` bits are all 1 by `phase`
+    OP_DIAG = 2,   // multiply by diag entry selected by the targets' bits
+    OP_SWAP = 3,   // swap qubits targets[0], targets[1] (where controls are 1)
+    OP_UCRY = 4,   // uniformly controlled RY
+};
+
+struct Op {
+    OpKind kind = OP_DENSE;
+    std::vector<int> targets;
+    std::vector<int> controls;
+    std::vector<cd> U;          // OP_DENSE: 2^k x 2^k; OP_DIAG: 2^k diagonal
+    cd phase = 1.0;             // OP_PHASE
+    std::vector<double> theta;  // OP_UCRY
+    // device offsets (bytes) into the circuit's device blob, per dtype
+    size_t dev_off[2] = {0, 0};
+};
+
+struct DeviceBlob {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    int device = -1;
+};
+
+}  // namespace qsim
+
+struct qsim_circuit {
+    int n = 0;
+    bool fused = false;
+    std::vector<qsim::Gate> gates;  // source list
+    std::vector<qsim::Op> ops;      // executable list (built lazily for unfused circuits)
+    bool ops_ready = false;
+    qsim::DeviceBlob blob[2];       // [0] complex64 matrices, [1] complex128 matrices
+    std::mutex mu;                  // guards ops/blob lazy construction
+    ~qsim_circuit();                // releases the device copies (kernels.cu)
+};
+
+struct hhl_circuit {
+    int N = 0, nb = 0, m = 0, n = 0;
+    double t = 0, C = 0, norm_b = 0, lam_min = 0, lam_max = 0;
+    int n_total_formula = 0;
+    std::vector<qsim::cd> b_pad;  // normalized, padded to 2^nb
+    qsim_circuit circ;
+};
+
+namespace qsim {
+// circuit.cpp
+void build_ops(qsim_circuit *c);                 // classify gates -> ops (no fusion)
+Op classify_dense(const std::vector<int> &targets, const std::vector<int> &controls,
+                  const std::vector<cd> &U);
+void circuit_info(const qsim_circuit *c, qsim_circuit_info *out);
+// kernels.cu
+void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream);
+void ensure_device_blob(qsim_circuit *c, int dtype);
+void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb, void *stream);
+void readout_device(const void *state, int dtype, int n, int nb, int m, void *stream,
+                    double sums[3], cd *slice);
+// linalg.cpp
+void hermitian_eig(int N, const std::vector<cd> &A, std::vector<double> &lam, std::vector<cd> &V);
+}  // namespace qsim

@@ -1,0 +1,278 @@
+// HHL circuit construction and solution readout (Sec. III-A "Practical HHL procedures",
+// Fig. 5 conceptual circuit, Sec. III-B resource estimate).
+#include <algorithm>
+#include <cmath>
+#include <memory>
+
+#include "common.h"
+
+namespace qsim {
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+// Sec. III-B: n_QPE = max(n_data + 1, ceil(log2(kappa + 1))).
+int qpe_formula(int n_data, double kappa) {
+    return std::max(n_data + 1, (int)std::ceil(std::log2(kappa + 1.0)));
+}
+
+void add_u(qsim_circuit &c, std::vector<int> targets, std::vector<int> controls, std::vector<cd> U) {
+    Gate g;
+    g.kind = GATE_U;
+    g.targets = std::move(targets);
+    g.controls = std::move(controls);
+    g.U = std::move(U);
+    c.gates.push_back(std::move(g));
+}
+
+std::vector<cd> hadamard() {
+    const double r = 1.0 / std::sqrt(2.0);
+    return {r, r, r, -r};
+}
+
+std::vector<cd> cphase(double phi) {
+    return {1.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, std::polar(1.0, phi)};
+}
+
+std::vector<cd> swap2() {
+    return {1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0};
+}
+
+std::vector<cd> adjoint(const std::vector<cd> &U) {
+    const int d = (int)std::lround(std::sqrt((double)U.size()));
+    std::vector<cd> out(U.size());
+    for (int r = 0; r < d; r++)
+        for (int c = 0; c < d; c++) out[(size_t)c * d + r] = std::conj(U[(size_t)r * d + c]);
+    return out;
+}
+
+// Inverse quantum Fourier transform on `q` (q[j] = bit j of the register value).  The forward
+// transform maps |x> to 2^{-m/2} sum_k exp(2 pi i x k / 2^m) |k>; its circuit handles the
+// most significant qubit first (H, then controlled phases 2 pi / 2^(d+1) from the qubit d
+// places below), followed by the bit-reversal swaps.  The inverse runs that sequence
+// backwards with conjugated phases.
+void append_iqft(qsim_circuit &c, const std::vector<int> &q) {
+    const int m = (int)q.size();
+    for (int j = m / 2 - 1; j >= 0; j--) add_u(c, {q[j], q[m - 1 - j]}, {}, swap2());
+    for (int j = 0; j < m; j++) {
+        for (int l = 0; l < j; l++) add_u(c, {q[l], q[j]}, {}, cphase(-2.0 * kPi / std::ldexp(1.0, j - l + 1)));
+        add_u(c, {q[j]}, {}, hadamard());
+    }
+}
+
+hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const std::vector<cd> &VA,
+                                 const std::vector<cd> &b, int n_clock, double t, double C) {
+    QSIM_REQUIRE(lamA.front() > 0.0, "A must be positive definite (smallest eigenvalue <= 0)");
+    std::unique_ptr<hhl_circuit> h(new hhl_circuit());
+    h->N = N;
+    // step 1: normalize b
+    double nb2 = 0.0;
+    for (const cd &z : b) nb2 += std::norm(z);
+    QSIM_REQUIRE(nb2 > 0.0, "b must be nonzero");
+    h->norm_b = std::sqrt(nb2);
+    // step 1(b): pad to a power of two with block-diag(A, lambda_max I)
+    int nb = 1;
+    while ((1 << nb) < N) nb++;
+    const int D = 1 << nb;
+    h->nb = nb;
+    h->lam_min = lamA.front();
+    h->lam_max = lamA.back();
+    std::vector<double> lam(D);
+    std::vector<cd> V((size_t)D * D, cd(0.0, 0.0));
+    for (int i = 0; i < N; i++) {
+        lam[i] = lamA[i];
+        for (int r = 0; r < N; r++) V[(size_t)r * D + i] = VA[(size_t)r * N + i];
+    }
+    for (int i = N; i < D; i++) {
+        lam[i] = h->lam_max;
+        V[(size_t)i * D + i] = 1.0;
+    }
+    h->b_pad.assign(D, cd(0.0, 0.0));
+    for (int i = 0; i < N; i++) h->b_pad[i] = b[i] / h->norm_b;
+    // Sec. III-B resources
+    const double kappa = h->lam_max / h->lam_min;
+    const int n_data = nb;
+    h->n_total_formula = n_data + qpe_formula(n_data, kappa) + 0 /* no negative eigenvalues */ + 1;
+    const int m = n_clock > 0 ? n_clock : qpe_formula(n_data, kappa);
+    QSIM_REQUIRE(m >= 1 && m <= 26, "clock qubit count must be in 1..26");
+    QSIM_REQUIRE(nb + m + 1 <= 34, "more than 34 qubits");
+    h->m = m;
+    h->n = nb + m + 1;
+    const double M = std::ldexp(1.0, m);
+    if (!(t > 0.0)) t = 2.0 * kPi * (M - 1.0) / (M * h->lam_max);
+    h->t = t;
+    const double step = 2.0 * kPi / (t * M);  // grid value of clock value k is k * step
+    if (!(C > 0.0)) {
+        C = std::max(1.0, std::floor(h->lam_min / step * (1.0 + 1e-9))) * step;
+    } else {
+        QSIM_REQUIRE(C <= h->lam_min * (1.0 + 1e-9), "C above the smallest eigenvalue");
+    }
+    h->C = C;
+    QSIM_REQUIRE(std::isfinite(t) && std::isfinite(C), "non-finite t or C");
+
+    // step 2: the circuit
+    qsim_circuit &c = h->circ;
+    c.n = h->n;
+    std::vector<int> data(nb), clock(m);
+    for (int i = 0; i < nb; i++) data[i] = i;
+    for (int j = 0; j < m; j++) clock[j] = nb + j;
+    const int anc = nb + m;
+    const size_t qpe_begin = c.gates.size();
+    for (int j = 0; j < m; j++) add_u(c, {clock[j]}, {}, hadamard());
+    for (int j = 0; j < m; j++) {
+        // U_j = V diag(exp(i lambda t 2^j)) V^H  (t 2^j scales by a power of two: exact)
+        const double tj = std::ldexp(t, j);
+        std::vector<cd> ph(D);
+        for (int i = 0; i < D; i++) ph[i] = std::polar(1.0, lam[i] * tj);
+        std::vector<cd> U((size_t)D * D, cd(0.0, 0.0));
+        for (int r = 0; r < D; r++)
+            for (int i = 0; i < D; i++) {
+                const cd vr = V[(size_t)r * D + i] * ph[i];
+                for (int s = 0; s < D; s++) U[(size_t)r * D + s] += vr * std::conj(V[(size_t)s * D + i]);
+            }
+        add_u(c, data, {clock[j]}, std::move(U));
+    }
+    append_iqft(c, clock);
+    const size_t qpe_end = c.gates.size();
+    // eigenvalue inversion: theta_k = 2 asin(min(1, C / (k step))), theta_0 = 0
+    {
+        Gate g;
+        g.kind = GATE_UCRY;
+        g.targets = {anc};
+        g.controls = clock;
+        g.theta.assign((size_t)1 << m, 0.0);
+        for (size_t k = 1; k < g.theta.size(); k++) {
+            const double r = C / ((double)k * step);
+            g.theta[k] = 2.0 * std::asin(std::min(1.0, r));
+        }
+        c.gates.push_back(std::move(g));
+    }
+    // uncompute: inverse of the phase estimation
+    for (size_t i = qpe_end; i-- > qpe_begin;) {
+        const Gate &g = c.gates[i];
+        add_u(c, g.targets, g.controls, adjoint(g.U));
+    }
+    return h.release();
+}
+
+std::vector<cd> read_complex(const double *p, size_t n) {
+    std::vector<cd> v(n);
+    for (size_t i = 0; i < n; i++) {
+        QSIM_REQUIRE(std::isfinite(p[2 * i]) && std::isfinite(p[2 * i + 1]), "non-finite input");
+        v[i] = cd(p[2 * i], p[2 * i + 1]);
+    }
+    return v;
+}
+
+}  // namespace
+}  // namespace qsim
+
+using namespace qsim;
+
+extern "C" {
+
+int hhl_build(const double *A, const double *b, int N, int n_clock, double t, double C,
+              hhl_circuit **out) {
+    return guarded([&] {
+        QSIM_REQUIRE(A != nullptr && b != nullptr && out != nullptr, "NULL argument");
+        QSIM_REQUIRE(N >= 1 && N <= 4096, "N must be in 1..4096");
+        std::vector<cd> Am = read_complex(A, (size_t)N * N), bv = read_complex(b, N);
+        double amax = 0.0;
+        for (const cd &z : Am) amax = std::max(amax, std::abs(z));
+        const double tol = 1e-12 * std::max(1.0, amax);
+        for (int r = 0; r < N; r++)
+            for (int c = 0; c <= r; c++)
+                QSIM_REQUIRE(std::abs(Am[(size_t)r * N + c] - std::conj(Am[(size_t)c * N + r])) <= tol,
+                             "A is not Hermitian");
+        for (int r = 0; r < N; r++) Am[(size_t)r * N + r] = Am[(size_t)r * N + r].real();
+        std::vector<double> lam;
+        std::vector<cd> V;
+        hermitian_eig(N, Am, lam, V);
+        *out = build_from_spectrum(N, lam, V, bv, n_clock, t, C);
+    });
+}
+
+int hhl_build_spectral(const double *lambda, const double *V, const double *b, int N, int n_clock,
+                       double t, double C, hhl_circuit **out) {
+    return guarded([&] {
+        QSIM_REQUIRE(lambda != nullptr && V != nullptr && b != nullptr && out != nullptr, "NULL argument");
+        QSIM_REQUIRE(N >= 1 && N <= 4096, "N must be in 1..4096");
+        std::vector<double> lam(lambda, lambda + N);
+        for (double v : lam) QSIM_REQUIRE(std::isfinite(v), "non-finite eigenvalue");
+        std::vector<cd> Vm = read_complex(V, (size_t)N * N), bv = read_complex(b, N);
+        std::vector<int> idx(N);
+        for (int i = 0; i < N; i++) idx[i] = i;
+        std::sort(idx.begin(), idx.end(), [&](int x, int y) { return lam[x] < lam[y]; });
+        std::vector<double> ls(N);
+        std::vector<cd> Vs((size_t)N * N);
+        for (int j = 0; j < N; j++) {
+            ls[j] = lam[idx[j]];
+            for (int r = 0; r < N; r++) Vs[(size_t)r * N + j] = Vm[(size_t)r * N + idx[j]];
+        }
+        *out = build_from_spectrum(N, ls, Vs, bv, n_clock, t, C);
+    });
+}
+
+void hhl_circuit_free(hhl_circuit *h) { delete h; }
+
+const qsim_circuit *hhl_as_circuit(const hhl_circuit *h) { return h ? &h->circ : nullptr; }
+
+int hhl_get_info(const hhl_circuit *h, hhl_info *o) {
+    return guarded([&] {
+        QSIM_REQUIRE(h != nullptr && o != nullptr, "NULL argument");
+        o->N = h->N;
+        o->nb = h->nb;
+        o->m = h->m;
+        o->n = h->n;
+        o->t = h->t;
+        o->C = h->C;
+        o->norm_b = h->norm_b;
+        o->lambda_min = h->lam_min;
+        o->lambda_max = h->lam_max;
+        o->n_total_formula = h->n_total_formula;
+        o->n_gates = (int)h->circ.gates.size();
+    });
+}
+
+int hhl_prepare_state(void *state, int dtype, const hhl_circuit *h, void *stream) {
+    return guarded([&] {
+        QSIM_REQUIRE(state != nullptr && h != nullptr, "NULL argument");
+        QSIM_REQUIRE(dtype == QSIM_C64 || dtype == QSIM_C128, "dtype must be QSIM_C64 or QSIM_C128");
+        launch_prepare_state(state, h->n, dtype, h->b_pad.data(), h->nb, stream);
+    });
+}
+
+int hhl_readout(const void *state, int dtype, const hhl_circuit *h, void *stream, double *x_out,
+                double *x_state_out, hhl_readout_stats *stats) {
+    return guarded([&] {
+        QSIM_REQUIRE(state != nullptr && h != nullptr, "NULL argument");
+        QSIM_REQUIRE(dtype == QSIM_C64 || dtype == QSIM_C128, "dtype must be QSIM_C64 or QSIM_C128");
+        double sums[3];  // ||psi||^2, P(anc = 1), P(anc = 1, clock = 0)
+        std::vector<cd> slice((size_t)1 << h->nb);
+        readout_device(state, dtype, h->n, h->nb, h->m, stream, sums, slice.data());
+        const double P = sums[1], P0 = sums[2];
+        const double inv = P0 > 0.0 ? 1.0 / std::sqrt(P0) : 0.0;
+        const double norm_x = std::sqrt(P) / h->C;
+        if (x_state_out)
+            for (size_t i = 0; i < slice.size(); i++) {
+                x_state_out[2 * i] = slice[i].real() * inv;
+                x_state_out[2 * i + 1] = slice[i].imag() * inv;
+            }
+        if (x_out)
+            for (int i = 0; i < h->N; i++) {
+                const cd x = slice[i] * (inv * norm_x * h->norm_b);
+                x_out[2 * i] = x.real();
+                x_out[2 * i + 1] = x.imag();
+            }
+        if (stats) {
+            stats->p_success = P;
+            stats->p_clock0 = P0;
+            stats->leakage = P - P0;
+            stats->norm2 = sums[0];
+            stats->norm_x = norm_x;
+            stats->norm_b = h->norm_b;
+        }
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,741 @@
+// Device side of the GB300 HHL state-vector simulator: gate-application kernels, HHL state
+// preparation and the FP64 readout reductions (sm_103a).
+//
+// The state is 2^n interleaved complex amplitudes (float2 for complex64, double2 for
+// complex128); qubit q is bit q of the amplitude index.
+//
+// Dense gates (Sec. II-C "unitary evolution of the state", fused products of Fig. 4) run as a
+// persistent tiled kernel: a CTA owns a tile of 2^T amplitudes spanned by the gate's target
+// qubits plus the lowest non-control qubits, so that every tile is a union of contiguous runs
+// of at least 16 amplitudes (coalesced, full 32-byte sectors).  The tile is staged in shared
+// memory, the 2^k x 2^k matrix sits in shared memory for the CTA's lifetime, and each thread
+// computes 16 output rows of one group column at a time, writing straight back to HBM.
+// Specialised kernels handle phase (controlled-phase, e.g. the QFT's), diagonal, swap and the
+// uniformly controlled RY of the eigenvalue inversion, touching only the amplitudes they change.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "common.h"
+
+namespace qsim {
+
+#define CUDA_OK(call)                                                                         \
+    do {                                                                                      \
+        cudaError_t e__ = (call);                                                             \
+        if (e__ != cudaSuccess)                                                               \
+            throw ::qsim::Error(QSIM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+static void check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    return sms;
+}
+
+template <typename R> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+
+template <typename V>
+__device__ __forceinline__ V cmul(V a, V b) {
+    V r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+// insert zero bits at the ascending positions pos[0..cnt-1]
+__device__ __forceinline__ uint64_t insert_zeros(uint64_t x, const int *pos, int cnt) {
+    for (int i = 0; i < cnt; i++) {
+        const int p = pos[i];
+        const uint64_t low = x & ((1ull << p) - 1ull);
+        x = ((x >> p) << (p + 1)) | low;
+    }
+    return x;
+}
+
+// ---------------------------------------------------------------------------------------
+// Dense k-qubit gate, tiled.
+constexpr int kThreads = 256;
+constexpr int kMaxFix = 40;
+
+struct DenseArgs {
+    void *psi;
+    const void *U;        // 2^K x 2^K, stored transposed: Ut[c * D + r] = U[r][c]
+    long long ntiles;
+    unsigned long long cmask;  // control bits that must be 1
+    int T;                // tile bits
+    int L0;               // tile bits 0..L0-1 are global qubits 0..L0-1
+    int nh;               // tile bits L0..T-1 map to global positions hpos[0..nh-1]
+    int hpos[16];
+    int nfix;             // ascending insertion positions (tile qubits above L0, controls)
+    int fix[kMaxFix];
+    int tloc[8];          // tile-local bit of target b
+};
+
+template <typename R, int K, bool USMEM>
+__global__ void __launch_bounds__(kThreads) dense_tile_kernel(const DenseArgs a) {
+    using V = typename C2<R>::T;
+    constexpr int D = 1 << K;
+    constexpr int RPT = D < 16 ? D : 16;  // output rows per thread
+    constexpr int RG = D / RPT;           // row groups
+    constexpr int WPG = (kThreads / 32) / RG;  // warps per row group
+    constexpr int CSTRIDE = 32 * WPG;     // column stride
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int T = a.T;
+    const int tile_amps = 1 << T;
+    const int G = tile_amps >> K;  // groups (columns) per tile
+    V *tile = reinterpret_cast<V *>(smem_raw);
+    V *Us = tile + tile_amps;                              // D*D if USMEM
+    int *toff = reinterpret_cast<int *>(Us + (USMEM ? D * D : 0));   // D entries
+    long long *hoff = reinterpret_cast<long long *>(toff + ((D + 1) & ~1));  // 2^nh entries
+
+    const int tid = threadIdx.x;
+    const V *Ug = reinterpret_cast<const V *>(a.U);
+    if (USMEM)
+        for (int i = tid; i < D * D; i += kThreads) Us[i] = Ug[i];
+    for (int c = tid; c < D; c += kThreads) {
+        int o = 0;
+        for (int b = 0; b < K; b++)
+            if ((c >> b) & 1) o |= 1 << a.tloc[b];
+        toff[c] = o;
+    }
+    const int nhv = 1 << a.nh;
+    for (int h = tid; h < nhv; h += kThreads) {
+        long long o = 0;
+        for (int i = 0; i < a.nh; i++)
+            if ((h >> i) & 1) o |= 1ll << a.hpos[i];
+        hoff[h] = o;
+    }
+    // tile-local index of the first amplitude of each group: insert zeros at target bits
+    int tsorted[K];
+    for (int b = 0; b < K; b++) tsorted[b] = a.tloc[b];
+    for (int i = 1; i < K; i++) {
+        int v = tsorted[i], j = i - 1;
+        while (j >= 0 && tsorted[j] > v) { tsorted[j + 1] = tsorted[j]; j--; }
+        tsorted[j + 1] = v;
+    }
+    __syncthreads();
+
+    const int warp = tid >> 5, lane = tid & 31;
+    const int rg = warp % RG;
+    const int col0 = (warp / RG) * 32 + lane;
+    const int lomask = (1 << a.L0) - 1;
+    V *psi = reinterpret_cast<V *>(a.psi);
+
+    for (long long tix = blockIdx.x; tix < a.ntiles; tix += gridDim.x) {
+        const unsigned long long base =
+            insert_zeros((unsigned long long)tix << a.L0, a.fix, a.nfix) | a.cmask;
+        for (int l = tid; l < tile_amps; l += kThreads)
+            tile[l] = psi[base + hoff[l >> a.L0] + (l & lomask)];
+        __syncthreads();
+        for (int g = col0; g < G; g += CSTRIDE) {
+            int gl = g;
+            for (int b = 0; b < K; b++) {
+                const int p = tsorted[b];
+                gl = ((gl >> p) << (p + 1)) | (gl & ((1 << p) - 1));
+            }
+            V acc[RPT];
+#pragma unroll
+            for (int r = 0; r < RPT; r++) acc[r] = V{0, 0};
+            for (int c = 0; c < D; c++) {
+                const V x = tile[gl + toff[c]];
+                const V *uc = (USMEM ? Us : Ug) + c * D + rg * RPT;
+#pragma unroll
+                for (int r = 0; r < RPT; r++) {
+                    const V u = uc[r];
+                    acc[r].x = fma(u.x, x.x, acc[r].x);
+                    acc[r].x = fma(-u.y, x.y, acc[r].x);
+                    acc[r].y = fma(u.x, x.y, acc[r].y);
+                    acc[r].y = fma(u.y, x.x, acc[r].y);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RPT; r++) {
+                const int l = gl + toff[rg * RPT + r];
+                psi[base + hoff[l >> a.L0] + (l & lomask)] = acc[r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Phase on the all-ones pattern of `mask` qubits: psi[i] *= ph for i with (i & mask) == mask.
+struct PhaseArgs {
+    void *psi;
+    long long count;  // 2^(n - nfix)
+    unsigned long long mask;
+    int nfix;
+    int fix[kMaxFix];
+    double ph_re, ph_im;
+};
+
+template <typename R>
+__global__ void phase_kernel(const PhaseArgs a) {
+    using V = typename C2<R>::T;
+    V *psi = reinterpret_cast<V *>(a.psi);
+    const V ph{(R)a.ph_re, (R)a.ph_im};
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.count;
+         g += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long i = insert_zeros((unsigned long long)g, a.fix, a.nfix) | a.mask;
+        psi[i] = cmul(psi[i], ph);
+    }
+}
+
+// Diagonal on k targets (entries d[pattern]) where the controls are 1.
+struct DiagArgs {
+    void *psi;
+    const void *d;
+    long long count;
+    unsigned long long cmask;
+    int nfix;
+    int fix[kMaxFix];
+    int k;
+    int targets[8];
+};
+
+template <typename R>
+__global__ void diag_kernel(const DiagArgs a) {
+    using V = typename C2<R>::T;
+    V *psi = reinterpret_cast<V *>(a.psi);
+    const V *d = reinterpret_cast<const V *>(a.d);
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.count;
+         g += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long i = insert_zeros((unsigned long long)g, a.fix, a.nfix) | a.cmask;
+        int p = 0;
+        for (int b = 0; b < a.k; b++) p |= (int)((i >> a.targets[b]) & 1ull) << b;
+        psi[i] = cmul(psi[i], d[p]);
+    }
+}
+
+// Swap qubits qa, qb where the controls are 1.
+struct SwapArgs {
+    void *psi;
+    long long count;
+    unsigned long long cmask;
+    unsigned long long ma, mb;
+    int nfix;
+    int fix[kMaxFix];
+};
+
+template <typename R>
+__global__ void swap_kernel(const SwapArgs a) {
+    using V = typename C2<R>::T;
+    V *psi = reinterpret_cast<V *>(a.psi);
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.count;
+         g += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long i = insert_zeros((unsigned long long)g, a.fix, a.nfix) | a.cmask;
+        const V x = psi[i | a.ma], y = psi[i | a.mb];
+        psi[i | a.ma] = y;
+        psi[i | a.mb] = x;
+    }
+}
+
+// Uniformly controlled RY on `target`: (psi0, psi1) <- [[c, -s], [s, c]] (psi0, psi1) with
+// (c, s) = cs[v], v = value of the control register at the pair's index.
+struct UcryArgs {
+    void *psi;
+    const void *cs;  // 2^nc (cos theta/2, sin theta/2) pairs, in the state's real type
+    long long count;  // 2^(n-1)
+    int target;
+    int nc;
+    int contiguous;  // controls are qubits c0 .. c0+nc-1 in order
+    int c0;
+    int ctrl[32];
+};
+
+template <typename R>
+__global__ void ucry_kernel(const UcryArgs a) {
+    using V = typename C2<R>::T;
+    V *psi = reinterpret_cast<V *>(a.psi);
+    const V *cs = reinterpret_cast<const V *>(a.cs);
+    const unsigned long long tb = 1ull << a.target;
+    const unsigned long long vmask = (1ull << a.nc) - 1ull;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.count;
+         g += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long i0 = (((unsigned long long)g >> a.target) << (a.target + 1)) |
+                                      ((unsigned long long)g & (tb - 1ull));
+        unsigned long long v;
+        if (a.contiguous) {
+            v = (i0 >> a.c0) & vmask;
+        } else {
+            v = 0;
+            for (int j = 0; j < a.nc; j++) v |= ((i0 >> a.ctrl[j]) & 1ull) << j;
+        }
+        const V t = cs[v];
+        const V x0 = psi[i0], x1 = psi[i0 | tb];
+        V y0, y1;
+        y0.x = t.x * x0.x - t.y * x1.x;
+        y0.y = t.x * x0.y - t.y * x1.y;
+        y1.x = t.y * x0.x + t.x * x1.x;
+        y1.y = t.y * x0.y + t.x * x1.y;
+        psi[i0] = y0;
+        psi[i0 | tb] = y1;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// HHL state preparation: psi = 0 except the first D amplitudes = b.
+constexpr int kMaxParamB = 256;
+struct PrepArgs {
+    void *psi;
+    long long N;
+    int D;
+    double b[2 * kMaxParamB];
+};
+
+template <typename R>
+__global__ void prep_kernel(const PrepArgs a) {
+    using V = typename C2<R>::T;
+    V *psi = reinterpret_cast<V *>(a.psi);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.N;
+         i += (long long)gridDim.x * blockDim.x) {
+        V v{0, 0};
+        if (i < a.D && i < kMaxParamB) v = V{(R)a.b[2 * i], (R)a.b[2 * i + 1]};
+        psi[i] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Readout reductions in FP64.  Block b of `nblk` sums |psi_i|^2 over its contiguous chunk in a
+// fixed order (per-thread strided sums, then a fixed shuffle/shared-memory tree); the final
+// single-block kernel adds the partials in index order.  The result therefore depends only on
+// the state and n, never on what else runs on the GPU.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+template <typename R>
+__global__ void norm_partials_kernel(const void *state, long long chunk, double *partials) {
+    using V = typename C2<R>::T;
+    __shared__ double sh[32];
+    const V *psi = reinterpret_cast<const V *>(state) + (long long)blockIdx.x * chunk;
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < chunk; i += blockDim.x) {
+        const V z = psi[i];
+        const double re = (double)z.x, im = (double)z.y;
+        s = fma(re, re, s);
+        s = fma(im, im, s);
+    }
+    const double t = block_sum(s, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// out[0] = sum of all partials, out[1] = sum of the upper half (ancilla = 1),
+// out[2] = sum over the slice psi[off .. off + len) (ancilla = 1, clock = 0).
+template <typename R>
+__global__ void norm_final_kernel(const double *partials, int nblk, const void *state,
+                                  long long off, int len, double *out) {
+    using V = typename C2<R>::T;
+    __shared__ double sh[32];
+    double lo = 0.0, hi = 0.0, sl = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+        if (i < nblk / 2) lo += partials[i];
+        else hi += partials[i];
+    }
+    const V *psi = reinterpret_cast<const V *>(state) + off;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const V z = psi[i];
+        const double re = (double)z.x, im = (double)z.y;
+        sl = fma(re, re, sl);
+        sl = fma(im, im, sl);
+    }
+    const double tlo = block_sum(lo, sh);
+    const double thi = block_sum(hi, sh);
+    const double tsl = block_sum(sl, sh);
+    if (threadIdx.x == 0) {
+        out[0] = tlo + thi;
+        out[1] = thi;
+        out[2] = tsl;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host side.
+namespace {
+
+size_t real_size(int dtype) { return dtype == QSIM_C128 ? 8 : 4; }
+
+void put_complex(std::vector<unsigned char> &blob, int dtype, const cd &z) {
+    if (dtype == QSIM_C128) {
+        double v[2] = {z.real(), z.imag()};
+        blob.insert(blob.end(), (unsigned char *)v, (unsigned char *)v + 16);
+    } else {
+        float v[2] = {(float)z.real(), (float)z.imag()};
+        blob.insert(blob.end(), (unsigned char *)v, (unsigned char *)v + 8);
+    }
+}
+
+void align_blob(std::vector<unsigned char> &blob) {
+    while (blob.size() % 256) blob.push_back(0);
+}
+
+std::vector<int> sorted_copy(std::vector<int> v) {
+    std::sort(v.begin(), v.end());
+    return v;
+}
+
+void fill_fix(int *dst, int &cnt, const std::vector<int> &pos) {
+    QSIM_REQUIRE((int)pos.size() <= kMaxFix, "too many fixed qubits");
+    cnt = (int)pos.size();
+    for (int i = 0; i < cnt; i++) dst[i] = pos[i];
+}
+
+unsigned long long mask_of(const std::vector<int> &q) {
+    unsigned long long m = 0;
+    for (int x : q) m |= 1ull << x;
+    return m;
+}
+
+int grid_for(long long work, int per_block) {
+    long long blocks = (work + per_block - 1) / per_block;
+    const long long cap = (long long)num_sms() * 16;
+    return (int)std::max(1ll, std::min(blocks, cap));
+}
+
+int tile_bits(int dtype) { return dtype == QSIM_C128 ? 11 : 12; }
+
+template <typename R, int K, bool USMEM>
+void launch_dense_t(const DenseArgs &a, size_t smem, cudaStream_t st) {
+    auto kern = dense_tile_kernel<R, K, USMEM>;
+    static bool attr = false;
+    if (!attr) {
+        CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr = true;
+    }
+    int per_sm = 0;
+    CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    QSIM_REQUIRE(per_sm > 0, "dense kernel does not fit on an SM");
+    const long long grid = std::min<long long>(a.ntiles, (long long)num_sms() * per_sm);
+    kern<<<(int)grid, kThreads, smem, st>>>(a);
+    check_launch("dense_tile_kernel");
+}
+
+template <typename R>
+void launch_dense(const DenseArgs &a, int K, size_t smem_base, cudaStream_t st) {
+    const size_t D = (size_t)1 << K;
+    const size_t vb = 2 * sizeof(R);
+    const size_t ubytes = D * D * vb;
+    const bool usmem = smem_base + ubytes <= 200 * 1024;
+    const size_t smem = smem_base + (usmem ? ubytes : 0);
+    switch (K) {
+#define QSIM_K(k)                                                    \
+    case k:                                                          \
+        if (usmem) launch_dense_t<R, k, true>(a, smem, st);          \
+        else launch_dense_t<R, k, false>(a, smem, st);               \
+        break;
+        QSIM_K(1) QSIM_K(2) QSIM_K(3) QSIM_K(4) QSIM_K(5) QSIM_K(6) QSIM_K(7)
+#undef QSIM_K
+        default:
+            throw Error(QSIM_EINVAL, "dense gate wider than 7 qubits");
+    }
+}
+
+void run_dense(void *state, int n, int dtype, const Op &op, const void *Udev, cudaStream_t st) {
+    const int K = (int)op.targets.size();
+    const std::vector<int> &ctl = op.controls;
+    const unsigned long long cm = mask_of(ctl);
+    const unsigned long long tm = mask_of(op.targets);
+    const int avail = n - (int)ctl.size();
+    const int T = std::min(tile_bits(dtype), avail);
+    // tile qubits: the targets plus the lowest non-control qubits
+    std::vector<int> tile(op.targets.begin(), op.targets.end());
+    for (int q = 0; q < n && (int)tile.size() < T; q++)
+        if (!((cm >> q) & 1ull) && !((tm >> q) & 1ull)) tile.push_back(q);
+    std::vector<int> ts = sorted_copy(tile);
+    DenseArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = state;
+    a.U = Udev;
+    a.T = (int)ts.size();
+    a.L0 = 0;
+    while (a.L0 < a.T && ts[a.L0] == a.L0) a.L0++;
+    a.nh = a.T - a.L0;
+    QSIM_REQUIRE(a.nh <= 16, "tile layout");
+    for (int i = 0; i < a.nh; i++) a.hpos[i] = ts[a.L0 + i];
+    std::vector<int> fix;
+    for (int i = a.L0; i < a.T; i++) fix.push_back(ts[i]);
+    for (int q : ctl) fix.push_back(q);
+    fix = sorted_copy(fix);
+    fill_fix(a.fix, a.nfix, fix);
+    a.cmask = cm;
+    a.ntiles = 1ll << (n - a.T - (int)ctl.size());
+    for (int b = 0; b < K; b++)
+        a.tloc[b] = (int)(std::find(ts.begin(), ts.end(), op.targets[b]) - ts.begin());
+    const size_t vb = 2 * real_size(dtype);
+    const size_t D = (size_t)1 << K;
+    const size_t smem_base = ((size_t)1 << a.T) * vb + ((D + 1) & ~(size_t)1) * 4 +
+                             ((size_t)1 << a.nh) * 8;
+    if (dtype == QSIM_C128) launch_dense<double>(a, K, smem_base, st);
+    else launch_dense<float>(a, K, smem_base, st);
+}
+
+void run_phase(void *state, int n, int dtype, const Op &op, cudaStream_t st) {
+    PhaseArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = state;
+    std::vector<int> q = sorted_copy(op.targets);
+    fill_fix(a.fix, a.nfix, q);
+    a.mask = mask_of(q);
+    a.count = 1ll << (n - (int)q.size());
+    a.ph_re = op.phase.real();
+    a.ph_im = op.phase.imag();
+    const int grid = grid_for(a.count, 256);
+    if (dtype == QSIM_C128) phase_kernel<double><<<grid, 256, 0, st>>>(a);
+    else phase_kernel<float><<<grid, 256, 0, st>>>(a);
+    check_launch("phase_kernel");
+}
+
+void run_diag(void *state, int n, int dtype, const Op &op, const void *ddev, cudaStream_t st) {
+    DiagArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = state;
+    a.d = ddev;
+    std::vector<int> c = sorted_copy(op.controls);
+    fill_fix(a.fix, a.nfix, c);
+    a.cmask = mask_of(c);
+    a.count = 1ll << (n - (int)c.size());
+    a.k = (int)op.targets.size();
+    for (int b = 0; b < a.k; b++) a.targets[b] = op.targets[b];
+    const int grid = grid_for(a.count, 256);
+    if (dtype == QSIM_C128) diag_kernel<double><<<grid, 256, 0, st>>>(a);
+    else diag_kernel<float><<<grid, 256, 0, st>>>(a);
+    check_launch("diag_kernel");
+}
+
+void run_swap(void *state, int n, int dtype, const Op &op, cudaStream_t st) {
+    SwapArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = state;
+    std::vector<int> f = op.controls;
+    f.push_back(op.targets[0]);
+    f.push_back(op.targets[1]);
+    f = sorted_copy(f);
+    fill_fix(a.fix, a.nfix, f);
+    a.cmask = mask_of(op.controls);
+    a.ma = (1ull << op.targets[0]) | a.cmask;
+    a.mb = (1ull << op.targets[1]) | a.cmask;
+    a.cmask = 0;  // folded into ma / mb
+    a.count = 1ll << (n - (int)f.size());
+    const int grid = grid_for(a.count, 256);
+    if (dtype == QSIM_C128) swap_kernel<double><<<grid, 256, 0, st>>>(a);
+    else swap_kernel<float><<<grid, 256, 0, st>>>(a);
+    check_launch("swap_kernel");
+}
+
+void run_ucry(void *state, int n, int dtype, const Op &op, const void *csdev, cudaStream_t st) {
+    UcryArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = state;
+    a.cs = csdev;
+    a.count = 1ll << (n - 1);
+    a.target = op.targets[0];
+    a.nc = (int)op.controls.size();
+    QSIM_REQUIRE(a.nc <= 32, "too many controls");
+    a.contiguous = 1;
+    a.c0 = op.controls[0];
+    for (int j = 0; j < a.nc; j++) {
+        a.ctrl[j] = op.controls[j];
+        if (op.controls[j] != a.c0 + j) a.contiguous = 0;
+    }
+    const int grid = grid_for(a.count, 256);
+    if (dtype == QSIM_C128) ucry_kernel<double><<<grid, 256, 0, st>>>(a);
+    else ucry_kernel<float><<<grid, 256, 0, st>>>(a);
+    check_launch("ucry_kernel");
+}
+
+}  // namespace
+
+// Pack every op's device data (dense matrices transposed, diagonals, UCRY (cos, sin) tables)
+// into one device allocation per dtype, uploaded once.
+void ensure_device_blob(qsim_circuit *c, int dtype) {
+    build_ops(c);
+    std::lock_guard<std::mutex> lk(c->mu);
+    const int slot = dtype == QSIM_C128 ? 1 : 0;
+    int dev = 0;
+    CUDA_OK(cudaGetDevice(&dev));
+    DeviceBlob &B = c->blob[slot];
+    if (B.ptr && B.device == dev) return;
+    QSIM_REQUIRE(B.ptr == nullptr, "circuit already uploaded to another device");
+    std::vector<unsigned char> blob;
+    for (Op &op : c->ops) {
+        align_blob(blob);
+        op.dev_off[slot] = blob.size();
+        if (op.kind == OP_DENSE) {
+            const int D = 1 << (int)op.targets.size();
+            for (int col = 0; col < D; col++)
+                for (int r = 0; r < D; r++) put_complex(blob, dtype, op.U[(size_t)r * D + col]);
+        } else if (op.kind == OP_DIAG) {
+            for (const cd &z : op.U) put_complex(blob, dtype, z);
+        } else if (op.kind == OP_UCRY) {
+            for (double th : op.theta) put_complex(blob, dtype, cd(std::cos(0.5 * th), std::sin(0.5 * th)));
+        }
+    }
+    align_blob(blob);
+    if (blob.empty()) blob.resize(256, 0);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, blob.size());
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(QSIM_ENOMEM, std::string("cudaMalloc for circuit matrices: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(p, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        throw Error(QSIM_ECUDA, std::string("cudaMemcpy circuit matrices: ") + cudaGetErrorString(e));
+    }
+    B.ptr = p;
+    B.bytes = blob.size();
+    B.device = dev;
+}
+
+void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream) {
+    ensure_device_blob(c, dtype);
+    const int slot = dtype == QSIM_C128 ? 1 : 0;
+    const unsigned char *base = static_cast<const unsigned char *>(c->blob[slot].ptr);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (const Op &op : c->ops) {
+        const void *dptr = base + op.dev_off[slot];
+        switch (op.kind) {
+            case OP_DENSE: run_dense(state, n, dtype, op, dptr, st); break;
+            case OP_PHASE: run_phase(state, n, dtype, op, st); break;
+            case OP_DIAG: run_diag(state, n, dtype, op, dptr, st); break;
+            case OP_SWAP: run_swap(state, n, dtype, op, st); break;
+            case OP_UCRY: run_ucry(state, n, dtype, op, dptr, st); break;
+        }
+    }
+}
+
+void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb, void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PrepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = state;
+    a.N = 1ll << n;
+    a.D = 1 << nb;
+    const int inl = std::min(a.D, kMaxParamB);
+    for (int i = 0; i < inl; i++) {
+        a.b[2 * i] = b_pad[i].real();
+        a.b[2 * i + 1] = b_pad[i].imag();
+    }
+    const int grid = grid_for(a.N, 256);
+    if (dtype == QSIM_C128) prep_kernel<double><<<grid, 256, 0, st>>>(a);
+    else prep_kernel<float><<<grid, 256, 0, st>>>(a);
+    check_launch("prep_kernel");
+    if (a.D > kMaxParamB) {  // rare: long right-hand sides go through a staged copy
+        const int rest = a.D - kMaxParamB;
+        std::vector<unsigned char> buf;
+        for (int i = kMaxParamB; i < a.D; i++) put_complex(buf, dtype, b_pad[i]);
+        const size_t vb = 2 * real_size(dtype);
+        CUDA_OK(cudaMemcpyAsync(static_cast<unsigned char *>(state) + (size_t)kMaxParamB * vb,
+                                buf.data(), (size_t)rest * vb, cudaMemcpyHostToDevice, st));
+        CUDA_OK(cudaStreamSynchronize(st));
+    }
+}
+
+void readout_device(const void *state, int dtype, int n, int nb, int m, void *stream,
+                    double sums[3], cd *slice) {
+    (void)m;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long N = 1ll << n;
+    // fixed block count for a given n: chunks of 2^12 amplitudes, at most 2048 blocks
+    int lg = std::max(1, std::min(11, n - 12));
+    if (n <= 1) lg = 0;
+    const int nblk = 1 << lg;
+    const long long chunk = N / nblk;
+    const size_t vb = 2 * real_size(dtype);
+    const size_t slice_len = (size_t)1 << nb;
+    void *scratch = nullptr;
+    const size_t scratch_bytes = (size_t)nblk * 8 + 64 + slice_len * vb;
+    cudaError_t e = cudaMallocAsync(&scratch, scratch_bytes, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(QSIM_ENOMEM, std::string("cudaMallocAsync readout scratch: ") + cudaGetErrorString(e));
+    }
+    double *partials = static_cast<double *>(scratch);
+    double *out = partials + nblk;
+    const long long off = N / 2;  // ancilla = 1 (the top qubit), clock = 0
+    try {
+        if (dtype == QSIM_C128) {
+            norm_partials_kernel<double><<<nblk, 256, 0, st>>>(state, chunk, partials);
+            norm_final_kernel<double><<<1, 256, 0, st>>>(partials, nblk, state, off, (int)slice_len, out);
+        } else {
+            norm_partials_kernel<float><<<nblk, 256, 0, st>>>(state, chunk, partials);
+            norm_final_kernel<float><<<1, 256, 0, st>>>(partials, nblk, state, off, (int)slice_len, out);
+        }
+        check_launch("readout kernels");
+        std::vector<unsigned char> hs(slice_len * vb);
+        double hsum[3];
+        CUDA_OK(cudaMemcpyAsync(hsum, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_OK(cudaMemcpyAsync(hs.data(), static_cast<const unsigned char *>(state) + off * vb,
+                                slice_len * vb, cudaMemcpyDeviceToHost, st));
+        CUDA_OK(cudaFreeAsync(scratch, st));
+        scratch = nullptr;
+        CUDA_OK(cudaStreamSynchronize(st));
+        for (int i = 0; i < 3; i++) sums[i] = hsum[i];
+        for (size_t i = 0; i < slice_len; i++) {
+            if (dtype == QSIM_C128) {
+                const double *p = reinterpret_cast<const double *>(hs.data()) + 2 * i;
+                slice[i] = cd(p[0], p[1]);
+            } else {
+                const float *p = reinterpret_cast<const float *>(hs.data()) + 2 * i;
+                slice[i] = cd(p[0], p[1]);
+            }
+        }
+    } catch (...) {
+        if (scratch) cudaFreeAsync(scratch, st);
+        throw;
+    }
+}
+
+}  // namespace qsim
+
+using namespace qsim;
+
+qsim_circuit::~qsim_circuit() {
+    for (DeviceBlob &b : blob) {
+        if (b.ptr) {
+            int cur = -1;
+            cudaGetDevice(&cur);
+            if (cur != b.device) cudaSetDevice(b.device);
+            cudaFree(b.ptr);
+            if (cur != b.device && cur >= 0) cudaSetDevice(cur);
+            b.ptr = nullptr;
+        }
+    }
+}
+
+extern "C" void qsim_circuit_free(qsim_circuit *c) { delete c; }
+
+extern "C" int qsim_apply(void *state, int n_qubits, int dtype, const qsim_circuit *c, void *stream) {
+    return guarded([&] {
+        QSIM_REQUIRE(state != nullptr && c != nullptr, "NULL argument");
+        QSIM_REQUIRE(dtype == QSIM_C64 || dtype == QSIM_C128, "dtype must be QSIM_C64 or QSIM_C128");
+        QSIM_REQUIRE(n_qubits == c->n, "state qubit count does not match the circuit");
+        apply_ops(state, n_qubits, dtype, const_cast<qsim_circuit *>(c), stream);
+    });
+}

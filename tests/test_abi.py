@@ -1,0 +1,165 @@
+"""The C-ABI library loads and exports every symbol include/*.h declares; host-only calls and
+their error paths (no device compute, runs without a GPU)."""
+import ctypes
+import glob
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def qs():
+    from paper_2402_08136_gb300 import build
+    build.build()
+    import paper_2402_08136_gb300 as q
+    return q
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b((?:qsim|hhl)_\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(qs):
+    names = declared_functions()
+    assert len(names) >= 14
+    lib = ctypes.CDLL(qs.library_path())
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_version_and_error_text(qs):
+    assert "sm_103a" in qs.qsim_version()
+    with pytest.raises(qs.QsimError) as e:
+        qs.Circuit(0)
+    assert e.value.code == -1 and "n_qubits" in str(e.value)
+
+
+def test_gate_argument_checks(qs):
+    c = qs.Circuit(5)
+    U = synth.haar_unitary(np.random.default_rng(0), 4)
+    c.add_gate([0, 3], U, controls=[4])
+    for bad in ([0, 0], [0, 5], [-1, 2]):
+        with pytest.raises(qs.QsimError):
+            c.add_gate(bad, U)
+    with pytest.raises(qs.QsimError):
+        c.add_gate([0, 1], U, controls=[1])
+    Unan = U.copy()
+    Unan[0, 0] = np.nan
+    with pytest.raises(qs.QsimError):
+        c.add_gate([0, 1], Unan)
+    with pytest.raises(qs.QsimError):
+        c.add_ucry(0, [0, 1], np.zeros(4))
+    info = c.info()
+    assert info["n_gates"] == 1 and info["n_dense"] == 1
+
+
+def test_classification_of_specialised_gates(qs):
+    c = qs.Circuit(4)
+    c.add_gate([0, 1], np.diag([1, 1, 1, np.exp(0.3j)]))          # controlled phase
+    c.add_gate([2], np.diag([np.exp(0.1j), np.exp(-0.1j)]))      # RZ: diagonal
+    swap = np.eye(4)[[0, 2, 1, 3]]
+    c.add_gate([1, 3], swap)                                      # swap
+    c.add_gate([0], np.array([[0, 1], [1, 0]]))                   # X: dense
+    c.add_ucry(3, [0, 1, 2], np.linspace(0, 1, 8))
+    i = c.info()
+    assert (i["n_diag"], i["n_perm"], i["n_dense"], i["n_ucry"]) == (2, 1, 1, 1)
+
+
+def test_fusion_counts(qs):
+    # QFT-like circuit on 6 qubits: fusion to width 2 and 6 reduces the executed gate count
+    n = 6
+    c = qs.Circuit(n)
+    H = np.array([[1, 1], [1, -1]]) / math.sqrt(2)
+    gates = 0
+    for j in range(n - 1, -1, -1):
+        c.add_gate([j], H)
+        gates += 1
+        for l in range(j - 1, -1, -1):
+            c.add_gate([l, j], np.diag([1, 1, 1, np.exp(2j * math.pi / 2 ** (j - l + 1))]))
+            gates += 1
+    f2 = qs.qsim_fuse(c, 2).info()
+    f6 = qs.qsim_fuse(c, 6).info()
+    assert c.info()["n_gates"] == gates
+    assert f2["fused"] == 1 and f2["max_k"] <= 2 and f2["n_gates"] < gates
+    assert f6["n_gates"] == 1 and f6["max_k"] == 6
+
+
+def test_fusion_keeps_controlled_and_ucry(qs):
+    c = qs.Circuit(5)
+    U = synth.haar_unitary(np.random.default_rng(1), 4)
+    c.add_gate([0], np.eye(2))
+    c.add_gate([0, 1], U, controls=[2])
+    c.add_ucry(4, [2, 3], np.zeros(4))
+    c.add_gate([1], np.eye(2))
+    f = qs.qsim_fuse(c, 4).info()
+    assert f["n_ucry"] == 1 and f["n_gates"] == 4
+
+
+def test_hhl_build_host_side(qs):
+    p = synth.hhl7_problem()
+    h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"])
+    i = h.info()
+    assert (i["N"], i["nb"], i["m"], i["n"]) == (4, 2, 4, 7)
+    w = np.linalg.eigvalsh(p["A"])
+    assert abs(i["lambda_min"] - w[0]) < 1e-12 and abs(i["lambda_max"] - w[-1]) < 1e-12
+    assert abs(i["C"] - w[0]) < 1e-9          # exact grid: C = lambda_min
+    assert abs(i["norm_b"] - np.linalg.norm(p["b"])) < 1e-14
+    # gate count: m H + m controlled-U + IQFT (m H + m(m-1)/2 CP + m/2 swaps) + UCRY, mirrored
+    m = 4
+    qpe = m + m + m + m * (m - 1) // 2 + m // 2
+    assert i["n_gates"] == 2 * qpe + 1
+    circ = h.as_circuit().info()
+    assert circ["n_ucry"] == 1
+
+
+def test_hhl_default_clock_count_follows_formula(qs):
+    rng = np.random.default_rng(3)
+    A, b, _ = synth.grid_system(rng, 17, avg_degree=3.0)
+    h = qs.hhl_build(A, b)
+    i = h.info()
+    w = np.linalg.eigvalsh(A)
+    kappa = w[-1] / w[0]
+    assert i["m"] == max(4 + 1, math.ceil(math.log2(kappa + 1)))
+    assert i["n_total_formula"] == i["nb"] + i["m"] + 1
+
+
+def test_hhl_build_errors(qs):
+    A = np.array([[2.0, 1.0], [0.0, 3.0]])
+    with pytest.raises(qs.QsimError):
+        qs.hhl_build(A, [1.0, 0.0], 3)                 # not Hermitian
+    with pytest.raises(qs.QsimError):
+        qs.hhl_build(-np.eye(2), [1.0, 0.0], 3)        # not positive definite
+    with pytest.raises(qs.QsimError):
+        qs.hhl_build(np.eye(2), [0.0, 0.0], 3)         # b = 0
+    with pytest.raises(qs.QsimError):
+        qs.hhl_build(np.diag([1.0, 2.0]), [1.0, 1.0], 3, C=1.5)   # C above lambda_min
+    with pytest.raises(qs.QsimError):
+        qs.hhl_build(np.diag([1.0, np.nan]), [1.0, 1.0], 3)
+
+
+def test_hhl_build_matches_spectral_path(qs):
+    rng = np.random.default_rng(8)
+    V = synth.haar_unitary(rng, 5)
+    lam = np.array([1.0, 2.5, 3.0, 7.0, 9.0])
+    A = (V * lam) @ V.conj().T
+    A = 0.5 * (A + A.conj().T)
+    b = rng.standard_normal(5)
+    h1 = qs.hhl_build(A, b, 5).info()
+    h2 = qs.hhl_build_spectral(lam, V, b, 5).info()
+    for key in ("N", "nb", "m", "n", "n_gates"):
+        assert h1[key] == h2[key]
+    for key in ("t", "C", "lambda_min", "lambda_max"):
+        assert abs(h1[key] - h2[key]) < 1e-12 * max(1.0, abs(h2[key]))
