@@ -193,6 +193,21 @@ typedef struct {
 int hhl_readout(const void *state, int dtype, const hhl_circuit *h, void *stream, double *x_out,
                 double *x_state_out, hhl_readout_stats *stats);
 
+/* hhl_readout for callers that cannot allocate device memory.  The paper has no counterpart;
+ * this is a library convenience.  Such callers include an application whose own pool
+ * allocator already owns all device memory, and code that must not call cudaMalloc or
+ * cudaMallocAsync while it reads results.  Arguments, outputs, reductions and results are
+ * those of hhl_readout.  The scratch (per-block partial sums, the totals and an FP64 copy of
+ * the solution slice) is one fixed array inside the library, about 33 KB, which every GPU
+ * that loads the library holds until the process exits; no device or host memory is
+ * allocated per call.  Limit: 2^nb <= 1024 amplitudes (N <= 1024), otherwise QSIM_EINVAL.
+ * The first call on a device looks up the array's device address, so make that first call
+ * before any stream capture.  All calls share the one array: calls that overlap on the GPU
+ * (other streams, other host threads) race on it and must be serialized by the caller.  The
+ * call synchronizes `stream`.  Errors: EINVAL, ECUDA. */
+int hhl_readout_noalloc(const void *state, int dtype, const hhl_circuit *h, void *stream,
+                        double *x_out, double *x_state_out, hhl_readout_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -712,7 +712,117 @@ void readout_device(const void *state, int dtype, int n, int nb, int m, void *st
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Readout without any device allocation.
+//
+// Some callers cannot allocate device memory while they read a result: an application that
+// hands all device memory to its own pool allocator up front, or code that runs where
+// cudaMalloc/cudaMallocAsync must not be called.  hhl_readout_noalloc gives them the same
+// readout as hhl_readout with its scratch (the per-block partial sums, the three totals and a
+// double-precision copy of the solution slice) in the file-scope device array below, which
+// every GPU that loads this library holds until the process exits.
+namespace {
+constexpr int kNoAllocMaxBlocks = 2048;          // partial sums (the readout grid never exceeds it)
+constexpr int kNoAllocMaxSlice = 1 << 10;        // amplitudes of the solution slice (2^nb)
+constexpr int kNoAllocDoubles = kNoAllocMaxBlocks + 8 + 2 * kNoAllocMaxSlice;
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+template <typename R>
+__global__ void slice_to_f64_kernel(const void *state, long long off, int len, double *out) {
+    using V = typename C2<R>::T;
+    const V *psi = reinterpret_cast<const V *>(state) + off;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+        const V z = psi[i];
+        out[2 * i] = (double)z.x;
+        out[2 * i + 1] = (double)z.y;
+    }
+}
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device (the
+// array's name in host code is only a host-side stand-in, not a device address).
+static double *noalloc_scratch_on_current_device() {
+    static std::mutex mu;
+    static double *addr[128] = {};
+    int dev = 0;
+    CUDA_OK(cudaGetDevice(&dev));
+    QSIM_REQUIRE(dev >= 0 && dev < 128, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    if (addr[dev] == nullptr) {
+        void *p = nullptr;
+        CUDA_OK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        addr[dev] = static_cast<double *>(p);
+    }
+    return addr[dev];
+}
+
 }  // namespace qsim
+
+extern "C" int hhl_readout_noalloc(const void *state, int dtype, const hhl_circuit *h, void *stream,
+                                   double *x_out, double *x_state_out, hhl_readout_stats *stats) {
+    using namespace qsim;
+    return guarded([&] {
+        QSIM_REQUIRE(state != nullptr && h != nullptr, "NULL argument");
+        QSIM_REQUIRE(dtype == QSIM_C64 || dtype == QSIM_C128, "dtype must be QSIM_C64 or QSIM_C128");
+        const int n = h->n, nb = h->nb;
+        const long long slice_len = 1ll << nb;
+        if (slice_len > kNoAllocMaxSlice)
+            throw Error(QSIM_EINVAL, "hhl_readout_noalloc: the solution slice has 2^" + std::to_string(nb) +
+                                         " amplitudes, more than the fixed scratch holds (2^10, i.e. N <= 1024)");
+        int lg = std::max(1, std::min(11, n - 12));
+        if (n <= 1) lg = 0;
+        const int nblk = 1 << lg;
+        QSIM_REQUIRE(nblk <= kNoAllocMaxBlocks, "hhl_readout_noalloc: too many partial sums");
+        const long long N = 1ll << n;
+        const long long chunk = N / nblk;
+        const long long off = N / 2;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        double *scratch = noalloc_scratch_on_current_device();
+        double *partials = scratch;
+        double *out = scratch + kNoAllocMaxBlocks;
+        double *slice = scratch + kNoAllocMaxBlocks + 8;
+        // every slot read below is written earlier in this same call, so nothing is cleared
+        if (dtype == QSIM_C128) {
+            norm_partials_kernel<double><<<nblk, 256, 0, st>>>(state, chunk, partials);
+            norm_final_kernel<double><<<1, 256, 0, st>>>(partials, nblk, state, off, (int)slice_len, out);
+            slice_to_f64_kernel<double><<<(int)((slice_len + 255) / 256), 256, 0, st>>>(state, off, (int)slice_len, slice);
+        } else {
+            norm_partials_kernel<float><<<nblk, 256, 0, st>>>(state, chunk, partials);
+            norm_final_kernel<float><<<1, 256, 0, st>>>(partials, nblk, state, off, (int)slice_len, out);
+            slice_to_f64_kernel<float><<<(int)((slice_len + 255) / 256), 256, 0, st>>>(state, off, (int)slice_len, slice);
+        }
+        check_launch("hhl_readout_noalloc kernels");
+        double sums[3];
+        CUDA_OK(cudaMemcpyAsync(sums, out, sizeof(sums), cudaMemcpyDeviceToHost, st));
+        // the slice lands straight in the caller's buffer: all 2^nb amplitudes, or the first N
+        double *dst = x_state_out ? x_state_out : x_out;
+        const long long cnt = x_state_out ? slice_len : (long long)h->N;
+        if (dst) CUDA_OK(cudaMemcpyAsync(dst, slice, (size_t)cnt * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_OK(cudaStreamSynchronize(st));
+        const double P = sums[1], P0 = sums[2];
+        const double inv = P0 > 0.0 ? 1.0 / std::sqrt(P0) : 0.0;
+        const double norm_x = std::sqrt(P) / h->C;
+        if (x_state_out) {
+            if (x_out)
+                for (int i = 0; i < h->N; i++) {
+                    x_out[2 * i] = x_state_out[2 * i] * inv * norm_x * h->norm_b;
+                    x_out[2 * i + 1] = x_state_out[2 * i + 1] * inv * norm_x * h->norm_b;
+                }
+            for (long long i = 0; i < 2 * slice_len; i++) x_state_out[i] *= inv;
+        } else if (x_out) {
+            for (int i = 0; i < 2 * h->N; i++) x_out[i] *= inv * norm_x * h->norm_b;
+        }
+        if (stats) {
+            stats->p_success = P;
+            stats->p_clock0 = P0;
+            stats->leakage = P - P0;
+            stats->norm2 = sums[0];
+            stats->norm_x = norm_x;
+            stats->norm_b = h->norm_b;
+        }
+    });
+}
 
 using namespace qsim;
 
