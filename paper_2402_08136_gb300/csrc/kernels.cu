@@ -173,6 +173,128 @@ __global__ void __launch_bounds__(kThreads) dense_tile_kernel(const DenseArgs a)
     }
 }
 
+// Same operation with a multi-stage cp.async pipeline: while the CTA computes tile i from
+// shared memory, the copies of tiles i+1 .. i+NS-1 are in flight (16-byte cp.async chunks, each
+// chunk contiguous in HBM because the tile always contains qubit 0).  Results are stored from
+// registers straight to HBM.  Used whenever qubit 0 is a tile qubit (always for complex128).
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+constexpr int kStages = 3;
+
+template <typename R, int K, bool USMEM>
+__global__ void __launch_bounds__(kThreads) dense_pipe_kernel(const DenseArgs a) {
+    using V = typename C2<R>::T;
+    constexpr int D = 1 << K;
+    constexpr int RPT = D < 16 ? D : 16;
+    constexpr int RG = D / RPT;
+    constexpr int WPG = (kThreads / 32) / RG;
+    constexpr int CSTRIDE = 32 * WPG;
+    constexpr int EPC = 16 / sizeof(V);  // amplitudes per 16-byte chunk
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int T = a.T;
+    const int tile_amps = 1 << T;
+    const int G = tile_amps >> K;
+    V *stages = reinterpret_cast<V *>(smem_raw);
+    V *Us = stages + kStages * tile_amps;
+    int *toff = reinterpret_cast<int *>(Us + (USMEM ? D * D : 0));
+    long long *hoff = reinterpret_cast<long long *>(toff + ((D + 1) & ~1));
+
+    const int tid = threadIdx.x;
+    const V *Ug = reinterpret_cast<const V *>(a.U);
+    if (USMEM)
+        for (int i = tid; i < D * D; i += kThreads) Us[i] = Ug[i];
+    for (int c = tid; c < D; c += kThreads) {
+        int o = 0;
+        for (int b = 0; b < K; b++)
+            if ((c >> b) & 1) o |= 1 << a.tloc[b];
+        toff[c] = o;
+    }
+    const int nhv = 1 << a.nh;
+    for (int h = tid; h < nhv; h += kThreads) {
+        long long o = 0;
+        for (int i = 0; i < a.nh; i++)
+            if ((h >> i) & 1) o |= 1ll << a.hpos[i];
+        hoff[h] = o;
+    }
+    int tsorted[K];
+    for (int b = 0; b < K; b++) tsorted[b] = a.tloc[b];
+    for (int i = 1; i < K; i++) {
+        int v = tsorted[i], j = i - 1;
+        while (j >= 0 && tsorted[j] > v) { tsorted[j + 1] = tsorted[j]; j--; }
+        tsorted[j + 1] = v;
+    }
+    __syncthreads();
+
+    const int warp = tid >> 5, lane = tid & 31;
+    const int rg = warp % RG;
+    const int col0 = (warp / RG) * 32 + lane;
+    const int lomask = (1 << a.L0) - 1;
+    V *psi = reinterpret_cast<V *>(a.psi);
+    const long long first = blockIdx.x, stride = gridDim.x;
+    const long long ntl = first < a.ntiles ? (a.ntiles - first + stride - 1) / stride : 0;
+    const int nchunk = tile_amps / EPC;
+
+    auto tile_base = [&](long long i) -> unsigned long long {
+        return insert_zeros((unsigned long long)(first + i * stride) << a.L0, a.fix, a.nfix) | a.cmask;
+    };
+    auto issue = [&](long long i) {
+        const unsigned long long base = tile_base(i);
+        V *dst = stages + (int)(i % kStages) * tile_amps;
+        for (int ch = tid; ch < nchunk; ch += kThreads) {
+            const int l0 = ch * EPC;
+            cp_async16(dst + l0, psi + base + hoff[l0 >> a.L0] + (l0 & lomask));
+        }
+    };
+
+    for (int p = 0; p < kStages - 1; p++) {
+        if (p < ntl) issue(p);
+        cp_async_commit();
+    }
+    for (long long i = 0; i < ntl; i++) {
+        cp_async_wait<kStages - 2>();
+        __syncthreads();  // tile i visible to all; every thread is done with tile i-1's stage
+        if (i + kStages - 1 < ntl) issue(i + kStages - 1);
+        cp_async_commit();
+        const V *tile = stages + (int)(i % kStages) * tile_amps;
+        const unsigned long long base = tile_base(i);
+        for (int g = col0; g < G; g += CSTRIDE) {
+            int gl = g;
+#pragma unroll
+            for (int b = 0; b < K; b++) {
+                const int p = tsorted[b];
+                gl = ((gl >> p) << (p + 1)) | (gl & ((1 << p) - 1));
+            }
+            V acc[RPT];
+#pragma unroll
+            for (int r = 0; r < RPT; r++) acc[r] = V{0, 0};
+            for (int c = 0; c < D; c++) {
+                const V x = tile[gl + toff[c]];
+                const V *uc = (USMEM ? Us : Ug) + c * D + rg * RPT;
+#pragma unroll
+                for (int r = 0; r < RPT; r++) {
+                    const V u = uc[r];
+                    acc[r].x = fma(u.x, x.x, acc[r].x);
+                    acc[r].x = fma(-u.y, x.y, acc[r].x);
+                    acc[r].y = fma(u.x, x.y, acc[r].y);
+                    acc[r].y = fma(u.y, x.x, acc[r].y);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RPT; r++) {
+                const int l = gl + toff[rg * RPT + r];
+                psi[base + hoff[l >> a.L0] + (l & lomask)] = acc[r];
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
 // ---------------------------------------------------------------------------------------
 // Phase on the all-ones pattern of `mask` qubits: psi[i] *= ph for i with (i & mask) == mask.
 struct PhaseArgs {
@@ -417,15 +539,15 @@ int grid_for(long long work, int per_block) {
     return (int)std::max(1ll, std::min(blocks, cap));
 }
 
-int tile_bits(int dtype) { return dtype == QSIM_C128 ? 11 : 12; }
+int tile_bits(int dtype) { return dtype == QSIM_C128 ? 11 : 11; }
 
 template <typename R, int K, bool USMEM>
-void launch_dense_t(const DenseArgs &a, size_t smem, cudaStream_t st) {
-    auto kern = dense_tile_kernel<R, K, USMEM>;
-    static bool attr = false;
-    if (!attr) {
+void launch_dense_t(const DenseArgs &a, size_t smem, bool pipe, cudaStream_t st) {
+    auto kern = pipe ? dense_pipe_kernel<R, K, USMEM> : dense_tile_kernel<R, K, USMEM>;
+    static bool attr[2] = {false, false};
+    if (!attr[pipe]) {
         CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr = true;
+        attr[pipe] = true;
     }
     int per_sm = 0;
     CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
@@ -440,13 +562,17 @@ void launch_dense(const DenseArgs &a, int K, size_t smem_base, cudaStream_t st) 
     const size_t D = (size_t)1 << K;
     const size_t vb = 2 * sizeof(R);
     const size_t ubytes = D * D * vb;
-    const bool usmem = smem_base + ubytes <= 200 * 1024;
-    const size_t smem = smem_base + (usmem ? ubytes : 0);
+    const size_t tile_bytes = ((size_t)1 << a.T) * vb;
+    // the pipelined kernel needs qubit 0 in the tile (16-byte chunks contiguous in HBM)
+    const bool pipe = a.L0 >= 1 && smem_base + (kStages - 1) * tile_bytes <= 200 * 1024;
+    const size_t base = smem_base + (pipe ? (kStages - 1) * tile_bytes : 0);
+    const bool usmem = base + ubytes <= 200 * 1024;
+    const size_t smem = base + (usmem ? ubytes : 0);
     switch (K) {
 #define QSIM_K(k)                                                    \
     case k:                                                          \
-        if (usmem) launch_dense_t<R, k, true>(a, smem, st);          \
-        else launch_dense_t<R, k, false>(a, smem, st);               \
+        if (usmem) launch_dense_t<R, k, true>(a, smem, pipe, st);    \
+        else launch_dense_t<R, k, false>(a, smem, pipe, st);         \
         break;
         QSIM_K(1) QSIM_K(2) QSIM_K(3) QSIM_K(4) QSIM_K(5) QSIM_K(6) QSIM_K(7)
 #undef QSIM_K
