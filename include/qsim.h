@@ -126,6 +126,11 @@ int qsim_fuse(const qsim_circuit *in, int max_k, qsim_circuit **out);
  * qsim_circuit_free.  Errors: EINVAL (size/dtype mismatch, NULL), ENOMEM, ECUDA. */
 int qsim_apply(void *state, int n_qubits, int dtype, const qsim_circuit *c, void *stream);
 
+/* Sticky device-side error flags of this process's kernels (bit 0: a bounded wait inside a
+ * tensor-core kernel ran out, its results are invalid).  Synchronizes the device; clear != 0
+ * resets the flags.  Errors: EINVAL, ECUDA. */
+int qsim_device_status(unsigned *flags, int clear);
+
 /* ======================================================================================= *
  * HHL (Sec. III-A procedure, Fig. 5 circuit, Sec. III-B resources)                         *
  * ======================================================================================= */

@@ -19,6 +19,7 @@ from ._binding import (  # noqa: F401
     library,
     library_path,
     qsim_apply,
+    qsim_device_status,
     qsim_fuse,
     qsim_version,
 )

@@ -68,6 +68,7 @@ _SIGS = {
     "hhl_as_circuit": ([_VP], _VP),
     "hhl_get_info": ([_VP, ctypes.POINTER(_HHLInfo)], ctypes.c_int),
     "hhl_prepare_state": ([_VP, ctypes.c_int, _VP, _VP], ctypes.c_int),
+    "qsim_device_status": ([ctypes.POINTER(ctypes.c_uint), ctypes.c_int], ctypes.c_int),
     "hhl_readout": ([_VP, ctypes.c_int, _VP, _VP, _DP, _DP, ctypes.POINTER(_ReadoutStats)],
                     ctypes.c_int),
 }
@@ -128,6 +129,13 @@ def _dtype_of(state):
 def _check_state(state, n: int):
     if not state.is_cuda or not state.is_contiguous() or state.numel() != (1 << n):
         raise QsimError(-1, "state must be a contiguous CUDA tensor of 2^n amplitudes")
+
+
+def qsim_device_status(clear: bool = False) -> int:
+    """Sticky device-side error flags (bit 0: a bounded wait in a tensor-core kernel ran out)."""
+    v = ctypes.c_uint(0)
+    _check(library().qsim_device_status(ctypes.byref(v), 1 if clear else 0))
+    return int(v.value)
 
 
 def qsim_version() -> str:

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "../../include/qsim.h"
 
 namespace qsim {
@@ -77,6 +79,9 @@ struct Op {
     std::vector<double> theta;  // OP_UCRY
     // device offsets (bytes) into the circuit's device blob, per dtype
     size_t dev_off[2] = {0, 0};
+    // complex64 dense ops with 4..6 targets: TF32 hi/lo split of the real form (tensor cores)
+    size_t dev_off_tc = 0;
+    bool has_tc = false;
 };
 
 struct DeviceBlob {
@@ -118,6 +123,12 @@ void ensure_device_blob(qsim_circuit *c, int dtype);
 void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb, void *stream);
 void readout_device(const void *state, int dtype, int n, int nb, int m, void *stream,
                     double sums[3], cd *slice);
+// dense_tc.cu
+bool dense_tc_supported(int k);
+size_t dense_tc_blob_bytes(int k);
+void dense_tc_pack(int k, const std::vector<cd> &U, unsigned char *out);
+bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const std::vector<int> &controls,
+                     const void *Bdev, int sms, cudaStream_t st);
 // linalg.cpp
 void hermitian_eig(int N, const std::vector<cd> &A, std::vector<double> &lam, std::vector<cd> &V);
 }  // namespace qsim

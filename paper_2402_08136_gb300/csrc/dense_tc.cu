@@ -1,0 +1,430 @@
+// Dense k-qubit gate on a complex64 state with the 5th-generation tensor cores (sm_103a):
+// tcgen05.mma kind::tf32, accumulators in tensor memory, split-precision "3xTF32" products.
+//
+// The update of every group of 2^k amplitudes (the amplitudes that differ only in the target
+// bits) is a complex matrix-vector product; 128 groups at a time it is the real GEMM
+//     Y[128 x 2D] = X[128 x 2D] * B^T,   D = 2^k,
+// where row m of X holds group m's amplitudes as (re_0, im_0, re_1, im_1, ...) and B is the
+// real 2D x 2D form of U: B[2r][2c] = B[2r+1][2c+1] = Re U[r][c], B[2r][2c+1] = -Im U[r][c],
+// B[2r+1][2c] = Im U[r][c].  Each FP32 operand is split into a TF32 "hi" part and a TF32 "lo"
+// part (x - hi rounded to TF32); Y = Xhi Bhi^T + Xhi Blo^T + Xlo Bhi^T accumulates in FP32,
+// which keeps ~22 significant bits per product (Markidis et al., "NVIDIA Tensor Core
+// Programmability, Performance & Precision", 2018, for the split scheme).
+//
+// CTA (one per SM, persistent): 256 threads.  B (hi and lo, host-split, canonical K-major
+// layout) stays in shared memory.  X is produced in chunks of 16 amplitudes (32 K-columns) per
+// group: every thread owns one group row m and half of the chunk, keeps three chunks of loads
+// in flight in registers, splits them into hi/lo and writes them to a ring of shared-memory
+// chunk buffers; thread 0 issues the 3 x 4 MMAs of a chunk and commits them to the buffer's
+// mbarrier, so loads, conversion and MMAs of consecutive chunks overlap.  After a tile's last
+// chunk all 8 warps read the accumulator from tensor memory (warps w and w+4 share lanes
+// 32(w%4).., splitting the columns) and store the 128 x D outputs straight to HBM.
+//
+// Shared-memory operand layout (no swizzle, K-major): 8-row x 16-byte core matrices; core
+// matrices adjacent along K are 128 bytes apart (leading byte offset), adjacent along M/N
+// (K/4) * 128 bytes apart (stride byte offset).
+//
+// Every wait on an mbarrier is bounded; on timeout the kernel raises a flag in device memory
+// (read by qsim_device_status), skips the remaining work, releases its tensor memory and exits.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "common.h"
+
+namespace qsim {
+
+__device__ unsigned int g_device_error = 0;
+
+namespace tc {
+
+constexpr int kThreads = 256;
+constexpr int kM = 128;      // groups per tile (MMA M)
+constexpr int kCH = 32;      // K-columns per chunk (16 complex amplitudes)
+constexpr int kNBuf = 3;     // chunk ring
+constexpr int kMaxFix = 40;
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
+
+struct Args {
+    void *psi;
+    const float *Bg;          // B_hi then B_lo, canonical layout, N*KK floats each
+    long long ntiles;         // groups / 128
+    unsigned long long cmask;
+    int nfix;
+    int fix[kMaxFix];         // ascending: targets and controls
+    int targets[8];
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t make_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    return d;                // base offset 0, no swizzle
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase with the given parity to complete: gives up after about one
+// second of wall-clock time and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    const unsigned a = smem_u32(bar);
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; it++) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 255) == 0) {
+            const unsigned long long t = global_ns();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > kWaitLimitNs) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned to_tf32(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long insert_zeros(unsigned long long x, const int *pos, int cnt) {
+    for (int i = 0; i < cnt; i++) {
+        const int p = pos[i];
+        x = ((x >> p) << (p + 1)) | (x & ((1ull << p) - 1ull));
+    }
+    return x;
+}
+
+template <int K>
+struct Cfg {
+    static constexpr int D = 1 << K;
+    static constexpr int N = 2 * D;       // MMA N (output reals per group)
+    static constexpr int KK = 2 * D;      // reduction length
+    static constexpr int NCH = KK / kCH;  // chunks per tile
+    static constexpr int BBYTES = N * KK * 4;
+    static constexpr int ABYTES = kM * kCH * 4;
+    static constexpr int SMEM = 2 * BBYTES + kNBuf * 2 * ABYTES + 8 * (kNBuf + 2) + 16 + 8 * D;
+    static constexpr unsigned IDESC = (1u << 4)          // D format F32
+                                      | (2u << 7)        // A format TF32
+                                      | (2u << 10)       // B format TF32
+                                      | ((unsigned)(N >> 3) << 17) | ((unsigned)(kM >> 4) << 24);
+};
+
+template <int K>
+__global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const Args a) {
+    using C = Cfg<K>;
+    constexpr int D = C::D, N = C::N, KK = C::KK, NCH = C::NCH;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float *Bs = reinterpret_cast<float *>(sm);                               // [2][N*KK]
+    unsigned char *Aring = sm + 2 * C::BBYTES;                               // [kNBuf][2][ABYTES]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(Aring + kNBuf * 2 * C::ABYTES);  // kNBuf + 1
+    unsigned *tslot = reinterpret_cast<unsigned *>(mbar + kNBuf + 2);
+    long long *toff = reinterpret_cast<long long *>(tslot + 4);              // D entries
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // ---- set-up: B into shared memory, target offsets, barriers, tensor memory
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(a.Bg);
+        float4 *dst = reinterpret_cast<float4 *>(Bs);
+        for (int i = tid; i < 2 * C::BBYTES / 16; i += kThreads) dst[i] = src[i];
+        for (int c = tid; c < D; c += kThreads) {
+            long long o = 0;
+            for (int b = 0; b < K; b++)
+                if ((c >> b) & 1) o |= 1ll << a.targets[b];
+            toff[c] = o;
+        }
+        if (tid == 0) {
+            for (int i = 0; i < kNBuf + 1; i++) mbar_init(&mbar[i], 1);
+        }
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                         "r"((unsigned)N)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    }
+    const unsigned tmem = *tslot;
+
+    const int m = tid & (kM - 1);   // group row owned by this thread
+    const int h = tid >> 7;         // which half (8 amplitudes) of each 16-amplitude chunk
+    float2 *psi = reinterpret_cast<float2 *>(a.psi);
+    const long long first = blockIdx.x, stride = gridDim.x;
+    const long long ntl = first < a.ntiles ? (a.ntiles - first + stride - 1) / stride : 0;
+    const long long total = ntl * NCH;
+    bool failed = false;
+
+    auto group_base = [&](long long tile_i) -> unsigned long long {
+        const unsigned long long gidx = (unsigned long long)(first + tile_i * stride) * kM + m;
+        return insert_zeros(gidx, a.fix, a.nfix) | a.cmask;
+    };
+    auto prefetch = [&](long long qq, float2(&r)[8]) {
+        if (qq < total) {
+            const unsigned long long gb = group_base(qq / NCH);
+            const int c0 = (int)(qq % NCH) * 16 + 8 * h;
+#pragma unroll
+            for (int e = 0; e < 8; e++) r[e] = __ldcs(psi + gb + toff[c0 + e]);
+        }
+    };
+    const unsigned aring_u32 = smem_u32(Aring);
+    const unsigned bs_u32 = smem_u32(Bs);
+
+    auto step = [&](long long qq, float2(&r)[8]) {
+        if (qq >= total || failed) return;
+        const int b = (int)(qq % kNBuf);
+        const long long use = qq / kNBuf;
+        // buffer b is free once the MMAs of its previous chunk completed; the decision to
+        // give up is made by the whole CTA so no thread is left behind at a barrier
+        const bool ok = use == 0 || mbar_wait(&mbar[b], (unsigned)((use - 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            return;
+        }
+        // split into TF32 hi / lo and write row m, columns [16h, 16h+16) of the chunk
+        unsigned char *ahi = Aring + b * 2 * C::ABYTES;
+        unsigned char *alo = ahi + C::ABYTES;
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const int k = 16 * h + 2 * e;  // K-column of the real part
+            const unsigned off = (m >> 3) * 1024 + (k >> 2) * 128 + (m & 7) * 16 + (k & 3) * 4;
+            const unsigned hx = to_tf32(r[e].x), hy = to_tf32(r[e].y);
+            const unsigned lx = to_tf32(r[e].x - __uint_as_float(hx));
+            const unsigned ly = to_tf32(r[e].y - __uint_as_float(hy));
+            *reinterpret_cast<uint2 *>(ahi + off) = make_uint2(hx, hy);
+            *reinterpret_cast<uint2 *>(alo + off) = make_uint2(lx, ly);
+        }
+        prefetch(qq + 3, r);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        const int j = (int)(qq % NCH);
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned a_hi = aring_u32 + b * 2 * C::ABYTES, a_lo = a_hi + C::ABYTES;
+            const unsigned b_hi = bs_u32, b_lo = bs_u32 + C::BBYTES;
+#pragma unroll
+            for (int kk = 0; kk < kCH / 8; kk++) {
+                const unsigned aoff = kk * 256;                       // 2 core matrices along K
+                const unsigned boff = (j * (kCH / 4) + kk * 2) * 128;
+                const uint64_t dAh = make_desc(a_hi + aoff, 128, 1024);
+                const uint64_t dAl = make_desc(a_lo + aoff, 128, 1024);
+                const uint64_t dBh = make_desc(b_hi + boff, 128, KK * 32);
+                const uint64_t dBl = make_desc(b_lo + boff, 128, KK * 32);
+                const unsigned acc0 = (j == 0 && kk == 0) ? 0u : 1u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                    "l"(dAh), "l"(dBh), "r"(C::IDESC), "r"(acc0)
+                    : "memory");
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                    "l"(dAh), "l"(dBl), "r"(C::IDESC), "r"(1u)
+                    : "memory");
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                    "l"(dAl), "l"(dBh), "r"(C::IDESC), "r"(1u)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&mbar[b]))
+                         : "memory");
+            if (j == NCH - 1)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 smem_u32(&mbar[kNBuf]))
+                             : "memory");
+        }
+        if (j == NCH - 1) {
+            // epilogue: accumulator -> HBM
+            const long long tile_i = qq / NCH;
+            const bool ok = mbar_wait(&mbar[kNBuf], (unsigned)(tile_i & 1));
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                return;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned long long gb = group_base(tile_i);
+            const unsigned lane_base = (unsigned)(warp & 3) * 32;
+            constexpr int HALF = N / 2;
+#pragma unroll
+            for (int cb = 0; cb < HALF; cb += 16) {
+                const int col = (warp >> 2) * HALF + cb;
+                unsigned v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                      "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                    : "r"(tmem + (lane_base << 16) + (unsigned)col));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                // thread's TMEM lane is its own group row m (lane_base + lane == m)
+#pragma unroll
+                for (int i = 0; i < 8; i++) {
+                    const int rr = col / 2 + i;
+                    __stcs(psi + gb + toff[rr], make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])));
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncthreads();
+        }
+    };
+
+    float2 r0[8], r1[8], r2[8];
+    prefetch(0, r0);
+    prefetch(1, r1);
+    prefetch(2, r2);
+    for (long long qq = 0; qq < total && !failed; qq += 3) {
+        step(qq, r0);
+        step(qq + 1, r1);
+        step(qq + 2, r2);
+    }
+    if (failed) atomicOr(&g_device_error, 1u);
+    // drain: all MMAs this CTA issued must be complete before tensor memory is released
+    if (!failed && total > 0) {  // already complete after the last epilogue; bounded anyway
+        if (!mbar_wait(&mbar[kNBuf], (unsigned)((ntl - 1) & 1))) atomicOr(&g_device_error, 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((unsigned)N)
+                     : "memory");
+    }
+}
+
+}  // namespace tc
+
+// Host-side split of the real form of U into TF32 hi/lo in the canonical shared-memory
+// layout (row n = output real index, column k = input real index).
+static unsigned tf32_rne_bits(float x) {
+    unsigned u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return u;  // inf/nan: keep
+    u += 0xFFFu + ((u >> 13) & 1u);
+    return u & 0xFFFFE000u;
+}
+
+size_t dense_tc_blob_bytes(int k) {
+    const size_t D = (size_t)1 << k;
+    return 2 * (2 * D) * (2 * D) * 4;
+}
+
+bool dense_tc_supported(int k) { return k >= 4 && k <= 6; }
+
+void dense_tc_pack(int k, const std::vector<cd> &U, unsigned char *out) {
+    const int D = 1 << k, N = 2 * D, KK = 2 * D;
+    float *hi = reinterpret_cast<float *>(out);
+    float *lo = hi + (size_t)N * KK;
+    for (int n = 0; n < N; n++)
+        for (int kc = 0; kc < KK; kc++) {
+            const int r = n >> 1, pr = n & 1, c = kc >> 1, pc = kc & 1;
+            const cd u = U[(size_t)r * D + c];
+            double v;
+            if (pr == 0) v = pc == 0 ? u.real() : -u.imag();
+            else v = pc == 0 ? u.imag() : u.real();
+            const float f = (float)v;
+            const unsigned hb = tf32_rne_bits(f);
+            float hf;
+            std::memcpy(&hf, &hb, 4);
+            const unsigned lb = tf32_rne_bits(f - hf);
+            float lf;
+            std::memcpy(&lf, &lb, 4);
+            const size_t idx = ((size_t)(n >> 3) * (KK * 32) + (size_t)(kc >> 2) * 128 + (n & 7) * 16 + (kc & 3) * 4) / 4;
+            hi[idx] = hf;
+            lo[idx] = lf;
+        }
+}
+
+template <int K>
+static void launch_tc_t(const tc::Args &a, int sms, cudaStream_t st) {
+    using C = tc::Cfg<K>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc::dense_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_kernel attribute: ") + cudaGetErrorString(e));
+        attr = true;
+    }
+    const long long grid = std::min<long long>(a.ntiles, sms);
+    tc::dense_tc_kernel<K><<<(int)grid, tc::kThreads, C::SMEM, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_kernel: ") + cudaGetErrorString(e));
+}
+
+// Returns false if this gate shape is not handled by the tensor-core kernel.
+bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const std::vector<int> &controls,
+                     const void *Bdev, int sms, cudaStream_t st) {
+    const int K = (int)targets.size();
+    if (!dense_tc_supported(K)) return false;
+    const int free_bits = n - K - (int)controls.size();
+    if (free_bits < 7) return false;  // fewer than 128 groups
+    tc::Args a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = state;
+    a.Bg = static_cast<const float *>(Bdev);
+    a.ntiles = 1ll << (free_bits - 7);
+    std::vector<int> fix(targets);
+    for (int q : controls) {
+        fix.push_back(q);
+        a.cmask |= 1ull << q;
+    }
+    std::sort(fix.begin(), fix.end());
+    if ((int)fix.size() > tc::kMaxFix) return false;
+    a.nfix = (int)fix.size();
+    for (int i = 0; i < a.nfix; i++) a.fix[i] = fix[i];
+    for (int b = 0; b < K; b++) a.targets[b] = targets[b];
+    switch (K) {
+        case 4: launch_tc_t<4>(a, sms, st); break;
+        case 5: launch_tc_t<5>(a, sms, st); break;
+        case 6: launch_tc_t<6>(a, sms, st); break;
+        default: return false;
+    }
+    return true;
+}
+
+unsigned read_device_error() {
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_device_error, sizeof(v));
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("reading device status: ") + cudaGetErrorString(e));
+    return v;
+}
+
+void clear_device_error() {
+    const unsigned z = 0;
+    cudaError_t e = cudaMemcpyToSymbol(g_device_error, &z, sizeof(z));
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("clearing device status: ") + cudaGetErrorString(e));
+}
+
+}  // namespace qsim
+
+extern "C" int qsim_device_status(unsigned *flags, int clear) {
+    using namespace qsim;
+    return guarded([&] {
+        QSIM_REQUIRE(flags != nullptr, "NULL argument");
+        *flags = read_device_error();
+        if (clear) clear_device_error();
+    });
+}

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -694,6 +695,17 @@ void run_ucry(void *state, int n, int dtype, const Op &op, const void *csdev, cu
     check_launch("ucry_kernel");
 }
 
+// Tensor-core dense path for complex64 (QSIM_DENSE_TC=0 in the environment selects the SIMT
+// kernel instead, for comparisons).
+bool tc_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("QSIM_DENSE_TC");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 }  // namespace
 
 // Pack every op's device data (dense matrices transposed, diagonals, UCRY (cos, sin) tables)
@@ -715,6 +727,14 @@ void ensure_device_blob(qsim_circuit *c, int dtype) {
             const int D = 1 << (int)op.targets.size();
             for (int col = 0; col < D; col++)
                 for (int r = 0; r < D; r++) put_complex(blob, dtype, op.U[(size_t)r * D + col]);
+            if (dtype == QSIM_C64 && dense_tc_supported((int)op.targets.size())) {
+                align_blob(blob);
+                op.dev_off_tc = blob.size();
+                op.has_tc = true;
+                const size_t nb = dense_tc_blob_bytes((int)op.targets.size());
+                blob.resize(blob.size() + nb);
+                dense_tc_pack((int)op.targets.size(), op.U, blob.data() + op.dev_off_tc);
+            }
         } else if (op.kind == OP_DIAG) {
             for (const cd &z : op.U) put_complex(blob, dtype, z);
         } else if (op.kind == OP_UCRY) {
@@ -747,7 +767,12 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream) {
     for (const Op &op : c->ops) {
         const void *dptr = base + op.dev_off[slot];
         switch (op.kind) {
-            case OP_DENSE: run_dense(state, n, dtype, op, dptr, st); break;
+            case OP_DENSE:
+                if (dtype == QSIM_C64 && op.has_tc && tc_enabled() &&
+                    launch_dense_tc(state, n, op.targets, op.controls, base + op.dev_off_tc, num_sms(), st))
+                    break;
+                run_dense(state, n, dtype, op, dptr, st);
+                break;
             case OP_PHASE: run_phase(state, n, dtype, op, st); break;
             case OP_DIAG: run_diag(state, n, dtype, op, dptr, st); break;
             case OP_SWAP: run_swap(state, n, dtype, op, st); break;
