@@ -11,14 +11,17 @@
 // which keeps ~22 significant bits per product (Markidis et al., "NVIDIA Tensor Core
 // Programmability, Performance & Precision", 2018, for the split scheme).
 //
-// CTA (one per SM, persistent): 256 threads.  B (hi and lo, host-split, canonical K-major
-// layout) stays in shared memory.  X is produced in chunks of 16 amplitudes (32 K-columns) per
-// group: every thread owns one group row m and half of the chunk, keeps three chunks of loads
-// in flight in registers, splits them into hi/lo and writes them to a ring of shared-memory
-// chunk buffers; thread 0 issues the 3 x 4 MMAs of a chunk and commits them to the buffer's
-// mbarrier, so loads, conversion and MMAs of consecutive chunks overlap.  After a tile's last
-// chunk all 8 warps read the accumulator from tensor memory (warps w and w+4 share lanes
-// 32(w%4).., splitting the columns) and store the 128 x D outputs straight to HBM.
+// CTA (persistent, as many per SM as shared and tensor memory allow): 13 warps in three roles
+// coupled only through mbarriers.  B (hi and lo, host-split, canonical K-major layout) stays in
+// shared memory.  X is produced in chunks of 16 amplitudes (32 K-columns) per group by 8
+// producer warps: every producer thread owns one group row m and half of each chunk, keeps
+// four chunks of loads in flight in registers, splits them into hi/lo, writes them into a ring
+// of shared-memory chunk buffers and arrives on the buffer's "full" barrier.  One lane of the
+// MMA warp waits for full buffers, issues the 3 x 4 MMAs of a chunk and commits them to the
+// buffer's "empty" barrier (and, after a tile's last chunk, to the accumulator's barrier).  Two
+// accumulators alternate between tiles; 4 epilogue warps (one per TMEM lane subpartition, lane
+// = group row) read a finished accumulator, store its 128 x D outputs straight to HBM and hand
+// it back, so the MMAs of one tile overlap the epilogue of the previous one.
 //
 // Shared-memory operand layout (no swizzle, K-major): 8-row x 16-byte core matrices; core
 // matrices adjacent along K are 128 bytes apart (leading byte offset), adjacent along M/N
@@ -39,7 +42,6 @@ __device__ unsigned int g_device_error = 0;
 
 namespace tc {
 
-constexpr int kThreads = 256;
 constexpr int kM = 128;      // groups per tile (MMA M)
 constexpr int kCH = 32;      // K-columns per chunk (16 complex amplitudes)
 constexpr int kNBuf = 3;     // chunk ring
@@ -102,6 +104,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
     }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(unsigned d_tmem, uint64_t adesc, uint64_t bdesc, unsigned idesc,
+                                         unsigned accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// arrive on `bar` once every tcgen05 operation issued so far by this thread has completed
+__device__ __forceinline__ void commit_to(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
 __device__ __forceinline__ unsigned to_tf32(float x) {
     unsigned r;
     asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
@@ -124,42 +146,66 @@ struct Cfg {
     static constexpr int NCH = KK / kCH;  // chunks per tile
     static constexpr int BBYTES = N * KK * 4;
     static constexpr int ABYTES = kM * kCH * 4;
-    static constexpr int SMEM = 2 * BBYTES + kNBuf * 2 * ABYTES + 8 * (kNBuf + 2) + 16 + 8 * D;
+    static constexpr int NBAR = 2 * kNBuf + 4;  // full/empty per buffer, accfull/accempty x2
+    static constexpr int SMEM = 2 * BBYTES + kNBuf * 2 * ABYTES + 8 * NBAR + 16 + 8 * D;
+    static constexpr int TMEM_COLS = 2 * N;  // two accumulators: the MMAs of a tile overlap
+                                             // the previous tile's epilogue
     static constexpr unsigned IDESC = (1u << 4)          // D format F32
                                       | (2u << 7)        // A format TF32
                                       | (2u << 10)       // B format TF32
                                       | ((unsigned)(N >> 3) << 17) | ((unsigned)(kM >> 4) << 24);
 };
 
+// Warp roles: warps 0-7 produce (256 threads; thread t owns group row t % 128 and half t / 128
+// of every chunk), warps 8-11 run the epilogue (warp 8+i reads TMEM lanes 32i..32i+31),
+// warp 12 issues the MMAs.  Roles hand chunks and accumulators to each other through
+// mbarriers only, so no role waits for another except for data it needs.
+constexpr int kProducers = 256;
+constexpr int kEpiWarp0 = 8;
+constexpr int kMmaWarp = 12;
+constexpr int kThreadsWS = 13 * 32;
+constexpr int kPrefetch = 4;  // chunks of loads in flight per producer thread
+
 template <int K>
-__global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const Args a) {
+__global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
     using C = Cfg<K>;
     constexpr int D = C::D, N = C::N, KK = C::KK, NCH = C::NCH;
     extern __shared__ __align__(1024) unsigned char sm[];
     float *Bs = reinterpret_cast<float *>(sm);                               // [2][N*KK]
     unsigned char *Aring = sm + 2 * C::BBYTES;                               // [kNBuf][2][ABYTES]
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(Aring + kNBuf * 2 * C::ABYTES);  // kNBuf + 1
-    unsigned *tslot = reinterpret_cast<unsigned *>(mbar + kNBuf + 2);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(Aring + kNBuf * 2 * C::ABYTES);
+    uint64_t *full = bars;                    // [kNBuf] producers -> MMA (count 256)
+    uint64_t *empty = bars + kNBuf;           // [kNBuf] MMA completion -> producers (commit)
+    uint64_t *accfull = bars + 2 * kNBuf;     // [2] MMA completion -> epilogue (commit)
+    uint64_t *accempty = bars + 2 * kNBuf + 2;  // [2] epilogue -> MMA (count 128)
+    unsigned *tslot = reinterpret_cast<unsigned *>(bars + C::NBAR);
     long long *toff = reinterpret_cast<long long *>(tslot + 4);              // D entries
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // ---- set-up: B into shared memory, target offsets, barriers, tensor memory
     {
         const float4 *src = reinterpret_cast<const float4 *>(a.Bg);
         float4 *dst = reinterpret_cast<float4 *>(Bs);
-        for (int i = tid; i < 2 * C::BBYTES / 16; i += kThreads) dst[i] = src[i];
-        for (int c = tid; c < D; c += kThreads) {
+        for (int i = tid; i < 2 * C::BBYTES / 16; i += kThreadsWS) dst[i] = src[i];
+        for (int c = tid; c < D; c += kThreadsWS) {
             long long o = 0;
             for (int b = 0; b < K; b++)
                 if ((c >> b) & 1) o |= 1ll << a.targets[b];
             toff[c] = o;
         }
         if (tid == 0) {
-            for (int i = 0; i < kNBuf + 1; i++) mbar_init(&mbar[i], 1);
+            for (int i = 0; i < kNBuf; i++) {
+                mbar_init(&full[i], kProducers);
+                mbar_init(&empty[i], 1);
+            }
+            for (int i = 0; i < 2; i++) {
+                mbar_init(&accfull[i], 1);
+                mbar_init(&accempty[i], 128);
+            }
         }
         if (warp == 0) {
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
-                         "r"((unsigned)N)
+                         "r"((unsigned)C::TMEM_COLS)
                          : "memory");
             asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -169,62 +215,112 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const Args a) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     }
     const unsigned tmem = *tslot;
-
-    const int m = tid & (kM - 1);   // group row owned by this thread
-    const int h = tid >> 7;         // which half (8 amplitudes) of each 16-amplitude chunk
     float2 *psi = reinterpret_cast<float2 *>(a.psi);
     const long long first = blockIdx.x, stride = gridDim.x;
     const long long ntl = first < a.ntiles ? (a.ntiles - first + stride - 1) / stride : 0;
     const long long total = ntl * NCH;
     bool failed = false;
 
-    auto group_base = [&](long long tile_i) -> unsigned long long {
+    auto group_base = [&](long long tile_i, int m) -> unsigned long long {
         const unsigned long long gidx = (unsigned long long)(first + tile_i * stride) * kM + m;
         return insert_zeros(gidx, a.fix, a.nfix) | a.cmask;
     };
-    auto prefetch = [&](long long qq, float2(&r)[8]) {
-        if (qq < total) {
-            const unsigned long long gb = group_base(qq / NCH);
-            const int c0 = (int)(qq % NCH) * 16 + 8 * h;
-#pragma unroll
-            for (int e = 0; e < 8; e++) r[e] = __ldcs(psi + gb + toff[c0 + e]);
-        }
-    };
-    const unsigned aring_u32 = smem_u32(Aring);
-    const unsigned bs_u32 = smem_u32(Bs);
 
-    auto step = [&](long long qq, float2(&r)[8]) {
-        if (qq >= total || failed) return;
-        const int b = (int)(qq % kNBuf);
-        const long long use = qq / kNBuf;
-        // buffer b is free once the MMAs of its previous chunk completed; the decision to
-        // give up is made by the whole CTA so no thread is left behind at a barrier
-        const bool ok = use == 0 || mbar_wait(&mbar[b], (unsigned)((use - 1) & 1));
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            return;
-        }
-        // split into TF32 hi / lo and write row m, columns [16h, 16h+16) of the chunk
-        unsigned char *ahi = Aring + b * 2 * C::ABYTES;
-        unsigned char *alo = ahi + C::ABYTES;
+    if (warp < kEpiWarp0) {
+        // ------------------------------------------------------------------ producers
+        const int m = tid & (kM - 1), h = tid >> 7;
+        const int sw = (m >> 3) & 1;  // rows m and m+8 share banks: swap amplitude pairs
+        float2 r[kPrefetch][8];
+        auto load = [&](long long qq, float2(&rr)[8]) {
+            if (qq < total) {
+                const unsigned long long gb = group_base(qq / NCH, m);
+                const int c0 = (int)(qq % NCH) * 16 + 8 * h;
 #pragma unroll
-        for (int e = 0; e < 8; e++) {
-            const int k = 16 * h + 2 * e;  // K-column of the real part
-            const unsigned off = (m >> 3) * 1024 + (k >> 2) * 128 + (m & 7) * 16 + (k & 3) * 4;
-            const unsigned hx = to_tf32(r[e].x), hy = to_tf32(r[e].y);
-            const unsigned lx = to_tf32(r[e].x - __uint_as_float(hx));
-            const unsigned ly = to_tf32(r[e].y - __uint_as_float(hy));
-            *reinterpret_cast<uint2 *>(ahi + off) = make_uint2(hx, hy);
-            *reinterpret_cast<uint2 *>(alo + off) = make_uint2(lx, ly);
+                for (int e = 0; e < 8; e++) rr[e] = __ldcs(psi + gb + toff[c0 + e]);
+            }
+        };
+#pragma unroll
+        for (int p = 0; p < kPrefetch; p++) load(p, r[p]);
+        for (long long q0 = 0; q0 < total && !failed; q0 += kPrefetch) {
+#pragma unroll
+            for (int p = 0; p < kPrefetch; p++) {
+                const long long qq = q0 + p;
+                if (qq >= total || failed) break;
+                const int b = (int)(qq % kNBuf);
+                const long long use = qq / kNBuf;
+                if (use > 0 && !mbar_wait(&empty[b], (unsigned)((use - 1) & 1))) {
+                    failed = true;
+                    break;
+                }
+                unsigned char *ahi = Aring + b * 2 * C::ABYTES;
+                unsigned char *alo = ahi + C::ABYTES;
+#pragma unroll
+                for (int e = 0; e < 8; e++) {
+                    const float2 x = sw ? r[p][e ^ 1] : r[p][e];
+                    const int k = 16 * h + 2 * (e ^ sw);
+                    const unsigned off = (m >> 3) * 1024 + (k >> 2) * 128 + (m & 7) * 16 + (k & 3) * 4;
+                    const unsigned hx = to_tf32(x.x), hy = to_tf32(x.y);
+                    const unsigned lx = to_tf32(x.x - __uint_as_float(hx));
+                    const unsigned ly = to_tf32(x.y - __uint_as_float(hy));
+                    *reinterpret_cast<uint2 *>(ahi + off) = make_uint2(hx, hy);
+                    *reinterpret_cast<uint2 *>(alo + off) = make_uint2(lx, ly);
+                }
+                load(qq + kPrefetch, r[p]);
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive(&full[b]);
+            }
         }
-        prefetch(qq + 3, r);
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        const int j = (int)(qq % NCH);
-        if (tid == 0) {
+    } else if (warp < kMmaWarp) {
+        // ------------------------------------------------------------------ epilogue
+        const int sub = warp - kEpiWarp0;         // TMEM lane subpartition
+        const int m = sub * 32 + lane;            // group row == TMEM lane
+        for (long long t = 0; t < ntl && !failed; t++) {
+            const int ab = (int)(t & 1);
+            if (!mbar_wait(&accfull[ab], (unsigned)((t >> 1) & 1))) {
+                failed = true;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned long long gb = group_base(t, m);
+            const unsigned acc = tmem + (unsigned)(ab * N) + ((unsigned)(sub * 32) << 16);
+#pragma unroll
+            for (int col = 0; col < N; col += 16) {
+                unsigned v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                      "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                    : "r"(acc + (unsigned)col));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                for (int i = 0; i < 8; i++)
+                    __stcs(psi + gb + toff[col / 2 + i],
+                           make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])));
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            mbar_arrive(&accempty[ab]);
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------------------ MMA issuer
+        const unsigned aring_u32 = smem_u32(Aring);
+        const unsigned b_hi = smem_u32(Bs), b_lo = b_hi + C::BBYTES;
+        for (long long qq = 0; qq < total && !failed; qq++) {
+            const int b = (int)(qq % kNBuf);
+            const int j = (int)(qq % NCH);
+            const long long t = qq / NCH;
+            const int ab = (int)(t & 1);
+            if (j == 0 && t >= 2 && !mbar_wait(&accempty[ab], (unsigned)(((t >> 1) - 1) & 1))) {
+                failed = true;
+                break;
+            }
+            if (!mbar_wait(&full[b], (unsigned)((qq / kNBuf) & 1))) {
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned acc = tmem + (unsigned)(ab * N);
             const unsigned a_hi = aring_u32 + b * 2 * C::ABYTES, a_lo = a_hi + C::ABYTES;
-            const unsigned b_hi = bs_u32, b_lo = bs_u32 + C::BBYTES;
 #pragma unroll
             for (int kk = 0; kk < kCH / 8; kk++) {
                 const unsigned aoff = kk * 256;                       // 2 core matrices along K
@@ -233,85 +329,23 @@ __global__ void __launch_bounds__(kThreads, 1) dense_tc_kernel(const Args a) {
                 const uint64_t dAl = make_desc(a_lo + aoff, 128, 1024);
                 const uint64_t dBh = make_desc(b_hi + boff, 128, KK * 32);
                 const uint64_t dBl = make_desc(b_lo + boff, 128, KK * 32);
-                const unsigned acc0 = (j == 0 && kk == 0) ? 0u : 1u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-                    "l"(dAh), "l"(dBh), "r"(C::IDESC), "r"(acc0)
-                    : "memory");
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-                    "l"(dAh), "l"(dBl), "r"(C::IDESC), "r"(1u)
-                    : "memory");
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-                    "l"(dAl), "l"(dBh), "r"(C::IDESC), "r"(1u)
-                    : "memory");
+                mma_tf32(acc, dAh, dBh, C::IDESC, (j == 0 && kk == 0) ? 0u : 1u);
+                mma_tf32(acc, dAh, dBl, C::IDESC, 1u);
+                mma_tf32(acc, dAl, dBh, C::IDESC, 1u);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             smem_u32(&mbar[b]))
-                         : "memory");
-            if (j == NCH - 1)
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                                 smem_u32(&mbar[kNBuf]))
-                             : "memory");
+            commit_to(&empty[b]);
+            if (j == NCH - 1) commit_to(&accfull[ab]);
         }
-        if (j == NCH - 1) {
-            // epilogue: accumulator -> HBM
-            const long long tile_i = qq / NCH;
-            const bool ok = mbar_wait(&mbar[kNBuf], (unsigned)(tile_i & 1));
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                return;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const unsigned long long gb = group_base(tile_i);
-            const unsigned lane_base = (unsigned)(warp & 3) * 32;
-            constexpr int HALF = N / 2;
-#pragma unroll
-            for (int cb = 0; cb < HALF; cb += 16) {
-                const int col = (warp >> 2) * HALF + cb;
-                unsigned v[16];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-                      "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                    : "r"(tmem + (lane_base << 16) + (unsigned)col));
-                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-                // thread's TMEM lane is its own group row m (lane_base + lane == m)
-#pragma unroll
-                for (int i = 0; i < 8; i++) {
-                    const int rr = col / 2 + i;
-                    __stcs(psi + gb + toff[rr], make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])));
-                }
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-            __syncthreads();
-        }
-    };
-
-    float2 r0[8], r1[8], r2[8];
-    prefetch(0, r0);
-    prefetch(1, r1);
-    prefetch(2, r2);
-    for (long long qq = 0; qq < total && !failed; qq += 3) {
-        step(qq, r0);
-        step(qq + 1, r1);
-        step(qq + 2, r2);
     }
     if (failed) atomicOr(&g_device_error, 1u);
-    // drain: all MMAs this CTA issued must be complete before tensor memory is released
-    if (!failed && total > 0) {  // already complete after the last epilogue; bounded anyway
-        if (!mbar_wait(&mbar[kNBuf], (unsigned)((ntl - 1) & 1))) atomicOr(&g_device_error, 1u);
-    }
+    __syncwarp();
+    // every MMA has completed once the epilogue warps consumed the last accumulator (or gave
+    // up after a bounded wait); only then is tensor memory released
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((unsigned)N)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((unsigned)C::TMEM_COLS)
                      : "memory");
     }
 }
@@ -368,8 +402,15 @@ static void launch_tc_t(const tc::Args &a, int sms, cudaStream_t st) {
         if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_kernel attribute: ") + cudaGetErrorString(e));
         attr = true;
     }
-    const long long grid = std::min<long long>(a.ntiles, sms);
-    tc::dense_tc_kernel<K><<<(int)grid, tc::kThreads, C::SMEM, st>>>(a);
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc::dense_tc_kernel<K>, tc::kThreadsWS, C::SMEM);
+        if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+        // tensor memory: every resident CTA holds TMEM_COLS of the SM's 512 columns
+        per_sm = std::min(per_sm, 512 / C::TMEM_COLS);
+    }
+    const long long grid = std::min<long long>(a.ntiles, (long long)sms * per_sm);
+    tc::dense_tc_kernel<K><<<(int)grid, tc::kThreadsWS, C::SMEM, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_kernel: ") + cudaGetErrorString(e));
 }
