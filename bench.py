@@ -132,6 +132,26 @@ def max_over_ranks(ws, v: float) -> float:
     return float(t.item())
 
 
+# DRAM bytes (read + write) per amplitude for one launch of each kernel family, from an ncu
+# capture of the current kernel on a 27-qubit state (the full-size launch is linear in 2^n).
+# An entry is removed whenever its kernel changes, until it is captured again.
+TRAFFIC = {
+    ("dense_tc_kernel", "c64"): {"bytes_per_amp": 2.0898e9 / 2 ** 27,
+                                 "source": "profiles/dense_gate_kernels_c64_27q.md (k=4..6 mean, "
+                                           "27-qubit capture scaled by 2^n)"},
+    ("dense_pipe_kernel", "c64"): {"bytes_per_amp": 2.0874e9 / 2 ** 27,
+                                   "source": "profiles/dense_gate_kernels_c64_27q.md (k=1..3 mean, "
+                                             "27-qubit capture scaled by 2^n)"},
+}
+
+
+def kernel_family(dtype_name: str, k: int) -> str:
+    """Which kernel runs a dense k-qubit gate (mirrors the library's dispatch)."""
+    if dtype_name == "c64" and 4 <= k <= 6 and os.environ.get("QSIM_DENSE_TC", "1") != "0":
+        return "dense_tc_kernel"
+    return "dense_pipe_kernel"
+
+
 # ------------------------------------------------------------------------ oracle baseline
 def oracle_gate_sample(seed: int, n_sample: int = 24, per_k: int = 1):
     """The oracle (FP64, OpenMP over the host cores) on a bounded sample of the gate
@@ -202,13 +222,31 @@ def run_gates(args, ws, rank, dtype_name):
         sel = [i for i, kk in enumerate(ks) if kk == k]
         d = durs[:, sel].mean()
         per_k[str(k)] = {"ms_per_gate": round(float(d), 4),
-                         "gbs": round(bytes_per_gate / (d / 1e3) / 1e9, 1)}
+                         "gbs": round(bytes_per_gate / (d / 1e3) / 1e9, 1),
+                         "kernel": kernel_family(dtype_name, k)}
+    # per kernel family: launches, time, share of the timed gate time
+    fams = {}
+    for i, k in enumerate(ks):
+        f = kernel_family(dtype_name, k)
+        e = fams.setdefault(f, {"launches": 0, "ms_total": 0.0})
+        e["launches"] += args.steps
+        e["ms_total"] += float(durs[:, i].sum())
+    tot = sum(e["ms_total"] for e in fams.values())
+    for f, e in fams.items():
+        e["share"] = round(e["ms_total"] / tot, 4)
+        e["achieved_gbs"] = round(bytes_per_gate * e["launches"] / (e["ms_total"] / 1e3) / 1e9, 1)
+        e["ms_total"] = round(e["ms_total"], 2)
+    dom = max(fams, key=lambda f: fams[f]["ms_total"])
     hbm, _, peak_kind = measured_peaks()
-    mean_launch = float(durs.mean())
-    achieved = bytes_per_gate / (mean_launch / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "dense_tile_kernel", "achieved": round(achieved, 1),
-                "peak": hbm, "peak_kind": peak_kind + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+    achieved = fams[dom]["achieved_gbs"]
+    tr = TRAFFIC.get((dom, dtype_name))
+    traffic = None
+    if tr is not None:
+        traffic = round(tr["bytes_per_amp"] * (1 << n))
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                "peak_kind": peak_kind + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
+                "traffic_source": tr["source"] if tr else None,
                 "bytes_per_launch": bytes_per_gate}
 
     # end to end through the public API from pinned host memory
@@ -246,7 +284,7 @@ def run_gates(args, ws, rank, dtype_name):
                    "n_qubits": n, "gates_per_step": len(gates), "state_bytes": S << n,
                    "l2": "inputs larger than L2 (state %d GiB vs 129 MB L2)" % ((S << n) >> 30),
                    "seed": seed},
-        "per_k": per_k, "roofline": roofline,
+        "per_k": per_k, "kernels": fams, "roofline": roofline,
         "e2e": {"value": round(e2e_val, 1), "unit": "GB/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "gpu_launches": len(circs) * args.steps,
