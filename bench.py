@@ -145,6 +145,9 @@ TRAFFIC = {
 }
 
 
+FP64_PEAK_TFLOPS = 1.25
+
+
 def kernel_family(dtype_name: str, k: int) -> str:
     """Which kernel runs a dense k-qubit gate (mirrors the library's dispatch)."""
     if dtype_name == "c64" and 4 <= k <= 6 and os.environ.get("QSIM_DENSE_TC", "1") != "0":
@@ -243,11 +246,23 @@ def run_gates(args, ws, rank, dtype_name):
     traffic = None
     if tr is not None:
         traffic = round(tr["bytes_per_amp"] * (1 << n))
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                "peak_kind": peak_kind + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
-                "traffic_source": tr["source"] if tr else None,
-                "bytes_per_launch": bytes_per_gate}
+    if dtype_name == "c64":
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                    "peak_kind": peak_kind + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                    "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
+                    "traffic_source": tr["source"] if tr else None,
+                    "bytes_per_launch": bytes_per_gate}
+    else:
+        # complex128: FP64 FMA bound (a dense k-qubit gate is 8 * 2^k real flops per amplitude)
+        sel = [i for i, k in enumerate(ks) if kernel_family(dtype_name, k) == dom]
+        fl = sum(8.0 * (2 ** ks[i]) * (1 << n) for i in sel) * args.steps
+        tf = fl / (fams[dom]["ms_total"] / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": round(tf, 4),
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "peak_kind": "nominal GB300 FP64 rate (1.25 TFLOP/s; a probe measured 1.21)",
+                    "frac": round(tf / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                    "traffic_source": tr["source"] if tr else None,
+                    "hbm_achieved_gbs": achieved}
 
     # end to end through the public API from pinned host memory
     host_in = synth.gaussian_state_torch(seed, n, dtype, "cpu", chunk=1 << 22, normalize=True) \
