@@ -198,6 +198,56 @@ typedef struct {
 int hhl_readout(const void *state, int dtype, const hhl_circuit *h, void *stream, double *x_out,
                 double *x_state_out, hhl_readout_stats *stats);
 
+/* ======================================================================================= *
+ * Batched execution: many small circuits in one persistent launch                          *
+ * ======================================================================================= */
+
+typedef struct qsim_batch qsim_batch; /* uploaded op tables of a set of circuits + results   */
+
+/* Upload the op tables of `count` circuits (each applied to states[i], a device buffer of
+ * 2^n_i amplitudes of `dtype`, n_i <= 30) into one device allocation (synchronous).  Every
+ * operation must be a dense gate of at most 5 targets, a phase, diagonal or swap gate, or a
+ * uniformly controlled RY over consecutive control qubits (fuse with max_k <= 5); otherwise
+ * QSIM_EINVAL.  The state pointers are stored: they must stay valid while the batch is run.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int qsim_batch_create(const qsim_circuit *const *cs, void *const *states, int count, int dtype,
+                      qsim_batch **out);
+
+/* HHL batch: circuit i is hhl i's gate list, or fused[i] when fused != NULL (a qsim_fuse
+ * result of hhl_as_circuit(hs[i])).  Each run also prepares |0>|0>|b_i> in states[i] and
+ * computes the FP64 readout sums and the solution slice of every circuit on the device. */
+int hhl_batch_create(const hhl_circuit *const *hs, const qsim_circuit *const *fused,
+                     void *const *states, int count, int dtype, qsim_batch **out);
+
+/* Run the batch: one cudaMemsetAsync of the work counter and one persistent kernel on
+ * `stream`, nothing else (no allocation, no synchronization), so the call can be captured
+ * into a CUDA graph.  Each CTA takes whole circuits (most expensive first); a state of up to
+ * 2^13 (complex128) or 2^14 (complex64) amplitudes stays in shared memory for the whole
+ * circuit, larger ones are updated in place.  One CTA runs one circuit in a fixed order, so a
+ * circuit's result is bit-identical whatever else is in the batch; it equals qsim_apply of
+ * the same circuit up to rounding (different kernels).  Errors: EINVAL, ECUDA. */
+int qsim_batch_run(qsim_batch *b, void *stream);
+
+/* After an HHL batch ran on `stream`: copy the results (synchronizes `stream`) and write, for
+ * batch entry i in order, x_i (N_i complex, concatenated into x_out) and stats[i], as
+ * hhl_readout would.  x_out / stats may be NULL.  Errors: EINVAL, ECUDA. */
+int hhl_batch_results(qsim_batch *b, void *stream, double *x_out, hhl_readout_stats *stats);
+
+void qsim_batch_free(qsim_batch *b);
+
+/* Autotuner of the fusion width for an HHL batch: for each candidate width candidates[i]
+ * (1..5) fuse every circuit, build the batch on `states`, run it once to warm up and twice
+ * timed with CUDA events on `stream`; *best_k receives the fastest width, ms_out[i] (may be
+ * NULL) the time per run.  The states are overwritten.  Synchronizes `stream`.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int hhl_batch_autotune(const hhl_circuit *const *hs, void *const *states, int count, int dtype,
+                       const int *candidates, int ncand, void *stream, int *best_k, double *ms_out);
+
+/* Convenience: qsim_batch_create + qsim_batch_run + wait + free.  n_qubits[i] must equal the
+ * qubit count of cs[i].  Synchronizes `stream`.  Errors: EINVAL, ENOMEM, ECUDA. */
+int qsim_apply_batched(void *const *states, const int *n_qubits, const qsim_circuit *const *cs,
+                       int count, int dtype, void *stream);
+
 /* hhl_readout for callers that cannot allocate device memory.  The paper has no counterpart;
  * this is a library convenience.  Such callers include an application whose own pool
  * allocator already owns all device memory, and code that must not call cudaMalloc or

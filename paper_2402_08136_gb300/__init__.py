@@ -10,7 +10,12 @@ from ._binding import (  # noqa: F401
     QSIM_C128,
     QsimError,
     QsimLibraryMissing,
+    Batch,
     Circuit,
+    hhl_batch_autotune,
+    hhl_batch_create,
+    qsim_apply_batched,
+    qsim_batch_create,
     HHLCircuit,
     hhl_build,
     hhl_build_spectral,

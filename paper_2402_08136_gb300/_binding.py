@@ -69,6 +69,17 @@ _SIGS = {
     "hhl_get_info": ([_VP, ctypes.POINTER(_HHLInfo)], ctypes.c_int),
     "hhl_prepare_state": ([_VP, ctypes.c_int, _VP, _VP], ctypes.c_int),
     "qsim_device_status": ([ctypes.POINTER(ctypes.c_uint), ctypes.c_int], ctypes.c_int),
+    "qsim_batch_create": ([ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int,
+                           ctypes.POINTER(_VP)], ctypes.c_int),
+    "hhl_batch_create": ([ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int,
+                          ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
+    "qsim_batch_run": ([_VP, _VP], ctypes.c_int),
+    "hhl_batch_results": ([_VP, _VP, _DP, ctypes.POINTER(_ReadoutStats)], ctypes.c_int),
+    "qsim_batch_free": ([_VP], None),
+    "hhl_batch_autotune": ([ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _IP,
+                            ctypes.c_int, _VP, _IP, _DP], ctypes.c_int),
+    "qsim_apply_batched": ([ctypes.POINTER(_VP), _IP, ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP],
+                           ctypes.c_int),
     "hhl_readout": ([_VP, ctypes.c_int, _VP, _VP, _DP, _DP, ctypes.POINTER(_ReadoutStats)],
                     ctypes.c_int),
 }
@@ -280,3 +291,108 @@ def hhl_readout(state, h: HHLCircuit, stream=None) -> dict:
     out["x"] = x
     out["x_state"] = xs
     return out
+
+
+def _ptr_array(items):
+    arr = (_VP * max(1, len(items)))()
+    for i, x in enumerate(items):
+        arr[i] = x
+    return arr
+
+
+class Batch:
+    """Owning handle of a qsim_batch; keeps the circuits and states it references alive."""
+
+    def __init__(self, ptr, keep, hhl=None):
+        self._ptr = ptr
+        self._keep = keep
+        self._hhl = hhl
+
+    @property
+    def ptr(self):
+        return self._ptr
+
+    def run(self, stream=None):
+        _check(library().qsim_batch_run(self._ptr, _stream_ptr(stream)))
+
+    def results(self, stream=None):
+        """HHL batches: list of dicts (x and the readout statistics) per entry."""
+        if self._hhl is None:
+            raise QsimError(-1, "not an HHL batch")
+        infos = [h.info() for h in self._hhl]
+        total = sum(i["N"] for i in infos)
+        x = np.zeros(max(1, total), dtype=np.complex128)
+        st = (_ReadoutStats * len(infos))()
+        _check(library().hhl_batch_results(self._ptr, _stream_ptr(stream),
+                                           x.view(np.float64).ctypes.data_as(_DP), st))
+        out, o = [], 0
+        for i, inf in enumerate(infos):
+            d = {f: getattr(st[i], f) for f, _ in st[i]._fields_}
+            d["x"] = x[o:o + inf["N"]].copy()
+            o += inf["N"]
+            out.append(d)
+        return out
+
+    def __del__(self):
+        if getattr(self, "_ptr", None):
+            try:
+                library().qsim_batch_free(self._ptr)
+            except Exception:
+                pass
+            self._ptr = None
+
+
+def qsim_batch_create(circuits, states) -> Batch:
+    dt = {_dtype_of(s) for s in states}
+    if len(dt) != 1:
+        raise QsimError(-1, "all states must have the same dtype")
+    for c, s in zip(circuits, states):
+        _check_state(s, c.n_qubits)
+    p = _VP()
+    _check(library().qsim_batch_create(_ptr_array([c.ptr for c in circuits]),
+                                       _ptr_array([s.data_ptr() for s in states]), len(circuits),
+                                       dt.pop(), ctypes.byref(p)))
+    return Batch(p, (list(circuits), list(states)))
+
+
+def hhl_batch_create(hhls, states, fused=None) -> Batch:
+    dt = {_dtype_of(s) for s in states}
+    if len(dt) != 1:
+        raise QsimError(-1, "all states must have the same dtype")
+    for h, s in zip(hhls, states):
+        _check_state(s, h.info()["n"])
+    p = _VP()
+    fz = _ptr_array([f.ptr for f in fused]) if fused is not None else None
+    _check(library().hhl_batch_create(_ptr_array([h.ptr for h in hhls]), fz,
+                                      _ptr_array([s.data_ptr() for s in states]), len(hhls),
+                                      dt.pop(), ctypes.byref(p)))
+    return Batch(p, (list(hhls), list(states), list(fused) if fused is not None else None),
+                 hhl=list(hhls))
+
+
+def qsim_apply_batched(states, circuits, stream=None):
+    dt = {_dtype_of(s) for s in states}
+    if len(dt) != 1:
+        raise QsimError(-1, "all states must have the same dtype")
+    ns = [c.n_qubits for c in circuits]
+    for n, s in zip(ns, states):
+        _check_state(s, n)
+    na = np.ascontiguousarray(np.asarray(ns if ns else [0], dtype=np.int32))
+    _check(library().qsim_apply_batched(_ptr_array([s.data_ptr() for s in states]),
+                                        na.ctypes.data_as(_IP), _ptr_array([c.ptr for c in circuits]),
+                                        len(circuits), dt.pop(), _stream_ptr(stream)))
+
+
+def hhl_batch_autotune(hhls, states, candidates=(1, 2, 3, 4, 5), stream=None):
+    """Fastest fusion width for this HHL batch (times real batch runs).  Returns (k, {k: ms})."""
+    dt = {_dtype_of(s) for s in states}
+    if len(dt) != 1:
+        raise QsimError(-1, "all states must have the same dtype")
+    cand = np.ascontiguousarray(np.asarray(list(candidates), dtype=np.int32))
+    ms = np.zeros(len(cand))
+    best = ctypes.c_int(0)
+    _check(library().hhl_batch_autotune(_ptr_array([h.ptr for h in hhls]),
+                                        _ptr_array([s.data_ptr() for s in states]), len(hhls), dt.pop(),
+                                        cand.ctypes.data_as(_IP), len(cand), _stream_ptr(stream),
+                                        ctypes.byref(best), ms.ctypes.data_as(_DP)))
+    return int(best.value), {int(k): float(t) for k, t in zip(cand, ms)}

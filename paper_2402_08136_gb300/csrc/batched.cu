@@ -1,0 +1,645 @@
+// Batched execution of many small circuits in one persistent launch (the batching pattern of the
+// HHL solver: many N-1 contingency solves of uneven size at once).
+//
+// Each CTA repeatedly takes the next circuit from a work counter (circuits ordered by
+// decreasing cost on the host) and runs the whole circuit by itself: optional HHL state
+// preparation, every operation of the (fused) gate list with a CTA barrier between operations,
+// and the optional FP64 readout sums.  A state of up to `smem_amps` amplitudes lives in shared
+// memory for the whole circuit (loaded once, written back once); a larger state is updated in
+// place in global memory, where it stays L2-resident.  Because one CTA executes one circuit
+// with a fixed instruction and reduction order, a circuit's result does not depend on what
+// else is in the batch.
+//
+// Supported operations: dense gates with up to 5 targets and any controls, phase, diagonal,
+// swap, and uniformly controlled RY over a contiguous control register; qubit masks are 32-bit
+// (states of at most 30 qubits).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+
+#include "common.h"
+
+namespace qsim {
+namespace batch {
+
+constexpr int kThreads = 256;
+
+enum BKind : unsigned char { B_DENSE = 0, B_PHASE = 1, B_DIAG = 2, B_SWAP = 3, B_UCRY = 4 };
+
+struct BOp {
+    unsigned char kind, k, c0, nreg;  // c0 / nreg: UCRY control register (contiguous)
+    signed char t[8];                 // targets in matrix-bit order (UCRY: t[0] = target)
+    unsigned fixmask;                 // targets | controls (zero bits inserted when enumerating)
+    unsigned cmask;                   // controls that must be 1 (PHASE: all its qubits)
+    unsigned data;                    // element offset into the circuit's data
+    unsigned pad;
+};
+
+struct BCirc {
+    void *state;
+    const BOp *ops;
+    const void *data;
+    double *result;  // readout: [norm2, P, P0, pad] then 2^nb complex (re, im) doubles
+    int n, nops, nb, flags;  // flags: 1 = prepare |0>|0>|b>, 2 = readout sums and slice
+    unsigned b_off, pad;
+};
+
+template <typename R> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+
+__device__ __forceinline__ unsigned expand(unsigned g, unsigned fixmask) {
+    for (unsigned m = fixmask; m; m &= m - 1) {
+        const int p = __ffs(m) - 1;
+        g = ((g >> p) << (p + 1)) | (g & ((1u << p) - 1u));
+    }
+    return g;
+}
+
+template <typename V, int K>
+__device__ void op_dense(V *psi, int n, const BOp &op, const V *U, int tid) {
+    constexpr int D = 1 << K;
+    const unsigned ngroups = 1u << (n - __popc(op.fixmask));  // fixmask = targets | controls
+    unsigned offs[D];
+#pragma unroll
+    for (int r = 0; r < D; r++) {
+        unsigned o = 0;
+#pragma unroll
+        for (int b = 0; b < K; b++)
+            if ((r >> b) & 1) o |= 1u << op.t[b];
+        offs[r] = o;
+    }
+    for (unsigned g = tid; g < ngroups; g += kThreads) {
+        const unsigned base = expand(g, op.fixmask) | op.cmask;
+        V x[D];
+#pragma unroll
+        for (int c = 0; c < D; c++) x[c] = psi[base + offs[c]];
+#pragma unroll 1
+        for (int r = 0; r < D; r++) {
+            V acc{0, 0};
+            const V *u = U + r * D;
+#pragma unroll
+            for (int c = 0; c < D; c++) {
+                const V w = u[c];
+                acc.x = fma(w.x, x[c].x, acc.x);
+                acc.x = fma(-w.y, x[c].y, acc.x);
+                acc.y = fma(w.x, x[c].y, acc.y);
+                acc.y = fma(w.y, x[c].x, acc.y);
+            }
+            psi[base + offs[r]] = acc;
+        }
+    }
+}
+
+template <typename V>
+__device__ __forceinline__ V cmulb(V a, V b) {
+    V r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+template <typename R>
+__device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typename C2<R>::T *data, int tid) {
+    using V = typename C2<R>::T;
+    const V *d = data + op.data;
+    switch (op.kind) {
+        case B_DENSE:
+            switch (op.k) {
+                case 1: op_dense<V, 1>(psi, n, op, d, tid); break;
+                case 2: op_dense<V, 2>(psi, n, op, d, tid); break;
+                case 3: op_dense<V, 3>(psi, n, op, d, tid); break;
+                case 4: op_dense<V, 4>(psi, n, op, d, tid); break;
+                case 5: op_dense<V, 5>(psi, n, op, d, tid); break;
+                default: break;
+            }
+            break;
+        case B_PHASE: {
+            const unsigned cnt = 1u << (n - __popc(op.fixmask));
+            const V ph = d[0];
+            for (unsigned g = tid; g < cnt; g += kThreads) {
+                const unsigned i = expand(g, op.fixmask) | op.cmask;
+                psi[i] = cmulb(psi[i], ph);
+            }
+            break;
+        }
+        case B_DIAG: {
+            const unsigned cnt = 1u << (n - __popc(op.cmask));  // every index with the controls set
+            for (unsigned g = tid; g < cnt; g += kThreads) {
+                const unsigned i = expand(g, op.cmask) | op.cmask;  // enumerate all but controls
+                unsigned p = 0;
+                for (int b = 0; b < op.k; b++) p |= ((i >> op.t[b]) & 1u) << b;
+                psi[i] = cmulb(psi[i], d[p]);
+            }
+            break;
+        }
+        case B_SWAP: {
+            const unsigned cnt = 1u << (n - __popc(op.fixmask));
+            const unsigned ma = 1u << op.t[0], mb = 1u << op.t[1];
+            for (unsigned g = tid; g < cnt; g += kThreads) {
+                const unsigned i = expand(g, op.fixmask) | op.cmask;
+                const V x = psi[i | ma], y = psi[i | mb];
+                psi[i | ma] = y;
+                psi[i | mb] = x;
+            }
+            break;
+        }
+        case B_UCRY: {
+            const unsigned cnt = 1u << (n - 1);
+            const int tq = op.t[0];
+            const unsigned tb = 1u << tq, vmask = (1u << op.nreg) - 1u;
+            for (unsigned g = tid; g < cnt; g += kThreads) {
+                const unsigned i0 = ((g >> tq) << (tq + 1)) | (g & (tb - 1u));
+                const V cs = d[(i0 >> op.c0) & vmask];
+                const V x0 = psi[i0], x1 = psi[i0 | tb];
+                V y0, y1;
+                y0.x = cs.x * x0.x - cs.y * x1.x;
+                y0.y = cs.x * x0.y - cs.y * x1.y;
+                y1.x = cs.y * x0.x + cs.x * x1.x;
+                y1.y = cs.y * x0.y + cs.x * x1.y;
+                psi[i0] = y0;
+                psi[i0 | tb] = y1;
+            }
+            break;
+        }
+        default: break;
+    }
+}
+
+__device__ __forceinline__ double block_sum_b(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = l < (kThreads >> 5) ? sh[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) batched_kernel(const BCirc *circs, const int *order, int count,
+                                                          unsigned *counter, int smem_amps) {
+    using V = typename C2<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V *sm = reinterpret_cast<V *>(smraw);
+    __shared__ int cur;
+    __shared__ double red[32];
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) cur = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int ci = cur;
+        __syncthreads();
+        if (ci >= count) break;
+        const BCirc c = circs[order[ci]];
+        const unsigned N = 1u << c.n;
+        V *g = reinterpret_cast<V *>(c.state);
+        V *psi = (int)N <= smem_amps ? sm : g;
+        const V *data = reinterpret_cast<const V *>(c.data);
+        if (c.flags & 1) {
+            const unsigned Db = 1u << c.nb;
+            for (unsigned i = tid; i < N; i += kThreads) psi[i] = i < Db ? data[c.b_off + i] : V{0, 0};
+        } else if (psi == sm) {
+            for (unsigned i = tid; i < N; i += kThreads) psi[i] = g[i];
+        }
+        __syncthreads();
+        for (int o = 0; o < c.nops; o++) {
+            run_op<R>(psi, c.n, c.ops[o], data, tid);
+            __syncthreads();
+        }
+        if (c.flags & 2) {
+            // FP64 sums in a fixed order: ||psi||^2, P(top qubit = 1), P(slice)
+            double s_all = 0.0, s_hi = 0.0;
+            for (unsigned i = tid; i < N; i += kThreads) {
+                const V z = psi[i];
+                const double q = (double)z.x * (double)z.x + (double)z.y * (double)z.y;
+                s_all += q;
+                if (i >= N / 2) s_hi += q;
+            }
+            const unsigned Db = 1u << c.nb;
+            double s_sl = 0.0;
+            for (unsigned i = tid; i < Db; i += kThreads) {
+                const V z = psi[N / 2 + i];
+                s_sl += (double)z.x * (double)z.x + (double)z.y * (double)z.y;
+                c.result[4 + 2 * i] = (double)z.x;
+                c.result[4 + 2 * i + 1] = (double)z.y;
+            }
+            const double ta = block_sum_b(s_all, red);
+            const double th = block_sum_b(s_hi, red);
+            const double ts = block_sum_b(s_sl, red);
+            if (tid == 0) {
+                c.result[0] = ta;
+                c.result[1] = th;
+                c.result[2] = ts;
+            }
+        }
+        if (psi == sm)
+            for (unsigned i = tid; i < N; i += kThreads) g[i] = psi[i];
+        __syncthreads();
+    }
+}
+
+}  // namespace batch
+}  // namespace qsim
+
+// ------------------------------------------------------------------------------- host side
+struct qsim_batch {
+    int count = 0, dtype = 0, smem_amps = 0, grid = 1;
+    size_t smem_bytes = 0;
+    bool hhl = false;
+    void *dev = nullptr;  // one allocation: circs | order | counter | ops | data | results
+    size_t dev_bytes = 0;
+    qsim::batch::BCirc *d_circs = nullptr;
+    int *d_order = nullptr;
+    unsigned *d_counter = nullptr;
+    double *d_results = nullptr;
+    size_t results_doubles = 0;
+    double *h_results = nullptr;  // pinned mirror
+    struct Meta {
+        int N = 0, nb = 0;
+        double C = 1, norm_b = 1;
+        size_t roff = 0;
+    };
+    std::vector<Meta> meta;
+    ~qsim_batch() {
+        if (dev) cudaFree(dev);
+        if (h_results) cudaFreeHost(h_results);
+    }
+};
+
+namespace qsim {
+namespace {
+
+using batch::BOp;
+
+void put_v(std::vector<unsigned char> &blob, int dtype, const cd &z) {
+    if (dtype == QSIM_C128) {
+        double v[2] = {z.real(), z.imag()};
+        blob.insert(blob.end(), (unsigned char *)v, (unsigned char *)v + 16);
+    } else {
+        float v[2] = {(float)z.real(), (float)z.imag()};
+        blob.insert(blob.end(), (unsigned char *)v, (unsigned char *)v + 8);
+    }
+}
+
+size_t vbytes(int dtype) { return dtype == QSIM_C128 ? 16 : 8; }
+
+unsigned maskq(const std::vector<int> &q) {
+    unsigned m = 0;
+    for (int x : q) m |= 1u << x;
+    return m;
+}
+
+// Translate one executable op; returns false if the batched kernel does not support it.
+bool encode(const Op &op, int dtype, std::vector<unsigned char> &data, BOp &b) {
+    std::memset(&b, 0, sizeof(b));
+    const size_t el = data.size() / vbytes(dtype);
+    b.data = (unsigned)el;
+    switch (op.kind) {
+        case OP_DENSE: {
+            const int k = (int)op.targets.size();
+            if (k > 5) return false;
+            b.kind = batch::B_DENSE;
+            b.k = (unsigned char)k;
+            for (int i = 0; i < k; i++) b.t[i] = (signed char)op.targets[i];
+            b.cmask = maskq(op.controls);
+            b.fixmask = maskq(op.targets) | b.cmask;
+            for (const cd &z : op.U) put_v(data, dtype, z);  // row-major
+            return true;
+        }
+        case OP_PHASE:
+            b.kind = batch::B_PHASE;
+            b.cmask = b.fixmask = maskq(op.targets);
+            put_v(data, dtype, op.phase);
+            return true;
+        case OP_DIAG: {
+            const int k = (int)op.targets.size();
+            if (k > 8) return false;
+            b.kind = batch::B_DIAG;
+            b.k = (unsigned char)k;
+            for (int i = 0; i < k; i++) b.t[i] = (signed char)op.targets[i];
+            b.cmask = maskq(op.controls);
+            b.fixmask = b.cmask;  // (k counted separately in the enumeration)
+            for (const cd &z : op.U) put_v(data, dtype, z);
+            return true;
+        }
+        case OP_SWAP:
+            b.kind = batch::B_SWAP;
+            b.t[0] = (signed char)op.targets[0];
+            b.t[1] = (signed char)op.targets[1];
+            b.cmask = maskq(op.controls);
+            b.fixmask = maskq(op.targets) | b.cmask;
+            return true;
+        case OP_UCRY: {
+            const int nc = (int)op.controls.size();
+            for (int j = 1; j < nc; j++)
+                if (op.controls[j] != op.controls[0] + j) return false;
+            b.kind = batch::B_UCRY;
+            b.t[0] = (signed char)op.targets[0];
+            b.c0 = (unsigned char)op.controls[0];
+            b.nreg = (unsigned char)nc;
+            for (double th : op.theta) put_v(data, dtype, cd(std::cos(0.5 * th), std::sin(0.5 * th)));
+            return true;
+        }
+    }
+    return false;
+}
+
+template <typename R>
+void configure_batch(qsim_batch *B);
+
+double circuit_cost(const qsim_circuit *c) {
+    double s = 0;
+    for (const Op &op : c->ops) s += (op.kind == OP_DENSE ? (double)(1 << op.targets.size()) : 1.0);
+    return s * std::ldexp(1.0, c->n);
+}
+
+qsim_batch *make_batch(const std::vector<const qsim_circuit *> &cs, const std::vector<const hhl_circuit *> &hs,
+                       void *const *states, int dtype) {
+    const int count = (int)cs.size();
+    std::unique_ptr<qsim_batch> B(new qsim_batch());
+    B->count = count;
+    B->dtype = dtype;
+    B->hhl = !hs.empty();
+    std::vector<BOp> ops;
+    std::vector<unsigned char> data;
+    std::vector<batch::BCirc> circs(count);
+    std::vector<size_t> op_first(count), data_first(count);
+    int max_n = 0;
+    size_t results = 0;
+    B->meta.resize(count);
+    for (int i = 0; i < count; i++) {
+        const qsim_circuit *c = cs[i];
+        build_ops(const_cast<qsim_circuit *>(c));
+        QSIM_REQUIRE(c->n <= 30, "batched states are limited to 30 qubits");
+        QSIM_REQUIRE(states[i] != nullptr, "NULL state");
+        max_n = std::max(max_n, c->n);
+        while (data.size() % 256) data.push_back(0);
+        data_first[i] = data.size();
+        op_first[i] = ops.size();
+        std::vector<unsigned char> local;
+        for (const Op &op : c->ops) {
+            BOp b;
+            QSIM_REQUIRE(encode(op, dtype, local, b), "operation not supported by the batched executor "
+                                                      "(dense gates wider than 5 qubits or a scattered "
+                                                      "rotation register): fuse with max_k <= 5");
+            ops.push_back(b);
+        }
+        batch::BCirc &bc = circs[i];
+        std::memset(&bc, 0, sizeof(bc));
+        bc.n = c->n;
+        bc.nops = (int)c->ops.size();
+        bc.state = states[i];
+        if (B->hhl) {
+            const hhl_circuit *h = hs[i];
+            QSIM_REQUIRE(h->n == c->n, "HHL circuit and gate list disagree on the qubit count");
+            bc.flags = 3;
+            bc.nb = h->nb;
+            bc.b_off = (unsigned)(local.size() / vbytes(dtype));
+            for (const cd &z : h->b_pad) put_v(local, dtype, z);
+            B->meta[i].N = h->N;
+            B->meta[i].nb = h->nb;
+            B->meta[i].C = h->C;
+            B->meta[i].norm_b = h->norm_b;
+            B->meta[i].roff = results;
+            results += 4 + 2 * ((size_t)1 << h->nb);
+        }
+        data.insert(data.end(), local.begin(), local.end());
+    }
+    // order: most expensive first
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::vector<double> cost(count);
+    for (int i = 0; i < count; i++) cost[i] = circuit_cost(cs[i]);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    // one device allocation
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_circs = 0, o_order = al(o_circs + sizeof(batch::BCirc) * count);
+    const size_t o_counter = al(o_order + sizeof(int) * count);
+    const size_t o_ops = al(o_counter + 256);
+    const size_t o_data = al(o_ops + sizeof(BOp) * std::max<size_t>(1, ops.size()));
+    const size_t o_res = al(o_data + std::max<size_t>(1, data.size()));
+    const size_t total = al(o_res + sizeof(double) * std::max<size_t>(1, results));
+    cudaError_t e = cudaMalloc(&B->dev, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(QSIM_ENOMEM, std::string("cudaMalloc for batch tables: ") + cudaGetErrorString(e));
+    }
+    B->dev_bytes = total;
+    unsigned char *base = static_cast<unsigned char *>(B->dev);
+    for (int i = 0; i < count; i++) {
+        circs[i].ops = reinterpret_cast<const BOp *>(base + o_ops) + op_first[i];
+        circs[i].data = base + o_data + data_first[i];
+        circs[i].result = B->hhl ? reinterpret_cast<double *>(base + o_res) + B->meta[i].roff : nullptr;
+    }
+    std::vector<unsigned char> host(total, 0);
+    std::memcpy(host.data() + o_circs, circs.data(), sizeof(batch::BCirc) * count);
+    std::memcpy(host.data() + o_order, order.data(), sizeof(int) * count);
+    if (!ops.empty()) std::memcpy(host.data() + o_ops, ops.data(), sizeof(BOp) * ops.size());
+    if (!data.empty()) std::memcpy(host.data() + o_data, data.data(), data.size());
+    e = cudaMemcpy(B->dev, host.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("uploading batch tables: ") + cudaGetErrorString(e));
+    B->d_circs = reinterpret_cast<batch::BCirc *>(base + o_circs);
+    B->d_order = reinterpret_cast<int *>(base + o_order);
+    B->d_counter = reinterpret_cast<unsigned *>(base + o_counter);
+    B->d_results = reinterpret_cast<double *>(base + o_res);
+    B->results_doubles = results;
+    if (results) {
+        e = cudaMallocHost(&B->h_results, sizeof(double) * results);
+        if (e != cudaSuccess) throw Error(QSIM_ENOMEM, "pinned host buffer for batch results");
+    }
+    // shared-memory residency: up to 2^13 (complex128) / 2^14 (complex64) amplitudes
+    const int cap_amps = dtype == QSIM_C128 ? (1 << 13) : (1 << 14);
+    B->smem_amps = std::min(cap_amps, 1 << max_n);
+    if (dtype == QSIM_C128) configure_batch<double>(B.get());
+    else configure_batch<float>(B.get());
+    return B.release();
+}
+
+// Kernel attributes and the grid are fixed when the batch is created, so that a run is only a
+// memset and a launch (capturable into a CUDA graph).
+template <typename R>
+void configure_batch(qsim_batch *B) {
+    const size_t smem = (size_t)B->smem_amps * vbytes(B->dtype);
+    auto kern = batch::batched_kernel<R>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel attribute: ") + cudaGetErrorString(e));
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, batch::kThreads, smem);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    B->grid = std::max(1, std::min(B->count, sms * per_sm));
+    B->smem_bytes = smem;
+}
+
+template <typename R>
+void launch_batch(qsim_batch *B, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batch counter reset: ") + cudaGetErrorString(e));
+    batch::batched_kernel<R><<<B->grid, batch::kThreads, B->smem_bytes, st>>>(B->d_circs, B->d_order, B->count,
+                                                                              B->d_counter, B->smem_amps);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel: ") + cudaGetErrorString(e));
+}
+
+void run_batch(qsim_batch *B, void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (B->count == 0) return;
+    if (B->dtype == QSIM_C128) launch_batch<double>(B, st);
+    else launch_batch<float>(B, st);
+}
+
+}  // namespace
+}  // namespace qsim
+
+using namespace qsim;
+
+extern "C" {
+
+int qsim_batch_create(const qsim_circuit *const *cs, void *const *states, int count, int dtype, qsim_batch **out) {
+    return guarded([&] {
+        QSIM_REQUIRE(out != nullptr && count >= 0 && (count == 0 || (cs && states)), "bad arguments");
+        QSIM_REQUIRE(dtype == QSIM_C64 || dtype == QSIM_C128, "dtype must be QSIM_C64 or QSIM_C128");
+        std::vector<const qsim_circuit *> v(cs, cs + count);
+        for (auto *c : v) QSIM_REQUIRE(c != nullptr, "NULL circuit");
+        *out = make_batch(v, {}, states, dtype);
+    });
+}
+
+int hhl_batch_create(const hhl_circuit *const *hs, const qsim_circuit *const *fused, void *const *states, int count,
+                     int dtype, qsim_batch **out) {
+    return guarded([&] {
+        QSIM_REQUIRE(out != nullptr && count >= 0 && (count == 0 || (hs && states)), "bad arguments");
+        QSIM_REQUIRE(dtype == QSIM_C64 || dtype == QSIM_C128, "dtype must be QSIM_C64 or QSIM_C128");
+        std::vector<const qsim_circuit *> v(count);
+        std::vector<const hhl_circuit *> h(hs, hs + count);
+        for (int i = 0; i < count; i++) {
+            QSIM_REQUIRE(h[i] != nullptr, "NULL HHL circuit");
+            v[i] = (fused && fused[i]) ? fused[i] : &h[i]->circ;
+        }
+        *out = make_batch(v, h, states, dtype);
+    });
+}
+
+int qsim_batch_run(qsim_batch *b, void *stream) {
+    return guarded([&] {
+        QSIM_REQUIRE(b != nullptr, "NULL batch");
+        run_batch(b, stream);
+    });
+}
+
+int hhl_batch_results(qsim_batch *b, void *stream, double *x_out, hhl_readout_stats *stats) {
+    return guarded([&] {
+        QSIM_REQUIRE(b != nullptr && b->hhl, "not an HHL batch");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        if (b->results_doubles) {
+            cudaError_t e = cudaMemcpyAsync(b->h_results, b->d_results, sizeof(double) * b->results_doubles,
+                                            cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batch results: ") + cudaGetErrorString(e));
+        }
+        size_t xo = 0;
+        for (int i = 0; i < b->count; i++) {
+            const qsim_batch::Meta &m = b->meta[i];
+            const double *r = b->h_results + m.roff;
+            const double P = r[1], P0 = r[2];
+            const double inv = P0 > 0 ? 1.0 / std::sqrt(P0) : 0.0;
+            const double norm_x = std::sqrt(P) / m.C;
+            if (x_out)
+                for (int j = 0; j < m.N; j++) {
+                    x_out[2 * (xo + j)] = r[4 + 2 * j] * inv * norm_x * m.norm_b;
+                    x_out[2 * (xo + j) + 1] = r[4 + 2 * j + 1] * inv * norm_x * m.norm_b;
+                }
+            xo += m.N;
+            if (stats) {
+                stats[i].p_success = P;
+                stats[i].p_clock0 = P0;
+                stats[i].leakage = P - P0;
+                stats[i].norm2 = r[0];
+                stats[i].norm_x = norm_x;
+                stats[i].norm_b = m.norm_b;
+            }
+        }
+    });
+}
+
+void qsim_batch_free(qsim_batch *b) { delete b; }
+
+int hhl_batch_autotune(const hhl_circuit *const *hs, void *const *states, int count, int dtype,
+                       const int *candidates, int ncand, void *stream, int *best_k, double *ms_out) {
+    return guarded([&] {
+        QSIM_REQUIRE(hs && states && best_k && count > 0 && candidates && ncand > 0, "bad arguments");
+        QSIM_REQUIRE(dtype == QSIM_C64 || dtype == QSIM_C128, "dtype must be QSIM_C64 or QSIM_C128");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        std::vector<const hhl_circuit *> h(hs, hs + count);
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+            throw Error(QSIM_ECUDA, "cudaEventCreate");
+        double best = 1e300;
+        int bk = -1;
+        try {
+            for (int ci = 0; ci < ncand; ci++) {
+                const int k = candidates[ci];
+                QSIM_REQUIRE(k >= 1 && k <= 5, "candidate fusion widths must be in 1..5");
+                std::vector<std::unique_ptr<qsim_circuit>> fused;
+                std::vector<const qsim_circuit *> v(count);
+                for (int i = 0; i < count; i++) {
+                    qsim_circuit *f = nullptr;
+                    if (qsim_fuse(&h[i]->circ, k, &f) != QSIM_OK) throw Error(QSIM_EINVAL, qsim_last_error());
+                    fused.emplace_back(f);
+                    v[i] = f;
+                }
+                std::unique_ptr<qsim_batch> B(make_batch(v, h, states, dtype));
+                run_batch(B.get(), stream);  // warm-up
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 2; r++) run_batch(B.get(), stream);
+                cudaEventRecord(e1, st);
+                cudaError_t e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const double per = ms / 2.0;
+                if (ms_out) ms_out[ci] = per;
+                if (per < best) {
+                    best = per;
+                    bk = k;
+                }
+            }
+        } catch (...) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        *best_k = bk;
+    });
+}
+
+int qsim_apply_batched(void *const *states, const int *n_qubits, const qsim_circuit *const *cs, int count, int dtype,
+                       void *stream) {
+    return guarded([&] {
+        QSIM_REQUIRE(count >= 0 && (count == 0 || (states && n_qubits && cs)), "bad arguments");
+        for (int i = 0; i < count; i++)
+            QSIM_REQUIRE(cs[i] != nullptr && n_qubits[i] == cs[i]->n, "state qubit count does not match its circuit");
+        if (count == 0) return;
+        std::vector<const qsim_circuit *> v(cs, cs + count);
+        std::unique_ptr<qsim_batch> B(make_batch(v, {}, states, dtype));
+        run_batch(B.get(), stream);
+        // the batch tables must outlive the launch
+        cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched apply: ") + cudaGetErrorString(e));
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+"""Batched executor (one persistent launch for many circuits) vs the FP64 oracle; a circuit's
+result is bit-identical alone and in a mixed batch; HHL batches reproduce the oracle's readout;
+the run can be captured in a CUDA graph."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import core as ocore
+from oracle import hhl as ohhl
+
+TOL = {torch.complex128: 1e-12, torch.complex64: 1e-5}
+DTYPES = [torch.complex128, torch.complex64]
+
+
+@pytest.fixture(scope="module")
+def qs():
+    from paper_2402_08136_gb300 import build
+    build.build()
+    import paper_2402_08136_gb300 as q
+    return q
+
+
+def random_circuit(qs, rng, n, count):
+    """Gates the batched executor supports: dense up to 5 targets (with controls), phases,
+    diagonals, swaps, a contiguous-register UCRY."""
+    c = qs.Circuit(n)
+    ref_gates = []
+    for _ in range(count):
+        r = rng.random()
+        if r < 0.5:
+            k = int(rng.integers(1, min(5, n - 1) + 1))
+            q = [int(v) for v in rng.permutation(n)]
+            t = q[:k]
+            ctl = q[k:k + int(rng.integers(0, 2))] if n - k >= 1 else []
+            U = synth.haar_unitary(rng, 1 << k)
+            c.add_gate(t, U, ctl)
+            ref_gates.append(("u", t, U, ctl))
+        elif r < 0.7:
+            t = synth.random_targets(rng, n, 2)
+            U = np.diag([1, 1, 1, np.exp(1j * rng.uniform(-3, 3))])
+            c.add_gate(t, U)
+            ref_gates.append(("u", t, U, []))
+        elif r < 0.8:
+            t = [int(rng.integers(n))]
+            U = np.diag(np.exp(1j * rng.uniform(-3, 3, 2)))
+            c.add_gate(t, U)
+            ref_gates.append(("u", t, U, []))
+        elif r < 0.9:
+            t = synth.random_targets(rng, n, 2)
+            U = np.eye(4)[[0, 2, 1, 3]]
+            c.add_gate(t, U)
+            ref_gates.append(("u", t, U, []))
+        else:
+            nr = min(3, n - 1)
+            c0 = int(rng.integers(0, n - nr))
+            reg = list(range(c0, c0 + nr))
+            tgt = [q for q in range(n) if q not in reg][int(rng.integers(0, n - nr))]
+            th = rng.uniform(-3, 3, size=1 << nr)
+            c.add_ucry(tgt, reg, th)
+            ref_gates.append(("ucry", tgt, reg, th))
+    return c, ref_gates
+
+
+def oracle_apply(psi, gates):
+    for g in gates:
+        if g[0] == "u":
+            ocore.apply_gate(psi, g[1], g[2], g[3])
+        else:
+            ocore.apply_ucry(psi, g[1], g[2], g[3])
+    return psi
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_batched_matches_oracle_and_is_batch_independent(qs, dtype, cuda_device):
+    rng = np.random.default_rng(31)
+    sizes = [5, 9, 12, 13, 14, 15, 16, 7, 11, 3]
+    circs, refs, inputs = [], [], []
+    for i, n in enumerate(sizes):
+        c, g = random_circuit(qs, rng, n, 40)
+        psi = synth.gaussian_state_np(100 + i, n)
+        if dtype == torch.complex64:
+            psi = psi.astype(np.complex64).astype(np.complex128)
+        circs.append(c)
+        refs.append(oracle_apply(psi.copy(), g))
+        inputs.append(psi)
+    states = [torch.from_numpy(x).to(dtype).cuda() for x in inputs]
+    qs.qsim_apply_batched(states, circs)
+    torch.cuda.synchronize()
+    for st, ref in zip(states, refs):
+        out = st.cpu().numpy().astype(np.complex128)
+        assert np.max(np.abs(out - ref)) <= TOL[dtype]
+    # each circuit alone in a batch of one: bit-identical to its result in the mix
+    for i in (0, 3, 6, 9):
+        alone = torch.from_numpy(inputs[i]).to(dtype).cuda()
+        qs.qsim_apply_batched([alone], [circs[i]])
+        torch.cuda.synchronize()
+        assert torch.equal(alone, states[i])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_hhl_batch_matches_oracle(qs, dtype, cuda_device):
+    probs = synth.batched_problems(seed=9, count=12)
+    hs, fused, states, refs = [], [], [], []
+    for p in probs:
+        h = qs.hhl_build(p["A"], p["b"], p["m"])
+        hs.append(h)
+        fused.append(qs.qsim_fuse(h.as_circuit(), 4))
+        states.append(torch.empty(1 << h.info()["n"], dtype=dtype, device="cuda"))
+        refs.append(ohhl.solve(p["A"], p["b"], p["m"]))
+    b = qs.hhl_batch_create(hs, states, fused)
+    b.run()
+    res = b.results()
+    for p, h, st, r, ref in zip(probs, hs, states, res, refs):
+        m = p["m"]
+        tol = max(1e-12, 2.0 ** m * 2 * math.pi * 8 * np.finfo(float).eps) \
+            if dtype == torch.complex128 else TOL[dtype]
+        out = st.cpu().numpy().astype(np.complex128)
+        assert np.max(np.abs(out - ref["psi"])) <= tol
+        assert abs(r["p_success"] - ref["P"]) <= 10 * tol
+        assert abs(r["p_clock0"] - ref["P0"]) <= 10 * tol
+        assert abs(r["norm2"] - 1.0) <= (1e-12 if dtype == torch.complex128 else 1e-5)
+        scale = max(1.0, np.max(np.abs(ref["x"])))
+        assert np.max(np.abs(r["x"] - ref["x"])) <= 1e3 * tol * scale / max(ref["P0"], 1e-3)
+
+
+@pytest.mark.gpu
+def test_batch_run_captures_in_cuda_graph(qs, cuda_device):
+    probs = synth.batched_problems(seed=10, count=6)
+    hs = [qs.hhl_build(p["A"], p["b"], p["m"]) for p in probs]
+    fused = [qs.qsim_fuse(h.as_circuit(), 3) for h in hs]
+    states = [torch.empty(1 << h.info()["n"], dtype=torch.complex64, device="cuda") for h in hs]
+    b = qs.hhl_batch_create(hs, states, fused)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.run(s)
+    s.synchronize()
+    eager = b.results(s)
+    snap = [st.clone() for st in states]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.run(s)
+    for st in states:
+        st.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    replay = b.results(s)
+    for a, c in zip(snap, states):
+        assert torch.equal(a, c)
+    for a, c in zip(eager, replay):
+        assert a["p_success"] == c["p_success"] and np.array_equal(a["x"], c["x"])
+
+
+def test_batch_rejects_wide_dense_gate(qs):
+    c = qs.Circuit(8).add_gate(list(range(6)), synth.haar_unitary(np.random.default_rng(0), 64))
+    fake = ctypes.c_void_p(256)  # never dereferenced: the op check fails before any CUDA call
+    with pytest.raises(qs.QsimError) as e:
+        qs._binding.library()
+        p = ctypes.c_void_p()
+        arr_c = (ctypes.c_void_p * 1)(c.ptr)
+        arr_s = (ctypes.c_void_p * 1)(fake)
+        qs._binding._check(qs._binding.library().qsim_batch_create(arr_c, arr_s, 1, qs.QSIM_C64,
+                                                                   ctypes.byref(p)))
+    assert "max_k <= 5" in str(e.value)
