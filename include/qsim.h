@@ -248,6 +248,57 @@ int hhl_batch_autotune(const hhl_circuit *const *hs, void *const *states, int co
 int qsim_apply_batched(void *const *states, const int *n_qubits, const qsim_circuit *const *cs,
                        int count, int dtype, void *stream);
 
+/* ======================================================================================= *
+ * Serving pool: HHL solves admitted as they arrive, states resident in one device arena     *
+ * ======================================================================================= */
+
+typedef struct {
+    const double *A; /* N x N complex, interleaved, row-major (copied by qsim_submit)          */
+    const double *b; /* N complex (copied)                                                     */
+    int N;
+    int n_clock;     /* as hhl_build                                                           */
+    double t, C;     /* as hhl_build                                                           */
+    int dtype;       /* QSIM_C64 or QSIM_C128 state                                            */
+} hhl_request;
+
+typedef struct {
+    size_t bytes_total, bytes_in_use, bytes_peak; /* device arena                           */
+    int queued, building, running, done, failed;
+    long long batches_launched, singles_launched;
+} qsim_pool_info;
+
+/* Create a pool owning one device arena of `bytes` (allocated now, on the current device),
+ * n_builders host threads that build and fuse submitted HHL circuits (<= 0: half the host
+ * threads) and n_streams CUDA streams (<= 0: 8).  A request is admitted once the arena has
+ * room for its state (8 * 2^n bytes for complex64, 16 * 2^n for complex128) and a stream is
+ * free.  Requests of at most 14 qubits that the batched executor supports (dense gates of at
+ * most 5 targets) and that are ready together run as one batched launch; the others run alone
+ * with the full-GPU kernels; launches on different streams overlap.
+ * Results equal those of the same request run alone (each circuit's arithmetic does not
+ * depend on its batch).  Errors: EINVAL, ENOMEM, ECUDA. */
+int qsim_pool_create(size_t bytes, int n_builders, int n_streams, qsim_pool **out);
+
+/* Queue a request (inputs copied; returns immediately) and return its ticket.
+ * Errors: EINVAL (NULL, N out of 1..4096, bad dtype, pool shutting down). */
+int qsim_submit(qsim_pool *p, const hhl_request *req, uint64_t *ticket);
+
+/* Non-blocking: QSIM_EBUSY while the request is pending; QSIM_OK when done (x_out receives N
+ * complex values, stats and latency_s = completion - submission in seconds; the ticket is
+ * released); the request's own error code if it failed (EINVAL for a bad system, ENOMEM if its
+ * state can never fit the arena, ECUDA; ticket released, message in qsim_last_error);
+ * QSIM_ENOTFOUND for an unknown or released ticket.  Outputs may be NULL. */
+int qsim_poll(qsim_pool *p, uint64_t ticket, double *x_out, hhl_readout_stats *stats,
+              double *latency_s);
+
+/* Block until the request is no longer pending or `timeout_s` seconds pass (QSIM_ETIMEOUT).
+ * Does not release the ticket.  Errors: ETIMEOUT, ENOTFOUND, EINVAL. */
+int qsim_pool_wait(qsim_pool *p, uint64_t ticket, double timeout_s);
+
+int qsim_pool_get_info(qsim_pool *p, qsim_pool_info *out);
+
+/* Finish admitted work, drop requests not yet built, release everything.  NULL is a no-op. */
+void qsim_pool_destroy(qsim_pool *p);
+
 /* hhl_readout for callers that cannot allocate device memory.  The paper has no counterpart;
  * this is a library convenience.  Such callers include an application whose own pool
  * allocator already owns all device memory, and code that must not call cudaMalloc or

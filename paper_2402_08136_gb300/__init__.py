@@ -17,6 +17,7 @@ from ._binding import (  # noqa: F401
     qsim_apply_batched,
     qsim_batch_create,
     HHLCircuit,
+    Pool,
     hhl_build,
     hhl_build_spectral,
     hhl_prepare_state,

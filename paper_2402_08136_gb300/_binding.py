@@ -45,6 +45,19 @@ class _ReadoutStats(ctypes.Structure):
                 ("norm_x", ctypes.c_double), ("norm_b", ctypes.c_double)]
 
 
+class _HHLRequest(ctypes.Structure):
+    _fields_ = [("A", ctypes.POINTER(ctypes.c_double)), ("b", ctypes.POINTER(ctypes.c_double)),
+                ("N", ctypes.c_int), ("n_clock", ctypes.c_int), ("t", ctypes.c_double),
+                ("C", ctypes.c_double), ("dtype", ctypes.c_int)]
+
+
+class _PoolInfo(ctypes.Structure):
+    _fields_ = [("bytes_total", ctypes.c_size_t), ("bytes_in_use", ctypes.c_size_t),
+                ("bytes_peak", ctypes.c_size_t), ("queued", ctypes.c_int), ("building", ctypes.c_int),
+                ("running", ctypes.c_int), ("done", ctypes.c_int), ("failed", ctypes.c_int),
+                ("batches_launched", ctypes.c_longlong), ("singles_launched", ctypes.c_longlong)]
+
+
 _lib = None
 
 _VP = ctypes.c_void_p
@@ -80,6 +93,12 @@ _SIGS = {
                             ctypes.c_int, _VP, _IP, _DP], ctypes.c_int),
     "qsim_apply_batched": ([ctypes.POINTER(_VP), _IP, ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP],
                            ctypes.c_int),
+    "qsim_pool_create": ([ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
+    "qsim_submit": ([_VP, ctypes.POINTER(_HHLRequest), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "qsim_poll": ([_VP, ctypes.c_uint64, _DP, ctypes.POINTER(_ReadoutStats), _DP], ctypes.c_int),
+    "qsim_pool_wait": ([_VP, ctypes.c_uint64, ctypes.c_double], ctypes.c_int),
+    "qsim_pool_get_info": ([_VP, ctypes.POINTER(_PoolInfo)], ctypes.c_int),
+    "qsim_pool_destroy": ([_VP], None),
     "hhl_readout": ([_VP, ctypes.c_int, _VP, _VP, _DP, _DP, ctypes.POINTER(_ReadoutStats)],
                     ctypes.c_int),
 }
@@ -396,3 +415,59 @@ def hhl_batch_autotune(hhls, states, candidates=(1, 2, 3, 4, 5), stream=None):
                                         cand.ctypes.data_as(_IP), len(cand), _stream_ptr(stream),
                                         ctypes.byref(best), ms.ctypes.data_as(_DP)))
     return int(best.value), {int(k): float(t) for k, t in zip(cand, ms)}
+
+
+class Pool:
+    """Serving pool (device arena, builder threads, continuous batching).  submit() returns a
+    ticket; poll() returns None while pending, else a dict (x, statistics, latency_s) or raises
+    the request's error."""
+
+    def __init__(self, bytes_: int, n_builders: int = 0, n_streams: int = 0):
+        p = _VP()
+        _check(library().qsim_pool_create(int(bytes_), int(n_builders), int(n_streams), ctypes.byref(p)))
+        self._ptr = p
+        self._N = {}
+
+    def submit(self, A, b, n_clock=0, t=0.0, C=0.0, dtype=QSIM_C64) -> int:
+        Aa, Ap = _cplx(A)
+        ba, bp = _cplx(np.ravel(b))
+        req = _HHLRequest(Ap, bp, ba.size, int(n_clock), float(t), float(C), int(dtype))
+        tk = ctypes.c_uint64(0)
+        _check(library().qsim_submit(self._ptr, ctypes.byref(req), ctypes.byref(tk)))
+        self._N[int(tk.value)] = ba.size
+        return int(tk.value)
+
+    def poll(self, ticket: int):
+        N = self._N.get(ticket, 1)
+        x = np.zeros(N, dtype=np.complex128)
+        st = _ReadoutStats()
+        lat = ctypes.c_double(0)
+        rc = library().qsim_poll(self._ptr, ctypes.c_uint64(ticket), x.view(np.float64).ctypes.data_as(_DP),
+                                 ctypes.byref(st), ctypes.byref(lat))
+        if rc == -3:  # EBUSY: pending
+            return None
+        self._N.pop(ticket, None)
+        _check(rc)
+        out = {f: getattr(st, f) for f, _ in st._fields_}
+        out["x"] = x
+        out["latency_s"] = lat.value
+        return out
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> None:
+        _check(library().qsim_pool_wait(self._ptr, ctypes.c_uint64(ticket), float(timeout_s)))
+
+    def info(self) -> dict:
+        s = _PoolInfo()
+        _check(library().qsim_pool_get_info(self._ptr, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "_ptr", None):
+            library().qsim_pool_destroy(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

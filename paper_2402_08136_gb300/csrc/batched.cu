@@ -269,7 +269,9 @@ struct qsim_batch {
         size_t roff = 0;
     };
     std::vector<Meta> meta;
+    bool external = false;  // device tables and pinned results owned by the serving pool
     ~qsim_batch() {
+        if (external) return;
         if (dev) cudaFree(dev);
         if (h_results) cudaFreeHost(h_results);
     }
@@ -279,6 +281,9 @@ namespace qsim {
 namespace {
 
 using batch::BOp;
+
+template <typename R>
+void configure_batch(qsim_batch *B);
 
 void put_v(std::vector<unsigned char> &blob, int dtype, const cd &z) {
     if (dtype == QSIM_C128) {
@@ -353,38 +358,48 @@ bool encode(const Op &op, int dtype, std::vector<unsigned char> &data, BOp &b) {
     return false;
 }
 
-template <typename R>
-void configure_batch(qsim_batch *B);
-
 double circuit_cost(const qsim_circuit *c) {
     double s = 0;
     for (const Op &op : c->ops) s += (op.kind == OP_DENSE ? (double)(1 << op.targets.size()) : 1.0);
     return s * std::ldexp(1.0, c->n);
 }
 
-qsim_batch *make_batch(const std::vector<const qsim_circuit *> &cs, const std::vector<const hhl_circuit *> &hs,
+}  // namespace
+
+// Host image of a batch: every table the kernel reads, laid out as one device allocation.
+// Device pointers inside the circuit descriptors are patched once the base address is known.
+struct BatchImage {
+    std::vector<unsigned char> host;
+    size_t o_circs = 0, o_order = 0, o_counter = 0, o_ops = 0, o_data = 0, o_res = 0, total = 0;
+    std::vector<size_t> op_first, data_first;
+    size_t results = 0;
+    std::vector<qsim_batch::Meta> meta;
+    int count = 0, dtype = 0, max_n = 0;
+    bool hhl = false;
+};
+
+BatchImage batch_image(const std::vector<const qsim_circuit *> &cs, const std::vector<const hhl_circuit *> &hs,
                        void *const *states, int dtype) {
+    BatchImage im;
     const int count = (int)cs.size();
-    std::unique_ptr<qsim_batch> B(new qsim_batch());
-    B->count = count;
-    B->dtype = dtype;
-    B->hhl = !hs.empty();
+    im.count = count;
+    im.dtype = dtype;
+    im.hhl = !hs.empty();
     std::vector<BOp> ops;
     std::vector<unsigned char> data;
     std::vector<batch::BCirc> circs(count);
-    std::vector<size_t> op_first(count), data_first(count);
-    int max_n = 0;
-    size_t results = 0;
-    B->meta.resize(count);
+    im.op_first.resize(count);
+    im.data_first.resize(count);
+    im.meta.resize(count);
     for (int i = 0; i < count; i++) {
         const qsim_circuit *c = cs[i];
         build_ops(const_cast<qsim_circuit *>(c));
         QSIM_REQUIRE(c->n <= 30, "batched states are limited to 30 qubits");
         QSIM_REQUIRE(states[i] != nullptr, "NULL state");
-        max_n = std::max(max_n, c->n);
+        im.max_n = std::max(im.max_n, c->n);
         while (data.size() % 256) data.push_back(0);
-        data_first[i] = data.size();
-        op_first[i] = ops.size();
+        im.data_first[i] = data.size();
+        im.op_first[i] = ops.size();
         std::vector<unsigned char> local;
         for (const Op &op : c->ops) {
             BOp b;
@@ -398,71 +413,129 @@ qsim_batch *make_batch(const std::vector<const qsim_circuit *> &cs, const std::v
         bc.n = c->n;
         bc.nops = (int)c->ops.size();
         bc.state = states[i];
-        if (B->hhl) {
+        if (im.hhl) {
             const hhl_circuit *h = hs[i];
             QSIM_REQUIRE(h->n == c->n, "HHL circuit and gate list disagree on the qubit count");
             bc.flags = 3;
             bc.nb = h->nb;
             bc.b_off = (unsigned)(local.size() / vbytes(dtype));
             for (const cd &z : h->b_pad) put_v(local, dtype, z);
-            B->meta[i].N = h->N;
-            B->meta[i].nb = h->nb;
-            B->meta[i].C = h->C;
-            B->meta[i].norm_b = h->norm_b;
-            B->meta[i].roff = results;
-            results += 4 + 2 * ((size_t)1 << h->nb);
+            im.meta[i].N = h->N;
+            im.meta[i].nb = h->nb;
+            im.meta[i].C = h->C;
+            im.meta[i].norm_b = h->norm_b;
+            im.meta[i].roff = im.results;
+            im.results += 4 + 2 * ((size_t)1 << h->nb);
         }
         data.insert(data.end(), local.begin(), local.end());
     }
-    // order: most expensive first
     std::vector<int> order(count);
     std::iota(order.begin(), order.end(), 0);
     std::vector<double> cost(count);
     for (int i = 0; i < count; i++) cost[i] = circuit_cost(cs[i]);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    // one device allocation
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t o_circs = 0, o_order = al(o_circs + sizeof(batch::BCirc) * count);
-    const size_t o_counter = al(o_order + sizeof(int) * count);
-    const size_t o_ops = al(o_counter + 256);
-    const size_t o_data = al(o_ops + sizeof(BOp) * std::max<size_t>(1, ops.size()));
-    const size_t o_res = al(o_data + std::max<size_t>(1, data.size()));
-    const size_t total = al(o_res + sizeof(double) * std::max<size_t>(1, results));
-    cudaError_t e = cudaMalloc(&B->dev, total);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        throw Error(QSIM_ENOMEM, std::string("cudaMalloc for batch tables: ") + cudaGetErrorString(e));
+    im.o_circs = 0;
+    im.o_order = al(im.o_circs + sizeof(batch::BCirc) * count);
+    im.o_counter = al(im.o_order + sizeof(int) * count);
+    im.o_ops = al(im.o_counter + 256);
+    im.o_data = al(im.o_ops + sizeof(BOp) * std::max<size_t>(1, ops.size()));
+    im.o_res = al(im.o_data + std::max<size_t>(1, data.size()));
+    im.total = al(im.o_res + sizeof(double) * std::max<size_t>(1, im.results));
+    im.host.assign(im.o_res, 0);  // results are written by the kernel, not uploaded
+    std::memcpy(im.host.data() + im.o_circs, circs.data(), sizeof(batch::BCirc) * count);
+    std::memcpy(im.host.data() + im.o_order, order.data(), sizeof(int) * count);
+    if (!ops.empty()) std::memcpy(im.host.data() + im.o_ops, ops.data(), sizeof(BOp) * ops.size());
+    if (!data.empty()) std::memcpy(im.host.data() + im.o_data, data.data(), data.size());
+    return im;
+}
+
+// Patch the device pointers of `im` for base address `dev` and build the batch object.
+// external: `dev` (im.total bytes) and `pinned_results` belong to the caller and the tables
+// are uploaded asynchronously on `st`; otherwise the batch allocates and uploads synchronously.
+qsim_batch *batch_from_image(BatchImage &im, void *dev, double *pinned_results, cudaStream_t st) {
+    std::unique_ptr<qsim_batch> B(new qsim_batch());
+    B->count = im.count;
+    B->dtype = im.dtype;
+    B->hhl = im.hhl;
+    B->meta = im.meta;
+    const bool external = dev != nullptr;
+    B->external = external;
+    if (!external) {
+        cudaError_t e = cudaMalloc(&dev, im.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error(QSIM_ENOMEM, std::string("cudaMalloc for batch tables: ") + cudaGetErrorString(e));
+        }
     }
-    B->dev_bytes = total;
-    unsigned char *base = static_cast<unsigned char *>(B->dev);
-    for (int i = 0; i < count; i++) {
-        circs[i].ops = reinterpret_cast<const BOp *>(base + o_ops) + op_first[i];
-        circs[i].data = base + o_data + data_first[i];
-        circs[i].result = B->hhl ? reinterpret_cast<double *>(base + o_res) + B->meta[i].roff : nullptr;
+    B->dev = dev;
+    B->dev_bytes = im.total;
+    unsigned char *base = static_cast<unsigned char *>(dev);
+    batch::BCirc *hc = reinterpret_cast<batch::BCirc *>(im.host.data() + im.o_circs);
+    for (int i = 0; i < im.count; i++) {
+        hc[i].ops = reinterpret_cast<const BOp *>(base + im.o_ops) + im.op_first[i];
+        hc[i].data = base + im.o_data + im.data_first[i];
+        hc[i].result = im.hhl ? reinterpret_cast<double *>(base + im.o_res) + im.meta[i].roff : nullptr;
     }
-    std::vector<unsigned char> host(total, 0);
-    std::memcpy(host.data() + o_circs, circs.data(), sizeof(batch::BCirc) * count);
-    std::memcpy(host.data() + o_order, order.data(), sizeof(int) * count);
-    if (!ops.empty()) std::memcpy(host.data() + o_ops, ops.data(), sizeof(BOp) * ops.size());
-    if (!data.empty()) std::memcpy(host.data() + o_data, data.data(), data.size());
-    e = cudaMemcpy(B->dev, host.data(), total, cudaMemcpyHostToDevice);
+    cudaError_t e;
+    if (external) {
+        // from pageable memory: the call returns once the source has been staged
+        e = cudaMemcpyAsync(dev, im.host.data(), im.host.size(), cudaMemcpyHostToDevice, st);
+    } else {
+        e = cudaMemcpy(dev, im.host.data(), im.host.size(), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("uploading batch tables: ") + cudaGetErrorString(e));
-    B->d_circs = reinterpret_cast<batch::BCirc *>(base + o_circs);
-    B->d_order = reinterpret_cast<int *>(base + o_order);
-    B->d_counter = reinterpret_cast<unsigned *>(base + o_counter);
-    B->d_results = reinterpret_cast<double *>(base + o_res);
-    B->results_doubles = results;
-    if (results) {
-        e = cudaMallocHost(&B->h_results, sizeof(double) * results);
-        if (e != cudaSuccess) throw Error(QSIM_ENOMEM, "pinned host buffer for batch results");
+    B->d_circs = reinterpret_cast<batch::BCirc *>(base + im.o_circs);
+    B->d_order = reinterpret_cast<int *>(base + im.o_order);
+    B->d_counter = reinterpret_cast<unsigned *>(base + im.o_counter);
+    B->d_results = reinterpret_cast<double *>(base + im.o_res);
+    B->results_doubles = im.results;
+    if (im.results) {
+        if (external) {
+            B->h_results = pinned_results;
+        } else {
+            e = cudaMallocHost(&B->h_results, sizeof(double) * im.results);
+            if (e != cudaSuccess) throw Error(QSIM_ENOMEM, "pinned host buffer for batch results");
+        }
     }
-    // shared-memory residency: up to 2^13 (complex128) / 2^14 (complex64) amplitudes
-    const int cap_amps = dtype == QSIM_C128 ? (1 << 13) : (1 << 14);
-    B->smem_amps = std::min(cap_amps, 1 << max_n);
-    if (dtype == QSIM_C128) configure_batch<double>(B.get());
+    const int cap_amps = im.dtype == QSIM_C128 ? (1 << 13) : (1 << 14);
+    B->smem_amps = std::min(cap_amps, 1 << im.max_n);
+    if (im.dtype == QSIM_C128) configure_batch<double>(B.get());
     else configure_batch<float>(B.get());
     return B.release();
 }
+
+qsim_batch *make_batch(const std::vector<const qsim_circuit *> &cs, const std::vector<const hhl_circuit *> &hs,
+                       void *const *states, int dtype) {
+    BatchImage im = batch_image(cs, hs, states, dtype);
+    return batch_from_image(im, nullptr, nullptr, nullptr);
+}
+
+bool batch_supported(const qsim_circuit *c) {
+    build_ops(const_cast<qsim_circuit *>(c));
+    if (c->n > 30) return false;
+    for (const Op &op : c->ops) {
+        if (op.kind == OP_DENSE && op.targets.size() > 5) return false;
+        if (op.kind == OP_DIAG && op.targets.size() > 8) return false;
+        if (op.kind == OP_UCRY)
+            for (size_t j = 1; j < op.controls.size(); j++)
+                if (op.controls[j] != op.controls[0] + (int)j) return false;
+    }
+    return true;
+}
+
+BatchImage *batch_plan(const std::vector<const qsim_circuit *> &cs, const std::vector<const hhl_circuit *> &hs,
+                       void *const *states, int dtype) {
+    return new BatchImage(batch_image(cs, hs, states, dtype));
+}
+size_t batch_plan_device_bytes(const BatchImage *im) { return im->total; }
+size_t batch_plan_result_doubles(const BatchImage *im) { return im->results; }
+void batch_plan_free(BatchImage *im) { delete im; }
+qsim_batch *batch_instantiate(BatchImage *im, void *dev, double *pinned, cudaStream_t st) {
+    return batch_from_image(*im, dev, pinned, st);
+}
+
+namespace {
 
 // Kernel attributes and the grid are fixed when the batch is created, so that a run is only a
 // memset and a launch (capturable into a CUDA graph).
@@ -500,6 +573,37 @@ void run_batch(qsim_batch *B, void *stream) {
 }
 
 }  // namespace
+
+void batch_launch(qsim_batch *b, cudaStream_t st) { run_batch(b, st); }
+
+void batch_enqueue_results(qsim_batch *b, cudaStream_t st) {
+    if (!b->results_doubles) return;
+    cudaError_t e = cudaMemcpyAsync(b->h_results, b->d_results, sizeof(double) * b->results_doubles,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batch results: ") + cudaGetErrorString(e));
+}
+
+void batch_host_result(const qsim_batch *b, int i, double *x_out, hhl_readout_stats *stats) {
+    const qsim_batch::Meta &m = b->meta[i];
+    const double *r = b->h_results + m.roff;
+    const double P = r[1], P0 = r[2];
+    const double inv = P0 > 0 ? 1.0 / std::sqrt(P0) : 0.0;
+    const double norm_x = std::sqrt(P) / m.C;
+    if (x_out)
+        for (int j = 0; j < m.N; j++) {
+            x_out[2 * j] = r[4 + 2 * j] * inv * norm_x * m.norm_b;
+            x_out[2 * j + 1] = r[4 + 2 * j + 1] * inv * norm_x * m.norm_b;
+        }
+    if (stats) {
+        stats->p_success = P;
+        stats->p_clock0 = P0;
+        stats->leakage = P - P0;
+        stats->norm2 = r[0];
+        stats->norm_x = norm_x;
+        stats->norm_b = m.norm_b;
+    }
+}
+
 }  // namespace qsim
 
 using namespace qsim;

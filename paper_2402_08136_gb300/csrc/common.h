@@ -88,6 +88,7 @@ struct DeviceBlob {
     void *ptr = nullptr;
     size_t bytes = 0;
     int device = -1;
+    bool external = false;  // memory owned by someone else (the serving pool's arena)
 };
 
 }  // namespace qsim
@@ -120,6 +121,13 @@ void circuit_info(const qsim_circuit *c, qsim_circuit_info *out);
 // kernels.cu
 void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream);
 void ensure_device_blob(qsim_circuit *c, int dtype);
+std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype);   // sets op offsets
+void attach_external_blob(qsim_circuit *c, int dtype, void *dev, size_t bytes);
+// launches the readout reductions and async copies of the sums (3 doubles) and of the raw
+// 2^nb-amplitude slice into pinned host memory; scratch holds >= readout_scratch_doubles(n)
+size_t readout_scratch_doubles(int n);
+void readout_launch_async(const void *state, int dtype, int n, int nb, cudaStream_t st, double *scratch,
+                          double *pinned_sums, void *pinned_slice);
 void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb, void *stream);
 void readout_device(const void *state, int dtype, int n, int nb, int m, void *stream,
                     double sums[3], cd *slice);
@@ -129,6 +137,19 @@ size_t dense_tc_blob_bytes(int k);
 void dense_tc_pack(int k, const std::vector<cd> &U, unsigned char *out);
 bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const std::vector<int> &controls,
                      const void *Bdev, int sms, cudaStream_t st);
+// batched.cu: plan (host image) / instantiate (device tables) / launch / results, for the pool
+struct BatchImage;
+bool batch_supported(const qsim_circuit *c);  // every op runs in the batched executor
+BatchImage *batch_plan(const std::vector<const qsim_circuit *> &cs, const std::vector<const hhl_circuit *> &hs,
+                       void *const *states, int dtype);
+size_t batch_plan_device_bytes(const BatchImage *im);
+size_t batch_plan_result_doubles(const BatchImage *im);
+void batch_plan_free(BatchImage *im);
+// tables uploaded asynchronously on `st` into `dev` (external memory); results go to `pinned`
+qsim_batch *batch_instantiate(BatchImage *im, void *dev, double *pinned, cudaStream_t st);
+void batch_launch(qsim_batch *b, cudaStream_t st);
+void batch_enqueue_results(qsim_batch *b, cudaStream_t st);
+void batch_host_result(const qsim_batch *b, int i, double *x_out, hhl_readout_stats *stats);
 // linalg.cpp
 void hermitian_eig(int N, const std::vector<cd> &A, std::vector<double> &lam, std::vector<cd> &V);
 }  // namespace qsim

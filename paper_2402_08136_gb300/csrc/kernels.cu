@@ -710,15 +710,8 @@ bool tc_enabled() {
 
 // Pack every op's device data (dense matrices transposed, diagonals, UCRY (cos, sin) tables)
 // into one device allocation per dtype, uploaded once.
-void ensure_device_blob(qsim_circuit *c, int dtype) {
-    build_ops(c);
-    std::lock_guard<std::mutex> lk(c->mu);
+std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype) {
     const int slot = dtype == QSIM_C128 ? 1 : 0;
-    int dev = 0;
-    CUDA_OK(cudaGetDevice(&dev));
-    DeviceBlob &B = c->blob[slot];
-    if (B.ptr && B.device == dev) return;
-    QSIM_REQUIRE(B.ptr == nullptr, "circuit already uploaded to another device");
     std::vector<unsigned char> blob;
     for (Op &op : c->ops) {
         align_blob(blob);
@@ -743,6 +736,31 @@ void ensure_device_blob(qsim_circuit *c, int dtype) {
     }
     align_blob(blob);
     if (blob.empty()) blob.resize(256, 0);
+    return blob;
+}
+
+void attach_external_blob(qsim_circuit *c, int dtype, void *dev, size_t bytes) {
+    std::lock_guard<std::mutex> lk(c->mu);
+    int d = 0;
+    CUDA_OK(cudaGetDevice(&d));
+    DeviceBlob &B = c->blob[dtype == QSIM_C128 ? 1 : 0];
+    QSIM_REQUIRE(B.ptr == nullptr, "circuit already has device matrices");
+    B.ptr = dev;
+    B.bytes = bytes;
+    B.device = d;
+    B.external = true;
+}
+
+void ensure_device_blob(qsim_circuit *c, int dtype) {
+    build_ops(c);
+    std::lock_guard<std::mutex> lk(c->mu);
+    const int slot = dtype == QSIM_C128 ? 1 : 0;
+    int dev = 0;
+    CUDA_OK(cudaGetDevice(&dev));
+    DeviceBlob &B = c->blob[slot];
+    if (B.ptr && B.device == dev) return;
+    QSIM_REQUIRE(B.ptr == nullptr, "circuit already uploaded to another device");
+    std::vector<unsigned char> blob = pack_device_blob(c, dtype);
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, blob.size());
     if (e != cudaSuccess) {
@@ -806,6 +824,36 @@ void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb
                                 buf.data(), (size_t)rest * vb, cudaMemcpyHostToDevice, st));
         CUDA_OK(cudaStreamSynchronize(st));
     }
+}
+
+static int readout_blocks(int n) {
+    int lg = std::max(1, std::min(11, n - 12));
+    if (n <= 1) lg = 0;
+    return 1 << lg;
+}
+
+size_t readout_scratch_doubles(int n) { return (size_t)readout_blocks(n) + 8; }
+
+void readout_launch_async(const void *state, int dtype, int n, int nb, cudaStream_t st, double *scratch,
+                          double *pinned_sums, void *pinned_slice) {
+    const long long N = 1ll << n;
+    const int nblk = readout_blocks(n);
+    const long long chunk = N / nblk;
+    const size_t vb = 2 * real_size(dtype);
+    const size_t slice_len = (size_t)1 << nb;
+    double *partials = scratch, *out = scratch + nblk;
+    const long long off = N / 2;
+    if (dtype == QSIM_C128) {
+        norm_partials_kernel<double><<<nblk, 256, 0, st>>>(state, chunk, partials);
+        norm_final_kernel<double><<<1, 256, 0, st>>>(partials, nblk, state, off, (int)slice_len, out);
+    } else {
+        norm_partials_kernel<float><<<nblk, 256, 0, st>>>(state, chunk, partials);
+        norm_final_kernel<float><<<1, 256, 0, st>>>(partials, nblk, state, off, (int)slice_len, out);
+    }
+    check_launch("readout kernels");
+    CUDA_OK(cudaMemcpyAsync(pinned_sums, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_OK(cudaMemcpyAsync(pinned_slice, static_cast<const unsigned char *>(state) + off * vb, slice_len * vb,
+                            cudaMemcpyDeviceToHost, st));
 }
 
 void readout_device(const void *state, int dtype, int n, int nb, int m, void *stream,
@@ -979,7 +1027,7 @@ using namespace qsim;
 
 qsim_circuit::~qsim_circuit() {
     for (DeviceBlob &b : blob) {
-        if (b.ptr) {
+        if (b.ptr && !b.external) {
             int cur = -1;
             cudaGetDevice(&cur);
             if (cur != b.device) cudaSetDevice(b.device);

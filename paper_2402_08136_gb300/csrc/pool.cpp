@@ -1,0 +1,559 @@
+// Serving pool: HHL solves of different sizes admitted as they arrive, state vectors resident in
+// one device arena with memory-budget admission, continuous batching across CUDA streams.
+//
+// Threads
+//   builders  (n_builders): hhl_build + qsim_fuse of submitted requests on the host;
+//   scheduler (1)         : admits built requests while the arena has room for their state
+//                           (S * 2^n bytes, S = 8 or 16) and a stream slot is free, launches
+//                           them, and retires finished work by polling CUDA events.
+// Small requests (at most `small_n` qubits, every fused operation supported by the batched
+// executor) that are ready together are launched as one
+// persistent batched kernel (one CTA per circuit, state in shared memory); larger requests run
+// alone on a stream with the full-GPU kernels (tensor cores for complex64 dense gates).  Work
+// keeps arriving while earlier launches run: every free stream slot takes the next admitted
+// group, so launches overlap on the device.
+//
+// The hot path allocates nothing from CUDA: states, batch tables, gate matrices and readout
+// scratch are carved out of the arena (first fit, coalescing), copies to the host land in
+// pinned per-slot buffers allocated when the pool is created, and table uploads are
+// cudaMemcpyAsync from pageable memory (returns once staged).  cudaFree, which would
+// synchronize the device, is only called when the pool is destroyed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <thread>
+#include <unordered_map>
+
+#include "common.h"
+
+namespace qsim {
+namespace {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over [0, cap) with coalescing free list; 256-byte granularity.
+class Arena {
+  public:
+    explicit Arena(size_t cap) : cap_(cap) { free_[0] = cap; }
+    bool alloc(size_t bytes, size_t *off) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes;
+                const size_t start = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                used_ += bytes;
+                peak_ = std::max(peak_, used_);
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t cap() const { return cap_; }
+    size_t used() const { return used_; }
+    size_t peak() const { return peak_; }
+
+  private:
+    size_t cap_, used_ = 0, peak_ = 0;
+    std::map<size_t, size_t> free_;
+};
+
+struct Block {
+    size_t off = 0, bytes = 0;
+};
+
+struct PoolReq {
+    uint64_t id = 0;
+    std::vector<double> A, b;
+    int N = 0, n_clock = 0, dtype = QSIM_C64;
+    double t = 0, C = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    int status = QSIM_EBUSY;  // EBUSY while pending
+    std::string err;
+    hhl_circuit *h = nullptr;
+    qsim_circuit *fused = nullptr;
+    int n = 0;
+    bool small = false;  // runs in a batched launch
+    std::vector<Block> blocks;  // arena blocks held while running
+    void *state = nullptr;
+    std::vector<double> x;
+    hhl_readout_stats stats{};
+    ~PoolReq() {
+        if (fused) qsim_circuit_free(fused);
+        if (h) hhl_circuit_free(h);
+    }
+};
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    double *pinned = nullptr;  // results / readout landing zone
+    size_t pinned_doubles = 0;
+    bool busy = false;
+    std::vector<PoolReq *> reqs;
+    qsim_batch *batch = nullptr;
+    std::vector<Block> blocks;  // tables / matrices / scratch of this launch
+    bool large = false;
+};
+
+}  // namespace
+}  // namespace qsim
+
+struct qsim_pool {
+    int device = 0;
+    void *arena_base = nullptr;
+    std::unique_ptr<qsim::Arena> arena;
+    std::vector<qsim::Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<qsim::PoolReq *> submitted, built;
+    std::unordered_map<uint64_t, std::unique_ptr<qsim::PoolReq>> reqs;
+    std::vector<std::thread> builders;
+    std::thread scheduler;
+    bool stop = false;
+    uint64_t next_id = 1;
+    int small_n = 14, max_batch = 512, k_small = 2, k_large_c64 = 6, k_large_c128 = 2;
+    int n_building = 0, n_running = 0, n_done = 0, n_failed = 0;
+    long long batches = 0, singles = 0;
+};
+
+namespace qsim {
+namespace {
+
+size_t amp_bytes(int dtype) { return dtype == QSIM_C128 ? 16 : 8; }
+
+void fail(qsim_pool *p, PoolReq *r, int code, const std::string &msg) {
+    r->status = code;
+    r->err = msg;
+    r->t_done = now_s();
+    p->n_failed++;
+}
+
+void builder_loop(qsim_pool *p) {
+    cudaSetDevice(p->device);
+    for (;;) {
+        PoolReq *r;
+        {
+            std::unique_lock<std::mutex> lk(p->mu);
+            p->cv_work.wait(lk, [&] { return p->stop || !p->submitted.empty(); });
+            if (p->stop) return;
+            r = p->submitted.front();
+            p->submitted.pop_front();
+            p->n_building++;
+        }
+        int rc = hhl_build(r->A.data(), r->b.data(), r->N, r->n_clock, r->t, r->C, &r->h);
+        std::string msg = rc == QSIM_OK ? "" : qsim_last_error();
+        if (rc == QSIM_OK) {
+            r->n = r->h->n;
+            const int k = r->n <= p->small_n ? p->k_small
+                                             : (r->dtype == QSIM_C64 ? p->k_large_c64 : p->k_large_c128);
+            rc = qsim_fuse(&r->h->circ, k, &r->fused);
+            if (rc != QSIM_OK) msg = qsim_last_error();
+            else r->small = r->n <= p->small_n && batch_supported(r->fused);
+        }
+        std::lock_guard<std::mutex> lk(p->mu);
+        p->n_building--;
+        if (rc != QSIM_OK) {
+            fail(p, r, rc, msg);
+            p->cv_done.notify_all();
+        } else {
+            p->built.push_back(r);
+            p->cv_work.notify_all();
+        }
+    }
+}
+
+void release_blocks(qsim_pool *p, std::vector<Block> &bl) {
+    for (const Block &b : bl) p->arena->release(b.off, b.bytes);
+    bl.clear();
+}
+
+bool take(qsim_pool *p, size_t bytes, std::vector<Block> &into) {
+    size_t off;
+    if (!p->arena->alloc(bytes, &off)) return false;
+    into.push_back({off, bytes});
+    return true;
+}
+
+void *addr(qsim_pool *p, const Block &b) { return static_cast<unsigned char *>(p->arena_base) + b.off; }
+
+// Retire a finished slot: results to the requests, memory back to the arena.  Caller holds mu.
+void retire(qsim_pool *p, Slot &s, cudaError_t status) {
+    const double t = now_s();
+    for (size_t i = 0; i < s.reqs.size(); i++) {
+        PoolReq *r = s.reqs[i];
+        if (status != cudaSuccess) {
+            fail(p, r, QSIM_ECUDA, std::string("device work failed: ") + cudaGetErrorString(status));
+        } else {
+            r->x.assign(2 * (size_t)r->N, 0.0);
+            if (s.batch) {
+                batch_host_result(s.batch, (int)i, r->x.data(), &r->stats);
+            } else {
+                const double *sums = s.pinned;
+                const unsigned char *slice = reinterpret_cast<const unsigned char *>(s.pinned + 4);
+                const double P = sums[1], P0 = sums[2];
+                const double inv = P0 > 0 ? 1.0 / std::sqrt(P0) : 0.0;
+                const double norm_x = std::sqrt(P) / r->h->C;
+                for (int j = 0; j < r->N; j++) {
+                    double re, im;
+                    if (r->dtype == QSIM_C128) {
+                        re = reinterpret_cast<const double *>(slice)[2 * j];
+                        im = reinterpret_cast<const double *>(slice)[2 * j + 1];
+                    } else {
+                        re = reinterpret_cast<const float *>(slice)[2 * j];
+                        im = reinterpret_cast<const float *>(slice)[2 * j + 1];
+                    }
+                    r->x[2 * j] = re * inv * norm_x * r->h->norm_b;
+                    r->x[2 * j + 1] = im * inv * norm_x * r->h->norm_b;
+                }
+                r->stats.p_success = P;
+                r->stats.p_clock0 = P0;
+                r->stats.leakage = P - P0;
+                r->stats.norm2 = sums[0];
+                r->stats.norm_x = norm_x;
+                r->stats.norm_b = r->h->norm_b;
+            }
+            r->status = QSIM_OK;
+            r->t_done = t;
+            p->n_done++;
+        }
+        release_blocks(p, r->blocks);
+        p->n_running--;
+    }
+    if (s.batch) {
+        qsim_batch_free(s.batch);  // external tables: no CUDA call
+        s.batch = nullptr;
+    }
+    release_blocks(p, s.blocks);
+    s.reqs.clear();
+    s.busy = false;
+}
+
+// Launch a group of small requests as one batch on slot s.  Caller holds mu; requests already
+// hold their state blocks.
+void launch_small(qsim_pool *p, Slot &s, std::vector<PoolReq *> &group) {
+    std::vector<const qsim_circuit *> cs;
+    std::vector<const hhl_circuit *> hs;
+    std::vector<void *> states;
+    for (PoolReq *r : group) {
+        cs.push_back(r->fused);
+        hs.push_back(r->h);
+        states.push_back(r->state);
+    }
+    std::unique_ptr<BatchImage, void (*)(BatchImage *)> im(batch_plan(cs, hs, states.data(), group[0]->dtype),
+                                                          batch_plan_free);
+    QSIM_REQUIRE(batch_plan_result_doubles(im.get()) <= s.pinned_doubles, "batch results exceed the slot buffer");
+    Block tb;
+    if (!p->arena->alloc(batch_plan_device_bytes(im.get()), &tb.off)) throw Error(QSIM_EBUSY, "arena full");
+    tb.bytes = batch_plan_device_bytes(im.get());
+    s.blocks.push_back(tb);
+    s.batch = batch_instantiate(im.get(), addr(p, tb), s.pinned, s.st);
+    batch_launch(s.batch, s.st);
+    batch_enqueue_results(s.batch, s.st);
+    cudaError_t e = cudaEventRecord(s.ev, s.st);
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, cudaGetErrorString(e));
+    s.reqs = group;
+    s.busy = true;
+    s.large = false;
+    p->batches++;
+}
+
+// Launch one large request on slot s (full-GPU kernels).  Caller holds mu.
+void launch_large(qsim_pool *p, Slot &s, PoolReq *r) {
+    const int dtype = r->dtype;
+    std::vector<unsigned char> blob = pack_device_blob(r->fused, dtype);
+    Block mb, sb;
+    if (!p->arena->alloc(blob.size(), &mb.off)) throw Error(QSIM_EBUSY, "arena full");
+    mb.bytes = blob.size();
+    s.blocks.push_back(mb);
+    const size_t scr = readout_scratch_doubles(r->n) * sizeof(double);
+    if (!p->arena->alloc(scr, &sb.off)) throw Error(QSIM_EBUSY, "arena full");
+    sb.bytes = scr;
+    s.blocks.push_back(sb);
+    cudaError_t e = cudaMemcpyAsync(addr(p, mb), blob.data(), blob.size(), cudaMemcpyHostToDevice, s.st);
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("matrix upload: ") + cudaGetErrorString(e));
+    attach_external_blob(r->fused, dtype, addr(p, mb), blob.size());
+    launch_prepare_state(r->state, r->n, dtype, r->h->b_pad.data(), r->h->nb, s.st);
+    apply_ops(r->state, r->n, dtype, r->fused, s.st);
+    readout_launch_async(r->state, dtype, r->n, r->h->nb, s.st, static_cast<double *>(addr(p, sb)), s.pinned,
+                         s.pinned + 4);
+    e = cudaEventRecord(s.ev, s.st);
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, cudaGetErrorString(e));
+    s.reqs = {r};
+    s.busy = true;
+    s.large = true;
+    p->singles++;
+}
+
+void scheduler_loop(qsim_pool *p) {
+    cudaSetDevice(p->device);
+    std::unique_lock<std::mutex> lk(p->mu);
+    for (;;) {
+        bool progress = false;
+        // 1. retire finished launches
+        for (Slot &s : p->slots) {
+            if (!s.busy) continue;
+            cudaError_t q = cudaEventQuery(s.ev);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) cudaGetLastError();
+            retire(p, s, q);
+            progress = true;
+        }
+        if (progress) p->cv_done.notify_all();
+        if (p->stop && p->built.empty() && p->submitted.empty() && p->n_building == 0) {
+            bool any = false;
+            for (Slot &s : p->slots) any |= s.busy;
+            if (!any) return;
+        }
+        // 2. admit built requests: states first (memory budget), then launches on free slots
+        for (Slot &s : p->slots) {
+            if (s.busy || p->built.empty()) continue;
+            std::vector<PoolReq *> group;
+            PoolReq *large = nullptr;
+            for (auto it = p->built.begin(); it != p->built.end();) {
+                PoolReq *r = *it;
+                const size_t need = amp_bytes(r->dtype) << r->n;
+                if (need > p->arena->cap()) {
+                    fail(p, r, QSIM_ENOMEM, "state larger than the pool");
+                    it = p->built.erase(it);
+                    p->cv_done.notify_all();
+                    continue;
+                }
+                const bool is_small = r->small;
+                if (!is_small && (!group.empty() || large)) {
+                    ++it;
+                    continue;
+                }
+                if (is_small && (large || (!group.empty() && r->dtype != group[0]->dtype) ||
+                                 (int)group.size() >= p->max_batch)) {
+                    ++it;
+                    continue;
+                }
+                if (!take(p, need, r->blocks)) break;  // memory budget: wait for retirements
+                r->state = addr(p, r->blocks.back());
+                r->t_admit = now_s();
+                p->n_running++;
+                it = p->built.erase(it);
+                if (is_small) group.push_back(r);
+                else large = r;
+                if (large) break;
+            }
+            try {
+                if (large) launch_large(p, s, large);
+                else if (!group.empty()) launch_small(p, s, group);
+                else continue;
+                progress = true;
+            } catch (const Error &e) {
+                // put the requests back if the arena was too full for the tables, fail otherwise
+                std::vector<PoolReq *> rs = large ? std::vector<PoolReq *>{large} : group;
+                release_blocks(p, s.blocks);
+                if (s.batch) {
+                    qsim_batch_free(s.batch);
+                    s.batch = nullptr;
+                }
+                for (PoolReq *r : rs) {
+                    release_blocks(p, r->blocks);
+                    p->n_running--;
+                    if (e.code == QSIM_EBUSY) p->built.push_front(r);
+                    else {
+                        fail(p, r, e.code, e.what());
+                        p->cv_done.notify_all();
+                    }
+                }
+                s.busy = false;
+                s.reqs.clear();
+                if (e.code == QSIM_EBUSY) break;
+            }
+        }
+        if (!progress) p->cv_work.wait_for(lk, std::chrono::microseconds(50));
+    }
+}
+
+}  // namespace
+}  // namespace qsim
+
+using namespace qsim;
+
+extern "C" {
+
+int qsim_pool_create(size_t bytes, int n_builders, int n_streams, qsim_pool **out) {
+    return guarded([&] {
+        QSIM_REQUIRE(out != nullptr && bytes >= (1u << 20), "pool needs at least 1 MiB");
+        if (n_builders <= 0) n_builders = std::max(1u, std::thread::hardware_concurrency() / 2);
+        if (n_streams <= 0) n_streams = 8;
+        std::unique_ptr<qsim_pool> p(new qsim_pool());
+        if (cudaGetDevice(&p->device) != cudaSuccess) throw Error(QSIM_ECUDA, "no CUDA device");
+        cudaError_t e = cudaMalloc(&p->arena_base, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error(QSIM_ENOMEM, std::string("pool arena: ") + cudaGetErrorString(e));
+        }
+        p->arena.reset(new Arena(bytes));
+        p->slots.resize(n_streams);
+        const size_t pin = 4 + 2 * ((size_t)1 << 12);  // large readout: sums + 2^12-amplitude slice
+        const size_t pin_batch = (size_t)p->max_batch * (4 + 2 * 128);
+        for (Slot &s : p->slots) {
+            s.pinned_doubles = std::max(pin, pin_batch);
+            if (cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess ||
+                cudaMallocHost(&s.pinned, s.pinned_doubles * sizeof(double)) != cudaSuccess)
+                throw Error(QSIM_ECUDA, "creating pool streams / pinned buffers");
+        }
+        qsim_pool *raw = p.get();
+        for (int i = 0; i < n_builders; i++) raw->builders.emplace_back(builder_loop, raw);
+        raw->scheduler = std::thread(scheduler_loop, raw);
+        *out = p.release();
+    });
+}
+
+int qsim_submit(qsim_pool *p, const hhl_request *req, uint64_t *ticket) {
+    return guarded([&] {
+        QSIM_REQUIRE(p != nullptr && req != nullptr && ticket != nullptr, "NULL argument");
+        QSIM_REQUIRE(req->A != nullptr && req->b != nullptr && req->N >= 1 && req->N <= 4096, "bad request shape");
+        QSIM_REQUIRE(req->dtype == QSIM_C64 || req->dtype == QSIM_C128, "dtype must be QSIM_C64 or QSIM_C128");
+        std::unique_ptr<PoolReq> r(new PoolReq());
+        r->A.assign(req->A, req->A + 2 * (size_t)req->N * req->N);
+        r->b.assign(req->b, req->b + 2 * (size_t)req->N);
+        r->N = req->N;
+        r->n_clock = req->n_clock;
+        r->t = req->t;
+        r->C = req->C;
+        r->dtype = req->dtype;
+        r->t_submit = now_s();
+        std::lock_guard<std::mutex> lk(p->mu);
+        QSIM_REQUIRE(!p->stop, "pool is shutting down");
+        r->id = p->next_id++;
+        *ticket = r->id;
+        p->submitted.push_back(r.get());
+        p->reqs.emplace(r->id, std::move(r));
+        p->cv_work.notify_all();
+    });
+}
+
+int qsim_poll(qsim_pool *p, uint64_t ticket, double *x_out, hhl_readout_stats *stats, double *latency_s) {
+    // status codes are returned directly (EBUSY pending, ENOTFOUND unknown, the request's error)
+    if (!p) {
+        set_last_error("NULL pool");
+        return QSIM_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(p->mu);
+    auto it = p->reqs.find(ticket);
+    if (it == p->reqs.end()) {
+        set_last_error("unknown ticket");
+        return QSIM_ENOTFOUND;
+    }
+    PoolReq *r = it->second.get();
+    if (r->status == QSIM_EBUSY) {
+        set_last_error("not finished");
+        return QSIM_EBUSY;
+    }
+    const int st = r->status;
+    if (st == QSIM_OK) {
+        if (x_out) std::memcpy(x_out, r->x.data(), r->x.size() * sizeof(double));
+        if (stats) *stats = r->stats;
+        clear_last_error();
+    } else {
+        set_last_error(r->err);
+    }
+    if (latency_s) *latency_s = r->t_done - r->t_submit;
+    p->reqs.erase(it);
+    return st;
+}
+
+int qsim_pool_wait(qsim_pool *p, uint64_t ticket, double timeout_s) {
+    if (!p) {
+        set_last_error("NULL pool");
+        return QSIM_EINVAL;
+    }
+    std::unique_lock<std::mutex> lk(p->mu);
+    auto done = [&] {
+        auto it = p->reqs.find(ticket);
+        return it == p->reqs.end() || it->second->status != QSIM_EBUSY;
+    };
+    if (!p->cv_done.wait_for(lk, std::chrono::duration<double>(std::max(0.0, timeout_s)), done)) {
+        set_last_error("timed out waiting for the request");
+        return QSIM_ETIMEOUT;
+    }
+    if (p->reqs.find(ticket) == p->reqs.end()) {
+        set_last_error("unknown ticket");
+        return QSIM_ENOTFOUND;
+    }
+    clear_last_error();
+    return QSIM_OK;
+}
+
+int qsim_pool_get_info(qsim_pool *p, qsim_pool_info *o) {
+    return guarded([&] {
+        QSIM_REQUIRE(p != nullptr && o != nullptr, "NULL argument");
+        std::lock_guard<std::mutex> lk(p->mu);
+        o->bytes_total = p->arena->cap();
+        o->bytes_in_use = p->arena->used();
+        o->bytes_peak = p->arena->peak();
+        o->queued = (int)(p->submitted.size() + p->built.size());
+        o->building = p->n_building;
+        o->running = p->n_running;
+        o->done = p->n_done;
+        o->failed = p->n_failed;
+        o->batches_launched = p->batches;
+        o->singles_launched = p->singles;
+    });
+}
+
+void qsim_pool_destroy(qsim_pool *p) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        p->stop = true;
+        // queued, unbuilt requests are dropped
+        for (PoolReq *r : p->submitted) fail(p, r, QSIM_EINVAL, "pool destroyed");
+        p->submitted.clear();
+        p->cv_work.notify_all();
+    }
+    for (std::thread &t : p->builders) t.join();
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        p->cv_work.notify_all();
+    }
+    if (p->scheduler.joinable()) p->scheduler.join();
+    for (Slot &s : p->slots) {
+        if (s.st) cudaStreamSynchronize(s.st);
+        if (s.ev) cudaEventDestroy(s.ev);
+        if (s.st) cudaStreamDestroy(s.st);
+        if (s.pinned) cudaFreeHost(s.pinned);
+    }
+    p->reqs.clear();
+    if (p->arena_base) cudaFree(p->arena_base);
+    delete p;
+}
+
+}  // extern "C"

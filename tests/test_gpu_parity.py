@@ -384,6 +384,9 @@ def test_full_size_forward_inverse_roundtrip(qs, dtype, n):
         # relative (FP32 dot products of length 2^(k+1); 3xTF32 keeps ~22 bits per product)
         bound = 2 * sum(2.0 ** len(t) for t, _ in gates) * 2.0 ** -22
         assert abs(n1 - n0) / n0 <= bound
-        ov = torch.vdot(x0.to(torch.complex128), st.to(torch.complex128))
-        fid = (ov.abs() ** 2).item() / (n0 ** 2 * n1 ** 2)
+        ov = 0j
+        for s0 in range(0, x0.numel(), 1 << 28):   # torch.vdot takes < 2^31 elements
+            ov += torch.vdot(x0[s0:s0 + (1 << 28)].to(torch.complex128),
+                             st[s0:s0 + (1 << 28)].to(torch.complex128)).item()
+        fid = abs(ov) ** 2 / (n0 ** 2 * n1 ** 2)
         assert fid >= 1 - 1e-6

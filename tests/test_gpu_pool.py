@@ -1,0 +1,121 @@
+"""Serving pool: results alone vs in a mixed, overlapping stream; parity with the oracle;
+memory-budget admission; failures injected on the host (poisoned systems, a request larger
+than the pool, a wait that times out, an unknown ticket).  No test faults or hangs a GPU."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import hhl as ohhl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs(cuda_device):
+    from paper_2402_08136_gb300 import build
+    build.build()
+    import paper_2402_08136_gb300 as q
+    return q
+
+
+def stream_items(count, max_n, seed=11):
+    return [r["problem"] for r in synth.serving_stream(seed=seed, count=count, max_n=max_n)]
+
+
+def run_all(pool, items, dtype):
+    tks = [pool.submit(p["A"], p["b"], p["m"], dtype=dtype) for p in items]
+    out = []
+    for t in tks:
+        pool.wait(t, 120.0)
+        out.append(pool.poll(t))
+    return out
+
+
+@pytest.mark.parametrize("dtype_name", ["c64", "c128"])
+def test_pool_mix_equals_alone_and_oracle(qs, dtype_name):
+    dtype = qs.QSIM_C64 if dtype_name == "c64" else qs.QSIM_C128
+    items = stream_items(40, max_n=17)
+    ns = [p["nb"] + p["m"] + 1 for p in items]
+    assert min(ns) <= 14 < max(ns)            # both batched and full-GPU launches
+    pool = qs.Pool(1 << 30, n_builders=4, n_streams=4)
+    mix = run_all(pool, items, dtype)
+    info = pool.info()
+    assert info["batches_launched"] >= 1 and info["singles_launched"] >= 1
+    alone = []
+    for p in items[:12]:
+        alone += run_all(pool, [p], dtype)
+    pool.close()
+    for a, b in zip(alone, mix[:12]):
+        assert np.max(np.abs(a["x"] - b["x"])) <= 1e-12 * max(1.0, np.max(np.abs(b["x"])))
+        assert abs(a["p_success"] - b["p_success"]) <= 1e-12
+    # FP64 oracle on the smaller requests
+    for p, r in list(zip(items, mix))[:10]:
+        if p["nb"] + p["m"] + 1 > 16:
+            continue
+        ref = ohhl.solve(p["A"], p["b"], p["m"])
+        tol = 1e-5 if dtype_name == "c64" else max(1e-12, 2.0 ** p["m"] * 2 * math.pi * 8 * 2.2e-16)
+        assert abs(r["p_success"] - ref["P"]) <= 10 * tol
+        scale = np.linalg.norm(ref["x"])
+        assert np.linalg.norm(r["x"] - ref["x"]) <= 1e4 * tol * scale / max(math.sqrt(ref["P0"]), 1e-3)
+
+
+def test_pool_memory_budget_admission(qs):
+    # 20-qubit complex64 states are 8 MiB; a 20 MiB arena holds two at a time
+    rng = np.random.default_rng(3)
+    items = []
+    for _ in range(6):
+        A, b = synth.contingency_system(rng, 2 ** 3 + 1)
+        items.append(dict(A=A, b=b, m=16))
+    pool = qs.Pool(20 << 20, n_builders=2, n_streams=4)
+    res = run_all(pool, items, qs.QSIM_C64)
+    info = pool.info()
+    pool.close()
+    assert all(r is not None for r in res)
+    assert info["bytes_peak"] <= 20 << 20 and info["done"] == 6
+
+
+def test_pool_failures_injected_on_host(qs):
+    pool = qs.Pool(16 << 20, n_builders=2, n_streams=2)
+    good = stream_items(3, max_n=12, seed=4)
+    bad_A = np.array([[2.0, 1.0], [0.0, 3.0]])               # not Hermitian
+    nan_b = np.array([1.0, np.nan])
+    tk_good = [pool.submit(p["A"], p["b"], p["m"]) for p in good]
+    tk_bad = [pool.submit(bad_A, [1.0, 0.0], 3), pool.submit(np.eye(2), nan_b, 3)]
+    rng = np.random.default_rng(0)
+    A, b = synth.contingency_system(rng, 5)
+    tk_big = pool.submit(A, b, 20)                            # 23 qubits: 64 MiB > 16 MiB arena
+    with pytest.raises(qs.QsimError) as e:
+        pool.wait(tk_big + 1000, 0.0)
+    assert e.value.code == -6                                  # unknown ticket
+    for t in tk_bad:
+        pool.wait(t, 60.0)
+        with pytest.raises(qs.QsimError) as e:
+            pool.poll(t)
+        assert e.value.code == -1
+    pool.wait(tk_big, 60.0)
+    with pytest.raises(qs.QsimError) as e:
+        pool.poll(tk_big)
+    assert e.value.code == -2
+    for t in tk_good:
+        pool.wait(t, 60.0)
+        assert pool.poll(t) is not None
+    with pytest.raises(qs.QsimError) as e:
+        pool.poll(tk_good[0])                                  # released
+    assert e.value.code == -6
+    pool.close()
+
+
+def test_pool_wait_times_out(qs):
+    pool = qs.Pool(64 << 20, n_builders=1, n_streams=1)
+    rng = np.random.default_rng(1)
+    A, b = synth.contingency_system(rng, 2 ** 4 + 1)
+    t = pool.submit(A, b, 14)
+    with pytest.raises(qs.QsimError) as e:
+        pool.wait(t, 0.0)
+    assert e.value.code == -5
+    pool.wait(t, 60.0)
+    assert pool.poll(t) is not None
+    pool.close()
