@@ -315,20 +315,21 @@ def run_hhl(args, ws, rank, which):
     if which == "hhl7":
         p = synth.hhl7_problem()
         dtypes = [("c128", torch.complex128)]
-        max_k = args.max_k or 4
     else:
         p = synth.hhl27_problem()
         dtypes = [("c64", torch.complex64), ("c128", torch.complex128)]
-        max_k = args.max_k or 4
-    h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"])
+    h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"], structured=args.structured)
     info = h.info()
     n = info["n"]
-    circ = qs.qsim_fuse(h.as_circuit(), max_k)
-    ci = circ.info()
     xt = np.linalg.solve(p["A"], p["b"])
     stream = torch.cuda.current_stream()
     res = {}
     for name, dt in dtypes:
+        # complex64: widest fusion (dense 4..6 run on the tensor cores); complex128: FP64-bound,
+        # narrow fusion keeps the flops per amplitude low
+        max_k = args.max_k or (6 if name == "c64" else 2)
+        circ = qs.qsim_fuse(h.as_circuit(), max_k)
+        ci = circ.info()
         st = torch.empty(1 << n, dtype=dt, device="cuda")
 
         def solve():
@@ -352,7 +353,8 @@ def run_hhl(args, ws, rank, which):
         rel = float(np.linalg.norm(r["x"] - xt) / np.linalg.norm(xt))
         res[name] = {"solves_per_s": ws * reps / dt_s, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                      "p99_ms": 1e3 * float(np.percentile(lat, 99)), "rel_err_vs_classical": rel,
-                     "p_success": r["p_success"], "leakage": r["leakage"]}
+                     "p_success": r["p_success"], "leakage": r["leakage"], "max_k": max_k,
+                     "fused_ops": ci["n_gates"], "algorithmic_gb": ci["bytes_c64" if name == "c64" else "bytes_c128"] / 1e9}
         del st
     main = res[dtypes[0][0]]
     return {
@@ -360,7 +362,7 @@ def run_hhl(args, ws, rank, which):
         "ms_per_step": round(1e3 / main["solves_per_s"], 3), "higher_is_better": True,
         "dtype": dtypes[0][0],
         "config": {"workload": which, "n_qubits": n, "nb": info["nb"], "m": info["m"],
-                   "fused_ops": ci["n_gates"], "unfused_gates": info["n_gates"], "max_k": max_k},
+                   "unfused_gates": info["n_gates"], "structured_qpe": bool(args.structured)},
         "paths": res,
         "gpu_launches": None,
     }
@@ -487,6 +489,124 @@ def run_batched(args, ws, rank):
         "gpu_launches": args.steps,
     }
 
+
+# ----------------------------------------------------------------------- serving workload
+def _oracle_solve_job(job):
+    """(index, A, b, m) -> oracle x (runs in a spawned worker process)."""
+    import sys as _sys
+    if ROOT not in _sys.path:
+        _sys.path.insert(0, ROOT)
+    from oracle import hhl as ohhl
+    i, A, b, m = job
+    r = ohhl.solve(A, b, m)
+    return i, r["x"], r["P"]
+
+
+def run_serving(args, ws, rank):
+    """Poisson stream of HHL contingency solves (serving form): arrivals replayed in real time
+    into the pool; latency = completion - arrival."""
+    import multiprocessing as mp
+    import threading as th
+    import torch
+    import paper_2402_08136_gb300 as qs
+
+    count = args.count or 20000
+    rate = args.rate
+    max_n = args.max_n or 30
+    t0 = time.perf_counter()
+    items = synth.serving_stream(seed=5, count=count, rate=rate, max_n=max_n)
+    t_gen = time.perf_counter() - t0
+    dtype = qs.QSIM_C64
+    arena = int(args.pool_gb * (1 << 30))
+    nproc = os.cpu_count() or 8
+    pool = qs.Pool(arena, n_builders=max(2, nproc - 4), n_streams=8)
+    # warm-up: one request of each path
+    for it in items[:8]:
+        tk = pool.submit(it["problem"]["A"], it["problem"]["b"], it["problem"]["m"], dtype=dtype,
+                         structured=True)
+        pool.wait(tk, 300.0)
+        pool.poll(tk)
+    tickets = [None] * count
+    t_arr = [0.0] * count
+    start = time.perf_counter() + 0.2
+
+    def submitter():
+        for i, it in enumerate(items):
+            due = start + it["arrival"]
+            d = due - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            p = it["problem"]
+            t_arr[i] = time.perf_counter()
+            tickets[i] = pool.submit(p["A"], p["b"], p["m"], dtype=dtype, structured=True)
+
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        thr = th.Thread(target=submitter)
+        thr.start()
+        results = [None] * count
+        pending = set(range(count))
+        t_last = start
+        while pending:
+            progressed = False
+            for i in list(pending):
+                if tickets[i] is None:
+                    continue
+                r = pool.poll(tickets[i])
+                if r is not None:
+                    results[i] = r
+                    pending.discard(i)
+                    t_last = time.perf_counter()
+                    progressed = True
+            if not progressed:
+                time.sleep(0.0005)
+        thr.join()
+    info = pool.info()
+    pool.close()
+    lat = np.array([r["latency_s"] for r in results])
+    span = t_last - start
+    sps = count / span
+    xt_err = []
+    for it, r in zip(items, results):
+        p = it["problem"]
+        xt = np.linalg.solve(p["A"], p["b"])
+        xt_err.append(float(np.linalg.norm(r["x"] - xt) / np.linalg.norm(xt)))
+    # FP64 oracle on a seeded 1% sample (requests of at most 16 qubits; larger sampled requests
+    # are compared with the classical solution only)
+    rng = np.random.default_rng(7)
+    sample = sorted(rng.choice(count, size=max(1, count // 100), replace=False).tolist())
+    jobs = [(i, items[i]["problem"]["A"], items[i]["problem"]["b"], items[i]["problem"]["m"])
+            for i in sample if items[i]["n"] <= 16]
+    t0 = time.perf_counter()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(len(jobs), nproc) or 1) as op:
+        ora = op.map(_oracle_solve_job, jobs)
+    t_ora = time.perf_counter() - t0
+    err_or = [float(np.linalg.norm(results[i]["x"] - x) / max(np.linalg.norm(x), 1e-300))
+              for i, x, _ in ora]
+    dp = [abs(results[i]["p_success"] - P) for i, _, P in ora]
+    ns = np.array([it["n"] for it in items])
+    return {
+        "metric": "HHL solves/s served (Poisson arrivals) with p50/p99 latency",
+        "value": round(sps, 1), "unit": "solves/s", "ms_per_step": round(1e3 * span, 1),
+        "higher_is_better": True, "dtype": "c64",
+        "config": {"workload": "serving: Poisson stream of N-1 contingency HHL solves, qubits "
+                               "log-uniform 8..30 (capped at %d), structured phase estimation, "
+                               "complex64" % max_n,
+                   "requests": count, "rate_per_s": rate, "max_n": max_n,
+                   "arena_gib": args.pool_gb, "stream_gen_s": round(t_gen, 1),
+                   "requests_n_ge_28": int((ns >= 28).sum())},
+        "latency_ms": {"p50": round(1e3 * float(np.percentile(lat, 50)), 3),
+                       "p99": round(1e3 * float(np.percentile(lat, 99)), 3),
+                       "max": round(1e3 * float(lat.max()), 3)},
+        "offered_rate": rate, "achieved_rate": round(sps, 1),
+        "pool": info,
+        "error": {"rel_vs_classical_median": float(np.median(xt_err)),
+                  "rel_vs_oracle_max": float(max(err_or)) if err_or else None,
+                  "p_success_vs_oracle_max": float(max(dp)) if dp else None,
+                  "oracle_sample": len(jobs), "oracle_seconds": round(t_ora, 1)},
+        "clocks": clk.summary(), "gpu_launches": int(info["batches_launched"] + info["singles_launched"]),
+    }
+
 # ---------------------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -495,11 +615,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gates",
-                    choices=["gates", "gates-c128", "hhl7", "hhl27", "batched"])
+                    choices=["gates", "gates-c128", "hhl7", "hhl27", "batched", "serving"])
+    ap.add_argument("--rate", type=float, default=2000.0, help="arrivals per second (serving)")
+    ap.add_argument("--max-n", type=int, default=0, help="cap on qubits per request (serving)")
+    ap.add_argument("--pool-gb", type=float, default=150.0, help="device arena (serving)")
     ap.add_argument("--count", type=int, default=0, help="circuits per batch (batched workload)")
     ap.add_argument("--n", type=int, default=0, help="override qubit count (gates workloads)")
     ap.add_argument("--per-k", type=int, default=200)
     ap.add_argument("--max-k", type=int, default=0)
+    ap.add_argument("--structured", action="store_true", help="diagonalised phase estimation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-from-host-gen", action="store_true")
     args = ap.parse_args()
@@ -538,6 +662,8 @@ def main():
         out = run_gates(args, ws, rank, "c64" if args.workload == "gates" else "c128")
     elif args.workload == "batched":
         out = run_batched(args, ws, rank)
+    elif args.workload == "serving":
+        out = run_serving(args, ws, rank)
     else:
         out = run_hhl(args, ws, rank, args.workload)
     line = {"metric": out.pop("metric"), "value": out.pop("value"), "unit": out.pop("unit"),

@@ -144,7 +144,8 @@ int qsim_device_status(unsigned *flags, int clear);
  *   C: inversion constant; <= 0 picks the largest clock grid value 2 pi k / (t 2^m) not above
  *      lambda_min (at least one grid step); a given C above lambda_min is EINVAL.
  * Steps: normalize b (record ||b||), pad to 2^nb with block-diag(A, lambda_max I) and zeros in
- * b, eigendecompose on the host (complex Jacobi, FP64), and emit: H on each clock qubit,
+ * b, eigendecompose on the host in FP64 (real symmetric A: Householder tridiagonalization and
+ * implicit QR; complex Hermitian A: cyclic Jacobi), and emit: H on each clock qubit,
  * clock j controls U_j = V diag(exp(i lambda t 2^j)) V^H on the data qubits, the inverse QFT
  * (with bit-reversal swaps) on the clock, the uniformly controlled RY with
  * theta_k = 2 asin(min(1, C / (2 pi k / (t 2^m)))) (theta_0 = 0) on the ancilla, then the
@@ -157,6 +158,21 @@ int hhl_build(const double *A, const double *b, int N, int n_clock, double t, do
  * column i is the eigenvector of lambda[i]).  Used when the spectrum is known exactly. */
 int hhl_build_spectral(const double *lambda, const double *V, const double *b, int N,
                        int n_clock, double t, double C, hhl_circuit **out);
+
+/* hhl_build / hhl_build_spectral with options.  flags: 0 or QSIM_HHL_STRUCTURED_QPE.
+ * QSIM_HHL_STRUCTURED_QPE emits the phase estimation in its diagonalised form (the paper's
+ * controlled evolutions, Fig. 5, multiplied out): prod_j C_j-U^(2^j) = (I (x) V)
+ * diag_c(exp(i lambda t c)) (I (x) V^H), where c is the clock value.  The V closing the phase
+ * estimation cancels against the V^H opening its inverse (nothing in between acts on the data
+ * register), so the list becomes H^m, V^H, phase(+), inverse QFT, rotation, QFT, phase(-), V,
+ * H^m: two dense nb-qubit gates and two phase passes instead of 2m controlled dense gates, and
+ * no U^(2^j) products on the host.  The final state equals the unstructured circuit's up to
+ * rounding. */
+#define QSIM_HHL_STRUCTURED_QPE 1
+int hhl_build_ex(const double *A, const double *b, int N, int n_clock, double t, double C, int flags,
+                 hhl_circuit **out);
+int hhl_build_spectral_ex(const double *lambda, const double *V, const double *b, int N, int n_clock,
+                          double t, double C, int flags, hhl_circuit **out);
 
 void hhl_circuit_free(hhl_circuit *h);
 
@@ -259,6 +275,7 @@ typedef struct {
     int n_clock;     /* as hhl_build                                                           */
     double t, C;     /* as hhl_build                                                           */
     int dtype;       /* QSIM_C64 or QSIM_C128 state                                            */
+    int flags;       /* hhl_build_ex flags (0 or QSIM_HHL_STRUCTURED_QPE)                       */
 } hhl_request;
 
 typedef struct {

@@ -48,7 +48,7 @@ class _ReadoutStats(ctypes.Structure):
 class _HHLRequest(ctypes.Structure):
     _fields_ = [("A", ctypes.POINTER(ctypes.c_double)), ("b", ctypes.POINTER(ctypes.c_double)),
                 ("N", ctypes.c_int), ("n_clock", ctypes.c_int), ("t", ctypes.c_double),
-                ("C", ctypes.c_double), ("dtype", ctypes.c_int)]
+                ("C", ctypes.c_double), ("dtype", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
 class _PoolInfo(ctypes.Structure):
@@ -77,6 +77,10 @@ _SIGS = {
                    ctypes.POINTER(_VP)], ctypes.c_int),
     "hhl_build_spectral": ([_DP, _DP, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                             ctypes.c_double, ctypes.POINTER(_VP)], ctypes.c_int),
+    "hhl_build_ex": ([_DP, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                      ctypes.POINTER(_VP)], ctypes.c_int),
+    "hhl_build_spectral_ex": ([_DP, _DP, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
     "hhl_circuit_free": ([_VP], None),
     "hhl_as_circuit": ([_VP], _VP),
     "hhl_get_info": ([_VP, ctypes.POINTER(_HHLInfo)], ctypes.c_int),
@@ -265,18 +269,29 @@ class HHLCircuit:
             self._ptr = None
 
 
-def hhl_build(A, b, n_clock: int = 0, t: float = 0.0, C: float = 0.0) -> HHLCircuit:
+QSIM_HHL_STRUCTURED_QPE = 1
+
+
+def hhl_build(A, b, n_clock: int = 0, t: float = 0.0, C: float = 0.0,
+              structured: bool = False) -> HHLCircuit:
+    """hhl_build (structured=False: the paper's controlled evolutions) or hhl_build_ex with
+    QSIM_HHL_STRUCTURED_QPE (diagonalised phase estimation)."""
     Aa, Ap = _cplx(A)
     ba, bp = _cplx(np.ravel(b))
     N = ba.size
     if Aa.shape != (N, N):
         raise QsimError(-1, "A must be N x N")
     p = _VP()
-    _check(library().hhl_build(Ap, bp, N, int(n_clock), float(t), float(C), ctypes.byref(p)))
+    if structured:
+        _check(library().hhl_build_ex(Ap, bp, N, int(n_clock), float(t), float(C),
+                                      QSIM_HHL_STRUCTURED_QPE, ctypes.byref(p)))
+    else:
+        _check(library().hhl_build(Ap, bp, N, int(n_clock), float(t), float(C), ctypes.byref(p)))
     return HHLCircuit(p)
 
 
-def hhl_build_spectral(lam, V, b, n_clock: int = 0, t: float = 0.0, C: float = 0.0) -> HHLCircuit:
+def hhl_build_spectral(lam, V, b, n_clock: int = 0, t: float = 0.0, C: float = 0.0,
+                       structured: bool = False) -> HHLCircuit:
     la = np.ascontiguousarray(np.asarray(lam, dtype=np.float64))
     Va, Vp = _cplx(V)
     ba, bp = _cplx(np.ravel(b))
@@ -284,8 +299,12 @@ def hhl_build_spectral(lam, V, b, n_clock: int = 0, t: float = 0.0, C: float = 0
     if Va.shape != (N, N) or la.size != N:
         raise QsimError(-1, "shape mismatch")
     p = _VP()
-    _check(library().hhl_build_spectral(la.ctypes.data_as(_DP), Vp, bp, N, int(n_clock),
-                                        float(t), float(C), ctypes.byref(p)))
+    if structured:
+        _check(library().hhl_build_spectral_ex(la.ctypes.data_as(_DP), Vp, bp, N, int(n_clock), float(t),
+                                               float(C), QSIM_HHL_STRUCTURED_QPE, ctypes.byref(p)))
+    else:
+        _check(library().hhl_build_spectral(la.ctypes.data_as(_DP), Vp, bp, N, int(n_clock),
+                                            float(t), float(C), ctypes.byref(p)))
     return HHLCircuit(p)
 
 
@@ -428,10 +447,11 @@ class Pool:
         self._ptr = p
         self._N = {}
 
-    def submit(self, A, b, n_clock=0, t=0.0, C=0.0, dtype=QSIM_C64) -> int:
+    def submit(self, A, b, n_clock=0, t=0.0, C=0.0, dtype=QSIM_C64, structured=False) -> int:
         Aa, Ap = _cplx(A)
         ba, bp = _cplx(np.ravel(b))
-        req = _HHLRequest(Ap, bp, ba.size, int(n_clock), float(t), float(C), int(dtype))
+        req = _HHLRequest(Ap, bp, ba.size, int(n_clock), float(t), float(C), int(dtype),
+                          QSIM_HHL_STRUCTURED_QPE if structured else 0)
         tk = ctypes.c_uint64(0)
         _check(library().qsim_submit(self._ptr, ctypes.byref(req), ctypes.byref(tk)))
         self._N[int(tk.value)] = ba.size

@@ -28,7 +28,7 @@ namespace batch {
 
 constexpr int kThreads = 256;
 
-enum BKind : unsigned char { B_DENSE = 0, B_PHASE = 1, B_DIAG = 2, B_SWAP = 3, B_UCRY = 4 };
+enum BKind : unsigned char { B_DENSE = 0, B_PHASE = 1, B_DIAG = 2, B_SWAP = 3, B_UCRY = 4, B_QPE = 5 };
 
 struct BOp {
     unsigned char kind, k, c0, nreg;  // c0 / nreg: UCRY control register (contiguous)
@@ -36,7 +36,7 @@ struct BOp {
     unsigned fixmask;                 // targets | controls (zero bits inserted when enumerating)
     unsigned cmask;                   // controls that must be 1 (PHASE: all its qubits)
     unsigned data;                    // element offset into the circuit's data
-    unsigned pad;
+    unsigned data2;                   // B_QPE: offset of the second phase table
 };
 
 struct BCirc {
@@ -163,6 +163,17 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
                 y1.y = cs.y * x0.y + cs.x * x1.y;
                 psi[i0] = y0;
                 psi[i0 | tb] = y1;
+            }
+            break;
+        }
+        case B_QPE: {  // data qubits 0..k-1, clock register k..k+nreg-1, split at c0 bits
+            const V *hi = data + op.data2;
+            const unsigned N = 1u << n, dmask = (1u << op.k) - 1u, cm = (1u << op.nreg) - 1u;
+            const unsigned hm = (1u << op.c0) - 1u;
+            for (unsigned i = tid; i < N; i += kThreads) {
+                const unsigned dd = i & dmask, c = (i >> op.k) & cm;
+                const V p = cmulb(d[((c & hm) << op.k) + dd], hi[((c >> op.c0) << op.k) + dd]);
+                psi[i] = cmulb(psi[i], p);
             }
             break;
         }
@@ -354,6 +365,24 @@ bool encode(const Op &op, int dtype, std::vector<unsigned char> &data, BOp &b) {
             for (double th : op.theta) put_v(data, dtype, cd(std::cos(0.5 * th), std::sin(0.5 * th)));
             return true;
         }
+        case OP_QPE_PHASE: {
+            const int nb = (int)op.targets.size(), m = (int)op.controls.size();
+            for (int i = 0; i < nb; i++)
+                if (op.targets[i] != i) return false;
+            for (int j = 0; j < m; j++)
+                if (op.controls[j] != nb + j) return false;
+            std::vector<cd> lo, hi;
+            int h = 0;
+            qpe_phase_tables(op, lo, hi, h);
+            b.kind = batch::B_QPE;
+            b.k = (unsigned char)nb;
+            b.nreg = (unsigned char)m;
+            b.c0 = (unsigned char)h;
+            for (const cd &z : lo) put_v(data, dtype, z);
+            b.data2 = (unsigned)(data.size() / vbytes(dtype));
+            for (const cd &z : hi) put_v(data, dtype, z);
+            return true;
+        }
     }
     return false;
 }
@@ -520,6 +549,12 @@ bool batch_supported(const qsim_circuit *c) {
         if (op.kind == OP_UCRY)
             for (size_t j = 1; j < op.controls.size(); j++)
                 if (op.controls[j] != op.controls[0] + (int)j) return false;
+        if (op.kind == OP_QPE_PHASE) {
+            for (size_t i = 0; i < op.targets.size(); i++)
+                if (op.targets[i] != (int)i) return false;
+            for (size_t j = 0; j < op.controls.size(); j++)
+                if (op.controls[j] != (int)(op.targets.size() + j)) return false;
+        }
     }
     return true;
 }

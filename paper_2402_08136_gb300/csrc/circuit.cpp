@@ -71,12 +71,14 @@ void build_ops(qsim_circuit *c) {
     if (c->ops_ready) return;
     c->ops.clear();
     for (const Gate &g : c->gates) {
-        if (g.kind == GATE_UCRY) {
+        if (g.kind == GATE_UCRY || g.kind == GATE_QPE_PHASE) {
             Op op;
-            op.kind = OP_UCRY;
+            op.kind = g.kind == GATE_UCRY ? OP_UCRY : OP_QPE_PHASE;
             op.targets = g.targets;
             op.controls = g.controls;
             op.theta = g.theta;
+            op.tq = g.tq;
+            op.sign = g.sign;
             c->ops.push_back(std::move(op));
         } else {
             c->ops.push_back(classify_dense(g.targets, g.controls, g.U));
@@ -222,6 +224,20 @@ static qsim_circuit *fuse_impl(const qsim_circuit *in, int max_k) {
     return out.release();
 }
 
+void qpe_phase_tables(const Op &op, std::vector<cd> &lo, std::vector<cd> &hi, int &h) {
+    const int nb = (int)op.targets.size(), m = (int)op.controls.size();
+    const int D = 1 << nb;
+    h = (m + 1) / 2;
+    const size_t nlo = (size_t)1 << h, nhi = (size_t)1 << (m - h);
+    lo.resize(nlo * D);
+    hi.resize(nhi * D);
+    for (size_t c = 0; c < nlo; c++)
+        for (int d = 0; d < D; d++) lo[c * D + d] = std::polar(1.0, op.sign * op.theta[d] * (op.tq * (double)c));
+    const double th = std::ldexp(op.tq, h);  // t 2^h: exact power-of-two scaling
+    for (size_t c = 0; c < nhi; c++)
+        for (int d = 0; d < D; d++) hi[c * D + d] = std::polar(1.0, op.sign * op.theta[d] * (th * (double)c));
+}
+
 void circuit_info(const qsim_circuit *c, qsim_circuit_info *o) {
     std::memset(o, 0, sizeof(*o));
     o->n_qubits = c->n;
@@ -256,6 +272,11 @@ void circuit_info(const qsim_circuit *c, qsim_circuit_info *o) {
                 o->n_ucry++;
                 amps = N;
                 flops = amps * 6.0;
+                break;
+            case OP_QPE_PHASE:
+                o->n_diag++;
+                amps = N;
+                flops = amps * 12.0;
                 break;
         }
         o->bytes_c64 += 2.0 * 8.0 * amps;

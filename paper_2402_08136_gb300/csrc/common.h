@@ -51,14 +51,16 @@ int guarded(F &&f) {
 
 // ---------------------------------------------------------------------------------------
 // Gate list entries (what the user or hhl_build appends).
-enum GateKind { GATE_U = 0, GATE_UCRY = 1 };
+enum GateKind { GATE_U = 0, GATE_UCRY = 1, GATE_QPE_PHASE = 2 };
 
 struct Gate {
     GateKind kind = GATE_U;
     std::vector<int> targets;   // GATE_U: matrix bit b <-> targets[b]; GATE_UCRY: {target}
     std::vector<int> controls;  // must be 1 (GATE_U); register bits (GATE_UCRY)
     std::vector<cd> U;          // GATE_U: 2^k x 2^k row-major
-    std::vector<double> theta;  // GATE_UCRY: 2^|controls|
+    std::vector<double> theta;  // GATE_UCRY: 2^|controls|; GATE_QPE_PHASE: eigenvalues (2^|targets|)
+    double tq = 0.0;            // GATE_QPE_PHASE: evolution time
+    int sign = 1;               // GATE_QPE_PHASE: +1 phase estimation, -1 its inverse
 };
 
 // Executable operation kinds (one device pass each, or a pass group for the tile kernel).
@@ -68,6 +70,7 @@ enum OpKind {
     OP_DIAG = 2,   // multiply by diag entry selected by the targets' bits
     OP_SWAP = 3,   // swap qubits targets[0], targets[1] (where controls are 1)
     OP_UCRY = 4,   // uniformly controlled RY
+    OP_QPE_PHASE = 5,  // psi[i] *= exp(i sign lam[d] t c), d = data bits (targets), c = clock bits
 };
 
 struct Op {
@@ -76,7 +79,9 @@ struct Op {
     std::vector<int> controls;
     std::vector<cd> U;          // OP_DENSE: 2^k x 2^k; OP_DIAG: 2^k diagonal
     cd phase = 1.0;             // OP_PHASE
-    std::vector<double> theta;  // OP_UCRY
+    std::vector<double> theta;  // OP_UCRY angles; OP_QPE_PHASE eigenvalues
+    double tq = 0.0;            // OP_QPE_PHASE
+    int sign = 1;               // OP_QPE_PHASE
     // device offsets (bytes) into the circuit's device blob, per dtype
     size_t dev_off[2] = {0, 0};
     // complex64 dense ops with 4..6 targets: TF32 hi/lo split of the real form (tensor cores)
@@ -152,4 +157,8 @@ void batch_enqueue_results(qsim_batch *b, cudaStream_t st);
 void batch_host_result(const qsim_batch *b, int i, double *x_out, hhl_readout_stats *stats);
 // linalg.cpp
 void hermitian_eig(int N, const std::vector<cd> &A, std::vector<double> &lam, std::vector<cd> &V);
+void symmetric_eig_real(int N, const std::vector<double> &A, std::vector<double> &lam, std::vector<double> &V);
+// host tables of the structured phase-estimation operator: lo[c * D + d] = exp(i s lam_d t c)
+// for c < 2^h, hi[c * D + d] = exp(i s lam_d t c 2^h) for c < 2^(m-h), h = (m + 1) / 2
+void qpe_phase_tables(const Op &op, std::vector<cd> &lo, std::vector<cd> &hi, int &h);
 }  // namespace qsim

@@ -61,7 +61,7 @@ void append_iqft(qsim_circuit &c, const std::vector<int> &q) {
 }
 
 hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const std::vector<cd> &VA,
-                                 const std::vector<cd> &b, int n_clock, double t, double C) {
+                                 const std::vector<cd> &b, int n_clock, double t, double C, int flags) {
     QSIM_REQUIRE(lamA.front() > 0.0, "A must be positive definite (smallest eigenvalue <= 0)");
     std::unique_ptr<hhl_circuit> h(new hhl_circuit());
     h->N = N;
@@ -119,19 +119,37 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
     const int anc = nb + m;
     const size_t qpe_begin = c.gates.size();
     for (int j = 0; j < m; j++) add_u(c, {clock[j]}, {}, hadamard());
-    for (int j = 0; j < m; j++) {
-        // U_j = V diag(exp(i lambda t 2^j)) V^H  (t 2^j scales by a power of two: exact)
-        const double tj = std::ldexp(t, j);
-        std::vector<cd> ph(D);
-        for (int i = 0; i < D; i++) ph[i] = std::polar(1.0, lam[i] * tj);
-        std::vector<cd> U((size_t)D * D, cd(0.0, 0.0));
+    if (flags & QSIM_HHL_STRUCTURED_QPE) {
+        // prod_j C_j-U^(2^j) = (I (x) V) diag_c(exp(i lam t c)) (I (x) V^H); the V that would
+        // follow is cancelled by the V^H of the uncomputation (nothing in between acts on the data)
+        std::vector<cd> VH((size_t)D * D);
         for (int r = 0; r < D; r++)
-            for (int i = 0; i < D; i++) {
-                const cd vr = V[(size_t)r * D + i] * ph[i];
-                for (int s = 0; s < D; s++) U[(size_t)r * D + s] += vr * std::conj(V[(size_t)s * D + i]);
-            }
-        add_u(c, data, {clock[j]}, std::move(U));
+            for (int s2 = 0; s2 < D; s2++) VH[(size_t)r * D + s2] = std::conj(V[(size_t)s2 * D + r]);
+        add_u(c, data, {}, std::move(VH));
+        Gate g;
+        g.kind = GATE_QPE_PHASE;
+        g.targets = data;
+        g.controls = clock;
+        g.theta = lam;
+        g.tq = t;
+        g.sign = 1;
+        c.gates.push_back(std::move(g));
+    } else {
+        for (int j = 0; j < m; j++) {
+            // U_j = V diag(exp(i lambda t 2^j)) V^H  (t 2^j scales by a power of two: exact)
+            const double tj = std::ldexp(t, j);
+            std::vector<cd> ph(D);
+            for (int i = 0; i < D; i++) ph[i] = std::polar(1.0, lam[i] * tj);
+            std::vector<cd> U((size_t)D * D, cd(0.0, 0.0));
+            for (int r = 0; r < D; r++)
+                for (int i = 0; i < D; i++) {
+                    const cd vr = V[(size_t)r * D + i] * ph[i];
+                    for (int s2 = 0; s2 < D; s2++) U[(size_t)r * D + s2] += vr * std::conj(V[(size_t)s2 * D + i]);
+                }
+            add_u(c, data, {clock[j]}, std::move(U));
+        }
     }
+    const size_t iqft_begin = c.gates.size();
     append_iqft(c, clock);
     const size_t qpe_end = c.gates.size();
     // eigenvalue inversion: theta_k = 2 asin(min(1, C / (k step))), theta_0 = 0
@@ -148,9 +166,21 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
         c.gates.push_back(std::move(g));
     }
     // uncompute: inverse of the phase estimation
-    for (size_t i = qpe_end; i-- > qpe_begin;) {
-        const Gate &g = c.gates[i];
-        add_u(c, g.targets, g.controls, adjoint(g.U));
+    if (flags & QSIM_HHL_STRUCTURED_QPE) {
+        for (size_t i = qpe_end; i-- > iqft_begin;) {  // QFT
+            const Gate &g = c.gates[i];
+            add_u(c, g.targets, g.controls, adjoint(g.U));
+        }
+        Gate g = c.gates[qpe_begin + m + 1];  // the phase operator, inverted
+        g.sign = -1;
+        c.gates.push_back(g);
+        add_u(c, data, {}, V);
+        for (int j = 0; j < m; j++) add_u(c, {clock[j]}, {}, hadamard());
+    } else {
+        for (size_t i = qpe_end; i-- > qpe_begin;) {
+            const Gate &g = c.gates[i];
+            add_u(c, g.targets, g.controls, adjoint(g.U));
+        }
     }
     return h.release();
 }
@@ -171,32 +201,51 @@ using namespace qsim;
 
 extern "C" {
 
-int hhl_build(const double *A, const double *b, int N, int n_clock, double t, double C,
-              hhl_circuit **out) {
+int hhl_build_ex(const double *A, const double *b, int N, int n_clock, double t, double C, int flags,
+                 hhl_circuit **out) {
     return guarded([&] {
         QSIM_REQUIRE(A != nullptr && b != nullptr && out != nullptr, "NULL argument");
         QSIM_REQUIRE(N >= 1 && N <= 4096, "N must be in 1..4096");
+        QSIM_REQUIRE((flags & ~QSIM_HHL_STRUCTURED_QPE) == 0, "unknown flags");
         std::vector<cd> Am = read_complex(A, (size_t)N * N), bv = read_complex(b, N);
         double amax = 0.0;
-        for (const cd &z : Am) amax = std::max(amax, std::abs(z));
+        bool real = true;
+        for (const cd &z : Am) {
+            amax = std::max(amax, std::abs(z));
+            real &= z.imag() == 0.0;
+        }
         const double tol = 1e-12 * std::max(1.0, amax);
         for (int r = 0; r < N; r++)
             for (int c = 0; c <= r; c++)
                 QSIM_REQUIRE(std::abs(Am[(size_t)r * N + c] - std::conj(Am[(size_t)c * N + r])) <= tol,
                              "A is not Hermitian");
-        for (int r = 0; r < N; r++) Am[(size_t)r * N + r] = Am[(size_t)r * N + r].real();
         std::vector<double> lam;
         std::vector<cd> V;
-        hermitian_eig(N, Am, lam, V);
-        *out = build_from_spectrum(N, lam, V, bv, n_clock, t, C);
+        if (real) {  // real symmetric: Householder tridiagonalization + implicit QR
+            std::vector<double> Ar((size_t)N * N), Vr;
+            for (int r = 0; r < N; r++)
+                for (int c = 0; c < N; c++)
+                    Ar[(size_t)r * N + c] = 0.5 * (Am[(size_t)r * N + c].real() + Am[(size_t)c * N + r].real());
+            symmetric_eig_real(N, Ar, lam, Vr);
+            V.assign(Vr.begin(), Vr.end());
+        } else {
+            for (int r = 0; r < N; r++) Am[(size_t)r * N + r] = Am[(size_t)r * N + r].real();
+            hermitian_eig(N, Am, lam, V);
+        }
+        *out = build_from_spectrum(N, lam, V, bv, n_clock, t, C, flags);
     });
 }
 
-int hhl_build_spectral(const double *lambda, const double *V, const double *b, int N, int n_clock,
-                       double t, double C, hhl_circuit **out) {
+int hhl_build(const double *A, const double *b, int N, int n_clock, double t, double C, hhl_circuit **out) {
+    return hhl_build_ex(A, b, N, n_clock, t, C, 0, out);
+}
+
+int hhl_build_spectral_ex(const double *lambda, const double *V, const double *b, int N, int n_clock, double t,
+                          double C, int flags, hhl_circuit **out) {
     return guarded([&] {
         QSIM_REQUIRE(lambda != nullptr && V != nullptr && b != nullptr && out != nullptr, "NULL argument");
         QSIM_REQUIRE(N >= 1 && N <= 4096, "N must be in 1..4096");
+        QSIM_REQUIRE((flags & ~QSIM_HHL_STRUCTURED_QPE) == 0, "unknown flags");
         std::vector<double> lam(lambda, lambda + N);
         for (double v : lam) QSIM_REQUIRE(std::isfinite(v), "non-finite eigenvalue");
         std::vector<cd> Vm = read_complex(V, (size_t)N * N), bv = read_complex(b, N);
@@ -209,8 +258,13 @@ int hhl_build_spectral(const double *lambda, const double *V, const double *b, i
             ls[j] = lam[idx[j]];
             for (int r = 0; r < N; r++) Vs[(size_t)r * N + j] = Vm[(size_t)r * N + idx[j]];
         }
-        *out = build_from_spectrum(N, ls, Vs, bv, n_clock, t, C);
+        *out = build_from_spectrum(N, ls, Vs, bv, n_clock, t, C, flags);
     });
+}
+
+int hhl_build_spectral(const double *lambda, const double *V, const double *b, int N, int n_clock, double t,
+                       double C, hhl_circuit **out) {
+    return hhl_build_spectral_ex(lambda, V, b, N, n_clock, t, C, 0, out);
 }
 
 void hhl_circuit_free(hhl_circuit *h) { delete h; }

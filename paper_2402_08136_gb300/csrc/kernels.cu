@@ -411,6 +411,33 @@ __global__ void ucry_kernel(const UcryArgs a) {
     }
 }
 
+// Structured phase estimation: in the data register's eigenbasis, all m controlled evolutions
+// together multiply amplitude (c, d) by exp(i s lam_d t c) (c = clock value, d = data index).
+// The phase is the product of two table entries, lo[(c mod 2^h) D + d] * hi[(c >> h) D + d].
+struct QpeArgs {
+    void *psi;
+    const void *lo, *hi;
+    long long N;
+    int nb, m, h;
+};
+
+template <typename R>
+__global__ void qpe_phase_kernel(const QpeArgs a) {
+    using V = typename C2<R>::T;
+    V *psi = reinterpret_cast<V *>(a.psi);
+    const V *lo = reinterpret_cast<const V *>(a.lo);
+    const V *hi = reinterpret_cast<const V *>(a.hi);
+    const unsigned long long dmask = (1ull << a.nb) - 1ull, cmask = (1ull << a.m) - 1ull;
+    const unsigned long long hmask = (1ull << a.h) - 1ull;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long d = (unsigned long long)i & dmask;
+        const unsigned long long c = ((unsigned long long)i >> a.nb) & cmask;
+        const V p = cmul(lo[((c & hmask) << a.nb) + d], hi[((c >> a.h) << a.nb) + d]);
+        psi[i] = cmul(psi[i], p);
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // HHL state preparation: psi = 0 except the first D amplitudes = b.
 constexpr int kMaxParamB = 256;
@@ -706,6 +733,24 @@ bool tc_enabled() {
     return v == 1;
 }
 
+void run_qpe_phase(void *state, int n, int dtype, const Op &op, const void *lo, const void *hi, cudaStream_t st) {
+    QpeArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = state;
+    a.lo = lo;
+    a.hi = hi;
+    a.N = 1ll << n;
+    a.nb = (int)op.targets.size();
+    a.m = (int)op.controls.size();
+    a.h = (a.m + 1) / 2;
+    for (int i = 0; i < a.nb; i++) QSIM_REQUIRE(op.targets[i] == i, "phase estimation: data qubits must be 0..nb-1");
+    for (int j = 0; j < a.m; j++) QSIM_REQUIRE(op.controls[j] == a.nb + j, "phase estimation: clock qubits must follow the data");
+    const int grid = grid_for(a.N, 256);
+    if (dtype == QSIM_C128) qpe_phase_kernel<double><<<grid, 256, 0, st>>>(a);
+    else qpe_phase_kernel<float><<<grid, 256, 0, st>>>(a);
+    check_launch("qpe_phase_kernel");
+}
+
 }  // namespace
 
 // Pack every op's device data (dense matrices transposed, diagonals, UCRY (cos, sin) tables)
@@ -732,6 +777,14 @@ std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype) {
             for (const cd &z : op.U) put_complex(blob, dtype, z);
         } else if (op.kind == OP_UCRY) {
             for (double th : op.theta) put_complex(blob, dtype, cd(std::cos(0.5 * th), std::sin(0.5 * th)));
+        } else if (op.kind == OP_QPE_PHASE) {
+            std::vector<cd> lo, hi;
+            int h = 0;
+            qpe_phase_tables(op, lo, hi, h);
+            for (const cd &z : lo) put_complex(blob, dtype, z);
+            align_blob(blob);
+            op.dev_off_tc = blob.size();  // second table
+            for (const cd &z : hi) put_complex(blob, dtype, z);
         }
     }
     align_blob(blob);
@@ -795,6 +848,7 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream) {
             case OP_DIAG: run_diag(state, n, dtype, op, dptr, st); break;
             case OP_SWAP: run_swap(state, n, dtype, op, st); break;
             case OP_UCRY: run_ucry(state, n, dtype, op, dptr, st); break;
+            case OP_QPE_PHASE: run_qpe_phase(state, n, dtype, op, dptr, base + op.dev_off_tc, st); break;
         }
     }
 }

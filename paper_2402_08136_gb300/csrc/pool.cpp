@@ -95,7 +95,7 @@ struct Block {
 struct PoolReq {
     uint64_t id = 0;
     std::vector<double> A, b;
-    int N = 0, n_clock = 0, dtype = QSIM_C64;
+    int N = 0, n_clock = 0, dtype = QSIM_C64, flags = 0;
     double t = 0, C = 0;
     double t_submit = 0, t_admit = 0, t_done = 0;
     int status = QSIM_EBUSY;  // EBUSY while pending
@@ -142,7 +142,7 @@ struct qsim_pool {
     std::thread scheduler;
     bool stop = false;
     uint64_t next_id = 1;
-    int small_n = 14, max_batch = 512, k_small = 2, k_large_c64 = 6, k_large_c128 = 2;
+    int small_n = 14, max_batch = 512, k_small = 2, k_large_c64 = 4, k_large_c128 = 2;
     int n_building = 0, n_running = 0, n_done = 0, n_failed = 0;
     long long batches = 0, singles = 0;
 };
@@ -171,7 +171,7 @@ void builder_loop(qsim_pool *p) {
             p->submitted.pop_front();
             p->n_building++;
         }
-        int rc = hhl_build(r->A.data(), r->b.data(), r->N, r->n_clock, r->t, r->C, &r->h);
+        int rc = hhl_build_ex(r->A.data(), r->b.data(), r->N, r->n_clock, r->t, r->C, r->flags, &r->h);
         std::string msg = rc == QSIM_OK ? "" : qsim_last_error();
         if (rc == QSIM_OK) {
             r->n = r->h->n;
@@ -449,6 +449,7 @@ int qsim_submit(qsim_pool *p, const hhl_request *req, uint64_t *ticket) {
         r->t = req->t;
         r->C = req->C;
         r->dtype = req->dtype;
+        r->flags = req->flags;
         r->t_submit = now_s();
         std::lock_guard<std::mutex> lk(p->mu);
         QSIM_REQUIRE(!p->stop, "pool is shutting down");

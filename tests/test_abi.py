@@ -163,3 +163,32 @@ def test_hhl_build_matches_spectral_path(qs):
         assert h1[key] == h2[key]
     for key in ("t", "C", "lambda_min", "lambda_max"):
         assert abs(h1[key] - h2[key]) < 1e-12 * max(1.0, abs(h2[key]))
+
+
+def test_structured_qpe_gate_counts(qs):
+    p = synth.hhl7_problem()
+    m = p["m"]
+    h = qs.hhl_build(p["A"], p["b"], m, p["t"], p["C"], structured=True)
+    iqft = m + m * (m - 1) // 2 + m // 2
+    assert h.info()["n_gates"] == 2 * m + 2 + 2 + 2 * iqft + 1
+    ci = h.as_circuit().info()
+    assert ci["n_ucry"] == 1 and ci["n_dense"] >= 2
+
+
+def test_real_and_complex_eigensolvers_agree(qs):
+    # the same spectrum as a real symmetric and as a complex Hermitian matrix (unitary similarity)
+    rng = np.random.default_rng(21)
+    Q, _ = np.linalg.qr(rng.standard_normal((24, 24)))
+    lam = np.sort(rng.uniform(1.0, 50.0, 24))
+    A = (Q * lam) @ Q.T
+    A = 0.5 * (A + A.T)
+    D = np.diag(np.exp(1j * rng.uniform(0, 6, 24)))
+    Ac = D @ A @ D.conj().T
+    b = rng.standard_normal(24)
+    i1 = qs.hhl_build(A, b, 6).info()
+    i2 = qs.hhl_build(0.5 * (Ac + Ac.conj().T), b, 6).info()
+    for key in ("lambda_min", "lambda_max", "t", "C"):
+        assert abs(i1[key] - lam[0 if key == "lambda_min" else -1]) < 1e-12 * lam[-1] \
+            if key.startswith("lambda") else abs(i1[key] - i2[key]) < 1e-12 * max(1, abs(i2[key]))
+    assert abs(i2["lambda_min"] - lam[0]) < 1e-12 * lam[-1]
+    assert abs(i2["lambda_max"] - lam[-1]) < 1e-12 * lam[-1]

@@ -130,6 +130,26 @@ def test_hhl_batch_matches_oracle(qs, dtype, cuda_device):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_hhl_batch_structured_matches_oracle(qs, dtype, cuda_device):
+    probs = synth.batched_problems(seed=19, count=10)
+    hs = [qs.hhl_build(p["A"], p["b"], p["m"], structured=True) for p in probs]
+    fused = [qs.qsim_fuse(h.as_circuit(), 3) for h in hs]
+    states = [torch.empty(1 << h.info()["n"], dtype=dtype, device="cuda") for h in hs]
+    b = qs.hhl_batch_create(hs, states, fused)
+    b.run()
+    res = b.results()
+    for p, st, r in zip(probs, states, res):
+        ref = ohhl.solve(p["A"], p["b"], p["m"])
+        m = p["m"]
+        tol = max(1e-12, 2.0 ** m * 2 * math.pi * 8 * np.finfo(float).eps) \
+            if dtype == torch.complex128 else TOL[dtype]
+        out = st.cpu().numpy().astype(np.complex128)
+        assert np.max(np.abs(out - ref["psi"])) <= tol
+        assert abs(r["p_success"] - ref["P"]) <= 10 * tol
+
+
+@pytest.mark.gpu
 def test_batch_run_captures_in_cuda_graph(qs, cuda_device):
     probs = synth.batched_problems(seed=10, count=6)
     hs = [qs.hhl_build(p["A"], p["b"], p["m"]) for p in probs]

@@ -257,6 +257,45 @@ def test_hhl7_parity_and_exact_grid(qs, dtype, max_k):
         assert abs(r["leakage"]) < 1e-13
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("max_k", [0, 3, 6])
+def test_hhl7_structured_qpe_parity(qs, dtype, max_k):
+    """Diagonalised phase estimation vs the oracle's controlled-evolution circuit."""
+    p = synth.hhl7_problem()
+    h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"], structured=True)
+    ref = ohhl.solve(p["A"], p["b"], p["m"], p["t"], p["C"])
+    st, r = run_product_hhl(qs, h, dtype, max_k)
+    compare_hhl(st, r, ref, dtype, TOL[dtype])
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_hhl_structured_offgrid_parity(qs, dtype, seed):
+    rng = np.random.default_rng(seed)
+    nb = int(rng.integers(2, 5))
+    m = int(rng.integers(5, 9))
+    A, b = synth.contingency_system(rng, 2 ** nb + 1)
+    h = qs.hhl_build(A, b, m, structured=True)
+    ref = ohhl.solve(A, b, m)
+    st, r = run_product_hhl(qs, h, dtype, 4)
+    tol = cond_tol(m) if dtype == torch.complex128 else TOL[dtype]
+    compare_hhl(st, r, ref, dtype, tol)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_hhl_structured_spectral_large_clock(qs, dtype):
+    rng = np.random.default_rng(21)
+    N, m = 6, 12
+    V = synth.haar_unitary(rng, N)
+    lam = np.sort(rng.uniform(0.5, 9.0, size=N))
+    b = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    t = 2 * math.pi * (2 ** m - 1) / (2 ** m * 9.0)
+    h = qs.hhl_build_spectral(lam, V, b, m, t, 0.4, structured=True)
+    ref = _oracle_spectral(lam, V, b, m, t, 0.4)
+    st, r = run_product_hhl(qs, h, dtype, 4)
+    compare_hhl(st, r, ref, dtype, 1e-12 if dtype == torch.complex128 else TOL[dtype])
+
+
 def cond_tol(m):
     return max(1e-12, 2.0 ** m * 2 * math.pi * 8 * EPS)
 
