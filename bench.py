@@ -609,9 +609,11 @@ def run_serving(args, ws, rank):
                          structured=True)
         pool.wait(tk, 300.0)
         pool.poll(tk)
-    tickets = [None] * count
+    while pool.take_completed(8192, 0.0):   # drop the warm-up tickets from the completion queue
+        pass
     t_arr = [0.0] * count
     start = time.perf_counter() + 0.2
+    index = {}
 
     def submitter():
         for i, it in enumerate(items):
@@ -621,27 +623,22 @@ def run_serving(args, ws, rank):
                 time.sleep(d)
             p = it["problem"]
             t_arr[i] = time.perf_counter()
-            tickets[i] = pool.submit(p["A"], p["b"], p["m"], dtype=dtype, structured=True)
+            tk = pool.submit(p["A"], p["b"], p["m"], dtype=dtype, structured=True)
+            index[tk] = i
 
     with ClockSampler(torch.cuda.current_device()) as clk:
         thr = th.Thread(target=submitter)
         thr.start()
         results = [None] * count
-        pending = set(range(count))
+        left = count
         t_last = start
-        while pending:
-            progressed = False
-            for i in list(pending):
-                if tickets[i] is None:
-                    continue
-                r = pool.poll(tickets[i])
-                if r is not None:
-                    results[i] = r
-                    pending.discard(i)
-                    t_last = time.perf_counter()
-                    progressed = True
-            if not progressed:
-                time.sleep(0.0005)
+        while left:
+            for tk in pool.take_completed(8192, 0.05):   # completion queue: finished tickets only
+                while tk not in index:                     # submit() returned, mapping not yet set
+                    time.sleep(0)
+                results[index[tk]] = pool.poll(tk)
+                left -= 1
+                t_last = time.perf_counter()
         thr.join()
     info = pool.info()
     pool.close()

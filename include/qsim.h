@@ -148,8 +148,9 @@ int qsim_device_status(unsigned *flags, int clear);
  * implicit QR; complex Hermitian A: cyclic Jacobi), and emit: H on each clock qubit,
  * clock j controls U_j = V diag(exp(i lambda t 2^j)) V^H on the data qubits, the inverse QFT
  * (with bit-reversal swaps) on the clock, the uniformly controlled RY with
- * theta_k = 2 asin(min(1, C / (2 pi k / (t 2^m)))) (theta_0 = 0) on the ancilla, then the
- * inverse of the phase estimation.  Errors: EINVAL, ENOMEM. */
+ * theta_k = 2 asin(min(1, C / (2 pi k / (t 2^m)))) (theta_0 = 0) on the ancilla (evaluated on
+ * the device as cos(theta_k/2) = sqrt((1-r)(1+r)), sin(theta_k/2) = r, r = min(1, C/lt_k)),
+ * then the inverse of the phase estimation.  Errors: EINVAL, ENOMEM. */
 int hhl_build(const double *A, const double *b, int N, int n_clock, double t, double C,
               hhl_circuit **out);
 
@@ -288,7 +289,7 @@ typedef struct {
  * n_builders host threads that build and fuse submitted HHL circuits (<= 0: half the host
  * threads) and n_streams CUDA streams (<= 0: 8).  A request is admitted once the arena has
  * room for its state (8 * 2^n bytes for complex64, 16 * 2^n for complex128) and a stream is
- * free.  Requests of at most 14 qubits that the batched executor supports (dense gates of at
+ * free.  Requests of at most 16 qubits that the batched executor supports (dense gates of at
  * most 5 targets) and that are ready together run as one batched launch; the others run alone
  * with the full-GPU kernels; launches on different streams overlap.
  * Results equal those of the same request run alone (each circuit's arithmetic does not
@@ -310,6 +311,13 @@ int qsim_poll(qsim_pool *p, uint64_t ticket, double *x_out, hhl_readout_stats *s
 /* Block until the request is no longer pending or `timeout_s` seconds pass (QSIM_ETIMEOUT).
  * Does not release the ticket.  Errors: ETIMEOUT, ENOTFOUND, EINVAL. */
 int qsim_pool_wait(qsim_pool *p, uint64_t ticket, double timeout_s);
+
+/* Completion queue: wait up to timeout_s for at least one finished request, then move up to
+ * `capacity` tickets of finished (done or failed) requests, oldest first, into `tickets` and
+ * set *count (0 on timeout).  Each finished ticket is handed out once; read it with
+ * qsim_poll.  Errors: EINVAL. */
+int qsim_pool_take_completed(qsim_pool *p, uint64_t *tickets, int capacity, int *count,
+                             double timeout_s);
 
 int qsim_pool_get_info(qsim_pool *p, qsim_pool_info *out);
 

@@ -102,6 +102,8 @@ _SIGS = {
     "qsim_poll": ([_VP, ctypes.c_uint64, _DP, ctypes.POINTER(_ReadoutStats), _DP], ctypes.c_int),
     "qsim_pool_wait": ([_VP, ctypes.c_uint64, ctypes.c_double], ctypes.c_int),
     "qsim_pool_get_info": ([_VP, ctypes.POINTER(_PoolInfo)], ctypes.c_int),
+    "qsim_pool_take_completed": ([_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, _IP, ctypes.c_double],
+                                 ctypes.c_int),
     "qsim_pool_destroy": ([_VP], None),
     "hhl_readout": ([_VP, ctypes.c_int, _VP, _VP, _DP, _DP, ctypes.POINTER(_ReadoutStats)],
                     ctypes.c_int),
@@ -472,6 +474,14 @@ class Pool:
         out["x"] = x
         out["latency_s"] = lat.value
         return out
+
+    def take_completed(self, capacity: int = 4096, timeout_s: float = 0.05) -> list:
+        """Tickets of requests that finished since the last call (each handed out once)."""
+        buf = (ctypes.c_uint64 * capacity)()
+        cnt = ctypes.c_int(0)
+        _check(library().qsim_pool_take_completed(self._ptr, buf, capacity, ctypes.byref(cnt),
+                                                   float(timeout_s)))
+        return [int(buf[i]) for i in range(cnt.value)]
 
     def wait(self, ticket: int, timeout_s: float = 60.0) -> None:
         _check(library().qsim_pool_wait(self._ptr, ctypes.c_uint64(ticket), float(timeout_s)))

@@ -28,7 +28,7 @@ namespace batch {
 
 constexpr int kThreads = 256;
 
-enum BKind : unsigned char { B_DENSE = 0, B_PHASE = 1, B_DIAG = 2, B_SWAP = 3, B_UCRY = 4, B_QPE = 5 };
+enum BKind : unsigned char { B_DENSE = 0, B_PHASE = 1, B_DIAG = 2, B_SWAP = 3, B_UCRY = 4, B_QPE = 5, B_INVERT = 6 };
 
 struct BOp {
     unsigned char kind, k, c0, nreg;  // c0 / nreg: UCRY control register (contiguous)
@@ -161,6 +161,32 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
                 y0.y = cs.x * x0.y - cs.y * x1.y;
                 y1.x = cs.y * x0.x + cs.x * x1.x;
                 y1.y = cs.y * x0.y + cs.x * x1.y;
+                psi[i0] = y0;
+                psi[i0 | tb] = y1;
+            }
+            break;
+        }
+        case B_INVERT: {  // HHL inversion: rotation from Cs / k (data holds (Cs, 0))
+            const unsigned cnt = 1u << (n - 1);
+            const int tq = op.t[0];
+            const unsigned tb = 1u << tq, vmask = (1u << op.nreg) - 1u;
+            using Rr = decltype(V{}.x);
+            const Rr Cs = d[0].x;
+            for (unsigned g = tid; g < cnt; g += kThreads) {
+                const unsigned i0 = ((g >> tq) << (tq + 1)) | (g & (tb - 1u));
+                const unsigned k = (i0 >> op.c0) & vmask;
+                Rr s = 0, c = 1;
+                if (k) {
+                    s = Cs / (Rr)k;
+                    if (s > (Rr)1) s = (Rr)1;
+                    c = sqrt(((Rr)1 - s) * ((Rr)1 + s));
+                }
+                const V x0 = psi[i0], x1 = psi[i0 | tb];
+                V y0, y1;
+                y0.x = c * x0.x - s * x1.x;
+                y0.y = c * x0.y - s * x1.y;
+                y1.x = s * x0.x + c * x1.x;
+                y1.y = s * x0.y + c * x1.y;
                 psi[i0] = y0;
                 psi[i0 | tb] = y1;
             }
@@ -365,6 +391,17 @@ bool encode(const Op &op, int dtype, std::vector<unsigned char> &data, BOp &b) {
             for (double th : op.theta) put_v(data, dtype, cd(std::cos(0.5 * th), std::sin(0.5 * th)));
             return true;
         }
+        case OP_HHL_INVERT: {
+            const int nc = (int)op.controls.size();
+            for (int j = 1; j < nc; j++)
+                if (op.controls[j] != op.controls[0] + j) return false;
+            b.kind = batch::B_INVERT;
+            b.t[0] = (signed char)op.targets[0];
+            b.c0 = (unsigned char)op.controls[0];
+            b.nreg = (unsigned char)nc;
+            put_v(data, dtype, cd(op.tq, 0.0));
+            return true;
+        }
         case OP_QPE_PHASE: {
             const int nb = (int)op.targets.size(), m = (int)op.controls.size();
             for (int i = 0; i < nb; i++)
@@ -546,7 +583,7 @@ bool batch_supported(const qsim_circuit *c) {
     for (const Op &op : c->ops) {
         if (op.kind == OP_DENSE && op.targets.size() > 5) return false;
         if (op.kind == OP_DIAG && op.targets.size() > 8) return false;
-        if (op.kind == OP_UCRY)
+        if (op.kind == OP_UCRY || op.kind == OP_HHL_INVERT)
             for (size_t j = 1; j < op.controls.size(); j++)
                 if (op.controls[j] != op.controls[0] + (int)j) return false;
         if (op.kind == OP_QPE_PHASE) {

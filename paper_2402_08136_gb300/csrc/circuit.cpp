@@ -71,9 +71,9 @@ void build_ops(qsim_circuit *c) {
     if (c->ops_ready) return;
     c->ops.clear();
     for (const Gate &g : c->gates) {
-        if (g.kind == GATE_UCRY || g.kind == GATE_QPE_PHASE) {
+        if (g.kind == GATE_UCRY || g.kind == GATE_QPE_PHASE || g.kind == GATE_HHL_INVERT) {
             Op op;
-            op.kind = g.kind == GATE_UCRY ? OP_UCRY : OP_QPE_PHASE;
+            op.kind = g.kind == GATE_UCRY ? OP_UCRY : (g.kind == GATE_QPE_PHASE ? OP_QPE_PHASE : OP_HHL_INVERT);
             op.targets = g.targets;
             op.controls = g.controls;
             op.theta = g.theta;
@@ -269,6 +269,7 @@ void circuit_info(const qsim_circuit *c, qsim_circuit_info *o) {
                 amps = N * frac_ctrl * 0.5;
                 break;
             case OP_UCRY:
+            case OP_HHL_INVERT:
                 o->n_ucry++;
                 amps = N;
                 flops = amps * 6.0;

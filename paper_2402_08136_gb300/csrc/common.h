@@ -51,7 +51,7 @@ int guarded(F &&f) {
 
 // ---------------------------------------------------------------------------------------
 // Gate list entries (what the user or hhl_build appends).
-enum GateKind { GATE_U = 0, GATE_UCRY = 1, GATE_QPE_PHASE = 2 };
+enum GateKind { GATE_U = 0, GATE_UCRY = 1, GATE_QPE_PHASE = 2, GATE_HHL_INVERT = 3 };
 
 struct Gate {
     GateKind kind = GATE_U;
@@ -59,7 +59,7 @@ struct Gate {
     std::vector<int> controls;  // must be 1 (GATE_U); register bits (GATE_UCRY)
     std::vector<cd> U;          // GATE_U: 2^k x 2^k row-major
     std::vector<double> theta;  // GATE_UCRY: 2^|controls|; GATE_QPE_PHASE: eigenvalues (2^|targets|)
-    double tq = 0.0;            // GATE_QPE_PHASE: evolution time
+    double tq = 0.0;            // GATE_QPE_PHASE: evolution time; GATE_HHL_INVERT: C / grid step
     int sign = 1;               // GATE_QPE_PHASE: +1 phase estimation, -1 its inverse
 };
 
@@ -71,6 +71,7 @@ enum OpKind {
     OP_SWAP = 3,   // swap qubits targets[0], targets[1] (where controls are 1)
     OP_UCRY = 4,   // uniformly controlled RY
     OP_QPE_PHASE = 5,  // psi[i] *= exp(i sign lam[d] t c), d = data bits (targets), c = clock bits
+    OP_HHL_INVERT = 6, // HHL inversion rotation: RY(2 asin(min(1, tq / k))) on the target, k = clock
 };
 
 struct Op {

@@ -152,17 +152,15 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
     const size_t iqft_begin = c.gates.size();
     append_iqft(c, clock);
     const size_t qpe_end = c.gates.size();
-    // eigenvalue inversion: theta_k = 2 asin(min(1, C / (k step))), theta_0 = 0
+    // eigenvalue inversion: theta_k = 2 asin(min(1, C / (k step))), theta_0 = 0.  Emitted as a
+    // uniformly controlled RY whose rotation is computed on the device from C / step (cos and sin
+    // of theta_k / 2 are sqrt((1 - r)(1 + r)) and r), instead of a table of 2^m angles.
     {
         Gate g;
-        g.kind = GATE_UCRY;
+        g.kind = GATE_HHL_INVERT;
         g.targets = {anc};
         g.controls = clock;
-        g.theta.assign((size_t)1 << m, 0.0);
-        for (size_t k = 1; k < g.theta.size(); k++) {
-            const double r = C / ((double)k * step);
-            g.theta[k] = 2.0 * std::asin(std::min(1.0, r));
-        }
+        g.tq = C / step;
         c.gates.push_back(std::move(g));
     }
     // uncompute: inverse of the phase estimation

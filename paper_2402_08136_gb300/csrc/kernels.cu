@@ -438,6 +438,44 @@ __global__ void qpe_phase_kernel(const QpeArgs a) {
     }
 }
 
+// HHL eigenvalue inversion over a contiguous clock register c0..c0+nc-1: for the pair of
+// amplitudes that differ in the ancilla, r = min(1, Cs / k) with k the clock value (r = 0 for
+// k = 0), and (psi0, psi1) <- [[sqrt((1 - r)(1 + r)), -r], [r, sqrt((1 - r)(1 + r))]] (psi0, psi1).
+struct InvertArgs {
+    void *psi;
+    long long count;  // 2^(n-1)
+    double Cs;
+    int target, c0, nc;
+};
+
+template <typename R>
+__global__ void hhl_invert_kernel(const InvertArgs a) {
+    using V = typename C2<R>::T;
+    V *psi = reinterpret_cast<V *>(a.psi);
+    const unsigned long long tb = 1ull << a.target, vmask = (1ull << a.nc) - 1ull;
+    const R Cs = (R)a.Cs;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.count;
+         g += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long i0 = (((unsigned long long)g >> a.target) << (a.target + 1)) |
+                                      ((unsigned long long)g & (tb - 1ull));
+        const unsigned long long k = (i0 >> a.c0) & vmask;
+        R s = 0, c = 1;
+        if (k) {
+            s = Cs / (R)k;
+            if (s > (R)1) s = (R)1;
+            c = sqrt(((R)1 - s) * ((R)1 + s));
+        }
+        const V x0 = psi[i0], x1 = psi[i0 | tb];
+        V y0, y1;
+        y0.x = c * x0.x - s * x1.x;
+        y0.y = c * x0.y - s * x1.y;
+        y1.x = s * x0.x + c * x1.x;
+        y1.y = s * x0.y + c * x1.y;
+        psi[i0] = y0;
+        psi[i0 | tb] = y1;
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // HHL state preparation: psi = 0 except the first D amplitudes = b.
 constexpr int kMaxParamB = 256;
@@ -751,6 +789,22 @@ void run_qpe_phase(void *state, int n, int dtype, const Op &op, const void *lo, 
     check_launch("qpe_phase_kernel");
 }
 
+void run_hhl_invert(void *state, int n, int dtype, const Op &op, cudaStream_t st) {
+    InvertArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = state;
+    a.count = 1ll << (n - 1);
+    a.Cs = op.tq;
+    a.target = op.targets[0];
+    a.nc = (int)op.controls.size();
+    a.c0 = op.controls[0];
+    for (int j = 0; j < a.nc; j++) QSIM_REQUIRE(op.controls[j] == a.c0 + j, "inversion register must be contiguous");
+    const int grid = grid_for(a.count, 256);
+    if (dtype == QSIM_C128) hhl_invert_kernel<double><<<grid, 256, 0, st>>>(a);
+    else hhl_invert_kernel<float><<<grid, 256, 0, st>>>(a);
+    check_launch("hhl_invert_kernel");
+}
+
 }  // namespace
 
 // Pack every op's device data (dense matrices transposed, diagonals, UCRY (cos, sin) tables)
@@ -849,6 +903,7 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream) {
             case OP_SWAP: run_swap(state, n, dtype, op, st); break;
             case OP_UCRY: run_ucry(state, n, dtype, op, dptr, st); break;
             case OP_QPE_PHASE: run_qpe_phase(state, n, dtype, op, dptr, base + op.dev_off_tc, st); break;
+            case OP_HHL_INVERT: run_hhl_invert(state, n, dtype, op, st); break;
         }
     }
 }

@@ -137,13 +137,14 @@ struct qsim_pool {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<qsim::PoolReq *> submitted, built;
+    std::deque<uint64_t> completed;  // tickets finished (ok or failed), not yet handed out
     std::unordered_map<uint64_t, std::unique_ptr<qsim::PoolReq>> reqs;
     std::vector<std::thread> builders;
     std::thread scheduler;
     bool stop = false;
     uint64_t next_id = 1;
-    int small_n = 14, max_batch = 512, k_small = 2, k_large_c64 = 4, k_large_c128 = 2;
-    int n_building = 0, n_running = 0, n_done = 0, n_failed = 0;
+    int small_n = 16, max_batch = 512, k_small = 2, k_large_c64 = 4, k_large_c128 = 2;
+    int n_building = 0, n_running = 0, n_done = 0, n_failed = 0, n_ready = 0;
     long long batches = 0, singles = 0;
 };
 
@@ -157,6 +158,7 @@ void fail(qsim_pool *p, PoolReq *r, int code, const std::string &msg) {
     r->err = msg;
     r->t_done = now_s();
     p->n_failed++;
+    p->completed.push_back(r->id);
 }
 
 void builder_loop(qsim_pool *p) {
@@ -207,14 +209,12 @@ bool take(qsim_pool *p, size_t bytes, std::vector<Block> &into) {
 
 void *addr(qsim_pool *p, const Block &b) { return static_cast<unsigned char *>(p->arena_base) + b.off; }
 
-// Retire a finished slot: results to the requests, memory back to the arena.  Caller holds mu.
-void retire(qsim_pool *p, Slot &s, cudaError_t status) {
-    const double t = now_s();
+// Results of a finished slot into its requests (scheduler thread, no lock: the requests are
+// not visible to pollers until their status is published), memory back to the arena.
+void collect(qsim_pool *p, Slot &s, cudaError_t status) {
     for (size_t i = 0; i < s.reqs.size(); i++) {
         PoolReq *r = s.reqs[i];
-        if (status != cudaSuccess) {
-            fail(p, r, QSIM_ECUDA, std::string("device work failed: ") + cudaGetErrorString(status));
-        } else {
+        if (status == cudaSuccess) {
             r->x.assign(2 * (size_t)r->N, 0.0);
             if (s.batch) {
                 batch_host_result(s.batch, (int)i, r->x.data(), &r->stats);
@@ -243,24 +243,33 @@ void retire(qsim_pool *p, Slot &s, cudaError_t status) {
                 r->stats.norm_x = norm_x;
                 r->stats.norm_b = r->h->norm_b;
             }
-            r->status = QSIM_OK;
-            r->t_done = t;
-            p->n_done++;
         }
         release_blocks(p, r->blocks);
-        p->n_running--;
     }
     if (s.batch) {
         qsim_batch_free(s.batch);  // external tables: no CUDA call
         s.batch = nullptr;
     }
     release_blocks(p, s.blocks);
-    s.reqs.clear();
-    s.busy = false;
 }
 
-// Launch a group of small requests as one batch on slot s.  Caller holds mu; requests already
-// hold their state blocks.
+// Publish finished requests (caller holds mu).
+void publish(qsim_pool *p, std::vector<PoolReq *> &rs, cudaError_t status) {
+    const double t = now_s();
+    for (PoolReq *r : rs) {
+        p->n_running--;
+        if (status != cudaSuccess) {
+            fail(p, r, QSIM_ECUDA, std::string("device work failed: ") + cudaGetErrorString(status));
+        } else {
+            r->status = QSIM_OK;
+            r->t_done = t;
+            p->n_done++;
+            p->completed.push_back(r->id);
+        }
+    }
+}
+
+// Launch a group of small requests as one batch on slot s (scheduler thread, no lock).
 void launch_small(qsim_pool *p, Slot &s, std::vector<PoolReq *> &group) {
     std::vector<const qsim_circuit *> cs;
     std::vector<const hhl_circuit *> hs;
@@ -285,10 +294,9 @@ void launch_small(qsim_pool *p, Slot &s, std::vector<PoolReq *> &group) {
     s.reqs = group;
     s.busy = true;
     s.large = false;
-    p->batches++;
 }
 
-// Launch one large request on slot s (full-GPU kernels).  Caller holds mu.
+// Launch one large request on slot s (full-GPU kernels; scheduler thread, no lock).
 void launch_large(qsim_pool *p, Slot &s, PoolReq *r) {
     const int dtype = r->dtype;
     std::vector<unsigned char> blob = pack_device_blob(r->fused, dtype);
@@ -312,12 +320,14 @@ void launch_large(qsim_pool *p, Slot &s, PoolReq *r) {
     s.reqs = {r};
     s.busy = true;
     s.large = true;
-    p->singles++;
 }
 
+// The scheduler owns the arena, the slots and its `ready` queue; the pool mutex only guards
+// what other threads see (submitted / built queues, ticket map, completion queue, counters),
+// so building plans, packing matrices and launching never block submitters or builders.
 void scheduler_loop(qsim_pool *p) {
     cudaSetDevice(p->device);
-    std::unique_lock<std::mutex> lk(p->mu);
+    std::deque<PoolReq *> ready;
     for (;;) {
         bool progress = false;
         // 1. retire finished launches
@@ -326,27 +336,44 @@ void scheduler_loop(qsim_pool *p) {
             cudaError_t q = cudaEventQuery(s.ev);
             if (q == cudaErrorNotReady) continue;
             if (q != cudaSuccess) cudaGetLastError();
-            retire(p, s, q);
+            collect(p, s, q);
+            {
+                std::lock_guard<std::mutex> lk(p->mu);
+                publish(p, s.reqs, q);
+            }
+            p->cv_done.notify_all();
+            s.reqs.clear();
+            s.busy = false;
             progress = true;
         }
-        if (progress) p->cv_done.notify_all();
-        if (p->stop && p->built.empty() && p->submitted.empty() && p->n_building == 0) {
+        // 2. take newly built requests
+        bool stopping;
+        {
+            std::lock_guard<std::mutex> lk(p->mu);
+            while (!p->built.empty()) {
+                ready.push_back(p->built.front());
+                p->built.pop_front();
+            }
+            p->n_ready = (int)ready.size();
+            stopping = p->stop && p->submitted.empty() && p->n_building == 0;
+        }
+        if (stopping && ready.empty()) {
             bool any = false;
             for (Slot &s : p->slots) any |= s.busy;
             if (!any) return;
         }
-        // 2. admit built requests: states first (memory budget), then launches on free slots
+        // 3. admit: states first (memory budget), then launches on free slots
+        std::vector<std::pair<PoolReq *, std::pair<int, std::string>>> failed;
         for (Slot &s : p->slots) {
-            if (s.busy || p->built.empty()) continue;
+            if (s.busy || ready.empty()) continue;
             std::vector<PoolReq *> group;
             PoolReq *large = nullptr;
-            for (auto it = p->built.begin(); it != p->built.end();) {
+            for (auto it = ready.begin(); it != ready.end();) {
                 PoolReq *r = *it;
                 const size_t need = amp_bytes(r->dtype) << r->n;
                 if (need > p->arena->cap()) {
-                    fail(p, r, QSIM_ENOMEM, "state larger than the pool");
-                    it = p->built.erase(it);
-                    p->cv_done.notify_all();
+                    failed.push_back({r, {QSIM_ENOMEM, "state larger than the pool"}});
+                    it = ready.erase(it);
                     continue;
                 }
                 const bool is_small = r->small;
@@ -362,40 +389,57 @@ void scheduler_loop(qsim_pool *p) {
                 if (!take(p, need, r->blocks)) break;  // memory budget: wait for retirements
                 r->state = addr(p, r->blocks.back());
                 r->t_admit = now_s();
-                p->n_running++;
-                it = p->built.erase(it);
+                it = ready.erase(it);
                 if (is_small) group.push_back(r);
                 else large = r;
                 if (large) break;
             }
+            if (!large && group.empty()) continue;
+            {
+                std::lock_guard<std::mutex> lk(p->mu);
+                p->n_running += large ? 1 : (int)group.size();
+                if (large) p->singles++;
+                else p->batches++;
+            }
             try {
                 if (large) launch_large(p, s, large);
-                else if (!group.empty()) launch_small(p, s, group);
-                else continue;
+                else launch_small(p, s, group);
                 progress = true;
             } catch (const Error &e) {
-                // put the requests back if the arena was too full for the tables, fail otherwise
+                // back to the queue if the arena was too full for the tables, fail otherwise
                 std::vector<PoolReq *> rs = large ? std::vector<PoolReq *>{large} : group;
                 release_blocks(p, s.blocks);
                 if (s.batch) {
                     qsim_batch_free(s.batch);
                     s.batch = nullptr;
                 }
+                {
+                    std::lock_guard<std::mutex> lk(p->mu);
+                    p->n_running -= (int)rs.size();
+                    if (large) p->singles--;
+                    else p->batches--;
+                }
                 for (PoolReq *r : rs) {
                     release_blocks(p, r->blocks);
-                    p->n_running--;
-                    if (e.code == QSIM_EBUSY) p->built.push_front(r);
-                    else {
-                        fail(p, r, e.code, e.what());
-                        p->cv_done.notify_all();
-                    }
+                    if (e.code == QSIM_EBUSY) ready.push_front(r);
+                    else failed.push_back({r, {e.code, e.what()}});
                 }
                 s.busy = false;
                 s.reqs.clear();
                 if (e.code == QSIM_EBUSY) break;
             }
         }
-        if (!progress) p->cv_work.wait_for(lk, std::chrono::microseconds(50));
+        if (!failed.empty()) {
+            {
+                std::lock_guard<std::mutex> lk(p->mu);
+                for (auto &f : failed) fail(p, f.first, f.second.first, f.second.second);
+            }
+            p->cv_done.notify_all();
+        }
+        if (!progress) {
+            std::unique_lock<std::mutex> lk(p->mu);
+            p->cv_work.wait_for(lk, std::chrono::microseconds(50));
+        }
     }
 }
 
@@ -513,6 +557,21 @@ int qsim_pool_wait(qsim_pool *p, uint64_t ticket, double timeout_s) {
     return QSIM_OK;
 }
 
+int qsim_pool_take_completed(qsim_pool *p, uint64_t *tickets, int capacity, int *count, double timeout_s) {
+    return guarded([&] {
+        QSIM_REQUIRE(p != nullptr && tickets != nullptr && count != nullptr && capacity > 0, "bad arguments");
+        std::unique_lock<std::mutex> lk(p->mu);
+        p->cv_done.wait_for(lk, std::chrono::duration<double>(std::max(0.0, timeout_s)),
+                            [&] { return !p->completed.empty(); });
+        int k = 0;
+        while (k < capacity && !p->completed.empty()) {
+            tickets[k++] = p->completed.front();
+            p->completed.pop_front();
+        }
+        *count = k;
+    });
+}
+
 int qsim_pool_get_info(qsim_pool *p, qsim_pool_info *o) {
     return guarded([&] {
         QSIM_REQUIRE(p != nullptr && o != nullptr, "NULL argument");
@@ -520,7 +579,7 @@ int qsim_pool_get_info(qsim_pool *p, qsim_pool_info *o) {
         o->bytes_total = p->arena->cap();
         o->bytes_in_use = p->arena->used();
         o->bytes_peak = p->arena->peak();
-        o->queued = (int)(p->submitted.size() + p->built.size());
+        o->queued = (int)(p->submitted.size() + p->built.size()) + p->n_ready;
         o->building = p->n_building;
         o->running = p->n_running;
         o->done = p->n_done;

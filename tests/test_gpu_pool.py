@@ -119,3 +119,19 @@ def test_pool_wait_times_out(qs):
     pool.wait(t, 60.0)
     assert pool.poll(t) is not None
     pool.close()
+
+
+def test_pool_completion_queue_hands_out_each_ticket_once(qs):
+    pool = qs.Pool(256 << 20, n_builders=2, n_streams=2)
+    items = stream_items(12, max_n=14, seed=21)
+    tks = {pool.submit(p["A"], p["b"], p["m"]) for p in items}
+    seen = []
+    while len(seen) < len(tks):
+        got = pool.take_completed(5, 30.0)
+        assert got, "completion queue timed out"
+        seen += got
+    assert sorted(seen) == sorted(tks)
+    assert pool.take_completed(5, 0.0) == []
+    for t in seen:
+        assert pool.poll(t) is not None
+    pool.close()
