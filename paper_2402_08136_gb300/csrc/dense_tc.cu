@@ -11,11 +11,11 @@
 // which keeps ~22 significant bits per product (Markidis et al., "NVIDIA Tensor Core
 // Programmability, Performance & Precision", 2018, for the split scheme).
 //
-// CTA (persistent, as many per SM as shared and tensor memory allow): 13 warps in three roles
+// CTA (persistent, as many per SM as shared and tensor memory allow): 21 warps in three roles
 // coupled only through mbarriers.  B (hi and lo, host-split, canonical K-major layout) stays in
-// shared memory.  X is produced in chunks of 16 amplitudes (32 K-columns) per group by 8
-// producer warps: every producer thread owns one group row m and half of each chunk, keeps
-// four chunks of loads in flight in registers, splits them into hi/lo, writes them into a ring
+// shared memory.  X is produced in chunks of 16 amplitudes (32 K-columns) per group by 16
+// producer warps: every producer thread owns one group row m and a quarter of each chunk, keeps
+// six chunks of loads in flight in registers, splits them into hi/lo, writes them into a ring
 // of shared-memory chunk buffers and arrives on the buffer's "full" barrier.  One lane of the
 // MMA warp waits for full buffers, issues the 3 x 4 MMAs of a chunk and commits them to the
 // buffer's "empty" barrier (and, after a tile's last chunk, to the accumulator's barrier).  Two
@@ -156,15 +156,16 @@ struct Cfg {
                                       | ((unsigned)(N >> 3) << 17) | ((unsigned)(kM >> 4) << 24);
 };
 
-// Warp roles: warps 0-7 produce (256 threads; thread t owns group row t % 128 and half t / 128
-// of every chunk), warps 8-11 run the epilogue (warp 8+i reads TMEM lanes 32i..32i+31),
-// warp 12 issues the MMAs.  Roles hand chunks and accumulators to each other through
+// Warp roles: warps 0-15 produce (512 threads; thread t owns group row t % 128 and quarter
+// t / 128 of every chunk), warps 16-19 run the epilogue (warp 16+i reads TMEM lanes
+// 32i..32i+31), warp 20 issues the MMAs.  Roles hand chunks and accumulators to each other through
 // mbarriers only, so no role waits for another except for data it needs.
-constexpr int kProducers = 256;
-constexpr int kEpiWarp0 = 8;
-constexpr int kMmaWarp = 12;
-constexpr int kThreadsWS = 13 * 32;
-constexpr int kPrefetch = 4;  // chunks of loads in flight per producer thread
+constexpr int kProducers = 512;
+constexpr int kAmpsPT = 16 * kM / kProducers;  // amplitudes of each chunk per producer thread
+constexpr int kEpiWarp0 = kProducers / 32;
+constexpr int kMmaWarp = kEpiWarp0 + 4;
+constexpr int kThreadsWS = (kMmaWarp + 1) * 32;
+constexpr int kPrefetch = 6;  // chunks of loads in flight per producer thread
 
 template <int K>
 __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
@@ -228,15 +229,15 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
 
     if (warp < kEpiWarp0) {
         // ------------------------------------------------------------------ producers
-        const int m = tid & (kM - 1), h = tid >> 7;
+        const int m = tid & (kM - 1), h = tid >> 7;  // group row, part of the chunk
         const int sw = (m >> 3) & 1;  // rows m and m+8 share banks: swap amplitude pairs
-        float2 r[kPrefetch][8];
-        auto load = [&](long long qq, float2(&rr)[8]) {
+        float2 r[kPrefetch][kAmpsPT];
+        auto load = [&](long long qq, float2(&rr)[kAmpsPT]) {
             if (qq < total) {
                 const unsigned long long gb = group_base(qq / NCH, m);
-                const int c0 = (int)(qq % NCH) * 16 + 8 * h;
+                const int c0 = (int)(qq % NCH) * 16 + kAmpsPT * h;
 #pragma unroll
-                for (int e = 0; e < 8; e++) rr[e] = __ldcs(psi + gb + toff[c0 + e]);
+                for (int e = 0; e < kAmpsPT; e++) rr[e] = __ldcs(psi + gb + toff[c0 + e]);
             }
         };
 #pragma unroll
@@ -255,9 +256,9 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
                 unsigned char *ahi = Aring + b * 2 * C::ABYTES;
                 unsigned char *alo = ahi + C::ABYTES;
 #pragma unroll
-                for (int e = 0; e < 8; e++) {
+                for (int e = 0; e < kAmpsPT; e++) {
                     const float2 x = sw ? r[p][e ^ 1] : r[p][e];
-                    const int k = 16 * h + 2 * (e ^ sw);
+                    const int k = 2 * kAmpsPT * h + 2 * (e ^ sw);
                     const unsigned off = (m >> 3) * 1024 + (k >> 2) * 128 + (m & 7) * 16 + (k & 3) * 4;
                     const unsigned hx = to_tf32(x.x), hy = to_tf32(x.y);
                     const unsigned lx = to_tf32(x.x - __uint_as_float(hx));
