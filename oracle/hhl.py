@@ -10,7 +10,9 @@ Readings of points the paper leaves open (the same list is kept with the design 
     value), the ancilla is qubit nb+m;
   * evolution U = exp(+iAt); clock qubit j controls U^(2^j); an eigenvalue lambda lands on clock
     value k = lambda t 2^m / (2 pi); the inverse QFT includes the final qubit-reversal swaps;
-  * default t = 2 pi (2^m - 1) / (2^m lambda_max) (lambda_max on the top grid value);
+  * default t = 2 pi (2^m - 1) / (2^m lambda_max) (lambda_max on the top grid value); for an
+    indefinite A the clock register is two's complement (its top bit is the sign qubit of
+    Sec. III-B) and t = 2 pi (2^(m-1) - 1) / (2^m max|lambda|);
     grid value of clock k: lt_k = 2 pi k / (t 2^m); default C = the largest grid value not above
     lambda_min (at least one grid step); theta_k = 2 asin(C / lt_k), clamped to pi where
     C / lt_k > 1, and theta_0 = 0;
@@ -82,6 +84,7 @@ def resource_counts(n_rows: int, kappa: float, has_negative: bool):
 
 
 def check_problem(A: np.ndarray, b: np.ndarray):
+    """Shape, finiteness and Hermiticity checks (step 1 takes A Hermitian)."""
     A = np.asarray(A, dtype=np.complex128)
     b = np.asarray(b, dtype=np.complex128).ravel()
     N = A.shape[0]
@@ -98,41 +101,50 @@ def check_problem(A: np.ndarray, b: np.ndarray):
 
 
 def build(A, b, m: int, t: float = 0.0, C: float = 0.0):
-    """Step 1 and 2 of the procedure: normalize b, pad, and emit the unfused HHL gate list."""
+    """Step 1 and 2 of the procedure: normalize b, pad, and emit the unfused HHL gate list.
+
+    A positive definite A uses the clock value k as is.  An indefinite A (Sec. III-B's sign
+    qubit, n_negval = 1) reads the clock register as a two's-complement number: clock value c
+    stands for c - 2^m when c >= 2^(m-1), t maps the largest |lambda| to 2^(m-1) - 1, and the
+    rotation angle takes the sign of the grid value."""
     A, b = check_problem(A, b)
     N = A.shape[0]
     bnorm = float(np.linalg.norm(b))
     bhat = b / bnorm
     nb = max(1, int(math.ceil(math.log2(N))))
     lam_A = np.linalg.eigvalsh(A)
-    if lam_A[0] <= 0:
-        raise ValueError("A must be positive definite")
-    lam_max = float(lam_A[-1])
+    absl = np.abs(lam_A)
+    if absl.min() == 0 or absl.min() <= 1e-14 * absl.max():
+        raise ValueError("A is singular")
+    signed = bool(lam_A[0] < 0)
+    lam_amax, lam_amin = float(absl.max()), float(absl.min())
     D = 1 << nb
     Ap = np.zeros((D, D), dtype=np.complex128)
     Ap[:N, :N] = A
     for i in range(N, D):
-        Ap[i, i] = lam_max
+        Ap[i, i] = lam_amax
     bp = np.zeros(D, dtype=np.complex128)
     bp[:N] = bhat
     lam, V = np.linalg.eigh(Ap)
     if m <= 0:
-        kappa = float(lam_A[-1] / lam_A[0])
-        m = resource_counts(N, kappa, False)[2]
+        m = resource_counts(N, lam_amax / lam_amin, signed)[2]
     M = 1 << m
     if t <= 0:
-        t = 2 * math.pi * (M - 1) / (M * lam_max)
+        top = (M // 2 - 1) if signed else (M - 1)
+        t = 2 * math.pi * top / (M * lam_amax)
     step = 2 * math.pi / (t * M)              # grid value of clock k is k * step
-    lam_min = float(lam[0])
     if C <= 0:
-        C = max(1.0, math.floor(lam_min / step * (1 + 1e-9))) * step
-    elif C > lam_min * (1 + 1e-9):
-        raise ValueError("C above the smallest eigenvalue")
+        C = max(1.0, math.floor(lam_amin / step * (1 + 1e-9))) * step
+    elif C > lam_amin * (1 + 1e-9):
+        raise ValueError("C above the smallest |eigenvalue|")
     k = np.arange(M, dtype=np.float64)
+    if signed:
+        k = np.where(k >= M // 2, k - M, k)   # two's complement clock value
     theta = np.zeros(M)
-    with np.errstate(divide="ignore"):
-        r = np.where(k > 0, C / np.where(k > 0, k * step, 1.0), 0.0)
-    theta[1:] = 2.0 * np.arcsin(np.minimum(r[1:], 1.0))
+    nz = k != 0
+    r = np.zeros(M)
+    r[nz] = C / (k[nz] * step)
+    theta[nz] = 2.0 * np.arcsin(np.clip(r[nz], -1.0, 1.0))
 
     data = list(range(nb))
     clock = [nb + j for j in range(m)]
@@ -150,7 +162,7 @@ def build(A, b, m: int, t: float = 0.0, C: float = 0.0):
     for g in reversed(qpe):
         gates.append(("u", g[1], g[2].conj().T, g[3], g[4]))
     return dict(N=N, nb=nb, m=m, n=nb + m + 1, t=t, C=C, bnorm=bnorm, b_pad=bp, gates=gates,
-                theta=theta, lam=lam)
+                theta=theta, lam=lam, signed=signed)
 
 
 def initial_state(h) -> np.ndarray:

@@ -186,6 +186,43 @@ def test_hhl_exact_grid(m, N, cplx, seed):
     assert abs(r["norm2"] - 1.0) < 1e-12
 
 
+@pytest.mark.parametrize("m,N,cplx,seed", [(4, 3, False, 10), (5, 4, True, 11), (6, 6, False, 12),
+                                           (7, 8, True, 13)])
+def test_hhl_exact_grid_indefinite(m, N, cplx, seed):
+    """Signed eigenvalues: integers in +-[1, 2^(m-1) - 1] with t = 2 pi / 2^m land exactly on the
+    two's-complement clock grid; the slice is then exactly A^-1 b / ||A^-1 b||."""
+    rng = np.random.default_rng(seed)
+    top = 2 ** (m - 1) - 1
+    k = rng.integers(1, top + 1, size=N).astype(float) * rng.choice([-1.0, 1.0], size=N)
+    k[0], k[-1] = -top, top
+    V = synth.haar_unitary(rng, N) if cplx else np.linalg.qr(rng.standard_normal((N, N)))[0]
+    A = (V * k) @ V.conj().T
+    A = 0.5 * (A + A.conj().T)
+    b = rng.standard_normal(N) + (1j * rng.standard_normal(N) if cplx else 0)
+    r = ohhl_solve_signed(A, b, m)
+    bh = b / np.linalg.norm(b)
+    y = np.linalg.solve(A, bh)
+    assert r["circuit"]["signed"]
+    assert np.max(np.abs(r["x_state"][:N] - y / np.linalg.norm(y))) < 1e-12
+    assert abs(r["leakage"]) < 1e-14
+    assert abs(r["norm_x"] - np.linalg.norm(y)) < 1e-12 * np.linalg.norm(y)
+    assert np.max(np.abs(r["x"] - np.linalg.solve(A, b))) < 1e-11 * np.linalg.norm(np.linalg.solve(A, b))
+
+
+def ohhl_solve_signed(A, b, m):
+    return hhl.solve(A, b, m, t=2 * math.pi / 2 ** m)
+
+
+def test_resource_formula_counts_sign_qubit_by_default():
+    rng = np.random.default_rng(3)
+    V = np.linalg.qr(rng.standard_normal((5, 5)))[0]
+    lam = np.array([-9.0, -2.0, 1.5, 4.0, 12.0])
+    A = (V * lam) @ V.T
+    h = hhl.build(0.5 * (A + A.T), rng.standard_normal(5), 0)
+    assert h["signed"]
+    assert h["m"] == max(3 + 1, math.ceil(math.log2(12.0 / 1.5 + 1))) + 1
+
+
 def test_hhl_padding_gives_zero_tail():
     A, b, _, _ = _grid_problem(7, 3, 5)
     r = hhl.solve(A, b, 5, t=2 * math.pi / 32)
