@@ -165,6 +165,40 @@ def build(A, b, m: int, t: float = 0.0, C: float = 0.0):
                 theta=theta, lam=lam, signed=signed)
 
 
+def preprocess(A, b, gauss_seidel: bool = False, dilate: bool = False):
+    """Sec. III-A step 1(a) and 1(c).
+
+    (a) Gauss-Seidel preconditioning: with M the lower triangle of A including the diagonal
+        (the Gauss-Seidel splitting), solve M A' = A and M b' = b; A' is generally not Hermitian.
+    (c) Hermitian dilation: a non-Hermitian A' (or `dilate`) becomes [[0, A'], [A'^H, 0]] with
+        right-hand side [b'; 0]; its solution is [0; x], so x is the lower half.
+    Returns (A_eff, b_eff, x_offset, N)."""
+    A = np.asarray(A, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128).ravel()
+    N = A.shape[0]
+    if gauss_seidel:
+        M = np.tril(A)
+        A = np.linalg.solve(M, A)
+        b = np.linalg.solve(M, b)
+    herm = np.max(np.abs(A - A.conj().T)) <= 1e-12 * max(1.0, float(np.max(np.abs(A))))
+    if dilate or not herm:
+        Z = np.zeros((N, N), dtype=np.complex128)
+        A = np.block([[Z, A], [A.conj().T, Z]])
+        b = np.concatenate([b, np.zeros(N, dtype=np.complex128)])
+        return A, b, N, N
+    return A, b, 0, N
+
+
+def solve_general(A, b, m: int, t: float = 0.0, C: float = 0.0, gauss_seidel: bool = False,
+                  dilate: bool = False):
+    """HHL with the optional preprocessing of Sec. III-A step 1; x is mapped back to A x = b."""
+    Ae, be, off, N = preprocess(A, b, gauss_seidel, dilate)
+    r = solve(Ae, be, m, t, C)
+    r["x_eff"] = r["x"]
+    r["x"] = r["x"][off: off + N]
+    return r
+
+
 def initial_state(h) -> np.ndarray:
     """|0>_anc |0>_clock |b>: the normalized, padded b in the lowest 2^nb amplitudes."""
     psi = np.zeros(1 << h["n"], dtype=np.complex128)

@@ -223,6 +223,46 @@ def test_resource_formula_counts_sign_qubit_by_default():
     assert h["m"] == max(3 + 1, math.ceil(math.log2(12.0 / 1.5 + 1))) + 1
 
 
+def test_dilation_exact_grid():
+    """Non-Hermitian A' = U diag(sigma) W^H with integer singular values: the dilation has
+    eigenvalues +-sigma, exactly on the signed clock grid, and HHL returns A'^-1 b exactly."""
+    rng = np.random.default_rng(31)
+    N, m = 3, 6
+    U, W = synth.haar_unitary(rng, N), synth.haar_unitary(rng, N)
+    sig = np.array([2.0, 5.0, 31.0])
+    A = (U * sig) @ W.conj().T
+    b = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    r = hhl.solve_general(A, b, m, t=2 * math.pi / 2 ** m)
+    xt = np.linalg.solve(A, b)
+    assert r["circuit"]["signed"] and r["circuit"]["N"] == 2 * N
+    assert np.max(np.abs(r["x"] - xt)) < 1e-11 * np.linalg.norm(xt)
+    assert np.max(np.abs(r["x_eff"][:N])) < 1e-12 * np.linalg.norm(xt)   # y = 0
+    assert abs(r["leakage"]) < 1e-14
+
+
+def test_gauss_seidel_on_lower_triangular_is_identity():
+    """For a lower-triangular A the Gauss-Seidel splitting is A itself: A' = I, b' = A^-1 b,
+    and the (dilated, signed) HHL solve is exact with eigenvalues +-1."""
+    rng = np.random.default_rng(32)
+    N = 4
+    A = np.tril(rng.standard_normal((N, N))) + 4 * np.eye(N)
+    b = rng.standard_normal(N)
+    Ae, be, off, _ = hhl.preprocess(A, b, gauss_seidel=True)
+    assert off == 0 and np.max(np.abs(Ae - np.eye(N))) < 1e-14          # Hermitian: no dilation
+    r = hhl.solve_general(A, b, 3, t=2 * math.pi / 8, gauss_seidel=True, dilate=True)
+    assert np.max(np.abs(r["x"] - np.linalg.solve(A, b))) < 1e-12 * np.linalg.norm(np.linalg.solve(A, b))
+
+
+def test_dilated_resources_match_table1_30bus_star():
+    """Table I, 30-bus*: a preconditioned (non-Hermitian) 29 x 29 system is dilated to 58 rows,
+    n_data = 6."""
+    rng = np.random.default_rng(33)
+    A, b, _ = synth.grid_system(rng, 30)
+    Ae, be, off, N = hhl.preprocess(A, b, gauss_seidel=True)
+    assert Ae.shape == (58, 58) and off == 29 and N == 29
+    assert hhl.resource_counts(Ae.shape[0], 109.3, True)[1] == 6
+
+
 def test_hhl_padding_gives_zero_tail():
     A, b, _, _ = _grid_problem(7, 3, 5)
     r = hhl.solve(A, b, 5, t=2 * math.pi / 32)
