@@ -136,20 +136,24 @@ int qsim_device_status(unsigned *flags, int clear);
  * ======================================================================================= */
 
 /* Build the HHL circuit for A x = b.
- *   A: N x N complex (interleaved, row-major), Hermitian to 1e-12 * max|A_ij| and positive
- *      definite; b: N complex (not necessarily normalized, nonzero).
+ *   A: N x N complex (interleaved, row-major), Hermitian to 1e-12 * max|A_ij|, nonsingular;
+ *      b: N complex (not necessarily normalized, nonzero).  An indefinite A (a negative
+ *      eigenvalue) reads the clock register as two's complement: its top bit is the sign qubit
+ *      n_negval of Sec. III-B.
  *   n_clock: clock qubits m (1..26); <= 0 uses the Sec. III-B formula
- *            max(n_data + 1, ceil(log2(kappa + 1))).
- *   t: evolution time; <= 0 picks t = 2 pi (2^m - 1) / (2^m lambda_max).
+ *            max(n_data + 1, ceil(log2(kappa + 1))) (+1 sign qubit for an indefinite A).
+ *   t: evolution time; <= 0 picks t = 2 pi (2^m - 1) / (2^m lambda_max), or
+ *      2 pi (2^(m-1) - 1) / (2^m max|lambda|) for an indefinite A.
  *   C: inversion constant; <= 0 picks the largest clock grid value 2 pi k / (t 2^m) not above
- *      lambda_min (at least one grid step); a given C above lambda_min is EINVAL.
+ *      min|lambda| (at least one grid step); a given C above min|lambda| is EINVAL.
  * Steps: normalize b (record ||b||), pad to 2^nb with block-diag(A, lambda_max I) and zeros in
  * b, eigendecompose on the host in FP64 (real symmetric A: Householder tridiagonalization and
  * implicit QR; complex Hermitian A: cyclic Jacobi), and emit: H on each clock qubit,
  * clock j controls U_j = V diag(exp(i lambda t 2^j)) V^H on the data qubits, the inverse QFT
  * (with bit-reversal swaps) on the clock, the uniformly controlled RY with
- * theta_k = 2 asin(min(1, C / (2 pi k / (t 2^m)))) (theta_0 = 0) on the ancilla (evaluated on
- * the device as cos(theta_k/2) = sqrt((1-r)(1+r)), sin(theta_k/2) = r, r = min(1, C/lt_k)),
+ * theta_k = 2 asin(clamp(C / (2 pi k / (t 2^m)), -1, 1)) (theta_0 = 0; k signed for an
+ * indefinite A) on the ancilla (evaluated on the device as sin(theta_k/2) = r,
+ * cos(theta_k/2) = sqrt((1-|r|)(1+|r|)), r = clamp(C/lt_k, -1, 1)),
  * then the inverse of the phase estimation.  Errors: EINVAL, ENOMEM. */
 int hhl_build(const double *A, const double *b, int N, int n_clock, double t, double C,
               hhl_circuit **out);
@@ -160,7 +164,8 @@ int hhl_build(const double *A, const double *b, int N, int n_clock, double t, do
 int hhl_build_spectral(const double *lambda, const double *V, const double *b, int N,
                        int n_clock, double t, double C, hhl_circuit **out);
 
-/* hhl_build / hhl_build_spectral with options.  flags: 0 or QSIM_HHL_STRUCTURED_QPE.
+/* hhl_build / hhl_build_spectral with options.  flags: any of QSIM_HHL_STRUCTURED_QPE,
+ * QSIM_HHL_GAUSS_SEIDEL, QSIM_HHL_DILATE (the last two for hhl_build_ex only).
  * QSIM_HHL_STRUCTURED_QPE emits the phase estimation in its diagonalised form (the paper's
  * controlled evolutions, Fig. 5, multiplied out): prod_j C_j-U^(2^j) = (I (x) V)
  * diag_c(exp(i lambda t c)) (I (x) V^H), where c is the clock value.  The V closing the phase
@@ -170,6 +175,15 @@ int hhl_build_spectral(const double *lambda, const double *V, const double *b, i
  * no U^(2^j) products on the host.  The final state equals the unstructured circuit's up to
  * rounding. */
 #define QSIM_HHL_STRUCTURED_QPE 1
+/* Sec. III-A step 1(a): precondition with the Gauss-Seidel splitting M = lower triangle of A
+ * (with the diagonal): A' = M^-1 A, b' = M^-1 b.  A' is generally not Hermitian, so the
+ * dilation below follows automatically. */
+#define QSIM_HHL_GAUSS_SEIDEL 2
+/* Sec. III-A step 1(c): solve the Hermitian dilation [[0, A], [A^H, 0]] [y; x] = [b; 0]
+ * (2N x 2N, eigenvalues +-sigma_i(A), sign qubit) and return x, the lower half; also accepts
+ * a non-Hermitian A.  Readouts then return the N entries of x (x_state_out keeps the whole
+ * dilated slice). */
+#define QSIM_HHL_DILATE 4
 int hhl_build_ex(const double *A, const double *b, int N, int n_clock, double t, double C, int flags,
                  hhl_circuit **out);
 int hhl_build_spectral_ex(const double *lambda, const double *V, const double *b, int N, int n_clock,
@@ -187,6 +201,8 @@ typedef struct {
     double lambda_min, lambda_max;
     int n_total_formula; /* Sec. III-B count (data + QPE + sign + ancilla) for this A           */
     int n_gates;         /* unfused gate count                                                */
+    int N_eff;           /* size of the system actually solved (2N after the dilation)         */
+    int flags;           /* hhl_build_ex flags                                                 */
 } hhl_info;
 
 int hhl_get_info(const hhl_circuit *h, hhl_info *out);

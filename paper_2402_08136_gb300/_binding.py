@@ -36,7 +36,8 @@ class _HHLInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("nb", ctypes.c_int), ("m", ctypes.c_int), ("n", ctypes.c_int),
                 ("t", ctypes.c_double), ("C", ctypes.c_double), ("norm_b", ctypes.c_double),
                 ("lambda_min", ctypes.c_double), ("lambda_max", ctypes.c_double),
-                ("n_total_formula", ctypes.c_int), ("n_gates", ctypes.c_int)]
+                ("n_total_formula", ctypes.c_int), ("n_gates", ctypes.c_int), ("N_eff", ctypes.c_int),
+                ("flags", ctypes.c_int)]
 
 
 class _ReadoutStats(ctypes.Structure):
@@ -272,21 +273,24 @@ class HHLCircuit:
 
 
 QSIM_HHL_STRUCTURED_QPE = 1
+QSIM_HHL_GAUSS_SEIDEL = 2
+QSIM_HHL_DILATE = 4
 
 
 def hhl_build(A, b, n_clock: int = 0, t: float = 0.0, C: float = 0.0,
-              structured: bool = False) -> HHLCircuit:
-    """hhl_build (structured=False: the paper's controlled evolutions) or hhl_build_ex with
-    QSIM_HHL_STRUCTURED_QPE (diagonalised phase estimation)."""
+              structured: bool = False, gauss_seidel: bool = False, dilate: bool = False) -> HHLCircuit:
+    """hhl_build (no options: the paper's controlled evolutions) or hhl_build_ex with the
+    options (structured phase estimation, Gauss-Seidel preconditioning, Hermitian dilation)."""
     Aa, Ap = _cplx(A)
     ba, bp = _cplx(np.ravel(b))
     N = ba.size
     if Aa.shape != (N, N):
         raise QsimError(-1, "A must be N x N")
     p = _VP()
-    if structured:
-        _check(library().hhl_build_ex(Ap, bp, N, int(n_clock), float(t), float(C),
-                                      QSIM_HHL_STRUCTURED_QPE, ctypes.byref(p)))
+    flags = ((QSIM_HHL_STRUCTURED_QPE if structured else 0) | (QSIM_HHL_GAUSS_SEIDEL if gauss_seidel else 0)
+             | (QSIM_HHL_DILATE if dilate else 0))
+    if flags:
+        _check(library().hhl_build_ex(Ap, bp, N, int(n_clock), float(t), float(C), flags, ctypes.byref(p)))
     else:
         _check(library().hhl_build(Ap, bp, N, int(n_clock), float(t), float(C), ctypes.byref(p)))
     return HHLCircuit(p)

@@ -166,7 +166,8 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
             }
             break;
         }
-        case B_INVERT: {  // HHL inversion: rotation from Cs / k (data holds (Cs, 0))
+        case B_INVERT: {  // HHL inversion: rotation from Cs / k (data holds (Cs, 0); op.k = 1:
+                          // two's-complement clock register)
             const unsigned cnt = 1u << (n - 1);
             const int tq = op.t[0];
             const unsigned tb = 1u << tq, vmask = (1u << op.nreg) - 1u;
@@ -177,9 +178,12 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
                 const unsigned k = (i0 >> op.c0) & vmask;
                 Rr s = 0, c = 1;
                 if (k) {
-                    s = Cs / (Rr)k;
+                    const int ks = (op.k && (k >> (op.nreg - 1))) ? (int)k - (1 << op.nreg) : (int)k;
+                    s = Cs / (Rr)ks;
                     if (s > (Rr)1) s = (Rr)1;
-                    c = sqrt(((Rr)1 - s) * ((Rr)1 + s));
+                    if (s < (Rr)-1) s = (Rr)-1;
+                    const Rr as = s < 0 ? -s : s;
+                    c = sqrt(((Rr)1 - as) * ((Rr)1 + as));
                 }
                 const V x0 = psi[i0], x1 = psi[i0 | tb];
                 V y0, y1;
@@ -301,7 +305,7 @@ struct qsim_batch {
     size_t results_doubles = 0;
     double *h_results = nullptr;  // pinned mirror
     struct Meta {
-        int N = 0, nb = 0;
+        int N = 0, nb = 0, x_off = 0;
         double C = 1, norm_b = 1;
         size_t roff = 0;
     };
@@ -396,6 +400,7 @@ bool encode(const Op &op, int dtype, std::vector<unsigned char> &data, BOp &b) {
             for (int j = 1; j < nc; j++)
                 if (op.controls[j] != op.controls[0] + j) return false;
             b.kind = batch::B_INVERT;
+            b.k = op.sign == -1 ? 1 : 0;
             b.t[0] = (signed char)op.targets[0];
             b.c0 = (unsigned char)op.controls[0];
             b.nreg = (unsigned char)nc;
@@ -487,6 +492,7 @@ BatchImage batch_image(const std::vector<const qsim_circuit *> &cs, const std::v
             bc.b_off = (unsigned)(local.size() / vbytes(dtype));
             for (const cd &z : h->b_pad) put_v(local, dtype, z);
             im.meta[i].N = h->N;
+            im.meta[i].x_off = h->x_off;
             im.meta[i].nb = h->nb;
             im.meta[i].C = h->C;
             im.meta[i].norm_b = h->norm_b;
@@ -663,8 +669,8 @@ void batch_host_result(const qsim_batch *b, int i, double *x_out, hhl_readout_st
     const double norm_x = std::sqrt(P) / m.C;
     if (x_out)
         for (int j = 0; j < m.N; j++) {
-            x_out[2 * j] = r[4 + 2 * j] * inv * norm_x * m.norm_b;
-            x_out[2 * j + 1] = r[4 + 2 * j + 1] * inv * norm_x * m.norm_b;
+            x_out[2 * j] = r[4 + 2 * (m.x_off + j)] * inv * norm_x * m.norm_b;
+            x_out[2 * j + 1] = r[4 + 2 * (m.x_off + j) + 1] * inv * norm_x * m.norm_b;
         }
     if (stats) {
         stats->p_success = P;
@@ -733,8 +739,8 @@ int hhl_batch_results(qsim_batch *b, void *stream, double *x_out, hhl_readout_st
             const double norm_x = std::sqrt(P) / m.C;
             if (x_out)
                 for (int j = 0; j < m.N; j++) {
-                    x_out[2 * (xo + j)] = r[4 + 2 * j] * inv * norm_x * m.norm_b;
-                    x_out[2 * (xo + j) + 1] = r[4 + 2 * j + 1] * inv * norm_x * m.norm_b;
+                    x_out[2 * (xo + j)] = r[4 + 2 * (m.x_off + j)] * inv * norm_x * m.norm_b;
+                    x_out[2 * (xo + j) + 1] = r[4 + 2 * (m.x_off + j) + 1] * inv * norm_x * m.norm_b;
                 }
             xo += m.N;
             if (stats) {

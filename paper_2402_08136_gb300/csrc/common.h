@@ -60,7 +60,8 @@ struct Gate {
     std::vector<cd> U;          // GATE_U: 2^k x 2^k row-major
     std::vector<double> theta;  // GATE_UCRY: 2^|controls|; GATE_QPE_PHASE: eigenvalues (2^|targets|)
     double tq = 0.0;            // GATE_QPE_PHASE: evolution time; GATE_HHL_INVERT: C / grid step
-    int sign = 1;               // GATE_QPE_PHASE: +1 phase estimation, -1 its inverse
+    int sign = 1;               // GATE_QPE_PHASE: +1 phase estimation, -1 its inverse;
+                                // GATE_HHL_INVERT: 1 unsigned, -1 two's-complement clock
 };
 
 // Executable operation kinds (one device pass each, or a pass group for the tile kernel).
@@ -71,7 +72,8 @@ enum OpKind {
     OP_SWAP = 3,   // swap qubits targets[0], targets[1] (where controls are 1)
     OP_UCRY = 4,   // uniformly controlled RY
     OP_QPE_PHASE = 5,  // psi[i] *= exp(i sign lam[d] t c), d = data bits (targets), c = clock bits
-    OP_HHL_INVERT = 6, // HHL inversion rotation: RY(2 asin(min(1, tq / k))) on the target, k = clock
+    OP_HHL_INVERT = 6, // HHL inversion rotation: RY(2 asin(clamp(tq / k, -1, 1))) on the target,
+                       // k = clock value (two's complement when sign == -1)
 };
 
 struct Op {
@@ -112,6 +114,7 @@ struct qsim_circuit {
 
 struct hhl_circuit {
     int N = 0, nb = 0, m = 0, n = 0;
+    int N_eff = 0, x_off = 0, flags = 0;  // system actually solved (dilated: 2N, x at offset N)
     double t = 0, C = 0, norm_b = 0, lam_min = 0, lam_max = 0;
     int n_total_formula = 0;
     std::vector<qsim::cd> b_pad;  // normalized, padded to 2^nb

@@ -62,7 +62,15 @@ void append_iqft(qsim_circuit &c, const std::vector<int> &q) {
 
 hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const std::vector<cd> &VA,
                                  const std::vector<cd> &b, int n_clock, double t, double C, int flags) {
-    QSIM_REQUIRE(lamA.front() > 0.0, "A must be positive definite (smallest eigenvalue <= 0)");
+    double amax = 0.0, amin = 1e300;
+    for (double l : lamA) {
+        amax = std::max(amax, std::fabs(l));
+        amin = std::min(amin, std::fabs(l));
+    }
+    QSIM_REQUIRE(amin > 1e-14 * amax && amin > 0.0, "A is singular");
+    // an indefinite A reads the clock register as two's complement: its top bit is the sign
+    // qubit n_negval of Sec. III-B
+    const bool is_signed = lamA.front() < 0.0;
     std::unique_ptr<hhl_circuit> h(new hhl_circuit());
     h->N = N;
     // step 1: normalize b
@@ -70,7 +78,7 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
     for (const cd &z : b) nb2 += std::norm(z);
     QSIM_REQUIRE(nb2 > 0.0, "b must be nonzero");
     h->norm_b = std::sqrt(nb2);
-    // step 1(b): pad to a power of two with block-diag(A, lambda_max I)
+    // step 1(b): pad to a power of two with block-diag(A, max|lambda| I)
     int nb = 1;
     while ((1 << nb) < N) nb++;
     const int D = 1 << nb;
@@ -84,28 +92,29 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
         for (int r = 0; r < N; r++) V[(size_t)r * D + i] = VA[(size_t)r * N + i];
     }
     for (int i = N; i < D; i++) {
-        lam[i] = h->lam_max;
+        lam[i] = amax;
         V[(size_t)i * D + i] = 1.0;
     }
     h->b_pad.assign(D, cd(0.0, 0.0));
     for (int i = 0; i < N; i++) h->b_pad[i] = b[i] / h->norm_b;
     // Sec. III-B resources
-    const double kappa = h->lam_max / h->lam_min;
-    const int n_data = nb;
-    h->n_total_formula = n_data + qpe_formula(n_data, kappa) + 0 /* no negative eigenvalues */ + 1;
-    const int m = n_clock > 0 ? n_clock : qpe_formula(n_data, kappa);
+    const double kappa = amax / amin;
+    const int n_data = nb, n_neg = is_signed ? 1 : 0;
+    h->n_total_formula = n_data + qpe_formula(n_data, kappa) + n_neg + 1;
+    const int m = n_clock > 0 ? n_clock : qpe_formula(n_data, kappa) + n_neg;
     QSIM_REQUIRE(m >= 1 && m <= 26, "clock qubit count must be in 1..26");
+    QSIM_REQUIRE(!is_signed || m >= 2, "an indefinite A needs at least 2 clock qubits");
     QSIM_REQUIRE(nb + m + 1 <= 34, "more than 34 qubits");
     h->m = m;
     h->n = nb + m + 1;
     const double M = std::ldexp(1.0, m);
-    if (!(t > 0.0)) t = 2.0 * kPi * (M - 1.0) / (M * h->lam_max);
+    if (!(t > 0.0)) t = 2.0 * kPi * ((is_signed ? M / 2 : M) - 1.0) / (M * amax);
     h->t = t;
     const double step = 2.0 * kPi / (t * M);  // grid value of clock value k is k * step
     if (!(C > 0.0)) {
-        C = std::max(1.0, std::floor(h->lam_min / step * (1.0 + 1e-9))) * step;
+        C = std::max(1.0, std::floor(amin / step * (1.0 + 1e-9))) * step;
     } else {
-        QSIM_REQUIRE(C <= h->lam_min * (1.0 + 1e-9), "C above the smallest eigenvalue");
+        QSIM_REQUIRE(C <= amin * (1.0 + 1e-9), "C above the smallest |eigenvalue|");
     }
     h->C = C;
     QSIM_REQUIRE(std::isfinite(t) && std::isfinite(C), "non-finite t or C");
@@ -161,6 +170,7 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
         g.targets = {anc};
         g.controls = clock;
         g.tq = C / step;
+        g.sign = is_signed ? -1 : 1;  // -1: two's-complement clock register
         c.gates.push_back(std::move(g));
     }
     // uncompute: inverse of the phase estimation
@@ -204,33 +214,76 @@ int hhl_build_ex(const double *A, const double *b, int N, int n_clock, double t,
     return guarded([&] {
         QSIM_REQUIRE(A != nullptr && b != nullptr && out != nullptr, "NULL argument");
         QSIM_REQUIRE(N >= 1 && N <= 4096, "N must be in 1..4096");
-        QSIM_REQUIRE((flags & ~QSIM_HHL_STRUCTURED_QPE) == 0, "unknown flags");
+        QSIM_REQUIRE((flags & ~(QSIM_HHL_STRUCTURED_QPE | QSIM_HHL_GAUSS_SEIDEL | QSIM_HHL_DILATE)) == 0,
+                     "unknown flags");
         std::vector<cd> Am = read_complex(A, (size_t)N * N), bv = read_complex(b, N);
-        double amax = 0.0;
-        bool real = true;
-        for (const cd &z : Am) {
-            amax = std::max(amax, std::abs(z));
-            real &= z.imag() == 0.0;
+        // Sec. III-A step 1(a): Gauss-Seidel preconditioning, M = lower triangle of A (with the
+        // diagonal); A <- M^-1 A, b <- M^-1 b by forward substitution
+        if (flags & QSIM_HHL_GAUSS_SEIDEL) {
+            for (int i = 0; i < N; i++) QSIM_REQUIRE(Am[(size_t)i * N + i] != cd(0.0, 0.0), "zero diagonal: no Gauss-Seidel splitting");
+            std::vector<cd> X((size_t)N * N), y(N);
+            for (int i = 0; i < N; i++) {
+                const cd inv = 1.0 / Am[(size_t)i * N + i];
+                for (int c = 0; c < N; c++) {
+                    cd s2 = Am[(size_t)i * N + c];
+                    for (int k = 0; k < i; k++) s2 -= Am[(size_t)i * N + k] * X[(size_t)k * N + c];
+                    X[(size_t)i * N + c] = s2 * inv;
+                }
+                cd sb = bv[i];
+                for (int k = 0; k < i; k++) sb -= Am[(size_t)i * N + k] * y[k];
+                y[i] = sb * inv;
+            }
+            Am.swap(X);
+            bv.swap(y);
         }
+        double amax = 0.0;
+        for (const cd &z : Am) amax = std::max(amax, std::abs(z));
         const double tol = 1e-12 * std::max(1.0, amax);
-        for (int r = 0; r < N; r++)
+        bool herm = true;
+        for (int r = 0; r < N && herm; r++)
             for (int c = 0; c <= r; c++)
-                QSIM_REQUIRE(std::abs(Am[(size_t)r * N + c] - std::conj(Am[(size_t)c * N + r])) <= tol,
-                             "A is not Hermitian");
+                if (std::abs(Am[(size_t)r * N + c] - std::conj(Am[(size_t)c * N + r])) > tol) {
+                    herm = false;
+                    break;
+                }
+        // Sec. III-A step 1(c): Hermitian dilation [[0, A], [A^H, 0]] with right-hand side [b; 0]
+        int Ne = N, off = 0;
+        if (!herm || (flags & QSIM_HHL_DILATE)) {
+            QSIM_REQUIRE(flags & (QSIM_HHL_DILATE | QSIM_HHL_GAUSS_SEIDEL),
+                         "A is not Hermitian (pass QSIM_HHL_DILATE for the Hermitian dilation)");
+            Ne = 2 * N;
+            off = N;
+            QSIM_REQUIRE(Ne <= 4096, "dilated system larger than 4096");
+            std::vector<cd> H((size_t)Ne * Ne, cd(0.0, 0.0));
+            for (int r = 0; r < N; r++)
+                for (int c = 0; c < N; c++) {
+                    H[(size_t)r * Ne + (N + c)] = Am[(size_t)r * N + c];
+                    H[(size_t)(N + c) * Ne + r] = std::conj(Am[(size_t)r * N + c]);
+                }
+            Am.swap(H);
+            bv.resize(Ne, cd(0.0, 0.0));
+        }
+        bool real = true;
+        for (const cd &z : Am) real &= z.imag() == 0.0;
         std::vector<double> lam;
         std::vector<cd> V;
         if (real) {  // real symmetric: Householder tridiagonalization + implicit QR
-            std::vector<double> Ar((size_t)N * N), Vr;
-            for (int r = 0; r < N; r++)
-                for (int c = 0; c < N; c++)
-                    Ar[(size_t)r * N + c] = 0.5 * (Am[(size_t)r * N + c].real() + Am[(size_t)c * N + r].real());
-            symmetric_eig_real(N, Ar, lam, Vr);
+            std::vector<double> Ar((size_t)Ne * Ne), Vr;
+            for (int r = 0; r < Ne; r++)
+                for (int c = 0; c < Ne; c++)
+                    Ar[(size_t)r * Ne + c] = 0.5 * (Am[(size_t)r * Ne + c].real() + Am[(size_t)c * Ne + r].real());
+            symmetric_eig_real(Ne, Ar, lam, Vr);
             V.assign(Vr.begin(), Vr.end());
         } else {
-            for (int r = 0; r < N; r++) Am[(size_t)r * N + r] = Am[(size_t)r * N + r].real();
-            hermitian_eig(N, Am, lam, V);
+            for (int r = 0; r < Ne; r++) Am[(size_t)r * Ne + r] = Am[(size_t)r * Ne + r].real();
+            hermitian_eig(Ne, Am, lam, V);
         }
-        *out = build_from_spectrum(N, lam, V, bv, n_clock, t, C, flags);
+        hhl_circuit *h = build_from_spectrum(Ne, lam, V, bv, n_clock, t, C, flags);
+        h->N_eff = Ne;
+        h->N = N;
+        h->x_off = off;
+        h->flags = flags;
+        *out = h;
     });
 }
 
@@ -243,7 +296,8 @@ int hhl_build_spectral_ex(const double *lambda, const double *V, const double *b
     return guarded([&] {
         QSIM_REQUIRE(lambda != nullptr && V != nullptr && b != nullptr && out != nullptr, "NULL argument");
         QSIM_REQUIRE(N >= 1 && N <= 4096, "N must be in 1..4096");
-        QSIM_REQUIRE((flags & ~QSIM_HHL_STRUCTURED_QPE) == 0, "unknown flags");
+        QSIM_REQUIRE((flags & ~QSIM_HHL_STRUCTURED_QPE) == 0,
+                     "hhl_build_spectral_ex takes only QSIM_HHL_STRUCTURED_QPE");
         std::vector<double> lam(lambda, lambda + N);
         for (double v : lam) QSIM_REQUIRE(std::isfinite(v), "non-finite eigenvalue");
         std::vector<cd> Vm = read_complex(V, (size_t)N * N), bv = read_complex(b, N);
@@ -256,7 +310,10 @@ int hhl_build_spectral_ex(const double *lambda, const double *V, const double *b
             ls[j] = lam[idx[j]];
             for (int r = 0; r < N; r++) Vs[(size_t)r * N + j] = Vm[(size_t)r * N + idx[j]];
         }
-        *out = build_from_spectrum(N, ls, Vs, bv, n_clock, t, C, flags);
+        hhl_circuit *h = build_from_spectrum(N, ls, Vs, bv, n_clock, t, C, flags);
+        h->N_eff = N;
+        h->flags = flags;
+        *out = h;
     });
 }
 
@@ -283,6 +340,8 @@ int hhl_get_info(const hhl_circuit *h, hhl_info *o) {
         o->lambda_max = h->lam_max;
         o->n_total_formula = h->n_total_formula;
         o->n_gates = (int)h->circ.gates.size();
+        o->N_eff = h->N_eff;
+        o->flags = h->flags;
     });
 }
 
@@ -312,7 +371,7 @@ int hhl_readout(const void *state, int dtype, const hhl_circuit *h, void *stream
             }
         if (x_out)
             for (int i = 0; i < h->N; i++) {
-                const cd x = slice[i] * (inv * norm_x * h->norm_b);
+                const cd x = slice[h->x_off + i] * (inv * norm_x * h->norm_b);
                 x_out[2 * i] = x.real();
                 x_out[2 * i + 1] = x.imag();
             }

@@ -439,13 +439,15 @@ __global__ void qpe_phase_kernel(const QpeArgs a) {
 }
 
 // HHL eigenvalue inversion over a contiguous clock register c0..c0+nc-1: for the pair of
-// amplitudes that differ in the ancilla, r = min(1, Cs / k) with k the clock value (r = 0 for
-// k = 0), and (psi0, psi1) <- [[sqrt((1 - r)(1 + r)), -r], [r, sqrt((1 - r)(1 + r))]] (psi0, psi1).
+// amplitudes that differ in the ancilla, r = clamp(Cs / k, -1, 1) with k the clock value (two's
+// complement for an indefinite A; r = 0 for k = 0), and
+// (psi0, psi1) <- [[sqrt((1 - |r|)(1 + |r|)), -r], [r, sqrt((1 - |r|)(1 + |r|))]] (psi0, psi1).
 struct InvertArgs {
     void *psi;
     long long count;  // 2^(n-1)
     double Cs;
     int target, c0, nc;
+    int twos;         // clock register read as two's complement (indefinite A)
 };
 
 template <typename R>
@@ -461,9 +463,12 @@ __global__ void hhl_invert_kernel(const InvertArgs a) {
         const unsigned long long k = (i0 >> a.c0) & vmask;
         R s = 0, c = 1;
         if (k) {
-            s = Cs / (R)k;
+            const long long ks = (a.twos && (k >> (a.nc - 1))) ? (long long)k - (1ll << a.nc) : (long long)k;
+            s = Cs / (R)ks;
             if (s > (R)1) s = (R)1;
-            c = sqrt(((R)1 - s) * ((R)1 + s));
+            if (s < (R)-1) s = (R)-1;
+            const R as = s < 0 ? -s : s;
+            c = sqrt(((R)1 - as) * ((R)1 + as));
         }
         const V x0 = psi[i0], x1 = psi[i0 | tb];
         V y0, y1;
@@ -798,6 +803,7 @@ void run_hhl_invert(void *state, int n, int dtype, const Op &op, cudaStream_t st
     a.target = op.targets[0];
     a.nc = (int)op.controls.size();
     a.c0 = op.controls[0];
+    a.twos = op.sign == -1 ? 1 : 0;
     for (int j = 0; j < a.nc; j++) QSIM_REQUIRE(op.controls[j] == a.c0 + j, "inversion register must be contiguous");
     const int grid = grid_for(a.count, 256);
     if (dtype == QSIM_C128) hhl_invert_kernel<double><<<grid, 256, 0, st>>>(a);
@@ -1103,10 +1109,12 @@ extern "C" int hhl_readout_noalloc(const void *state, int dtype, const hhl_circu
         check_launch("hhl_readout_noalloc kernels");
         double sums[3];
         CUDA_OK(cudaMemcpyAsync(sums, out, sizeof(sums), cudaMemcpyDeviceToHost, st));
-        // the slice lands straight in the caller's buffer: all 2^nb amplitudes, or the first N
+        // the slice lands straight in the caller's buffer: all 2^nb amplitudes, or the N entries
+        // of x (from offset x_off of a dilated system)
         double *dst = x_state_out ? x_state_out : x_out;
         const long long cnt = x_state_out ? slice_len : (long long)h->N;
-        if (dst) CUDA_OK(cudaMemcpyAsync(dst, slice, (size_t)cnt * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        const double *src = x_state_out ? slice : slice + 2 * (size_t)h->x_off;
+        if (dst) CUDA_OK(cudaMemcpyAsync(dst, src, (size_t)cnt * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         CUDA_OK(cudaStreamSynchronize(st));
         const double P = sums[1], P0 = sums[2];
         const double inv = P0 > 0.0 ? 1.0 / std::sqrt(P0) : 0.0;
@@ -1114,8 +1122,8 @@ extern "C" int hhl_readout_noalloc(const void *state, int dtype, const hhl_circu
         if (x_state_out) {
             if (x_out)
                 for (int i = 0; i < h->N; i++) {
-                    x_out[2 * i] = x_state_out[2 * i] * inv * norm_x * h->norm_b;
-                    x_out[2 * i + 1] = x_state_out[2 * i + 1] * inv * norm_x * h->norm_b;
+                    x_out[2 * i] = x_state_out[2 * (h->x_off + i)] * inv * norm_x * h->norm_b;
+                    x_out[2 * i + 1] = x_state_out[2 * (h->x_off + i) + 1] * inv * norm_x * h->norm_b;
                 }
             for (long long i = 0; i < 2 * slice_len; i++) x_state_out[i] *= inv;
         } else if (x_out) {

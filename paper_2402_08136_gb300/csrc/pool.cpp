@@ -226,12 +226,13 @@ void collect(qsim_pool *p, Slot &s, cudaError_t status) {
                 const double norm_x = std::sqrt(P) / r->h->C;
                 for (int j = 0; j < r->N; j++) {
                     double re, im;
+                    const int jj = r->h->x_off + j;
                     if (r->dtype == QSIM_C128) {
-                        re = reinterpret_cast<const double *>(slice)[2 * j];
-                        im = reinterpret_cast<const double *>(slice)[2 * j + 1];
+                        re = reinterpret_cast<const double *>(slice)[2 * jj];
+                        im = reinterpret_cast<const double *>(slice)[2 * jj + 1];
                     } else {
-                        re = reinterpret_cast<const float *>(slice)[2 * j];
-                        im = reinterpret_cast<const float *>(slice)[2 * j + 1];
+                        re = reinterpret_cast<const float *>(slice)[2 * jj];
+                        im = reinterpret_cast<const float *>(slice)[2 * jj + 1];
                     }
                     r->x[2 * j] = re * inv * norm_x * r->h->norm_b;
                     r->x[2 * j + 1] = im * inv * norm_x * r->h->norm_b;

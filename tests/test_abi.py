@@ -141,7 +141,8 @@ def test_hhl_build_errors(qs):
     with pytest.raises(qs.QsimError):
         qs.hhl_build(A, [1.0, 0.0], 3)                 # not Hermitian
     with pytest.raises(qs.QsimError):
-        qs.hhl_build(-np.eye(2), [1.0, 0.0], 3)        # not positive definite
+        qs.hhl_build(np.diag([1.0, 0.0]), [1.0, 0.0], 3)   # singular
+    qs.hhl_build(-np.eye(2), [1.0, 0.0], 3)            # negative definite: sign qubit, accepted
     with pytest.raises(qs.QsimError):
         qs.hhl_build(np.eye(2), [0.0, 0.0], 3)         # b = 0
     with pytest.raises(qs.QsimError):
@@ -192,3 +193,29 @@ def test_real_and_complex_eigensolvers_agree(qs):
             if key.startswith("lambda") else abs(i1[key] - i2[key]) < 1e-12 * max(1, abs(i2[key]))
     assert abs(i2["lambda_min"] - lam[0]) < 1e-12 * lam[-1]
     assert abs(i2["lambda_max"] - lam[-1]) < 1e-12 * lam[-1]
+
+
+def test_indefinite_system_uses_sign_qubit(qs):
+    rng = np.random.default_rng(5)
+    V = np.linalg.qr(rng.standard_normal((6, 6)))[0]
+    lam = np.array([-20.0, -3.0, 1.0, 2.0, 8.0, 16.0])
+    A = (V * lam) @ V.T
+    i = qs.hhl_build(0.5 * (A + A.T), rng.standard_normal(6)).info()
+    assert i["m"] == max(3 + 1, math.ceil(math.log2(20.0 / 1.0 + 1))) + 1
+    assert i["n_total_formula"] == i["nb"] + i["m"] + 1
+    assert abs(i["t"] - 2 * math.pi * (2 ** (i["m"] - 1) - 1) / (2 ** i["m"] * 20.0)) < 1e-14
+    assert abs(i["lambda_min"] + 20.0) < 1e-12 and abs(i["lambda_max"] - 16.0) < 1e-12
+
+
+def test_gauss_seidel_and_dilation_host_side(qs):
+    """Table I, 30-bus*: a Gauss-Seidel preconditioned 29 x 29 system is dilated to 58 rows
+    (n_data = 6) and has negative eigenvalues (sign qubit)."""
+    rng = np.random.default_rng(33)
+    A, b, _ = synth.grid_system(rng, 30)
+    h = qs.hhl_build(A, b, 0, gauss_seidel=True).info()
+    assert (h["N"], h["N_eff"], h["nb"]) == (29, 58, 6)
+    assert h["lambda_min"] < 0 < h["lambda_max"] and abs(h["lambda_min"] + h["lambda_max"]) < 1e-9 * h["lambda_max"]
+    with pytest.raises(qs.QsimError):
+        qs.hhl_build(np.array([[2.0, 1.0], [0.0, 3.0]]), [1.0, 0.0], 3)        # needs dilate
+    d = qs.hhl_build(np.array([[2.0, 1.0], [0.0, 3.0]]), [1.0, 0.0], 3, dilate=True).info()
+    assert d["N_eff"] == 4 and d["N"] == 2

@@ -429,3 +429,117 @@ def test_full_size_forward_inverse_roundtrip(qs, dtype, n):
                              st[s0:s0 + (1 << 28)].to(torch.complex128)).item()
         fid = abs(ov) ** 2 / (n0 ** 2 * n1 ** 2)
         assert fid >= 1 - 1e-6
+
+
+# ------------------------------------------------------------------ degenerate HHL systems
+def _degenerate_cases():
+    rng = np.random.default_rng(77)
+    yield "1x1", np.array([[3.0]]), np.array([2.0]), 4, 2 * math.pi / 16, 0.0
+    yield "scaled identity", 5.0 * np.eye(4), rng.standard_normal(4), 5, 0.0, 0.0
+    A, _, _ = synth.grid_system(rng, 9)
+    w, V = np.linalg.eigh(A)
+    yield "b is an eigenvector", A, V[:, 3].astype(np.complex128), 6, 0.0, 0.0
+    # eigenvalues far below the first grid step: clock value 0 carries weight, theta_0 = 0
+    A2 = np.diag([1e-3, 0.5, 40.0, 100.0])
+    yield "eigenvalues under the grid", A2, np.ones(4), 4, 0.0, 0.0
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("case", list(range(4)))
+def test_hhl_degenerate_systems(qs, dtype, case):
+    name, A, b, m, t, C = list(_degenerate_cases())[case]
+    for structured in (False, True):
+        h = qs.hhl_build(A, b, m, t, C, structured=structured)
+        ref = ohhl.solve(A, b, m, t, C)
+        st, r = run_product_hhl(qs, h, dtype, 3)
+        tol = cond_tol(m) if dtype == torch.complex128 else TOL[dtype]
+        compare_hhl(st, r, ref, dtype, tol)
+
+
+
+# ------------------------------------------------------------ indefinite systems (sign qubit)
+def _indefinite(seed, N, m, grid):
+    rng = np.random.default_rng(seed)
+    V = synth.haar_unitary(rng, N)
+    if grid:
+        top = 2 ** (m - 1) - 1
+        lam = rng.integers(1, top + 1, size=N).astype(float) * rng.choice([-1.0, 1.0], size=N)
+        lam[0], lam[-1] = -top, top
+    else:
+        lam = rng.uniform(0.5, 10.0, size=N) * rng.choice([-1.0, 1.0], size=N)
+        lam[0] = -abs(lam[0])
+    A = (V * lam) @ V.conj().T
+    return 0.5 * (A + A.conj().T), rng.standard_normal(N) + 1j * rng.standard_normal(N)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("structured", [False, True])
+def test_hhl_indefinite_exact_grid(qs, dtype, structured):
+    m, N = 6, 5
+    A, b = _indefinite(3, N, m, grid=True)
+    t = 2 * math.pi / 2 ** m
+    h = qs.hhl_build(A, b, m, t, structured=structured)
+    ref = ohhl.solve(A, b, m, t)
+    st, r = run_product_hhl(qs, h, dtype, 3)
+    compare_hhl(st, r, ref, dtype, TOL[dtype])
+    xt = np.linalg.solve(A, b)
+    assert np.linalg.norm(r["x"] - xt) / np.linalg.norm(xt) < (1e-10 if dtype == torch.complex128 else 1e-4)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_hhl_indefinite_offgrid(qs, dtype):
+    m = 8
+    A, b = _indefinite(4, 6, m, grid=False)
+    h = qs.hhl_build(A, b, m, structured=True)
+    ref = ohhl.solve(A, b, m)
+    st, r = run_product_hhl(qs, h, dtype, 3)
+    compare_hhl(st, r, ref, dtype, cond_tol(m) if dtype == torch.complex128 else TOL[dtype])
+
+
+# ------------------------------------------- Gauss-Seidel preconditioning, Hermitian dilation
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_dilation_exact_grid(qs, dtype):
+    rng = np.random.default_rng(31)
+    N, m = 3, 6
+    U, W = synth.haar_unitary(rng, N), synth.haar_unitary(rng, N)
+    A = (U * np.array([2.0, 5.0, 31.0])) @ W.conj().T
+    b = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    t = 2 * math.pi / 2 ** m
+    for structured in (False, True):
+        h = qs.hhl_build(A, b, m, t, dilate=True, structured=structured)
+        ref = ohhl.solve_general(A, b, m, t)
+        st, r = run_product_hhl(qs, h, dtype, 3)
+        compare_hhl(st, r, ref, dtype, TOL[dtype])
+        xt = np.linalg.solve(A, b)
+        assert np.linalg.norm(r["x"] - xt) / np.linalg.norm(xt) < (1e-10 if dtype == torch.complex128 else 1e-4)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_gauss_seidel_dilated_offgrid(qs, dtype):
+    rng = np.random.default_rng(8)
+    A, b, _ = synth.grid_system(rng, 9)
+    m = 9
+    h = qs.hhl_build(A, b, m, gauss_seidel=True, structured=True)
+    ref = ohhl.solve_general(A, b, m, gauss_seidel=True)
+    st, r = run_product_hhl(qs, h, dtype, 3)
+    compare_hhl(st, r, ref, dtype, cond_tol(m) * 100 if dtype == torch.complex128 else TOL[dtype])
+    assert np.max(np.abs(r["x"] - ref["x"])) <= 1e-4 * np.linalg.norm(ref["x"])
+
+
+def test_dilated_batch_readout_offset(qs):
+    """The batched executor returns x from the lower half of the dilated slice."""
+    rng = np.random.default_rng(12)
+    probs = []
+    for _ in range(3):
+        N = 3
+        U, W = synth.haar_unitary(rng, N), synth.haar_unitary(rng, N)
+        probs.append(((U * np.array([1.0, 3.0, 7.0])) @ W.conj().T, rng.standard_normal(N)))
+    m, t = 4, 2 * math.pi / 16
+    hs = [qs.hhl_build(A, b, m, t, dilate=True, structured=True) for A, b in probs]
+    fused = [qs.qsim_fuse(h.as_circuit(), 3) for h in hs]
+    states = [torch.empty(1 << h.info()["n"], dtype=torch.complex128, device="cuda") for h in hs]
+    bt = qs.hhl_batch_create(hs, states, fused)
+    bt.run()
+    for (A, b), r in zip(probs, bt.results()):
+        xt = np.linalg.solve(A, b)
+        assert np.linalg.norm(r["x"] - xt) / np.linalg.norm(xt) < 1e-10
