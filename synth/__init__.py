@@ -27,6 +27,7 @@ from .states import (  # noqa: F401
     gaussian_amplitudes_at,
     STATE_SCALE_NOTE,
 )
+from .acgrid import ac_case  # noqa: F401
 from .workloads import (  # noqa: F401
     hhl7_problem,
     hhl27_problem,
