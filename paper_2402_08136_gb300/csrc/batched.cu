@@ -26,7 +26,9 @@
 namespace qsim {
 namespace batch {
 
-constexpr int kThreads = 256;
+// threads per CTA: 512 for complex64 (more independent loads in flight for states updated in
+// global memory), 256 for complex128 (register budget of the 5-target dense gate)
+template <typename V> struct Threads { static constexpr int n = sizeof(V) == 8 ? 512 : 256; };
 
 enum BKind : unsigned char { B_DENSE = 0, B_PHASE = 1, B_DIAG = 2, B_SWAP = 3, B_UCRY = 4, B_QPE = 5, B_INVERT = 6 };
 
@@ -63,6 +65,10 @@ __device__ __forceinline__ unsigned expand(unsigned g, unsigned fixmask) {
 template <typename V, int K>
 __device__ void op_dense(V *psi, int n, const BOp &op, const V *U, int tid) {
     constexpr int D = 1 << K;
+    constexpr int NT = Threads<V>::n;
+    // independent groups per iteration (their loads overlap); complex128 keeps the register
+    // count of the 3..5-target gates in check with one group
+    constexpr int ILP = (K <= 2 || (K <= 4 && sizeof(V) == 8)) ? 2 : 1;
     const unsigned ngroups = 1u << (n - __popc(op.fixmask));  // fixmask = targets | controls
     unsigned offs[D];
 #pragma unroll
@@ -73,24 +79,33 @@ __device__ void op_dense(V *psi, int n, const BOp &op, const V *U, int tid) {
             if ((r >> b) & 1) o |= 1u << op.t[b];
         offs[r] = o;
     }
-    for (unsigned g = tid; g < ngroups; g += kThreads) {
-        const unsigned base = expand(g, op.fixmask) | op.cmask;
-        V x[D];
+    for (unsigned g0 = tid; g0 < ngroups; g0 += ILP * NT) {
+        unsigned base[ILP];
+        bool live[ILP];
+        V x[ILP][D];
 #pragma unroll
-        for (int c = 0; c < D; c++) x[c] = psi[base + offs[c]];
+        for (int j = 0; j < ILP; j++) {
+            live[j] = g0 + j * NT < ngroups;
+            base[j] = live[j] ? (expand(g0 + j * NT, op.fixmask) | op.cmask) : 0u;
+#pragma unroll
+            for (int c = 0; c < D; c++) x[j][c] = live[j] ? psi[base[j] + offs[c]] : V{0, 0};
+        }
 #pragma unroll 1
         for (int r = 0; r < D; r++) {
-            V acc{0, 0};
             const V *u = U + r * D;
 #pragma unroll
-            for (int c = 0; c < D; c++) {
-                const V w = u[c];
-                acc.x = fma(w.x, x[c].x, acc.x);
-                acc.x = fma(-w.y, x[c].y, acc.x);
-                acc.y = fma(w.x, x[c].y, acc.y);
-                acc.y = fma(w.y, x[c].x, acc.y);
+            for (int j = 0; j < ILP; j++) {
+                V acc{0, 0};
+#pragma unroll
+                for (int c = 0; c < D; c++) {
+                    const V w = u[c];
+                    acc.x = fma(w.x, x[j][c].x, acc.x);
+                    acc.x = fma(-w.y, x[j][c].y, acc.x);
+                    acc.y = fma(w.x, x[j][c].y, acc.y);
+                    acc.y = fma(w.y, x[j][c].x, acc.y);
+                }
+                if (live[j]) psi[base[j] + offs[r]] = acc;
             }
-            psi[base + offs[r]] = acc;
         }
     }
 }
@@ -106,6 +121,7 @@ __device__ __forceinline__ V cmulb(V a, V b) {
 template <typename R>
 __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typename C2<R>::T *data, int tid) {
     using V = typename C2<R>::T;
+    constexpr int kThreads = Threads<V>::n;
     const V *d = data + op.data;
     switch (op.kind) {
         case B_DENSE:
@@ -211,6 +227,7 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
     }
 }
 
+template <int kThreads>
 __device__ __forceinline__ double block_sum_b(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -226,9 +243,11 @@ __device__ __forceinline__ double block_sum_b(double v, double *sh) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads) batched_kernel(const BCirc *circs, const int *order, int count,
-                                                          unsigned *counter, int smem_amps) {
+__global__ void __launch_bounds__(Threads<typename C2<R>::T>::n) batched_kernel(const BCirc *circs, const int *order,
+                                                                              int count, unsigned *counter,
+                                                                              int smem_amps) {
     using V = typename C2<R>::T;
+    constexpr int kThreads = Threads<V>::n;
     extern __shared__ __align__(16) unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
     __shared__ int cur;
@@ -273,9 +292,9 @@ __global__ void __launch_bounds__(kThreads) batched_kernel(const BCirc *circs, c
                 c.result[4 + 2 * i] = (double)z.x;
                 c.result[4 + 2 * i + 1] = (double)z.y;
             }
-            const double ta = block_sum_b(s_all, red);
-            const double th = block_sum_b(s_hi, red);
-            const double ts = block_sum_b(s_sl, red);
+            const double ta = block_sum_b<kThreads>(s_all, red);
+            const double th = block_sum_b<kThreads>(s_hi, red);
+            const double ts = block_sum_b<kThreads>(s_sl, red);
             if (tid == 0) {
                 c.result[0] = ta;
                 c.result[1] = th;
@@ -624,7 +643,7 @@ void configure_batch(qsim_batch *B) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel attribute: ") + cudaGetErrorString(e));
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, batch::kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, batch::Threads<typename batch::C2<R>::T>::n, smem);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -637,7 +656,7 @@ template <typename R>
 void launch_batch(qsim_batch *B, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batch counter reset: ") + cudaGetErrorString(e));
-    batch::batched_kernel<R><<<B->grid, batch::kThreads, B->smem_bytes, st>>>(B->d_circs, B->d_order, B->count,
+    batch::batched_kernel<R><<<B->grid, batch::Threads<typename batch::C2<R>::T>::n, B->smem_bytes, st>>>(B->d_circs, B->d_order, B->count,
                                                                               B->d_counter, B->smem_amps);
     e = cudaGetLastError();
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel: ") + cudaGetErrorString(e));
