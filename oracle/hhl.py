@@ -73,6 +73,30 @@ def qft_gates(qubits, inverse: bool):
     return out
 
 
+def dft_pass(psi: np.ndarray, targets, sign: int, src=(), pre: bool = False) -> None:
+    """In place: one Cooley-Tukey stage of a (inverse) QFT on the register `targets`.
+
+    With y the value of `targets` (bit j <-> targets[j], k bits) and w the value of `src`
+    (bit j <-> src[j], s bits), for every w apply the 2^k x 2^k unitary
+        F[y', y] = 2^{-k/2} exp(sign 2 pi i y y' / 2^k)
+    followed (pre=False) or preceded (pre=True) by the diagonal twiddle
+        T_w[y] = exp(sign 2 pi i w y / 2^(k+s)).
+    A QFT on m qubits splits into such passes by the Cooley-Tukey factorisation of the DFT of
+    size 2^m (Cooley & Tukey 1965): the top field's pass carries the twiddle of the bits below
+    it, and the result is the QFT with its output digits in field order.  Written with the
+    textbook dense-gate rule: one gate per value w, conditioned on src == w.
+    """
+    k, s = len(targets), len(src)
+    K = 1 << k
+    y = np.arange(K, dtype=np.int64)
+    F = np.exp(sign * 2j * np.pi * ((np.outer(y, y) % K) / K)) / math.sqrt(K)
+    for w in range(1 << s):
+        T = np.exp(sign * 2j * np.pi * (((w * y) % (1 << (k + s))) / (1 << (k + s))))
+        G = F * T[None, :] if pre else T[:, None] * F
+        vals = [(w >> j) & 1 for j in range(s)]
+        core.apply_gate(psi, list(targets), G, list(src), vals)
+
+
 def resource_counts(n_rows: int, kappa: float, has_negative: bool):
     """Sec. III-B qubit count, with Table I's conventions (ancilla counted, sign qubit in n_QPE).
 

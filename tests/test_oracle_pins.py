@@ -3,12 +3,14 @@
   * gate rule          -> brute-force full 2^n x 2^n operator built from Kronecker products
   * UCRY               -> brute-force block-diagonal operator
   * QFT / inverse QFT  -> numpy's FFT (the DFT up to normalisation)
+  * DFT passes         -> the textbook QFT gate circuit (H, controlled phases, swaps): the
+                          Cooley-Tukey field passes plus a relabelling of the register equal it
   * QPE                -> an eigenvector whose phase lies on the clock grid lands on exactly |k>
   * HHL (exact grid)   -> the postselected slice equals A^-1 b / ||A^-1 b||, P = C^2 ||A^-1 b||^2,
                           no leakage, and x = A^-1 b (Sec. III-A)
   * resource formula   -> the qubit counts printed in Table I (tests/golden)
   * compensated sums   -> math.fsum (exactly rounded)
-Two mutation tests plant a plausible mistake in the oracle and check that a pin catches it.
+Mutation tests plant a plausible mistake in the oracle and check that a pin catches it.
 """
 import math
 import os
@@ -333,3 +335,74 @@ def test_planted_wrong_evolution_sign_is_caught(monkeypatch):
     y = np.linalg.solve(A, b / np.linalg.norm(b))
     err = np.max(np.abs(r["x_state"][:4] - y / np.linalg.norm(y))) if r["P0"] > 1e-30 else 1.0
     assert err > 1e-3 or abs(r["leakage"]) > 1e-3
+
+
+# ------------------------------------------------------------------ QFT as Cooley-Tukey passes
+def _split_fields(reg, sizes):
+    """Fields of `reg` (bit j <-> reg[j]) from the top down: sizes[0] top bits first."""
+    out, hi = [], len(reg)
+    for s in sizes:
+        out.append(list(reg[hi - s: hi]))
+        hi -= s
+    assert hi == 0
+    return out
+
+
+def _relabel(psi, reg, order, to_natural=True):
+    """Move register value v between the layouts 'bit j of v at order[j]' and 'at reg[j]'."""
+    idx = np.arange(psi.size)
+    src, dst = (order, reg) if to_natural else (reg, order)
+    v = sum(((idx >> q) & 1) << j for j, q in enumerate(src))
+    rest = idx & ~sum(1 << q for q in reg)
+    dest = rest | sum(((v >> j) & 1) << q for j, q in enumerate(dst))
+    out = np.empty_like(psi)
+    out[dest] = psi
+    return out
+
+
+def _check_dft_factorisation(m, sizes, dft):
+    rng = np.random.default_rng(100 + m)
+    n = m + 2
+    reg = list(range(1, m + 1))  # spectator qubits 0 and m+1
+    fields = _split_fields(reg, sizes)
+    order = [q for f in fields for q in f]
+    psi = rand_state(rng, n)
+    # inverse QFT: passes top field first, each with the twiddle of the bits below it
+    p = psi.copy()
+    for f in fields:
+        dft(p, f, -1, [q for q in reg if q < min(f)], False)
+    ref = psi.copy()
+    for g in hhl.qft_gates(reg, inverse=True):
+        core.apply_gate(ref, g[1], g[2])
+    assert np.max(np.abs(_relabel(p, reg, order) - ref)) < 1e-13
+    # QFT from the field-ordered layout: the passes reversed, conjugated, twiddle first
+    for f in reversed(fields):
+        dft(p, f, +1, [q for q in reg if q < min(f)], True)
+    assert np.max(np.abs(p - psi)) < 1e-13
+    # forward QFT of a natural-order state
+    q2 = _relabel(psi, reg, order, to_natural=False)
+    for f in reversed(fields):
+        dft(q2, f, +1, [q for q in reg if q < min(f)], True)
+    ref2 = psi.copy()
+    for g in hhl.qft_gates(reg, inverse=False):
+        core.apply_gate(ref2, g[1], g[2])
+    assert np.max(np.abs(q2 - ref2)) < 1e-13
+
+
+@pytest.mark.parametrize("m,sizes", [(5, [5]), (6, [3, 3]), (7, [4, 3]), (8, [3, 5]), (9, [3, 3, 3])])
+def test_dft_passes_factor_the_textbook_qft(m, sizes):
+    _check_dft_factorisation(m, sizes, hhl.dft_pass)
+
+
+def test_planted_twiddle_mistakes_are_caught():
+    def wrong_denominator(psi, targets, sign, src, pre):
+        hhl.dft_pass(psi, targets, sign, list(src)[1:], pre)   # drops the lowest twiddle bit
+
+    def wrong_side(psi, targets, sign, src, pre):
+        hhl.dft_pass(psi, targets, sign, src, not pre)         # twiddle on the wrong side
+
+    def wrong_sign(psi, targets, sign, src, pre):
+        hhl.dft_pass(psi, targets, sign, (), pre)              # twiddle left out
+    for bad in (wrong_denominator, wrong_side, wrong_sign):
+        with pytest.raises(AssertionError):
+            _check_dft_factorisation(6, [3, 3], bad)
