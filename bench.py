@@ -363,7 +363,8 @@ def run_hhl(args, ws, rank, which):
     else:
         p = synth.hhl27_problem()
         dtypes = [("c64", torch.complex64), ("c128", torch.complex128)]
-    h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"], structured=args.structured)
+    h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"], structured=args.structured,
+                     fft_qft=args.fft_qft)
     info = h.info()
     n = info["n"]
     xt = np.linalg.solve(p["A"], p["b"])
@@ -445,7 +446,8 @@ def run_hhl(args, ws, rank, which):
         "ms_per_step": round(1e3 / main["solves_per_s"], 4), "higher_is_better": True,
         "dtype": "c128" if which == "hhl7" else "c64",
         "config": {"workload": which, "n_qubits": n, "nb": info["nb"], "m": info["m"],
-                   "unfused_gates": info["n_gates"], "structured_qpe": bool(args.structured)},
+                   "unfused_gates": info["n_gates"], "structured_qpe": bool(args.structured),
+                   "qft": "fourier passes" if args.fft_qft else "gates"},
         "latency_ms": {"p50": round(main["p50_ms"], 4), "p99": round(main["p99_ms"], 4)},
         "paths": res,
         "gpu_launches": launches,
@@ -704,6 +706,7 @@ def main():
     ap.add_argument("--per-k", type=int, default=200)
     ap.add_argument("--max-k", type=int, default=0)
     ap.add_argument("--structured", action="store_true", help="diagonalised phase estimation")
+    ap.add_argument("--fft-qft", action="store_true", help="QFTs as Fourier-transform passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-from-host-gen", action="store_true")
     args = ap.parse_args()

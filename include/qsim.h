@@ -81,6 +81,25 @@ int qsim_circuit_add_gate(qsim_circuit *c, int k, const int *targets, int n_cont
 int qsim_circuit_add_ucry(qsim_circuit *c, int target, int n_controls, const int *controls,
                           const double *theta);
 
+/* Append one Cooley-Tukey pass of a quantum Fourier transform (the QFT of the phase
+ * estimation, Sec. III-A and Fig. 5, with the DFT of size 2^m factored into passes over fields
+ * of the register as in Cooley & Tukey 1965).  With y the value of the field targets[0..k-1]
+ * (bit j <-> targets[j], 1 <= k <= 10) and w the value of the twiddle-source register
+ * src[0..n_src-1] (bit j <-> src[j]), the 2^k amplitudes of every assignment of the other
+ * qubits are mapped by
+ *     out[y'] = 2^{-k/2} sum_y exp(sign 2 pi i y y' / 2^k) in[y]          (sign = +1 or -1)
+ * and multiplied by the twiddle exp(sign 2 pi i w y' / 2^(k + n_src)) on the output index
+ * (twiddle_first = 0), or by exp(sign 2 pi i w y / 2^(k + n_src)) on the input index before
+ * the transform (twiddle_first = 1).  k + n_src <= 30; targets and src distinct.  The inverse
+ * QFT of an m-qubit register is the passes over its fields from the top field down, each with
+ * sign -1, twiddle after, and the register bits below the field as src; its output holds the
+ * register value v with the digits of v in field order (the top field holds the lowest digits
+ * of v).  The QFT back is the same passes in reverse order with sign +1 and twiddle first.
+ * The operation runs as one pass over the state (tile-resident radix-2 transform).
+ * Errors: EINVAL. */
+int qsim_circuit_add_dft(qsim_circuit *c, int k, const int *targets, int n_src, const int *src, int sign,
+                         int twiddle_first);
+
 /* Release a circuit and any device copy of its matrices.  NULL is a no-op. */
 void qsim_circuit_free(qsim_circuit *c);
 
@@ -97,6 +116,7 @@ typedef struct {
     double bytes_c64;   /* algorithmic HBM bytes of one application to a complex64 state     */
     double bytes_c128;  /* same for complex128                                                */
     double flops;       /* algorithmic real flops of one application                          */
+    int n_dft;          /* Fourier-transform passes (qsim_circuit_add_dft)                    */
 } qsim_circuit_info;
 
 int qsim_circuit_get_info(const qsim_circuit *c, qsim_circuit_info *out);
@@ -165,7 +185,8 @@ int hhl_build_spectral(const double *lambda, const double *V, const double *b, i
                        int n_clock, double t, double C, hhl_circuit **out);
 
 /* hhl_build / hhl_build_spectral with options.  flags: any of QSIM_HHL_STRUCTURED_QPE,
- * QSIM_HHL_GAUSS_SEIDEL, QSIM_HHL_DILATE (the last two for hhl_build_ex only).
+ * QSIM_HHL_FFT_QFT, QSIM_HHL_GAUSS_SEIDEL, QSIM_HHL_DILATE (the last two for hhl_build_ex
+ * only).
  * QSIM_HHL_STRUCTURED_QPE emits the phase estimation in its diagonalised form (the paper's
  * controlled evolutions, Fig. 5, multiplied out): prod_j C_j-U^(2^j) = (I (x) V)
  * diag_c(exp(i lambda t c)) (I (x) V^H), where c is the clock value.  The V closing the phase
@@ -184,6 +205,13 @@ int hhl_build_spectral(const double *lambda, const double *V, const double *b, i
  * a non-Hermitian A.  Readouts then return the N entries of x (x_state_out keeps the whole
  * dilated slice). */
 #define QSIM_HHL_DILATE 4
+/* Emit the inverse QFT and the QFT of the phase estimation as Fourier-transform passes
+ * (qsim_circuit_add_dft) over fields of at most 10 clock qubits instead of H, controlled-phase
+ * and swap gates: 1 pass for m <= 10, 2 for m <= 20, 3 above.  The inverse QFT leaves the
+ * clock value with its digits in field order, the rotation reads it in that order and the QFT
+ * consumes it, so no relabelling pass is needed; the final state equals the gate-level
+ * circuit's up to rounding. */
+#define QSIM_HHL_FFT_QFT 8
 int hhl_build_ex(const double *A, const double *b, int N, int n_clock, double t, double C, int flags,
                  hhl_circuit **out);
 int hhl_build_spectral_ex(const double *lambda, const double *V, const double *b, int N, int n_clock,
@@ -292,7 +320,7 @@ typedef struct {
     int n_clock;     /* as hhl_build                                                           */
     double t, C;     /* as hhl_build                                                           */
     int dtype;       /* QSIM_C64 or QSIM_C128 state                                            */
-    int flags;       /* hhl_build_ex flags (0 or QSIM_HHL_STRUCTURED_QPE)                       */
+    int flags;       /* hhl_build_ex flags (QSIM_HHL_STRUCTURED_QPE, QSIM_HHL_FFT_QFT, ...)     */
 } hhl_request;
 
 typedef struct {
@@ -307,7 +335,8 @@ typedef struct {
  * room for its state (8 * 2^n bytes for complex64, 16 * 2^n for complex128) and a stream is
  * free.  Requests of at most 16 qubits that the batched executor supports (dense gates of at
  * most 5 targets) and that are ready together run as one batched launch; the others run alone
- * with the full-GPU kernels; launches on different streams overlap.
+ * with the full-GPU kernels, their QFTs as Fourier passes (QSIM_HHL_FFT_QFT is added for them);
+ * launches on different streams overlap.
  * Results equal those of the same request run alone (each circuit's arithmetic does not
  * depend on its batch).  Errors: EINVAL, ENOMEM, ECUDA. */
 int qsim_pool_create(size_t bytes, int n_builders, int n_streams, qsim_pool **out);

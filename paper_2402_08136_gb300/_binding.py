@@ -29,7 +29,7 @@ class _CircuitInfo(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int), ("n_gates", ctypes.c_int), ("n_dense", ctypes.c_int),
                 ("n_diag", ctypes.c_int), ("n_perm", ctypes.c_int), ("n_ucry", ctypes.c_int),
                 ("max_k", ctypes.c_int), ("fused", ctypes.c_int), ("bytes_c64", ctypes.c_double),
-                ("bytes_c128", ctypes.c_double), ("flops", ctypes.c_double)]
+                ("bytes_c128", ctypes.c_double), ("flops", ctypes.c_double), ("n_dft", ctypes.c_int)]
 
 
 class _HHLInfo(ctypes.Structure):
@@ -70,6 +70,8 @@ _SIGS = {
     "qsim_circuit_create": ([ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
     "qsim_circuit_add_gate": ([_VP, ctypes.c_int, _IP, ctypes.c_int, _IP, _DP], ctypes.c_int),
     "qsim_circuit_add_ucry": ([_VP, ctypes.c_int, ctypes.c_int, _IP, _DP], ctypes.c_int),
+    "qsim_circuit_add_dft": ([_VP, ctypes.c_int, _IP, ctypes.c_int, _IP, ctypes.c_int, ctypes.c_int],
+                             ctypes.c_int),
     "qsim_circuit_free": ([_VP], None),
     "qsim_circuit_get_info": ([_VP, ctypes.POINTER(_CircuitInfo)], ctypes.c_int),
     "qsim_fuse": ([_VP, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
@@ -214,6 +216,14 @@ class Circuit:
                                                th.ctypes.data_as(_DP)))
         return self
 
+    def add_dft(self, targets, sign: int, src=(), twiddle_first: bool = False):
+        """One Cooley-Tukey pass of a QFT on the field `targets` (qsim_circuit_add_dft)."""
+        t, tp = _ints(targets)
+        s_, sp = _ints(src)
+        _check(library().qsim_circuit_add_dft(self._ptr, len(targets), tp, len(src), sp, int(sign),
+                                              1 if twiddle_first else 0))
+        return self
+
     def info(self) -> dict:
         s = _CircuitInfo()
         _check(library().qsim_circuit_get_info(self._ptr, ctypes.byref(s)))
@@ -275,12 +285,15 @@ class HHLCircuit:
 QSIM_HHL_STRUCTURED_QPE = 1
 QSIM_HHL_GAUSS_SEIDEL = 2
 QSIM_HHL_DILATE = 4
+QSIM_HHL_FFT_QFT = 8
 
 
 def hhl_build(A, b, n_clock: int = 0, t: float = 0.0, C: float = 0.0,
-              structured: bool = False, gauss_seidel: bool = False, dilate: bool = False) -> HHLCircuit:
+              structured: bool = False, gauss_seidel: bool = False, dilate: bool = False,
+              fft_qft: bool = False) -> HHLCircuit:
     """hhl_build (no options: the paper's controlled evolutions) or hhl_build_ex with the
-    options (structured phase estimation, Gauss-Seidel preconditioning, Hermitian dilation)."""
+    options (structured phase estimation, Gauss-Seidel preconditioning, Hermitian dilation,
+    QFTs as Fourier-transform passes)."""
     Aa, Ap = _cplx(A)
     ba, bp = _cplx(np.ravel(b))
     N = ba.size
@@ -288,7 +301,7 @@ def hhl_build(A, b, n_clock: int = 0, t: float = 0.0, C: float = 0.0,
         raise QsimError(-1, "A must be N x N")
     p = _VP()
     flags = ((QSIM_HHL_STRUCTURED_QPE if structured else 0) | (QSIM_HHL_GAUSS_SEIDEL if gauss_seidel else 0)
-             | (QSIM_HHL_DILATE if dilate else 0))
+             | (QSIM_HHL_DILATE if dilate else 0) | (QSIM_HHL_FFT_QFT if fft_qft else 0))
     if flags:
         _check(library().hhl_build_ex(Ap, bp, N, int(n_clock), float(t), float(C), flags, ctypes.byref(p)))
     else:
@@ -297,7 +310,7 @@ def hhl_build(A, b, n_clock: int = 0, t: float = 0.0, C: float = 0.0,
 
 
 def hhl_build_spectral(lam, V, b, n_clock: int = 0, t: float = 0.0, C: float = 0.0,
-                       structured: bool = False) -> HHLCircuit:
+                       structured: bool = False, fft_qft: bool = False) -> HHLCircuit:
     la = np.ascontiguousarray(np.asarray(lam, dtype=np.float64))
     Va, Vp = _cplx(V)
     ba, bp = _cplx(np.ravel(b))
@@ -305,9 +318,10 @@ def hhl_build_spectral(lam, V, b, n_clock: int = 0, t: float = 0.0, C: float = 0
     if Va.shape != (N, N) or la.size != N:
         raise QsimError(-1, "shape mismatch")
     p = _VP()
-    if structured:
+    flags = (QSIM_HHL_STRUCTURED_QPE if structured else 0) | (QSIM_HHL_FFT_QFT if fft_qft else 0)
+    if flags:
         _check(library().hhl_build_spectral_ex(la.ctypes.data_as(_DP), Vp, bp, N, int(n_clock), float(t),
-                                               float(C), QSIM_HHL_STRUCTURED_QPE, ctypes.byref(p)))
+                                               float(C), flags, ctypes.byref(p)))
     else:
         _check(library().hhl_build_spectral(la.ctypes.data_as(_DP), Vp, bp, N, int(n_clock),
                                             float(t), float(C), ctypes.byref(p)))

@@ -71,14 +71,18 @@ void build_ops(qsim_circuit *c) {
     if (c->ops_ready) return;
     c->ops.clear();
     for (const Gate &g : c->gates) {
-        if (g.kind == GATE_UCRY || g.kind == GATE_QPE_PHASE || g.kind == GATE_HHL_INVERT) {
+        if (g.kind != GATE_U) {
             Op op;
-            op.kind = g.kind == GATE_UCRY ? OP_UCRY : (g.kind == GATE_QPE_PHASE ? OP_QPE_PHASE : OP_HHL_INVERT);
+            op.kind = g.kind == GATE_UCRY        ? OP_UCRY
+                      : g.kind == GATE_QPE_PHASE ? OP_QPE_PHASE
+                      : g.kind == GATE_DFT       ? OP_DFT
+                                                 : OP_HHL_INVERT;
             op.targets = g.targets;
             op.controls = g.controls;
             op.theta = g.theta;
             op.tq = g.tq;
             op.sign = g.sign;
+            op.pre = g.pre;
             c->ops.push_back(std::move(op));
         } else {
             c->ops.push_back(classify_dense(g.targets, g.controls, g.U));
@@ -279,6 +283,11 @@ void circuit_info(const qsim_circuit *c, qsim_circuit_info *o) {
                 amps = N;
                 flops = amps * 12.0;
                 break;
+            case OP_DFT:  // radix-2 count 5 k per amplitude, plus the twiddle and the scaling
+                o->n_dft++;
+                amps = N;
+                flops = amps * (5.0 * k + (op.controls.empty() ? 2.0 : 8.0));
+                break;
         }
         o->bytes_c64 += 2.0 * 8.0 * amps;
         o->bytes_c128 += 2.0 * 16.0 * amps;
@@ -350,6 +359,31 @@ int qsim_circuit_add_ucry(qsim_circuit *c, int target, int n_controls, const int
         const size_t cnt = (size_t)1 << n_controls;
         g.theta.assign(theta, theta + cnt);
         for (double v : g.theta) QSIM_REQUIRE(std::isfinite(v), "non-finite angle");
+        std::lock_guard<std::mutex> lk(c->mu);
+        QSIM_REQUIRE(!c->fused, "cannot append to a fused circuit");
+        c->gates.push_back(std::move(g));
+        c->ops_ready = false;
+    });
+}
+
+int qsim_circuit_add_dft(qsim_circuit *c, int k, const int *targets, int n_src, const int *src, int sign,
+                         int twiddle_first) {
+    return guarded([&] {
+        QSIM_REQUIRE(c != nullptr && targets != nullptr, "NULL argument");
+        QSIM_REQUIRE(k >= 1 && k <= 10, "k must be in 1..10");
+        QSIM_REQUIRE(n_src >= 0 && (n_src == 0 || src != nullptr), "bad twiddle-source register");
+        QSIM_REQUIRE(k + n_src <= 30 && k + n_src <= c->n, "k + n_src must be at most 30 and the qubit count");
+        QSIM_REQUIRE(sign == 1 || sign == -1, "sign must be +1 or -1");
+        QSIM_REQUIRE(twiddle_first == 0 || twiddle_first == 1, "twiddle_first must be 0 or 1");
+        uint64_t seen = 0;
+        check_qubits(c->n, targets, k, seen, "target");
+        check_qubits(c->n, src, n_src, seen, "twiddle-source");
+        Gate g;
+        g.kind = GATE_DFT;
+        g.targets.assign(targets, targets + k);
+        if (n_src) g.controls.assign(src, src + n_src);
+        g.sign = sign;
+        g.pre = twiddle_first;
         std::lock_guard<std::mutex> lk(c->mu);
         QSIM_REQUIRE(!c->fused, "cannot append to a fused circuit");
         c->gates.push_back(std::move(g));

@@ -51,7 +51,7 @@ int guarded(F &&f) {
 
 // ---------------------------------------------------------------------------------------
 // Gate list entries (what the user or hhl_build appends).
-enum GateKind { GATE_U = 0, GATE_UCRY = 1, GATE_QPE_PHASE = 2, GATE_HHL_INVERT = 3 };
+enum GateKind { GATE_U = 0, GATE_UCRY = 1, GATE_QPE_PHASE = 2, GATE_HHL_INVERT = 3, GATE_DFT = 4 };
 
 struct Gate {
     GateKind kind = GATE_U;
@@ -61,7 +61,10 @@ struct Gate {
     std::vector<double> theta;  // GATE_UCRY: 2^|controls|; GATE_QPE_PHASE: eigenvalues (2^|targets|)
     double tq = 0.0;            // GATE_QPE_PHASE: evolution time; GATE_HHL_INVERT: C / grid step
     int sign = 1;               // GATE_QPE_PHASE: +1 phase estimation, -1 its inverse;
-                                // GATE_HHL_INVERT: 1 unsigned, -1 two's-complement clock
+                                // GATE_HHL_INVERT: 1 unsigned, -1 two's-complement clock;
+                                // GATE_DFT: sign of the exponent
+    int pre = 0;                // GATE_DFT: twiddle before (1) or after (0) the transform;
+                                // GATE_DFT uses `controls` as the twiddle-source register
 };
 
 // Executable operation kinds (one device pass each, or a pass group for the tile kernel).
@@ -74,6 +77,7 @@ enum OpKind {
     OP_QPE_PHASE = 5,  // psi[i] *= exp(i sign lam[d] t c), d = data bits (targets), c = clock bits
     OP_HHL_INVERT = 6, // HHL inversion rotation: RY(2 asin(clamp(tq / k, -1, 1))) on the target,
                        // k = clock value (two's complement when sign == -1)
+    OP_DFT = 7,        // DFT of size 2^k on the targets with a twiddle from the controls
 };
 
 struct Op {
@@ -84,7 +88,8 @@ struct Op {
     cd phase = 1.0;             // OP_PHASE
     std::vector<double> theta;  // OP_UCRY angles; OP_QPE_PHASE eigenvalues
     double tq = 0.0;            // OP_QPE_PHASE
-    int sign = 1;               // OP_QPE_PHASE
+    int sign = 1;               // OP_QPE_PHASE, OP_HHL_INVERT, OP_DFT
+    int pre = 0;                // OP_DFT
     // device offsets (bytes) into the circuit's device blob, per dtype
     size_t dev_off[2] = {0, 0};
     // complex64 dense ops with 4..6 targets: TF32 hi/lo split of the real form (tensor cores)
@@ -159,6 +164,9 @@ qsim_batch *batch_instantiate(BatchImage *im, void *dev, double *pinned, cudaStr
 void batch_launch(qsim_batch *b, cudaStream_t st);
 void batch_enqueue_results(qsim_batch *b, cudaStream_t st);
 void batch_host_result(const qsim_batch *b, int i, double *x_out, hhl_readout_stats *stats);
+// dft.cu: Fourier-transform pass; tables packed into the circuit blob as W, Tlo, Thi
+void dft_tables(const Op &op, std::vector<cd> &W, std::vector<cd> &Tlo, std::vector<cd> &Thi);
+void run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cudaStream_t st);
 // linalg.cpp
 void hermitian_eig(int N, const std::vector<cd> &A, std::vector<double> &lam, std::vector<cd> &V);
 void symmetric_eig_real(int N, const std::vector<double> &A, std::vector<double> &lam, std::vector<double> &V);

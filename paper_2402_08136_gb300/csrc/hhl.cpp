@@ -60,6 +60,45 @@ void append_iqft(qsim_circuit &c, const std::vector<int> &q) {
     }
 }
 
+// Inverse of a gate of the phase estimation (dense: adjoint; Fourier pass: opposite sign with
+// the twiddle moved to the other side of the transform).
+Gate inverse_gate(const Gate &g) {
+    Gate r = g;
+    if (g.kind == GATE_DFT) {
+        r.sign = -g.sign;
+        r.pre = 1 - g.pre;
+    } else {
+        r.U = adjoint(g.U);
+    }
+    return r;
+}
+
+// Inverse QFT on `q` as Cooley-Tukey passes (Cooley & Tukey 1965): the DFT of size 2^m with
+// sign -1 factors into a DFT over the top field of the register followed by the twiddle
+// exp(-2 pi i u a / 2^m) (u = value of the bits below the field, a = the field's output
+// digit), then the same factorisation of the remaining lower bits.  Fields hold at most 10
+// qubits.  The result holds the register value v with its digits in field order: the top field
+// carries the lowest digits of v.  Returns that order (bit j of v <-> order[j]).
+std::vector<int> append_iqft_passes(qsim_circuit &c, const std::vector<int> &q) {
+    const int m = (int)q.size();
+    std::vector<int> order;
+    int rem = m;
+    while (rem > 0) {
+        const int parts = (rem + 9) / 10;
+        const int k = (rem + parts - 1) / parts;
+        Gate g;
+        g.kind = GATE_DFT;
+        g.targets.assign(q.begin() + (rem - k), q.begin() + rem);
+        g.controls.assign(q.begin(), q.begin() + (rem - k));
+        g.sign = -1;
+        g.pre = 0;
+        c.gates.push_back(g);
+        order.insert(order.end(), g.targets.begin(), g.targets.end());
+        rem -= k;
+    }
+    return order;
+}
+
 hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const std::vector<cd> &VA,
                                  const std::vector<cd> &b, int n_clock, double t, double C, int flags) {
     double amax = 0.0, amin = 1e300;
@@ -159,7 +198,10 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
         }
     }
     const size_t iqft_begin = c.gates.size();
-    append_iqft(c, clock);
+    // the rotation reads the clock value in the order the inverse QFT leaves it in
+    std::vector<int> clock_order = clock;
+    if (flags & QSIM_HHL_FFT_QFT) clock_order = append_iqft_passes(c, clock);
+    else append_iqft(c, clock);
     const size_t qpe_end = c.gates.size();
     // eigenvalue inversion: theta_k = 2 asin(min(1, C / (k step))), theta_0 = 0.  Emitted as a
     // uniformly controlled RY whose rotation is computed on the device from C / step (cos and sin
@@ -168,27 +210,21 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
         Gate g;
         g.kind = GATE_HHL_INVERT;
         g.targets = {anc};
-        g.controls = clock;
+        g.controls = clock_order;
         g.tq = C / step;
         g.sign = is_signed ? -1 : 1;  // -1: two's-complement clock register
         c.gates.push_back(std::move(g));
     }
     // uncompute: inverse of the phase estimation
     if (flags & QSIM_HHL_STRUCTURED_QPE) {
-        for (size_t i = qpe_end; i-- > iqft_begin;) {  // QFT
-            const Gate &g = c.gates[i];
-            add_u(c, g.targets, g.controls, adjoint(g.U));
-        }
+        for (size_t i = qpe_end; i-- > iqft_begin;) c.gates.push_back(inverse_gate(c.gates[i]));  // QFT
         Gate g = c.gates[qpe_begin + m + 1];  // the phase operator, inverted
         g.sign = -1;
         c.gates.push_back(g);
         add_u(c, data, {}, V);
         for (int j = 0; j < m; j++) add_u(c, {clock[j]}, {}, hadamard());
     } else {
-        for (size_t i = qpe_end; i-- > qpe_begin;) {
-            const Gate &g = c.gates[i];
-            add_u(c, g.targets, g.controls, adjoint(g.U));
-        }
+        for (size_t i = qpe_end; i-- > qpe_begin;) c.gates.push_back(inverse_gate(c.gates[i]));
     }
     return h.release();
 }
@@ -214,7 +250,7 @@ int hhl_build_ex(const double *A, const double *b, int N, int n_clock, double t,
     return guarded([&] {
         QSIM_REQUIRE(A != nullptr && b != nullptr && out != nullptr, "NULL argument");
         QSIM_REQUIRE(N >= 1 && N <= 4096, "N must be in 1..4096");
-        QSIM_REQUIRE((flags & ~(QSIM_HHL_STRUCTURED_QPE | QSIM_HHL_GAUSS_SEIDEL | QSIM_HHL_DILATE)) == 0,
+        QSIM_REQUIRE((flags & ~(QSIM_HHL_STRUCTURED_QPE | QSIM_HHL_FFT_QFT | QSIM_HHL_GAUSS_SEIDEL | QSIM_HHL_DILATE)) == 0,
                      "unknown flags");
         std::vector<cd> Am = read_complex(A, (size_t)N * N), bv = read_complex(b, N);
         // Sec. III-A step 1(a): Gauss-Seidel preconditioning, M = lower triangle of A (with the
@@ -296,7 +332,7 @@ int hhl_build_spectral_ex(const double *lambda, const double *V, const double *b
     return guarded([&] {
         QSIM_REQUIRE(lambda != nullptr && V != nullptr && b != nullptr && out != nullptr, "NULL argument");
         QSIM_REQUIRE(N >= 1 && N <= 4096, "N must be in 1..4096");
-        QSIM_REQUIRE((flags & ~QSIM_HHL_STRUCTURED_QPE) == 0,
+        QSIM_REQUIRE((flags & ~(QSIM_HHL_STRUCTURED_QPE | QSIM_HHL_FFT_QFT)) == 0,
                      "hhl_build_spectral_ex takes only QSIM_HHL_STRUCTURED_QPE");
         std::vector<double> lam(lambda, lambda + N);
         for (double v : lam) QSIM_REQUIRE(std::isfinite(v), "non-finite eigenvalue");

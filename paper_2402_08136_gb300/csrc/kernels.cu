@@ -438,29 +438,37 @@ __global__ void qpe_phase_kernel(const QpeArgs a) {
     }
 }
 
-// HHL eigenvalue inversion over a contiguous clock register c0..c0+nc-1: for the pair of
-// amplitudes that differ in the ancilla, r = clamp(Cs / k, -1, 1) with k the clock value (two's
-// complement for an indefinite A; r = 0 for k = 0), and
+// HHL eigenvalue inversion: for the pair of amplitudes that differ in the ancilla,
+// r = clamp(Cs / k, -1, 1) with k the clock value (two's complement for an indefinite A; r = 0
+// for k = 0), and
 // (psi0, psi1) <- [[sqrt((1 - |r|)(1 + |r|)), -r], [r, sqrt((1 - |r|)(1 + |r|))]] (psi0, psi1).
+// The clock register may sit in any bit order made of contiguous runs of qubits (the order a
+// Fourier-pass inverse QFT leaves it in): run s holds bits dst[s] .. dst[s] + w[s] - 1 of k
+// on qubits src[s] .. src[s] + w[s] - 1.
+constexpr int kMaxSeg = 8;
 struct InvertArgs {
     void *psi;
     long long count;  // 2^(n-1)
     double Cs;
-    int target, c0, nc;
+    int target, nc;
     int twos;         // clock register read as two's complement (indefinite A)
+    int nseg;
+    int seg_src[kMaxSeg], seg_w[kMaxSeg], seg_dst[kMaxSeg];
 };
 
 template <typename R>
 __global__ void hhl_invert_kernel(const InvertArgs a) {
     using V = typename C2<R>::T;
     V *psi = reinterpret_cast<V *>(a.psi);
-    const unsigned long long tb = 1ull << a.target, vmask = (1ull << a.nc) - 1ull;
+    const unsigned long long tb = 1ull << a.target;
     const R Cs = (R)a.Cs;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.count;
          g += (long long)gridDim.x * blockDim.x) {
         const unsigned long long i0 = (((unsigned long long)g >> a.target) << (a.target + 1)) |
                                       ((unsigned long long)g & (tb - 1ull));
-        const unsigned long long k = (i0 >> a.c0) & vmask;
+        unsigned long long k = 0;
+        for (int sg = 0; sg < a.nseg; sg++)
+            k |= ((i0 >> a.seg_src[sg]) & ((1ull << a.seg_w[sg]) - 1ull)) << a.seg_dst[sg];
         R s = 0, c = 1;
         if (k) {
             const long long ks = (a.twos && (k >> (a.nc - 1))) ? (long long)k - (1ll << a.nc) : (long long)k;
@@ -802,9 +810,17 @@ void run_hhl_invert(void *state, int n, int dtype, const Op &op, cudaStream_t st
     a.Cs = op.tq;
     a.target = op.targets[0];
     a.nc = (int)op.controls.size();
-    a.c0 = op.controls[0];
     a.twos = op.sign == -1 ? 1 : 0;
-    for (int j = 0; j < a.nc; j++) QSIM_REQUIRE(op.controls[j] == a.c0 + j, "inversion register must be contiguous");
+    for (int j = 0; j < a.nc;) {
+        int w = 1;
+        while (j + w < a.nc && op.controls[j + w] == op.controls[j] + w) w++;
+        QSIM_REQUIRE(a.nseg < kMaxSeg, "inversion register: more than 8 runs of consecutive qubits");
+        a.seg_src[a.nseg] = op.controls[j];
+        a.seg_w[a.nseg] = w;
+        a.seg_dst[a.nseg] = j;
+        a.nseg++;
+        j += w;
+    }
     const int grid = grid_for(a.count, 256);
     if (dtype == QSIM_C128) hhl_invert_kernel<double><<<grid, 256, 0, st>>>(a);
     else hhl_invert_kernel<float><<<grid, 256, 0, st>>>(a);
@@ -845,6 +861,12 @@ std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype) {
             align_blob(blob);
             op.dev_off_tc = blob.size();  // second table
             for (const cd &z : hi) put_complex(blob, dtype, z);
+        } else if (op.kind == OP_DFT) {
+            std::vector<cd> W, Tlo, Thi;
+            dft_tables(op, W, Tlo, Thi);
+            for (const cd &z : W) put_complex(blob, dtype, z);
+            for (const cd &z : Tlo) put_complex(blob, dtype, z);
+            for (const cd &z : Thi) put_complex(blob, dtype, z);
         }
     }
     align_blob(blob);
@@ -910,6 +932,7 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream) {
             case OP_UCRY: run_ucry(state, n, dtype, op, dptr, st); break;
             case OP_QPE_PHASE: run_qpe_phase(state, n, dtype, op, dptr, base + op.dev_off_tc, st); break;
             case OP_HHL_INVERT: run_hhl_invert(state, n, dtype, op, st); break;
+            case OP_DFT: run_dft(state, n, dtype, op, dptr, st); break;
         }
     }
 }

@@ -219,3 +219,33 @@ def test_gauss_seidel_and_dilation_host_side(qs):
         qs.hhl_build(np.array([[2.0, 1.0], [0.0, 3.0]]), [1.0, 0.0], 3)        # needs dilate
     d = qs.hhl_build(np.array([[2.0, 1.0], [0.0, 3.0]]), [1.0, 0.0], 3, dilate=True).info()
     assert d["N_eff"] == 4 and d["N"] == 2
+
+
+def test_dft_argument_checks(qs):
+    c = qs.Circuit(8)
+    c.add_dft([4, 5, 6], -1, src=[0, 1, 2, 3])
+    c.add_dft([0, 1], +1, twiddle_first=True)
+    assert c.info()["n_dft"] == 2 and c.info()["n_gates"] == 2
+    for bad in (dict(targets=[], sign=1), dict(targets=[1, 1], sign=1), dict(targets=[12], sign=1),
+                dict(targets=[1, 2], sign=0), dict(targets=[1, 2], sign=1, src=[2]),
+                dict(targets=list(range(11)), sign=1)):
+        with pytest.raises(qs.QsimError):
+            qs.Circuit(12).add_dft(**bad)
+
+
+@pytest.mark.parametrize("m,fields", [(4, 1), (10, 1), (11, 2), (20, 2), (21, 3), (26, 3)])
+def test_fft_qft_pass_counts(qs, m, fields):
+    """QFTs as Fourier passes: one pass per field of at most 10 clock qubits, each way."""
+    rng = np.random.default_rng(m)
+    lam = np.array([1.0, 3.0])
+    V = np.eye(2)
+    b = rng.standard_normal(2)
+    for structured in (False, True):
+        h = qs.hhl_build_spectral(lam, V, b, m, structured=structured, fft_qft=True)
+        ci = h.as_circuit().info()
+        assert ci["n_dft"] == 2 * fields
+        assert ci["n_perm"] == 0
+        g = qs.hhl_build_spectral(lam, V, b, m, structured=structured)
+        assert g.info()["n_gates"] - h.info()["n_gates"] == 2 * (m + m * (m - 1) // 2 + m // 2 - fields)
+    fz = qs.qsim_fuse(h.as_circuit(), 4).info()
+    assert fz["n_dft"] == 2 * fields
