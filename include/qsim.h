@@ -100,6 +100,12 @@ int qsim_circuit_add_ucry(qsim_circuit *c, int target, int n_controls, const int
 int qsim_circuit_add_dft(qsim_circuit *c, int k, const int *targets, int n_src, const int *src, int sign,
                          int twiddle_first);
 
+/* Append H on each of targets[0..k-1] (1 <= k <= 10, distinct): the Walsh-Hadamard transform
+ * out[y'] = 2^{-k/2} sum_y (-1)^{popcount(y & y')} in[y] of the field, run as one pass over the
+ * state like qsim_circuit_add_dft (the Hadamard layers of the phase estimation, Sec. III-A,
+ * Fig. 5).  Errors: EINVAL. */
+int qsim_circuit_add_walsh(qsim_circuit *c, int k, const int *targets);
+
 /* Release a circuit and any device copy of its matrices.  NULL is a no-op. */
 void qsim_circuit_free(qsim_circuit *c);
 
@@ -116,7 +122,7 @@ typedef struct {
     double bytes_c64;   /* algorithmic HBM bytes of one application to a complex64 state     */
     double bytes_c128;  /* same for complex128                                                */
     double flops;       /* algorithmic real flops of one application                          */
-    int n_dft;          /* Fourier-transform passes (qsim_circuit_add_dft)                    */
+    int n_dft;          /* Fourier and Walsh-Hadamard passes (qsim_circuit_add_dft / _walsh)  */
 } qsim_circuit_info;
 
 int qsim_circuit_get_info(const qsim_circuit *c, qsim_circuit_info *out);
@@ -207,10 +213,11 @@ int hhl_build_spectral(const double *lambda, const double *V, const double *b, i
 #define QSIM_HHL_DILATE 4
 /* Emit the inverse QFT and the QFT of the phase estimation as Fourier-transform passes
  * (qsim_circuit_add_dft) over fields of at most 10 clock qubits instead of H, controlled-phase
- * and swap gates: 1 pass for m <= 10, 2 for m <= 20, 3 above.  The inverse QFT leaves the
- * clock value with its digits in field order, the rotation reads it in that order and the QFT
- * consumes it, so no relabelling pass is needed; the final state equals the gate-level
- * circuit's up to rounding. */
+ * and swap gates: 1 pass for m <= 10, 2 for m <= 20, 3 above; and the two Hadamard layers on
+ * the clock as Walsh-Hadamard passes over the same fields (qsim_circuit_add_walsh).  The
+ * inverse QFT leaves the clock value with its digits in field order, the rotation reads it in
+ * that order and the QFT consumes it, so no relabelling pass is needed; the final state equals
+ * the gate-level circuit's up to rounding. */
 #define QSIM_HHL_FFT_QFT 8
 int hhl_build_ex(const double *A, const double *b, int N, int n_clock, double t, double C, int flags,
                  hhl_circuit **out);

@@ -72,6 +72,7 @@ _SIGS = {
     "qsim_circuit_add_ucry": ([_VP, ctypes.c_int, ctypes.c_int, _IP, _DP], ctypes.c_int),
     "qsim_circuit_add_dft": ([_VP, ctypes.c_int, _IP, ctypes.c_int, _IP, ctypes.c_int, ctypes.c_int],
                              ctypes.c_int),
+    "qsim_circuit_add_walsh": ([_VP, ctypes.c_int, _IP], ctypes.c_int),
     "qsim_circuit_free": ([_VP], None),
     "qsim_circuit_get_info": ([_VP, ctypes.POINTER(_CircuitInfo)], ctypes.c_int),
     "qsim_fuse": ([_VP, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
@@ -222,6 +223,12 @@ class Circuit:
         s_, sp = _ints(src)
         _check(library().qsim_circuit_add_dft(self._ptr, len(targets), tp, len(src), sp, int(sign),
                                               1 if twiddle_first else 0))
+        return self
+
+    def add_walsh(self, targets):
+        """H on every target qubit as one Walsh-Hadamard pass (qsim_circuit_add_walsh)."""
+        t, tp = _ints(targets)
+        _check(library().qsim_circuit_add_walsh(self._ptr, len(targets), tp))
         return self
 
     def info(self) -> dict:

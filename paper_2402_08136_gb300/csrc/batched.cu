@@ -445,6 +445,7 @@ bool encode(const Op &op, int dtype, std::vector<unsigned char> &data, BOp &b) {
             return true;
         }
         case OP_DFT:
+        case OP_WALSH:
             return false;
     }
     return false;
@@ -608,7 +609,7 @@ bool batch_supported(const qsim_circuit *c) {
     build_ops(const_cast<qsim_circuit *>(c));
     if (c->n > 30) return false;
     for (const Op &op : c->ops) {
-        if (op.kind == OP_DFT) return false;
+        if (op.kind == OP_DFT || op.kind == OP_WALSH) return false;
         if (op.kind == OP_DENSE && op.targets.size() > 5) return false;
         if (op.kind == OP_DIAG && op.targets.size() > 8) return false;
         if (op.kind == OP_UCRY || op.kind == OP_HHL_INVERT)

@@ -62,7 +62,28 @@ Op classify_dense(const std::vector<int> &targets, const std::vector<int> &contr
         }
     }
     op.kind = OP_DENSE;
-    op.U = U;
+    // canonical order: targets ascending (rows and columns of U relabelled to match), so that
+    // the kernels see contiguous amplitude runs whenever the lowest qubits are targets
+    std::vector<int> perm(k);  // perm[b'] = original matrix bit of sorted position b'
+    for (int b = 0; b < k; b++) perm[b] = b;
+    std::sort(perm.begin(), perm.end(), [&](int x, int y) { return targets[x] < targets[y]; });
+    bool sorted = true;
+    for (int b = 0; b < k; b++) sorted = sorted && perm[b] == b;
+    if (sorted) {
+        op.U = U;
+        return op;
+    }
+    std::vector<int> idx(d);  // sorted-basis index -> original index
+    for (int r = 0; r < d; r++) {
+        int o = 0;
+        for (int b = 0; b < k; b++)
+            if ((r >> b) & 1) o |= 1 << perm[b];
+        idx[r] = o;
+    }
+    for (int b = 0; b < k; b++) op.targets[b] = targets[perm[b]];
+    op.U.resize((size_t)d * d);
+    for (int r = 0; r < d; r++)
+        for (int c = 0; c < d; c++) op.U[(size_t)r * d + c] = U[(size_t)idx[r] * d + idx[c]];
     return op;
 }
 
@@ -76,6 +97,7 @@ void build_ops(qsim_circuit *c) {
             op.kind = g.kind == GATE_UCRY        ? OP_UCRY
                       : g.kind == GATE_QPE_PHASE ? OP_QPE_PHASE
                       : g.kind == GATE_DFT       ? OP_DFT
+                      : g.kind == GATE_WALSH     ? OP_WALSH
                                                  : OP_HHL_INVERT;
             op.targets = g.targets;
             op.controls = g.controls;
@@ -288,6 +310,11 @@ void circuit_info(const qsim_circuit *c, qsim_circuit_info *o) {
                 amps = N;
                 flops = amps * (5.0 * k + (op.controls.empty() ? 2.0 : 8.0));
                 break;
+            case OP_WALSH:  // one complex add or subtract per amplitude and qubit, the scaling
+                o->n_dft++;
+                amps = N;
+                flops = amps * (2.0 * k + 2.0);
+                break;
         }
         o->bytes_c64 += 2.0 * 8.0 * amps;
         o->bytes_c128 += 2.0 * 16.0 * amps;
@@ -384,6 +411,22 @@ int qsim_circuit_add_dft(qsim_circuit *c, int k, const int *targets, int n_src, 
         if (n_src) g.controls.assign(src, src + n_src);
         g.sign = sign;
         g.pre = twiddle_first;
+        std::lock_guard<std::mutex> lk(c->mu);
+        QSIM_REQUIRE(!c->fused, "cannot append to a fused circuit");
+        c->gates.push_back(std::move(g));
+        c->ops_ready = false;
+    });
+}
+
+int qsim_circuit_add_walsh(qsim_circuit *c, int k, const int *targets) {
+    return guarded([&] {
+        QSIM_REQUIRE(c != nullptr && targets != nullptr, "NULL argument");
+        QSIM_REQUIRE(k >= 1 && k <= 10 && k <= c->n, "k must be in 1..10");
+        uint64_t seen = 0;
+        check_qubits(c->n, targets, k, seen, "target");
+        Gate g;
+        g.kind = GATE_WALSH;
+        g.targets.assign(targets, targets + k);
         std::lock_guard<std::mutex> lk(c->mu);
         QSIM_REQUIRE(!c->fused, "cannot append to a fused circuit");
         c->gates.push_back(std::move(g));

@@ -51,7 +51,7 @@ int guarded(F &&f) {
 
 // ---------------------------------------------------------------------------------------
 // Gate list entries (what the user or hhl_build appends).
-enum GateKind { GATE_U = 0, GATE_UCRY = 1, GATE_QPE_PHASE = 2, GATE_HHL_INVERT = 3, GATE_DFT = 4 };
+enum GateKind { GATE_U = 0, GATE_UCRY = 1, GATE_QPE_PHASE = 2, GATE_HHL_INVERT = 3, GATE_DFT = 4, GATE_WALSH = 5 };
 
 struct Gate {
     GateKind kind = GATE_U;
@@ -78,6 +78,7 @@ enum OpKind {
     OP_HHL_INVERT = 6, // HHL inversion rotation: RY(2 asin(clamp(tq / k, -1, 1))) on the target,
                        // k = clock value (two's complement when sign == -1)
     OP_DFT = 7,        // DFT of size 2^k on the targets with a twiddle from the controls
+    OP_WALSH = 8,      // H on every target (Walsh-Hadamard transform of the field), one pass
 };
 
 struct Op {

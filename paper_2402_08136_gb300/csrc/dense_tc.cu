@@ -27,6 +27,16 @@
 // matrices adjacent along K are 128 bytes apart (leading byte offset), adjacent along M/N
 // (K/4) * 128 bytes apart (stride byte offset).
 //
+// Transposed form (TR, 6 targets including qubits 0 and 1): when the targets are the lowest
+// qubits, a group's amplitudes are contiguous but consecutive groups are 2^k amplitudes apart,
+// and the group-major form above reads and writes 8-byte pieces at that stride.  TR computes
+//     Y^T[2D x 128] = B[2D x 2D] * X^T,
+// with B (the real form of U) as the MMA's A operand (M = 2D = 128) and the tile's 128 groups
+// as its B operand (N = 128), chunk by chunk along K as above.  Producers load each group's 16
+// amplitudes of a chunk as 16-byte vectors (a warp reads 8 groups x 64 contiguous bytes), and
+// the accumulator's TMEM lanes are output reals, so the epilogue's warp stores write 32
+// consecutive floats of one group.
+//
 // Every wait on an mbarrier is bounded; on timeout the kernel raises a flag in device memory
 // (read by qsim_device_status), skips the remaining work, releases its tensor memory and exits.
 #include <cuda_runtime.h>
@@ -147,7 +157,7 @@ struct Cfg {
     static constexpr int BBYTES = N * KK * 4;
     static constexpr int ABYTES = kM * kCH * 4;
     static constexpr int NBAR = 2 * kNBuf + 4;  // full/empty per buffer, accfull/accempty x2
-    static constexpr int SMEM = 2 * BBYTES + kNBuf * 2 * ABYTES + 8 * NBAR + 16 + 8 * D;
+    static constexpr int SMEM = 2 * BBYTES + kNBuf * 2 * ABYTES + 8 * NBAR + 16 + 8 * D + 8 * kM;
     static constexpr int TMEM_COLS = 2 * N;  // two accumulators: the MMAs of a tile overlap
                                              // the previous tile's epilogue
     static constexpr unsigned IDESC = (1u << 4)          // D format F32
@@ -167,10 +177,11 @@ constexpr int kMmaWarp = kEpiWarp0 + 4;
 constexpr int kThreadsWS = (kMmaWarp + 1) * 32;
 constexpr int kPrefetch = 6;  // chunks of loads in flight per producer thread
 
-template <int K>
+template <int K, bool TR>
 __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
     using C = Cfg<K>;
     constexpr int D = C::D, N = C::N, KK = C::KK, NCH = C::NCH;
+    static_assert(!TR || N == kM, "the transposed form needs 2D = 128 output reals (6 targets)");
     extern __shared__ __align__(1024) unsigned char sm[];
     float *Bs = reinterpret_cast<float *>(sm);                               // [2][N*KK]
     unsigned char *Aring = sm + 2 * C::BBYTES;                               // [kNBuf][2][ABYTES]
@@ -181,6 +192,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
     uint64_t *accempty = bars + 2 * kNBuf + 2;  // [2] epilogue -> MMA (count 128)
     unsigned *tslot = reinterpret_cast<unsigned *>(bars + C::NBAR);
     long long *toff = reinterpret_cast<long long *>(tslot + 4);              // D entries
+    long long *goff = toff + D;  // kM entries: offset of group m of a tile from the tile's group 0
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // ---- set-up: B into shared memory, target offsets, barriers, tensor memory
@@ -194,6 +206,11 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
                 if ((c >> b) & 1) o |= 1ll << a.targets[b];
             toff[c] = o;
         }
+        // TR epilogue: group index = tile * 128 + m, whose zero-inserted offset splits into the
+        // tile's part and m's part (disjoint bits)
+        if (TR)
+            for (int mm = tid; mm < kM; mm += kThreadsWS)
+                goff[mm] = (long long)insert_zeros((unsigned long long)mm, a.fix, a.nfix);
         if (tid == 0) {
             for (int i = 0; i < kNBuf; i++) {
                 mbar_init(&full[i], kProducers);
@@ -222,6 +239,10 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
     const long long total = ntl * NCH;
     bool failed = false;
 
+    auto tile_base = [&](long long tile_i) -> unsigned long long {
+        const unsigned long long gidx = (unsigned long long)(first + tile_i * stride) * kM;
+        return insert_zeros(gidx, a.fix, a.nfix) | a.cmask;
+    };
     auto group_base = [&](long long tile_i, int m) -> unsigned long long {
         const unsigned long long gidx = (unsigned long long)(first + tile_i * stride) * kM + m;
         return insert_zeros(gidx, a.fix, a.nfix) | a.cmask;
@@ -229,15 +250,34 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
 
     if (warp < kEpiWarp0) {
         // ------------------------------------------------------------------ producers
-        const int m = tid & (kM - 1), h = tid >> 7;  // group row, part of the chunk
-        const int sw = (m >> 3) & 1;  // rows m and m+8 share banks: swap amplitude pairs
+        // Group-major form: thread t owns group row m = t % 128 and quarter h = t / 128 of every
+        // chunk (amplitudes 4h .. 4h+3); rows m and m+8 share banks: every other row block
+        // swaps its amplitude pairs.
+        // TR: thread t owns group row m and amplitude pairs h and h + 4 of every chunk
+        // (amplitudes 2h, 2h+1, 2h+8, 2h+9 of its 16).  A warp is 8 rows x 4 consecutive pairs
+        // (8 runs of 64 bytes per vector load), a quarter-warp 8 rows x 1 pair (16-byte
+        // shared-memory stores into 8 distinct bank slots).
+        const int m = TR ? 8 * (tid >> 5) + (tid & 7) : tid & (kM - 1);
+        const int h = TR ? (tid >> 3) & 3 : tid >> 7;
+        const int sw = TR ? 0 : (m >> 3) & 1;
         float2 r[kPrefetch][kAmpsPT];
         auto load = [&](long long qq, float2(&rr)[kAmpsPT]) {
             if (qq < total) {
-                const unsigned long long gb = group_base(qq / NCH, m);
-                const int c0 = (int)(qq % NCH) * 16 + kAmpsPT * h;
+                if (TR) {  // qubit 0 is a target: each pair is contiguous
+                    const unsigned long long gb = group_base(qq / NCH, m);
+                    const int c0 = (int)(qq % NCH) * 16 + 2 * h;
+                    const float4 u0 = __ldcs(reinterpret_cast<const float4 *>(psi + gb + toff[c0]));
+                    const float4 u1 = __ldcs(reinterpret_cast<const float4 *>(psi + gb + toff[c0 + 8]));
+                    rr[0] = make_float2(u0.x, u0.y);
+                    rr[1] = make_float2(u0.z, u0.w);
+                    rr[2] = make_float2(u1.x, u1.y);
+                    rr[3] = make_float2(u1.z, u1.w);
+                } else {
+                    const unsigned long long gb = group_base(qq / NCH, m);
+                    const int c0 = (int)(qq % NCH) * 16 + kAmpsPT * h;
 #pragma unroll
-                for (int e = 0; e < kAmpsPT; e++) rr[e] = __ldcs(psi + gb + toff[c0 + e]);
+                    for (int e = 0; e < kAmpsPT; e++) rr[e] = __ldcs(psi + gb + toff[c0 + e]);
+                }
             }
         };
 #pragma unroll
@@ -255,16 +295,30 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
                 }
                 unsigned char *ahi = Aring + b * 2 * C::ABYTES;
                 unsigned char *alo = ahi + C::ABYTES;
+                if (TR) {
 #pragma unroll
-                for (int e = 0; e < kAmpsPT; e++) {
-                    const float2 x = sw ? r[p][e ^ 1] : r[p][e];
-                    const int k = 2 * kAmpsPT * h + 2 * (e ^ sw);
-                    const unsigned off = (m >> 3) * 1024 + (k >> 2) * 128 + (m & 7) * 16 + (k & 3) * 4;
-                    const unsigned hx = to_tf32(x.x), hy = to_tf32(x.y);
-                    const unsigned lx = to_tf32(x.x - __uint_as_float(hx));
-                    const unsigned ly = to_tf32(x.y - __uint_as_float(hy));
-                    *reinterpret_cast<uint2 *>(ahi + off) = make_uint2(hx, hy);
-                    *reinterpret_cast<uint2 *>(alo + off) = make_uint2(lx, ly);
+                    for (int pi = 0; pi < 2; pi++) {  // pair h + 4 pi: chunk reals 4h + 16 pi .. +3
+                        const float2 x0 = r[p][2 * pi], x1 = r[p][2 * pi + 1];
+                        const unsigned off = (m >> 3) * 1024 + (h + 4 * pi) * 128 + (m & 7) * 16;
+                        const unsigned h0 = to_tf32(x0.x), h1 = to_tf32(x0.y);
+                        const unsigned h2 = to_tf32(x1.x), h3 = to_tf32(x1.y);
+                        *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(h0, h1, h2, h3);
+                        *reinterpret_cast<uint4 *>(alo + off) =
+                            make_uint4(to_tf32(x0.x - __uint_as_float(h0)), to_tf32(x0.y - __uint_as_float(h1)),
+                                       to_tf32(x1.x - __uint_as_float(h2)), to_tf32(x1.y - __uint_as_float(h3)));
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < kAmpsPT; e++) {
+                        const float2 x = sw ? r[p][e ^ 1] : r[p][e];
+                        const int k = 2 * kAmpsPT * h + 2 * (e ^ sw);
+                        const unsigned off = (m >> 3) * 1024 + (k >> 2) * 128 + (m & 7) * 16 + (k & 3) * 4;
+                        const unsigned hx = to_tf32(x.x), hy = to_tf32(x.y);
+                        const unsigned lx = to_tf32(x.x - __uint_as_float(hx));
+                        const unsigned ly = to_tf32(x.y - __uint_as_float(hy));
+                        *reinterpret_cast<uint2 *>(ahi + off) = make_uint2(hx, hy);
+                        *reinterpret_cast<uint2 *>(alo + off) = make_uint2(lx, ly);
+                    }
                 }
                 load(qq + kPrefetch, r[p]);
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -274,7 +328,9 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
     } else if (warp < kMmaWarp) {
         // ------------------------------------------------------------------ epilogue
         const int sub = warp - kEpiWarp0;         // TMEM lane subpartition
-        const int m = sub * 32 + lane;            // group row == TMEM lane
+        const int m = sub * 32 + lane;            // group row == TMEM lane (TR: output real)
+        const long long ta = TR ? toff[m >> 1] : 0;  // TR: amplitude of output real m
+        float *psif = reinterpret_cast<float *>(a.psi);
         for (long long t = 0; t < ntl && !failed; t++) {
             const int ab = (int)(t & 1);
             if (!mbar_wait(&accfull[ab], (unsigned)((t >> 1) & 1))) {
@@ -282,7 +338,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const unsigned long long gb = group_base(t, m);
+            const unsigned long long gb = TR ? tile_base(t) : group_base(t, m);
             const unsigned acc = tmem + (unsigned)(ab * N) + ((unsigned)(sub * 32) << 16);
 #pragma unroll
             for (int col = 0; col < N; col += 16) {
@@ -294,10 +350,16 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
                       "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                     : "r"(acc + (unsigned)col));
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                if (TR) {  // v[i] = output real m of tile group col + i
 #pragma unroll
-                for (int i = 0; i < 8; i++)
-                    __stcs(psi + gb + toff[col / 2 + i],
-                           make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])));
+                    for (int i = 0; i < 16; i++)
+                        __stcs(psif + 2 * (long long)(gb + goff[col + i] + ta) + (m & 1), __uint_as_float(v[i]));
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; i++)
+                        __stcs(psi + gb + toff[col / 2 + i],
+                               make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])));
+                }
             }
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             mbar_arrive(&accempty[ab]);
@@ -320,8 +382,8 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const unsigned acc = tmem + (unsigned)(ab * N);
             const unsigned a_hi = aring_u32 + b * 2 * C::ABYTES, a_lo = a_hi + C::ABYTES;
+            const unsigned acc = tmem + (unsigned)(ab * N);
 #pragma unroll
             for (int kk = 0; kk < kCH / 8; kk++) {
                 const unsigned aoff = kk * 256;                       // 2 core matrices along K
@@ -330,9 +392,10 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
                 const uint64_t dAl = make_desc(a_lo + aoff, 128, 1024);
                 const uint64_t dBh = make_desc(b_hi + boff, 128, KK * 32);
                 const uint64_t dBl = make_desc(b_lo + boff, 128, KK * 32);
-                mma_tf32(acc, dAh, dBh, C::IDESC, (j == 0 && kk == 0) ? 0u : 1u);
-                mma_tf32(acc, dAh, dBl, C::IDESC, 1u);
-                mma_tf32(acc, dAl, dBh, C::IDESC, 1u);
+                // group-major: D[group][real] = X U^T; TR: D[real][group] = U X^T (M = N = 128)
+                mma_tf32(acc, TR ? dBh : dAh, TR ? dAh : dBh, C::IDESC, (j == 0 && kk == 0) ? 0u : 1u);
+                mma_tf32(acc, TR ? dBl : dAh, TR ? dAh : dBl, C::IDESC, 1u);
+                mma_tf32(acc, TR ? dBh : dAl, TR ? dAl : dBh, C::IDESC, 1u);
             }
             commit_to(&empty[b]);
             if (j == NCH - 1) commit_to(&accfull[ab]);
@@ -394,24 +457,24 @@ void dense_tc_pack(int k, const std::vector<cd> &U, unsigned char *out) {
         }
 }
 
-template <int K>
+template <int K, bool TR>
 static void launch_tc_t(const tc::Args &a, int sms, cudaStream_t st) {
     using C = tc::Cfg<K>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc::dense_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(tc::dense_tc_kernel<K, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_kernel attribute: ") + cudaGetErrorString(e));
         attr = true;
     }
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc::dense_tc_kernel<K>, tc::kThreadsWS, C::SMEM);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc::dense_tc_kernel<K, TR>, tc::kThreadsWS, C::SMEM);
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
         // tensor memory: every resident CTA holds TMEM_COLS of the SM's 512 columns
         per_sm = std::min(per_sm, 512 / C::TMEM_COLS);
     }
     const long long grid = std::min<long long>(a.ntiles, (long long)sms * per_sm);
-    tc::dense_tc_kernel<K><<<(int)grid, tc::kThreadsWS, C::SMEM, st>>>(a);
+    tc::dense_tc_kernel<K, TR><<<(int)grid, tc::kThreadsWS, C::SMEM, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_kernel: ") + cudaGetErrorString(e));
 }
@@ -438,10 +501,12 @@ bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const 
     a.nfix = (int)fix.size();
     for (int i = 0; i < a.nfix; i++) a.fix[i] = fix[i];
     for (int b = 0; b < K; b++) a.targets[b] = targets[b];
+    // targets ascending (canonical order); qubits 0 and 1 among them: transposed form
+    const bool tr = K == 6 && targets[0] == 0 && targets[1] == 1;
     switch (K) {
-        case 4: launch_tc_t<4>(a, sms, st); break;
-        case 5: launch_tc_t<5>(a, sms, st); break;
-        case 6: launch_tc_t<6>(a, sms, st); break;
+        case 4: launch_tc_t<4, false>(a, sms, st); break;
+        case 5: launch_tc_t<5, false>(a, sms, st); break;
+        case 6: tr ? launch_tc_t<6, true>(a, sms, st) : launch_tc_t<6, false>(a, sms, st); break;
         default: return false;
     }
     return true;

@@ -67,10 +67,38 @@ Gate inverse_gate(const Gate &g) {
     if (g.kind == GATE_DFT) {
         r.sign = -g.sign;
         r.pre = 1 - g.pre;
-    } else {
+    } else if (g.kind != GATE_WALSH) {  // a Walsh-Hadamard pass is its own inverse
         r.U = adjoint(g.U);
     }
     return r;
+}
+
+// Fields of at most 10 clock qubits for the Fourier and Walsh-Hadamard passes, top field first:
+// [lo, hi) ranges of register bit positions.
+std::vector<std::pair<int, int>> clock_fields(int m) {
+    std::vector<std::pair<int, int>> f;
+    int rem = m;
+    while (rem > 0) {
+        const int parts = (rem + 9) / 10;
+        const int k = (rem + parts - 1) / parts;
+        f.push_back({rem - k, rem});
+        rem -= k;
+    }
+    return f;
+}
+
+// H on every clock qubit: m Hadamard gates, or one Walsh-Hadamard pass per field.
+void append_hadamards(qsim_circuit &c, const std::vector<int> &q, bool passes) {
+    if (!passes) {
+        for (int x : q) add_u(c, {x}, {}, hadamard());
+        return;
+    }
+    for (const auto &f : clock_fields((int)q.size())) {
+        Gate g;
+        g.kind = GATE_WALSH;
+        g.targets.assign(q.begin() + f.first, q.begin() + f.second);
+        c.gates.push_back(std::move(g));
+    }
 }
 
 // Inverse QFT on `q` as Cooley-Tukey passes (Cooley & Tukey 1965): the DFT of size 2^m with
@@ -80,21 +108,16 @@ Gate inverse_gate(const Gate &g) {
 // qubits.  The result holds the register value v with its digits in field order: the top field
 // carries the lowest digits of v.  Returns that order (bit j of v <-> order[j]).
 std::vector<int> append_iqft_passes(qsim_circuit &c, const std::vector<int> &q) {
-    const int m = (int)q.size();
     std::vector<int> order;
-    int rem = m;
-    while (rem > 0) {
-        const int parts = (rem + 9) / 10;
-        const int k = (rem + parts - 1) / parts;
+    for (const auto &f : clock_fields((int)q.size())) {
         Gate g;
         g.kind = GATE_DFT;
-        g.targets.assign(q.begin() + (rem - k), q.begin() + rem);
-        g.controls.assign(q.begin(), q.begin() + (rem - k));
+        g.targets.assign(q.begin() + f.first, q.begin() + f.second);
+        g.controls.assign(q.begin(), q.begin() + f.first);
         g.sign = -1;
         g.pre = 0;
         c.gates.push_back(g);
         order.insert(order.end(), g.targets.begin(), g.targets.end());
-        rem -= k;
     }
     return order;
 }
@@ -165,8 +188,10 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
     for (int i = 0; i < nb; i++) data[i] = i;
     for (int j = 0; j < m; j++) clock[j] = nb + j;
     const int anc = nb + m;
+    const bool passes = (flags & QSIM_HHL_FFT_QFT) != 0;
     const size_t qpe_begin = c.gates.size();
-    for (int j = 0; j < m; j++) add_u(c, {clock[j]}, {}, hadamard());
+    append_hadamards(c, clock, passes);
+    size_t phase_idx = 0;
     if (flags & QSIM_HHL_STRUCTURED_QPE) {
         // prod_j C_j-U^(2^j) = (I (x) V) diag_c(exp(i lam t c)) (I (x) V^H); the V that would
         // follow is cancelled by the V^H of the uncomputation (nothing in between acts on the data)
@@ -181,6 +206,7 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
         g.theta = lam;
         g.tq = t;
         g.sign = 1;
+        phase_idx = c.gates.size();
         c.gates.push_back(std::move(g));
     } else {
         for (int j = 0; j < m; j++) {
@@ -200,7 +226,7 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
     const size_t iqft_begin = c.gates.size();
     // the rotation reads the clock value in the order the inverse QFT leaves it in
     std::vector<int> clock_order = clock;
-    if (flags & QSIM_HHL_FFT_QFT) clock_order = append_iqft_passes(c, clock);
+    if (passes) clock_order = append_iqft_passes(c, clock);
     else append_iqft(c, clock);
     const size_t qpe_end = c.gates.size();
     // eigenvalue inversion: theta_k = 2 asin(min(1, C / (k step))), theta_0 = 0.  Emitted as a
@@ -218,11 +244,11 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
     // uncompute: inverse of the phase estimation
     if (flags & QSIM_HHL_STRUCTURED_QPE) {
         for (size_t i = qpe_end; i-- > iqft_begin;) c.gates.push_back(inverse_gate(c.gates[i]));  // QFT
-        Gate g = c.gates[qpe_begin + m + 1];  // the phase operator, inverted
+        Gate g = c.gates[phase_idx];  // the phase operator, inverted
         g.sign = -1;
         c.gates.push_back(g);
         add_u(c, data, {}, V);
-        for (int j = 0; j < m; j++) add_u(c, {clock[j]}, {}, hadamard());
+        append_hadamards(c, clock, passes);
     } else {
         for (size_t i = qpe_end; i-- > qpe_begin;) c.gates.push_back(inverse_gate(c.gates[i]));
     }

@@ -499,16 +499,13 @@ struct PrepArgs {
     double b[2 * kMaxParamB];
 };
 
+// After the state has been zeroed (cudaMemsetAsync): write the first min(D, 256) amplitudes.
 template <typename R>
 __global__ void prep_kernel(const PrepArgs a) {
     using V = typename C2<R>::T;
     V *psi = reinterpret_cast<V *>(a.psi);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.N;
-         i += (long long)gridDim.x * blockDim.x) {
-        V v{0, 0};
-        if (i < a.D && i < kMaxParamB) v = V{(R)a.b[2 * i], (R)a.b[2 * i + 1]};
-        psi[i] = v;
-    }
+    const int i = threadIdx.x;
+    if (i < a.D && i < kMaxParamB && i < a.N) psi[i] = V{(R)a.b[2 * i], (R)a.b[2 * i + 1]};
 }
 
 // ---------------------------------------------------------------------------------------
@@ -530,17 +527,54 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return r;  // valid in thread 0
 }
 
+// Partial sums of |psi_i|^2 over contiguous chunks.  complex128: FP64 products and sums.
+// complex64: the FP64 pipe (1/64 of the FP32 rate on this GPU) would bound the pass, so each
+// square x^2 is formed exactly as an FP32 pair (p, e) with p = fl(x^2), e = fma(x, x, -p)
+// (Dekker's product), 16 amplitudes per thread are summed in double-single arithmetic (Knuth's
+// two-sum on the high part, ~48-bit result), and each group sum enters the FP64 accumulator;
+// from there on the reduction is FP64 as for complex128.  The intrinsics keep the compiler from
+// contracting the error-free steps into fused operations.
+__device__ __forceinline__ void ds_add_square(float x, float &hi, float &lo) {
+    const float p = __fmul_rn(x, x);
+    const float e = __fmaf_rn(x, x, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+constexpr int kNormGroup = 16;
+
 template <typename R>
 __global__ void norm_partials_kernel(const void *state, long long chunk, double *partials) {
     using V = typename C2<R>::T;
     __shared__ double sh[32];
     const V *psi = reinterpret_cast<const V *>(state) + (long long)blockIdx.x * chunk;
     double s = 0.0;
-    for (long long i = threadIdx.x; i < chunk; i += blockDim.x) {
-        const V z = psi[i];
-        const double re = (double)z.x, im = (double)z.y;
-        s = fma(re, re, s);
-        s = fma(im, im, s);
+    if (sizeof(R) == 8) {
+        for (long long i = threadIdx.x; i < chunk; i += blockDim.x) {
+            const V z = psi[i];
+            s = fma((double)z.x, (double)z.x, s);
+            s = fma((double)z.y, (double)z.y, s);
+        }
+    } else {
+        const long long span = (long long)blockDim.x * kNormGroup;
+        for (long long i0 = threadIdx.x; i0 < chunk; i0 += span) {
+            V z[kNormGroup];
+#pragma unroll
+            for (int g = 0; g < kNormGroup; g++) {
+                const long long i = i0 + (long long)g * blockDim.x;
+                z[g] = i < chunk ? psi[i] : V{0, 0};
+            }
+            float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+            for (int g = 0; g < kNormGroup; g++) {
+                ds_add_square((float)z[g].x, hi, lo);
+                ds_add_square((float)z[g].y, hi, lo);
+            }
+            s += (double)hi + (double)lo;
+        }
     }
     const double t = block_sum(s, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = t;
@@ -861,7 +895,7 @@ std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype) {
             align_blob(blob);
             op.dev_off_tc = blob.size();  // second table
             for (const cd &z : hi) put_complex(blob, dtype, z);
-        } else if (op.kind == OP_DFT) {
+        } else if (op.kind == OP_DFT || op.kind == OP_WALSH) {
             std::vector<cd> W, Tlo, Thi;
             dft_tables(op, W, Tlo, Thi);
             for (const cd &z : W) put_complex(blob, dtype, z);
@@ -932,7 +966,8 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream) {
             case OP_UCRY: run_ucry(state, n, dtype, op, dptr, st); break;
             case OP_QPE_PHASE: run_qpe_phase(state, n, dtype, op, dptr, base + op.dev_off_tc, st); break;
             case OP_HHL_INVERT: run_hhl_invert(state, n, dtype, op, st); break;
-            case OP_DFT: run_dft(state, n, dtype, op, dptr, st); break;
+            case OP_DFT:
+            case OP_WALSH: run_dft(state, n, dtype, op, dptr, st); break;
         }
     }
 }
@@ -949,9 +984,10 @@ void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb
         a.b[2 * i] = b_pad[i].real();
         a.b[2 * i + 1] = b_pad[i].imag();
     }
-    const int grid = grid_for(a.N, 256);
-    if (dtype == QSIM_C128) prep_kernel<double><<<grid, 256, 0, st>>>(a);
-    else prep_kernel<float><<<grid, 256, 0, st>>>(a);
+    const size_t vbytes = 2 * real_size(dtype);
+    CUDA_OK(cudaMemsetAsync(state, 0, (size_t)a.N * vbytes, st));
+    if (dtype == QSIM_C128) prep_kernel<double><<<1, kMaxParamB, 0, st>>>(a);
+    else prep_kernel<float><<<1, kMaxParamB, 0, st>>>(a);
     check_launch("prep_kernel");
     if (a.D > kMaxParamB) {  // rare: long right-hand sides go through a staged copy
         const int rest = a.D - kMaxParamB;

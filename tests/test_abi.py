@@ -225,7 +225,11 @@ def test_dft_argument_checks(qs):
     c = qs.Circuit(8)
     c.add_dft([4, 5, 6], -1, src=[0, 1, 2, 3])
     c.add_dft([0, 1], +1, twiddle_first=True)
-    assert c.info()["n_dft"] == 2 and c.info()["n_gates"] == 2
+    c.add_walsh([7, 2, 5])
+    assert c.info()["n_dft"] == 3 and c.info()["n_gates"] == 3
+    for bad in ([], [1, 1], [12], list(range(11))):
+        with pytest.raises(qs.QsimError):
+            qs.Circuit(12).add_walsh(bad)
     for bad in (dict(targets=[], sign=1), dict(targets=[1, 1], sign=1), dict(targets=[12], sign=1),
                 dict(targets=[1, 2], sign=0), dict(targets=[1, 2], sign=1, src=[2]),
                 dict(targets=list(range(11)), sign=1)):
@@ -243,9 +247,10 @@ def test_fft_qft_pass_counts(qs, m, fields):
     for structured in (False, True):
         h = qs.hhl_build_spectral(lam, V, b, m, structured=structured, fft_qft=True)
         ci = h.as_circuit().info()
-        assert ci["n_dft"] == 2 * fields
+        assert ci["n_dft"] == 4 * fields          # inverse QFT, QFT and the two Hadamard layers
         assert ci["n_perm"] == 0
         g = qs.hhl_build_spectral(lam, V, b, m, structured=structured)
-        assert g.info()["n_gates"] - h.info()["n_gates"] == 2 * (m + m * (m - 1) // 2 + m // 2 - fields)
+        iqft = m + m * (m - 1) // 2 + m // 2
+        assert g.info()["n_gates"] - h.info()["n_gates"] == 2 * (iqft + m) - 4 * fields
     fz = qs.qsim_fuse(h.as_circuit(), 4).info()
-    assert fz["n_dft"] == 2 * fields
+    assert fz["n_dft"] == 4 * fields

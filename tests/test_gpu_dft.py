@@ -16,6 +16,7 @@ import pytest
 import torch
 
 import synth
+from oracle import core as ocore
 from oracle import hhl as ohhl
 from test_gpu_parity import (DTYPES, TOL, _indefinite, _oracle_spectral, check, compare_hhl, cond_tol,
                              dev_state, host_input, run_product_hhl)
@@ -90,7 +91,7 @@ def test_dft_passes_compose_to_qft_and_back(qs, dtype):
 def test_hhl7_fft_qft_exact_grid(qs, dtype, structured, max_k):
     p = synth.hhl7_problem()
     h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"], structured=structured, fft_qft=True)
-    assert h.as_circuit().info()["n_dft"] == 2
+    assert h.as_circuit().info()["n_dft"] == 4
     ref = ohhl.solve(p["A"], p["b"], p["m"], p["t"], p["C"])
     st, r = run_product_hhl(qs, h, dtype, max_k)
     compare_hhl(st, r, ref, dtype, TOL[dtype])
@@ -129,7 +130,7 @@ def test_hhl_fft_qft_two_and_three_fields(qs, dtype, N, m, structured):
     the clock value in field order and the QFT back restores the natural order."""
     lam, V, b, t, C, ref = _spectral_case(N, m, 21)
     h = qs.hhl_build_spectral(lam, V, b, m, t, C, structured=structured, fft_qft=True)
-    assert h.as_circuit().info()["n_dft"] == 2 * ((m + 9) // 10)
+    assert h.as_circuit().info()["n_dft"] == 4 * ((m + 9) // 10)
     st, r = run_product_hhl(qs, h, dtype, 4)
     compare_hhl(st, r, ref, dtype, 1e-12 if dtype == torch.complex128 else TOL[dtype])
 
@@ -157,3 +158,25 @@ def test_hhl_fft_qft_dilated(qs, dtype):
     ref = ohhl.solve_general(A, b, m)
     st, r = run_product_hhl(qs, h, dtype, 3)
     compare_hhl(st, r, ref, dtype, cond_tol(m) if dtype == torch.complex128 else TOL[dtype])
+
+
+# (n, field): H on every field qubit as one Walsh-Hadamard pass
+WALSH = [(14, list(range(3, 13))), (12, [0, 1, 2]), (13, [2, 7, 5, 11]), (6, list(range(6))),
+         (16, list(range(6, 15))), (9, [8])]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("case", list(range(len(WALSH))))
+def test_walsh_pass_parity(qs, dtype, case):
+    n, field = WALSH[case]
+    psi = synth.gaussian_state_np(700 + case, n)
+    x0 = host_input(psi, dtype)
+    ref = x0.copy()
+    for q in field:
+        ocore.apply_gate(ref, [q], ohhl.H)
+    c = qs.Circuit(n)
+    c.add_walsh(field)
+    st = dev_state(x0, dtype)
+    qs.qsim_apply(st, c)
+    torch.cuda.synchronize()
+    check(st, ref, dtype)

@@ -106,6 +106,33 @@ def test_tensor_core_dense_parity_complex64(qs, k):
     check(st, ref, torch.complex64)
 
 
+@pytest.mark.parametrize("k", [4, 5, 6])
+def test_tensor_core_low_target_layouts(qs, k):
+    """Gates whose targets include qubits 0 and 1 (vector loads across a group's amplitudes,
+    shuffle-transposed stores), in any given order, with scattered upper targets and controls;
+    and gates with qubit 0 but not qubit 1 (the group-major layout)."""
+    rng = np.random.default_rng(900 + k)
+    n = 19
+    psi = host_input(synth.gaussian_state_np(900 + k, n), torch.complex64)
+    c = qs.Circuit(n)
+    ref = psi.copy()
+    up = [int(q) for q in rng.permutation(range(2, n))]
+    cases = [([1, 0] + up[:k - 2], []),
+             (up[:k - 2][::-1] + [0, 1], [up[k]]),
+             (list(range(k)), [n - 1, n - 2]),
+             ([0] + up[:k - 1], []),
+             ([1] + up[:k - 1], [0])]
+    for t, ctl in cases:
+        U = synth.haar_unitary(rng, 1 << k)
+        c.add_gate(t, U, ctl)
+        ocore.apply_gate(ref, t, U, ctl)
+    st = dev_state(psi, torch.complex64)
+    qs.qsim_apply(st, c)
+    torch.cuda.synchronize()
+    assert qs.qsim_device_status() == 0
+    check(st, ref, torch.complex64)
+
+
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_control_on_low_qubits_and_small_states(qs, dtype):
     rng = np.random.default_rng(7)
@@ -360,6 +387,27 @@ def _oracle_spectral(lam, V, b, m, t, C):
     out = ohhl.readout(h, psi)
     out["psi"] = psi
     return out
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [7, 16, 23])
+def test_readout_sums_match_compensated_fp64(qs, dtype, n):
+    """||psi||^2, P(ancilla = 1) and P(ancilla = 1, clock = 0) of an arbitrary state against the
+    oracle's compensated FP64 sums of the same (rounded) amplitudes: relative 1e-13 for both
+    dtypes (complex64 squares are formed exactly and summed in double-single groups)."""
+    m = n - 2
+    h = qs.hhl_build_spectral([1.0, 3.0], np.eye(2), [1.0, 0.5], m)
+    psi = synth.gaussian_state_np(40 + n, n)
+    psi[::7] *= 1e-6                                  # a wide dynamic range
+    psi = host_input(psi, dtype)
+    st = dev_state(psi, dtype)
+    r = qs.hhl_readout(st, h)
+    anc = 1 << (n - 1)
+    clock = ((1 << m) - 1) << 1
+    want = {"norm2": ocore.masked_norm2(psi, 0, 0), "p_success": ocore.masked_norm2(psi, anc, anc),
+            "p_clock0": ocore.masked_norm2(psi, anc | clock, anc)}
+    for key, v in want.items():
+        assert abs(r[key] - v) <= 1e-13 * v, (key, r[key], v)
 
 
 # --------------------------------------------------------------- full-size sampled checks
