@@ -72,6 +72,26 @@ void run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
     L = std::max(L, 0);
     unsigned long long fmask = 0;
     for (int q : op.targets) fmask |= 1ull << q;
+    // staged input (complex64): the lanes must be qubits 0..L-1 (16-byte runs) and two input
+    // tiles must fit beside the exchange buffer; the lane count drops until they do
+    {
+        // opt-in: with one 256-thread CTA per SM the transform work is exposed, and the
+        // measured passes were slower than the unstaged kernel
+        const char *e = std::getenv("QSIM_DFT_STAGE");
+        const bool allow = dtype == QSIM_C64 && e && e[0] == '1';
+        int Ls = L;
+        auto smem_for = [&](int l, bool st) {
+            const size_t tile = (size_t)1 << (K + l);
+            return vb * ((st ? 2 * tile : 0) + ((size_t)1 << K) + tile + ((size_t)1 << k1 << l)) +
+                   8 * (((size_t)1 << k1) + ((size_t)1 << (K - k1)) + ((size_t)1 << l));
+        };
+        while (Ls > 1 && smem_for(Ls, true) > 220 * 1024) Ls--;
+        const bool lanes_low = (fmask & ((1ull << Ls) - 1ull)) == 0;
+        if (allow && lanes_low && Ls >= 1 && smem_for(Ls, true) <= 220 * 1024 && ((size_t)vb << Ls) >= 16) {
+            a.stage = 1;
+            L = Ls;
+        }
+    }
     std::vector<int> fix(op.targets.begin(), op.targets.end());
     int cnt = 0;
     for (int q = 0; q < n && cnt < L; q++)
@@ -86,8 +106,15 @@ void run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
     a.ntiles = 1ll << (n - K - L);
     const int N1 = 1 << k1, N2 = 1 << (K - k1), NL = 1 << L;
     const int threads = N1 << L;
-    const size_t smem = vb * (((size_t)1 << K) + ((size_t)1 << (K + L)) + (size_t)N1 * NL) +
-                        8 * ((size_t)N1 + N2 + NL);
+    size_t smem = vb * ((a.stage ? 2 * ((size_t)1 << (K + L)) : 0) + ((size_t)1 << K) +
+                        ((size_t)1 << (K + L)) + (size_t)N1 * NL) +
+                  8 * ((size_t)N1 + N2 + NL + ((N1 + N2 + NL) & 1));
+    // twiddle tables in shared memory when they fit (they are read once per amplitude)
+    const size_t tw_bytes = vb * (((size_t)1 << hT) + ((size_t)1 << (K + ns - hT)));
+    if (ns > 0 && smem + tw_bytes <= 200 * 1024) {
+        a.tw_smem = 1;
+        smem += tw_bytes;
+    }
     bool contig = true;
     for (int j = 0; j < K; j++) contig = contig && op.targets[j] == op.targets[0] + j;
     a.f0 = op.targets[0];

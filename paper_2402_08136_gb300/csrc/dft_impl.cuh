@@ -72,6 +72,9 @@ struct DftArgs {
     int twmode;       // 0 no twiddle, 1 before the transform, 2 after
     int hT, ns, nfix;
     int f0;                     // lowest field qubit (contiguous field: bit j on qubit f0 + j)
+    int stage;                  // 1: the lanes are qubits 0..L-1 and each tile's input is
+                                // prefetched into shared memory (cp.async, double buffer)
+    int tw_smem;                // 1: the twiddle tables Tlo, Thi are copied to shared memory
     int fpos[kMaxK];            // qubit of field bit j
     int lpos[kMaxLane];         // qubit of lane bit j
     int spos[kMaxSrc];          // qubit of twiddle-source bit j
@@ -146,6 +149,14 @@ template <> __device__ __forceinline__ double2 tw32<double2>(int e, int sgn) {
     return make_double2(kTw32.re[e], sgn > 0 ? -kTw32.im[e] : kTw32.im[e]);
 }
 
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 __host__ __device__ constexpr int bitrev(int i, int bits) {
     int r = 0;
     for (int b = 0; b < bits; b++) r |= ((i >> b) & 1) << (bits - 1 - b);
@@ -210,13 +221,19 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
     const int L = a.L, NL = 1 << L;
     const int nthr = N1 << L;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V *Ws = reinterpret_cast<V *>(smem_raw);
+    // [input stages x2 (if staged)] [W] [S] [offset tables]
+    V *stages = reinterpret_cast<V *>(smem_raw);
+    const int tile_elems = KN << L;
+    V *Ws = stages + (a.stage ? 2 * tile_elems : 0);
     V *S = Ws + KN;
     // S: block of output digit a at a N1 2^L + (a / RR) 2^L: the 2^L-element gap between the
     // blocks of consecutive thread groups spreads pass 2's reads over the banks
     long long *fo_lo = reinterpret_cast<long long *>(S + (KN << L) + N1 * NL);
     long long *fo_hi = fo_lo + N1;
     long long *lane_off = fo_hi + N2;
+    // twiddle tables after the offset tables, padded to a 16-byte boundary
+    V *Tsm = reinterpret_cast<V *>(lane_off + NL + ((N1 + N2 + NL) & 1));
+    const int ntlo = 1 << a.hT, nthi = 1 << (K + a.ns - a.hT);
 
     const int tid = threadIdx.x;
     const V *Wg = reinterpret_cast<const V *>(a.W);
@@ -240,6 +257,11 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
             if ((i >> b) & 1) o |= 1ll << a.lpos[b];
         lane_off[i] = o;
     }
+    if (a.tw_smem) {
+        const V *tg = reinterpret_cast<const V *>(a.Tlo), *th = reinterpret_cast<const V *>(a.Thi);
+        for (int i = tid; i < ntlo; i += nthr) Tsm[i] = tg[i];
+        for (int i = tid; i < nthi; i += nthr) Tsm[ntlo + i] = th[i];
+    }
     __syncthreads();
 
     // offsets are re-read from shared memory at every use: kept in registers across the tile
@@ -249,19 +271,45 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
     const int l = tid & (NL - 1);
     const int u = tid >> L;  // pass 1: low field digit; pass 2: group of output digits a
     const int pad2 = u * NL;
-    const V *Tlo = reinterpret_cast<const V *>(a.Tlo);
-    const V *Thi = reinterpret_cast<const V *>(a.Thi);
+    const V *Tlo = a.tw_smem ? Tsm : reinterpret_cast<const V *>(a.Tlo);
+    const V *Thi = a.tw_smem ? Tsm + ntlo : reinterpret_cast<const V *>(a.Thi);
     const unsigned tmask = (1u << a.hT) - 1u;
     const R scale = (R)a.scale;
     V *psi = reinterpret_cast<V *>(a.psi);
     V x[N2];
 
-    for (long long tix = blockIdx.x; tix < a.ntiles; tix += gridDim.x) {
+    // staged input: tile tix lands in stages[(it & 1)] as [field value y][lane], 16-byte
+    // chunks of the contiguous lane runs; the next tile's copies fly during this tile's work
+    constexpr int EPC = 16 / (int)sizeof(V);  // amplitudes per 16-byte chunk
+    auto issue = [&](long long tix, V *dst) {
+        if (tix < a.ntiles) {
+            const unsigned long long tb = insert_zero_bits((unsigned long long)tix, a.fix, a.nfix);
+            const int cpr_log = L - (sizeof(V) == 8 ? 1 : 0);  // log2 of chunks per lane run
+            for (int c = tid; c < (KN << cpr_log); c += nthr) {
+                const int y = c >> cpr_log, part = c & ((1 << cpr_log) - 1);
+                const long long fo = CONTIG ? (long long)((unsigned long long)y << a.f0) : vlo[y & (N1 - 1)] + vhi[y >> k1];
+                cp_async16(dst + y * NL + part * EPC, psi + tb + fo + part * EPC);
+            }
+        }
+        cp_async_commit();
+    };
+    if (a.stage) issue(blockIdx.x, stages);
+    int it = 0;
+    for (long long tix = blockIdx.x; tix < a.ntiles; tix += gridDim.x, it++) {
         const unsigned long long base = insert_zero_bits((unsigned long long)tix, a.fix, a.nfix) + lane_off[l];
         unsigned w = 0;
         for (int j = 0; j < a.ns; j++) w |= (unsigned)((base >> a.spos[j]) & 1ull) << j;
         // pass 1
-        if (CONTIG) {
+        if (a.stage) {
+            // the buffer refilled now was read by the previous tile's pass 1, which every thread
+            // finished before that tile's barrier
+            issue(tix + gridDim.x, stages + ((it + 1) & 1) * tile_elems);
+            cp_async_wait<1>();
+            __syncthreads();
+            const V *cur = stages + (it & 1) * tile_elems;
+#pragma unroll
+            for (int v = 0; v < N2; v++) x[v] = cur[((u + N1 * v) << L) + l];
+        } else if (CONTIG) {
             const V *src = psi + base + ((unsigned long long)u << a.f0);
             const long long step = 1ll << (a.f0 + k1);
 #pragma unroll
@@ -310,6 +358,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
         }
         __syncthreads();  // S is rewritten by the next tile's pass 1
     }
+    if (a.stage) cp_async_wait<0>();
 }
 
 inline int num_sms_dft() {
