@@ -327,7 +327,8 @@ typedef struct {
     int n_clock;     /* as hhl_build                                                           */
     double t, C;     /* as hhl_build                                                           */
     int dtype;       /* QSIM_C64 or QSIM_C128 state                                            */
-    int flags;       /* hhl_build_ex flags (QSIM_HHL_STRUCTURED_QPE, QSIM_HHL_FFT_QFT, ...)     */
+    int flags;       /* hhl_build_ex flags (QSIM_HHL_STRUCTURED_QPE, ...; the pool adds      */
+                     /* QSIM_HHL_FFT_QFT)                                                      */
 } hhl_request;
 
 typedef struct {
@@ -342,8 +343,8 @@ typedef struct {
  * room for its state (8 * 2^n bytes for complex64, 16 * 2^n for complex128) and a stream is
  * free.  Requests of at most 16 qubits that the batched executor supports (dense gates of at
  * most 5 targets) and that are ready together run as one batched launch; the others run alone
- * with the full-GPU kernels, their QFTs as Fourier passes (QSIM_HHL_FFT_QFT is added for them);
- * launches on different streams overlap.
+ * with the full-GPU kernels; launches on different streams overlap.  Every request is built
+ * with QSIM_HHL_FFT_QFT added (the QFTs and clock Hadamard layers as passes).
  * Results equal those of the same request run alone (each circuit's arithmetic does not
  * depend on its batch).  Errors: EINVAL, ENOMEM, ECUDA. */
 int qsim_pool_create(size_t bytes, int n_builders, int n_streams, qsim_pool **out);

@@ -30,10 +30,16 @@ namespace batch {
 // global memory), 256 for complex128 (register budget of the 5-target dense gate)
 template <typename V> struct Threads { static constexpr int n = sizeof(V) == 8 ? 512 : 256; };
 
-enum BKind : unsigned char { B_DENSE = 0, B_PHASE = 1, B_DIAG = 2, B_SWAP = 3, B_UCRY = 4, B_QPE = 5, B_INVERT = 6 };
+enum BKind : unsigned char {
+    B_DENSE = 0, B_PHASE = 1, B_DIAG = 2, B_SWAP = 3, B_UCRY = 4, B_QPE = 5, B_INVERT = 6,
+    B_DFT = 7,    // DFT over the contiguous field c0 .. c0+k-1; t[0] twiddle-source start, nreg its
+                  // width, t[1] twiddle mode (0 none, 1 before, 2 after), t[2] sign, t[3] table split
+    B_WALSH = 8,  // H on every qubit of the contiguous field c0 .. c0+k-1
+};
 
 struct BOp {
-    unsigned char kind, k, c0, nreg;  // c0 / nreg: UCRY control register (contiguous)
+    unsigned char kind, k, c0, nreg;  // c0 / nreg: UCRY control register (contiguous);
+                                      // B_INVERT: t[1] = rotation of that register
     signed char t[8];                 // targets in matrix-bit order (UCRY: t[0] = target)
     unsigned fixmask;                 // targets | controls (zero bits inserted when enumerating)
     unsigned cmask;                   // controls that must be 1 (PHASE: all its qubits)
@@ -118,6 +124,68 @@ __device__ __forceinline__ V cmulb(V a, V b) {
     return r;
 }
 
+// Fourier (DFT) or Walsh-Hadamard transform of the contiguous field f0 .. f0+K-1 inside one
+// circuit: K radix-2 decimation-in-frequency stages (stage j pairs the amplitudes that differ
+// in field bit j; the DFT multiplies the difference by exp(s 2 pi i r / 2^(j+1)), r = the field
+// bits below j, from the table W[e] = exp(s 2 pi i e / 2^K), e = r 2^(K-1-j)), a barrier after
+// each, then one pass that undoes the digit reversal of the DFT, scales by 2^(-K/2) and
+// applies the output twiddle.  The input twiddle, if any, is a pass of its own first.
+template <typename V>
+__device__ void op_fourier(V *psi, int n, const BOp &op, const V *data, int tid, bool walsh) {
+    constexpr int NT = Threads<V>::n;
+    using Rr = decltype(V{}.x);
+    const int K = op.k, f0 = op.c0;
+    const unsigned N = 1u << n, fmask = ((1u << K) - 1u) << f0;
+    const V *W = data + op.data;
+    const int twmode = walsh ? 0 : op.t[1];
+    const int ns = op.nreg, s0 = op.t[0], hT = op.t[3];
+    const V *Tlo = data + op.data2, *Thi = Tlo + (1u << hT);
+    const unsigned smask = (1u << ns) - 1u, tmask = (1u << hT) - 1u;
+    auto tw = [&](unsigned i, unsigned y) -> V {  // exp(s 2 pi i w y / 2^(K+ns))
+        const unsigned q = ((i >> s0) & smask) * y;
+        return cmulb(Tlo[q & tmask], Thi[q >> hT]);
+    };
+    if (twmode == 1) {
+        for (unsigned i = tid; i < N; i += NT) psi[i] = cmulb(psi[i], tw(i, (i & fmask) >> f0));
+        __syncthreads();
+    }
+    for (int j = K - 1; j >= 0; j--) {
+        const int p = f0 + j;
+        const unsigned bit = 1u << p, rmask = (1u << j) - 1u;
+        for (unsigned g = tid; g < N / 2; g += NT) {
+            const unsigned i0 = ((g >> p) << (p + 1)) | (g & (bit - 1u));
+            const V a = psi[i0], b = psi[i0 | bit];
+            V d;
+            d.x = a.x - b.x;
+            d.y = a.y - b.y;
+            psi[i0] = V{a.x + b.x, a.y + b.y};
+            if (!walsh) {
+                const unsigned r = (i0 >> f0) & rmask;
+                if (r) d = cmulb(d, W[r << (K - 1 - j)]);
+            }
+            psi[i0 | bit] = d;
+        }
+        __syncthreads();
+    }
+    const Rr scale = (K & 1) ? (Rr)(0.70710678118654752440 / (double)(1u << (K / 2))) : (Rr)(1.0 / (double)(1u << (K / 2)));
+    for (unsigned i = tid; i < N; i += NT) {
+        const unsigned y = (i & fmask) >> f0;
+        const unsigned yr = walsh ? y : (__brev(y) >> (32 - K));
+        if (yr < y) continue;  // the pair (y, yr) belongs to the thread that holds the smaller one
+        const unsigned rest = i & ~fmask, ir = rest | (yr << f0);
+        V u = psi[i], v = psi[ir];  // position p holds output bitrev(p)
+        V out_y = walsh ? u : v, out_r = walsh ? v : u;
+        out_y.x *= scale; out_y.y *= scale;
+        out_r.x *= scale; out_r.y *= scale;
+        if (twmode == 2) {
+            out_y = cmulb(out_y, tw(i, y));
+            if (ir != i) out_r = cmulb(out_r, tw(ir, yr));
+        }
+        psi[i] = out_y;
+        if (ir != i) psi[ir] = out_r;
+    }
+}
+
 template <typename R>
 __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typename C2<R>::T *data, int tid) {
     using V = typename C2<R>::T;
@@ -183,15 +251,17 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
             break;
         }
         case B_INVERT: {  // HHL inversion: rotation from Cs / k (data holds (Cs, 0); op.k = 1:
-                          // two's-complement clock register)
+                          // two's-complement clock register; t[1] = rot: the register's low rot
+                          // qubits hold the top digits of k, as Fourier passes leave it)
             const unsigned cnt = 1u << (n - 1);
-            const int tq = op.t[0];
+            const int tq = op.t[0], rot = op.t[1];
             const unsigned tb = 1u << tq, vmask = (1u << op.nreg) - 1u;
             using Rr = decltype(V{}.x);
             const Rr Cs = d[0].x;
             for (unsigned g = tid; g < cnt; g += kThreads) {
                 const unsigned i0 = ((g >> tq) << (tq + 1)) | (g & (tb - 1u));
-                const unsigned k = (i0 >> op.c0) & vmask;
+                const unsigned raw = (i0 >> op.c0) & vmask;
+                const unsigned k = rot ? ((raw >> rot) | ((raw & ((1u << rot) - 1u)) << (op.nreg - rot))) : raw;
                 Rr s = 0, c = 1;
                 if (k) {
                     const int ks = (op.k && (k >> (op.nreg - 1))) ? (int)k - (1 << op.nreg) : (int)k;
@@ -212,6 +282,8 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
             }
             break;
         }
+        case B_DFT: op_fourier<V>(psi, n, op, data, tid, false); break;
+        case B_WALSH: op_fourier<V>(psi, n, op, data, tid, true); break;
         case B_QPE: {  // data qubits 0..k-1, clock register k..k+nreg-1, split at c0 bits
             const V *hi = data + op.data2;
             const unsigned N = 1u << n, dmask = (1u << op.k) - 1u, cm = (1u << op.nreg) - 1u;
@@ -357,6 +429,26 @@ void put_v(std::vector<unsigned char> &blob, int dtype, const cd &z) {
 
 size_t vbytes(int dtype) { return dtype == QSIM_C128 ? 16 : 8; }
 
+// Rotation r of a register given bit by bit: controls[j] = c0 + ((j + r) mod nc) with c0 the
+// lowest qubit; -1 if the list is not a rotated contiguous register.
+int register_rotation(const std::vector<int> &controls) {
+    const int nc = (int)controls.size();
+    if (nc == 0) return -1;
+    const int c0 = *std::min_element(controls.begin(), controls.end());
+    for (int r = 0; r < nc; r++) {
+        bool ok = true;
+        for (int j = 0; j < nc && ok; j++) ok = controls[j] == c0 + (j + r) % nc;
+        if (ok) return r;
+    }
+    return -1;
+}
+
+bool contiguous_ascending(const std::vector<int> &q) {
+    for (size_t j = 1; j < q.size(); j++)
+        if (q[j] != q[0] + (int)j) return false;
+    return true;
+}
+
 unsigned maskq(const std::vector<int> &q) {
     unsigned m = 0;
     for (int x : q) m |= 1u << x;
@@ -416,12 +508,13 @@ bool encode(const Op &op, int dtype, std::vector<unsigned char> &data, BOp &b) {
         }
         case OP_HHL_INVERT: {
             const int nc = (int)op.controls.size();
-            for (int j = 1; j < nc; j++)
-                if (op.controls[j] != op.controls[0] + j) return false;
+            const int rot = register_rotation(op.controls);
+            if (rot < 0) return false;
             b.kind = batch::B_INVERT;
             b.k = op.sign == -1 ? 1 : 0;
             b.t[0] = (signed char)op.targets[0];
-            b.c0 = (unsigned char)op.controls[0];
+            b.t[1] = (signed char)rot;
+            b.c0 = (unsigned char)*std::min_element(op.controls.begin(), op.controls.end());
             b.nreg = (unsigned char)nc;
             put_v(data, dtype, cd(op.tq, 0.0));
             return true;
@@ -444,9 +537,35 @@ bool encode(const Op &op, int dtype, std::vector<unsigned char> &data, BOp &b) {
             for (const cd &z : hi) put_v(data, dtype, z);
             return true;
         }
-        case OP_DFT:
-        case OP_WALSH:
-            return false;
+        case OP_DFT: {
+            const int K = (int)op.targets.size(), ns = (int)op.controls.size();
+            if (K > 10 || K + ns > 20 || !contiguous_ascending(op.targets) || !contiguous_ascending(op.controls))
+                return false;
+            std::vector<cd> W, Tlo, Thi;
+            dft_tables(op, W, Tlo, Thi);
+            b.kind = batch::B_DFT;
+            b.k = (unsigned char)K;
+            b.c0 = (unsigned char)op.targets[0];
+            b.nreg = (unsigned char)ns;
+            b.t[0] = (signed char)(ns ? op.controls[0] : 0);
+            b.t[1] = (signed char)(ns == 0 ? 0 : (op.pre ? 1 : 2));
+            b.t[2] = (signed char)op.sign;
+            b.t[3] = (signed char)((K + ns) / 2);  // the split dft_tables uses
+            for (const cd &z : W) put_v(data, dtype, z);
+            b.data2 = (unsigned)(data.size() / vbytes(dtype));
+            for (const cd &z : Tlo) put_v(data, dtype, z);
+            for (const cd &z : Thi) put_v(data, dtype, z);
+            return true;
+        }
+        case OP_WALSH: {
+            std::vector<int> q = op.targets;
+            std::sort(q.begin(), q.end());
+            if (q.size() > 10 || !contiguous_ascending(q)) return false;
+            b.kind = batch::B_WALSH;
+            b.k = (unsigned char)q.size();
+            b.c0 = (unsigned char)q[0];
+            return true;
+        }
     }
     return false;
 }
@@ -609,12 +728,19 @@ bool batch_supported(const qsim_circuit *c) {
     build_ops(const_cast<qsim_circuit *>(c));
     if (c->n > 30) return false;
     for (const Op &op : c->ops) {
-        if (op.kind == OP_DFT || op.kind == OP_WALSH) return false;
+        if (op.kind == OP_DFT &&
+            (op.targets.size() > 10 || op.targets.size() + op.controls.size() > 20 ||
+             !contiguous_ascending(op.targets) || !contiguous_ascending(op.controls)))
+            return false;
+        if (op.kind == OP_WALSH) {
+            std::vector<int> q = op.targets;
+            std::sort(q.begin(), q.end());
+            if (q.size() > 10 || !contiguous_ascending(q)) return false;
+        }
         if (op.kind == OP_DENSE && op.targets.size() > 5) return false;
         if (op.kind == OP_DIAG && op.targets.size() > 8) return false;
-        if (op.kind == OP_UCRY || op.kind == OP_HHL_INVERT)
-            for (size_t j = 1; j < op.controls.size(); j++)
-                if (op.controls[j] != op.controls[0] + (int)j) return false;
+        if (op.kind == OP_UCRY && !contiguous_ascending(op.controls)) return false;
+        if (op.kind == OP_HHL_INVERT && register_rotation(op.controls) < 0) return false;
         if (op.kind == OP_QPE_PHASE) {
             for (size_t i = 0; i < op.targets.size(); i++)
                 if (op.targets[i] != (int)i) return false;

@@ -173,14 +173,10 @@ void builder_loop(qsim_pool *p) {
             p->submitted.pop_front();
             p->n_building++;
         }
-        int rc = hhl_build_ex(r->A.data(), r->b.data(), r->N, r->n_clock, r->t, r->C, r->flags, &r->h);
-        if (rc == QSIM_OK && r->h->n > p->small_n && !(r->flags & QSIM_HHL_FFT_QFT)) {
-            // too large for the batched executor: the QFTs run as Fourier passes instead
-            hhl_circuit_free(r->h);
-            r->h = nullptr;
-            rc = hhl_build_ex(r->A.data(), r->b.data(), r->N, r->n_clock, r->t, r->C,
+        // QFTs and clock Hadamard layers as passes: both executors run them, and they replace
+        // O(m^2) gates by O(m / 10) state passes
+        int rc = hhl_build_ex(r->A.data(), r->b.data(), r->N, r->n_clock, r->t, r->C,
                               r->flags | QSIM_HHL_FFT_QFT, &r->h);
-        }
         std::string msg = rc == QSIM_OK ? "" : qsim_last_error();
         if (rc == QSIM_OK) {
             r->n = r->h->n;

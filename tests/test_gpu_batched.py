@@ -187,3 +187,65 @@ def test_batch_rejects_wide_dense_gate(qs):
         qs._binding._check(qs._binding.library().qsim_batch_create(arr_c, arr_s, 1, qs.QSIM_C64,
                                                                    ctypes.byref(p)))
     assert "max_k <= 5" in str(e.value)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_batched_fourier_and_walsh_passes_match_oracle(qs, dtype, cuda_device):
+    """Fourier passes (contiguous fields, twiddle before / after / none) and Walsh-Hadamard
+    passes inside the batched executor, states in shared memory (n = 11) and in place (n = 16),
+    vs the oracle; a circuit's result is the same alone and in the batch."""
+    rng = np.random.default_rng(44)
+    circs, states, refs = [], [], []
+    for n, f0, K, src, sign, pre in [(11, 5, 6, [1, 2, 3, 4], -1, False), (11, 0, 5, [5, 6], +1, True),
+                                     (16, 8, 8, list(range(2, 8)), -1, False), (16, 3, 10, [], +1, False)]:
+        field = list(range(f0, f0 + K))
+        psi = synth.gaussian_state_np(int(rng.integers(1 << 30)), n)
+        x0 = psi.astype(np.complex64).astype(np.complex128) if dtype == torch.complex64 else psi
+        c = qs.Circuit(n)
+        c.add_walsh(field[::-1])
+        c.add_dft(field, sign, src, twiddle_first=pre)
+        ref = x0.copy()
+        for q in field:
+            ocore.apply_gate(ref, [q], ohhl.H)
+        ohhl.dft_pass(ref, field, sign, src, pre)
+        circs.append(c)
+        states.append(torch.from_numpy(x0).to(dtype).cuda())
+        refs.append(ref)
+    batch_states = [s.clone() for s in states]
+    qs.qsim_apply_batched(batch_states, circs)
+    torch.cuda.synchronize()
+    for i, (st, ref) in enumerate(zip(batch_states, refs)):
+        out = st.cpu().numpy().astype(np.complex128)
+        assert np.max(np.abs(out - ref)) <= TOL[dtype]
+        alone = states[i].clone()
+        qs.qsim_apply_batched([alone], [circs[i]])
+        torch.cuda.synchronize()
+        assert torch.equal(alone, st)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_hhl_batch_with_qft_passes_matches_oracle(qs, dtype, cuda_device):
+    """HHL circuits whose QFTs and Hadamard layers are passes, in one batched launch: one field
+    (m <= 10) and two fields (m = 12, 13: the rotation reads the clock register rotated)."""
+    probs = synth.batched_problems(seed=29, count=8)
+    rng = np.random.default_rng(3)
+    for m in (12, 13):
+        A, b = synth.contingency_system(rng, 5)
+        probs.append({"A": A, "b": b, "m": m})
+    hs = [qs.hhl_build(p["A"], p["b"], p["m"], structured=True, fft_qft=True) for p in probs]
+    fused = [qs.qsim_fuse(h.as_circuit(), 3) for h in hs]
+    states = [torch.empty(1 << h.info()["n"], dtype=dtype, device="cuda") for h in hs]
+    b = qs.hhl_batch_create(hs, states, fused)
+    b.run()
+    res = b.results()
+    for p, st, r in zip(probs, states, res):
+        ref = ohhl.solve(p["A"], p["b"], p["m"])
+        m = p["m"]
+        tol = max(1e-12, 2.0 ** m * 2 * math.pi * 8 * np.finfo(float).eps) \
+            if dtype == torch.complex128 else TOL[dtype]
+        out = st.cpu().numpy().astype(np.complex128)
+        assert np.max(np.abs(out - ref["psi"])) <= tol
+        assert abs(r["p_success"] - ref["P"]) <= 10 * tol
+        assert abs(r["p_clock0"] - ref["P0"]) <= 10 * tol
