@@ -167,7 +167,10 @@ void batch_enqueue_results(qsim_batch *b, cudaStream_t st);
 void batch_host_result(const qsim_batch *b, int i, double *x_out, hhl_readout_stats *stats);
 // dft.cu: Fourier-transform pass; tables packed into the circuit blob as W, Tlo, Thi
 void dft_tables(const Op &op, std::vector<cd> &W, std::vector<cd> &Tlo, std::vector<cd> &Thi);
-void run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cudaStream_t st);
+// qop (OP_QPE_PHASE, optional): its diagonal applied to the pass's inputs (qmode 1) or outputs
+// (qmode 2), tables qlo / qhi as packed for that op
+void run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cudaStream_t st,
+             const Op *qop = nullptr, const void *qlo = nullptr, const void *qhi = nullptr, int qmode = 0);
 // linalg.cpp
 void hermitian_eig(int N, const std::vector<cd> &A, std::vector<double> &lam, std::vector<cd> &V);
 void symmetric_eig_real(int N, const std::vector<double> &A, std::vector<double> &lam, std::vector<double> &V);

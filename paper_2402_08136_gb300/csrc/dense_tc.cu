@@ -260,11 +260,24 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
         const int m = TR ? 8 * (tid >> 5) + (tid & 7) : tid & (kM - 1);
         const int h = TR ? (tid >> 3) & 3 : tid >> 7;
         const int sw = TR ? 0 : (m >> 3) & 1;
+        unsigned soff[kAmpsPT];  // canonical-layout byte offset of this thread's amplitude e
+#pragma unroll
+        for (int e = 0; e < kAmpsPT; e++) {
+            const int k = 2 * kAmpsPT * h + 2 * (e ^ sw);
+            soff[e] = (m >> 3) * 1024 + (k >> 2) * 128 + (m & 7) * 16 + (k & 3) * 4;
+        }
         float2 r[kPrefetch][kAmpsPT];
+        // the row's group base changes once per tile: computed when a tile's first chunk loads
+        long long gb_tile = -1;
+        unsigned long long gb_row = 0;
         auto load = [&](long long qq, float2(&rr)[kAmpsPT]) {
             if (qq < total) {
+                if (qq / NCH != gb_tile) {
+                    gb_tile = qq / NCH;
+                    gb_row = group_base(gb_tile, m);
+                }
+                const unsigned long long gb = gb_row;
                 if (TR) {  // qubit 0 is a target: each pair is contiguous
-                    const unsigned long long gb = group_base(qq / NCH, m);
                     const int c0 = (int)(qq % NCH) * 16 + 2 * h;
                     const float4 u0 = __ldcs(reinterpret_cast<const float4 *>(psi + gb + toff[c0]));
                     const float4 u1 = __ldcs(reinterpret_cast<const float4 *>(psi + gb + toff[c0 + 8]));
@@ -273,7 +286,6 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
                     rr[2] = make_float2(u1.x, u1.y);
                     rr[3] = make_float2(u1.z, u1.w);
                 } else {
-                    const unsigned long long gb = group_base(qq / NCH, m);
                     const int c0 = (int)(qq % NCH) * 16 + kAmpsPT * h;
 #pragma unroll
                     for (int e = 0; e < kAmpsPT; e++) rr[e] = __ldcs(psi + gb + toff[c0 + e]);
@@ -311,8 +323,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
 #pragma unroll
                     for (int e = 0; e < kAmpsPT; e++) {
                         const float2 x = sw ? r[p][e ^ 1] : r[p][e];
-                        const int k = 2 * kAmpsPT * h + 2 * (e ^ sw);
-                        const unsigned off = (m >> 3) * 1024 + (k >> 2) * 128 + (m & 7) * 16 + (k & 3) * 4;
+                        const unsigned off = soff[e];
                         const unsigned hx = to_tf32(x.x), hy = to_tf32(x.y);
                         const unsigned lx = to_tf32(x.x - __uint_as_float(hx));
                         const unsigned ly = to_tf32(x.y - __uint_as_float(hy));

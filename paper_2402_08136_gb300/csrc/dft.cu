@@ -45,7 +45,8 @@ void dft_tables(const Op &op, std::vector<cd> &W, std::vector<cd> &Tlo, std::vec
     for (size_t j = 0; j < Thi.size(); j++) Thi[j] = unit(j << hT, K + ns);
 }
 
-void run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cudaStream_t st) {
+void run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cudaStream_t st, const Op *qop,
+             const void *qlo, const void *qhi, int qmode) {
     const int K = (int)op.targets.size(), ns = (int)op.controls.size();
     QSIM_REQUIRE(K >= 1 && K <= kMaxK && ns <= kMaxSrc && K + ns <= 30 && K <= n, "Fourier pass shape");
     DftArgs a;
@@ -60,6 +61,17 @@ void run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
     a.hT = hT;
     a.ns = ns;
     a.twmode = ns == 0 ? 0 : (op.pre ? 1 : 2);
+    if (qop != nullptr && qmode != 0) {
+        a.qmode = qmode;
+        a.qlo = qlo;
+        a.qhi = qhi;
+        a.qnb = (int)qop->targets.size();
+        a.qm = (int)qop->controls.size();
+        a.qh = (a.qm + 1) / 2;  // the split qpe_phase_tables uses
+        for (int i = 0; i < a.qnb; i++) QSIM_REQUIRE(qop->targets[i] == i, "phase estimation: data qubits must be 0..nb-1");
+        for (int j = 0; j < a.qm; j++)
+            QSIM_REQUIRE(qop->controls[j] == a.qnb + j, "phase estimation: clock qubits must follow the data");
+    }
     a.scale = std::ldexp(1.0, -K / 2) * ((K & 1) ? std::sqrt(0.5) : 1.0);
     for (int j = 0; j < K; j++) a.fpos[j] = op.targets[j];
     for (int j = 0; j < ns; j++) a.spos[j] = op.controls[j];

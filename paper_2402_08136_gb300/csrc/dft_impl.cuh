@@ -75,6 +75,11 @@ struct DftArgs {
     int stage;                  // 1: the lanes are qubits 0..L-1 and each tile's input is
                                 // prefetched into shared memory (cp.async, double buffer)
     int tw_smem;                // 1: the twiddle tables Tlo, Thi are copied to shared memory
+    // structured phase-estimation diagonal exp(i s lam_d t c) applied inside the pass (qmode 1:
+    // to the inputs, 2: to the outputs): d = qubits 0..qnb-1, c = qubits qnb..qnb+qm-1, tables
+    // qlo[(c mod 2^qh) 2^qnb + d], qhi[(c >> qh) 2^qnb + d]
+    const void *qlo, *qhi;
+    int qmode, qnb, qm, qh;
     int fpos[kMaxK];            // qubit of field bit j
     int lpos[kMaxLane];         // qubit of lane bit j
     int spos[kMaxSrc];          // qubit of twiddle-source bit j
@@ -276,6 +281,12 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
     const unsigned tmask = (1u << a.hT) - 1u;
     const R scale = (R)a.scale;
     V *psi = reinterpret_cast<V *>(a.psi);
+    const V *qlo = reinterpret_cast<const V *>(a.qlo), *qhi = reinterpret_cast<const V *>(a.qhi);
+    const unsigned long long qdm = (1ull << a.qnb) - 1ull, qcm = (1ull << a.qm) - 1ull, qhm = (1ull << a.qh) - 1ull;
+    auto qphase = [&](unsigned long long idx) -> V {
+        const unsigned long long d = idx & qdm, cv = (idx >> a.qnb) & qcm;
+        return cmul(__ldg(qlo + (((cv & qhm) << a.qnb) + d)), __ldg(qhi + (((cv >> a.qh) << a.qnb) + d)));
+    };
     V x[N2];
 
     // staged input: tile tix lands in stages[(it & 1)] as [field value y][lane], 16-byte
@@ -319,6 +330,14 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
 #pragma unroll
             for (int v = 0; v < N2; v++) x[v] = src[vhi[v]];
         }
+        if (a.qmode == 1) {
+#pragma unroll
+            for (int v = 0; v < N2; v++) {
+                const unsigned long long idx =
+                    CONTIG ? base + ((unsigned long long)(u + N1 * v) << a.f0) : base + vlo[u] + vhi[v];
+                x[v] = cmul(x[v], qphase(idx));
+            }
+        }
         if (a.twmode == 1) {
 #pragma unroll
             for (int v = 0; v < N2; v++) {
@@ -352,8 +371,10 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
                     const unsigned q = w * (unsigned)y;
                     z = cmul(z, cmul(Tlo[q & tmask], Thi[q >> a.hT]));
                 }
-                if (CONTIG) psi[base + ((unsigned long long)y << a.f0)] = z;
-                else psi[base + vlo[y & (N1 - 1)] + vhi[y >> k1]] = z;
+                const unsigned long long oi =
+                    CONTIG ? base + ((unsigned long long)y << a.f0) : base + vlo[y & (N1 - 1)] + vhi[y >> k1];
+                if (a.qmode == 2) z = cmul(z, qphase(oi));
+                psi[oi] = z;
             }
         }
         __syncthreads();  // S is rewritten by the next tile's pass 1

@@ -189,16 +189,21 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
     for (int j = 0; j < m; j++) clock[j] = nb + j;
     const int anc = nb + m;
     const bool passes = (flags & QSIM_HHL_FFT_QFT) != 0;
+    const bool structured = (flags & QSIM_HHL_STRUCTURED_QPE) != 0;
     const size_t qpe_begin = c.gates.size();
-    append_hadamards(c, clock, passes);
+    // structured with passes: V^H comes first (it acts on the data register only and commutes
+    // with the clock's Hadamard layer), so the phase operator directly follows the layer's last
+    // pass and the executor can apply it inside that pass
+    if (!(structured && passes)) append_hadamards(c, clock, passes);
     size_t phase_idx = 0;
-    if (flags & QSIM_HHL_STRUCTURED_QPE) {
+    if (structured) {
         // prod_j C_j-U^(2^j) = (I (x) V) diag_c(exp(i lam t c)) (I (x) V^H); the V that would
         // follow is cancelled by the V^H of the uncomputation (nothing in between acts on the data)
         std::vector<cd> VH((size_t)D * D);
         for (int r = 0; r < D; r++)
             for (int s2 = 0; s2 < D; s2++) VH[(size_t)r * D + s2] = std::conj(V[(size_t)s2 * D + r]);
         add_u(c, data, {}, std::move(VH));
+        if (passes) append_hadamards(c, clock, true);
         Gate g;
         g.kind = GATE_QPE_PHASE;
         g.targets = data;
@@ -247,8 +252,13 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
         Gate g = c.gates[phase_idx];  // the phase operator, inverted
         g.sign = -1;
         c.gates.push_back(g);
-        add_u(c, data, {}, V);
-        append_hadamards(c, clock, passes);
+        if (passes) {  // mirror of the opening order: phase, Hadamard layer, then V
+            append_hadamards(c, clock, true);
+            add_u(c, data, {}, V);
+        } else {
+            add_u(c, data, {}, V);
+            append_hadamards(c, clock, false);
+        }
     } else {
         for (size_t i = qpe_end; i-- > qpe_begin;) c.gates.push_back(inverse_gate(c.gates[i]));
     }

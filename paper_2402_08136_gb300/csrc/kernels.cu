@@ -946,13 +946,47 @@ void ensure_device_blob(qsim_circuit *c, int dtype) {
     B.device = dev;
 }
 
+// A structured phase (diagonal) next to a Fourier or Walsh-Hadamard pass is applied inside that
+// pass (to its outputs or inputs) instead of as a pass of its own; a pass without twiddle is
+// preferred.  QSIM_FUSE_DIAG=0 in the environment keeps them apart (for comparisons).
+static bool fuse_diag_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("QSIM_FUSE_DIAG");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
+static bool is_pass(const Op &op) { return op.kind == OP_DFT || op.kind == OP_WALSH; }
+
 void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream) {
     ensure_device_blob(c, dtype);
     const int slot = dtype == QSIM_C128 ? 1 : 0;
     const unsigned char *base = static_cast<const unsigned char *>(c->blob[slot].ptr);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    for (const Op &op : c->ops) {
+    const std::vector<Op> &ops = c->ops;
+    const bool fuse = fuse_diag_enabled();
+    for (size_t i = 0; i < ops.size(); i++) {
+        const Op &op = ops[i];
         const void *dptr = base + op.dev_off[slot];
+        if (fuse && is_pass(op) && i + 1 < ops.size() && ops[i + 1].kind == OP_QPE_PHASE) {
+            // outputs of this pass, unless this pass has a twiddle and the next one has none
+            const bool next_better = !op.controls.empty() && i + 2 < ops.size() && is_pass(ops[i + 2]) &&
+                                     ops[i + 2].controls.empty();
+            if (!next_better) {
+                const Op &q = ops[i + 1];
+                run_dft(state, n, dtype, op, dptr, st, &q, base + q.dev_off[slot], base + q.dev_off_tc, 2);
+                i++;
+                continue;
+            }
+        }
+        if (fuse && op.kind == OP_QPE_PHASE && i + 1 < ops.size() && is_pass(ops[i + 1])) {
+            const Op &p = ops[i + 1];
+            run_dft(state, n, dtype, p, base + p.dev_off[slot], st, &op, dptr, base + op.dev_off_tc, 1);
+            i++;
+            continue;
+        }
         switch (op.kind) {
             case OP_DENSE:
                 if (dtype == QSIM_C64 && op.has_tc && tc_enabled() &&
