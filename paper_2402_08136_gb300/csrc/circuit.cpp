@@ -62,6 +62,8 @@ Op classify_dense(const std::vector<int> &targets, const std::vector<int> &contr
         }
     }
     op.kind = OP_DENSE;
+    op.real_u = true;
+    for (const cd &z : U) op.real_u = op.real_u && z.imag() == 0.0;
     // canonical order: targets ascending (rows and columns of U relabelled to match), so that
     // the kernels see contiguous amplitude runs whenever the lowest qubits are targets
     std::vector<int> perm(k);  // perm[b'] = original matrix bit of sorted position b'

@@ -96,6 +96,7 @@ struct Op {
     // complex64 dense ops with 4..6 targets: TF32 hi/lo split of the real form (tensor cores)
     size_t dev_off_tc = 0;
     bool has_tc = false;
+    bool real_u = false;        // OP_DENSE: every entry of U is real (SIMT kernels use 2 FMAs per entry)
 };
 
 struct DeviceBlob {

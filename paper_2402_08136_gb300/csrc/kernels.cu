@@ -87,7 +87,7 @@ struct DenseArgs {
     int tloc[8];          // tile-local bit of target b
 };
 
-template <typename R, int K, bool USMEM>
+template <typename R, int K, bool USMEM, bool REALU>
 __global__ void __launch_bounds__(kThreads) dense_tile_kernel(const DenseArgs a) {
     using V = typename C2<R>::T;
     constexpr int D = 1 << K;
@@ -100,14 +100,21 @@ __global__ void __launch_bounds__(kThreads) dense_tile_kernel(const DenseArgs a)
     const int tile_amps = 1 << T;
     const int G = tile_amps >> K;  // groups (columns) per tile
     V *tile = reinterpret_cast<V *>(smem_raw);
-    V *Us = tile + tile_amps;                              // D*D if USMEM
-    int *toff = reinterpret_cast<int *>(Us + (USMEM ? D * D : 0));   // D entries
+    // U in shared memory (USMEM): D*D complex, or D*D reals when U is real (REALU)
+    constexpr int UBYTES = USMEM ? D * D * (REALU ? (int)sizeof(R) : (int)sizeof(V)) : 0;
+    unsigned char *Usb = reinterpret_cast<unsigned char *>(tile + tile_amps);
+    V *Us = reinterpret_cast<V *>(Usb);
+    R *Usr = reinterpret_cast<R *>(Usb);
+    int *toff = reinterpret_cast<int *>(Usb + UBYTES);  // D entries
     long long *hoff = reinterpret_cast<long long *>(toff + ((D + 1) & ~1));  // 2^nh entries
 
     const int tid = threadIdx.x;
     const V *Ug = reinterpret_cast<const V *>(a.U);
     if (USMEM)
-        for (int i = tid; i < D * D; i += kThreads) Us[i] = Ug[i];
+        for (int i = tid; i < D * D; i += kThreads) {
+            if (REALU) Usr[i] = Ug[i].x;
+            else Us[i] = Ug[i];
+        }
     for (int c = tid; c < D; c += kThreads) {
         int o = 0;
         for (int b = 0; b < K; b++)
@@ -154,14 +161,25 @@ __global__ void __launch_bounds__(kThreads) dense_tile_kernel(const DenseArgs a)
             for (int r = 0; r < RPT; r++) acc[r] = V{0, 0};
             for (int c = 0; c < D; c++) {
                 const V x = tile[gl + toff[c]];
-                const V *uc = (USMEM ? Us : Ug) + c * D + rg * RPT;
+                if (REALU) {  // real U: two multiply-adds per entry
+                    const R *ucr = Usr + c * D + rg * RPT;
+                    const V *ucg = Ug + c * D + rg * RPT;
 #pragma unroll
-                for (int r = 0; r < RPT; r++) {
-                    const V u = uc[r];
-                    acc[r].x = fma(u.x, x.x, acc[r].x);
-                    acc[r].x = fma(-u.y, x.y, acc[r].x);
-                    acc[r].y = fma(u.x, x.y, acc[r].y);
-                    acc[r].y = fma(u.y, x.x, acc[r].y);
+                    for (int r = 0; r < RPT; r++) {
+                        const R u = USMEM ? ucr[r] : ucg[r].x;
+                        acc[r].x = fma(u, x.x, acc[r].x);
+                        acc[r].y = fma(u, x.y, acc[r].y);
+                    }
+                } else {
+                    const V *uc = (USMEM ? Us : Ug) + c * D + rg * RPT;
+#pragma unroll
+                    for (int r = 0; r < RPT; r++) {
+                        const V u = uc[r];
+                        acc[r].x = fma(u.x, x.x, acc[r].x);
+                        acc[r].x = fma(-u.y, x.y, acc[r].x);
+                        acc[r].y = fma(u.x, x.y, acc[r].y);
+                        acc[r].y = fma(u.y, x.x, acc[r].y);
+                    }
                 }
             }
 #pragma unroll
@@ -188,7 +206,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 constexpr int kStages = 3;
 
-template <typename R, int K, bool USMEM>
+template <typename R, int K, bool USMEM, bool REALU>
 __global__ void __launch_bounds__(kThreads) dense_pipe_kernel(const DenseArgs a) {
     using V = typename C2<R>::T;
     constexpr int D = 1 << K;
@@ -202,14 +220,20 @@ __global__ void __launch_bounds__(kThreads) dense_pipe_kernel(const DenseArgs a)
     const int tile_amps = 1 << T;
     const int G = tile_amps >> K;
     V *stages = reinterpret_cast<V *>(smem_raw);
-    V *Us = stages + kStages * tile_amps;
-    int *toff = reinterpret_cast<int *>(Us + (USMEM ? D * D : 0));
+    constexpr int UBYTES = USMEM ? D * D * (REALU ? (int)sizeof(R) : (int)sizeof(V)) : 0;
+    unsigned char *Usb = reinterpret_cast<unsigned char *>(stages + kStages * tile_amps);
+    V *Us = reinterpret_cast<V *>(Usb);
+    R *Usr = reinterpret_cast<R *>(Usb);
+    int *toff = reinterpret_cast<int *>(Usb + UBYTES);
     long long *hoff = reinterpret_cast<long long *>(toff + ((D + 1) & ~1));
 
     const int tid = threadIdx.x;
     const V *Ug = reinterpret_cast<const V *>(a.U);
     if (USMEM)
-        for (int i = tid; i < D * D; i += kThreads) Us[i] = Ug[i];
+        for (int i = tid; i < D * D; i += kThreads) {
+            if (REALU) Usr[i] = Ug[i].x;
+            else Us[i] = Ug[i];
+        }
     for (int c = tid; c < D; c += kThreads) {
         int o = 0;
         for (int b = 0; b < K; b++)
@@ -276,14 +300,25 @@ __global__ void __launch_bounds__(kThreads) dense_pipe_kernel(const DenseArgs a)
             for (int r = 0; r < RPT; r++) acc[r] = V{0, 0};
             for (int c = 0; c < D; c++) {
                 const V x = tile[gl + toff[c]];
-                const V *uc = (USMEM ? Us : Ug) + c * D + rg * RPT;
+                if (REALU) {  // real U: two multiply-adds per entry
+                    const R *ucr = Usr + c * D + rg * RPT;
+                    const V *ucg = Ug + c * D + rg * RPT;
 #pragma unroll
-                for (int r = 0; r < RPT; r++) {
-                    const V u = uc[r];
-                    acc[r].x = fma(u.x, x.x, acc[r].x);
-                    acc[r].x = fma(-u.y, x.y, acc[r].x);
-                    acc[r].y = fma(u.x, x.y, acc[r].y);
-                    acc[r].y = fma(u.y, x.x, acc[r].y);
+                    for (int r = 0; r < RPT; r++) {
+                        const R u = USMEM ? ucr[r] : ucg[r].x;
+                        acc[r].x = fma(u, x.x, acc[r].x);
+                        acc[r].y = fma(u, x.y, acc[r].y);
+                    }
+                } else {
+                    const V *uc = (USMEM ? Us : Ug) + c * D + rg * RPT;
+#pragma unroll
+                    for (int r = 0; r < RPT; r++) {
+                        const V u = uc[r];
+                        acc[r].x = fma(u.x, x.x, acc[r].x);
+                        acc[r].x = fma(-u.y, x.y, acc[r].x);
+                        acc[r].y = fma(u.x, x.y, acc[r].y);
+                        acc[r].y = fma(u.y, x.x, acc[r].y);
+                    }
                 }
             }
 #pragma unroll
@@ -654,9 +689,9 @@ int grid_for(long long work, int per_block) {
 
 int tile_bits(int dtype) { return dtype == QSIM_C128 ? 11 : 11; }
 
-template <typename R, int K, bool USMEM>
+template <typename R, int K, bool USMEM, bool REALU>
 void launch_dense_t(const DenseArgs &a, size_t smem, bool pipe, cudaStream_t st) {
-    auto kern = pipe ? dense_pipe_kernel<R, K, USMEM> : dense_tile_kernel<R, K, USMEM>;
+    auto kern = pipe ? dense_pipe_kernel<R, K, USMEM, REALU> : dense_tile_kernel<R, K, USMEM, REALU>;
     static bool attr[2] = {false, false};
     if (!attr[pipe]) {
         CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -671,10 +706,10 @@ void launch_dense_t(const DenseArgs &a, size_t smem, bool pipe, cudaStream_t st)
 }
 
 template <typename R>
-void launch_dense(const DenseArgs &a, int K, size_t smem_base, cudaStream_t st) {
+void launch_dense(const DenseArgs &a, int K, bool real_u, size_t smem_base, cudaStream_t st) {
     const size_t D = (size_t)1 << K;
     const size_t vb = 2 * sizeof(R);
-    const size_t ubytes = D * D * vb;
+    const size_t ubytes = D * D * (real_u ? sizeof(R) : vb);
     const size_t tile_bytes = ((size_t)1 << a.T) * vb;
     // the pipelined kernel needs qubit 0 in the tile (16-byte chunks contiguous in HBM)
     const bool pipe = a.L0 >= 1 && smem_base + (kStages - 1) * tile_bytes <= 200 * 1024;
@@ -682,10 +717,15 @@ void launch_dense(const DenseArgs &a, int K, size_t smem_base, cudaStream_t st) 
     const bool usmem = base + ubytes <= 200 * 1024;
     const size_t smem = base + (usmem ? ubytes : 0);
     switch (K) {
-#define QSIM_K(k)                                                    \
-    case k:                                                          \
-        if (usmem) launch_dense_t<R, k, true>(a, smem, pipe, st);    \
-        else launch_dense_t<R, k, false>(a, smem, pipe, st);         \
+#define QSIM_K(k)                                                                \
+    case k:                                                                      \
+        if (real_u) {                                                            \
+            if (usmem) launch_dense_t<R, k, true, true>(a, smem, pipe, st);      \
+            else launch_dense_t<R, k, false, true>(a, smem, pipe, st);           \
+        } else {                                                                 \
+            if (usmem) launch_dense_t<R, k, true, false>(a, smem, pipe, st);     \
+            else launch_dense_t<R, k, false, false>(a, smem, pipe, st);          \
+        }                                                                        \
         break;
         QSIM_K(1) QSIM_K(2) QSIM_K(3) QSIM_K(4) QSIM_K(5) QSIM_K(6) QSIM_K(7)
 #undef QSIM_K
@@ -700,7 +740,9 @@ void run_dense(void *state, int n, int dtype, const Op &op, const void *Udev, cu
     const unsigned long long cm = mask_of(ctl);
     const unsigned long long tm = mask_of(op.targets);
     const int avail = n - (int)ctl.size();
-    const int T = std::min(tile_bits(dtype), avail);
+    // a 7-target real gate on complex64: a wider tile gives each warp 32 groups (the real U
+    // leaves room for it in shared memory)
+    const int T = std::min(tile_bits(dtype) + (K == 7 && op.real_u && dtype == QSIM_C64 ? 1 : 0), avail);
     // tile qubits: the targets plus the lowest non-control qubits
     std::vector<int> tile(op.targets.begin(), op.targets.end());
     for (int q = 0; q < n && (int)tile.size() < T; q++)
@@ -729,8 +771,8 @@ void run_dense(void *state, int n, int dtype, const Op &op, const void *Udev, cu
     const size_t D = (size_t)1 << K;
     const size_t smem_base = ((size_t)1 << a.T) * vb + ((D + 1) & ~(size_t)1) * 4 +
                              ((size_t)1 << a.nh) * 8;
-    if (dtype == QSIM_C128) launch_dense<double>(a, K, smem_base, st);
-    else launch_dense<float>(a, K, smem_base, st);
+    if (dtype == QSIM_C128) launch_dense<double>(a, K, op.real_u, smem_base, st);
+    else launch_dense<float>(a, K, op.real_u, smem_base, st);
 }
 
 void run_phase(void *state, int n, int dtype, const Op &op, cudaStream_t st) {

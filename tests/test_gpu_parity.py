@@ -106,6 +106,28 @@ def test_tensor_core_dense_parity_complex64(qs, k):
     check(st, ref, torch.complex64)
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_real_matrix_gates(qs, dtype):
+    """Real orthogonal gates (the eigenvector matrices of real symmetric systems) run the SIMT
+    kernels' real-matrix variant (two multiply-adds per entry), k = 1..7, with low, high and
+    random targets and a control; k = 7 on complex64 uses the wider tile."""
+    rng = np.random.default_rng(61)
+    n = 15
+    psi = host_input(synth.gaussian_state_np(61, n), dtype)
+    c = qs.Circuit(n)
+    ref = psi.copy()
+    for k in range(1, 8):
+        for t, ctl in ((list(range(k)), []), (synth.random_targets(rng, n, k), []),
+                       ([n - 1 - i for i in range(k)], [0] if k < 7 else [])):
+            Q, _ = np.linalg.qr(rng.standard_normal((1 << k, 1 << k)))
+            c.add_gate(t, Q, ctl)
+            ocore.apply_gate(ref, t, Q.astype(np.complex128), ctl)
+    st = dev_state(psi, dtype)
+    qs.qsim_apply(st, c)
+    torch.cuda.synchronize()
+    check(st, ref, dtype)
+
+
 @pytest.mark.parametrize("k", [4, 5, 6])
 def test_tensor_core_low_target_layouts(qs, k):
     """Gates whose targets include qubits 0 and 1 (vector loads across a group's amplitudes,
