@@ -153,6 +153,12 @@ size_t dense_tc_blob_bytes(int k);
 void dense_tc_pack(int k, const std::vector<cd> &U, unsigned char *out);
 bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const std::vector<int> &controls,
                      const void *Bdev, int sms, cudaStream_t st);
+// complex64, real U on 7 targets including qubits 0 and 1 (ascending)
+bool dense_tc_real7_applies(const Op &op);
+size_t dense_tc_real7_blob_bytes();
+void dense_tc_pack_real7(const std::vector<cd> &U, unsigned char *out);
+bool launch_dense_tc_real7(void *state, int n, const std::vector<int> &targets, const std::vector<int> &controls,
+                           const void *Bdev, int sms, cudaStream_t st);
 // batched.cu: plan (host image) / instantiate (device tables) / launch / results, for the pool
 struct BatchImage;
 bool batch_supported(const qsim_circuit *c);  // every op runs in the batched executor

@@ -425,6 +425,225 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Real 7-target gates (a real U, e.g. the eigenvector matrix of a real symmetric system) on the
+// lowest qubits, complex64.  For real U the complex product splits into two real ones,
+// Y_re = U X_re and Y_im = U X_im, so one real GEMM does both:
+//     Y^T[128 out amps x 128 rows] = U[128 x 128] * X^T,   row = (group, re or im),
+// U (TF32 hi/lo, 128 KB) is the MMA's A operand, a chunk of 32 input amplitudes of 64 groups
+// (128 rows) its B operand, and the accumulator's TMEM lanes are output amplitudes, so each
+// epilogue warp stores 32 consecutive complex amplitudes of one group.  Same roles, barriers
+// and bounded waits as dense_tc_kernel.
+namespace tcr {
+constexpr int D = 128;           // amplitudes per group (7 targets)
+constexpr int KK = 128;          // reduction length: input amplitudes
+constexpr int MG = 64;           // groups per tile (128 rows: re and im of each)
+constexpr int NCH = KK / kCH;    // chunks of 32 input amplitudes
+constexpr int BBYTES = D * KK * 4;
+constexpr int ABYTES = 2 * MG * kCH * 4;
+constexpr int NBAR = 2 * kNBuf + 4;
+constexpr int SMEM = 2 * BBYTES + kNBuf * 2 * ABYTES + 8 * NBAR + 16 + 8 * D + 8 * MG;
+constexpr int TMEM_COLS = 2 * 2 * MG;
+constexpr unsigned IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)((2 * MG) >> 3) << 17) |
+                           ((unsigned)(D >> 4) << 24);
+}  // namespace tcr
+
+__global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Args a) {
+    using namespace tcr;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float *Bs = reinterpret_cast<float *>(sm);  // U hi, U lo
+    unsigned char *Aring = sm + 2 * BBYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(Aring + kNBuf * 2 * ABYTES);
+    uint64_t *full = bars, *empty = bars + kNBuf, *accfull = bars + 2 * kNBuf, *accempty = bars + 2 * kNBuf + 2;
+    unsigned *tslot = reinterpret_cast<unsigned *>(bars + NBAR);
+    long long *toff = reinterpret_cast<long long *>(tslot + 4);  // D entries
+    long long *goff = toff + D;                                  // MG entries
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(a.Bg);
+        float4 *dst = reinterpret_cast<float4 *>(Bs);
+        for (int i = tid; i < 2 * BBYTES / 16; i += kThreadsWS) dst[i] = src[i];
+        for (int c = tid; c < D; c += kThreadsWS) {
+            long long o = 0;
+            for (int b = 0; b < 7; b++)
+                if ((c >> b) & 1) o |= 1ll << a.targets[b];
+            toff[c] = o;
+        }
+        for (int g = tid; g < MG; g += kThreadsWS) goff[g] = (long long)insert_zeros((unsigned long long)g, a.fix, a.nfix);
+        if (tid == 0) {
+            for (int i = 0; i < kNBuf; i++) {
+                mbar_init(&full[i], kProducers);
+                mbar_init(&empty[i], 1);
+            }
+            for (int i = 0; i < 2; i++) {
+                mbar_init(&accfull[i], 1);
+                mbar_init(&accempty[i], 128);
+            }
+        }
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                         "r"((unsigned)TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    }
+    const unsigned tmem = *tslot;
+    float2 *psi = reinterpret_cast<float2 *>(a.psi);
+    const long long first = blockIdx.x, stride = gridDim.x;
+    const long long ntl = first < a.ntiles ? (a.ntiles - first + stride - 1) / stride : 0;
+    const long long total = ntl * NCH;
+    bool failed = false;
+    auto tile_base = [&](long long tile_i) -> unsigned long long {
+        const unsigned long long gidx = (unsigned long long)(first + tile_i * stride) * MG;
+        return insert_zeros(gidx, a.fix, a.nfix) | a.cmask;
+    };
+
+    if (warp < kEpiWarp0) {
+        // ------------------------------------------------------------------ producers
+        // thread t: group gi = 4 w + (l mod 4), amplitude pairs p and p + 8 (p = l / 4) of every
+        // chunk.  A warp's vector load reads 4 groups x 128 contiguous bytes; a quarter-warp's
+        // 8-byte stores (rows 2 gi, 2 gi + 1) fill 8 distinct bank slots.
+        const int gi = 4 * warp + (lane & 3), p0 = lane >> 2;
+        unsigned off[2][2];  // [pair][re, im]
+#pragma unroll
+        for (int pi = 0; pi < 2; pi++) {
+            const int k = 2 * (p0 + 8 * pi);
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const int r = 2 * gi + c;
+                off[pi][c] = (r >> 3) * 1024 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
+            }
+        }
+        float4 rr[kPrefetch][2];
+        long long gb_tile = -1;
+        unsigned long long gb_row = 0;
+        auto load = [&](long long qq, float4(&q4)[2]) {
+            if (qq < total) {
+                if (qq / NCH != gb_tile) {
+                    gb_tile = qq / NCH;
+                    gb_row = tile_base(gb_tile) + (unsigned long long)goff[gi];
+                }
+                const int c0 = (int)(qq % NCH) * kCH;
+#pragma unroll
+                for (int pi = 0; pi < 2; pi++)
+                    q4[pi] = __ldcs(reinterpret_cast<const float4 *>(psi + gb_row + toff[c0 + 2 * (p0 + 8 * pi)]));
+            }
+        };
+#pragma unroll
+        for (int p = 0; p < kPrefetch; p++) load(p, rr[p]);
+        for (long long q0 = 0; q0 < total && !failed; q0 += kPrefetch) {
+#pragma unroll
+            for (int p = 0; p < kPrefetch; p++) {
+                const long long qq = q0 + p;
+                if (qq >= total || failed) break;
+                const int b = (int)(qq % kNBuf);
+                const long long use = qq / kNBuf;
+                if (use > 0 && !mbar_wait(&empty[b], (unsigned)((use - 1) & 1))) {
+                    failed = true;
+                    break;
+                }
+                unsigned char *ahi = Aring + b * 2 * ABYTES;
+                unsigned char *alo = ahi + ABYTES;
+#pragma unroll
+                for (int pi = 0; pi < 2; pi++) {
+                    const float4 x = rr[p][pi];  // (re, im) of amplitudes k and k + 1
+                    const unsigned hr0 = to_tf32(x.x), hr1 = to_tf32(x.z);
+                    const unsigned hi0 = to_tf32(x.y), hi1 = to_tf32(x.w);
+                    *reinterpret_cast<uint2 *>(ahi + off[pi][0]) = make_uint2(hr0, hr1);
+                    *reinterpret_cast<uint2 *>(ahi + off[pi][1]) = make_uint2(hi0, hi1);
+                    *reinterpret_cast<uint2 *>(alo + off[pi][0]) =
+                        make_uint2(to_tf32(x.x - __uint_as_float(hr0)), to_tf32(x.z - __uint_as_float(hr1)));
+                    *reinterpret_cast<uint2 *>(alo + off[pi][1]) =
+                        make_uint2(to_tf32(x.y - __uint_as_float(hi0)), to_tf32(x.w - __uint_as_float(hi1)));
+                }
+                load(qq + kPrefetch, rr[p]);
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive(&full[b]);
+            }
+        }
+    } else if (warp < kMmaWarp) {
+        // ------------------------------------------------------------------ epilogue
+        const int sub = warp - kEpiWarp0;
+        const int n = sub * 32 + lane;  // output amplitude == TMEM lane
+        const long long ta = toff[n];
+        for (long long t = 0; t < ntl && !failed; t++) {
+            const int ab = (int)(t & 1);
+            if (!mbar_wait(&accfull[ab], (unsigned)((t >> 1) & 1))) {
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned long long tb = tile_base(t);
+            const unsigned acc = tmem + (unsigned)(ab * 2 * MG) + ((unsigned)(sub * 32) << 16);
+#pragma unroll
+            for (int col = 0; col < 2 * MG; col += 16) {  // 16 columns = re, im of 8 groups
+                unsigned v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                      "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                    : "r"(acc + (unsigned)col));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                for (int i = 0; i < 8; i++)
+                    __stcs(psi + tb + goff[col / 2 + i] + ta,
+                           make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])));
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            mbar_arrive(&accempty[ab]);
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------------------ MMA issuer
+        const unsigned aring_u32 = smem_u32(Aring);
+        const unsigned u_hi = smem_u32(Bs), u_lo = u_hi + BBYTES;
+        for (long long qq = 0; qq < total && !failed; qq++) {
+            const int b = (int)(qq % kNBuf);
+            const int j = (int)(qq % NCH);
+            const long long t = qq / NCH;
+            const int ab = (int)(t & 1);
+            if (j == 0 && t >= 2 && !mbar_wait(&accempty[ab], (unsigned)(((t >> 1) - 1) & 1))) {
+                failed = true;
+                break;
+            }
+            if (!mbar_wait(&full[b], (unsigned)((qq / kNBuf) & 1))) {
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned acc = tmem + (unsigned)(ab * 2 * MG);
+            const unsigned x_hi = aring_u32 + b * 2 * ABYTES, x_lo = x_hi + ABYTES;
+#pragma unroll
+            for (int kk = 0; kk < kCH / 8; kk++) {
+                const unsigned uoff = (j * (kCH / 4) + kk * 2) * 128;
+                const uint64_t dUh = make_desc(u_hi + uoff, 128, KK * 32);
+                const uint64_t dUl = make_desc(u_lo + uoff, 128, KK * 32);
+                const uint64_t dXh = make_desc(x_hi + kk * 256, 128, 1024);
+                const uint64_t dXl = make_desc(x_lo + kk * 256, 128, 1024);
+                mma_tf32(acc, dUh, dXh, IDESC, (j == 0 && kk == 0) ? 0u : 1u);
+                mma_tf32(acc, dUl, dXh, IDESC, 1u);
+                mma_tf32(acc, dUh, dXl, IDESC, 1u);
+            }
+            commit_to(&empty[b]);
+            if (j == NCH - 1) commit_to(&accfull[ab]);
+        }
+    }
+    if (failed) atomicOr(&g_device_error, 1u);
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((unsigned)TMEM_COLS)
+                     : "memory");
+    }
+}
+
 }  // namespace tc
 
 // Host-side split of the real form of U into TF32 hi/lo in the canonical shared-memory
@@ -443,6 +662,66 @@ size_t dense_tc_blob_bytes(int k) {
 }
 
 bool dense_tc_supported(int k) { return k >= 4 && k <= 6; }
+
+bool dense_tc_real7_applies(const Op &op) {
+    return op.real_u && op.targets.size() == 7 && op.targets[0] == 0 && op.targets[1] == 1;
+}
+
+size_t dense_tc_real7_blob_bytes() { return 2 * (size_t)tc::tcr::BBYTES; }
+
+// Real U (rows = output amplitudes, columns = input amplitudes) split into TF32 hi/lo in the
+// canonical K-major layout of the real 7-target kernel.
+void dense_tc_pack_real7(const std::vector<cd> &U, unsigned char *out) {
+    constexpr int D = tc::tcr::D, KK = tc::tcr::KK;
+    float *hi = reinterpret_cast<float *>(out);
+    float *lo = hi + (size_t)D * KK;
+    for (int n = 0; n < D; n++)
+        for (int k = 0; k < KK; k++) {
+            const float f = (float)U[(size_t)n * D + k].real();
+            const unsigned hb = tf32_rne_bits(f);
+            float hf;
+            std::memcpy(&hf, &hb, 4);
+            const unsigned lb = tf32_rne_bits(f - hf);
+            float lf;
+            std::memcpy(&lf, &lb, 4);
+            const size_t idx = ((size_t)(n >> 3) * (KK * 32) + (size_t)(k >> 2) * 128 + (n & 7) * 16 + (k & 3) * 4) / 4;
+            hi[idx] = hf;
+            lo[idx] = lf;
+        }
+}
+
+bool launch_dense_tc_real7(void *state, int n, const std::vector<int> &targets, const std::vector<int> &controls,
+                           const void *Bdev, int sms, cudaStream_t st) {
+    const int free_bits = n - 7 - (int)controls.size();
+    if (free_bits < 6) return false;  // fewer than 64 groups
+    tc::Args a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = state;
+    a.Bg = static_cast<const float *>(Bdev);
+    a.ntiles = 1ll << (free_bits - 6);
+    std::vector<int> fix(targets);
+    for (int q : controls) {
+        fix.push_back(q);
+        a.cmask |= 1ull << q;
+    }
+    std::sort(fix.begin(), fix.end());
+    if ((int)fix.size() > tc::kMaxFix) return false;
+    a.nfix = (int)fix.size();
+    for (int i = 0; i < a.nfix; i++) a.fix[i] = fix[i];
+    for (int b = 0; b < 7; b++) a.targets[b] = targets[b];
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc::dense_tc_real7_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             tc::tcr::SMEM);
+        if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_real7_kernel attribute: ") + cudaGetErrorString(e));
+        attr = true;
+    }
+    const long long grid = std::min<long long>(a.ntiles, (long long)sms);  // one CTA per SM (TMEM, smem)
+    tc::dense_tc_real7_kernel<<<(int)grid, tc::kThreadsWS, tc::tcr::SMEM, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_real7_kernel: ") + cudaGetErrorString(e));
+    return true;
+}
 
 void dense_tc_pack(int k, const std::vector<cd> &U, unsigned char *out) {
     const int D = 1 << k, N = 2 * D, KK = 2 * D;

@@ -924,6 +924,12 @@ std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype) {
                 const size_t nb = dense_tc_blob_bytes((int)op.targets.size());
                 blob.resize(blob.size() + nb);
                 dense_tc_pack((int)op.targets.size(), op.U, blob.data() + op.dev_off_tc);
+            } else if (dtype == QSIM_C64 && dense_tc_real7_applies(op)) {
+                align_blob(blob);
+                op.dev_off_tc = blob.size();
+                op.has_tc = true;
+                blob.resize(blob.size() + dense_tc_real7_blob_bytes());
+                dense_tc_pack_real7(op.U, blob.data() + op.dev_off_tc);
             }
         } else if (op.kind == OP_DIAG) {
             for (const cd &z : op.U) put_complex(blob, dtype, z);
@@ -1032,7 +1038,9 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream) {
         switch (op.kind) {
             case OP_DENSE:
                 if (dtype == QSIM_C64 && op.has_tc && tc_enabled() &&
-                    launch_dense_tc(state, n, op.targets, op.controls, base + op.dev_off_tc, num_sms(), st))
+                    (op.targets.size() == 7
+                         ? launch_dense_tc_real7(state, n, op.targets, op.controls, base + op.dev_off_tc, num_sms(), st)
+                         : launch_dense_tc(state, n, op.targets, op.controls, base + op.dev_off_tc, num_sms(), st)))
                     break;
                 run_dense(state, n, dtype, op, dptr, st);
                 break;

@@ -110,15 +110,19 @@ def test_tensor_core_dense_parity_complex64(qs, k):
 def test_real_matrix_gates(qs, dtype):
     """Real orthogonal gates (the eigenvector matrices of real symmetric systems) run the SIMT
     kernels' real-matrix variant (two multiply-adds per entry), k = 1..7, with low, high and
-    random targets and a control; k = 7 on complex64 uses the wider tile."""
+    random targets and a control; k = 7 on complex64 uses the wider tile, or the real tensor-core
+    form when qubits 0 and 1 are targets."""
     rng = np.random.default_rng(61)
     n = 15
     psi = host_input(synth.gaussian_state_np(61, n), dtype)
     c = qs.Circuit(n)
     ref = psi.copy()
     for k in range(1, 8):
-        for t, ctl in ((list(range(k)), []), (synth.random_targets(rng, n, k), []),
-                       ([n - 1 - i for i in range(k)], [0] if k < 7 else [])):
+        cases = [(list(range(k)), []), (synth.random_targets(rng, n, k), []),
+                 ([n - 1 - i for i in range(k)], [0] if k < 7 else [])]
+        if k == 7:  # the complex64 tensor-core form for real 7-target gates on the lowest qubits
+            cases += [([1, 0, 6, 5, 4, 3, 2], [n - 1]), (list(range(7)), [9, 12])]
+        for t, ctl in cases:
             Q, _ = np.linalg.qr(rng.standard_normal((1 << k, 1 << k)))
             c.add_gate(t, Q, ctl)
             ocore.apply_gate(ref, t, Q.astype(np.complex128), ctl)
