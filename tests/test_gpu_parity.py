@@ -471,6 +471,84 @@ def test_full_size_gate_apply_sampled(qs, dtype, n):
         torch.cuda.empty_cache()
 
 
+def _sample_groups(rng, n, group_qubits, count):
+    """`count` random assignments of the qubits outside `group_qubits`, as base indices."""
+    others = [q for q in range(n) if q not in group_qubits]
+    bases = []
+    for _ in range(count):
+        base = 0
+        for q in others:
+            if rng.random() < 0.5:
+                base |= 1 << q
+        bases.append(base)
+    return bases
+
+
+@pytest.mark.parametrize("dtype,n", [(torch.complex64, 34), (torch.complex128, 33)])
+def test_maximum_size_sampled(qs, dtype, n):
+    """The largest states the library accepts (2^34 complex64 = 2^33 complex128 = 128 GiB,
+    amplitude indices beyond 2^32): a dense gate on the top qubit, a dense gate with random
+    targets (tensor cores for complex64), a Fourier pass on the top 10 qubits with a twiddle and
+    a Walsh-Hadamard pass on scattered qubits, each on the seeded state, checked on sampled
+    groups recomputed by the oracle from the generator's amplitudes."""
+    free = torch.cuda.mem_get_info()[0]
+    if free < (1 << n) * (16 if dtype == torch.complex128 else 8) * 1.15:
+        pytest.skip("not enough device memory")
+    seed, rng = 91, np.random.default_rng(8)
+    k2 = 6 if dtype == torch.complex64 else 3
+    U1 = synth.haar_unitary(rng, 2)
+    t2 = [n - 1] + [int(q) for q in rng.permutation(n - 1)[:k2 - 1]]
+    U2 = synth.haar_unitary(rng, 1 << k2)
+    field, src = list(range(n - 10, n)), list(range(n - 13, n - 10))
+    walsh = [0, 5, 17, n - 1]
+
+    def apply_and_get(build):
+        st = synth.gaussian_state_torch(seed, n, dtype, "cuda")
+        c = qs.Circuit(n)
+        build(c)
+        qs.qsim_apply(st, c)
+        torch.cuda.synchronize()
+        return st
+
+    def check_groups(st, qubits, bases, expect):
+        offs = np.array([sum(((r >> b) & 1) << qubits[b] for b in range(len(qubits)))
+                         for r in range(1 << len(qubits))], dtype=np.int64)
+        for base in bases:
+            idx = base + offs
+            x = host_input(synth.gaussian_amplitudes_at(seed, n, idx.astype(np.uint64)), dtype)
+            want = expect(x, base)
+            got = st[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.complex128)
+            assert np.max(np.abs(got - want)) <= TOL[dtype]
+
+    def dense(U, k):
+        def f(x, base):
+            ocore.apply_gate(x, list(range(k)), U)
+            return x
+        return f
+
+    def fourier(x, base):  # the group as a (10 + 3)-qubit system with the source bits of base
+        w = sum(((base >> q) & 1) << j for j, q in enumerate(src))
+        mini = np.zeros(1 << 13, dtype=np.complex128)
+        mini[w << 10: (w << 10) + 1024] = x
+        ohhl.dft_pass(mini, list(range(10)), -1, [10, 11, 12], False)
+        return mini[w << 10: (w << 10) + 1024]
+
+    def hadamards(x, base):
+        for q in range(4):
+            ocore.apply_gate(x, [q], ohhl.H)
+        return x
+
+    for qubits, build, expect, count in (
+            ([n - 1], lambda c: c.add_gate([n - 1], U1), dense(U1, 1), 64),
+            (t2, lambda c: c.add_gate(t2, U2), dense(U2, k2), 32),
+            (field, lambda c: c.add_dft(field, -1, src), fourier, 8),
+            (walsh, lambda c: c.add_walsh(walsh), hadamards, 32)):
+        st = apply_and_get(build)
+        check_groups(st, qubits, _sample_groups(rng, n, qubits, count), expect)
+        del st
+        torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("dtype,n", [(torch.complex128, 30), (torch.complex64, 31)])
 def test_full_size_forward_inverse_roundtrip(qs, dtype, n):
     """Property at full size: the benchmark's gate kinds (4 per k) followed by their inverses
