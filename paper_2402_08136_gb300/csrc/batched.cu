@@ -152,18 +152,34 @@ __device__ void op_fourier(V *psi, int n, const BOp &op, const V *data, int tid,
     for (int j = K - 1; j >= 0; j--) {
         const int p = f0 + j;
         const unsigned bit = 1u << p, rmask = (1u << j) - 1u;
-        for (unsigned g = tid; g < N / 2; g += NT) {
-            const unsigned i0 = ((g >> p) << (p + 1)) | (g & (bit - 1u));
-            const V a = psi[i0], b = psi[i0 | bit];
-            V d;
-            d.x = a.x - b.x;
-            d.y = a.y - b.y;
-            psi[i0] = V{a.x + b.x, a.y + b.y};
-            if (!walsh) {
-                const unsigned r = (i0 >> f0) & rmask;
-                if (r) d = cmulb(d, W[r << (K - 1 - j)]);
+        // two independent pairs per iteration: their loads are in flight together (states
+        // updated in place in L2 would otherwise wait for one round trip per pair)
+        constexpr int U4 = 2;
+        for (unsigned g0 = tid; g0 < N / 2; g0 += U4 * NT) {
+            V a[U4], b[U4];
+            unsigned i0[U4];
+#pragma unroll
+            for (int e = 0; e < U4; e++) {
+                const unsigned g = g0 + e * NT;
+                i0[e] = ((g >> p) << (p + 1)) | (g & (bit - 1u));
+                if (g < N / 2) {
+                    a[e] = psi[i0[e]];
+                    b[e] = psi[i0[e] | bit];
+                }
             }
-            psi[i0 | bit] = d;
+#pragma unroll
+            for (int e = 0; e < U4; e++) {
+                if (g0 + e * NT >= N / 2) break;
+                V d;
+                d.x = a[e].x - b[e].x;
+                d.y = a[e].y - b[e].y;
+                psi[i0[e]] = V{a[e].x + b[e].x, a[e].y + b[e].y};
+                if (!walsh) {
+                    const unsigned r = (i0[e] >> f0) & rmask;
+                    if (r) d = cmulb(d, W[r << (K - 1 - j)]);
+                }
+                psi[i0[e] | bit] = d;
+            }
         }
         __syncthreads();
     }
@@ -186,8 +202,76 @@ __device__ void op_fourier(V *psi, int n, const BOp &op, const V *data, int tid,
     }
 }
 
+// The same transform for a state updated in place in global memory (L2): tile by tile through
+// the CTA's shared memory.  A tile is the whole field times the L lowest qubits (lanes, below
+// the field); it is read once, all K stages run on it in shared memory, and the write-back
+// undoes the digit reversal and applies the scaling and the output twiddle.  One L2 read and
+// write per amplitude instead of one per stage.
+template <typename V>
+__device__ void op_fourier_tiled(V *g, int n, const BOp &op, const V *data, int tid, bool walsh, V *sm, int L) {
+    constexpr int NT = Threads<V>::n;
+    using Rr = decltype(V{}.x);
+    const int K = op.k, f0 = op.c0;
+    const unsigned TN = 1u << (K + L), lmask = (1u << L) - 1u;
+    const int mid = f0 - L;  // qubits between the lanes and the field
+    const unsigned ntile = 1u << (n - K - L);
+    const V *W = data + op.data;
+    const int twmode = walsh ? 0 : op.t[1];
+    const int ns = op.nreg, s0 = op.t[0], hT = op.t[3];
+    const V *Tlo = data + op.data2, *Thi = Tlo + (1u << hT);
+    const unsigned smask = (1u << ns) - 1u, tmask = (1u << hT) - 1u;
+    auto tw = [&](unsigned i, unsigned y) -> V {
+        const unsigned q = ((i >> s0) & smask) * y;
+        return cmulb(Tlo[q & tmask], Thi[q >> hT]);
+    };
+    auto gidx = [&](unsigned o, unsigned j) -> unsigned {  // tile o, local index j = lane + (y << L)
+        const unsigned olo = o & ((1u << mid) - 1u), ohi = o >> mid;
+        return (j & lmask) | (olo << L) | ((j >> L) << f0) | (ohi << (f0 + K));
+    };
+    const Rr scale = (K & 1) ? (Rr)(0.70710678118654752440 / (double)(1u << (K / 2))) : (Rr)(1.0 / (double)(1u << (K / 2)));
+    for (unsigned o = 0; o < ntile; o++) {
+        for (unsigned j = tid; j < TN; j += NT) {
+            const unsigned gi = gidx(o, j);
+            V x = g[gi];
+            if (twmode == 1) x = cmulb(x, tw(gi, j >> L));
+            sm[j] = x;
+        }
+        __syncthreads();
+        for (int jj = K - 1; jj >= 0; jj--) {
+            const int p = L + jj;
+            const unsigned bit = 1u << p, rmask = (1u << jj) - 1u;
+            for (unsigned q = tid; q < TN / 2; q += NT) {
+                const unsigned i0 = ((q >> p) << (p + 1)) | (q & (bit - 1u));
+                const V a = sm[i0], b = sm[i0 | bit];
+                V d;
+                d.x = a.x - b.x;
+                d.y = a.y - b.y;
+                sm[i0] = V{a.x + b.x, a.y + b.y};
+                if (!walsh) {
+                    const unsigned r = (i0 >> L) & rmask;
+                    if (r) d = cmulb(d, W[r << (K - 1 - jj)]);
+                }
+                sm[i0 | bit] = d;
+            }
+            __syncthreads();
+        }
+        for (unsigned j = tid; j < TN; j += NT) {
+            const unsigned y = j >> L;
+            const unsigned yr = walsh ? y : (__brev(y) >> (32 - K));
+            V v = sm[(j & lmask) | (yr << L)];  // position yr holds output y
+            v.x *= scale;
+            v.y *= scale;
+            const unsigned gi = gidx(o, j);
+            if (twmode == 2) v = cmulb(v, tw(gi, y));
+            g[gi] = v;
+        }
+        __syncthreads();  // the next tile reuses the buffer
+    }
+}
+
 template <typename R>
-__device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typename C2<R>::T *data, int tid) {
+__device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typename C2<R>::T *data, int tid,
+                       typename C2<R>::T *sm, int smem_log) {
     using V = typename C2<R>::T;
     constexpr int kThreads = Threads<V>::n;
     const V *d = data + op.data;
@@ -282,16 +366,33 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
             }
             break;
         }
-        case B_DFT: op_fourier<V>(psi, n, op, data, tid, false); break;
-        case B_WALSH: op_fourier<V>(psi, n, op, data, tid, true); break;
+        case B_DFT:
+        case B_WALSH: {
+            const bool walsh = op.kind == B_WALSH;
+            const int L = min((int)op.c0, smem_log - (int)op.k);  // lanes below the field
+            if (psi != sm && L >= 0) op_fourier_tiled<V>(psi, n, op, data, tid, walsh, sm, L);
+            else op_fourier<V>(psi, n, op, data, tid, walsh);
+            break;
+        }
         case B_QPE: {  // data qubits 0..k-1, clock register k..k+nreg-1, split at c0 bits
             const V *hi = data + op.data2;
             const unsigned N = 1u << n, dmask = (1u << op.k) - 1u, cm = (1u << op.nreg) - 1u;
             const unsigned hm = (1u << op.c0) - 1u;
-            for (unsigned i = tid; i < N; i += kThreads) {
-                const unsigned dd = i & dmask, c = (i >> op.k) & cm;
-                const V p = cmulb(d[((c & hm) << op.k) + dd], hi[((c >> op.c0) << op.k) + dd]);
-                psi[i] = cmulb(psi[i], p);
+            constexpr int U4 = 2;  // independent amplitudes per iteration (loads in flight together)
+            for (unsigned i0 = tid; i0 < N; i0 += U4 * kThreads) {
+                V x[U4], ph[U4];
+#pragma unroll
+                for (int e = 0; e < U4; e++) {
+                    const unsigned i = i0 + e * kThreads;
+                    if (i < N) {
+                        const unsigned dd = i & dmask, c = (i >> op.k) & cm;
+                        x[e] = psi[i];
+                        ph[e] = cmulb(d[((c & hm) << op.k) + dd], hi[((c >> op.c0) << op.k) + dd]);
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < U4; e++)
+                    if (i0 + e * kThreads < N) psi[i0 + e * kThreads] = cmulb(x[e], ph[e]);
             }
             break;
         }
@@ -325,6 +426,7 @@ __global__ void __launch_bounds__(Threads<typename C2<R>::T>::n) batched_kernel(
     __shared__ int cur;
     __shared__ double red[32];
     const int tid = threadIdx.x;
+    const int smem_log = 31 - __clz(smem_amps);
     for (;;) {
         if (tid == 0) cur = (int)atomicAdd(counter, 1u);
         __syncthreads();
@@ -334,7 +436,8 @@ __global__ void __launch_bounds__(Threads<typename C2<R>::T>::n) batched_kernel(
         const BCirc c = circs[order[ci]];
         const unsigned N = 1u << c.n;
         V *g = reinterpret_cast<V *>(c.state);
-        V *psi = (int)N <= smem_amps ? sm : g;
+        V *psi = (int)N <= smem_amps ? sm : g;  // larger states stay in global memory (L2); the
+                                                 // passes then tile through shared memory
         const V *data = reinterpret_cast<const V *>(c.data);
         if (c.flags & 1) {
             const unsigned Db = 1u << c.nb;
@@ -344,7 +447,7 @@ __global__ void __launch_bounds__(Threads<typename C2<R>::T>::n) batched_kernel(
         }
         __syncthreads();
         for (int o = 0; o < c.nops; o++) {
-            run_op<R>(psi, c.n, c.ops[o], data, tid);
+            run_op<R>(psi, c.n, c.ops[o], data, tid, sm, smem_log);
             __syncthreads();
         }
         if (c.flags & 2) {
