@@ -39,7 +39,8 @@ enum BKind : unsigned char {
 
 struct BOp {
     unsigned char kind, k, c0, nreg;  // c0 / nreg: UCRY control register (contiguous);
-                                      // B_INVERT: t[1] = rotation of that register
+                                      // B_INVERT: t[1] = rotation of that register;
+                                      // B_DENSE: c0 = 1 if U is real
     signed char t[8];                 // targets in matrix-bit order (UCRY: t[0] = target)
     unsigned fixmask;                 // targets | controls (zero bits inserted when enumerating)
     unsigned cmask;                   // controls that must be 1 (PHASE: all its qubits)
@@ -68,7 +69,7 @@ __device__ __forceinline__ unsigned expand(unsigned g, unsigned fixmask) {
     return g;
 }
 
-template <typename V, int K>
+template <typename V, int K, bool REAL>
 __device__ void op_dense(V *psi, int n, const BOp &op, const V *U, int tid) {
     constexpr int D = 1 << K;
     constexpr int NT = Threads<V>::n;
@@ -106,9 +107,11 @@ __device__ void op_dense(V *psi, int n, const BOp &op, const V *U, int tid) {
                 for (int c = 0; c < D; c++) {
                     const V w = u[c];
                     acc.x = fma(w.x, x[j][c].x, acc.x);
-                    acc.x = fma(-w.y, x[j][c].y, acc.x);
                     acc.y = fma(w.x, x[j][c].y, acc.y);
-                    acc.y = fma(w.y, x[j][c].x, acc.y);
+                    if (!REAL) {  // real U: the imaginary parts are zero
+                        acc.x = fma(-w.y, x[j][c].y, acc.x);
+                        acc.y = fma(w.y, x[j][c].x, acc.y);
+                    }
                 }
                 if (live[j]) psi[base[j] + offs[r]] = acc;
             }
@@ -277,14 +280,24 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
     const V *d = data + op.data;
     switch (op.kind) {
         case B_DENSE:
-            switch (op.k) {
-                case 1: op_dense<V, 1>(psi, n, op, d, tid); break;
-                case 2: op_dense<V, 2>(psi, n, op, d, tid); break;
-                case 3: op_dense<V, 3>(psi, n, op, d, tid); break;
-                case 4: op_dense<V, 4>(psi, n, op, d, tid); break;
-                case 5: op_dense<V, 5>(psi, n, op, d, tid); break;
-                default: break;
-            }
+            if (op.c0)  // real U (flag set by the encoder)
+                switch (op.k) {
+                    case 1: op_dense<V, 1, true>(psi, n, op, d, tid); break;
+                    case 2: op_dense<V, 2, true>(psi, n, op, d, tid); break;
+                    case 3: op_dense<V, 3, true>(psi, n, op, d, tid); break;
+                    case 4: op_dense<V, 4, true>(psi, n, op, d, tid); break;
+                    case 5: op_dense<V, 5, true>(psi, n, op, d, tid); break;
+                    default: break;
+                }
+            else
+                switch (op.k) {
+                    case 1: op_dense<V, 1, false>(psi, n, op, d, tid); break;
+                    case 2: op_dense<V, 2, false>(psi, n, op, d, tid); break;
+                    case 3: op_dense<V, 3, false>(psi, n, op, d, tid); break;
+                    case 4: op_dense<V, 4, false>(psi, n, op, d, tid); break;
+                    case 5: op_dense<V, 5, false>(psi, n, op, d, tid); break;
+                    default: break;
+                }
             break;
         case B_PHASE: {
             const unsigned cnt = 1u << (n - __popc(op.fixmask));
@@ -569,6 +582,7 @@ bool encode(const Op &op, int dtype, std::vector<unsigned char> &data, BOp &b) {
             if (k > 5) return false;
             b.kind = batch::B_DENSE;
             b.k = (unsigned char)k;
+            b.c0 = op.real_u ? 1 : 0;  // B_DENSE: real U flag
             for (int i = 0; i < k; i++) b.t[i] = (signed char)op.targets[i];
             b.cmask = maskq(op.controls);
             b.fixmask = maskq(op.targets) | b.cmask;
