@@ -372,6 +372,9 @@ class Batch:
         self._ptr = ptr
         self._keep = keep
         self._hhl = hhl
+        self._Ns = [h.info()["N"] for h in hhl] if hhl is not None else None
+        self._stats = None
+        self._x = None
 
     @property
     def ptr(self):
@@ -380,21 +383,27 @@ class Batch:
     def run(self, stream=None):
         _check(library().qsim_batch_run(self._ptr, _stream_ptr(stream)))
 
-    def results(self, stream=None):
-        """HHL batches: list of dicts (x and the readout statistics) per entry."""
+    def results_arrays(self, stream=None):
+        """HHL batches: (x, stats) -- all solutions concatenated (complex128, entry i has N_i
+        values, in batch order) and a structured array of the readout statistics per entry.
+        The buffers are reused by the next call."""
         if self._hhl is None:
             raise QsimError(-1, "not an HHL batch")
-        infos = [h.info() for h in self._hhl]
-        total = sum(i["N"] for i in infos)
-        x = np.zeros(max(1, total), dtype=np.complex128)
-        st = (_ReadoutStats * len(infos))()
+        if self._x is None:
+            self._x = np.zeros(max(1, sum(self._Ns)), dtype=np.complex128)
+            self._stats = (_ReadoutStats * len(self._Ns))()
         _check(library().hhl_batch_results(self._ptr, _stream_ptr(stream),
-                                           x.view(np.float64).ctypes.data_as(_DP), st))
+                                           self._x.view(np.float64).ctypes.data_as(_DP), self._stats))
+        return self._x, np.ctypeslib.as_array(self._stats)
+
+    def results(self, stream=None):
+        """HHL batches: list of dicts (x and the readout statistics) per entry."""
+        x, st = self.results_arrays(stream)
         out, o = [], 0
-        for i, inf in enumerate(infos):
-            d = {f: getattr(st[i], f) for f, _ in st[i]._fields_}
-            d["x"] = x[o:o + inf["N"]].copy()
-            o += inf["N"]
+        for i, n in enumerate(self._Ns):
+            d = {f: float(st[i][f]) for f, _ in _ReadoutStats._fields_}
+            d["x"] = x[o:o + n].copy()
+            o += n
             out.append(d)
         return out
 
