@@ -86,6 +86,45 @@ __device__ void op_dense(V *psi, int n, const BOp &op, const V *U, int tid) {
             if ((r >> b) & 1) o |= 1u << op.t[b];
         offs[r] = o;
     }
+    if (sizeof(V) == 16 && ngroups < (unsigned)(ILP * NT)) {
+        // complex128 with fewer groups than the loop below has slots (small states): S =
+        // min(D, NT / ngroups) threads share a group, each computing D / S of its rows, so that
+        // the FP64 work, whose pipe is narrow, spreads over every warp instead of the first
+        // (and no dead second group issues arithmetic); a barrier separates the group's loads
+        // from its stores.  ngroups and NT are powers of two.  complex64 keeps the loop: its
+        // arithmetic is cheap and the loop's two interleaved groups pay more than the split.
+        const int S = min(D, NT / (int)ngroups);
+        const unsigned gi = (unsigned)tid / (unsigned)S;
+        const int s = tid & (S - 1);
+        const bool live = gi < ngroups;
+        const unsigned base = live ? (expand(gi, op.fixmask) | op.cmask) : 0u;
+        V x[D];
+#pragma unroll
+        for (int c = 0; c < D; c++) x[c] = live ? psi[base + offs[c]] : V{0, 0};
+        __syncthreads();
+        if (!live) return;
+#pragma unroll 1
+        for (int r = s; r < D; r += S) {
+            const V *u = U + r * D;
+            V acc{0, 0};
+#pragma unroll
+            for (int c = 0; c < D; c++) {
+                const V w = u[c];
+                acc.x = fma(w.x, x[c].x, acc.x);
+                acc.y = fma(w.x, x[c].y, acc.y);
+                if (!REAL) {
+                    acc.x = fma(-w.y, x[c].y, acc.x);
+                    acc.y = fma(w.y, x[c].x, acc.y);
+                }
+            }
+            unsigned o = 0;  // offs[r] without a dynamic register-array index
+#pragma unroll
+            for (int b = 0; b < K; b++)
+                if ((r >> b) & 1) o |= 1u << op.t[b];
+            psi[base + o] = acc;
+        }
+        return;
+    }
     for (unsigned g0 = tid; g0 < ngroups; g0 += ILP * NT) {
         unsigned base[ILP];
         bool live[ILP];
