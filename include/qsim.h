@@ -287,19 +287,28 @@ int qsim_batch_create(const qsim_circuit *const *cs, void *const *states, int co
 int hhl_batch_create(const hhl_circuit *const *hs, const qsim_circuit *const *fused,
                      void *const *states, int count, int dtype, qsim_batch **out);
 
-/* Run the batch: one cudaMemsetAsync of the work counter and one persistent kernel on
- * `stream`, nothing else (no allocation, no synchronization), so the call can be captured
- * into a CUDA graph.  Each CTA takes whole circuits (most expensive first); a state of up to
+/* Run the batch: one persistent kernel on `stream`, nothing else (no allocation, no copy, no
+ * synchronization; the kernel resets its own work counter when it ends), so the call can be
+ * captured into a CUDA graph.  Runs of one batch must not overlap (same stream, or ordered).  Each CTA takes whole circuits (most expensive first); a state of up to
  * 2^13 (complex128) or 2^14 (complex64) amplitudes stays in shared memory for the whole
  * circuit, larger ones are updated in place.  One CTA runs one circuit in a fixed order, so a
  * circuit's result is bit-identical whatever else is in the batch; it equals qsim_apply of
  * the same circuit up to rounding (different kernels).  Errors: EINVAL, ECUDA. */
 int qsim_batch_run(qsim_batch *b, void *stream);
 
-/* After an HHL batch ran on `stream`: copy the results (synchronizes `stream`) and write, for
- * batch entry i in order, x_i (N_i complex, concatenated into x_out) and stats[i], as
- * hhl_readout would.  x_out / stats may be NULL.  Errors: EINVAL, ECUDA. */
+/* After an HHL batch ran on `stream`: wait for `stream` and write, for batch entry i in order,
+ * x_i (N_i complex, concatenated into x_out) and stats[i], as hhl_readout would.  The kernel
+ * writes its readout sums straight into the batch's pinned host buffer (no copy), so a run
+ * overwrites them; the outputs here are the caller's and stay as written.  x_out / stats may
+ * be NULL.  Errors: EINVAL, ECUDA. */
 int hhl_batch_results(qsim_batch *b, void *stream, double *x_out, hhl_readout_stats *stats);
+
+/* One solve of every circuit of an HHL batch in a single call: qsim_batch_run followed by
+ * hhl_batch_results on `stream` (one kernel launch, which writes the readout sums into pinned
+ * host memory, one stream synchronization, the host-side scaling of Sec. III-A steps 3-4), for
+ * latency-bound use such as one small system at a time.  x_out / stats as in
+ * hhl_batch_results (caller-owned, may be NULL).  Errors: EINVAL, ECUDA. */
+int hhl_batch_solve(qsim_batch *b, void *stream, double *x_out, hhl_readout_stats *stats);
 
 void qsim_batch_free(qsim_batch *b);
 

@@ -96,6 +96,7 @@ _SIGS = {
                           ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
     "qsim_batch_run": ([_VP, _VP], ctypes.c_int),
     "hhl_batch_results": ([_VP, _VP, _DP, ctypes.POINTER(_ReadoutStats)], ctypes.c_int),
+    "hhl_batch_solve": ([_VP, _VP, _DP, ctypes.POINTER(_ReadoutStats)], ctypes.c_int),
     "qsim_batch_free": ([_VP], None),
     "hhl_batch_autotune": ([ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _IP,
                             ctypes.c_int, _VP, _IP, _DP], ctypes.c_int),
@@ -387,14 +388,25 @@ class Batch:
         """HHL batches: (x, stats) -- all solutions concatenated (complex128, entry i has N_i
         values, in batch order) and a structured array of the readout statistics per entry.
         The buffers are reused by the next call."""
+        self._result_buffers()
+        _check(library().hhl_batch_results(self._ptr, _stream_ptr(stream), self._xp, self._stats))
+        return self._x, self._stats_np
+
+    def solve(self, stream=None):
+        """HHL batches: run the batch and read its results in one library call (launch, copy,
+        synchronize, host scaling); returns (x, stats) as results_arrays does."""
+        self._result_buffers()
+        _check(library().hhl_batch_solve(self._ptr, _stream_ptr(stream), self._xp, self._stats))
+        return self._x, self._stats_np
+
+    def _result_buffers(self):
         if self._hhl is None:
             raise QsimError(-1, "not an HHL batch")
         if self._x is None:
             self._x = np.zeros(max(1, sum(self._Ns)), dtype=np.complex128)
+            self._xp = self._x.view(np.float64).ctypes.data_as(_DP)
             self._stats = (_ReadoutStats * len(self._Ns))()
-        _check(library().hhl_batch_results(self._ptr, _stream_ptr(stream),
-                                           self._x.view(np.float64).ctypes.data_as(_DP), self._stats))
-        return self._x, np.ctypeslib.as_array(self._stats)
+            self._stats_np = np.ctypeslib.as_array(self._stats)
 
     def results(self, stream=None):
         """HHL batches: list of dicts (x and the readout statistics) per entry."""

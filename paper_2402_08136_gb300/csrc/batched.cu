@@ -46,7 +46,9 @@ struct BOp {
     unsigned cmask;                   // controls that must be 1 (PHASE: all its qubits)
     unsigned data;                    // element offset into the circuit's data
     unsigned data2;                   // B_QPE: offset of the second phase table
+    unsigned pad;                     // 32-byte records (copied to shared memory in 16-byte units)
 };
+static_assert(sizeof(BOp) == 32, "BOp is copied in 16-byte units");
 
 struct BCirc {
     void *state;
@@ -54,7 +56,8 @@ struct BCirc {
     const void *data;
     double *result;  // readout: [norm2, P, P0, pad] then 2^nb complex (re, im) doubles
     int n, nops, nb, flags;  // flags: 1 = prepare |0>|0>|b>, 2 = readout sums and slice
-    unsigned b_off, pad;
+    unsigned b_off;       // element offset of b (HHL preparation) in the data
+    unsigned data_bytes;  // size of the circuit's data (a multiple of 8)
 };
 
 template <typename R> struct C2;
@@ -452,31 +455,50 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
     }
 }
 
+// Three CTA-wide FP64 sums at once (one pair of barriers instead of three), each in a fixed
+// order: warp shuffles, then the warp totals in warp order; thread 0 receives the totals.
 template <int kThreads>
-__device__ __forceinline__ double block_sum_b(double v, double *sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+__device__ __forceinline__ void block_sum3(double &a, double &b, double &c, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    constexpr int W = kThreads >> 5;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (w == 0) {
-        r = l < (kThreads >> 5) ? sh[l] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    if (l == 0) {
+        sh[w] = a;
+        sh[W + w] = b;
+        sh[2 * W + w] = c;
     }
     __syncthreads();
-    return r;
+    if (w == 0) {
+        a = l < W ? sh[l] : 0.0;
+        b = l < W ? sh[W + l] : 0.0;
+        c = l < W ? sh[2 * W + l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+            c += __shfl_down_sync(0xffffffffu, c, o);
+        }
+    }
+    __syncthreads();
 }
 
 template <typename R>
 __global__ void __launch_bounds__(Threads<typename C2<R>::T>::n) batched_kernel(const BCirc *circs, const int *order,
                                                                               int count, unsigned *counter,
-                                                                              int smem_amps) {
+                                                                              int smem_amps, int stage_bytes) {
     using V = typename C2<R>::T;
     constexpr int kThreads = Threads<V>::n;
     extern __shared__ __align__(16) unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
+    // after the state area: the running circuit's data (matrices, tables) and op list when they
+    // fit, so that each op reads its descriptor and operands from shared memory rather than
+    // through two dependent L2 round trips
+    unsigned char *stage = smraw + (((size_t)smem_amps * sizeof(V) + 15) & ~(size_t)15);
     __shared__ int cur;
-    __shared__ double red[32];
+    __shared__ double red[3 * (Threads<V>::n >> 5)];
     const int tid = threadIdx.x;
     const int smem_log = 31 - __clz(smem_amps);
     for (;;) {
@@ -484,22 +506,50 @@ __global__ void __launch_bounds__(Threads<typename C2<R>::T>::n) batched_kernel(
         __syncthreads();
         const int ci = cur;
         __syncthreads();
-        if (ci >= count) break;
+        if (ci >= count) {
+            // Every CTA ends with one increment that returns count or more; the one that
+            // returns count + gridDim.x - 1 is the launch's last, so it puts the counter back to
+            // zero for the next launch (no separate reset before each run).
+            if (tid == 0 && ci == count + (int)gridDim.x - 1) *counter = 0u;
+            break;
+        }
         const BCirc c = circs[order[ci]];
         const unsigned N = 1u << c.n;
         V *g = reinterpret_cast<V *>(c.state);
         V *psi = (int)N <= smem_amps ? sm : g;  // larger states stay in global memory (L2); the
                                                  // passes then tile through shared memory
-        const V *data = reinterpret_cast<const V *>(c.data);
+        const V *gdata = reinterpret_cast<const V *>(c.data);
+        const V *data = gdata;
+        const BOp *ops = c.ops;
+        {
+            // data (8-byte units: its size is a multiple of 8 and it starts 256-byte aligned)
+            // first, then the ops (32-byte records, 16-byte units)
+            const unsigned ob = (unsigned)c.nops * (unsigned)sizeof(BOp);
+            const unsigned db = (c.data_bytes + 15u) & ~15u;
+            const bool with_data = db + ob <= (unsigned)stage_bytes;
+            if (with_data) {
+                const uint2 *src = reinterpret_cast<const uint2 *>(c.data);
+                uint2 *dst = reinterpret_cast<uint2 *>(stage);
+                for (unsigned i = tid; i < c.data_bytes / 8u; i += kThreads) dst[i] = src[i];
+                data = reinterpret_cast<const V *>(stage);
+            }
+            if (ob <= (unsigned)stage_bytes) {
+                const unsigned o0 = with_data ? db : 0u;
+                const uint4 *src = reinterpret_cast<const uint4 *>(c.ops);
+                uint4 *dst = reinterpret_cast<uint4 *>(stage + o0);
+                for (unsigned i = tid; i < ob / 16u; i += kThreads) dst[i] = src[i];
+                ops = reinterpret_cast<const BOp *>(stage + o0);
+            }
+        }
         if (c.flags & 1) {
             const unsigned Db = 1u << c.nb;
-            for (unsigned i = tid; i < N; i += kThreads) psi[i] = i < Db ? data[c.b_off + i] : V{0, 0};
+            for (unsigned i = tid; i < N; i += kThreads) psi[i] = i < Db ? gdata[c.b_off + i] : V{0, 0};
         } else if (psi == sm) {
             for (unsigned i = tid; i < N; i += kThreads) psi[i] = g[i];
         }
         __syncthreads();
         for (int o = 0; o < c.nops; o++) {
-            run_op<R>(psi, c.n, c.ops[o], data, tid, sm, smem_log);
+            run_op<R>(psi, c.n, ops[o], data, tid, sm, smem_log);
             __syncthreads();
         }
         if (c.flags & 2) {
@@ -519,13 +569,11 @@ __global__ void __launch_bounds__(Threads<typename C2<R>::T>::n) batched_kernel(
                 c.result[4 + 2 * i] = (double)z.x;
                 c.result[4 + 2 * i + 1] = (double)z.y;
             }
-            const double ta = block_sum_b<kThreads>(s_all, red);
-            const double th = block_sum_b<kThreads>(s_hi, red);
-            const double ts = block_sum_b<kThreads>(s_sl, red);
+            block_sum3<kThreads>(s_all, s_hi, s_sl, red);
             if (tid == 0) {
-                c.result[0] = ta;
-                c.result[1] = th;
-                c.result[2] = ts;
+                c.result[0] = s_all;
+                c.result[1] = s_hi;
+                c.result[2] = s_sl;
             }
         }
         if (psi == sm)
@@ -539,7 +587,7 @@ __global__ void __launch_bounds__(Threads<typename C2<R>::T>::n) batched_kernel(
 
 // ------------------------------------------------------------------------------- host side
 struct qsim_batch {
-    int count = 0, dtype = 0, smem_amps = 0, grid = 1;
+    int count = 0, dtype = 0, smem_amps = 0, stage_bytes = 0, grid = 1;
     size_t smem_bytes = 0;
     bool hhl = false;
     void *dev = nullptr;  // one allocation: circs | order | counter | ops | data | results
@@ -557,6 +605,7 @@ struct qsim_batch {
     };
     std::vector<Meta> meta;
     bool external = false;  // device tables and pinned results owned by the serving pool
+    bool results_on_host = false;  // the kernel writes the readout into h_results directly
     ~qsim_batch() {
         if (external) return;
         if (dev) cudaFree(dev);
@@ -743,8 +792,13 @@ struct BatchImage {
     size_t results = 0;
     std::vector<qsim_batch::Meta> meta;
     int count = 0, dtype = 0, max_n = 0;
+    size_t stage_bytes = 0;  // shared memory for the largest circuit's data and op list (capped)
     bool hhl = false;
 };
+
+// Shared memory set aside per CTA for a circuit's data and op list (larger ones stay in global
+// memory; an op list alone is staged when it fits).
+constexpr size_t kStageCap = 32768;
 
 BatchImage batch_image(const std::vector<const qsim_circuit *> &cs, const std::vector<const hhl_circuit *> &hs,
                        void *const *states, int dtype) {
@@ -796,8 +850,11 @@ BatchImage batch_image(const std::vector<const qsim_circuit *> &cs, const std::v
             im.meta[i].roff = im.results;
             im.results += 4 + 2 * ((size_t)1 << h->nb);
         }
+        bc.data_bytes = (unsigned)local.size();
+        im.stage_bytes = std::max(im.stage_bytes, ((local.size() + 15) & ~(size_t)15) + sizeof(BOp) * c->ops.size());
         data.insert(data.end(), local.begin(), local.end());
     }
+    im.stage_bytes = std::min(im.stage_bytes, kStageCap);
     std::vector<int> order(count);
     std::iota(order.begin(), order.end(), 0);
     std::vector<double> cost(count);
@@ -839,14 +896,22 @@ qsim_batch *batch_from_image(BatchImage &im, void *dev, double *pinned_results, 
     }
     B->dev = dev;
     B->dev_bytes = im.total;
+    cudaError_t e;
+    if (im.results && !external) {
+        // pinned host memory is device-accessible under unified addressing: the kernel writes
+        // the readout there itself, so reading the results needs no copy, only the stream's end
+        e = cudaMallocHost(&B->h_results, sizeof(double) * im.results);
+        if (e != cudaSuccess) throw Error(QSIM_ENOMEM, "pinned host buffer for batch results");
+        B->results_on_host = true;
+    }
     unsigned char *base = static_cast<unsigned char *>(dev);
+    double *res = B->results_on_host ? B->h_results : reinterpret_cast<double *>(base + im.o_res);
     batch::BCirc *hc = reinterpret_cast<batch::BCirc *>(im.host.data() + im.o_circs);
     for (int i = 0; i < im.count; i++) {
         hc[i].ops = reinterpret_cast<const BOp *>(base + im.o_ops) + im.op_first[i];
         hc[i].data = base + im.o_data + im.data_first[i];
-        hc[i].result = im.hhl ? reinterpret_cast<double *>(base + im.o_res) + im.meta[i].roff : nullptr;
+        hc[i].result = im.hhl ? res + im.meta[i].roff : nullptr;
     }
-    cudaError_t e;
     if (external) {
         // from pageable memory: the call returns once the source has been staged
         e = cudaMemcpyAsync(dev, im.host.data(), im.host.size(), cudaMemcpyHostToDevice, st);
@@ -859,16 +924,10 @@ qsim_batch *batch_from_image(BatchImage &im, void *dev, double *pinned_results, 
     B->d_counter = reinterpret_cast<unsigned *>(base + im.o_counter);
     B->d_results = reinterpret_cast<double *>(base + im.o_res);
     B->results_doubles = im.results;
-    if (im.results) {
-        if (external) {
-            B->h_results = pinned_results;
-        } else {
-            e = cudaMallocHost(&B->h_results, sizeof(double) * im.results);
-            if (e != cudaSuccess) throw Error(QSIM_ENOMEM, "pinned host buffer for batch results");
-        }
-    }
+    if (im.results && external) B->h_results = pinned_results;
     const int cap_amps = im.dtype == QSIM_C128 ? (1 << 13) : (1 << 14);
     B->smem_amps = std::min(cap_amps, 1 << im.max_n);
+    B->stage_bytes = (int)im.stage_bytes;
     if (im.dtype == QSIM_C128) configure_batch<double>(B.get());
     else configure_batch<float>(B.get());
     return B.release();
@@ -924,7 +983,7 @@ namespace {
 // memset and a launch (capturable into a CUDA graph).
 template <typename R>
 void configure_batch(qsim_batch *B) {
-    const size_t smem = (size_t)B->smem_amps * vbytes(B->dtype);
+    const size_t smem = (((size_t)B->smem_amps * vbytes(B->dtype) + 15) & ~(size_t)15) + (size_t)B->stage_bytes;
     auto kern = batch::batched_kernel<R>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel attribute: ") + cudaGetErrorString(e));
@@ -938,13 +997,12 @@ void configure_batch(qsim_batch *B) {
     B->smem_bytes = smem;
 }
 
+// The work counter is zero when the batch is uploaded and the kernel leaves it at zero.
 template <typename R>
 void launch_batch(qsim_batch *B, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned), st);
-    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batch counter reset: ") + cudaGetErrorString(e));
     batch::batched_kernel<R><<<B->grid, batch::Threads<typename batch::C2<R>::T>::n, B->smem_bytes, st>>>(B->d_circs, B->d_order, B->count,
-                                                                              B->d_counter, B->smem_amps);
-    e = cudaGetLastError();
+                                                                              B->d_counter, B->smem_amps, B->stage_bytes);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel: ") + cudaGetErrorString(e));
 }
 
@@ -960,7 +1018,7 @@ void run_batch(qsim_batch *B, void *stream) {
 void batch_launch(qsim_batch *b, cudaStream_t st) { run_batch(b, st); }
 
 void batch_enqueue_results(qsim_batch *b, cudaStream_t st) {
-    if (!b->results_doubles) return;
+    if (!b->results_doubles || b->results_on_host) return;
     cudaError_t e = cudaMemcpyAsync(b->h_results, b->d_results, sizeof(double) * b->results_doubles,
                                     cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batch results: ") + cudaGetErrorString(e));
@@ -1025,38 +1083,60 @@ int qsim_batch_run(qsim_batch *b, void *stream) {
     });
 }
 
+}  // extern "C"
+
+namespace {
+
+void collect_results(qsim_batch *b, void *stream, double *x_out, hhl_readout_stats *stats) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (b->results_doubles) {
+        cudaError_t e = cudaSuccess;
+        if (!b->results_on_host)
+            e = cudaMemcpyAsync(b->h_results, b->d_results, sizeof(double) * b->results_doubles,
+                                cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batch results: ") + cudaGetErrorString(e));
+    }
+    size_t xo = 0;
+    for (int i = 0; i < b->count; i++) {
+        const qsim_batch::Meta &m = b->meta[i];
+        const double *r = b->h_results + m.roff;
+        const double P = r[1], P0 = r[2];
+        const double inv = P0 > 0 ? 1.0 / std::sqrt(P0) : 0.0;
+        const double norm_x = std::sqrt(P) / m.C;
+        if (x_out)
+            for (int j = 0; j < m.N; j++) {
+                x_out[2 * (xo + j)] = r[4 + 2 * (m.x_off + j)] * inv * norm_x * m.norm_b;
+                x_out[2 * (xo + j) + 1] = r[4 + 2 * (m.x_off + j) + 1] * inv * norm_x * m.norm_b;
+            }
+        xo += m.N;
+        if (stats) {
+            stats[i].p_success = P;
+            stats[i].p_clock0 = P0;
+            stats[i].leakage = P - P0;
+            stats[i].norm2 = r[0];
+            stats[i].norm_x = norm_x;
+            stats[i].norm_b = m.norm_b;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
 int hhl_batch_results(qsim_batch *b, void *stream, double *x_out, hhl_readout_stats *stats) {
     return guarded([&] {
         QSIM_REQUIRE(b != nullptr && b->hhl, "not an HHL batch");
-        cudaStream_t st = static_cast<cudaStream_t>(stream);
-        if (b->results_doubles) {
-            cudaError_t e = cudaMemcpyAsync(b->h_results, b->d_results, sizeof(double) * b->results_doubles,
-                                            cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batch results: ") + cudaGetErrorString(e));
-        }
-        size_t xo = 0;
-        for (int i = 0; i < b->count; i++) {
-            const qsim_batch::Meta &m = b->meta[i];
-            const double *r = b->h_results + m.roff;
-            const double P = r[1], P0 = r[2];
-            const double inv = P0 > 0 ? 1.0 / std::sqrt(P0) : 0.0;
-            const double norm_x = std::sqrt(P) / m.C;
-            if (x_out)
-                for (int j = 0; j < m.N; j++) {
-                    x_out[2 * (xo + j)] = r[4 + 2 * (m.x_off + j)] * inv * norm_x * m.norm_b;
-                    x_out[2 * (xo + j) + 1] = r[4 + 2 * (m.x_off + j) + 1] * inv * norm_x * m.norm_b;
-                }
-            xo += m.N;
-            if (stats) {
-                stats[i].p_success = P;
-                stats[i].p_clock0 = P0;
-                stats[i].leakage = P - P0;
-                stats[i].norm2 = r[0];
-                stats[i].norm_x = norm_x;
-                stats[i].norm_b = m.norm_b;
-            }
-        }
+        collect_results(b, stream, x_out, stats);
+    });
+}
+
+int hhl_batch_solve(qsim_batch *b, void *stream, double *x_out, hhl_readout_stats *stats) {
+    return guarded([&] {
+        QSIM_REQUIRE(b != nullptr && b->hhl, "not an HHL batch");
+        run_batch(b, stream);
+        collect_results(b, stream, x_out, stats);
     });
 }
 

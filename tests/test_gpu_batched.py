@@ -176,6 +176,66 @@ def test_batch_run_captures_in_cuda_graph(qs, cuda_device):
         assert a["p_success"] == c["p_success"] and np.array_equal(a["x"], c["x"])
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_repeated_runs_reset_the_work_counter(qs, dtype, cuda_device):
+    """More circuits than CTAs (each CTA takes several), run three times eagerly and twice from
+    a CUDA graph: every run must apply every circuit once more (the kernel leaves its work
+    counter at zero for the next launch), so each state ends at U^5 psi."""
+    rng = np.random.default_rng(41)
+    count = 400
+    circs, refs, inputs = [], [], []
+    for i in range(count):
+        n = int(rng.integers(3, 9))
+        c, g = random_circuit(qs, rng, n, 8)
+        psi = synth.gaussian_state_np(500 + i, n)
+        if dtype == torch.complex64:
+            psi = psi.astype(np.complex64).astype(np.complex128)
+        ref = psi.copy()
+        for _ in range(5):
+            oracle_apply(ref, g)
+        circs.append(c)
+        refs.append(ref)
+        inputs.append(psi)
+    states = [torch.from_numpy(x).to(dtype).cuda() for x in inputs]
+    b = qs.qsim_batch_create(circs, states)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            b.run(s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    snap = [st.clone() for st in states]
+    with torch.cuda.graph(g, stream=s):
+        b.run(s)
+    for st, x in zip(states, snap):  # capturing records the launch without running it
+        assert torch.equal(st, x)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for st, ref in zip(states, refs):
+        out = st.cpu().numpy().astype(np.complex128)
+        assert np.max(np.abs(out - ref)) <= 5 * TOL[dtype]
+
+
+@pytest.mark.gpu
+def test_hhl_batch_solve_single_call(qs, cuda_device):
+    """hhl_batch_solve (launch, copy, synchronize, host scaling in one call) gives the same
+    bits as a run followed by hhl_batch_results, every time, and the oracle's solution."""
+    p = synth.hhl7_problem()
+    h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"])
+    st = torch.empty(1 << h.info()["n"], dtype=torch.complex128, device="cuda")
+    b = qs.hhl_batch_create([h], [st], [qs.qsim_fuse(h.as_circuit(), 2)])
+    b.run()
+    x0, s0 = (a.copy() for a in b.results_arrays())
+    ref = ohhl.solve(p["A"], p["b"], p["m"], p["t"], p["C"])
+    assert np.max(np.abs(x0 - ref["x"])) <= 1e-11 * np.linalg.norm(ref["x"])
+    for _ in range(50):
+        x, stats = b.solve()
+        assert np.array_equal(x, x0) and np.array_equal(stats, s0)
+    assert qs.qsim_device_status() == 0
+
+
 def test_batch_rejects_wide_dense_gate(qs):
     c = qs.Circuit(8).add_gate(list(range(6)), synth.haar_unitary(np.random.default_rng(0), 64))
     fake = ctypes.c_void_p(256)  # never dereferenced: the op check fails before any CUDA call
