@@ -112,6 +112,12 @@ void run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
             fix.push_back(q);
         }
     a.L = L;
+    {
+        const bool lanes_low = (fmask & ((1ull << L) - 1ull)) == 0;
+        const char *e = std::getenv("QSIM_DFT_PF");
+        const int dist = e ? std::max(0, std::atoi(e)) : 1;  // tiles ahead
+        a.pf = (!a.stage && lanes_low && ((size_t)vb << L) == 128) ? dist : 0;
+    }
     std::sort(fix.begin(), fix.end());
     a.nfix = (int)fix.size();
     for (int i = 0; i < a.nfix; i++) a.fix[i] = fix[i];

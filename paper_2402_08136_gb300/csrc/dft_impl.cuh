@@ -75,6 +75,9 @@ struct DftArgs {
     int stage;                  // 1: the lanes are qubits 0..L-1 and each tile's input is
                                 // prefetched into shared memory (cp.async, double buffer)
     int tw_smem;                // 1: the twiddle tables Tlo, Thi are copied to shared memory
+    int pf;                     // > 0: the lanes are qubits 0..L-1 and a lane run is one
+                                // 128-byte line: each tile prefetches the lines of the tile pf
+                                // steps ahead of it (in this CTA's sequence) into L2
     // structured phase-estimation diagonal exp(i s lam_d t c) applied inside the pass (qmode 1:
     // to the inputs, 2: to the outputs): d = qubits 0..qnb-1, c = qubits qnb..qnb+qm-1, tables
     // qlo[(c mod 2^qh) 2^qnb + d], qhi[(c >> qh) 2^qnb + d]
@@ -346,6 +349,20 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
             }
         }
         dft_regs<N2, SGN, WALSH>(x);
+        if (a.pf) {
+            // this tile's inputs are in registers: pull a later tile's lines into L2 so that
+            // DRAM stays busy through the transform and the stores (thread (u, l) takes the
+            // runs of field values u + N1 v, v = l, l + 2^L, ...: each line once)
+            const long long nt = tix + (long long)a.pf * gridDim.x;
+            if (nt < a.ntiles) {
+                const unsigned long long nb = insert_zero_bits((unsigned long long)nt, a.fix, a.nfix);
+                for (int v = l; v < N2; v += NL) {
+                    const unsigned long long off = CONTIG ? nb + ((unsigned long long)(u + N1 * v) << a.f0)
+                                                          : nb + vlo[u] + vhi[v];
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(psi + off));
+                }
+            }
+        }
 #pragma unroll
         for (int i = 0; i < N2; i++) {
             const int aa = WALSH ? i : bitrev(i, k2);
