@@ -394,8 +394,9 @@ def run_hhl(args, ws, rank, which):
         st = torch.empty(1 << n, dtype=dt, device="cuda")
 
         def solve():
-            qs.hhl_prepare_state(st, h, stream)
-            qs.qsim_apply(st, circ, stream, n_qubits=n)
+            # preparation and circuit; the operations before the inversion on the lower half
+            # (the ancilla is |0> until then)
+            qs.hhl_run(st, h, circ, stream)
             return qs.hhl_readout(st, h, stream)
 
         for _ in range(args.warmup):

@@ -246,6 +246,18 @@ int hhl_get_info(const hhl_circuit *h, hhl_info *out);
  * asynchronously on `stream`.  Errors: EINVAL, ECUDA. */
 int hhl_prepare_state(void *state, int dtype, const hhl_circuit *h, void *stream);
 
+/* The device part of one HHL solve, enqueued on `stream`: prepare |0>_anc |0>_clock |b> in
+ * `state` and apply circuit `c` (h's gate list, or a qsim_fuse of hhl_as_circuit(h); NULL
+ * means h's own list).  The ancilla is the top qubit and stays |0> until the first operation
+ * acting on it (the eigenvalue-inversion rotation of Fig. 5, Sec. III-A step 2), so every
+ * operation before that one runs on the lower half of the state only (the upper half is
+ * exactly zero: half the HBM traffic), the preparation zeroes only the lower half, and the
+ * inversion writes the upper
+ * half without reading it (any other first operation on the ancilla, or none at all, zeroes
+ * the upper half first).  The final state equals hhl_prepare_state followed by qsim_apply of
+ * the same circuit, up to rounding.  Errors: EINVAL, ENOMEM, ECUDA. */
+int hhl_run(void *state, int dtype, const hhl_circuit *h, const qsim_circuit *c, void *stream);
+
 typedef struct {
     double p_success;  /* P(ancilla = 1)                                                       */
     double p_clock0;   /* P(ancilla = 1 and clock = 0)                                         */

@@ -21,6 +21,7 @@ from ._binding import (  # noqa: F401
     hhl_build,
     hhl_build_spectral,
     hhl_prepare_state,
+    hhl_run,
     hhl_readout,
     library,
     library_path,

@@ -89,6 +89,7 @@ _SIGS = {
     "hhl_as_circuit": ([_VP], _VP),
     "hhl_get_info": ([_VP, ctypes.POINTER(_HHLInfo)], ctypes.c_int),
     "hhl_prepare_state": ([_VP, ctypes.c_int, _VP, _VP], ctypes.c_int),
+    "hhl_run": ([_VP, ctypes.c_int, _VP, _VP, _VP], ctypes.c_int),
     "qsim_device_status": ([ctypes.POINTER(ctypes.c_uint), ctypes.c_int], ctypes.c_int),
     "qsim_batch_create": ([ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int,
                            ctypes.POINTER(_VP)], ctypes.c_int),
@@ -340,6 +341,16 @@ def hhl_prepare_state(state, h: HHLCircuit, stream=None):
     _check_state(state, h.info()["n"])
     _check(library().hhl_prepare_state(ctypes.c_void_p(state.data_ptr()), _dtype_of(state), h.ptr,
                                        _stream_ptr(stream)))
+    return state
+
+
+def hhl_run(state, h: HHLCircuit, circuit=None, stream=None):
+    """Prepare |0>|0>|b> and apply `circuit` (h's gate list if None, else a qsim_fuse of
+    h.as_circuit()) with the operations before the inversion on half the state (the ancilla is
+    |0> until then).  Enqueued on `stream`."""
+    _check_state(state, h.info()["n"])
+    _check(library().hhl_run(ctypes.c_void_p(state.data_ptr()), _dtype_of(state), h.ptr,
+                             circuit.ptr if circuit is not None else None, _stream_ptr(stream)))
     return state
 
 

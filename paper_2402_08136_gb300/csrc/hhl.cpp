@@ -425,6 +425,17 @@ int hhl_prepare_state(void *state, int dtype, const hhl_circuit *h, void *stream
     });
 }
 
+int hhl_run(void *state, int dtype, const hhl_circuit *h, const qsim_circuit *c, void *stream) {
+    return guarded([&] {
+        QSIM_REQUIRE(state != nullptr && h != nullptr, "NULL argument");
+        QSIM_REQUIRE(dtype == QSIM_C64 || dtype == QSIM_C128, "dtype must be QSIM_C64 or QSIM_C128");
+        const qsim_circuit *g = c ? c : &h->circ;
+        QSIM_REQUIRE(g->n == h->n, "circuit and HHL problem disagree on the qubit count");
+        launch_prepare_state(state, h->n, dtype, h->b_pad.data(), h->nb, stream, true);
+        apply_ops(state, h->n, dtype, const_cast<qsim_circuit *>(g), stream, true);
+    });
+}
+
 int hhl_readout(const void *state, int dtype, const hhl_circuit *h, void *stream, double *x_out,
                 double *x_state_out, hhl_readout_stats *stats) {
     return guarded([&] {

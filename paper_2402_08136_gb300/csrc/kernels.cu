@@ -413,6 +413,7 @@ struct UcryArgs {
     int nc;
     int contiguous;  // controls are qubits c0 .. c0+nc-1 in order
     int c0;
+    int src_zero;    // the target-1 half is known to be zero: written, not read
     int ctrl[32];
 };
 
@@ -435,7 +436,7 @@ __global__ void ucry_kernel(const UcryArgs a) {
             for (int j = 0; j < a.nc; j++) v |= ((i0 >> a.ctrl[j]) & 1ull) << j;
         }
         const V t = cs[v];
-        const V x0 = psi[i0], x1 = psi[i0 | tb];
+        const V x0 = psi[i0], x1 = a.src_zero ? V{0, 0} : psi[i0 | tb];
         V y0, y1;
         y0.x = t.x * x0.x - t.y * x1.x;
         y0.y = t.x * x0.y - t.y * x1.y;
@@ -487,6 +488,7 @@ struct InvertArgs {
     double Cs;
     int target, nc;
     int twos;         // clock register read as two's complement (indefinite A)
+    int src_zero;     // the target-1 half is known to be zero: written, not read
     int nseg;
     int seg_src[kMaxSeg], seg_w[kMaxSeg], seg_dst[kMaxSeg];
 };
@@ -513,7 +515,7 @@ __global__ void hhl_invert_kernel(const InvertArgs a) {
             const R as = s < 0 ? -s : s;
             c = sqrt(((R)1 - as) * ((R)1 + as));
         }
-        const V x0 = psi[i0], x1 = psi[i0 | tb];
+        const V x0 = psi[i0], x1 = a.src_zero ? V{0, 0} : psi[i0 | tb];
         V y0, y1;
         y0.x = c * x0.x - s * x1.x;
         y0.y = c * x0.y - s * x1.y;
@@ -828,10 +830,12 @@ void run_swap(void *state, int n, int dtype, const Op &op, cudaStream_t st) {
     check_launch("swap_kernel");
 }
 
-void run_ucry(void *state, int n, int dtype, const Op &op, const void *csdev, cudaStream_t st) {
+void run_ucry(void *state, int n, int dtype, const Op &op, const void *csdev, cudaStream_t st,
+              bool src_zero = false) {
     UcryArgs a;
     std::memset(&a, 0, sizeof(a));
     a.psi = state;
+    a.src_zero = src_zero ? 1 : 0;
     a.cs = csdev;
     a.count = 1ll << (n - 1);
     a.target = op.targets[0];
@@ -878,10 +882,11 @@ void run_qpe_phase(void *state, int n, int dtype, const Op &op, const void *lo, 
     check_launch("qpe_phase_kernel");
 }
 
-void run_hhl_invert(void *state, int n, int dtype, const Op &op, cudaStream_t st) {
+void run_hhl_invert(void *state, int n, int dtype, const Op &op, cudaStream_t st, bool src_zero = false) {
     InvertArgs a;
     std::memset(&a, 0, sizeof(a));
     a.psi = state;
+    a.src_zero = src_zero ? 1 : 0;
     a.count = 1ll << (n - 1);
     a.Cs = op.tq;
     a.target = op.targets[0];
@@ -1008,30 +1013,66 @@ static bool fuse_diag_enabled() {
 
 static bool is_pass(const Op &op) { return op.kind == OP_DFT || op.kind == OP_WALSH; }
 
-void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream) {
+static bool touches(const Op &op, int q) {
+    for (int t : op.targets)
+        if (t == q) return true;
+    for (int t : op.controls)
+        if (t == q) return true;
+    return false;
+}
+
+void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, bool top_zero) {
     ensure_device_blob(c, dtype);
     const int slot = dtype == QSIM_C128 ? 1 : 0;
     const unsigned char *base = static_cast<const unsigned char *>(c->blob[slot].ptr);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const std::vector<Op> &ops = c->ops;
     const bool fuse = fuse_diag_enabled();
+    // Top qubit known |0> (HHL ancilla): until the first op acting on it, every op leaves the
+    // upper half of the state zero and runs on the lower half as an (n-1)-qubit state; that op,
+    // if it is the inversion rotation on the top qubit, writes the upper half without reading
+    // it, otherwise the upper half is zeroed first (or at the end if no op acts on it).
+    size_t first_top = ops.size();
+    if (top_zero)
+        for (size_t i = 0; i < ops.size(); i++)
+            if (touches(ops[i], n - 1)) {
+                first_top = i;
+                break;
+            }
+    const size_t half_bytes = (size_t)2 * real_size(dtype) << (n - 1);
+    auto zero_upper = [&] {
+        CUDA_OK(cudaMemsetAsync(static_cast<unsigned char *>(state) + half_bytes, 0, half_bytes, st));
+    };
+    auto width = [&](size_t i) { return top_zero && i < first_top ? n - 1 : n; };
     for (size_t i = 0; i < ops.size(); i++) {
         const Op &op = ops[i];
         const void *dptr = base + op.dev_off[slot];
-        if (fuse && is_pass(op) && i + 1 < ops.size() && ops[i + 1].kind == OP_QPE_PHASE) {
+        if (top_zero && i == first_top) {
+            if ((op.kind == OP_HHL_INVERT || op.kind == OP_UCRY) && op.targets[0] == n - 1) {
+                if (op.kind == OP_HHL_INVERT) run_hhl_invert(state, n, dtype, op, st, true);
+                else run_ucry(state, n, dtype, op, dptr, st, true);
+                continue;
+            }
+            zero_upper();
+        }
+        const int w = width(i);
+        // a fused pair stays on one side of the first top-qubit op
+        const bool pair_ok = i + 1 < ops.size() && width(i + 1) == w && !(top_zero && i + 1 == first_top);
+        if (fuse && is_pass(op) && pair_ok && ops[i + 1].kind == OP_QPE_PHASE) {
             // outputs of this pass, unless this pass has a twiddle and the next one has none
             const bool next_better = !op.controls.empty() && i + 2 < ops.size() && is_pass(ops[i + 2]) &&
-                                     ops[i + 2].controls.empty();
+                                     ops[i + 2].controls.empty() && width(i + 2) == w &&
+                                     !(top_zero && i + 2 == first_top);
             if (!next_better) {
                 const Op &q = ops[i + 1];
-                run_dft(state, n, dtype, op, dptr, st, &q, base + q.dev_off[slot], base + q.dev_off_tc, 2);
+                run_dft(state, w, dtype, op, dptr, st, &q, base + q.dev_off[slot], base + q.dev_off_tc, 2);
                 i++;
                 continue;
             }
         }
-        if (fuse && op.kind == OP_QPE_PHASE && i + 1 < ops.size() && is_pass(ops[i + 1])) {
+        if (fuse && op.kind == OP_QPE_PHASE && pair_ok && is_pass(ops[i + 1])) {
             const Op &p = ops[i + 1];
-            run_dft(state, n, dtype, p, base + p.dev_off[slot], st, &op, dptr, base + op.dev_off_tc, 1);
+            run_dft(state, w, dtype, p, base + p.dev_off[slot], st, &op, dptr, base + op.dev_off_tc, 1);
             i++;
             continue;
         }
@@ -1039,24 +1080,25 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream) {
             case OP_DENSE:
                 if (dtype == QSIM_C64 && op.has_tc && tc_enabled() &&
                     (op.targets.size() == 7
-                         ? launch_dense_tc_real7(state, n, op.targets, op.controls, base + op.dev_off_tc, num_sms(), st)
-                         : launch_dense_tc(state, n, op.targets, op.controls, base + op.dev_off_tc, num_sms(), st)))
+                         ? launch_dense_tc_real7(state, w, op.targets, op.controls, base + op.dev_off_tc, num_sms(), st)
+                         : launch_dense_tc(state, w, op.targets, op.controls, base + op.dev_off_tc, num_sms(), st)))
                     break;
-                run_dense(state, n, dtype, op, dptr, st);
+                run_dense(state, w, dtype, op, dptr, st);
                 break;
-            case OP_PHASE: run_phase(state, n, dtype, op, st); break;
-            case OP_DIAG: run_diag(state, n, dtype, op, dptr, st); break;
-            case OP_SWAP: run_swap(state, n, dtype, op, st); break;
-            case OP_UCRY: run_ucry(state, n, dtype, op, dptr, st); break;
-            case OP_QPE_PHASE: run_qpe_phase(state, n, dtype, op, dptr, base + op.dev_off_tc, st); break;
-            case OP_HHL_INVERT: run_hhl_invert(state, n, dtype, op, st); break;
+            case OP_PHASE: run_phase(state, w, dtype, op, st); break;
+            case OP_DIAG: run_diag(state, w, dtype, op, dptr, st); break;
+            case OP_SWAP: run_swap(state, w, dtype, op, st); break;
+            case OP_UCRY: run_ucry(state, w, dtype, op, dptr, st); break;
+            case OP_QPE_PHASE: run_qpe_phase(state, w, dtype, op, dptr, base + op.dev_off_tc, st); break;
+            case OP_HHL_INVERT: run_hhl_invert(state, w, dtype, op, st); break;
             case OP_DFT:
-            case OP_WALSH: run_dft(state, n, dtype, op, dptr, st); break;
+            case OP_WALSH: run_dft(state, w, dtype, op, dptr, st); break;
         }
     }
+    if (top_zero && first_top == ops.size()) zero_upper();
 }
 
-void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb, void *stream) {
+void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb, void *stream, bool lower_half) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     PrepArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -1069,7 +1111,9 @@ void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb
         a.b[2 * i + 1] = b_pad[i].imag();
     }
     const size_t vbytes = 2 * real_size(dtype);
-    CUDA_OK(cudaMemsetAsync(state, 0, (size_t)a.N * vbytes, st));
+    // lower_half: only amplitudes with the top qubit 0 are written (the caller treats the upper
+    // half as known zero)
+    CUDA_OK(cudaMemsetAsync(state, 0, (size_t)(lower_half ? a.N / 2 : a.N) * vbytes, st));
     if (dtype == QSIM_C128) prep_kernel<double><<<1, kMaxParamB, 0, st>>>(a);
     else prep_kernel<float><<<1, kMaxParamB, 0, st>>>(a);
     check_launch("prep_kernel");

@@ -315,8 +315,9 @@ void launch_large(qsim_pool *p, Slot &s, PoolReq *r) {
     cudaError_t e = cudaMemcpyAsync(addr(p, mb), blob.data(), blob.size(), cudaMemcpyHostToDevice, s.st);
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("matrix upload: ") + cudaGetErrorString(e));
     attach_external_blob(r->fused, dtype, addr(p, mb), blob.size());
-    launch_prepare_state(r->state, r->n, dtype, r->h->b_pad.data(), r->h->nb, s.st);
-    apply_ops(r->state, r->n, dtype, r->fused, s.st);
+    // the ancilla (top qubit) is |0> until the inversion: the ops before it run on half the state
+    launch_prepare_state(r->state, r->n, dtype, r->h->b_pad.data(), r->h->nb, s.st, true);
+    apply_ops(r->state, r->n, dtype, r->fused, s.st, true);
     readout_launch_async(r->state, dtype, r->n, r->h->nb, s.st, static_cast<double *>(addr(p, sb)), s.pinned,
                          s.pinned + 4);
     e = cudaEventRecord(s.ev, s.st);

@@ -1,0 +1,134 @@
+"""hhl_run (state preparation plus the circuit, every operation before the first one on the
+ancilla run on the lower half of the state, which is exactly zero above) against
+hhl_prepare_state + qsim_apply of the same circuit and against the FP64 oracle.  The state is
+filled with NaN first: an amplitude that hhl_run reads before writing would poison the
+result."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import core as ocore
+from oracle import hhl as ohhl
+
+DTYPES = [torch.complex128, torch.complex64]
+TOL = {torch.complex128: 1e-12, torch.complex64: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def qs():
+    from paper_2402_08136_gb300 import build
+    build.build()
+    import paper_2402_08136_gb300 as q
+    return q
+
+
+def nan_state(n, dtype):
+    return torch.full((1 << n,), complex(float("nan"), float("nan")), dtype=dtype, device="cuda")
+
+
+def both_ways(qs, h, circ, dtype):
+    n = h.info()["n"]
+    a = nan_state(n, dtype)
+    qs.hhl_run(a, h, circ)
+    b = torch.empty(1 << n, dtype=dtype, device="cuda")
+    qs.hhl_prepare_state(b, h)
+    qs.qsim_apply(b, circ if circ is not None else h.as_circuit(), n_qubits=n)
+    torch.cuda.synchronize()
+    a_np = a.cpu().numpy().astype(np.complex128)
+    b_np = b.cpu().numpy().astype(np.complex128)
+    assert np.all(np.isfinite(a_np)), "hhl_run left or read unwritten amplitudes"
+    return a, a_np, b_np
+
+
+FORMS = [("gates", 0), ("gates", 4), ("structured", 3), ("structured_fft", 4), ("structured_fft", 0)]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("form,max_k", FORMS)
+@pytest.mark.parametrize("problem", ["hhl7", "contingency"])
+def test_hhl_run_matches_two_step_path_and_oracle(qs, cuda_device, dtype, form, max_k, problem):
+    if problem == "hhl7":
+        p = synth.hhl7_problem()
+        A, b, m, t, C = p["A"], p["b"], p["m"], p["t"], p["C"]
+    else:
+        A, b = synth.contingency_system(np.random.default_rng(5), 9)
+        m, t, C = 7, 0.0, 0.0
+    h = qs.hhl_build(A, b, m, t, C, structured=form != "gates", fft_qft=form == "structured_fft")
+    circ = qs.qsim_fuse(h.as_circuit(), max_k) if max_k else None
+    st, a_np, b_np = both_ways(qs, h, circ, dtype)
+    # same operations on the same values: equal up to rounding of the reordered launches
+    assert np.max(np.abs(a_np - b_np)) <= TOL[dtype] / 10
+    ref = ohhl.solve(A, b, m, t, C)
+    tol = max(TOL[dtype], 2.0 ** m * 2 * math.pi * 8 * np.finfo(float).eps) if dtype == torch.complex128 \
+        else TOL[dtype]
+    assert np.max(np.abs(a_np - ref["psi"])) <= tol
+    r = qs.hhl_readout(st, h)
+    assert abs(r["p_success"] - ref["P"]) <= 10 * tol
+    assert abs(r["norm2"] - 1.0) <= (1e-12 if dtype == torch.complex128 else 1e-5)
+
+
+def reference_state(p):
+    """|0>|0>|b> from the oracle (complex128)."""
+    return ohhl.initial_state(ohhl.build(p["A"], p["b"], p["m"], p["t"], p["C"]))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_hhl_run_first_top_operation_not_an_inversion(qs, cuda_device, dtype):
+    """A dense gate reaches the ancilla first: the upper half is zeroed before it."""
+    p = synth.hhl7_problem()
+    h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"])
+    n = h.info()["n"]
+    rng = np.random.default_rng(3)
+    gates = [([1, 2], synth.haar_unitary(rng, 4)), ([n - 1, 0], synth.haar_unitary(rng, 4)),
+             ([3, 4, 5], synth.haar_unitary(rng, 8)), ([n - 1], synth.haar_unitary(rng, 2))]
+    c = qs.Circuit(n)
+    for t, U in gates:
+        c.add_gate(t, U)
+    _, a_np, b_np = both_ways(qs, h, c, dtype)
+    ref = reference_state(p)
+    for t, U in gates:
+        ocore.apply_gate(ref, t, U)
+    assert np.max(np.abs(a_np - b_np)) <= TOL[dtype] / 10
+    assert np.max(np.abs(a_np - ref)) <= TOL[dtype]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_hhl_run_rotation_on_the_ancilla_first(qs, cuda_device, dtype):
+    """A uniformly controlled RY on the ancilla is the first operation on it: it writes the upper
+    half without reading it."""
+    p = synth.hhl7_problem()
+    h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"])
+    n = h.info()["n"]
+    rng = np.random.default_rng(4)
+    U = synth.haar_unitary(rng, 8)
+    reg = [2, 3, 4]
+    th = rng.uniform(-3, 3, size=8)
+    U2 = synth.haar_unitary(rng, 4)
+    c = qs.Circuit(n).add_gate([0, 1, 5], U).add_ucry(n - 1, reg, th).add_gate([n - 1, 2], U2)
+    _, a_np, b_np = both_ways(qs, h, c, dtype)
+    assert np.max(np.abs(a_np - b_np)) <= TOL[dtype] / 10
+    ref = reference_state(p)
+    ocore.apply_gate(ref, [0, 1, 5], U)
+    ocore.apply_ucry(ref, n - 1, reg, th)
+    ocore.apply_gate(ref, [n - 1, 2], U2)
+    assert np.max(np.abs(a_np - ref)) <= 10 * TOL[dtype]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_hhl_run_circuit_that_never_touches_the_ancilla(qs, cuda_device, dtype):
+    """No operation on the ancilla: the upper half is zeroed at the end."""
+    p = synth.hhl7_problem()
+    h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"])
+    n = h.info()["n"]
+    rng = np.random.default_rng(6)
+    c = qs.Circuit(n).add_gate([0, 4], synth.haar_unitary(rng, 4)).add_gate([5], synth.haar_unitary(rng, 2))
+    _, a_np, b_np = both_ways(qs, h, c, dtype)
+    assert np.max(np.abs(a_np - b_np)) <= TOL[dtype] / 10
+    assert np.all(a_np[1 << (n - 1):] == 0)
