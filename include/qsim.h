@@ -248,14 +248,17 @@ int hhl_prepare_state(void *state, int dtype, const hhl_circuit *h, void *stream
 
 /* The device part of one HHL solve, enqueued on `stream`: prepare |0>_anc |0>_clock |b> in
  * `state` and apply circuit `c` (h's gate list, or a qsim_fuse of hhl_as_circuit(h); NULL
- * means h's own list).  The ancilla is the top qubit and stays |0> until the first operation
- * acting on it (the eigenvalue-inversion rotation of Fig. 5, Sec. III-A step 2), so every
- * operation before that one runs on the lower half of the state only (the upper half is
- * exactly zero: half the HBM traffic), the preparation zeroes only the lower half, and the
- * inversion writes the upper
- * half without reading it (any other first operation on the ancilla, or none at all, zeroes
- * the upper half first).  The final state equals hhl_prepare_state followed by qsim_apply of
- * the same circuit, up to rounding.  Errors: EINVAL, ENOMEM, ECUDA. */
+ * means h's own list), skipping work on amplitudes that are provably zero.  After the
+ * preparation only the 2^nb data amplitudes are populated, and the executor tracks a live width
+ * w (every amplitude from index 2^w on is zero and unwritten): an operation on qubits below w
+ * runs on the first 2^w amplitudes; a Walsh-Hadamard or Fourier pass on the field right above w
+ * (the clock's Hadamard layer of Fig. 5 on |0>) only broadcasts column 0 of the transform (a
+ * write-only pass) and widens w; diagonal operations leave the zeros alone; the eigenvalue-
+ * inversion rotation of Fig. 5 (Sec. III-A step 2) on the top qubit, the ancilla, writes the
+ * upper half without reading it, so everything before it runs on at most half the state; any
+ * other operation first zero-fills up to its top qubit.  The final state equals
+ * hhl_prepare_state followed by qsim_apply of the same circuit, up to rounding.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
 int hhl_run(void *state, int dtype, const hhl_circuit *h, const qsim_circuit *c, void *stream);
 
 typedef struct {

@@ -135,9 +135,9 @@ Op classify_dense(const std::vector<int> &targets, const std::vector<int> &contr
                   const std::vector<cd> &U);
 void circuit_info(const qsim_circuit *c, qsim_circuit_info *out);
 // kernels.cu
-// top_zero: the caller guarantees that the top qubit is |0> in the input and that only the
-// lower half of the state has been written (see hhl_run).
-void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, bool top_zero = false);
+// live < n: the caller guarantees that the input is zero at every index >= 2^live and that only
+// the first 2^live amplitudes have been written (see hhl_run); the result is the full state.
+void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int live = -1);
 void ensure_device_blob(qsim_circuit *c, int dtype);
 std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype);   // sets op offsets
 void attach_external_blob(qsim_circuit *c, int dtype, void *dev, size_t bytes);
@@ -146,10 +146,10 @@ void attach_external_blob(qsim_circuit *c, int dtype, void *dev, size_t bytes);
 size_t readout_scratch_doubles(int n);
 void readout_launch_async(const void *state, int dtype, int n, int nb, cudaStream_t st, double *scratch,
                           double *pinned_sums, void *pinned_slice);
-// lower_half: zero and write only the amplitudes with the top qubit 0 (apply_ops with
-// top_zero = true then treats the upper half as zero)
+// live in [nb, n): zero and write only the first 2^live amplitudes (apply_ops with the same
+// live width treats the rest as zero)
 void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb, void *stream,
-                          bool lower_half = false);
+                          int live = -1);
 void readout_device(const void *state, int dtype, int n, int nb, int m, void *stream,
                     double sums[3], cd *slice);
 // dense_tc.cu

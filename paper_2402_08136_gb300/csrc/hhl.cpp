@@ -87,13 +87,17 @@ std::vector<std::pair<int, int>> clock_fields(int m) {
     return f;
 }
 
-// H on every clock qubit: m Hadamard gates, or one Walsh-Hadamard pass per field.
-void append_hadamards(qsim_circuit &c, const std::vector<int> &q, bool passes) {
+// H on every clock qubit: m Hadamard gates, or one Walsh-Hadamard pass per field (the passes
+// commute; low_first emits the lowest field first, so that on the clock register's |0> each pass
+// fills the qubits right above those already filled).
+void append_hadamards(qsim_circuit &c, const std::vector<int> &q, bool passes, bool low_first = false) {
     if (!passes) {
         for (int x : q) add_u(c, {x}, {}, hadamard());
         return;
     }
-    for (const auto &f : clock_fields((int)q.size())) {
+    std::vector<std::pair<int, int>> fields = clock_fields((int)q.size());
+    if (low_first) std::reverse(fields.begin(), fields.end());
+    for (const auto &f : fields) {
         Gate g;
         g.kind = GATE_WALSH;
         g.targets.assign(q.begin() + f.first, q.begin() + f.second);
@@ -194,7 +198,7 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
     // structured with passes: V^H comes first (it acts on the data register only and commutes
     // with the clock's Hadamard layer), so the phase operator directly follows the layer's last
     // pass and the executor can apply it inside that pass
-    if (!(structured && passes)) append_hadamards(c, clock, passes);
+    if (!(structured && passes)) append_hadamards(c, clock, passes, true);
     size_t phase_idx = 0;
     if (structured) {
         // prod_j C_j-U^(2^j) = (I (x) V) diag_c(exp(i lam t c)) (I (x) V^H); the V that would
@@ -203,7 +207,7 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
         for (int r = 0; r < D; r++)
             for (int s2 = 0; s2 < D; s2++) VH[(size_t)r * D + s2] = std::conj(V[(size_t)s2 * D + r]);
         add_u(c, data, {}, std::move(VH));
-        if (passes) append_hadamards(c, clock, true);
+        if (passes) append_hadamards(c, clock, true, true);
         Gate g;
         g.kind = GATE_QPE_PHASE;
         g.targets = data;
@@ -431,8 +435,9 @@ int hhl_run(void *state, int dtype, const hhl_circuit *h, const qsim_circuit *c,
         QSIM_REQUIRE(dtype == QSIM_C64 || dtype == QSIM_C128, "dtype must be QSIM_C64 or QSIM_C128");
         const qsim_circuit *g = c ? c : &h->circ;
         QSIM_REQUIRE(g->n == h->n, "circuit and HHL problem disagree on the qubit count");
-        launch_prepare_state(state, h->n, dtype, h->b_pad.data(), h->nb, stream, true);
-        apply_ops(state, h->n, dtype, const_cast<qsim_circuit *>(g), stream, true);
+        // only the data register is populated: every amplitude from 2^nb on is zero
+        launch_prepare_state(state, h->n, dtype, h->b_pad.data(), h->nb, stream, h->nb);
+        apply_ops(state, h->n, dtype, const_cast<qsim_circuit *>(g), stream, h->nb);
     });
 }
 

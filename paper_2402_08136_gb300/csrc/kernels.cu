@@ -474,6 +474,46 @@ __global__ void qpe_phase_kernel(const QpeArgs a) {
     }
 }
 
+// A Fourier or Walsh-Hadamard pass (no twiddle after the transform) on the field w .. w+K-1 of
+// a state that is zero at every index >= 2^w: only field value 0 is populated, and column 0 of
+// the transform is 2^(-K/2) for every output digit, so out[y 2^w + l] = 2^(-K/2) in[l] (times a
+// fused structured phase, on the input or the output index).  col0 = 0 writes the outputs
+// y >= 1 from the untouched column y = 0; col0 = 1 then rescales that column in place.
+struct ExpandArgs {
+    void *psi;
+    const void *qlo, *qhi;  // structured phase tables (qmode 1: input index l, 2: output index)
+    long long lowN;         // 2^w
+    long long count;        // outputs this launch writes
+    double scale;
+    int w, col0, qmode, qnb, qm, qh;
+};
+
+template <typename R>
+__global__ void expand_kernel(const ExpandArgs a) {
+    using V = typename C2<R>::T;
+    V *psi = reinterpret_cast<V *>(a.psi);
+    const V *lo = reinterpret_cast<const V *>(a.qlo);
+    const V *hi = reinterpret_cast<const V *>(a.qhi);
+    const unsigned long long dmask = (1ull << a.qnb) - 1ull, cmask = (1ull << a.qm) - 1ull;
+    const unsigned long long hmask = (1ull << a.qh) - 1ull;
+    auto phase = [&](unsigned long long i) -> V {
+        const unsigned long long d = i & dmask, c = (i >> a.qnb) & cmask;
+        return cmul(lo[((c & hmask) << a.qnb) + d], hi[((c >> a.qh) << a.qnb) + d]);
+    };
+    const R sc = (R)a.scale;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.count;
+         g += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long l = (unsigned long long)g & (unsigned long long)(a.lowN - 1);
+        const unsigned long long idx = a.col0 ? l : (unsigned long long)g + (unsigned long long)a.lowN;
+        V z = psi[l];
+        if (a.qmode == 1) z = cmul(z, phase(l));
+        z.x *= sc;
+        z.y *= sc;
+        if (a.qmode == 2) z = cmul(z, phase(idx));
+        psi[idx] = z;
+    }
+}
+
 // HHL eigenvalue inversion: for the pair of amplitudes that differ in the ancilla,
 // r = clamp(Cs / k, -1, 1) with k the clock value (two's complement for an indefinite A; r = 0
 // for k = 0), and
@@ -882,6 +922,35 @@ void run_qpe_phase(void *state, int n, int dtype, const Op &op, const void *lo, 
     check_launch("qpe_phase_kernel");
 }
 
+// The pass `op` on the field w .. w+K-1 of a state that is zero from index 2^w on (see
+// expand_kernel); qop: structured phase fused on the inputs (qmode 1) or outputs (qmode 2).
+void run_expand(void *state, int w, int dtype, const Op &op, const Op *qop, const void *qlo, const void *qhi,
+                int qmode, cudaStream_t st) {
+    const int K = (int)op.targets.size();
+    ExpandArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = state;
+    a.lowN = 1ll << w;
+    a.w = w;
+    a.scale = std::ldexp(1.0, -K / 2) * ((K & 1) ? std::sqrt(0.5) : 1.0);
+    if (qop && qmode) {
+        a.qlo = qlo;
+        a.qhi = qhi;
+        a.qmode = qmode;
+        a.qnb = (int)qop->targets.size();
+        a.qm = (int)qop->controls.size();
+        a.qh = (a.qm + 1) / 2;  // the split qpe_phase_tables uses
+    }
+    for (int pass = 0; pass < 2; pass++) {  // outputs y >= 1 first, then column 0 in place
+        a.col0 = pass;
+        a.count = pass ? a.lowN : (a.lowN << K) - a.lowN;
+        const int grid = grid_for(a.count, 256);
+        if (dtype == QSIM_C128) expand_kernel<double><<<grid, 256, 0, st>>>(a);
+        else expand_kernel<float><<<grid, 256, 0, st>>>(a);
+        check_launch("expand_kernel");
+    }
+}
+
 void run_hhl_invert(void *state, int n, int dtype, const Op &op, cudaStream_t st, bool src_zero = false) {
     InvertArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -1013,69 +1082,92 @@ static bool fuse_diag_enabled() {
 
 static bool is_pass(const Op &op) { return op.kind == OP_DFT || op.kind == OP_WALSH; }
 
-static bool touches(const Op &op, int q) {
-    for (int t : op.targets)
-        if (t == q) return true;
-    for (int t : op.controls)
-        if (t == q) return true;
-    return false;
+static int top_qubit(const Op &op) {
+    int q = -1;
+    for (int t : op.targets) q = std::max(q, t);
+    for (int t : op.controls) q = std::max(q, t);
+    return q;
 }
 
-void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, bool top_zero) {
+void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int live) {
     ensure_device_blob(c, dtype);
     const int slot = dtype == QSIM_C128 ? 1 : 0;
     const unsigned char *base = static_cast<const unsigned char *>(c->blob[slot].ptr);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const std::vector<Op> &ops = c->ops;
     const bool fuse = fuse_diag_enabled();
-    // Top qubit known |0> (HHL ancilla): until the first op acting on it, every op leaves the
-    // upper half of the state zero and runs on the lower half as an (n-1)-qubit state; that op,
-    // if it is the inversion rotation on the top qubit, writes the upper half without reading
-    // it, otherwise the upper half is zeroed first (or at the end if no op acts on it).
-    size_t first_top = ops.size();
-    if (top_zero)
-        for (size_t i = 0; i < ops.size(); i++)
-            if (touches(ops[i], n - 1)) {
-                first_top = i;
-                break;
-            }
-    const size_t half_bytes = (size_t)2 * real_size(dtype) << (n - 1);
-    auto zero_upper = [&] {
-        CUDA_OK(cudaMemsetAsync(static_cast<unsigned char *>(state) + half_bytes, 0, half_bytes, st));
+    // Live width w: every amplitude at an index >= 2^w is zero and has not been written (HHL: after
+    // the preparation only the data register is populated).  An op on qubits below w runs as a
+    // w-qubit state; a twiddle-free pass on the field right above w broadcasts column 0 (write
+    // only) and widens w; diagonal ops leave zeros zero; the inversion rotation on the top qubit
+    // writes the upper half without reading it; any other op first zero-fills up to its top qubit.
+    int w = (live >= 0 && live < n) ? live : n;
+    const size_t vb = 2 * real_size(dtype);
+    auto materialize = [&](int to) {
+        if (to <= w) return;
+        unsigned char *p = static_cast<unsigned char *>(state);
+        CUDA_OK(cudaMemsetAsync(p + (vb << w), 0, (vb << to) - (vb << w), st));
+        w = to;
     };
-    auto width = [&](size_t i) { return top_zero && i < first_top ? n - 1 : n; };
+    auto expandable = [&](const Op &p) {
+        if (!is_pass(p) || w >= n) return false;
+        for (size_t j = 0; j < p.targets.size(); j++)
+            if (p.targets[j] != w + (int)j) return false;
+        for (int q : p.controls)
+            if (q >= w) return false;
+        return p.kind == OP_WALSH || p.controls.empty() || p.pre;  // no twiddle on the outputs
+    };
     for (size_t i = 0; i < ops.size(); i++) {
         const Op &op = ops[i];
         const void *dptr = base + op.dev_off[slot];
-        if (top_zero && i == first_top) {
-            if ((op.kind == OP_HHL_INVERT || op.kind == OP_UCRY) && op.targets[0] == n - 1) {
-                if (op.kind == OP_HHL_INVERT) run_hhl_invert(state, n, dtype, op, st, true);
-                else run_ucry(state, n, dtype, op, dptr, st, true);
-                continue;
+        if (fuse && i + 1 < ops.size()) {
+            // a structured phase next to a pass runs inside it: on the pass's outputs, unless this
+            // pass has a twiddle and the pass after the phase has none (then on that one's inputs)
+            size_t pi = ops.size(), qi = ops.size();
+            int qmode = 0;
+            if (is_pass(op) && ops[i + 1].kind == OP_QPE_PHASE) {
+                const bool next_better = !op.controls.empty() && i + 2 < ops.size() && is_pass(ops[i + 2]) &&
+                                         ops[i + 2].controls.empty();
+                if (!next_better) pi = i, qi = i + 1, qmode = 2;
+            } else if (op.kind == OP_QPE_PHASE && is_pass(ops[i + 1])) {
+                pi = i + 1, qi = i, qmode = 1;
             }
-            zero_upper();
-        }
-        const int w = width(i);
-        // a fused pair stays on one side of the first top-qubit op
-        const bool pair_ok = i + 1 < ops.size() && width(i + 1) == w && !(top_zero && i + 1 == first_top);
-        if (fuse && is_pass(op) && pair_ok && ops[i + 1].kind == OP_QPE_PHASE) {
-            // outputs of this pass, unless this pass has a twiddle and the next one has none
-            const bool next_better = !op.controls.empty() && i + 2 < ops.size() && is_pass(ops[i + 2]) &&
-                                     ops[i + 2].controls.empty() && width(i + 2) == w &&
-                                     !(top_zero && i + 2 == first_top);
-            if (!next_better) {
-                const Op &q = ops[i + 1];
-                run_dft(state, w, dtype, op, dptr, st, &q, base + q.dev_off[slot], base + q.dev_off_tc, 2);
+            if (qmode) {
+                const Op &p = ops[pi], &q = ops[qi];
+                const void *qlo = base + q.dev_off[slot], *qhi = base + q.dev_off_tc;
+                if (expandable(p)) {
+                    run_expand(state, w, dtype, p, &q, qlo, qhi, qmode, st);
+                    w += (int)p.targets.size();
+                } else {
+                    materialize(top_qubit(p) + 1);  // the phase is diagonal: zeros stay zero
+                    run_dft(state, w, dtype, p, base + p.dev_off[slot], st, &q, qlo, qhi, qmode);
+                }
                 i++;
                 continue;
             }
         }
-        if (fuse && op.kind == OP_QPE_PHASE && pair_ok && is_pass(ops[i + 1])) {
-            const Op &p = ops[i + 1];
-            run_dft(state, w, dtype, p, base + p.dev_off[slot], st, &op, dptr, base + op.dev_off_tc, 1);
-            i++;
+        if (expandable(op)) {
+            run_expand(state, w, dtype, op, nullptr, nullptr, nullptr, 0, st);
+            w += (int)op.targets.size();
             continue;
         }
+        if (op.kind == OP_QPE_PHASE) {  // diagonal: only the live part needs it
+            run_qpe_phase(state, w, dtype, op, dptr, base + op.dev_off_tc, st);
+            continue;
+        }
+        if (op.kind == OP_PHASE && top_qubit(op) >= w) continue;  // needs a 1 where all are 0
+        if ((op.kind == OP_HHL_INVERT || op.kind == OP_UCRY) && w < n && op.targets[0] == n - 1) {
+            bool low = true;
+            for (int q : op.controls) low = low && q < n - 1;
+            if (low) {
+                materialize(n - 1);
+                if (op.kind == OP_HHL_INVERT) run_hhl_invert(state, n, dtype, op, st, true);
+                else run_ucry(state, n, dtype, op, dptr, st, true);
+                w = n;
+                continue;
+            }
+        }
+        materialize(top_qubit(op) + 1);
         switch (op.kind) {
             case OP_DENSE:
                 if (dtype == QSIM_C64 && op.has_tc && tc_enabled() &&
@@ -1089,16 +1181,16 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, boo
             case OP_DIAG: run_diag(state, w, dtype, op, dptr, st); break;
             case OP_SWAP: run_swap(state, w, dtype, op, st); break;
             case OP_UCRY: run_ucry(state, w, dtype, op, dptr, st); break;
-            case OP_QPE_PHASE: run_qpe_phase(state, w, dtype, op, dptr, base + op.dev_off_tc, st); break;
+            case OP_QPE_PHASE: break;  // handled above
             case OP_HHL_INVERT: run_hhl_invert(state, w, dtype, op, st); break;
             case OP_DFT:
             case OP_WALSH: run_dft(state, w, dtype, op, dptr, st); break;
         }
     }
-    if (top_zero && first_top == ops.size()) zero_upper();
+    materialize(n);
 }
 
-void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb, void *stream, bool lower_half) {
+void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb, void *stream, int live) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     PrepArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -1111,9 +1203,10 @@ void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb
         a.b[2 * i + 1] = b_pad[i].imag();
     }
     const size_t vbytes = 2 * real_size(dtype);
-    // lower_half: only amplitudes with the top qubit 0 are written (the caller treats the upper
-    // half as known zero)
-    CUDA_OK(cudaMemsetAsync(state, 0, (size_t)(lower_half ? a.N / 2 : a.N) * vbytes, st));
+    // live < n: only the first 2^live amplitudes are written (the caller treats the rest as
+    // known zero)
+    const long long written = (live >= nb && live < n) ? (1ll << live) : a.N;
+    CUDA_OK(cudaMemsetAsync(state, 0, (size_t)written * vbytes, st));
     if (dtype == QSIM_C128) prep_kernel<double><<<1, kMaxParamB, 0, st>>>(a);
     else prep_kernel<float><<<1, kMaxParamB, 0, st>>>(a);
     check_launch("prep_kernel");

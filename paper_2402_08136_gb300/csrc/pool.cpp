@@ -315,9 +315,10 @@ void launch_large(qsim_pool *p, Slot &s, PoolReq *r) {
     cudaError_t e = cudaMemcpyAsync(addr(p, mb), blob.data(), blob.size(), cudaMemcpyHostToDevice, s.st);
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("matrix upload: ") + cudaGetErrorString(e));
     attach_external_blob(r->fused, dtype, addr(p, mb), blob.size());
-    // the ancilla (top qubit) is |0> until the inversion: the ops before it run on half the state
-    launch_prepare_state(r->state, r->n, dtype, r->h->b_pad.data(), r->h->nb, s.st, true);
-    apply_ops(r->state, r->n, dtype, r->fused, s.st, true);
+    // only the data register is populated after the preparation (clock and ancilla |0>): the
+    // executor widens the live part as the circuit fills it (as hhl_run does)
+    launch_prepare_state(r->state, r->n, dtype, r->h->b_pad.data(), r->h->nb, s.st, r->h->nb);
+    apply_ops(r->state, r->n, dtype, r->fused, s.st, r->h->nb);
     readout_launch_async(r->state, dtype, r->n, r->h->nb, s.st, static_cast<double *>(addr(p, sb)), s.pinned,
                          s.pinned + 4);
     e = cudaEventRecord(s.ev, s.st);
