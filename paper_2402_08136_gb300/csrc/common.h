@@ -93,8 +93,9 @@ struct Op {
     int pre = 0;                // OP_DFT
     // device offsets (bytes) into the circuit's device blob, per dtype
     size_t dev_off[2] = {0, 0};
-    // complex64 dense ops with 4..6 targets: TF32 hi/lo split of the real form (tensor cores)
-    size_t dev_off_tc = 0;
+    // second table, per dtype: complex64 dense ops with 4..7 targets, the TF32 hi/lo split of
+    // the real form (tensor cores); OP_QPE_PHASE, the high half of its two-table split
+    size_t dev_off_tc[2] = {0, 0};
     bool has_tc = false;
     bool real_u = false;        // OP_DENSE: every entry of U is real (SIMT kernels use 2 FMAs per entry)
 };

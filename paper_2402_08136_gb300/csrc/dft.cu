@@ -68,6 +68,12 @@ void run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
         a.qnb = (int)qop->targets.size();
         a.qm = (int)qop->controls.size();
         a.qh = (a.qm + 1) / 2;  // the split qpe_phase_tables uses
+        bool contig_field = true;
+        for (int j = 0; j < K; j++) contig_field = contig_field && op.targets[j] == op.targets[0] + j;
+        // complex64 only: the recurrence rounds differently from the tables, which complex128's
+        // 1e-12 state tolerance at 20+ clock qubits (phase angles near 1e7 rad) does not allow
+        a.qrec = dtype == QSIM_C64 && contig_field && op.targets[0] >= a.qnb && op.targets[0] + K <= a.qnb + a.qm
+                     ? 1 : 0;
         for (int i = 0; i < a.qnb; i++) QSIM_REQUIRE(qop->targets[i] == i, "phase estimation: data qubits must be 0..nb-1");
         for (int j = 0; j < a.qm; j++)
             QSIM_REQUIRE(qop->controls[j] == a.qnb + j, "phase estimation: clock qubits must follow the data");

@@ -83,6 +83,9 @@ struct DftArgs {
     // qlo[(c mod 2^qh) 2^qnb + d], qhi[(c >> qh) 2^qnb + d]
     const void *qlo, *qhi;
     int qmode, qnb, qm, qh;
+    int qrec;                   // 1 (complex64): the field lies inside the clock register
+                                // (contiguous), so a thread's phases along the field are a
+                                // geometric sequence, refreshed from the tables every 8 terms
     int fpos[kMaxK];            // qubit of field bit j
     int lpos[kMaxLane];         // qubit of lane bit j
     int spos[kMaxSrc];          // qubit of twiddle-source bit j
@@ -286,10 +289,10 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
     V *psi = reinterpret_cast<V *>(a.psi);
     const V *qlo = reinterpret_cast<const V *>(a.qlo), *qhi = reinterpret_cast<const V *>(a.qhi);
     const unsigned long long qdm = (1ull << a.qnb) - 1ull, qcm = (1ull << a.qm) - 1ull, qhm = (1ull << a.qh) - 1ull;
-    auto qphase = [&](unsigned long long idx) -> V {
-        const unsigned long long d = idx & qdm, cv = (idx >> a.qnb) & qcm;
+    auto qphase_cd = [&](unsigned long long cv, unsigned long long d) -> V {
         return cmul(__ldg(qlo + (((cv & qhm) << a.qnb) + d)), __ldg(qhi + (((cv >> a.qh) << a.qnb) + d)));
     };
+    auto qphase = [&](unsigned long long idx) -> V { return qphase_cd((idx >> a.qnb) & qcm, idx & qdm); };
     V x[N2];
 
     // staged input: tile tix lands in stages[(it & 1)] as [field value y][lane], 16-byte
@@ -334,11 +337,25 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
             for (int v = 0; v < N2; v++) x[v] = src[vhi[v]];
         }
         if (a.qmode == 1) {
+            if (CONTIG && a.qrec) {
+                // inputs at field values u + N1 v, one data index: the phase is P Q^v with
+                // Q = the phase of clock value N1 2^(f0 - qnb)
+                const unsigned long long i0 = base + ((unsigned long long)u << a.f0);
+                const V Q = qphase_cd((unsigned long long)N1 << (a.f0 - a.qnb), i0 & qdm);
+                V P{1, 0};
 #pragma unroll
-            for (int v = 0; v < N2; v++) {
-                const unsigned long long idx =
-                    CONTIG ? base + ((unsigned long long)(u + N1 * v) << a.f0) : base + vlo[u] + vhi[v];
-                x[v] = cmul(x[v], qphase(idx));
+                for (int v = 0; v < N2; v++) {
+                    if ((v & 7) == 0) P = qphase(i0 + ((unsigned long long)(N1 * v) << a.f0));
+                    x[v] = cmul(x[v], P);
+                    P = cmul(P, Q);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < N2; v++) {
+                    const unsigned long long idx =
+                        CONTIG ? base + ((unsigned long long)(u + N1 * v) << a.f0) : base + vlo[u] + vhi[v];
+                    x[v] = cmul(x[v], qphase(idx));
+                }
             }
         }
         if (a.twmode == 1) {
@@ -378,6 +395,11 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
 #pragma unroll
             for (int uu = 0; uu < N1; uu++) x[r * N1 + uu] = S[((aa * N1 + uu) << L) + l + pad2];
             dft_regs<N1, SGN, WALSH>(x + r * N1);
+            // Walsh outputs N1 aa + i in natural order: their phases are P Q^i (see qrec)
+            const bool qseq = WALSH && CONTIG && a.qmode == 2 && a.qrec;
+            V P{1, 0}, Q{1, 0};
+            const unsigned long long q0 = base + ((unsigned long long)(N1 * aa) << a.f0);
+            if (qseq) Q = qphase_cd(1ull << (a.f0 - a.qnb), q0 & qdm);
 #pragma unroll
             for (int i = 0; i < N1; i++) {
                 const int y = WALSH ? i + N1 * aa : aa + N2 * bitrev(i, k1);
@@ -390,7 +412,13 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
                 }
                 const unsigned long long oi =
                     CONTIG ? base + ((unsigned long long)y << a.f0) : base + vlo[y & (N1 - 1)] + vhi[y >> k1];
-                if (a.qmode == 2) z = cmul(z, qphase(oi));
+                if (qseq) {
+                    if ((i & 7) == 0) P = qphase(q0 + ((unsigned long long)i << a.f0));
+                    z = cmul(z, P);
+                    P = cmul(P, Q);
+                } else if (a.qmode == 2) {
+                    z = cmul(z, qphase(oi));
+                }
                 psi[oi] = z;
             }
         }

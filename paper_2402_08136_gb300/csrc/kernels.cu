@@ -477,15 +477,18 @@ __global__ void qpe_phase_kernel(const QpeArgs a) {
 // A Fourier or Walsh-Hadamard pass (no twiddle after the transform) on the field w .. w+K-1 of
 // a state that is zero at every index >= 2^w: only field value 0 is populated, and column 0 of
 // the transform is 2^(-K/2) for every output digit, so out[y 2^w + l] = 2^(-K/2) in[l] (times a
-// fused structured phase, on the input or the output index).  col0 = 0 writes the outputs
-// y >= 1 from the untouched column y = 0; col0 = 1 then rescales that column in place.
+// fused structured phase, on the input or the output index).  col0 = 0: each thread writes the
+// outputs y = y0 .. y0+run-1 (y >= 1) of one l from the untouched column y = 0; along y the
+// output phase is a geometric sequence when the field lies inside the clock register (qrec,
+// complex64: refreshed from the tables every 8 terms).
+// col0 = 1 then rescales the column y = 0 in place.
 struct ExpandArgs {
     void *psi;
     const void *qlo, *qhi;  // structured phase tables (qmode 1: input index l, 2: output index)
     long long lowN;         // 2^w
-    long long count;        // outputs this launch writes
+    long long count;        // threads' work items this launch
     double scale;
-    int w, col0, qmode, qnb, qm, qh;
+    int w, K, run, col0, qmode, qnb, qm, qh, qrec;
 };
 
 template <typename R>
@@ -496,21 +499,42 @@ __global__ void expand_kernel(const ExpandArgs a) {
     const V *hi = reinterpret_cast<const V *>(a.qhi);
     const unsigned long long dmask = (1ull << a.qnb) - 1ull, cmask = (1ull << a.qm) - 1ull;
     const unsigned long long hmask = (1ull << a.qh) - 1ull;
-    auto phase = [&](unsigned long long i) -> V {
-        const unsigned long long d = i & dmask, c = (i >> a.qnb) & cmask;
+    auto phase_cd = [&](unsigned long long c, unsigned long long d) -> V {
         return cmul(lo[((c & hmask) << a.qnb) + d], hi[((c >> a.qh) << a.qnb) + d]);
     };
+    auto phase = [&](unsigned long long i) -> V { return phase_cd((i >> a.qnb) & cmask, i & dmask); };
     const R sc = (R)a.scale;
+    const unsigned long long ymax = 1ull << a.K;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.count;
          g += (long long)gridDim.x * blockDim.x) {
         const unsigned long long l = (unsigned long long)g & (unsigned long long)(a.lowN - 1);
-        const unsigned long long idx = a.col0 ? l : (unsigned long long)g + (unsigned long long)a.lowN;
         V z = psi[l];
         if (a.qmode == 1) z = cmul(z, phase(l));
         z.x *= sc;
         z.y *= sc;
-        if (a.qmode == 2) z = cmul(z, phase(idx));
-        psi[idx] = z;
+        if (a.col0) {
+            if (a.qmode == 2) z = cmul(z, phase(l));
+            psi[l] = z;
+            continue;
+        }
+        const unsigned long long y0 = 1ull + ((unsigned long long)g >> a.w) * (unsigned long long)a.run;
+        const bool seq = a.qmode == 2 && a.qrec;
+        V P{1, 0}, Q{1, 0};
+        if (seq) Q = phase_cd(1ull << (a.w - a.qnb), l & dmask);
+        for (int j = 0; j < a.run; j++) {
+            const unsigned long long y = y0 + (unsigned long long)j;
+            if (y >= ymax) break;
+            const unsigned long long idx = (y << a.w) | l;
+            V o = z;
+            if (seq) {
+                if ((j & 7) == 0) P = phase(idx);  // refreshed from the tables every 8 terms
+                o = cmul(z, P);
+                P = cmul(P, Q);
+            } else if (a.qmode == 2) {
+                o = cmul(z, phase(idx));
+            }
+            psi[idx] = o;
+        }
     }
 }
 
@@ -933,6 +957,8 @@ void run_expand(void *state, int w, int dtype, const Op &op, const Op *qop, cons
     a.lowN = 1ll << w;
     a.w = w;
     a.scale = std::ldexp(1.0, -K / 2) * ((K & 1) ? std::sqrt(0.5) : 1.0);
+    a.K = K;
+    a.run = std::min(32, (1 << K) - 1);
     if (qop && qmode) {
         a.qlo = qlo;
         a.qhi = qhi;
@@ -940,10 +966,13 @@ void run_expand(void *state, int w, int dtype, const Op &op, const Op *qop, cons
         a.qnb = (int)qop->targets.size();
         a.qm = (int)qop->controls.size();
         a.qh = (a.qm + 1) / 2;  // the split qpe_phase_tables uses
+        // the field is clock bits; complex64 only (as in the Fourier passes)
+        a.qrec = dtype == QSIM_C64 && w >= a.qnb && w + K <= a.qnb + a.qm ? 1 : 0;
     }
     for (int pass = 0; pass < 2; pass++) {  // outputs y >= 1 first, then column 0 in place
         a.col0 = pass;
-        a.count = pass ? a.lowN : (a.lowN << K) - a.lowN;
+        const long long runs = (((1ll << K) - 1) + a.run - 1) / a.run;
+        a.count = pass ? a.lowN : a.lowN * runs;
         const int grid = grid_for(a.count, 256);
         if (dtype == QSIM_C128) expand_kernel<double><<<grid, 256, 0, st>>>(a);
         else expand_kernel<float><<<grid, 256, 0, st>>>(a);
@@ -993,17 +1022,17 @@ std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype) {
                 for (int r = 0; r < D; r++) put_complex(blob, dtype, op.U[(size_t)r * D + col]);
             if (dtype == QSIM_C64 && dense_tc_supported((int)op.targets.size())) {
                 align_blob(blob);
-                op.dev_off_tc = blob.size();
+                op.dev_off_tc[slot] = blob.size();
                 op.has_tc = true;
                 const size_t nb = dense_tc_blob_bytes((int)op.targets.size());
                 blob.resize(blob.size() + nb);
-                dense_tc_pack((int)op.targets.size(), op.U, blob.data() + op.dev_off_tc);
+                dense_tc_pack((int)op.targets.size(), op.U, blob.data() + op.dev_off_tc[slot]);
             } else if (dtype == QSIM_C64 && dense_tc_real7_applies(op)) {
                 align_blob(blob);
-                op.dev_off_tc = blob.size();
+                op.dev_off_tc[slot] = blob.size();
                 op.has_tc = true;
                 blob.resize(blob.size() + dense_tc_real7_blob_bytes());
-                dense_tc_pack_real7(op.U, blob.data() + op.dev_off_tc);
+                dense_tc_pack_real7(op.U, blob.data() + op.dev_off_tc[slot]);
             }
         } else if (op.kind == OP_DIAG) {
             for (const cd &z : op.U) put_complex(blob, dtype, z);
@@ -1015,7 +1044,7 @@ std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype) {
             qpe_phase_tables(op, lo, hi, h);
             for (const cd &z : lo) put_complex(blob, dtype, z);
             align_blob(blob);
-            op.dev_off_tc = blob.size();  // second table
+            op.dev_off_tc[slot] = blob.size();  // second table
             for (const cd &z : hi) put_complex(blob, dtype, z);
         } else if (op.kind == OP_DFT || op.kind == OP_WALSH) {
             std::vector<cd> W, Tlo, Thi;
@@ -1134,7 +1163,7 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
             }
             if (qmode) {
                 const Op &p = ops[pi], &q = ops[qi];
-                const void *qlo = base + q.dev_off[slot], *qhi = base + q.dev_off_tc;
+                const void *qlo = base + q.dev_off[slot], *qhi = base + q.dev_off_tc[slot];
                 if (expandable(p)) {
                     run_expand(state, w, dtype, p, &q, qlo, qhi, qmode, st);
                     w += (int)p.targets.size();
@@ -1152,7 +1181,7 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
             continue;
         }
         if (op.kind == OP_QPE_PHASE) {  // diagonal: only the live part needs it
-            run_qpe_phase(state, w, dtype, op, dptr, base + op.dev_off_tc, st);
+            run_qpe_phase(state, w, dtype, op, dptr, base + op.dev_off_tc[slot], st);
             continue;
         }
         if (op.kind == OP_PHASE && top_qubit(op) >= w) continue;  // needs a 1 where all are 0
@@ -1172,8 +1201,8 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
             case OP_DENSE:
                 if (dtype == QSIM_C64 && op.has_tc && tc_enabled() &&
                     (op.targets.size() == 7
-                         ? launch_dense_tc_real7(state, w, op.targets, op.controls, base + op.dev_off_tc, num_sms(), st)
-                         : launch_dense_tc(state, w, op.targets, op.controls, base + op.dev_off_tc, num_sms(), st)))
+                         ? launch_dense_tc_real7(state, w, op.targets, op.controls, base + op.dev_off_tc[slot], num_sms(), st)
+                         : launch_dense_tc(state, w, op.targets, op.controls, base + op.dev_off_tc[slot], num_sms(), st)))
                     break;
                 run_dense(state, w, dtype, op, dptr, st);
                 break;

@@ -132,3 +132,25 @@ def test_hhl_run_circuit_that_never_touches_the_ancilla(qs, cuda_device, dtype):
     _, a_np, b_np = both_ways(qs, h, c, dtype)
     assert np.max(np.abs(a_np - b_np)) <= TOL[dtype] / 10
     assert np.all(a_np[1 << (n - 1):] == 0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("fft", [False, True])
+def test_one_circuit_in_both_dtypes(qs, cuda_device, fft):
+    """The same circuit object applied in complex128, then complex64 (its device tables are
+    packed per dtype, the structured phase's second and per-chunk tables included)."""
+    A, b = synth.contingency_system(np.random.default_rng(8), 9)
+    m = 7
+    h = qs.hhl_build(A, b, m, structured=True, fft_qft=fft)
+    circ = qs.qsim_fuse(h.as_circuit(), 3)
+    ref = ohhl.solve(A, b, m)
+    n = h.info()["n"]
+    for dtype in (torch.complex128, torch.complex64):
+        st = torch.empty(1 << n, dtype=dtype, device="cuda")
+        qs.hhl_prepare_state(st, h)
+        qs.qsim_apply(st, circ, n_qubits=n)
+        torch.cuda.synchronize()
+        out = st.cpu().numpy().astype(np.complex128)
+        tol = max(TOL[dtype], 2.0 ** m * 2 * math.pi * 8 * np.finfo(float).eps) \
+            if dtype == torch.complex128 else TOL[dtype]
+        assert np.max(np.abs(out - ref["psi"])) <= tol
