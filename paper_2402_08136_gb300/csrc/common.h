@@ -182,8 +182,12 @@ void batch_host_result(const qsim_batch *b, int i, double *x_out, hhl_readout_st
 void dft_tables(const Op &op, std::vector<cd> &W, std::vector<cd> &Tlo, std::vector<cd> &Thi);
 // qop (OP_QPE_PHASE, optional): its diagonal applied to the pass's inputs (qmode 1) or outputs
 // (qmode 2), tables qlo / qhi as packed for that op
-void run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cudaStream_t st,
-             const Op *qop = nullptr, const void *qlo = nullptr, const void *qhi = nullptr, int qmode = 0);
+// inv (OP_HHL_INVERT on qubit n, optional): applied to the outputs, which then also fill the
+// unwritten upper half 2^n .. 2^(n+1); returns false (nothing launched) if the field is not one
+// contiguous run of the rotation's clock order
+bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cudaStream_t st,
+             const Op *qop = nullptr, const void *qlo = nullptr, const void *qhi = nullptr, int qmode = 0,
+             const Op *inv = nullptr);
 // linalg.cpp
 void hermitian_eig(int N, const std::vector<cd> &A, std::vector<double> &lam, std::vector<cd> &V);
 void symmetric_eig_real(int N, const std::vector<double> &A, std::vector<double> &lam, std::vector<double> &V);

@@ -45,8 +45,8 @@ void dft_tables(const Op &op, std::vector<cd> &W, std::vector<cd> &Tlo, std::vec
     for (size_t j = 0; j < Thi.size(); j++) Thi[j] = unit(j << hT, K + ns);
 }
 
-void run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cudaStream_t st, const Op *qop,
-             const void *qlo, const void *qhi, int qmode) {
+bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cudaStream_t st, const Op *qop,
+             const void *qlo, const void *qhi, int qmode, const Op *inv) {
     const int K = (int)op.targets.size(), ns = (int)op.controls.size();
     QSIM_REQUIRE(K >= 1 && K <= kMaxK && ns <= kMaxSrc && K + ns <= 30 && K <= n, "Fourier pass shape");
     DftArgs a;
@@ -77,6 +77,32 @@ void run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
         for (int i = 0; i < a.qnb; i++) QSIM_REQUIRE(qop->targets[i] == i, "phase estimation: data qubits must be 0..nb-1");
         for (int j = 0; j < a.qm; j++)
             QSIM_REQUIRE(qop->controls[j] == a.qnb + j, "phase estimation: clock qubits must follow the data");
+    }
+    if (inv != nullptr) {
+        // the rotation reads the clock value through runs of consecutive qubits; the field must
+        // be one contiguous piece of one run (its bits then land on consecutive bits of k)
+        bool contig_field = true;
+        for (int j = 0; j < K; j++) contig_field = contig_field && op.targets[j] == op.targets[0] + j;
+        if (!contig_field || inv->targets[0] != n || op.kind != OP_DFT || op.sign != -1) return false;
+        a.inv = 1;
+        a.inv_bit = n;
+        a.inv_Cs = inv->tq;
+        a.inv_nc = (int)inv->controls.size();
+        a.inv_twos = inv->sign == -1 ? 1 : 0;
+        a.inv_fdst = -1;
+        for (int j = 0; j < a.inv_nc;) {
+            int wd = 1;
+            while (j + wd < a.inv_nc && inv->controls[j + wd] == inv->controls[j] + wd) wd++;
+            if (a.inv_nseg == 8) return false;
+            a.inv_src[a.inv_nseg] = inv->controls[j];
+            a.inv_w[a.inv_nseg] = wd;
+            a.inv_dst[a.inv_nseg] = j;
+            if (op.targets[0] >= inv->controls[j] && op.targets[0] + K <= inv->controls[j] + wd)
+                a.inv_fdst = j + (op.targets[0] - inv->controls[j]);
+            a.inv_nseg++;
+            j += wd;
+        }
+        if (a.inv_fdst < 0) return false;
     }
     a.scale = std::ldexp(1.0, -K / 2) * ((K & 1) ? std::sqrt(0.5) : 1.0);
     for (int j = 0; j < K; j++) a.fpos[j] = op.targets[j];
@@ -142,9 +168,10 @@ void run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
     bool contig = true;
     for (int j = 0; j < K; j++) contig = contig && op.targets[j] == op.targets[0] + j;
     a.f0 = op.targets[0];
-    const int kind = op.kind == OP_WALSH ? 1 : 0;
+    const int kind = op.kind == OP_WALSH ? 1 : (a.inv ? 2 : 0);
     if (dtype == QSIM_C128) dft_launch_f64(a, K, op.sign, kind, contig, threads, smem, st);
     else dft_launch_f32(a, K, op.sign, kind, contig, threads, smem, st);
+    return true;
 }
 
 }  // namespace qsim

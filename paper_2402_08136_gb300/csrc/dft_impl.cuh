@@ -86,6 +86,14 @@ struct DftArgs {
     int qrec;                   // 1 (complex64): the field lies inside the clock register
                                 // (contiguous), so a thread's phases along the field are a
                                 // geometric sequence, refreshed from the tables every 8 terms
+    // HHL eigenvalue inversion fused into the outputs (contiguous field, upper half unwritten):
+    // the ancilla is index bit inv_bit; k = clock value, bits from the index through nseg runs
+    // (run s: bits dst[s] .. dst[s]+w[s]-1 of k on qubits src[s] ..), the field's own bits land
+    // on bits inv_fdst .. of k; r = clamp(Cs / k) (two's complement if inv_twos), the output z
+    // goes to psi[idx] as sqrt((1 - |r|)(1 + |r|)) z and to psi[idx + 2^inv_bit] as r z
+    int inv, inv_bit, inv_twos, inv_nc, inv_fdst, inv_nseg;
+    double inv_Cs;
+    int inv_src[8], inv_w[8], inv_dst[8];
     int fpos[kMaxK];            // qubit of field bit j
     int lpos[kMaxLane];         // qubit of lane bit j
     int spos[kMaxSrc];          // qubit of twiddle-source bit j
@@ -221,10 +229,12 @@ __device__ __forceinline__ void dft_regs(V *x) {
 
 template <typename R> struct MaxThreads { static constexpr int n = sizeof(R) == 4 ? 512 : 256; };
 
-// KIND 0: DFT (output digits reversed by the radix-2 network), 1: Walsh-Hadamard (natural order)
+// KIND 0: DFT (output digits reversed by the radix-2 network), 1: Walsh-Hadamard (natural order),
+// 2: DFT with the HHL inversion fused into its outputs (inv; contiguous fields only)
 template <typename R, int K, int SGN, int KIND, bool CONTIG>
 __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) {
     constexpr bool WALSH = KIND == 1;
+    constexpr bool INV = KIND == 2 && CONTIG;
     using V = typename CV<R>::T;
     constexpr int k1 = K / 2, k2 = K - k1;
     constexpr int N1 = 1 << k1, N2 = 1 << k2, RR = N2 / N1;
@@ -314,6 +324,10 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
     int it = 0;
     for (long long tix = blockIdx.x; tix < a.ntiles; tix += gridDim.x, it++) {
         const unsigned long long base = insert_zero_bits((unsigned long long)tix, a.fix, a.nfix) + lane_off[l];
+        unsigned long long kb = 0;  // clock value bits outside the field (inversion)
+        if (INV)
+            for (int sg = 0; sg < a.inv_nseg; sg++)
+                kb |= ((base >> a.inv_src[sg]) & ((1ull << a.inv_w[sg]) - 1ull)) << a.inv_dst[sg];
         unsigned w = 0;
         for (int j = 0; j < a.ns; j++) w |= (unsigned)((base >> a.spos[j]) & 1ull) << j;
         // pass 1
@@ -419,6 +433,21 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
                 } else if (a.qmode == 2) {
                     z = cmul(z, qphase(oi));
                 }
+                if (INV) {
+                    const unsigned long long kk = kb | ((unsigned long long)y << a.inv_fdst);
+                    R sr = 0, cr = 1;
+                    if (kk) {
+                        const long long ks = (a.inv_twos && (kk >> (a.inv_nc - 1))) ? (long long)kk - (1ll << a.inv_nc)
+                                                                                   : (long long)kk;
+                        sr = (R)a.inv_Cs / (R)ks;
+                        if (sr > (R)1) sr = (R)1;
+                        if (sr < (R)-1) sr = (R)-1;
+                        const R as = sr < 0 ? -sr : sr;
+                        cr = sqrt(((R)1 - as) * ((R)1 + as));
+                    }
+                    psi[oi + (1ull << a.inv_bit)] = V{sr * z.x, sr * z.y};
+                    z = V{cr * z.x, cr * z.y};
+                }
                 psi[oi] = z;
             }
         }
@@ -444,11 +473,17 @@ void launch_kind(const DftArgs &a, bool contig, int threads, size_t smem, cudaSt
     if (!attr) {
         DFT_CUDA_OK(cudaFuncSetAttribute(dft_kernel<R, K, SGN, KIND, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        DFT_CUDA_OK(cudaFuncSetAttribute(dft_kernel<R, K, SGN, KIND, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        if constexpr (KIND != 2)
+            DFT_CUDA_OK(cudaFuncSetAttribute(dft_kernel<R, K, SGN, KIND, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         attr = true;
     }
-    auto kern = contig ? dft_kernel<R, K, SGN, KIND, true> : dft_kernel<R, K, SGN, KIND, false>;
+    auto kern = dft_kernel<R, K, SGN, KIND, true>;
+    if constexpr (KIND != 2) {
+        if (!contig) kern = dft_kernel<R, K, SGN, KIND, false>;
+    } else {
+        QSIM_REQUIRE(contig, "fused inversion needs a contiguous field");
+    }
     int per_sm = 0;
     DFT_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     QSIM_REQUIRE(per_sm > 0, "Fourier pass does not fit on an SM");
@@ -460,7 +495,8 @@ void launch_kind(const DftArgs &a, bool contig, int threads, size_t smem, cudaSt
 
 template <typename R, int K>
 void launch_k(const DftArgs &a, int sign, int kind, bool contig, int threads, size_t smem, cudaStream_t st) {
-    if (kind == 1) launch_kind<R, K, 1, 1>(a, contig, threads, smem, st);
+    if (kind == 2) launch_kind<R, K, -1, 2>(a, contig, threads, smem, st);
+    else if (kind == 1) launch_kind<R, K, 1, 1>(a, contig, threads, smem, st);
     else if (sign > 0) launch_kind<R, K, 1, 0>(a, contig, threads, smem, st);
     else launch_kind<R, K, -1, 0>(a, contig, threads, smem, st);
 }

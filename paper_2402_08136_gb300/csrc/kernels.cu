@@ -1129,7 +1129,8 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
     // the preparation only the data register is populated).  An op on qubits below w runs as a
     // w-qubit state; a twiddle-free pass on the field right above w broadcasts column 0 (write
     // only) and widens w; diagonal ops leave zeros zero; the inversion rotation on the top qubit
-    // writes the upper half without reading it; any other op first zero-fills up to its top qubit.
+    // writes the upper half without reading it (inside the preceding pass when that pass runs
+    // right below it); any other op first zero-fills up to its top qubit.
     int w = (live >= 0 && live < n) ? live : n;
     const size_t vb = 2 * real_size(dtype);
     auto materialize = [&](int to) {
@@ -1171,6 +1172,17 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
                     materialize(top_qubit(p) + 1);  // the phase is diagonal: zeros stay zero
                     run_dft(state, w, dtype, p, base + p.dev_off[slot], st, &q, qlo, qhi, qmode);
                 }
+                i++;
+                continue;
+            }
+        }
+        if (is_pass(op) && i + 1 < ops.size() && ops[i + 1].kind == OP_HHL_INVERT && w == n - 1 &&
+            ops[i + 1].targets[0] == n - 1 && top_qubit(op) < w && top_qubit(ops[i + 1]) == n - 1) {
+            // the pass writes the rotated outputs into both halves (the upper one is unwritten)
+            bool low = true;
+            for (int q : ops[i + 1].controls) low = low && q < n - 1;
+            if (low && run_dft(state, w, dtype, op, dptr, st, nullptr, nullptr, nullptr, 0, &ops[i + 1])) {
+                w = n;
                 i++;
                 continue;
             }

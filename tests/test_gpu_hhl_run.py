@@ -154,3 +154,22 @@ def test_one_circuit_in_both_dtypes(qs, cuda_device, fft):
         tol = max(TOL[dtype], 2.0 ** m * 2 * math.pi * 8 * np.finfo(float).eps) \
             if dtype == torch.complex128 else TOL[dtype]
         assert np.max(np.abs(out - ref["psi"])) <= tol
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("m", [12, 17])
+def test_hhl_run_multi_field_clock(qs, cuda_device, dtype, m):
+    """Clock registers of two Fourier fields: the inverse QFT's last pass carries the inversion
+    rotation into the unwritten upper half, the opening layer expands field by field."""
+    A, b = synth.contingency_system(np.random.default_rng(12), 5)
+    h = qs.hhl_build(A, b, m, structured=True, fft_qft=True)
+    circ = qs.qsim_fuse(h.as_circuit(), 4)
+    st, a_np, b_np = both_ways(qs, h, circ, dtype)
+    assert np.max(np.abs(a_np - b_np)) <= TOL[dtype] / 10
+    ref = ohhl.solve(A, b, m)
+    tol = max(TOL[dtype], 2.0 ** m * 2 * math.pi * 8 * np.finfo(float).eps) if dtype == torch.complex128 \
+        else TOL[dtype]
+    assert np.max(np.abs(a_np - ref["psi"])) <= tol
+    r = qs.hhl_readout(st, h)
+    assert abs(r["p_success"] - ref["P"]) <= 10 * tol
