@@ -155,6 +155,10 @@ int qsim_apply(void *state, int n_qubits, int dtype, const qsim_circuit *c, void
 /* Sticky device-side error flags of this process's kernels (bit 0: a bounded wait inside a
  * tensor-core kernel ran out, its results are invalid).  Synchronizes the device; clear != 0
  * resets the flags.  Errors: EINVAL, ECUDA. */
+/* Number of kernels this library has launched in this process (every launch site counts; the
+ * replay of a CUDA graph that captured library calls does not).  Never fails. */
+unsigned long long qsim_launch_count(void);
+
 int qsim_device_status(unsigned *flags, int clear);
 
 /* ======================================================================================= *

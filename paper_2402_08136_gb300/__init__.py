@@ -27,6 +27,7 @@ from ._binding import (  # noqa: F401
     library_path,
     qsim_apply,
     qsim_device_status,
+    qsim_launch_count,
     qsim_fuse,
     qsim_version,
 )

@@ -90,6 +90,7 @@ _SIGS = {
     "hhl_get_info": ([_VP, ctypes.POINTER(_HHLInfo)], ctypes.c_int),
     "hhl_prepare_state": ([_VP, ctypes.c_int, _VP, _VP], ctypes.c_int),
     "hhl_run": ([_VP, ctypes.c_int, _VP, _VP, _VP], ctypes.c_int),
+    "qsim_launch_count": ([], ctypes.c_ulonglong),
     "qsim_device_status": ([ctypes.POINTER(ctypes.c_uint), ctypes.c_int], ctypes.c_int),
     "qsim_batch_create": ([ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int,
                            ctypes.POINTER(_VP)], ctypes.c_int),
@@ -171,6 +172,11 @@ def _dtype_of(state):
 def _check_state(state, n: int):
     if not state.is_cuda or not state.is_contiguous() or state.numel() != (1 << n):
         raise QsimError(-1, "state must be a contiguous CUDA tensor of 2^n amplitudes")
+
+
+def qsim_launch_count() -> int:
+    """Kernels this library has launched in this process (graph replays not included)."""
+    return int(library().qsim_launch_count())
 
 
 def qsim_device_status(clear: bool = False) -> int:

@@ -139,6 +139,8 @@ void circuit_info(const qsim_circuit *c, qsim_circuit_info *out);
 // live < n: the caller guarantees that the input is zero at every index >= 2^live and that only
 // the first 2^live amplitudes have been written (see hhl_run); the result is the full state.
 void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int live = -1);
+// every kernel launch site reports its launches (qsim_launch_count)
+void note_launches(int k);
 void ensure_device_blob(qsim_circuit *c, int dtype);
 std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype);   // sets op offsets
 void attach_external_blob(qsim_circuit *c, int dtype, void *dev, size_t bytes);

@@ -720,6 +720,7 @@ bool launch_dense_tc_real7(void *state, int n, const std::vector<int> &targets, 
     tc::dense_tc_real7_kernel<<<(int)grid, tc::kThreadsWS, tc::tcr::SMEM, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_real7_kernel: ") + cudaGetErrorString(e));
+    note_launches(1);
     return true;
 }
 
@@ -767,6 +768,7 @@ static void launch_tc_t(const tc::Args &a, int sms, cudaStream_t st) {
     tc::dense_tc_kernel<K, TR><<<(int)grid, tc::kThreadsWS, C::SMEM, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_kernel: ") + cudaGetErrorString(e));
+    note_launches(1);
 }
 
 // Returns false if this gate shape is not handled by the tensor-core kernel.

@@ -491,6 +491,7 @@ void launch_kind(const DftArgs &a, bool contig, int threads, size_t smem, cudaSt
     kern<<<(int)grid, threads, smem, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dft_kernel: ") + cudaGetErrorString(e));
+    note_launches(1);
 }
 
 template <typename R, int K>

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -30,9 +31,15 @@ namespace qsim {
             throw ::qsim::Error(QSIM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
     } while (0)
 
-static void check_launch(const char *what) {
+// Kernels launched by this library (every launch site reports here; a CUDA graph replay does
+// not go through them).
+static std::atomic<unsigned long long> g_launches{0};
+void note_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+
+static void check_launch(const char *what, int launches = 1) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    note_launches(launches);
 }
 
 static int num_sms() {
@@ -1286,7 +1293,7 @@ void readout_launch_async(const void *state, int dtype, int n, int nb, cudaStrea
         norm_partials_kernel<float><<<nblk, 256, 0, st>>>(state, chunk, partials);
         norm_final_kernel<float><<<1, 256, 0, st>>>(partials, nblk, state, off, (int)slice_len, out);
     }
-    check_launch("readout kernels");
+    check_launch("readout kernels", 2);
     CUDA_OK(cudaMemcpyAsync(pinned_sums, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_OK(cudaMemcpyAsync(pinned_slice, static_cast<const unsigned char *>(state) + off * vb, slice_len * vb,
                             cudaMemcpyDeviceToHost, st));
@@ -1322,7 +1329,7 @@ void readout_device(const void *state, int dtype, int n, int nb, int m, void *st
             norm_partials_kernel<float><<<nblk, 256, 0, st>>>(state, chunk, partials);
             norm_final_kernel<float><<<1, 256, 0, st>>>(partials, nblk, state, off, (int)slice_len, out);
         }
-        check_launch("readout kernels");
+        check_launch("readout kernels", 2);
         std::vector<unsigned char> hs(slice_len * vb);
         double hsum[3];
         CUDA_OK(cudaMemcpyAsync(hsum, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1427,7 +1434,7 @@ extern "C" int hhl_readout_noalloc(const void *state, int dtype, const hhl_circu
             norm_final_kernel<float><<<1, 256, 0, st>>>(partials, nblk, state, off, (int)slice_len, out);
             slice_to_f64_kernel<float><<<(int)((slice_len + 255) / 256), 256, 0, st>>>(state, off, (int)slice_len, slice);
         }
-        check_launch("hhl_readout_noalloc kernels");
+        check_launch("hhl_readout_noalloc kernels", 3);
         double sums[3];
         CUDA_OK(cudaMemcpyAsync(sums, out, sizeof(sums), cudaMemcpyDeviceToHost, st));
         // the slice lands straight in the caller's buffer: all 2^nb amplitudes, or the N entries
@@ -1477,6 +1484,8 @@ qsim_circuit::~qsim_circuit() {
 }
 
 extern "C" void qsim_circuit_free(qsim_circuit *c) { delete c; }
+
+extern "C" unsigned long long qsim_launch_count(void) { return g_launches.load(); }
 
 extern "C" int qsim_apply(void *state, int n_qubits, int dtype, const qsim_circuit *c, void *stream) {
     return guarded([&] {

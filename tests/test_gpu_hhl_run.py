@@ -173,3 +173,22 @@ def test_hhl_run_multi_field_clock(qs, cuda_device, dtype, m):
     assert np.max(np.abs(a_np - ref["psi"])) <= tol
     r = qs.hhl_readout(st, h)
     assert abs(r["p_success"] - ref["P"]) <= 10 * tol
+
+
+@pytest.mark.gpu
+def test_launch_counter_counts_kernels(qs, cuda_device):
+    """qsim_launch_count: one launch per applied gate here, two for the readout reductions."""
+    rng = np.random.default_rng(9)
+    st = torch.from_numpy(synth.gaussian_state_np(1, 12)).cuda()
+    c = qs.Circuit(12).add_gate([0], synth.haar_unitary(rng, 2)).add_gate([3, 4], synth.haar_unitary(rng, 4))
+    l0 = qs.qsim_launch_count()
+    qs.qsim_apply(st, c)
+    torch.cuda.synchronize()
+    assert qs.qsim_launch_count() - l0 == 2
+    p = synth.hhl7_problem()
+    h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"])
+    s2 = torch.empty(1 << h.info()["n"], dtype=torch.complex128, device="cuda")
+    qs.hhl_run(s2, h)
+    l1 = qs.qsim_launch_count()
+    qs.hhl_readout(s2, h)
+    assert qs.qsim_launch_count() - l1 == 2
