@@ -134,10 +134,12 @@ __device__ __forceinline__ void commit_to(uint64_t *bar) {
                  : "memory");
 }
 
+// TF32 of a finite float, rounded to nearest with ties away from zero: add half a TF32 unit in
+// the last place to the magnitude bits and clear the 13 mantissa bits TF32 drops (integer
+// arithmetic, so the producers' split does not queue on the conversion pipe; same bits as
+// cvt.rna.tf32.f32 for finite inputs, and the state's entries are at most 1 in magnitude)
 __device__ __forceinline__ unsigned to_tf32(float x) {
-    unsigned r;
-    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-    return r;
+    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
 }
 
 __device__ __forceinline__ unsigned long long insert_zeros(unsigned long long x, const int *pos, int cnt) {
