@@ -148,7 +148,7 @@ def rank_seed(base: int, rank: int) -> int:
 # capture of the current kernel on a 27-qubit state (the full-size launch is linear in 2^n).
 # An entry is removed whenever its kernel changes, until it is captured again.
 TRAFFIC = {
-    ("dense_tc_kernel", "c64"): {"bytes_per_amp": 2.0867e9 / 2 ** 27,
+    ("dense_tc_kernel", "c64"): {"bytes_per_amp": 2.0868e9 / 2 ** 27,
                                  "source": "profiles/dense_gate_kernels_c64_27q.md (k=4..6 mean, "
                                            "27-qubit capture scaled by 2^n)"},
     ("dense_pipe_kernel", "c64"): {"bytes_per_amp": 2.0874e9 / 2 ** 27,
