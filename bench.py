@@ -380,8 +380,10 @@ def run_hhl(args, ws, rank, which):
     else:
         p = synth.hhl27_problem()
         dtypes = [("c64", torch.complex64), ("c128", torch.complex128)]
+    tb = time.perf_counter()
     h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"], structured=args.structured,
                      fft_qft=args.fft_qft)
+    build_ms = 1e3 * (time.perf_counter() - tb)  # host: eigendecomposition and gate list
     info = h.info()
     n = info["n"]
     xt = np.linalg.solve(p["A"], p["b"])
@@ -391,7 +393,9 @@ def run_hhl(args, ws, rank, which):
         # complex64: widest fusion (dense 4..6 run on the tensor cores); complex128: FP64-bound,
         # narrow fusion keeps the flops per amplitude low
         max_k = args.max_k or (6 if name == "c64" else 2)
+        tf = time.perf_counter()
         circ = qs.qsim_fuse(h.as_circuit(), max_k)
+        fuse_ms = 1e3 * (time.perf_counter() - tf)
         ci = circ.info()
         st = torch.empty(1 << n, dtype=dt, device="cuda")
 
@@ -421,6 +425,7 @@ def run_hhl(args, ws, rank, which):
                      "p99_ms": 1e3 * float(np.percentile(lat, 99)), "rel_err_vs_classical": rel,
                      "p_success": r["p_success"], "leakage": r["leakage"], "max_k": max_k,
                      "gpu_launches": n_launch, "launches_per_solve": n_launch / reps,
+                     "host_fuse_ms": round(fuse_ms, 3),
                      "fused_ops": ci["n_gates"], "algorithmic_gb": ci["bytes_c64" if name == "c64" else "bytes_c128"] / 1e9}
         del st
     if which == "hhl7":
@@ -465,7 +470,8 @@ def run_hhl(args, ws, rank, which):
         "dtype": "c128" if which == "hhl7" else "c64",
         "config": {"workload": which, "n_qubits": n, "nb": info["nb"], "m": info["m"],
                    "unfused_gates": info["n_gates"], "structured_qpe": bool(args.structured),
-                   "qft": "fourier passes" if args.fft_qft else "gates"},
+                   "qft": "fourier passes" if args.fft_qft else "gates",
+                   "host_build_ms": round(build_ms, 3)},
         "latency_ms": {"p50": round(main["p50_ms"], 4), "p99": round(main["p99_ms"], 4)},
         "paths": res,
         "gpu_launches": main["gpu_launches"],  # counted by the library's launch sites
