@@ -254,3 +254,24 @@ def test_fft_qft_pass_counts(qs, m, fields):
         assert g.info()["n_gates"] - h.info()["n_gates"] == 2 * (iqft + m) - 4 * fields
     fz = qs.qsim_fuse(h.as_circuit(), 4).info()
     assert fz["n_dft"] == 4 * fields
+
+
+def test_run_and_solve_argument_checks(qs):
+    """hhl_run, hhl_batch_solve, hhl_batch_results reject bad arguments before touching the
+    device; qsim_launch_count needs no GPU."""
+    import ctypes
+    from paper_2402_08136_gb300 import _binding as B
+    L = B.library()
+    p = synth.hhl7_problem()
+    h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"])
+    fake = ctypes.c_void_p(256)  # never dereferenced: every call below fails its checks first
+    assert L.hhl_run(None, B.QSIM_C64, h.ptr, None, None) != 0
+    assert L.hhl_run(fake, 7, h.ptr, None, None) != 0                      # dtype
+    assert L.hhl_run(fake, B.QSIM_C64, None, None, None) != 0              # no problem
+    other = qs.Circuit(h.info()["n"] + 1)
+    assert L.hhl_run(fake, B.QSIM_C64, h.ptr, other.ptr, None) != 0        # qubit count
+    assert "qubit count" in L.qsim_last_error().decode()
+    assert L.hhl_batch_solve(None, None, None, None) != 0
+    assert L.hhl_batch_results(None, None, None, None) != 0
+    n0 = qs.qsim_launch_count()
+    assert isinstance(n0, int) and n0 >= 0
