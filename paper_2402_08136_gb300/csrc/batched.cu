@@ -11,8 +11,10 @@
 // else is in the batch.
 //
 // Supported operations: dense gates with up to 5 targets and any controls, phase, diagonal,
-// swap, and uniformly controlled RY over a contiguous control register; qubit masks are 32-bit
-// (states of at most 30 qubits).
+// swap, uniformly controlled RY over a contiguous control register, the structured phase, the HHL
+// inversion, and Fourier / Walsh-Hadamard passes over contiguous fields; qubit masks are 32-bit
+// (states of at most 30 qubits).  The running circuit's op list and data are staged in shared
+// memory when they fit; the work counter is reset by the last CTA of a launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -980,7 +982,7 @@ qsim_batch *batch_instantiate(BatchImage *im, void *dev, double *pinned, cudaStr
 namespace {
 
 // Kernel attributes and the grid are fixed when the batch is created, so that a run is only a
-// memset and a launch (capturable into a CUDA graph).
+// launch (capturable into a CUDA graph).
 template <typename R>
 void configure_batch(qsim_batch *B) {
     const size_t smem = (((size_t)B->smem_amps * vbytes(B->dtype) + 15) & ~(size_t)15) + (size_t)B->stage_bytes;
