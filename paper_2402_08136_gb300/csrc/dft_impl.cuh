@@ -25,6 +25,10 @@
 // The same kernel with every twiddle equal to 1 and no digit reversal is the Walsh-Hadamard
 // transform of the field, H on each of its qubits (qsim_circuit_add_walsh): the Hadamard
 // layers of the phase estimation in one pass per field.
+//
+// Options: the structured phase-estimation diagonal on the inputs or outputs (qmode), the HHL
+// inversion rotation on the outputs (KIND 2, writing the unwritten upper half), and an L2
+// prefetch of the next tile's lines once a tile's inputs are in registers (pf).
 #pragma once
 #include <cuda_runtime.h>
 

@@ -12,6 +12,12 @@
 // computes 16 output rows of one group column at a time, writing straight back to HBM.
 // Specialised kernels handle phase (controlled-phase, e.g. the QFT's), diagonal, swap and the
 // uniformly controlled RY of the eigenvalue inversion, touching only the amplitudes they change.
+//
+// The executor (apply_ops) can also run an HHL solve on the populated part of the state only
+// (hhl_run): after the preparation every amplitude from 2^nb on is zero, so it tracks a live
+// width, runs ops below it on the prefix, turns a pass onto the field right above it into a
+// write-only broadcast (expand_kernel), and lets the inversion write the ancilla's upper half
+// without reading it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
