@@ -97,6 +97,9 @@ struct Op {
     // the real form (tensor cores); OP_QPE_PHASE, the high half of its two-table split
     size_t dev_off_tc[2] = {0, 0};
     bool has_tc = false;
+    // complex64 real 6-target op on qubits 0 and 1 run by the real 7-target tensor-core kernel
+    // as I (x) U: the added qubit (-1: none), the lowest one that is neither target nor control
+    int tc_pad = -1;
     bool real_u = false;        // OP_DENSE: every entry of U is real (SIMT kernels use 2 FMAs per entry)
 };
 

@@ -106,6 +106,35 @@ def test_tensor_core_dense_parity_complex64(qs, k):
     check(st, ref, torch.complex64)
 
 
+def test_real_six_target_gates_on_low_qubits(qs):
+    """complex64 real 6-target gates whose targets include qubits 0 and 1 run in the real
+    7-target tensor-core kernel as I (x) U on the lowest free qubit (at the top of the target
+    list, in its middle, and moved up by a control); applied alone and in one circuit."""
+    dtype = torch.complex64
+    rng = np.random.default_rng(66)
+    n = 14
+    psi = host_input(synth.gaussian_state_np(44, n), dtype)
+    cases = [([0, 1, 2, 3, 4, 5], []), ([0, 1, 3, 4, 5, 7], []), ([0, 1, 2, 4, 6, 8], [13]),
+             ([0, 1, 3, 4, 5, 6], [2])]
+    c_all = qs.Circuit(n)
+    ref_all = psi.copy()
+    for t, ctl in cases:
+        Q, _ = np.linalg.qr(rng.standard_normal((64, 64)))
+        U = Q.astype(np.complex128)
+        c_all.add_gate(t, U, ctl)
+        ocore.apply_gate(ref_all, t, U, ctl)
+        ref = psi.copy()
+        ocore.apply_gate(ref, t, U, ctl)
+        st = dev_state(psi, dtype)
+        qs.qsim_apply(st, qs.Circuit(n).add_gate(t, U, ctl))
+        torch.cuda.synchronize()
+        check(st, ref, dtype)
+    st = dev_state(psi, dtype)
+    qs.qsim_apply(st, c_all)
+    torch.cuda.synchronize()
+    check(st, ref_all, dtype)
+
+
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_real_matrix_gates(qs, dtype):
     """Real orthogonal gates (the eigenvector matrices of real symmetric systems) run the SIMT
