@@ -155,11 +155,11 @@ int qsim_apply(void *state, int n_qubits, int dtype, const qsim_circuit *c, void
 /* Sticky device-side error flags of this process's kernels (bit 0: a bounded wait inside a
  * tensor-core kernel ran out, its results are invalid).  Synchronizes the device; clear != 0
  * resets the flags.  Errors: EINVAL, ECUDA. */
+int qsim_device_status(unsigned *flags, int clear);
+
 /* Number of kernels this library has launched in this process (every launch site counts; the
  * replay of a CUDA graph that captured library calls does not).  Never fails. */
 unsigned long long qsim_launch_count(void);
-
-int qsim_device_status(unsigned *flags, int clear);
 
 /* ======================================================================================= *
  * HHL (Sec. III-A procedure, Fig. 5 circuit, Sec. III-B resources)                         *
@@ -293,10 +293,11 @@ typedef struct qsim_batch qsim_batch; /* uploaded op tables of a set of circuits
 
 /* Upload the op tables of `count` circuits (each applied to states[i], a device buffer of
  * 2^n_i amplitudes of `dtype`, n_i <= 30) into one device allocation (synchronous).  Every
- * operation must be a dense gate of at most 5 targets, a phase, diagonal or swap gate, or a
- * uniformly controlled RY over consecutive control qubits (fuse with max_k <= 5); otherwise
- * QSIM_EINVAL.  The state pointers are stored: they must stay valid while the batch is run.
- * Errors: EINVAL, ENOMEM, ECUDA. */
+ * operation must be a dense gate of at most 5 targets, a phase, diagonal or swap gate, a
+ * uniformly controlled RY over consecutive control qubits, the structured phase or the HHL
+ * inversion, or a Fourier / Walsh-Hadamard pass over consecutive ascending qubits (fuse with
+ * max_k <= 5); otherwise QSIM_EINVAL.  The state pointers are stored: they must stay valid
+ * while the batch is run.  Errors: EINVAL, ENOMEM, ECUDA. */
 int qsim_batch_create(const qsim_circuit *const *cs, void *const *states, int count, int dtype,
                       qsim_batch **out);
 
@@ -308,9 +309,10 @@ int hhl_batch_create(const hhl_circuit *const *hs, const qsim_circuit *const *fu
 
 /* Run the batch: one persistent kernel on `stream`, nothing else (no allocation, no copy, no
  * synchronization; the kernel resets its own work counter when it ends), so the call can be
- * captured into a CUDA graph.  Runs of one batch must not overlap (same stream, or ordered).  Each CTA takes whole circuits (most expensive first); a state of up to
- * 2^13 (complex128) or 2^14 (complex64) amplitudes stays in shared memory for the whole
- * circuit, larger ones are updated in place.  One CTA runs one circuit in a fixed order, so a
+ * captured into a CUDA graph.  Runs of one batch must not overlap (same stream, or ordered).
+ * Each CTA takes whole circuits (most expensive first); a state of up to 2^13 (complex128) or
+ * 2^14 (complex64) amplitudes stays in shared memory for the whole circuit, larger ones are
+ * updated in place.  One CTA runs one circuit in a fixed order, so a
  * circuit's result is bit-identical whatever else is in the batch; it equals qsim_apply of
  * the same circuit up to rounding (different kernels).  Errors: EINVAL, ECUDA. */
 int qsim_batch_run(qsim_batch *b, void *stream);
@@ -371,7 +373,8 @@ typedef struct {
  * room for its state (8 * 2^n bytes for complex64, 16 * 2^n for complex128) and a stream is
  * free.  Requests of at most 16 qubits that the batched executor supports (dense gates of at
  * most 5 targets) and that are ready together run as one batched launch; the others run alone
- * with the full-GPU kernels; launches on different streams overlap.  Every request is built
+ * with the full-GPU kernels, preparation and circuit as in hhl_run; launches on different
+ * streams overlap.  Every request is built
  * with QSIM_HHL_FFT_QFT added (the QFTs and clock Hadamard layers as passes).
  * Results equal those of the same request run alone (each circuit's arithmetic does not
  * depend on its batch).  Errors: EINVAL, ENOMEM, ECUDA. */
