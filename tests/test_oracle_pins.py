@@ -50,6 +50,35 @@ def rand_state(rng, n):
     return v / np.linalg.norm(v)
 
 
+def test_threaded_oracle_is_deterministic():
+    """The C oracle's parallel loops (gate groups, UCRY pairs, Neumaier partial sums) give the
+    same bits with 1 thread and with several: its groups are disjoint and its sums are combined
+    in a fixed order, so a race or an order that depends on the thread count would show."""
+    rng = np.random.default_rng(5)
+    n = 16
+    psi0 = rand_state(rng, n)
+    gates = []
+    for _ in range(12):
+        k = int(rng.integers(1, 5))
+        qs = [int(q) for q in rng.choice(n, size=k + 1, replace=False)]
+        gates.append((qs[:k], synth.haar_unitary(rng, 1 << k), qs[k:], [1]))
+    th = rng.uniform(-3, 3, size=8)
+    saved = core.num_threads()
+    outs = []
+    try:
+        for t in (1, max(2, saved)):
+            core.set_num_threads(t)
+            psi = psi0.copy()
+            for tg, U, ctl, vals in gates:
+                core.apply_gate(psi, tg, U, ctl, vals)
+            core.apply_ucry(psi, n - 1, [3, 4, 5], th)
+            outs.append((psi, core.masked_norm2(psi, 1 << (n - 1), 1 << (n - 1))))
+    finally:
+        core.set_num_threads(saved)
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_gate_rule_matches_bruteforce(seed):
     rng = np.random.default_rng(seed)
