@@ -195,9 +195,9 @@ def oracle_gate_sample(seed: int, n_sample: int = 24, per_k: int = 4):
                       "streaming rule)" % (done, per_k, n_sample)}
 
 
-def oracle_hhl_sample(problems, what: str):
+def oracle_hhl_sample(problems, what: str, min_seconds: float = ORACLE_MIN_SECONDS):
     """The oracle solving a bounded list of HHL problems one after another, the list repeated
-    until ORACLE_MIN_SECONDS of work: solves/s."""
+    until `min_seconds` of work: solves/s."""
     from oracle import core as ocore
     from oracle import hhl as ohhl
     done = 0
@@ -207,10 +207,25 @@ def oracle_hhl_sample(problems, what: str):
             ohhl.solve(p["A"], p["b"], p["m"], p.get("t", 0.0), p.get("C", 0.0))
         done += len(problems)
         dt = time.perf_counter() - t0
-        if dt >= ORACLE_MIN_SECONDS:
+        if dt >= min_seconds:
             break
     return {"value": done / dt, "unit": "solves/s", "cores": ocore.num_threads(),
             "kind": "oracle", "seconds": dt, "sample": "%d solves in rounds of %s" % (done, what)}
+
+
+def oracle_hhl_both(problems, what: str, min_seconds: float = 3.0):
+    """The oracle on all host cores (OpenMP) and on one thread: the all-core figure at the top,
+    the single-thread one under "single_thread"."""
+    from oracle import core as ocore
+    allc = ocore.num_threads()
+    rec = oracle_hhl_sample(problems, what, min_seconds)
+    try:
+        ocore.set_num_threads(1)
+        one = oracle_hhl_sample(problems, what, min_seconds)
+    finally:
+        ocore.set_num_threads(allc)
+    rec["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "seconds")}
+    return rec
 
 
 def oracle_baseline(workload: str, rank: int = 0):
@@ -331,7 +346,7 @@ def run_gates(args, ws, rank, dtype_name):
         if args.e2e_from_host_gen else st.cpu()
     host_in = host_in.pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
-    e2e_steps = args.steps
+    e2e_steps = min(args.steps, 5)  # 2 x 16 GiB of host copies per step: a few steps suffice
 
     def e2e_step():
         st.copy_(host_in, non_blocking=True)
@@ -374,12 +389,9 @@ def run_hhl(args, ws, rank, which):
     import torch
     import paper_2402_08136_gb300 as qs
 
-    if which == "hhl7":
-        p = synth.hhl7_problem()
-        dtypes = [("c128", torch.complex128)]
-    else:
-        p = synth.hhl27_problem()
-        dtypes = [("c64", torch.complex64), ("c128", torch.complex128)]
+    assert which == "hhl7"
+    p = synth.hhl7_problem()
+    dtypes = [("c128", torch.complex128)]
     tb = time.perf_counter()
     h = qs.hhl_build(p["A"], p["b"], p["m"], p["t"], p["C"], structured=args.structured,
                      fft_qft=args.fft_qft)
@@ -411,7 +423,7 @@ def run_hhl(args, ws, rank, which):
         lat = []
         barrier(ws)
         t0 = time.perf_counter()
-        reps = args.steps * (200 if which == "hhl7" else 1)
+        reps = args.steps * 200
         l0 = qs.qsim_launch_count()
         for _ in range(reps):
             a = time.perf_counter()
@@ -428,7 +440,7 @@ def run_hhl(args, ws, rank, which):
                      "host_fuse_ms": round(fuse_ms, 3),
                      "fused_ops": ci["n_gates"], "algorithmic_gb": ci["bytes_c64" if name == "c64" else "bytes_c128"] / 1e9}
         del st
-    if which == "hhl7":
+    if True:
         # single-launch form: the whole circuit, state preparation and readout in one persistent
         # kernel (batched executor with one circuit, fusion width autotuned on it); each solve
         # is one library call (launch, synchronization, host scaling of the readout sums the
@@ -460,22 +472,208 @@ def run_hhl(args, ws, rank, which):
                                      "p_success": float(stats[0]["p_success"]),
                                      "leakage": float(stats[0]["leakage"])}
         res["c128_single_launch"]["gpu_launches"] = n_single
+        flops = circ.info()["flops"]
         main_name = "c128_single_launch"
-    else:
-        main_name = dtypes[0][0]
     main = res[main_name]
+    tf = flops * main["solves_per_s"] / 1e12
+    roof = {"bound": "alu", "kernel": "batched_kernel<double> (one circuit)", "achieved": round(tf, 6),
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(tf / FP64_PEAK_TFLOPS, 6),
+            "traffic": None, "flops_per_solve": flops,
+            "peak_kind": "nominal GB300 FP64 rate (1.25 TFLOP/s; a probe measured 1.21)",
+            "note": "a 7-qubit solve (2 KiB state) is launch- and latency-bound: one CTA, a barrier per op"}
     return {
         "metric": "HHL solves/s", "value": round(main["solves_per_s"], 3), "unit": "solves/s",
         "ms_per_step": round(1e3 / main["solves_per_s"], 4), "higher_is_better": True,
-        "dtype": "c128" if which == "hhl7" else "c64",
+        "dtype": "c128",
         "config": {"workload": which, "n_qubits": n, "nb": info["nb"], "m": info["m"],
                    "unfused_gates": info["n_gates"], "structured_qpe": bool(args.structured),
                    "qft": "fourier passes" if args.fft_qft else "gates",
                    "host_build_ms": round(build_ms, 3)},
         "latency_ms": {"p50": round(main["p50_ms"], 4), "p99": round(main["p99_ms"], 4)},
-        "paths": res,
+        "paths": res, "roofline": roof,
         "gpu_launches": main["gpu_launches"],  # counted by the library's launch sites
     }
+
+
+# ------------------------------------------------------------- 27-qubit HHL (precision form)
+# Fourier-pass shapes of the 27-qubit solve (nb = 6, m = 20: two clock fields of 10 qubits):
+# the inverse QFT's top-field pass with its twiddle from the 10 clock bits below, the
+# bottom-field pass, and a Walsh-Hadamard pass; each streams a 2^27 state once
+PASS_SHAPES = (("dft_top_field_twiddle", lambda c: c.add_dft(list(range(16, 26)), -1, src=list(range(6, 16)))),
+               ("dft_bottom_field", lambda c: c.add_dft(list(range(6, 16)), -1)),
+               ("walsh_top_field", lambda c: c.add_walsh(list(range(16, 26)))))
+
+
+def fourier_pass_roofline(qs, torch, launches: int = 10):
+    """Average launch time of each Fourier-pass shape on a 27-qubit complex64 state (1 GiB,
+    larger than L2), CUDA events on the launching stream; algorithmic bytes 2 x 8 x 2^27."""
+    n = 27
+    st = synth.gaussian_state_torch(27, n, torch.complex64, "cuda", normalize=True)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, add in PASS_SHAPES:
+        c = qs.Circuit(n)
+        add(c)
+        for _ in range(3):
+            qs.qsim_apply(st, c, stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(launches)]
+        for a, b in evs:
+            a.record(stream)
+            qs.qsim_apply(st, c, stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        out[name] = {"us_per_launch": round(1e3 * ms, 2), "gbs": round(2.0 * 8 * (1 << n) / (ms / 1e3) / 1e9, 1)}
+    del st
+    return out
+
+
+def sub_hhl27(args, ws, rank):
+    """The 27-qubit precision-form solve: complex64 (structured phase estimation, QFTs as
+    passes, fused dense gates on the tensor cores) and complex128 (FP64 SIMT), both through
+    hhl_run + hhl_readout; solves/s, latency, readout error against the classical A^-1 b; the
+    Fourier-pass kernel's roofline; the final states kept on the host for the comparison with
+    the full-size oracle (oracle_hhl27_compare, run after every GPU measurement)."""
+    import torch
+    import paper_2402_08136_gb300 as qs
+
+    p = synth.hhl27_problem()
+    tb = time.perf_counter()
+    h = qs.hhl_build(p["A"], p["b"], p["m"], structured=True, fft_qft=True)
+    build_ms = 1e3 * (time.perf_counter() - tb)
+    info = h.info()
+    n = info["n"]
+    xt = np.linalg.solve(p["A"], p["b"])
+    stream = torch.cuda.current_stream()
+    paths, keep = {}, {}
+    reps = {"c64": 20, "c128": 5}
+    for name, dt, max_k in (("c64", torch.complex64, 6), ("c128", torch.complex128, 2)):
+        tf = time.perf_counter()
+        circ = qs.qsim_fuse(h.as_circuit(), max_k)
+        fuse_ms = 1e3 * (time.perf_counter() - tf)
+        ci = circ.info()
+        st = torch.empty(1 << n, dtype=dt, device="cuda")
+        for _ in range(3):
+            qs.hhl_run(st, h, circ, stream)
+            qs.hhl_readout(st, h, stream)
+        torch.cuda.synchronize()
+        lat = []
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            l0 = qs.qsim_launch_count()
+            t0 = time.perf_counter()
+            for _ in range(reps[name]):
+                a = time.perf_counter()
+                qs.hhl_run(st, h, circ, stream)
+                r = qs.hhl_readout(st, h, stream)
+                lat.append(time.perf_counter() - a)
+            dt_s = time.perf_counter() - t0
+            nl = qs.qsim_launch_count() - l0
+        dt_s = max_over_ranks(ws, dt_s)
+        rel = float(np.linalg.norm(r["x"] - xt) / np.linalg.norm(xt))
+        paths[name] = {"solves_per_s": round(ws * reps[name] / dt_s, 2), "ms_per_solve": round(1e3 * dt_s / reps[name], 3),
+                       "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+                       "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+                       "readout_rel_err_vs_classical": rel, "p_success": r["p_success"],
+                       "leakage": r["leakage"], "max_k": max_k, "fused_ops": ci["n_gates"],
+                       "launches_per_solve": nl / reps[name], "host_fuse_ms": round(fuse_ms, 3),
+                       "solves_timed": reps[name], "clocks": clk.summary()}
+        keep[name] = (st.cpu().numpy(), r)
+        del st
+        torch.cuda.empty_cache()
+    passes = fourier_pass_roofline(qs, torch)
+    hbm, _, peak_kind = measured_peaks()
+    ach = float(np.mean([v["gbs"] for v in passes.values()]))
+    roof = {"bound": "hbm", "kernel": "dft_kernel", "achieved": round(ach, 1), "peak": hbm,
+            "peak_kind": peak_kind + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)", "unit": "GB/s",
+            "frac": round(ach / hbm, 4), "traffic": None,
+            "bytes_per_launch": 2.0 * 8 * (1 << n), "per_shape": passes,
+            "note": "mean of the three pass shapes of the solve, each timed alone on a 27-qubit complex64 state"}
+    oracle_p = dict(p)
+    oracle_p["m"] = 12
+    rec = {
+        "metric": "HHL solves/s (27 qubits, complex64 precision form)", "value": paths["c64"]["solves_per_s"],
+        "unit": "solves/s", "ms_per_solve": paths["c64"]["ms_per_solve"], "dtype": "c64",
+        "config": {"workload": "27-qubit HHL: 64x64 reduced Laplacian of a random 65-bus grid (98 lines), "
+                               "nb=6, m=20, structured phase estimation, QFTs as Fourier passes",
+                   "n_qubits": n, "nb": info["nb"], "m": info["m"], "host_build_ms": round(build_ms, 3),
+                   "l2": "state 1 GiB (c64) / 2 GiB (c128), larger than L2"},
+        "latency_ms": {"p50": paths["c64"]["p50_ms"], "p99": paths["c64"]["p99_ms"]},
+        "paths": paths, "roofline": roof,
+        "speedup_c64_vs_c128": round(paths["c64"]["solves_per_s"] / paths["c128"]["solves_per_s"], 2),
+        "gpu_launches": int(paths["c64"]["launches_per_solve"] * reps["c64"]),
+    }
+    if rank == 0:
+        rec["cpu_baseline"] = oracle_hhl_both(
+            [oracle_p], "one solve of the same 64x64 system with 12 instead of 20 clock qubits (19 "
+                        "qubits; the 27-qubit solve has 2^8 x the amplitudes)")
+    return rec, keep, p
+
+
+def oracle_hhl27_compare(rec, keep, p):
+    """The full-size FP64 oracle (plain gate-level HHL on 2^27 amplitudes, all host cores) and
+    the error of each kept device state against it: max |d amp|, fidelity, and the readout
+    relative error of the oracle itself against A^-1 b."""
+    from oracle import core as ocore
+    from oracle import hhl as ohhl
+    t0 = time.perf_counter()
+    ref = ohhl.solve(p["A"], p["b"], p["m"])
+    secs = time.perf_counter() - t0
+    xt = np.linalg.solve(p["A"], p["b"])
+    rec["oracle_full_size"] = {"seconds": round(secs, 1), "cores": ocore.num_threads(),
+                               "readout_rel_err_vs_classical": float(np.linalg.norm(ref["x"] - xt) / np.linalg.norm(xt)),
+                               "p_success": ref["P"]}
+    ps = ref["psi"]
+    nps = np.vdot(ps, ps).real
+    for name, (psi, r) in keep.items():
+        z = psi.astype(np.complex128)
+        fid = abs(np.vdot(ps, z)) ** 2 / (np.vdot(z, z).real * nps)
+        rec["paths"][name]["err_vs_oracle"] = {"max_abs_amp": float(np.max(np.abs(z - ps))), "fidelity": float(fid),
+                                               "p_success": abs(r["p_success"] - ref["P"])}
+    rec["error_note"] = ("both library paths eigendecompose A themselves, like the oracle: complex64 is held "
+                         "to 1e-5 per amplitude; complex128 here differs from the oracle by the eigensolvers' "
+                         "rounding times t 2^m (bound 2^m 2 pi 8 eps = 1.2e-8); with a shared spectral "
+                         "decomposition the complex128 path is held to 1e-12 (tests/test_gpu_hhl27.py)")
+
+
+def with_args(args, **kw):
+    a = argparse.Namespace(**vars(args))
+    for k, v in kw.items():
+        setattr(a, k, v)
+    return a
+
+
+def sub_records(args, ws, rank):
+    """Configs 1, 3, 4 and 5 as sub-records of the default line, each at a fixed, bounded size
+    (not scaled by --steps): the 7-qubit plain FP64 solve, the 27-qubit precision form, the
+    512-circuit batch and a serving stream at a rate the box sustains; the full-size 27-qubit
+    oracle last, after every GPU measurement."""
+    import torch
+    out = {}
+    t0 = time.perf_counter()
+    r7 = run_hhl(with_args(args, steps=2, warmup=3, structured=False, fft_qft=False, max_k=0), ws, rank, "hhl7")
+    if rank == 0:
+        r7["cpu_baseline"] = oracle_hhl_both([synth.hhl7_problem()] * 20, "20 solves of the 7-qubit problem")
+    out["hhl7"] = r7
+    r27, keep, p27 = sub_hhl27(args, ws, rank)
+    out["hhl27"] = r27
+    rb = run_batched(with_args(args, steps=20, warmup=3, count=512, structured=True, fft_qft=True), ws, rank)
+    if rank == 0:
+        probs = synth.batched_problems(seed=rank_seed(4, rank), count=512)[:16]
+        rb["cpu_baseline"] = oracle_hhl_both(probs, "the first 16 circuits of the 512-circuit batch")
+    out["batched512"] = rb
+    torch.cuda.empty_cache()
+    rs = run_serving(with_args(args, count=4000, rate=2000.0, max_n=22, pool_gb=150.0), ws, rank)
+    if rank == 0:
+        items = synth.serving_stream(seed=rank_seed(5, rank), count=200, max_n=16)
+        rs["cpu_baseline"] = oracle_hhl_both([it["problem"] for it in items[:16]],
+                                             "16 requests of the stream (qubits capped at 16)")
+    out["serving"] = rs
+    if rank == 0 and not args.no_oracle27:
+        oracle_hhl27_compare(r27, keep, p27)
+    del keep
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 # ----------------------------------------------------------------------- batched workload
@@ -699,8 +897,26 @@ def run_serving(args, ws, rank):
               for i, x, _ in ora]
     dp = [abs(results[i]["p_success"] - P) for i, _, P in ora]
     ns = np.array([it["n"] for it in items])
+    # algorithmic HBM bytes of the served stream: per request, its full-state circuit (structured
+    # phase estimation, QFTs as passes) in complex64; the live-width executor moves fewer
+    shape_bytes = {}
+    for it in items:
+        pp = it["problem"]
+        key = (pp["nb"], pp["m"])
+        if key not in shape_bytes:
+            hh = qs.hhl_build(pp["A"], pp["b"], pp["m"], structured=True, fft_qft=True)
+            shape_bytes[key] = qs.qsim_fuse(hh.as_circuit(), 4).info()["bytes_c64"]
+    tot_bytes = sum(shape_bytes[(it["problem"]["nb"], it["problem"]["m"])] for it in items)
+    hbm, _, peak_kind = measured_peaks()
+    gbs = tot_bytes / span / 1e9
+    roof = {"bound": "hbm", "kernel": "whole served stream (batched_kernel, dft_kernel, dense kernels)",
+            "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
+            "traffic": None, "peak_kind": peak_kind + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "note": "full-state algorithmic bytes of every request over the span from the first arrival "
+                    "to the last completion; arrival-limited when the offered rate is below capacity"}
     return {
         "metric": "HHL solves/s served (Poisson arrivals) with p50/p99 latency",
+        "roofline": roof,
         "value": round(sps, 1), "unit": "solves/s", "ms_per_step": round(1e3 * span, 1),
         "higher_is_better": True, "dtype": "c64",
         "config": {"workload": "serving: Poisson stream of N-1 contingency HHL solves, qubits "
@@ -741,6 +957,10 @@ def main():
     ap.add_argument("--fft-qft", action="store_true", help="QFTs as Fourier-transform passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-from-host-gen", action="store_true")
+    ap.add_argument("--no-subrecords", action="store_true",
+                    help="default workload only: skip the configs 1, 3, 4, 5 sub-records")
+    ap.add_argument("--no-oracle27", action="store_true",
+                    help="skip the full-size 27-qubit oracle comparison (about 2 minutes of host time)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -778,10 +998,19 @@ def main():
     ws, rank, local = dist_setup(args.gpus)
     if args.workload in ("gates", "gates-c128"):
         out = run_gates(args, ws, rank, "c64" if args.workload == "gates" else "c128")
+        if args.workload == "gates" and not args.no_subrecords:
+            out["workloads"] = sub_records(args, ws, rank)
     elif args.workload == "batched":
         out = run_batched(args, ws, rank)
     elif args.workload == "serving":
         out = run_serving(args, ws, rank)
+    elif args.workload == "hhl27":
+        out, keep, p27 = sub_hhl27(args, ws, rank)
+        if rank == 0 and not args.no_oracle27:
+            oracle_hhl27_compare(out, keep, p27)
+        out["ms_per_step"] = out.pop("ms_per_solve")
+        out["higher_is_better"] = True
+        out.pop("cpu_baseline", None)
     else:
         out = run_hhl(args, ws, rank, args.workload)
     line = {"metric": out.pop("metric"), "value": out.pop("value"), "unit": out.pop("unit"),

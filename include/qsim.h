@@ -228,6 +228,17 @@ int hhl_build_ex(const double *A, const double *b, int N, int n_clock, double t,
 int hhl_build_spectral_ex(const double *lambda, const double *V, const double *b, int N, int n_clock,
                           double t, double C, int flags, hhl_circuit **out);
 
+/* The host eigensolver behind hhl_build (Sec. III-A: U = exp(iAt) of the phase estimation is
+ * formed from A = V diag(lambda) V^H), exposed so that callers can check a system before
+ * building.  A: N x N complex (interleaved, row-major), Hermitian to 1e-12 * max|A_ij|.
+ * A real symmetric A takes Householder tridiagonalisation + implicit symmetric QR with
+ * Wilkinson shifts (max_iter = QR steps, <= 0: 60 N); a complex A cyclic Jacobi (max_iter =
+ * sweeps, <= 0: 100).  Outputs (caller-owned): lambda[N] ascending, V N x N complex
+ * (interleaved, row-major, column i = eigenvector of lambda[i]).  Errors: EINVAL (NULL, N out
+ * of 1..4096, not Hermitian, or "eigensolver did not converge" when the iteration cap ends
+ * before the matrix is diagonal to rounding; hhl_build reports the same error). */
+int qsim_hermitian_eig(const double *A, int N, int max_iter, double *lambda, double *V);
+
 void hhl_circuit_free(hhl_circuit *h);
 
 /* Borrowed view of the HHL gate list as a circuit (valid until hhl_circuit_free). */
@@ -416,10 +427,11 @@ void qsim_pool_destroy(qsim_pool *p);
  * the solution slice) is one fixed array inside the library, about 33 KB, which every GPU
  * that loads the library holds until the process exits; no device or host memory is
  * allocated per call.  Limit: 2^nb <= 1024 amplitudes (N <= 1024), otherwise QSIM_EINVAL.
- * The first call on a device looks up the array's device address, so make that first call
- * before any stream capture.  All calls share the one array: calls that overlap on the GPU
- * (other streams, other host threads) race on it and must be serialized by the caller.  The
- * call synchronizes `stream`.  Errors: EINVAL, ECUDA. */
+ * The first call on a device looks up the array's device address (once per device).  The
+ * call copies its results into host memory and synchronizes `stream`, so it cannot be
+ * captured into a CUDA graph.  All calls share the one array: calls that overlap on the GPU
+ * (other streams, other host threads) race on it and must be serialized by the caller.
+ * Errors: EINVAL (including nb > 10, before any device access), ECUDA. */
 int hhl_readout_noalloc(const void *state, int dtype, const hhl_circuit *h, void *stream,
                         double *x_out, double *x_state_out, hhl_readout_stats *stats);
 

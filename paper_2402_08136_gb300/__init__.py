@@ -29,5 +29,6 @@ from ._binding import (  # noqa: F401
     qsim_device_status,
     qsim_launch_count,
     qsim_fuse,
+    qsim_hermitian_eig,
     qsim_version,
 )

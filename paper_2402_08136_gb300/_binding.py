@@ -85,6 +85,7 @@ _SIGS = {
                       ctypes.POINTER(_VP)], ctypes.c_int),
     "hhl_build_spectral_ex": ([_DP, _DP, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                ctypes.c_double, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
+    "qsim_hermitian_eig": ([_DP, ctypes.c_int, ctypes.c_int, _DP, _DP], ctypes.c_int),
     "hhl_circuit_free": ([_VP], None),
     "hhl_as_circuit": ([_VP], _VP),
     "hhl_get_info": ([_VP, ctypes.POINTER(_HHLInfo)], ctypes.c_int),
@@ -341,6 +342,19 @@ def hhl_build_spectral(lam, V, b, n_clock: int = 0, t: float = 0.0, C: float = 0
         _check(library().hhl_build_spectral(la.ctypes.data_as(_DP), Vp, bp, N, int(n_clock),
                                             float(t), float(C), ctypes.byref(p)))
     return HHLCircuit(p)
+
+
+def qsim_hermitian_eig(A, max_iter: int = 0):
+    """The library's host eigensolver (the one hhl_build uses): (lambda ascending, V)."""
+    Aa, Ap = _cplx(A)
+    N = Aa.shape[0]
+    if Aa.shape != (N, N):
+        raise QsimError(-1, "A must be N x N")
+    lam = np.zeros(N, dtype=np.float64)
+    V = np.zeros((N, N), dtype=np.complex128)
+    _check(library().qsim_hermitian_eig(Ap, N, int(max_iter), lam.ctypes.data_as(_DP),
+                                        V.view(np.float64).ctypes.data_as(_DP)))
+    return lam, V
 
 
 def hhl_prepare_state(state, h: HHLCircuit, stream=None):

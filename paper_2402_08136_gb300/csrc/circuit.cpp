@@ -252,6 +252,30 @@ static qsim_circuit *fuse_impl(const qsim_circuit *in, int max_k) {
     return out.release();
 }
 
+namespace {
+// exp(i x c) for a double x and an integer c, |c| < 2^27, to a few ulps however large x c is.
+// The product is formed exactly as p + e (e = fma(x, c, -p)), reduced by 2 pi split into three
+// 26-bit heads and a double tail (Cody & Waite 1980: k P1, k P2, k P3 are exact for k < 2^27 and
+// p - k P1 is exact, so the reduced argument carries the rounding of a few additions near pi),
+// then cos and sin of the reduced argument.  At 20+ clock qubits the phase estimation's angles
+// lambda t c reach ~1e7 rad, where rounding the product x c to a double alone would move the
+// phase by ~1e-9.
+cd exp_i_times(double x, double c) {
+    constexpr double P1 = 0x1.921fb58p+2, P2 = -0x1.dde974p-25, P3 = 0x1.1a62630p-52,
+                     P4 = 0x1.8a2e03707344ap-79;  // P1 + P2 + P3 + P4 = 2 pi to ~1e-40
+    const double p = x * c;
+    const double e = std::fma(x, c, -p);
+    const double k = std::nearbyint(p * 0.15915494309189533577);  // p / (2 pi), to the nearest integer
+    if (!(std::fabs(k) < 134217728.0)) throw Error(QSIM_EINVAL, "phase argument out of range");
+    double r = (p - k * P1) - k * P2;
+    r = ((r - k * P3) - k * P4) + e;
+    return cd(std::cos(r), std::sin(r));
+}
+}  // namespace
+
+// Tables of the structured phase exp(i s x_d c), x_d = lambda_d t (one rounding, as
+// lambda_d * t), c = the clock value split as c_lo + 2^h c_hi: lo[c_lo][d] and hi[c_hi][d],
+// each the exponential of the exact product x_d c_lo or x_d (c_hi 2^h).
 void qpe_phase_tables(const Op &op, std::vector<cd> &lo, std::vector<cd> &hi, int &h) {
     const int nb = (int)op.targets.size(), m = (int)op.controls.size();
     const int D = 1 << nb;
@@ -259,11 +283,12 @@ void qpe_phase_tables(const Op &op, std::vector<cd> &lo, std::vector<cd> &hi, in
     const size_t nlo = (size_t)1 << h, nhi = (size_t)1 << (m - h);
     lo.resize(nlo * D);
     hi.resize(nhi * D);
+    std::vector<double> x(D);
+    for (int d = 0; d < D; d++) x[d] = op.sign * (op.theta[d] * op.tq);
     for (size_t c = 0; c < nlo; c++)
-        for (int d = 0; d < D; d++) lo[c * D + d] = std::polar(1.0, op.sign * op.theta[d] * (op.tq * (double)c));
-    const double th = std::ldexp(op.tq, h);  // t 2^h: exact power-of-two scaling
+        for (int d = 0; d < D; d++) lo[c * D + d] = exp_i_times(x[d], (double)c);
     for (size_t c = 0; c < nhi; c++)
-        for (int d = 0; d < D; d++) hi[c * D + d] = std::polar(1.0, op.sign * op.theta[d] * (th * (double)c));
+        for (int d = 0; d < D; d++) hi[c * D + d] = exp_i_times(x[d], std::ldexp((double)c, h));
 }
 
 void circuit_info(const qsim_circuit *c, qsim_circuit_info *o) {

@@ -194,8 +194,12 @@ bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
              const Op *qop = nullptr, const void *qlo = nullptr, const void *qhi = nullptr, int qmode = 0,
              const Op *inv = nullptr);
 // linalg.cpp
-void hermitian_eig(int N, const std::vector<cd> &A, std::vector<double> &lam, std::vector<cd> &V);
-void symmetric_eig_real(int N, const std::vector<double> &A, std::vector<double> &lam, std::vector<double> &V);
+// Both throw Error(QSIM_EINVAL, "eigensolver did not converge ...") when the iteration cap
+// (<= 0: 100 Jacobi sweeps / 60 N implicit QR steps) ends before the matrix is diagonal.
+void hermitian_eig(int N, const std::vector<cd> &A, std::vector<double> &lam, std::vector<cd> &V,
+                   int max_sweeps = 0);
+void symmetric_eig_real(int N, const std::vector<double> &A, std::vector<double> &lam, std::vector<double> &V,
+                        int max_iter = 0);
 // host tables of the structured phase-estimation operator: lo[c * D + d] = exp(i s lam_d t c)
 // for c < 2^h, hi[c * D + d] = exp(i s lam_d t c 2^h) for c < 2^(m-h), h = (m + 1) / 2
 void qpe_phase_tables(const Op &op, std::vector<cd> &lo, std::vector<cd> &hi, int &h);

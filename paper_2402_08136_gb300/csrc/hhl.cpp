@@ -363,6 +363,41 @@ int hhl_build_ex(const double *A, const double *b, int N, int n_clock, double t,
     });
 }
 
+int qsim_hermitian_eig(const double *A, int N, int max_iter, double *lambda, double *V) {
+    return guarded([&] {
+        QSIM_REQUIRE(A != nullptr && lambda != nullptr && V != nullptr, "NULL argument");
+        QSIM_REQUIRE(N >= 1 && N <= 4096, "N must be in 1..4096");
+        std::vector<cd> Am = read_complex(A, (size_t)N * N);
+        double amax = 0.0;
+        for (const cd &z : Am) amax = std::max(amax, std::abs(z));
+        const double tol = 1e-12 * std::max(1.0, amax);
+        for (int r = 0; r < N; r++)
+            for (int c = 0; c <= r; c++)
+                QSIM_REQUIRE(std::abs(Am[(size_t)r * N + c] - std::conj(Am[(size_t)c * N + r])) <= tol,
+                             "A is not Hermitian");
+        bool real = true;
+        for (const cd &z : Am) real &= z.imag() == 0.0;
+        std::vector<double> lam;
+        std::vector<cd> Vc;
+        if (real) {  // the same solver and symmetrisation as hhl_build
+            std::vector<double> Ar((size_t)N * N), Vr;
+            for (int r = 0; r < N; r++)
+                for (int c = 0; c < N; c++)
+                    Ar[(size_t)r * N + c] = 0.5 * (Am[(size_t)r * N + c].real() + Am[(size_t)c * N + r].real());
+            symmetric_eig_real(N, Ar, lam, Vr, max_iter);
+            Vc.assign(Vr.begin(), Vr.end());
+        } else {
+            for (int r = 0; r < N; r++) Am[(size_t)r * N + r] = Am[(size_t)r * N + r].real();
+            hermitian_eig(N, Am, lam, Vc, max_iter);
+        }
+        for (int i = 0; i < N; i++) lambda[i] = lam[i];
+        for (size_t i = 0; i < (size_t)N * N; i++) {
+            V[2 * i] = Vc[i].real();
+            V[2 * i + 1] = Vc[i].imag();
+        }
+    });
+}
+
 int hhl_build(const double *A, const double *b, int N, int n_clock, double t, double C, hhl_circuit **out) {
     return hhl_build_ex(A, b, N, n_clock, t, C, 0, out);
 }

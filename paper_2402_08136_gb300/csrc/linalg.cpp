@@ -11,7 +11,8 @@
 namespace qsim {
 
 void hermitian_eig(int N, const std::vector<cd> &Ain, std::vector<double> &lam,
-                   std::vector<cd> &V) {
+                   std::vector<cd> &V, int max_sweeps) {
+    if (max_sweeps <= 0) max_sweeps = 100;
     std::vector<cd> A(Ain);
     V.assign((size_t)N * N, cd(0.0, 0.0));
     for (int i = 0; i < N; i++) V[(size_t)i * N + i] = 1.0;
@@ -19,11 +20,14 @@ void hermitian_eig(int N, const std::vector<cd> &Ain, std::vector<double> &lam,
     double fro = 0.0;
     for (const cd &z : A) fro += std::norm(z);
     fro = std::sqrt(fro);
-    for (int sweep = 0; sweep < 100; sweep++) {
+    auto off_norm = [&] {
         double off = 0.0;
         for (int p = 0; p < N; p++)
             for (int q = p + 1; q < N; q++) off += std::norm(a(p, q));
-        off = std::sqrt(2.0 * off);
+        return std::sqrt(2.0 * off);
+    };
+    for (int sweep = 0; sweep < max_sweeps; sweep++) {
+        const double off = off_norm();
         if (off <= 1e-17 * fro || off == 0.0) break;
         for (int p = 0; p < N - 1; p++) {
             for (int q = p + 1; q < N; q++) {
@@ -59,6 +63,16 @@ void hermitian_eig(int N, const std::vector<cd> &Ain, std::vector<double> &lam,
             }
         }
     }
+    // The sweeps aim below rounding level; what remains must at least be rounding noise
+    // (a few ulps of ||A||_F per entry), otherwise the diagonal is not the spectrum.
+    {
+        const double off = off_norm();
+        const double accept = std::max(1e-14, 4.0 * N * 2.220446049250313e-16) * fro;
+        if (!(off <= accept))
+            throw Error(QSIM_EINVAL, "eigensolver did not converge (cyclic Jacobi: off-diagonal norm " +
+                                         std::to_string(off) + " after " + std::to_string(max_sweeps) +
+                                         " sweeps)");
+    }
     // sort ascending
     std::vector<int> idx(N);
     for (int i = 0; i < N; i++) idx[i] = i;
@@ -83,7 +97,8 @@ void hermitian_eig(int N, const std::vector<cd> &Ain, std::vector<double> &lam,
 namespace qsim {
 
 void symmetric_eig_real(int N, const std::vector<double> &Ain, std::vector<double> &lam,
-                        std::vector<double> &V) {
+                        std::vector<double> &V, int max_iter) {
+    if (max_iter <= 0) max_iter = 60 * N;
     std::vector<double> A(Ain);
     auto a = [&](int i, int j) -> double & { return A[(size_t)i * N + j]; };
     V.assign((size_t)N * N, 0.0);
@@ -131,7 +146,7 @@ void symmetric_eig_real(int N, const std::vector<double> &Ain, std::vector<doubl
     // 2. implicit symmetric QR with Wilkinson shift on unreduced blocks [lo, hi]
     const double eps = 2.220446049250313e-16;
     int hi = N - 1, iter = 0;
-    while (hi > 0 && iter < 60 * N) {
+    while (hi > 0 && iter < max_iter) {
         // deflate negligible off-diagonals
         for (int i = 0; i < hi; i++)
             if (std::fabs(e[i]) <= eps * (std::fabs(d[i]) + std::fabs(d[i + 1]))) e[i] = 0.0;
@@ -179,6 +194,13 @@ void symmetric_eig_real(int N, const std::vector<double> &Ain, std::vector<doubl
             }
         }
     }
+    // converged = every off-diagonal deflated; otherwise d is not the spectrum
+    for (int i = 0; i < hi; i++)
+        if (std::fabs(e[i]) <= eps * (std::fabs(d[i]) + std::fabs(d[i + 1]))) e[i] = 0.0;
+    while (hi > 0 && e[hi - 1] == 0.0) hi--;
+    if (hi > 0)
+        throw Error(QSIM_EINVAL, "eigensolver did not converge (implicit symmetric QR: " + std::to_string(max_iter) +
+                                     " steps, block ending at row " + std::to_string(hi) + " not deflated)");
     std::vector<int> idx(N);
     for (int i = 0; i < N; i++) idx[i] = i;
     std::sort(idx.begin(), idx.end(), [&](int x0, int y0) { return d[x0] < d[y0]; });

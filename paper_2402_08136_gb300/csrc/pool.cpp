@@ -412,7 +412,12 @@ void scheduler_loop(qsim_pool *p) {
                 else launch_small(p, s, group);
                 progress = true;
             } catch (const Error &e) {
-                // back to the queue if the arena was too full for the tables, fail otherwise
+                // back to the queue if the arena was too full for the tables, fail otherwise.
+                // Kernels or copies may already be queued on the slot's stream (preparation, an
+                // upload, part of the circuit): its memory goes back to the arena only once they
+                // are finished, or the next request on another stream could be handed blocks that
+                // are still being read and written.
+                if (cudaStreamSynchronize(s.st) != cudaSuccess) cudaGetLastError();
                 std::vector<PoolReq *> rs = large ? std::vector<PoolReq *>{large} : group;
                 release_blocks(p, s.blocks);
                 if (s.batch) {

@@ -275,3 +275,50 @@ def test_run_and_solve_argument_checks(qs):
     assert L.hhl_batch_results(None, None, None, None) != 0
     n0 = qs.qsim_launch_count()
     assert isinstance(n0, int) and n0 >= 0
+
+
+def test_host_eigensolver_matches_numpy(qs):
+    """The eigensolver behind hhl_build: eigenvalues equal numpy's eigh, V is unitary and
+    A V = V diag(lambda), for a real symmetric (power-flow) and a complex Hermitian matrix."""
+    rng = np.random.default_rng(3)
+    A_real, _ = synth.contingency_system(rng, 33)
+    G = rng.standard_normal((24, 24)) + 1j * rng.standard_normal((24, 24))
+    A_cplx = G + G.conj().T
+    for A in (A_real, A_cplx):
+        lam, V = qs.qsim_hermitian_eig(A)
+        ref = np.linalg.eigvalsh(A)
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(lam - ref)) <= 1e-13 * scale
+        assert np.max(np.abs(V.conj().T @ V - np.eye(len(lam)))) <= 1e-13
+        assert np.max(np.abs(A @ V - V * lam)) <= 1e-12 * scale
+
+
+def test_eigensolver_reports_non_convergence(qs):
+    """A capped iteration that stops before the matrix is diagonal is an error (EINVAL), not
+    an unconverged V handed on to the circuit."""
+    rng = np.random.default_rng(5)
+    A_real, _ = synth.contingency_system(rng, 33)   # 32 x 32 real symmetric
+    G = rng.standard_normal((32, 32)) + 1j * rng.standard_normal((32, 32))
+    for A in (A_real, G + G.conj().T):
+        with pytest.raises(qs.QsimError) as e:
+            qs.qsim_hermitian_eig(A, max_iter=1)
+        assert e.value.code == -1 and "did not converge" in str(e.value)
+        lam, _ = qs.qsim_hermitian_eig(A)          # the default cap converges
+        assert np.all(np.isfinite(lam))
+
+
+def test_noalloc_readout_rejects_a_slice_beyond_its_scratch(qs):
+    """nb = 11 (2^11 amplitudes in the solution slice) is beyond the allocation-free readout's
+    fixed scratch: QSIM_EINVAL before any device access (the state pointer is never used)."""
+    from paper_2402_08136_gb300._binding import _DP, _VP, _ReadoutStats, library
+    f = library().hhl_readout_noalloc
+    f.argtypes = [_VP, ctypes.c_int, _VP, _VP, _DP, _DP, ctypes.POINTER(_ReadoutStats)]
+    f.restype = ctypes.c_int
+    N = 1025
+    h = qs.hhl_build_spectral(np.linspace(1.0, 2.0, N), np.eye(N), np.ones(N), 1, structured=True)
+    assert h.info()["nb"] == 11
+    x = np.zeros(N, dtype=np.complex128)
+    rc = f(ctypes.c_void_p(256), qs.QSIM_C128, h.ptr, None, x.view(np.float64).ctypes.data_as(_DP),
+           None, None)
+    assert rc == -1
+    assert "2^10" in library().qsim_last_error().decode()

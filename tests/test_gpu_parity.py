@@ -13,6 +13,7 @@ import pytest
 import torch
 
 import synth
+from hhl_bounds import cond_tol, prob_bound, readout_bounds
 from oracle import core as ocore
 from oracle import hhl as ohhl
 
@@ -310,18 +311,24 @@ def run_product_hhl(qs, h, dtype, max_k):
 
 
 def compare_hhl(st, r, ref, dtype, tol_state):
+    """State element by element within tol_state (and fidelity for complex64); the readout
+    within the bounds that the state bound implies (tests/hhl_bounds.py)."""
     out = st.cpu().numpy().astype(np.complex128)
     err = np.max(np.abs(out - ref["psi"]))
     assert err <= tol_state, "state max|d| %.3e > %.1e" % (err, tol_state)
     if dtype == torch.complex64:
         f = abs(np.vdot(ref["psi"], out)) ** 2 / np.vdot(out, out).real
         assert f >= 1 - 1e-6
-    tol_r = max(tol_state, 1e-12) * 10
-    assert abs(r["p_success"] - ref["P"]) <= tol_r
-    assert abs(r["p_clock0"] - ref["P0"]) <= tol_r
-    assert abs(r["norm2"] - ref["norm2"]) <= tol_r
-    rel = 1.0 if ref["P0"] < 1e-300 else 1.0 / math.sqrt(ref["P0"])
-    assert np.max(np.abs(r["x_state"] - ref["x_state"])) <= tol_r * rel * 10
+    h = ref["circuit"]
+    xs_b = readout_bounds(ref, h["nb"], h["m"], tol_state, h["C"], h["bnorm"], 1 << h["nb"])
+    assert abs(r["p_success"] - ref["P"]) <= xs_b["P"]
+    assert abs(r["p_clock0"] - ref["P0"]) <= xs_b["P0"]
+    assert abs(r["norm2"] - ref["norm2"]) <= prob_bound(ref["psi"], tol_state)
+    assert np.all(np.abs(r["x_state"] - ref["x_state"]) <= xs_b["x_state"])
+    N = len(ref["x"])
+    off = len(ref["x_eff"]) - N if "x_eff" in ref else 0
+    x_b = readout_bounds(ref, h["nb"], h["m"], tol_state, h["C"], h["bnorm"], N, off)
+    assert np.all(np.abs(r["x"] - ref["x"]) <= x_b["x"])
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -376,10 +383,6 @@ def test_hhl_structured_spectral_large_clock(qs, dtype):
     ref = _oracle_spectral(lam, V, b, m, t, 0.4)
     st, r = run_product_hhl(qs, h, dtype, 4)
     compare_hhl(st, r, ref, dtype, 1e-12 if dtype == torch.complex128 else TOL[dtype])
-
-
-def cond_tol(m):
-    return max(1e-12, 2.0 ** m * 2 * math.pi * 8 * EPS)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -703,8 +706,11 @@ def test_gauss_seidel_dilated_offgrid(qs, dtype):
     h = qs.hhl_build(A, b, m, gauss_seidel=True, structured=True)
     ref = ohhl.solve_general(A, b, m, gauss_seidel=True)
     st, r = run_product_hhl(qs, h, dtype, 3)
-    compare_hhl(st, r, ref, dtype, cond_tol(m) * 100 if dtype == torch.complex128 else TOL[dtype])
-    assert np.max(np.abs(r["x"] - ref["x"])) <= 1e-4 * np.linalg.norm(ref["x"])
+    # Both sides form A' = M^-1 A with their own triangular solve: the results differ by up to
+    # cond(M) eps relative (forward error of a triangular solve), which the dilation's
+    # eigenvalues inherit; the phase estimation amplifies that like any eigenvalue rounding.
+    condM = np.linalg.cond(np.tril(A))
+    compare_hhl(st, r, ref, dtype, cond_tol(m) * max(1.0, condM) if dtype == torch.complex128 else TOL[dtype])
 
 
 def test_dilated_batch_readout_offset(qs):

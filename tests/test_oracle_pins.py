@@ -435,3 +435,88 @@ def test_planted_twiddle_mistakes_are_caught():
     for bad in (wrong_denominator, wrong_side, wrong_sign):
         with pytest.raises(AssertionError):
             _check_dft_factorisation(6, [3, 3], bad)
+
+
+# ------------------------------------------------------------ default evolution time and C
+def _clock_distribution(h, b_vec):
+    """Run the phase-estimation part of the oracle's gate list (everything before the
+    rotation) from |0>|b_vec> and return the probability of each clock value."""
+    h = dict(h)
+    bp = np.zeros(1 << h["nb"], dtype=np.complex128)
+    bp[: len(b_vec)] = b_vec / np.linalg.norm(b_vec)
+    h["b_pad"] = bp
+    psi = hhl.initial_state(h)
+    for g in h["gates"]:
+        if g[0] == "ucry":
+            break
+        core.apply_gate(psi, g[1], g[2], g[3], g[4])
+    nb, m = h["nb"], h["m"]
+    return (np.abs(psi.reshape(-1, 1 << nb)) ** 2).sum(axis=1)[: 1 << m]
+
+
+def _default_t_problems():
+    """An off-grid power-flow matrix (positive definite) and an indefinite one."""
+    A, b = synth.contingency_system(np.random.default_rng(21), 9)     # 8 x 8 SPD, generic spectrum
+    rng = np.random.default_rng(22)
+    V = np.linalg.qr(rng.standard_normal((6, 6)))[0]
+    lam = np.array([-7.3, -2.2, 0.9, 1.7, 4.4, 9.1])
+    Ai = (V * lam) @ V.T
+    return [(A, b, False), (0.5 * (Ai + Ai.T), rng.standard_normal(6), True)]
+
+
+@pytest.mark.parametrize("m", [5, 7])
+def test_default_t_puts_the_largest_eigenvalue_on_the_top_clock_value(m):
+    """With the default evolution time, phase estimation of the eigenvector of the largest
+    |lambda| lands exactly on the top clock value: 2^m - 1 for a positive definite A, and
+    +-(2^(m-1) - 1) in two's complement for an indefinite A (the sign qubit of Sec. III-B).
+    The spectrum is off the grid, so only the extreme eigenvector is exact."""
+    for A, b, signed in _default_t_problems():
+        h = hhl.build(A, b, m)
+        assert h["signed"] == signed
+        w, V = np.linalg.eigh(A)
+        i = int(np.argmax(np.abs(w)))
+        M = 1 << m
+        if signed:
+            want = (M // 2 - 1) if w[i] > 0 else M - (M // 2 - 1)
+        else:
+            want = M - 1
+        prob = _clock_distribution(h, V[:, i])
+        assert abs(prob[want] - 1.0) < 1e-12
+        # an off-grid eigenvalue spreads over several clock values
+        j = int(np.argmin(np.abs(w)))
+        assert _clock_distribution(h, V[:, j]).max() < 1.0 - 1e-6
+
+
+def test_default_c_is_the_largest_grid_value_below_lambda_min_and_hhl_is_exact_on_it():
+    """Default C: a clock grid value (C / step an integer, with the grid step fixed by where the
+    largest eigenvalue lands) not above min|lambda|, and the next grid value is above it.  With
+    b the (on-grid) top eigenvector, HHL is exact even though A is off the grid: P = (C /
+    lambda_max)^2, no leakage, x = A^-1 b."""
+    m = 6
+    for A, _, signed in _default_t_problems():
+        h = hhl.build(A, np.ones(A.shape[0]), m)
+        w, V = np.linalg.eigh(A)
+        amin, amax = np.abs(w).min(), np.abs(w).max()
+        top = (2 ** (m - 1) - 1) if signed else (2 ** m - 1)
+        step = amax / top                                 # where the largest eigenvalue lands
+        C = h["C"]
+        q = C / step
+        assert abs(q - round(q)) < 1e-9 and round(q) >= 1
+        assert C <= amin * (1 + 1e-12) and C + step > amin
+        i = int(np.argmax(np.abs(w)))
+        bi = V[:, i]
+        r = hhl.solve(A, bi, m)
+        assert abs(r["P"] - (C / w[i]) ** 2) < 1e-12
+        assert abs(r["leakage"]) < 1e-13
+        assert np.max(np.abs(r["x"] - bi / w[i])) < 1e-11 / amin
+
+
+def test_planted_off_by_one_evolution_time_is_caught():
+    """t = 2 pi 2^m / (2^m lambda_max) (top = 2^m instead of 2^m - 1) wraps the largest
+    eigenvalue around the clock: the pin above sees it."""
+    m = 5
+    A, b, _ = _default_t_problems()[0]
+    w, V = np.linalg.eigh(A)
+    M = 1 << m
+    h = hhl.build(A, b, m, t=2 * math.pi * M / (M * w[-1]))
+    assert _clock_distribution(h, V[:, -1])[M - 1] < 0.5
