@@ -160,11 +160,17 @@ TRAFFIC = {
 FP64_PEAK_TFLOPS = 1.25
 
 
-def kernel_family(dtype_name: str, k: int) -> str:
-    """Which kernel runs a dense k-qubit gate (mirrors the library's dispatch)."""
-    if dtype_name == "c64" and 4 <= k <= 6 and os.environ.get("QSIM_DENSE_TC", "1") != "0":
-        return "dense_tc_kernel"
-    return "dense_pipe_kernel"
+FAMILY_KERNEL = {"dense_simt": "dense_pipe_kernel", "dense_tc": "dense_tc_kernel",
+                 "fourier": "dft_kernel", "fourier_tma": "dft_tma_kernel"}
+
+
+def launched_family(qs, fn):
+    """Run fn() and return the kernel family the library reports for the launch it made."""
+    before = qs.qsim_launch_counts()
+    fn()
+    after = qs.qsim_launch_counts()
+    fams = [f for f in after if after[f] != before[f]]
+    return FAMILY_KERNEL.get(fams[0], fams[0]) if len(fams) == 1 else "+".join(sorted(fams))
 
 
 # ------------------------------------------------------------------------ oracle baseline
@@ -261,8 +267,14 @@ def run_gates(args, ws, rank, dtype_name):
     gates = synth.gate_microbench_list(seed, n, per_k=args.per_k)
     circs = [qs.Circuit(n).add_gate(t, U) for t, U in gates]
     ks = [len(t) for t, _ in gates]
-    st = synth.gaussian_state_torch(seed, n, dtype, "cuda", normalize=True)
     stream = torch.cuda.current_stream()
+    # the library's autotuner picks its kernel variants on this state buffer first (it
+    # overwrites the contents), then the benchmark's input is written
+    st = torch.empty(1 << n, dtype=dtype, device="cuda")
+    t0 = time.perf_counter()
+    tune = qs.qsim_autotune(st, stream)
+    tune["seconds"] = round(time.perf_counter() - t0, 2)
+    st.copy_(synth.gaussian_state_torch(seed, n, dtype, "cuda", normalize=True))
     bytes_per_gate = 2.0 * S * (1 << n)
     step_bytes = bytes_per_gate * len(gates)
 
@@ -274,6 +286,8 @@ def run_gates(args, ws, rank, dtype_name):
             if evs is not None:
                 evs[i][1].record(stream)
 
+    # which kernel the library launches for each gate (its per-family launch counters)
+    fam_of = [launched_family(qs, lambda c=c: qs.qsim_apply(st, c, stream)) for c in circs]
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -303,11 +317,11 @@ def run_gates(args, ws, rank, dtype_name):
         d = durs[:, sel].mean()
         per_k[str(k)] = {"ms_per_gate": round(float(d), 4),
                          "gbs": round(bytes_per_gate / (d / 1e3) / 1e9, 1),
-                         "kernel": kernel_family(dtype_name, k)}
+                         "kernel": "/".join(sorted({fam_of[i] for i in sel}))}
     # per kernel family: launches, time, share of the timed gate time
     fams = {}
     for i, k in enumerate(ks):
-        f = kernel_family(dtype_name, k)
+        f = fam_of[i]
         e = fams.setdefault(f, {"launches": 0, "ms_total": 0.0})
         e["launches"] += args.steps
         e["ms_total"] += float(durs[:, i].sum())
@@ -331,7 +345,7 @@ def run_gates(args, ws, rank, dtype_name):
                     "bytes_per_launch": bytes_per_gate}
     else:
         # complex128: FP64 FMA bound (a dense k-qubit gate is 8 * 2^k real flops per amplitude)
-        sel = [i for i, k in enumerate(ks) if kernel_family(dtype_name, k) == dom]
+        sel = [i for i, k in enumerate(ks) if fam_of[i] == dom]
         fl = sum(8.0 * (2 ** ks[i]) * (1 << n) for i in sel) * args.steps
         tf = fl / (fams[dom]["ms_total"] / 1e3) / 1e12
         roofline = {"bound": "alu", "kernel": dom, "achieved": round(tf, 4),
@@ -376,7 +390,7 @@ def run_gates(args, ws, rank, dtype_name):
                    "n_qubits": n, "gates_per_step": len(gates), "state_bytes": S << n,
                    "l2": "inputs larger than L2 (state %d GiB vs 129 MB L2)" % ((S << n) >> 30),
                    "seed": seed},
-        "per_k": per_k, "kernels": fams, "roofline": roofline,
+        "per_k": per_k, "kernels": fams, "roofline": roofline, "autotune": tune,
         "e2e": {"value": round(e2e_val, 1), "unit": "GB/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "gpu_launches": launches,  # counted by the library's launch sites
@@ -548,12 +562,15 @@ def sub_hhl27(args, ws, rank):
     stream = torch.cuda.current_stream()
     paths, keep = {}, {}
     reps = {"c64": 20, "c128": 5}
+    tune = {}
     for name, dt, max_k in (("c64", torch.complex64, 6), ("c128", torch.complex128, 2)):
         tf = time.perf_counter()
         circ = qs.qsim_fuse(h.as_circuit(), max_k)
         fuse_ms = 1e3 * (time.perf_counter() - tf)
         ci = circ.info()
         st = torch.empty(1 << n, dtype=dt, device="cuda")
+        if not qs.qsim_tune_get(qs.QSIM_C64 if name == "c64" else qs.QSIM_C128, qs.QSIM_TUNE_TUNED):
+            tune[name] = qs.qsim_autotune(st, stream)
         for _ in range(3):
             qs.hhl_run(st, h, circ, stream)
             qs.hhl_readout(st, h, stream)
@@ -599,7 +616,7 @@ def sub_hhl27(args, ws, rank):
                    "n_qubits": n, "nb": info["nb"], "m": info["m"], "host_build_ms": round(build_ms, 3),
                    "l2": "state 1 GiB (c64) / 2 GiB (c128), larger than L2"},
         "latency_ms": {"p50": paths["c64"]["p50_ms"], "p99": paths["c64"]["p99_ms"]},
-        "paths": paths, "roofline": roof,
+        "paths": paths, "roofline": roof, "tuning": qs.qsim_tune_table(), "autotune": tune,
         "speedup_c64_vs_c128": round(paths["c64"]["solves_per_s"] / paths["c128"]["solves_per_s"], 2),
         "gpu_launches": int(paths["c64"]["launches_per_solve"] * reps["c64"]),
     }

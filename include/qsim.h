@@ -132,7 +132,8 @@ int qsim_circuit_get_info(const qsim_circuit *c, qsim_circuit_info *out);
  * ======================================================================================= */
 
 /* Fuse `in` into a new circuit whose dense operations act on at most max_k qubits
- * (1 <= max_k <= 6; 0 picks the width tuned for this GPU and dtype QSIM_C64).  Uncontrolled
+ * (1 <= max_k <= 6; 0 takes the complex64 entry QSIM_TUNE_FUSE_WIDTH of the kernel-choice table,
+ * 4 until qsim_autotune has measured it).  Uncontrolled
  * gates are merged greedily in circuit order (a gate joins the latest block that touches any
  * of its qubits when the union stays within max_k, which for max_k = 2 realises the paper's
  * four strategies: 1q+1q, 1q into 2q before and after, 2q+2q); each product is multiplied
@@ -160,6 +161,64 @@ int qsim_device_status(unsigned *flags, int clear);
 /* Number of kernels this library has launched in this process (every launch site counts; the
  * replay of a CUDA graph that captured library calls does not).  Never fails. */
 unsigned long long qsim_launch_count(void);
+
+/* The same count split by kernel family (so a caller can tell which kernel ran an operation):
+ * counts[i] for family i (QSIM_KERNEL_*), i < n; entries beyond the families are 0. */
+#define QSIM_KERNEL_DENSE_SIMT 0   /* dense gates, SIMT (dense_pipe_kernel, dense_tile_kernel)      */
+#define QSIM_KERNEL_DENSE_TC 1     /* dense gates on the tensor cores (complex64)                   */
+#define QSIM_KERNEL_FOURIER 2      /* Fourier / Walsh-Hadamard passes, thread loads                 */
+#define QSIM_KERNEL_FOURIER_TMA 3  /* Fourier / Walsh-Hadamard passes, bulk-copy (TMA) tiles       */
+#define QSIM_KERNEL_EXPAND 4       /* write-only broadcast of a pass on an unwritten field          */
+#define QSIM_KERNEL_ELEMENTWISE 5  /* phase, diagonal, swap, UCRY, structured phase, inversion     */
+#define QSIM_KERNEL_BATCHED 6      /* persistent batched executor                                   */
+#define QSIM_KERNEL_READOUT 7      /* readout reductions                                            */
+#define QSIM_KERNEL_PREP 8         /* state preparation                                             */
+#define QSIM_KERNEL_FAMILIES 9
+int qsim_launch_counts(unsigned long long *counts, int n);
+
+/* ======================================================================================= *
+ * Kernel-choice table and autotuner                                                        *
+ * ======================================================================================= */
+
+/* Every choice the library makes between equivalent kernels or launch shapes reads one table
+ * per state dtype (the paper has no counterpart; the benchmark spec asks for fusion width and tile
+ * shapes chosen by an autotuner).  Keys: */
+#define QSIM_TUNE_DFT_TMA 0      /* Fourier / Walsh-Hadamard passes on complex64 with a contiguous
+                                    field of 9-10 qubits above qubit 2: 1 = tile moved by the
+                                    tensor memory accelerator (bulk copies), 0 = thread loads     */
+#define QSIM_TUNE_DFT_LANES 1    /* thread-load pass kernel: lane qubits per tile (0 = 128-byte
+                                    runs: 4 for complex64, 3 for complex128)                       */
+#define QSIM_TUNE_DFT_PREFETCH 2 /* thread-load pass kernel: L2 prefetch distance in tiles (0 off) */
+#define QSIM_TUNE_DENSE_TC 3     /* complex64 dense gates: bit k set = gates of k targets (4..6)
+                                    on the tensor cores; bit 7 = real 7-target gates (and real
+                                    6-target gates on qubits 0 and 1) on the tensor cores          */
+#define QSIM_TUNE_FUSE_WIDTH 4   /* width qsim_fuse uses when called with max_k = 0 (the
+                                    complex64 entry; 1..6)                                          */
+#define QSIM_TUNE_TUNED 5        /* 1 once qsim_autotune has written this dtype's entries        */
+#define QSIM_TUNE_COUNT 6
+
+/* Read / write one entry for dtype QSIM_C64 or QSIM_C128.  Writes take effect for launches
+ * enqueued afterwards.  Errors: EINVAL (unknown key, value out of range). */
+int qsim_tune_get(int dtype, int key, int *value);
+int qsim_tune_set(int dtype, int key, int value);
+/* Every entry of both dtypes back to its default. */
+int qsim_tune_reset(void);
+
+typedef struct {
+    int n_qubits;           /* state size the measurements were taken on                       */
+    int values[QSIM_TUNE_COUNT]; /* the table after tuning                                      */
+    double dft_ms;          /* fastest Fourier-pass variant, ms per pass                        */
+    double dense_ms[3];     /* complex64 dense gates of 4, 5, 6 targets: faster kernel, ms/gate */
+    double fuse_ms[5];      /* fused gate-level test circuit at widths 2..6, ms per application */
+} qsim_tune_report;
+
+/* Time the alternatives on `state` (device, 2^n_qubits amplitudes of `dtype`, 20 <= n <= 34;
+ * its contents are overwritten) with CUDA events on `stream` and write the fastest into the
+ * table: the Fourier-pass kernel and its lane count and prefetch distance (three 10-qubit
+ * passes), tensor cores or SIMT for complex64 dense gates of 4, 5 and 6 targets (three Haar
+ * gates each), and the fusion width (a gate-level circuit of 48 random 1- and 2-qubit gates
+ * fused at widths 2..6).  Synchronizes `stream`.  out may be NULL.  Errors: EINVAL, ECUDA. */
+int qsim_autotune(void *state, int n_qubits, int dtype, void *stream, qsim_tune_report *out);
 
 /* ======================================================================================= *
  * HHL (Sec. III-A procedure, Fig. 5 circuit, Sec. III-B resources)                         *

@@ -28,7 +28,19 @@ from ._binding import (  # noqa: F401
     qsim_apply,
     qsim_device_status,
     qsim_launch_count,
+    qsim_launch_counts,
     qsim_fuse,
     qsim_hermitian_eig,
+    qsim_autotune,
+    qsim_tune_get,
+    qsim_tune_reset,
+    qsim_tune_set,
+    qsim_tune_table,
+    QSIM_TUNE_DFT_TMA,
+    QSIM_TUNE_DFT_LANES,
+    QSIM_TUNE_DFT_PREFETCH,
+    QSIM_TUNE_DENSE_TC,
+    QSIM_TUNE_FUSE_WIDTH,
+    QSIM_TUNE_TUNED,
     qsim_version,
 )

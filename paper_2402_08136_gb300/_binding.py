@@ -59,6 +59,22 @@ class _PoolInfo(ctypes.Structure):
                 ("batches_launched", ctypes.c_longlong), ("singles_launched", ctypes.c_longlong)]
 
 
+QSIM_TUNE_DFT_TMA = 0
+QSIM_TUNE_DFT_LANES = 1
+QSIM_TUNE_DFT_PREFETCH = 2
+QSIM_TUNE_DENSE_TC = 3
+QSIM_TUNE_FUSE_WIDTH = 4
+QSIM_TUNE_TUNED = 5
+QSIM_TUNE_COUNT = 6
+TUNE_NAMES = ("dft_tma", "dft_lanes", "dft_prefetch", "dense_tc", "fuse_width", "tuned")
+
+
+class _TuneReport(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int), ("values", ctypes.c_int * QSIM_TUNE_COUNT),
+                ("dft_ms", ctypes.c_double), ("dense_ms", ctypes.c_double * 3),
+                ("fuse_ms", ctypes.c_double * 5)]
+
+
 _lib = None
 
 _VP = ctypes.c_void_p
@@ -86,6 +102,11 @@ _SIGS = {
     "hhl_build_spectral_ex": ([_DP, _DP, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                ctypes.c_double, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
     "qsim_hermitian_eig": ([_DP, ctypes.c_int, ctypes.c_int, _DP, _DP], ctypes.c_int),
+    "qsim_launch_counts": ([ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int], ctypes.c_int),
+    "qsim_tune_get": ([ctypes.c_int, ctypes.c_int, _IP], ctypes.c_int),
+    "qsim_tune_set": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "qsim_tune_reset": ([], ctypes.c_int),
+    "qsim_autotune": ([_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(_TuneReport)], ctypes.c_int),
     "hhl_circuit_free": ([_VP], None),
     "hhl_as_circuit": ([_VP], _VP),
     "hhl_get_info": ([_VP, ctypes.POINTER(_HHLInfo)], ctypes.c_int),
@@ -178,6 +199,17 @@ def _check_state(state, n: int):
 def qsim_launch_count() -> int:
     """Kernels this library has launched in this process (graph replays not included)."""
     return int(library().qsim_launch_count())
+
+
+KERNEL_FAMILIES = ("dense_simt", "dense_tc", "fourier", "fourier_tma", "expand", "elementwise", "batched",
+                   "readout", "prep")
+
+
+def qsim_launch_counts() -> dict:
+    """Kernels launched by the library in this process, by family (see QSIM_KERNEL_*)."""
+    arr = (ctypes.c_ulonglong * len(KERNEL_FAMILIES))()
+    _check(library().qsim_launch_counts(arr, len(KERNEL_FAMILIES)))
+    return {name: int(arr[i]) for i, name in enumerate(KERNEL_FAMILIES)}
 
 
 def qsim_device_status(clear: bool = False) -> int:
@@ -342,6 +374,40 @@ def hhl_build_spectral(lam, V, b, n_clock: int = 0, t: float = 0.0, C: float = 0
         _check(library().hhl_build_spectral(la.ctypes.data_as(_DP), Vp, bp, N, int(n_clock),
                                             float(t), float(C), ctypes.byref(p)))
     return HHLCircuit(p)
+
+
+def qsim_tune_get(dtype: int, key: int) -> int:
+    """One entry of the kernel-choice table (QSIM_TUNE_* key) for QSIM_C64 or QSIM_C128."""
+    v = ctypes.c_int(0)
+    _check(library().qsim_tune_get(int(dtype), int(key), ctypes.byref(v)))
+    return int(v.value)
+
+
+def qsim_tune_set(dtype: int, key: int, value: int):
+    _check(library().qsim_tune_set(int(dtype), int(key), int(value)))
+
+
+def qsim_tune_reset():
+    _check(library().qsim_tune_reset())
+
+
+def qsim_tune_table() -> dict:
+    """The whole table, by dtype name and key name."""
+    return {name: {TUNE_NAMES[k]: qsim_tune_get(dt, k) for k in range(QSIM_TUNE_COUNT)}
+            for name, dt in (("c64", QSIM_C64), ("c128", QSIM_C128))}
+
+
+def qsim_autotune(state, stream=None) -> dict:
+    """Time the kernel alternatives on `state` (contents overwritten) and write the fastest into
+    the table for the state's dtype; returns the report."""
+    n = state.numel().bit_length() - 1
+    _check_state(state, n)
+    r = _TuneReport()
+    _check(library().qsim_autotune(ctypes.c_void_p(state.data_ptr()), n, _dtype_of(state), _stream_ptr(stream),
+                                   ctypes.byref(r)))
+    return {"n_qubits": r.n_qubits, "table": {TUNE_NAMES[k]: r.values[k] for k in range(QSIM_TUNE_COUNT)},
+            "dft_ms": r.dft_ms, "dense_ms": {str(4 + i): r.dense_ms[i] for i in range(3)},
+            "fuse_ms": {str(2 + i): r.fuse_ms[i] for i in range(5)}}
 
 
 def qsim_hermitian_eig(A, max_iter: int = 0):

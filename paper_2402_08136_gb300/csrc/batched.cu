@@ -1006,7 +1006,7 @@ void launch_batch(qsim_batch *B, cudaStream_t st) {
                                                                               B->d_counter, B->smem_amps, B->stage_bytes);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel: ") + cudaGetErrorString(e));
-    note_launches(1);
+    note_launches(1, QSIM_KERNEL_BATCHED);
 }
 
 void run_batch(qsim_batch *B, void *stream) {

@@ -143,7 +143,7 @@ void circuit_info(const qsim_circuit *c, qsim_circuit_info *out);
 // the first 2^live amplitudes have been written (see hhl_run); the result is the full state.
 void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int live = -1);
 // every kernel launch site reports its launches (qsim_launch_count)
-void note_launches(int k);
+void note_launches(int k, int family);
 void ensure_device_blob(qsim_circuit *c, int dtype);
 std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype);   // sets op offsets
 void attach_external_blob(qsim_circuit *c, int dtype, void *dev, size_t bytes);
@@ -193,6 +193,12 @@ void dft_tables(const Op &op, std::vector<cd> &W, std::vector<cd> &Tlo, std::vec
 bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cudaStream_t st,
              const Op *qop = nullptr, const void *qlo = nullptr, const void *qhi = nullptr, int qmode = 0,
              const Op *inv = nullptr);
+// tuning.cpp: the kernel-choice table (QSIM_TUNE_* keys of qsim.h)
+int tune_get(int dtype, int key);
+// dft_tma.cu: complex64 pass with bulk-copy (TMA) tiles; false when the shape does not fit
+bool dft_tma_launch(const void *dft_args, int n, int K, int sign, int kind, cudaStream_t st);
+unsigned dft_tma_read_error();
+void dft_tma_clear_error();
 // linalg.cpp
 // Both throw Error(QSIM_EINVAL, "eigensolver did not converge ...") when the iteration cap
 // (<= 0: 100 Jacobi sweeps / 60 N implicit QR steps) ends before the matrix is diagonal.

@@ -722,7 +722,7 @@ bool launch_dense_tc_real7(void *state, int n, const std::vector<int> &targets, 
     tc::dense_tc_real7_kernel<<<(int)grid, tc::kThreadsWS, tc::tcr::SMEM, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_real7_kernel: ") + cudaGetErrorString(e));
-    note_launches(1);
+    note_launches(1, QSIM_KERNEL_DENSE_TC);
     return true;
 }
 
@@ -770,7 +770,7 @@ static void launch_tc_t(const tc::Args &a, int sms, cudaStream_t st) {
     tc::dense_tc_kernel<K, TR><<<(int)grid, tc::kThreadsWS, C::SMEM, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_kernel: ") + cudaGetErrorString(e));
-    note_launches(1);
+    note_launches(1, QSIM_KERNEL_DENSE_TC);
 }
 
 // Returns false if this gate shape is not handled by the tensor-core kernel.
@@ -810,13 +810,14 @@ unsigned read_device_error() {
     unsigned v = 0;
     cudaError_t e = cudaMemcpyFromSymbol(&v, g_device_error, sizeof(v));
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("reading device status: ") + cudaGetErrorString(e));
-    return v;
+    return v | dft_tma_read_error();  // bit 0 either way: a bounded wait ran out
 }
 
 void clear_device_error() {
     const unsigned z = 0;
     cudaError_t e = cudaMemcpyToSymbol(g_device_error, &z, sizeof(z));
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("clearing device status: ") + cudaGetErrorString(e));
+    dft_tma_clear_error();
 }
 
 }  // namespace qsim

@@ -4,7 +4,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -108,34 +107,27 @@ bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
     for (int j = 0; j < K; j++) a.fpos[j] = op.targets[j];
     for (int j = 0; j < ns; j++) a.spos[j] = op.controls[j];
     const int k1 = K / 2;
-    int L = std::min(lane_bits_default(dtype, k1), n - K);
-    if (const char *e = std::getenv("QSIM_DFT_LANES")) {
-        const int v = std::atoi(e);
-        if (v >= 1) L = std::min({v, n - K, (dtype == QSIM_C128 ? 8 : 9) - k1, kMaxLane});
+    const bool contig = [&] {
+        for (int j = 0; j < K; j++)
+            if (op.targets[j] != op.targets[0] + j) return false;
+        return true;
+    }();
+    a.f0 = op.targets[0];
+    const int kind = op.kind == OP_WALSH ? 1 : (a.inv ? 2 : 0);
+    // complex64 with a contiguous field: the bulk-copy tile kernel, when the table selects it
+    // and the shape fits
+    if (dtype == QSIM_C64 && contig && tune_get(QSIM_C64, QSIM_TUNE_DFT_TMA) == 1) {
+        DftArgs t = a;
+        t.hT = hT;
+        t.tw_smem = 0;
+        if (dft_tma_launch(&t, n, K, op.sign, kind, st)) return true;
     }
+    int L = std::min(lane_bits_default(dtype, k1), n - K);
+    if (const int v = tune_get(dtype, QSIM_TUNE_DFT_LANES))
+        L = std::min({v, n - K, (dtype == QSIM_C128 ? 8 : 9) - k1, kMaxLane});
     L = std::max(L, 0);
     unsigned long long fmask = 0;
     for (int q : op.targets) fmask |= 1ull << q;
-    // staged input (complex64): the lanes must be qubits 0..L-1 (16-byte runs) and two input
-    // tiles must fit beside the exchange buffer; the lane count drops until they do
-    {
-        // opt-in: with one 256-thread CTA per SM the transform work is exposed, and the
-        // measured passes were slower than the unstaged kernel
-        const char *e = std::getenv("QSIM_DFT_STAGE");
-        const bool allow = dtype == QSIM_C64 && e && e[0] == '1';
-        int Ls = L;
-        auto smem_for = [&](int l, bool st) {
-            const size_t tile = (size_t)1 << (K + l);
-            return vb * ((st ? 2 * tile : 0) + ((size_t)1 << K) + tile + ((size_t)1 << k1 << l)) +
-                   8 * (((size_t)1 << k1) + ((size_t)1 << (K - k1)) + ((size_t)1 << l));
-        };
-        while (Ls > 1 && smem_for(Ls, true) > 220 * 1024) Ls--;
-        const bool lanes_low = (fmask & ((1ull << Ls) - 1ull)) == 0;
-        if (allow && lanes_low && Ls >= 1 && smem_for(Ls, true) <= 220 * 1024 && ((size_t)vb << Ls) >= 16) {
-            a.stage = 1;
-            L = Ls;
-        }
-    }
     std::vector<int> fix(op.targets.begin(), op.targets.end());
     int cnt = 0;
     for (int q = 0; q < n && cnt < L; q++)
@@ -146,9 +138,8 @@ bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
     a.L = L;
     {
         const bool lanes_low = (fmask & ((1ull << L) - 1ull)) == 0;
-        const char *e = std::getenv("QSIM_DFT_PF");
-        const int dist = e ? std::max(0, std::atoi(e)) : 1;  // tiles ahead
-        a.pf = (!a.stage && lanes_low && ((size_t)vb << L) == 128) ? dist : 0;
+        const int dist = tune_get(dtype, QSIM_TUNE_DFT_PREFETCH);  // tiles ahead
+        a.pf = (lanes_low && ((size_t)vb << L) == 128) ? dist : 0;
     }
     std::sort(fix.begin(), fix.end());
     a.nfix = (int)fix.size();
@@ -156,8 +147,7 @@ bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
     a.ntiles = 1ll << (n - K - L);
     const int N1 = 1 << k1, N2 = 1 << (K - k1), NL = 1 << L;
     const int threads = N1 << L;
-    size_t smem = vb * ((a.stage ? 2 * ((size_t)1 << (K + L)) : 0) + ((size_t)1 << K) +
-                        ((size_t)1 << (K + L)) + (size_t)N1 * NL) +
+    size_t smem = vb * (((size_t)1 << K) + ((size_t)1 << (K + L)) + (size_t)N1 * NL) +
                   8 * ((size_t)N1 + N2 + NL + ((N1 + N2 + NL) & 1));
     // twiddle tables in shared memory when they fit (they are read once per amplitude)
     const size_t tw_bytes = vb * (((size_t)1 << hT) + ((size_t)1 << (K + ns - hT)));
@@ -165,10 +155,6 @@ bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
         a.tw_smem = 1;
         smem += tw_bytes;
     }
-    bool contig = true;
-    for (int j = 0; j < K; j++) contig = contig && op.targets[j] == op.targets[0] + j;
-    a.f0 = op.targets[0];
-    const int kind = op.kind == OP_WALSH ? 1 : (a.inv ? 2 : 0);
     if (dtype == QSIM_C128) dft_launch_f64(a, K, op.sign, kind, contig, threads, smem, st);
     else dft_launch_f32(a, K, op.sign, kind, contig, threads, smem, st);
     return true;

@@ -76,8 +76,6 @@ struct DftArgs {
     int twmode;       // 0 no twiddle, 1 before the transform, 2 after
     int hT, ns, nfix;
     int f0;                     // lowest field qubit (contiguous field: bit j on qubit f0 + j)
-    int stage;                  // 1: the lanes are qubits 0..L-1 and each tile's input is
-                                // prefetched into shared memory (cp.async, double buffer)
     int tw_smem;                // 1: the twiddle tables Tlo, Thi are copied to shared memory
     int pf;                     // > 0: the lanes are qubits 0..L-1 and a lane run is one
                                 // 128-byte line: each tile prefetches the lines of the tile pf
@@ -246,10 +244,8 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
     const int L = a.L, NL = 1 << L;
     const int nthr = N1 << L;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // [input stages x2 (if staged)] [W] [S] [offset tables]
-    V *stages = reinterpret_cast<V *>(smem_raw);
-    const int tile_elems = KN << L;
-    V *Ws = stages + (a.stage ? 2 * tile_elems : 0);
+    // [W] [S] [offset tables]
+    V *Ws = reinterpret_cast<V *>(smem_raw);
     V *S = Ws + KN;
     // S: block of output digit a at a N1 2^L + (a / RR) 2^L: the 2^L-element gap between the
     // blocks of consecutive thread groups spreads pass 2's reads over the banks
@@ -309,24 +305,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
     auto qphase = [&](unsigned long long idx) -> V { return qphase_cd((idx >> a.qnb) & qcm, idx & qdm); };
     V x[N2];
 
-    // staged input: tile tix lands in stages[(it & 1)] as [field value y][lane], 16-byte
-    // chunks of the contiguous lane runs; the next tile's copies fly during this tile's work
-    constexpr int EPC = 16 / (int)sizeof(V);  // amplitudes per 16-byte chunk
-    auto issue = [&](long long tix, V *dst) {
-        if (tix < a.ntiles) {
-            const unsigned long long tb = insert_zero_bits((unsigned long long)tix, a.fix, a.nfix);
-            const int cpr_log = L - (sizeof(V) == 8 ? 1 : 0);  // log2 of chunks per lane run
-            for (int c = tid; c < (KN << cpr_log); c += nthr) {
-                const int y = c >> cpr_log, part = c & ((1 << cpr_log) - 1);
-                const long long fo = CONTIG ? (long long)((unsigned long long)y << a.f0) : vlo[y & (N1 - 1)] + vhi[y >> k1];
-                cp_async16(dst + y * NL + part * EPC, psi + tb + fo + part * EPC);
-            }
-        }
-        cp_async_commit();
-    };
-    if (a.stage) issue(blockIdx.x, stages);
-    int it = 0;
-    for (long long tix = blockIdx.x; tix < a.ntiles; tix += gridDim.x, it++) {
+    for (long long tix = blockIdx.x; tix < a.ntiles; tix += gridDim.x) {
         const unsigned long long base = insert_zero_bits((unsigned long long)tix, a.fix, a.nfix) + lane_off[l];
         unsigned long long kb = 0;  // clock value bits outside the field (inversion)
         if (INV)
@@ -335,16 +314,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
         unsigned w = 0;
         for (int j = 0; j < a.ns; j++) w |= (unsigned)((base >> a.spos[j]) & 1ull) << j;
         // pass 1
-        if (a.stage) {
-            // the buffer refilled now was read by the previous tile's pass 1, which every thread
-            // finished before that tile's barrier
-            issue(tix + gridDim.x, stages + ((it + 1) & 1) * tile_elems);
-            cp_async_wait<1>();
-            __syncthreads();
-            const V *cur = stages + (it & 1) * tile_elems;
-#pragma unroll
-            for (int v = 0; v < N2; v++) x[v] = cur[((u + N1 * v) << L) + l];
-        } else if (CONTIG) {
+        if (CONTIG) {
             const V *src = psi + base + ((unsigned long long)u << a.f0);
             const long long step = 1ll << (a.f0 + k1);
 #pragma unroll
@@ -457,7 +427,6 @@ __global__ void __launch_bounds__(MaxThreads<R>::n) dft_kernel(const DftArgs a) 
         }
         __syncthreads();  // S is rewritten by the next tile's pass 1
     }
-    if (a.stage) cp_async_wait<0>();
 }
 
 inline int num_sms_dft() {
@@ -495,7 +464,7 @@ void launch_kind(const DftArgs &a, bool contig, int threads, size_t smem, cudaSt
     kern<<<(int)grid, threads, smem, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dft_kernel: ") + cudaGetErrorString(e));
-    note_launches(1);
+    note_launches(1, QSIM_KERNEL_FOURIER);
 }
 
 template <typename R, int K>

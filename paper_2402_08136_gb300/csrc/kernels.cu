@@ -40,12 +40,17 @@ namespace qsim {
 // Kernels launched by this library (every launch site reports here; a CUDA graph replay does
 // not go through them).
 static std::atomic<unsigned long long> g_launches{0};
-void note_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+static std::atomic<unsigned long long> g_family[QSIM_KERNEL_FAMILIES];
+void note_launches(int k, int family) {
+    g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed);
+    if (family >= 0 && family < QSIM_KERNEL_FAMILIES)
+        g_family[family].fetch_add((unsigned long long)k, std::memory_order_relaxed);
+}
 
-static void check_launch(const char *what, int launches = 1) {
+static void check_launch(const char *what, int launches, int family) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
-    note_launches(launches);
+    note_launches(launches, family);
 }
 
 static int num_sms() {
@@ -781,7 +786,7 @@ void launch_dense_t(const DenseArgs &a, size_t smem, bool pipe, cudaStream_t st)
     QSIM_REQUIRE(per_sm > 0, "dense kernel does not fit on an SM");
     const long long grid = std::min<long long>(a.ntiles, (long long)num_sms() * per_sm);
     kern<<<(int)grid, kThreads, smem, st>>>(a);
-    check_launch("dense_tile_kernel");
+    check_launch("dense_tile_kernel", 1, QSIM_KERNEL_DENSE_SIMT);
 }
 
 template <typename R>
@@ -867,7 +872,7 @@ void run_phase(void *state, int n, int dtype, const Op &op, cudaStream_t st) {
     const int grid = grid_for(a.count, 256);
     if (dtype == QSIM_C128) phase_kernel<double><<<grid, 256, 0, st>>>(a);
     else phase_kernel<float><<<grid, 256, 0, st>>>(a);
-    check_launch("phase_kernel");
+    check_launch("phase_kernel", 1, QSIM_KERNEL_ELEMENTWISE);
 }
 
 void run_diag(void *state, int n, int dtype, const Op &op, const void *ddev, cudaStream_t st) {
@@ -884,7 +889,7 @@ void run_diag(void *state, int n, int dtype, const Op &op, const void *ddev, cud
     const int grid = grid_for(a.count, 256);
     if (dtype == QSIM_C128) diag_kernel<double><<<grid, 256, 0, st>>>(a);
     else diag_kernel<float><<<grid, 256, 0, st>>>(a);
-    check_launch("diag_kernel");
+    check_launch("diag_kernel", 1, QSIM_KERNEL_ELEMENTWISE);
 }
 
 void run_swap(void *state, int n, int dtype, const Op &op, cudaStream_t st) {
@@ -904,7 +909,7 @@ void run_swap(void *state, int n, int dtype, const Op &op, cudaStream_t st) {
     const int grid = grid_for(a.count, 256);
     if (dtype == QSIM_C128) swap_kernel<double><<<grid, 256, 0, st>>>(a);
     else swap_kernel<float><<<grid, 256, 0, st>>>(a);
-    check_launch("swap_kernel");
+    check_launch("swap_kernel", 1, QSIM_KERNEL_ELEMENTWISE);
 }
 
 void run_ucry(void *state, int n, int dtype, const Op &op, const void *csdev, cudaStream_t st,
@@ -927,19 +932,12 @@ void run_ucry(void *state, int n, int dtype, const Op &op, const void *csdev, cu
     const int grid = grid_for(a.count, 256);
     if (dtype == QSIM_C128) ucry_kernel<double><<<grid, 256, 0, st>>>(a);
     else ucry_kernel<float><<<grid, 256, 0, st>>>(a);
-    check_launch("ucry_kernel");
+    check_launch("ucry_kernel", 1, QSIM_KERNEL_ELEMENTWISE);
 }
 
-// Tensor-core dense path for complex64 (QSIM_DENSE_TC=0 in the environment selects the SIMT
-// kernel instead, for comparisons).
-bool tc_enabled() {
-    static int v = -1;
-    if (v < 0) {
-        const char *e = std::getenv("QSIM_DENSE_TC");
-        v = (e && e[0] == '0') ? 0 : 1;
-    }
-    return v == 1;
-}
+// Tensor-core dense path for complex64: the kernel-choice table says which widths use it
+// (bit k: k targets; bit 7: the real 7-target kernel).
+bool tc_enabled(int k) { return (tune_get(QSIM_C64, QSIM_TUNE_DENSE_TC) >> k) & 1; }
 
 void run_qpe_phase(void *state, int n, int dtype, const Op &op, const void *lo, const void *hi, cudaStream_t st) {
     QpeArgs a;
@@ -956,7 +954,7 @@ void run_qpe_phase(void *state, int n, int dtype, const Op &op, const void *lo, 
     const int grid = grid_for(a.N, 256);
     if (dtype == QSIM_C128) qpe_phase_kernel<double><<<grid, 256, 0, st>>>(a);
     else qpe_phase_kernel<float><<<grid, 256, 0, st>>>(a);
-    check_launch("qpe_phase_kernel");
+    check_launch("qpe_phase_kernel", 1, QSIM_KERNEL_ELEMENTWISE);
 }
 
 // The pass `op` on the field w .. w+K-1 of a state that is zero from index 2^w on (see
@@ -989,7 +987,7 @@ void run_expand(void *state, int w, int dtype, const Op &op, const Op *qop, cons
         const int grid = grid_for(a.count, 256);
         if (dtype == QSIM_C128) expand_kernel<double><<<grid, 256, 0, st>>>(a);
         else expand_kernel<float><<<grid, 256, 0, st>>>(a);
-        check_launch("expand_kernel");
+        check_launch("expand_kernel", 1, QSIM_KERNEL_EXPAND);
     }
 }
 
@@ -1016,7 +1014,7 @@ void run_hhl_invert(void *state, int n, int dtype, const Op &op, cudaStream_t st
     const int grid = grid_for(a.count, 256);
     if (dtype == QSIM_C128) hhl_invert_kernel<double><<<grid, 256, 0, st>>>(a);
     else hhl_invert_kernel<float><<<grid, 256, 0, st>>>(a);
-    check_launch("hhl_invert_kernel");
+    check_launch("hhl_invert_kernel", 1, QSIM_KERNEL_ELEMENTWISE);
 }
 
 }  // namespace
@@ -1139,16 +1137,7 @@ void ensure_device_blob(qsim_circuit *c, int dtype) {
 
 // A structured phase (diagonal) next to a Fourier or Walsh-Hadamard pass is applied inside that
 // pass (to its outputs or inputs) instead of as a pass of its own; a pass without twiddle is
-// preferred.  QSIM_FUSE_DIAG=0 in the environment keeps them apart (for comparisons).
-static bool fuse_diag_enabled() {
-    static int v = -1;
-    if (v < 0) {
-        const char *e = std::getenv("QSIM_FUSE_DIAG");
-        v = (e && e[0] == '0') ? 0 : 1;
-    }
-    return v == 1;
-}
-
+// preferred.
 static bool is_pass(const Op &op) { return op.kind == OP_DFT || op.kind == OP_WALSH; }
 
 static int top_qubit(const Op &op) {
@@ -1164,7 +1153,6 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
     const unsigned char *base = static_cast<const unsigned char *>(c->blob[slot].ptr);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const std::vector<Op> &ops = c->ops;
-    const bool fuse = fuse_diag_enabled();
     // Live width w: every amplitude at an index >= 2^w is zero and has not been written (HHL: after
     // the preparation only the data register is populated).  An op on qubits below w runs as a
     // w-qubit state; a twiddle-free pass on the field right above w broadcasts column 0 (write
@@ -1190,7 +1178,7 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
     for (size_t i = 0; i < ops.size(); i++) {
         const Op &op = ops[i];
         const void *dptr = base + op.dev_off[slot];
-        if (fuse && i + 1 < ops.size()) {
+        if (i + 1 < ops.size()) {
             // a structured phase next to a pass runs inside it: on the pass's outputs, unless this
             // pass has a twiddle and the pass after the phase has none (then on that one's inputs)
             size_t pi = ops.size(), qi = ops.size();
@@ -1251,7 +1239,7 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
         materialize(top_qubit(op) + 1);
         switch (op.kind) {
             case OP_DENSE:
-                if (dtype == QSIM_C64 && op.has_tc && tc_enabled() && op.tc_pad >= 0) {
+                if (dtype == QSIM_C64 && op.has_tc && tc_enabled(7) && op.tc_pad >= 0) {
                     // real 6-target gate padded to 7 targets (the pad must lie inside the live width)
                     std::vector<int> t7(op.targets);
                     t7.push_back(op.tc_pad);
@@ -1259,7 +1247,7 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
                     if (op.tc_pad < w &&
                         launch_dense_tc_real7(state, w, t7, op.controls, base + op.dev_off_tc[slot], num_sms(), st))
                         break;
-                } else if (dtype == QSIM_C64 && op.has_tc && tc_enabled() &&
+                } else if (dtype == QSIM_C64 && op.has_tc && tc_enabled((int)op.targets.size()) &&
                            (op.targets.size() == 7
                                 ? launch_dense_tc_real7(state, w, op.targets, op.controls, base + op.dev_off_tc[slot], num_sms(), st)
                                 : launch_dense_tc(state, w, op.targets, op.controls, base + op.dev_off_tc[slot], num_sms(), st))) {
@@ -1299,7 +1287,7 @@ void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb
     CUDA_OK(cudaMemsetAsync(state, 0, (size_t)written * vbytes, st));
     if (dtype == QSIM_C128) prep_kernel<double><<<1, kMaxParamB, 0, st>>>(a);
     else prep_kernel<float><<<1, kMaxParamB, 0, st>>>(a);
-    check_launch("prep_kernel");
+    check_launch("prep_kernel", 1, QSIM_KERNEL_PREP);
     if (a.D > kMaxParamB) {  // rare: long right-hand sides go through a staged copy
         const int rest = a.D - kMaxParamB;
         std::vector<unsigned char> buf;
@@ -1335,7 +1323,7 @@ void readout_launch_async(const void *state, int dtype, int n, int nb, cudaStrea
         norm_partials_kernel<float><<<nblk, 256, 0, st>>>(state, chunk, partials);
         norm_final_kernel<float><<<1, 256, 0, st>>>(partials, nblk, state, off, (int)slice_len, out);
     }
-    check_launch("readout kernels", 2);
+    check_launch("readout kernels", 2, QSIM_KERNEL_READOUT);
     CUDA_OK(cudaMemcpyAsync(pinned_sums, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_OK(cudaMemcpyAsync(pinned_slice, static_cast<const unsigned char *>(state) + off * vb, slice_len * vb,
                             cudaMemcpyDeviceToHost, st));
@@ -1371,7 +1359,7 @@ void readout_device(const void *state, int dtype, int n, int nb, int m, void *st
             norm_partials_kernel<float><<<nblk, 256, 0, st>>>(state, chunk, partials);
             norm_final_kernel<float><<<1, 256, 0, st>>>(partials, nblk, state, off, (int)slice_len, out);
         }
-        check_launch("readout kernels", 2);
+        check_launch("readout kernels", 2, QSIM_KERNEL_READOUT);
         std::vector<unsigned char> hs(slice_len * vb);
         double hsum[3];
         CUDA_OK(cudaMemcpyAsync(hsum, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1476,7 +1464,7 @@ extern "C" int hhl_readout_noalloc(const void *state, int dtype, const hhl_circu
             norm_final_kernel<float><<<1, 256, 0, st>>>(partials, nblk, state, off, (int)slice_len, out);
             slice_to_f64_kernel<float><<<(int)((slice_len + 255) / 256), 256, 0, st>>>(state, off, (int)slice_len, slice);
         }
-        check_launch("hhl_readout_noalloc kernels", 3);
+        check_launch("hhl_readout_noalloc kernels", 3, QSIM_KERNEL_READOUT);
         double sums[3];
         CUDA_OK(cudaMemcpyAsync(sums, out, sizeof(sums), cudaMemcpyDeviceToHost, st));
         // the slice lands straight in the caller's buffer: all 2^nb amplitudes, or the N entries
@@ -1528,6 +1516,14 @@ qsim_circuit::~qsim_circuit() {
 extern "C" void qsim_circuit_free(qsim_circuit *c) { delete c; }
 
 extern "C" unsigned long long qsim_launch_count(void) { return g_launches.load(); }
+
+extern "C" int qsim_launch_counts(unsigned long long *counts, int n) {
+    return guarded([&] {
+        QSIM_REQUIRE(counts != nullptr && n >= 0, "NULL argument");
+        for (int i = 0; i < n && i < QSIM_KERNEL_FAMILIES; i++) counts[i] = g_family[i].load();
+        for (int i = QSIM_KERNEL_FAMILIES; i < n; i++) counts[i] = 0;
+    });
+}
 
 extern "C" int qsim_apply(void *state, int n_qubits, int dtype, const qsim_circuit *c, void *stream) {
     return guarded([&] {

@@ -322,3 +322,29 @@ def test_noalloc_readout_rejects_a_slice_beyond_its_scratch(qs):
            None, None)
     assert rc == -1
     assert "2^10" in library().qsim_last_error().decode()
+
+
+def test_kernel_choice_table(qs):
+    """The table that replaces environment knobs: defaults, set, range checks, reset."""
+    t = qs.qsim_tune_table()
+    assert t["c64"]["dft_tma"] == 1 and t["c128"]["dft_tma"] == 0
+    assert t["c64"]["fuse_width"] == 4 and t["c64"]["tuned"] == 0
+    assert t["c64"]["dense_tc"] == (1 << 4) | (1 << 5) | (1 << 6) | (1 << 7)
+    qs.qsim_tune_set(qs.QSIM_C64, qs.QSIM_TUNE_FUSE_WIDTH, 3)
+    try:
+        assert qs.qsim_tune_get(qs.QSIM_C64, qs.QSIM_TUNE_FUSE_WIDTH) == 3
+        # qsim_fuse(max_k = 0) takes the table's width
+        n = 6
+        c = qs.Circuit(n)
+        H = np.array([[1, 1], [1, -1]]) / math.sqrt(2)
+        for q in range(n):
+            c.add_gate([q], H)
+        assert qs.qsim_fuse(c, 0).info()["max_k"] == 3
+        for key, bad in ((qs.QSIM_TUNE_FUSE_WIDTH, 7), (qs.QSIM_TUNE_DFT_TMA, 2), (99, 1)):
+            with pytest.raises(qs.QsimError):
+                qs.qsim_tune_set(qs.QSIM_C64, key, bad)
+        with pytest.raises(qs.QsimError):
+            qs.qsim_tune_get(3, 0)
+    finally:
+        qs.qsim_tune_reset()
+    assert qs.qsim_tune_get(qs.QSIM_C64, qs.QSIM_TUNE_FUSE_WIDTH) == 4

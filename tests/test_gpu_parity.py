@@ -444,6 +444,7 @@ def _oracle_spectral(lam, V, b, m, t, C):
     psi = ohhl.run(h)
     out = ohhl.readout(h, psi)
     out["psi"] = psi
+    out["circuit"] = h
     return out
 
 
