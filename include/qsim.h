@@ -147,7 +147,9 @@ int qsim_fuse(const qsim_circuit *in, int max_k, qsim_circuit **out);
  * Application (the hot loop)                                                               *
  * ======================================================================================= */
 
-/* Apply every operation of `c` in order to `state` (device, 2^n_qubits amplitudes of `dtype`,
+/* The paper's hot loop, the "unitary evolution of the state" of Sec. II-C (gate by gate, fused
+ * gates as dense 2^k x 2^k products, Fig. 4):
+ * apply every operation of `c` in order to `state` (device, 2^n_qubits amplitudes of `dtype`,
  * n_qubits == the circuit's qubit count), asynchronously on `stream`.  The first call for a
  * circuit and dtype uploads its matrices to the device (synchronously) and keeps them until
  * qsim_circuit_free.  Errors: EINVAL (size/dtype mismatch, NULL), ENOMEM, ECUDA. */
@@ -184,8 +186,12 @@ int qsim_launch_counts(unsigned long long *counts, int n);
  * per state dtype (the paper has no counterpart; the benchmark spec asks for fusion width and tile
  * shapes chosen by an autotuner).  Keys: */
 #define QSIM_TUNE_DFT_TMA 0      /* Fourier / Walsh-Hadamard passes on complex64 with a contiguous
-                                    field of 9-10 qubits above qubit 2: 1 = tile moved by the
-                                    tensor memory accelerator (bulk copies), 0 = thread loads     */
+                                    field of 9-10 qubits above the lane qubits: 0 = thread loads
+                                    and stores; tile loaded by the tensor memory accelerator (bulk
+                                    tensor copy) with rows of 8 amplitudes (64 B) and 1 = bulk
+                                    stores, 2 = thread stores with the next tile's load issued
+                                    while the current one is transformed; 3, 4 = the same with
+                                    rows of 16 amplitudes (128 B)                                 */
 #define QSIM_TUNE_DFT_LANES 1    /* thread-load pass kernel: lane qubits per tile (0 = 128-byte
                                     runs: 4 for complex64, 3 for complex128)                       */
 #define QSIM_TUNE_DFT_PREFETCH 2 /* thread-load pass kernel: L2 prefetch distance in tiles (0 off) */
@@ -194,13 +200,19 @@ int qsim_launch_counts(unsigned long long *counts, int n);
                                     6-target gates on qubits 0 and 1) on the tensor cores          */
 #define QSIM_TUNE_FUSE_WIDTH 4   /* width qsim_fuse uses when called with max_k = 0 (the
                                     complex64 entry; 1..6)                                          */
-#define QSIM_TUNE_TUNED 5        /* 1 once qsim_autotune has written this dtype's entries        */
-#define QSIM_TUNE_COUNT 6
+#define QSIM_TUNE_DFT_L2PROMO 5  /* bulk-copy pass kernel: L2 promotion of its tile loads (0 none,
+                                    1 64 B, 2 128 B, 3 256 B)                                      */
+#define QSIM_TUNE_TUNED 6        /* 1 once qsim_autotune has written this dtype's entries        */
+#define QSIM_TUNE_COUNT 7
 
-/* Read / write one entry for dtype QSIM_C64 or QSIM_C128.  Writes take effect for launches
- * enqueued afterwards.  Errors: EINVAL (unknown key, value out of range). */
-int qsim_tune_get(int dtype, int key, int *value);
-int qsim_tune_set(int dtype, int key, int value);
+/* Each entry is kept per state dtype and per size class (states of up to 24 qubits, 25..28,
+ * 29 and more: on a 31-qubit state a pass over the top qubits meets other bounds than on a
+ * 27-qubit one).  qsim_tune_get reads the entry that applies to an n_qubits state (1..34);
+ * qsim_tune_set writes it for the class of n_qubits, or for every class when n_qubits is 0.
+ * Writes take effect for launches enqueued afterwards.  Errors: EINVAL (unknown key, value out
+ * of range). */
+int qsim_tune_get(int dtype, int key, int n_qubits, int *value);
+int qsim_tune_set(int dtype, int key, int n_qubits, int value);
 /* Every entry of both dtypes back to its default. */
 int qsim_tune_reset(void);
 
@@ -217,7 +229,8 @@ typedef struct {
  * table: the Fourier-pass kernel and its lane count and prefetch distance (three 10-qubit
  * passes), tensor cores or SIMT for complex64 dense gates of 4, 5 and 6 targets (three Haar
  * gates each), and the fusion width (a gate-level circuit of 48 random 1- and 2-qubit gates
- * fused at widths 2..6).  Synchronizes `stream`.  out may be NULL.  Errors: EINVAL, ECUDA. */
+ * fused at widths 2..6).  Writes the entries of the size class of n_qubits only.  Synchronizes
+ * `stream`.  out may be NULL.  Errors: EINVAL, ECUDA. */
 int qsim_autotune(void *state, int n_qubits, int dtype, void *stream, qsim_tune_report *out);
 
 /* ======================================================================================= *
@@ -474,6 +487,23 @@ int qsim_pool_take_completed(qsim_pool *p, uint64_t *tickets, int capacity, int 
                              double timeout_s);
 
 int qsim_pool_get_info(qsim_pool *p, qsim_pool_info *out);
+
+/* One retired launch of the pool: the stream slot, whether it was a batched launch (1) or one
+ * large request with the full-GPU kernels (0), the requests it carried (tickets first..last in
+ * submission order), and its device-time interval [t_start, t_end] in seconds since the pool was
+ * created (CUDA events recorded on the slot's stream around the launch's work; -1 if the work
+ * failed).  Intervals of launches on different slots that intersect ran concurrently. */
+typedef struct {
+    int slot;
+    int batched;
+    int n_requests;
+    uint64_t first_ticket, last_ticket;
+    double t_start, t_end;
+} qsim_pool_launch;
+
+/* The most recent retired launches (at most 4096 are kept), oldest first: up to `capacity`
+ * entries into out, *count set.  Errors: EINVAL. */
+int qsim_pool_launch_log(qsim_pool *p, qsim_pool_launch *out, int capacity, int *count);
 
 /* Finish admitted work, drop requests not yet built, release everything.  NULL is a no-op. */
 void qsim_pool_destroy(qsim_pool *p);

@@ -64,9 +64,16 @@ QSIM_TUNE_DFT_LANES = 1
 QSIM_TUNE_DFT_PREFETCH = 2
 QSIM_TUNE_DENSE_TC = 3
 QSIM_TUNE_FUSE_WIDTH = 4
-QSIM_TUNE_TUNED = 5
-QSIM_TUNE_COUNT = 6
-TUNE_NAMES = ("dft_tma", "dft_lanes", "dft_prefetch", "dense_tc", "fuse_width", "tuned")
+QSIM_TUNE_DFT_L2PROMO = 5
+QSIM_TUNE_TUNED = 6
+QSIM_TUNE_COUNT = 7
+TUNE_NAMES = ("dft_tma", "dft_lanes", "dft_prefetch", "dense_tc", "fuse_width", "dft_l2promo", "tuned")
+
+
+class _PoolLaunch(ctypes.Structure):
+    _fields_ = [("slot", ctypes.c_int), ("batched", ctypes.c_int), ("n_requests", ctypes.c_int),
+                ("first_ticket", ctypes.c_uint64), ("last_ticket", ctypes.c_uint64),
+                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double)]
 
 
 class _TuneReport(ctypes.Structure):
@@ -103,8 +110,8 @@ _SIGS = {
                                ctypes.c_double, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
     "qsim_hermitian_eig": ([_DP, ctypes.c_int, ctypes.c_int, _DP, _DP], ctypes.c_int),
     "qsim_launch_counts": ([ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int], ctypes.c_int),
-    "qsim_tune_get": ([ctypes.c_int, ctypes.c_int, _IP], ctypes.c_int),
-    "qsim_tune_set": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "qsim_tune_get": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _IP], ctypes.c_int),
+    "qsim_tune_set": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "qsim_tune_reset": ([], ctypes.c_int),
     "qsim_autotune": ([_VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(_TuneReport)], ctypes.c_int),
     "hhl_circuit_free": ([_VP], None),
@@ -134,6 +141,7 @@ _SIGS = {
     "qsim_pool_take_completed": ([_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, _IP, ctypes.c_double],
                                  ctypes.c_int),
     "qsim_pool_destroy": ([_VP], None),
+    "qsim_pool_launch_log": ([_VP, ctypes.POINTER(_PoolLaunch), ctypes.c_int, _IP], ctypes.c_int),
     "hhl_readout": ([_VP, ctypes.c_int, _VP, _VP, _DP, _DP, ctypes.POINTER(_ReadoutStats)],
                     ctypes.c_int),
 }
@@ -376,15 +384,17 @@ def hhl_build_spectral(lam, V, b, n_clock: int = 0, t: float = 0.0, C: float = 0
     return HHLCircuit(p)
 
 
-def qsim_tune_get(dtype: int, key: int) -> int:
-    """One entry of the kernel-choice table (QSIM_TUNE_* key) for QSIM_C64 or QSIM_C128."""
+def qsim_tune_get(dtype: int, key: int, n_qubits: int = 27) -> int:
+    """The kernel-choice table's entry (QSIM_TUNE_* key) for a QSIM_C64 / QSIM_C128 state of
+    n_qubits (entries are kept per size class: <= 24, 25..28, >= 29 qubits)."""
     v = ctypes.c_int(0)
-    _check(library().qsim_tune_get(int(dtype), int(key), ctypes.byref(v)))
+    _check(library().qsim_tune_get(int(dtype), int(key), int(n_qubits), ctypes.byref(v)))
     return int(v.value)
 
 
-def qsim_tune_set(dtype: int, key: int, value: int):
-    _check(library().qsim_tune_set(int(dtype), int(key), int(value)))
+def qsim_tune_set(dtype: int, key: int, value: int, n_qubits: int = 0):
+    """Set an entry for the size class of n_qubits (0: every class)."""
+    _check(library().qsim_tune_set(int(dtype), int(key), int(n_qubits), int(value)))
 
 
 def qsim_tune_reset():
@@ -392,8 +402,10 @@ def qsim_tune_reset():
 
 
 def qsim_tune_table() -> dict:
-    """The whole table, by dtype name and key name."""
-    return {name: {TUNE_NAMES[k]: qsim_tune_get(dt, k) for k in range(QSIM_TUNE_COUNT)}
+    """The whole table, by dtype, size class and key name."""
+    classes = (("le24", 24), ("25to28", 27), ("ge29", 31))
+    return {name: {cn: {TUNE_NAMES[k]: qsim_tune_get(dt, k, n) for k in range(QSIM_TUNE_COUNT)}
+                   for cn, n in classes}
             for name, dt in (("c64", QSIM_C64), ("c128", QSIM_C128))}
 
 
@@ -633,6 +645,14 @@ class Pool:
         s = _PoolInfo()
         _check(library().qsim_pool_get_info(self._ptr, ctypes.byref(s)))
         return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def launch_log(self, capacity: int = 4096) -> list:
+        """The most recent retired launches, oldest first: slot, batched, n_requests, tickets and
+        the device-time interval [t_start, t_end] (seconds since the pool was created)."""
+        buf = (_PoolLaunch * capacity)()
+        cnt = ctypes.c_int(0)
+        _check(library().qsim_pool_launch_log(self._ptr, buf, capacity, ctypes.byref(cnt)))
+        return [{f: getattr(buf[i], f) for f, _ in _PoolLaunch._fields_} for i in range(cnt.value)]
 
     def close(self):
         if getattr(self, "_ptr", None):

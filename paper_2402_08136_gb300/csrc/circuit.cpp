@@ -474,7 +474,7 @@ int qsim_fuse(const qsim_circuit *in, int max_k, qsim_circuit **out) {
     return guarded([&] {
         QSIM_REQUIRE(in != nullptr && out != nullptr, "NULL argument");
         QSIM_REQUIRE(max_k >= 0 && max_k <= 6, "max_k must be in 0..6");
-        if (max_k == 0) max_k = tune_get(QSIM_C64, QSIM_TUNE_FUSE_WIDTH);
+        if (max_k == 0) max_k = tune_get(QSIM_C64, QSIM_TUNE_FUSE_WIDTH, in->n);
         qsim_circuit *f = fuse_impl(in, max_k);
         build_ops(f);
         *out = f;

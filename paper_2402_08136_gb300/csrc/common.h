@@ -194,9 +194,10 @@ bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
              const Op *qop = nullptr, const void *qlo = nullptr, const void *qhi = nullptr, int qmode = 0,
              const Op *inv = nullptr);
 // tuning.cpp: the kernel-choice table (QSIM_TUNE_* keys of qsim.h)
-int tune_get(int dtype, int key);
+int tune_get(int dtype, int key, int n_qubits);  // entry of the size class of n_qubits
 // dft_tma.cu: complex64 pass with bulk-copy (TMA) tiles; false when the shape does not fit
-bool dft_tma_launch(const void *dft_args, int n, int K, int sign, int kind, cudaStream_t st);
+bool dft_tma_launch(const void *dft_args, int n, int K, int sign, int kind, int variant, int l2promo,
+                    cudaStream_t st);
 unsigned dft_tma_read_error();
 void dft_tma_clear_error();
 // linalg.cpp

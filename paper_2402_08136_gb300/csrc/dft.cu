@@ -116,14 +116,15 @@ bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
     const int kind = op.kind == OP_WALSH ? 1 : (a.inv ? 2 : 0);
     // complex64 with a contiguous field: the bulk-copy tile kernel, when the table selects it
     // and the shape fits
-    if (dtype == QSIM_C64 && contig && tune_get(QSIM_C64, QSIM_TUNE_DFT_TMA) == 1) {
+    if (const int variant = dtype == QSIM_C64 && contig ? tune_get(QSIM_C64, QSIM_TUNE_DFT_TMA, n) : 0) {
         DftArgs t = a;
         t.hT = hT;
         t.tw_smem = 0;
-        if (dft_tma_launch(&t, n, K, op.sign, kind, st)) return true;
+        if (dft_tma_launch(&t, n, K, op.sign, kind, variant, tune_get(QSIM_C64, QSIM_TUNE_DFT_L2PROMO, n), st))
+            return true;
     }
     int L = std::min(lane_bits_default(dtype, k1), n - K);
-    if (const int v = tune_get(dtype, QSIM_TUNE_DFT_LANES))
+    if (const int v = tune_get(dtype, QSIM_TUNE_DFT_LANES, n))
         L = std::min({v, n - K, (dtype == QSIM_C128 ? 8 : 9) - k1, kMaxLane});
     L = std::max(L, 0);
     unsigned long long fmask = 0;
@@ -138,7 +139,7 @@ bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
     a.L = L;
     {
         const bool lanes_low = (fmask & ((1ull << L) - 1ull)) == 0;
-        const int dist = tune_get(dtype, QSIM_TUNE_DFT_PREFETCH);  // tiles ahead
+        const int dist = tune_get(dtype, QSIM_TUNE_DFT_PREFETCH, n);  // tiles ahead
         a.pf = (lanes_low && ((size_t)vb << L) == 128) ? dist : 0;
     }
     std::sort(fix.begin(), fix.end());

@@ -54,8 +54,6 @@ using dftk::cmul;
 using dftk::DftArgs;
 using dftk::dft_regs;
 
-constexpr int kL = 3;                  // lane qubits: 8 amplitudes = 64 bytes per row
-constexpr int kNL = 1 << kL;
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -119,19 +117,27 @@ struct TmaExtra {
     long long ntiles;  // tiles to transform (the lower half only for KIND 2)
 };
 
-template <int K>
+// L lane qubits (the lowest qubits): rows of 2^L amplitudes, 64 (L = 3) or 128 bytes (L = 4)
+template <int K, int L>
 struct Shape {
     static constexpr int k1 = K / 2, k2 = K - k1;
     static constexpr int N1 = 1 << k1, N2 = 1 << k2, RR = N2 / N1;
-    static constexpr int threads = N1 * kNL;
-    static constexpr int tile = (1 << K) * kNL;  // amplitudes
+    static constexpr int NL = 1 << L;
+    static constexpr int threads = N1 * NL;
+    static constexpr int tile = (1 << K) * NL;  // amplitudes
+    static constexpr int min_blocks = threads >= 512 ? 1 : 512 / threads;  // 128 registers a thread
 };
 
-// KIND 0: DFT, 1: Walsh-Hadamard, 2: DFT with the HHL inversion on its outputs
-template <int K, int SGN, int KIND>
-__global__ void __launch_bounds__(Shape<K>::threads, 256 / Shape<K>::threads > 1 ? 256 / Shape<K>::threads * 2 : 2)
+// KIND 0: DFT, 1: Walsh-Hadamard, 2: DFT with the HHL inversion on its outputs.
+// EARLY: the outputs leave by thread stores straight from registers, and the next tile's bulk
+// load is issued as soon as step 2 has read the buffer, so that copy overlaps step 2's
+// transform and stores; otherwise the outputs go back through the buffer and a bulk store,
+// and the next load waits for that store to have read the buffer.
+template <int K, int L, int SGN, int KIND, bool EARLY>
+__global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
     dft_tma_kernel(const __grid_constant__ CUtensorMap tmap, const DftArgs a, const TmaExtra x) {
-    using S = Shape<K>;
+    using S = Shape<K, L>;
+    constexpr int kL = L, kNL = S::NL;
     constexpr bool WALSH = KIND == 1;
     constexpr bool INV = KIND == 2;
     constexpr int k1 = S::k1, k2 = S::k2, N1 = S::N1, N2 = S::N2, RR = S::RR, KN = 1 << K;
@@ -176,16 +182,23 @@ __global__ void __launch_bounds__(Shape<K>::threads, 256 / Shape<K>::threads > 1
         c1 = (int)((unsigned long long)t & gapm);
         c4 = (int)((unsigned long long)t >> x.gap);
     };
+    float2 *psi = reinterpret_cast<float2 *>(a.psi);
+    auto issue_load = [&](long long t) {
+        int c1, c4;
+        coords(t, c1, c4);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar_a), "r"(tx_bytes) : "memory");
+        tma_load(buf_a, &tmap, c1, c4, bar_a);
+    };
     bool failed = false;
     float2 v[N2];
     unsigned it = 0;
+    if (EARLY && tid == 0 && (long long)blockIdx.x < x.ntiles) issue_load(blockIdx.x);
     for (long long t = blockIdx.x; t < x.ntiles; t += gridDim.x, it++) {
         int c1, c4;
         coords(t, c1, c4);
-        if (tid == 0) {
+        if (!EARLY && tid == 0) {
             tma_store_wait_read();  // the previous tile's store has read the buffer
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar_a), "r"(tx_bytes) : "memory");
-            tma_load(buf_a, &tmap, c1, c4, bar_a);
+            issue_load(t);
         }
         const bool ok = mbar_wait(bar_a, it & 1u);
         if (__syncthreads_or(!ok)) {  // every thread takes the same decision
@@ -193,7 +206,8 @@ __global__ void __launch_bounds__(Shape<K>::threads, 256 / Shape<K>::threads > 1
             break;
         }
         if (tid == 0) {
-            const long long tn = t + gridDim.x;
+            // L2 prefetch of the first tile whose load is not issued yet
+            const long long tn = t + (EARLY ? 2 : 1) * (long long)gridDim.x;
             if (tn < x.ntiles) {
                 int n1, n4;
                 coords(tn, n1, n4);
@@ -260,9 +274,11 @@ __global__ void __launch_bounds__(Shape<K>::threads, 256 / Shape<K>::threads > 1
             const int sw = u & 1;
 #pragma unroll
             for (int uu = 0; uu < N1; uu++) v[r * N1 + uu] = buf[(aa * N1 + (uu ^ sw)) * kNL + l];
-            dft_regs<N1, SGN, WALSH>(v + r * N1);
         }
-        __syncthreads();  // every thread has read its step-2 points: the buffer takes the outputs
+        __syncthreads();  // every thread has read its step-2 points: the buffer is free
+        if (EARLY && tid == 0 && t + gridDim.x < x.ntiles) issue_load(t + gridDim.x);
+#pragma unroll
+        for (int r = 0; r < RR; r++) dft_regs<N1, SGN, WALSH>(v + r * N1);
 #pragma unroll
         for (int r = 0; r < RR; r++) {
             const int aa = u * RR + r;
@@ -287,6 +303,24 @@ __global__ void __launch_bounds__(Shape<K>::threads, 256 / Shape<K>::threads > 1
                 } else if (a.qmode == 2) {
                     z = cmul(z, qphase(base + ((unsigned long long)y << a.f0)));
                 }
+                if (EARLY) {
+                    const unsigned long long oi = base + ((unsigned long long)y << a.f0);
+                    if (INV) {
+                        const unsigned long long kk = kb | ((unsigned long long)y << a.inv_fdst);
+                        float sr = 0.f, cr = 1.f;
+                        if (kk) {
+                            const long long ks = (a.inv_twos && (kk >> (a.inv_nc - 1))) ? (long long)kk - (1ll << a.inv_nc)
+                                                                                       : (long long)kk;
+                            sr = fminf(fmaxf((float)a.inv_Cs / (float)ks, -1.f), 1.f);
+                            const float as = fabsf(sr);
+                            cr = sqrtf((1.f - as) * (1.f + as));
+                        }
+                        psi[oi + (1ull << a.inv_bit)] = make_float2(sr * z.x, sr * z.y);
+                        z = make_float2(cr * z.x, cr * z.y);
+                    }
+                    psi[oi] = z;
+                    continue;
+                }
                 if (INV) {
                     // keep z for the upper half; the buffer takes the lower half's cos part first
                     v[r * N1 + i] = z;
@@ -306,6 +340,7 @@ __global__ void __launch_bounds__(Shape<K>::threads, 256 / Shape<K>::threads > 1
                 buf[y * kNL + l] = z;
             }
         }
+        if (EARLY) continue;
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         if (tid == 0) tma_store(&tmap, c1, c4, buf_a);
@@ -372,10 +407,10 @@ int num_sms() {
     return sms;
 }
 
-template <int K, int SGN, int KIND>
+template <int K, int L, int SGN, int KIND, bool EARLY>
 void launch(const CUtensorMap &map, const DftArgs &a, const TmaExtra &x, size_t smem, cudaStream_t st) {
-    using S = Shape<K>;
-    auto kern = dft_tma_kernel<K, SGN, KIND>;
+    using S = Shape<K, L>;
+    auto kern = dft_tma_kernel<K, L, SGN, KIND, EARLY>;
     static bool attr = false;
     if (!attr) {
         DFT_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -391,13 +426,13 @@ void launch(const CUtensorMap &map, const DftArgs &a, const TmaExtra &x, size_t 
     note_launches(1, QSIM_KERNEL_FOURIER_TMA);
 }
 
-template <int K>
+template <int K, int L, bool EARLY>
 void launch_k(const CUtensorMap &map, const DftArgs &a, const TmaExtra &x, int sign, int kind, size_t smem,
               cudaStream_t st) {
-    if (kind == 2) launch<K, -1, 2>(map, a, x, smem, st);
-    else if (kind == 1) launch<K, 1, 1>(map, a, x, smem, st);
-    else if (sign > 0) launch<K, 1, 0>(map, a, x, smem, st);
-    else launch<K, -1, 0>(map, a, x, smem, st);
+    if (kind == 2) launch<K, L, -1, 2, EARLY>(map, a, x, smem, st);
+    else if (kind == 1) launch<K, L, 1, 1, EARLY>(map, a, x, smem, st);
+    else if (sign > 0) launch<K, L, 1, 0, EARLY>(map, a, x, smem, st);
+    else launch<K, L, -1, 0, EARLY>(map, a, x, smem, st);
 }
 
 }  // namespace dftt
@@ -417,14 +452,17 @@ void dft_tma_clear_error() {
 }
 
 // The complex64 pass `a` (built by run_dft for a state of n qubits) through the bulk-copy
-// kernel, when its shape allows: a contiguous field of 9 or 10 qubits starting at qubit 3 or
+// kernel (variant 1: bulk load and bulk store; 2: bulk load issued early, thread stores), when
+// its shape allows: a contiguous field of 9 or 10 qubits starting at qubit 3 or
 // above, the lanes on qubits 0..2.  kind: 0 DFT, 1 Walsh-Hadamard, 2 DFT with the inversion
 // (inv_bit = n, the ancilla right above the state).  Returns false when the shape does not
 // fit (the caller then runs dft_kernel).
-bool dft_tma_launch(const void *args, int n, int K, int sign, int kind, cudaStream_t st) {
+bool dft_tma_launch(const void *args, int n, int K, int sign, int kind, int variant, int promo, cudaStream_t st) {
     using namespace dftt;
     const DftArgs &a0 = *static_cast<const DftArgs *>(args);
-    if (K < 9 || K > 10) return false;
+    if (K < 9 || K > 10 || variant < 1 || variant > 4) return false;
+    const int kL = variant <= 2 ? 3 : 4, kNL = 1 << kL;
+    const bool early = variant == 2 || variant == 4;
     const int f0 = a0.f0;
     if (f0 < kL || f0 + K > n) return false;
     for (int j = 0; j < K; j++)
@@ -444,8 +482,10 @@ bool dft_tma_launch(const void *args, int n, int K, int sign, int kind, cudaStre
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
+    const CUtensorMapL2promotion prom[4] = {CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
+                                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B};
     CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, a0.psi, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, prom[std::min(std::max(promo, 0), 3)],
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return false;
     DftArgs a = a0;
@@ -459,13 +499,18 @@ bool dft_tma_launch(const void *args, int n, int K, int sign, int kind, cudaStre
     const int ntw = a.ns > 0 ? (1 << a.hT) + (1 << (K + a.ns - a.hT)) : 0;
     size_t smem = tile_bytes + ((size_t)1 << K) * 8;
     a.tw_smem = 0;
-    if (ntw > 0 && smem + (size_t)ntw * 8 + 16 <= 110 * 1024) {
+    if (ntw > 0 && smem + (size_t)ntw * 8 + 16 <= (kL == 3 ? 110 : 200) * 1024) {
         a.tw_smem = 1;
         smem += (size_t)ntw * 8;
     }
     smem += 16 + 1024;  // mbarrier, alignment slack
-    if (K == 10) launch_k<10>(map, a, x, sign, kind, smem, st);
-    else launch_k<9>(map, a, x, sign, kind, smem, st);
+    if (kL == 3) {
+        if (early) K == 10 ? launch_k<10, 3, true>(map, a, x, sign, kind, smem, st) : launch_k<9, 3, true>(map, a, x, sign, kind, smem, st);
+        else K == 10 ? launch_k<10, 3, false>(map, a, x, sign, kind, smem, st) : launch_k<9, 3, false>(map, a, x, sign, kind, smem, st);
+    } else {
+        if (early) K == 10 ? launch_k<10, 4, true>(map, a, x, sign, kind, smem, st) : launch_k<9, 4, true>(map, a, x, sign, kind, smem, st);
+        else K == 10 ? launch_k<10, 4, false>(map, a, x, sign, kind, smem, st) : launch_k<9, 4, false>(map, a, x, sign, kind, smem, st);
+    }
     return true;
 }
 

@@ -937,7 +937,7 @@ void run_ucry(void *state, int n, int dtype, const Op &op, const void *csdev, cu
 
 // Tensor-core dense path for complex64: the kernel-choice table says which widths use it
 // (bit k: k targets; bit 7: the real 7-target kernel).
-bool tc_enabled(int k) { return (tune_get(QSIM_C64, QSIM_TUNE_DENSE_TC) >> k) & 1; }
+bool tc_enabled(int k, int n) { return (tune_get(QSIM_C64, QSIM_TUNE_DENSE_TC, n) >> k) & 1; }
 
 void run_qpe_phase(void *state, int n, int dtype, const Op &op, const void *lo, const void *hi, cudaStream_t st) {
     QpeArgs a;
@@ -1239,7 +1239,7 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
         materialize(top_qubit(op) + 1);
         switch (op.kind) {
             case OP_DENSE:
-                if (dtype == QSIM_C64 && op.has_tc && tc_enabled(7) && op.tc_pad >= 0) {
+                if (dtype == QSIM_C64 && op.has_tc && tc_enabled(7, w) && op.tc_pad >= 0) {
                     // real 6-target gate padded to 7 targets (the pad must lie inside the live width)
                     std::vector<int> t7(op.targets);
                     t7.push_back(op.tc_pad);
@@ -1247,7 +1247,7 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
                     if (op.tc_pad < w &&
                         launch_dense_tc_real7(state, w, t7, op.controls, base + op.dev_off_tc[slot], num_sms(), st))
                         break;
-                } else if (dtype == QSIM_C64 && op.has_tc && tc_enabled((int)op.targets.size()) &&
+                } else if (dtype == QSIM_C64 && op.has_tc && tc_enabled((int)op.targets.size(), w) &&
                            (op.targets.size() == 7
                                 ? launch_dense_tc_real7(state, w, op.targets, op.controls, base + op.dev_off_tc[slot], num_sms(), st)
                                 : launch_dense_tc(state, w, op.targets, op.controls, base + op.dev_off_tc[slot], num_sms(), st))) {

@@ -117,6 +117,7 @@ struct PoolReq {
 struct Slot {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // device time of the launch (launch log)
     double *pinned = nullptr;  // results / readout landing zone
     size_t pinned_doubles = 0;
     bool busy = false;
@@ -146,6 +147,8 @@ struct qsim_pool {
     int small_n = 16, max_batch = 512, k_small = 2, k_large_c64 = 4, k_large_c128 = 2;
     int n_building = 0, n_running = 0, n_done = 0, n_failed = 0, n_ready = 0;
     long long batches = 0, singles = 0;
+    cudaEvent_t ev_ref = nullptr;             // device time zero of the launch log
+    std::deque<qsim_pool_launch> launch_log;  // the most recent retired launches (guarded by mu)
 };
 
 namespace qsim {
@@ -290,10 +293,14 @@ void launch_small(qsim_pool *p, Slot &s, std::vector<PoolReq *> &group) {
     if (!p->arena->alloc(batch_plan_device_bytes(im.get()), &tb.off)) throw Error(QSIM_EBUSY, "arena full");
     tb.bytes = batch_plan_device_bytes(im.get());
     s.blocks.push_back(tb);
+    cudaError_t e = cudaEventRecord(s.ev_start, s.st);
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, cudaGetErrorString(e));
     s.batch = batch_instantiate(im.get(), addr(p, tb), s.pinned, s.st);
     batch_launch(s.batch, s.st);
     batch_enqueue_results(s.batch, s.st);
-    cudaError_t e = cudaEventRecord(s.ev, s.st);
+    e = cudaEventRecord(s.ev_end, s.st);
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, cudaGetErrorString(e));
+    e = cudaEventRecord(s.ev, s.st);
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, cudaGetErrorString(e));
     s.reqs = group;
     s.busy = true;
@@ -312,7 +319,9 @@ void launch_large(qsim_pool *p, Slot &s, PoolReq *r) {
     if (!p->arena->alloc(scr, &sb.off)) throw Error(QSIM_EBUSY, "arena full");
     sb.bytes = scr;
     s.blocks.push_back(sb);
-    cudaError_t e = cudaMemcpyAsync(addr(p, mb), blob.data(), blob.size(), cudaMemcpyHostToDevice, s.st);
+    cudaError_t e = cudaEventRecord(s.ev_start, s.st);
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, cudaGetErrorString(e));
+    e = cudaMemcpyAsync(addr(p, mb), blob.data(), blob.size(), cudaMemcpyHostToDevice, s.st);
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("matrix upload: ") + cudaGetErrorString(e));
     attach_external_blob(r->fused, dtype, addr(p, mb), blob.size());
     // only the data register is populated after the preparation (clock and ancilla |0>): the
@@ -321,6 +330,8 @@ void launch_large(qsim_pool *p, Slot &s, PoolReq *r) {
     apply_ops(r->state, r->n, dtype, r->fused, s.st, r->h->nb);
     readout_launch_async(r->state, dtype, r->n, r->h->nb, s.st, static_cast<double *>(addr(p, sb)), s.pinned,
                          s.pinned + 4);
+    e = cudaEventRecord(s.ev_end, s.st);
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, cudaGetErrorString(e));
     e = cudaEventRecord(s.ev, s.st);
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, cudaGetErrorString(e));
     s.reqs = {r};
@@ -342,10 +353,27 @@ void scheduler_loop(qsim_pool *p) {
             cudaError_t q = cudaEventQuery(s.ev);
             if (q == cudaErrorNotReady) continue;
             if (q != cudaSuccess) cudaGetLastError();
+            qsim_pool_launch rec{};
+            rec.slot = (int)(&s - p->slots.data());
+            rec.batched = s.large ? 0 : 1;
+            rec.n_requests = (int)s.reqs.size();
+            rec.first_ticket = s.reqs.empty() ? 0 : s.reqs.front()->id;
+            rec.last_ticket = s.reqs.empty() ? 0 : s.reqs.back()->id;
+            float t0 = 0.f, t1 = 0.f;
+            if (q == cudaSuccess && cudaEventElapsedTime(&t0, p->ev_ref, s.ev_start) == cudaSuccess &&
+                cudaEventElapsedTime(&t1, p->ev_ref, s.ev_end) == cudaSuccess) {
+                rec.t_start = 1e-3 * t0;
+                rec.t_end = 1e-3 * t1;
+            } else {
+                cudaGetLastError();
+                rec.t_start = rec.t_end = -1.0;
+            }
             collect(p, s, q);
             {
                 std::lock_guard<std::mutex> lk(p->mu);
                 publish(p, s.reqs, q);
+                p->launch_log.push_back(rec);
+                if (p->launch_log.size() > 4096) p->launch_log.pop_front();
             }
             p->cv_done.notify_all();
             s.reqs.clear();
@@ -481,9 +509,13 @@ int qsim_pool_create(size_t bytes, int n_builders, int n_streams, qsim_pool **ou
             s.pinned_doubles = std::max(pin, pin_batch);
             if (cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreate(&s.ev_start) != cudaSuccess || cudaEventCreate(&s.ev_end) != cudaSuccess ||
                 cudaMallocHost(&s.pinned, s.pinned_doubles * sizeof(double)) != cudaSuccess)
                 throw Error(QSIM_ECUDA, "creating pool streams / pinned buffers");
         }
+        if (cudaEventCreate(&p->ev_ref) != cudaSuccess || cudaEventRecord(p->ev_ref, p->slots[0].st) != cudaSuccess ||
+            cudaEventSynchronize(p->ev_ref) != cudaSuccess)
+            throw Error(QSIM_ECUDA, "creating the pool's reference event");
         qsim_pool *raw = p.get();
         for (int i = 0; i < n_builders; i++) raw->builders.emplace_back(builder_loop, raw);
         raw->scheduler = std::thread(scheduler_loop, raw);
@@ -600,6 +632,17 @@ int qsim_pool_get_info(qsim_pool *p, qsim_pool_info *o) {
     });
 }
 
+int qsim_pool_launch_log(qsim_pool *p, qsim_pool_launch *out, int capacity, int *count) {
+    return guarded([&] {
+        QSIM_REQUIRE(p != nullptr && out != nullptr && count != nullptr && capacity >= 0, "bad arguments");
+        std::lock_guard<std::mutex> lk(p->mu);
+        const int k = std::min<int>(capacity, (int)p->launch_log.size());
+        const size_t from = p->launch_log.size() - (size_t)k;
+        for (int i = 0; i < k; i++) out[i] = p->launch_log[from + i];
+        *count = k;
+    });
+}
+
 void qsim_pool_destroy(qsim_pool *p) {
     if (!p) return;
     {
@@ -619,10 +662,13 @@ void qsim_pool_destroy(qsim_pool *p) {
     for (Slot &s : p->slots) {
         if (s.st) cudaStreamSynchronize(s.st);
         if (s.ev) cudaEventDestroy(s.ev);
+        if (s.ev_start) cudaEventDestroy(s.ev_start);
+        if (s.ev_end) cudaEventDestroy(s.ev_end);
         if (s.st) cudaStreamDestroy(s.st);
         if (s.pinned) cudaFreeHost(s.pinned);
     }
     p->reqs.clear();
+    if (p->ev_ref) cudaEventDestroy(p->ev_ref);
     if (p->arena_base) cudaFree(p->arena_base);
     delete p;
 }

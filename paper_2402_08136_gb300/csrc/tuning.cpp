@@ -20,17 +20,24 @@
 namespace qsim {
 namespace {
 
-std::atomic<int> g_tune[2][QSIM_TUNE_COUNT];
+// [dtype][size class][key]: the pass-kernel entries depend on the state size (a 31-qubit state
+// spans 8192 pages of 2 MiB, and passes on its top qubits meet other bounds than a 27-qubit one),
+// so each entry is kept per size class: up to 24 qubits, 25..28, 29 and more
+constexpr int kClasses = 3;
+std::atomic<int> g_tune[2][kClasses][QSIM_TUNE_COUNT];
 std::atomic<bool> g_tune_init{false};
 std::mutex g_tune_mu;
 
+int class_of(int n) { return n <= 24 ? 0 : (n <= 28 ? 1 : 2); }
+
 int default_value(int slot, int key) {
     switch (key) {
-        case QSIM_TUNE_DFT_TMA: return slot == 0 ? 1 : 0;  // complex64 only
+        case QSIM_TUNE_DFT_TMA: return slot == 0 ? 4 : 0;  // complex64 only
         case QSIM_TUNE_DFT_LANES: return 0;                // 0: 128-byte lane runs
         case QSIM_TUNE_DFT_PREFETCH: return 1;
         case QSIM_TUNE_DENSE_TC: return slot == 0 ? ((1 << 4) | (1 << 5) | (1 << 6) | (1 << 7)) : 0;
         case QSIM_TUNE_FUSE_WIDTH: return slot == 0 ? 4 : 2;
+        case QSIM_TUNE_DFT_L2PROMO: return 2;
         case QSIM_TUNE_TUNED: return 0;
         default: return 0;
     }
@@ -41,7 +48,8 @@ void ensure_init() {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     if (g_tune_init.load(std::memory_order_relaxed)) return;
     for (int s = 0; s < 2; s++)
-        for (int k = 0; k < QSIM_TUNE_COUNT; k++) g_tune[s][k].store(default_value(s, k));
+        for (int c = 0; c < kClasses; c++)
+            for (int k = 0; k < QSIM_TUNE_COUNT; k++) g_tune[s][c][k].store(default_value(s, k));
     g_tune_init.store(true, std::memory_order_release);
 }
 
@@ -49,7 +57,8 @@ int slot_of(int dtype) { return dtype == QSIM_C128 ? 1 : 0; }
 
 bool valid_value(int key, int v) {
     switch (key) {
-        case QSIM_TUNE_DFT_TMA: return v == 0 || v == 1;
+        case QSIM_TUNE_DFT_TMA: return v >= 0 && v <= 4;
+        case QSIM_TUNE_DFT_L2PROMO: return v >= 0 && v <= 3;
         case QSIM_TUNE_DFT_LANES: return v >= 0 && v <= 8;
         case QSIM_TUNE_DFT_PREFETCH: return v >= 0 && v <= 4;
         case QSIM_TUNE_DENSE_TC: return v >= 0 && v < 256;
@@ -61,31 +70,35 @@ bool valid_value(int key, int v) {
 
 }  // namespace
 
-int tune_get(int dtype, int key) {
+int tune_get(int dtype, int key, int n) {
     ensure_init();
-    return g_tune[slot_of(dtype)][key].load(std::memory_order_relaxed);
+    return g_tune[slot_of(dtype)][class_of(n)][key].load(std::memory_order_relaxed);
 }
 
 }  // namespace qsim
 
 using namespace qsim;
 
-extern "C" int qsim_tune_get(int dtype, int key, int *value) {
+extern "C" int qsim_tune_get(int dtype, int key, int n_qubits, int *value) {
     return guarded([&] {
         QSIM_REQUIRE(value != nullptr, "NULL argument");
         QSIM_REQUIRE(dtype == QSIM_C64 || dtype == QSIM_C128, "dtype must be QSIM_C64 or QSIM_C128");
         QSIM_REQUIRE(key >= 0 && key < QSIM_TUNE_COUNT, "unknown tuning key");
-        *value = tune_get(dtype, key);
+        QSIM_REQUIRE(n_qubits >= 1 && n_qubits <= 34, "n_qubits must be in 1..34");
+        *value = tune_get(dtype, key, n_qubits);
     });
 }
 
-extern "C" int qsim_tune_set(int dtype, int key, int value) {
+extern "C" int qsim_tune_set(int dtype, int key, int n_qubits, int value) {
     return guarded([&] {
         QSIM_REQUIRE(dtype == QSIM_C64 || dtype == QSIM_C128, "dtype must be QSIM_C64 or QSIM_C128");
         QSIM_REQUIRE(key >= 0 && key < QSIM_TUNE_COUNT, "unknown tuning key");
+        QSIM_REQUIRE(n_qubits >= 0 && n_qubits <= 34, "n_qubits must be in 0..34");
         QSIM_REQUIRE(valid_value(key, value), "value out of range for this tuning key");
         ensure_init();
-        g_tune[slot_of(dtype)][key].store(value, std::memory_order_relaxed);
+        for (int c = 0; c < kClasses; c++)
+            if (n_qubits == 0 || c == class_of(n_qubits))
+                g_tune[slot_of(dtype)][c][key].store(value, std::memory_order_relaxed);
     });
 }
 
@@ -94,7 +107,8 @@ extern "C" int qsim_tune_reset(void) {
         ensure_init();
         std::lock_guard<std::mutex> lk(g_tune_mu);
         for (int s = 0; s < 2; s++)
-            for (int k = 0; k < QSIM_TUNE_COUNT; k++) g_tune[s][k].store(default_value(s, k));
+            for (int c = 0; c < kClasses; c++)
+                for (int k = 0; k < QSIM_TUNE_COUNT; k++) g_tune[s][c][k].store(default_value(s, k));
     });
 }
 
@@ -165,6 +179,7 @@ extern "C" int qsim_autotune(void *state, int n_qubits, int dtype, void *stream,
         ensure_init();
         const int s = slot_of(dtype);
         const int n = n_qubits;
+        std::atomic<int> *T = g_tune[s][class_of(n)];
         qsim_tune_report rep;
         std::memset(&rep, 0, sizeof(rep));
         std::mt19937_64 rng(2402);
@@ -185,27 +200,28 @@ extern "C" int qsim_autotune(void *state, int n_qubits, int dtype, void *stream,
                 int tma, lanes, pf;
             };
             std::vector<Cand> cands;
-            if (dtype == QSIM_C64) cands.push_back({1, 0, 1});
+            if (dtype == QSIM_C64)
+                for (int v : {4, 3, 2, 1}) cands.push_back({v, 0, 1});
             for (int lanes : {0, 3, 5})
                 for (int pf : {0, 1}) cands.push_back({0, lanes, pf});
             double best = 1e300;
             Cand bc = cands.front();
             for (const Cand &c : cands) {
-                g_tune[s][QSIM_TUNE_DFT_TMA].store(c.tma);
-                g_tune[s][QSIM_TUNE_DFT_LANES].store(c.lanes);
-                g_tune[s][QSIM_TUNE_DFT_PREFETCH].store(c.pf);
+                T[QSIM_TUNE_DFT_TMA].store(c.tma);
+                T[QSIM_TUNE_DFT_LANES].store(c.lanes);
+                T[QSIM_TUNE_DFT_PREFETCH].store(c.pf);
                 const double ms = time_apply(state, n, dtype, ch.c, st, 3);
                 if (ms < best) best = ms, bc = c;
             }
-            g_tune[s][QSIM_TUNE_DFT_TMA].store(bc.tma);
-            g_tune[s][QSIM_TUNE_DFT_LANES].store(bc.lanes);
-            g_tune[s][QSIM_TUNE_DFT_PREFETCH].store(bc.pf);
+            T[QSIM_TUNE_DFT_TMA].store(bc.tma);
+            T[QSIM_TUNE_DFT_LANES].store(bc.lanes);
+            T[QSIM_TUNE_DFT_PREFETCH].store(bc.pf);
             rep.dft_ms = best / 3.0;
         }
         // 2. dense gates of 4..6 targets (complex64): tensor cores or SIMT, per width (bit 7, the
         //    real 7-target tensor-core kernel, keeps its value)
         if (dtype == QSIM_C64) {
-            int mask = g_tune[s][QSIM_TUNE_DENSE_TC].load() & (1 << 7);
+            int mask = T[QSIM_TUNE_DENSE_TC].load() & (1 << 7);
             for (int k = 4; k <= 6; k++) {
                 CircuitHolder ch(n);
                 for (int g = 0; g < 3; g++) {
@@ -220,13 +236,13 @@ extern "C" int qsim_autotune(void *state, int n_qubits, int dtype, void *stream,
                 }
                 double t[2];
                 for (int use = 0; use < 2; use++) {
-                    g_tune[s][QSIM_TUNE_DENSE_TC].store(mask | (use ? (1 << k) : 0));
+                    T[QSIM_TUNE_DENSE_TC].store(mask | (use ? (1 << k) : 0));
                     t[use] = time_apply(state, n, dtype, ch.c, st, 2);
                 }
                 if (t[1] < t[0]) mask |= 1 << k;
                 rep.dense_ms[k - 4] = std::min(t[0], t[1]) / 3.0;
             }
-            g_tune[s][QSIM_TUNE_DENSE_TC].store(mask);
+            T[QSIM_TUNE_DENSE_TC].store(mask);
         }
         // 3. fusion width for gate-level circuits: a layer of random 1- and 2-qubit gates on the
         //    lowest 12 qubits (the shape of the phase estimation's gate-level QFT), fused at each
@@ -259,10 +275,10 @@ extern "C" int qsim_autotune(void *state, int n_qubits, int dtype, void *stream,
                 rep.fuse_ms[k - 2] = ms;
                 if (ms < best) best = ms, bk = k;
             }
-            g_tune[s][QSIM_TUNE_FUSE_WIDTH].store(bk);
+            T[QSIM_TUNE_FUSE_WIDTH].store(bk);
         }
-        g_tune[s][QSIM_TUNE_TUNED].store(1);
-        for (int k = 0; k < QSIM_TUNE_COUNT; k++) rep.values[k] = g_tune[s][k].load();
+        T[QSIM_TUNE_TUNED].store(1);
+        for (int k = 0; k < QSIM_TUNE_COUNT; k++) rep.values[k] = T[k].load();
         rep.n_qubits = n;
         if (out) *out = rep;
     });

@@ -325,14 +325,20 @@ def test_noalloc_readout_rejects_a_slice_beyond_its_scratch(qs):
 
 
 def test_kernel_choice_table(qs):
-    """The table that replaces environment knobs: defaults, set, range checks, reset."""
+    """The table that replaces environment knobs: defaults, per-size-class entries, range checks,
+    reset."""
     t = qs.qsim_tune_table()
-    assert t["c64"]["dft_tma"] == 1 and t["c128"]["dft_tma"] == 0
-    assert t["c64"]["fuse_width"] == 4 and t["c64"]["tuned"] == 0
-    assert t["c64"]["dense_tc"] == (1 << 4) | (1 << 5) | (1 << 6) | (1 << 7)
+    for cls in ("le24", "25to28", "ge29"):
+        assert t["c64"][cls]["dft_tma"] == 4 and t["c128"][cls]["dft_tma"] == 0
+        assert t["c64"][cls]["fuse_width"] == 4 and t["c64"][cls]["tuned"] == 0
+        assert t["c64"][cls]["dense_tc"] == (1 << 4) | (1 << 5) | (1 << 6) | (1 << 7)
     qs.qsim_tune_set(qs.QSIM_C64, qs.QSIM_TUNE_FUSE_WIDTH, 3)
+    qs.qsim_tune_set(qs.QSIM_C64, qs.QSIM_TUNE_DFT_TMA, 1, n_qubits=31)   # one size class only
     try:
         assert qs.qsim_tune_get(qs.QSIM_C64, qs.QSIM_TUNE_FUSE_WIDTH) == 3
+        assert qs.qsim_tune_get(qs.QSIM_C64, qs.QSIM_TUNE_DFT_TMA, 30) == 1
+        assert qs.qsim_tune_get(qs.QSIM_C64, qs.QSIM_TUNE_DFT_TMA, 27) == 4
+        assert qs.qsim_tune_get(qs.QSIM_C64, qs.QSIM_TUNE_DFT_TMA, 20) == 4
         # qsim_fuse(max_k = 0) takes the table's width
         n = 6
         c = qs.Circuit(n)
@@ -340,11 +346,14 @@ def test_kernel_choice_table(qs):
         for q in range(n):
             c.add_gate([q], H)
         assert qs.qsim_fuse(c, 0).info()["max_k"] == 3
-        for key, bad in ((qs.QSIM_TUNE_FUSE_WIDTH, 7), (qs.QSIM_TUNE_DFT_TMA, 2), (99, 1)):
+        for key, bad in ((qs.QSIM_TUNE_FUSE_WIDTH, 7), (qs.QSIM_TUNE_DFT_TMA, 5), (99, 1)):
             with pytest.raises(qs.QsimError):
                 qs.qsim_tune_set(qs.QSIM_C64, key, bad)
         with pytest.raises(qs.QsimError):
             qs.qsim_tune_get(3, 0)
+        with pytest.raises(qs.QsimError):
+            qs.qsim_tune_get(qs.QSIM_C64, 0, 35)
     finally:
         qs.qsim_tune_reset()
     assert qs.qsim_tune_get(qs.QSIM_C64, qs.QSIM_TUNE_FUSE_WIDTH) == 4
+    assert qs.qsim_tune_get(qs.QSIM_C64, qs.QSIM_TUNE_DFT_TMA, 31) == 4

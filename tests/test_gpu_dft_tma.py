@@ -1,5 +1,6 @@
-"""The complex64 Fourier / Walsh-Hadamard pass with bulk-copy (TMA) tiles against the FP64
-oracle, and against the thread-load kernel, both selected through the kernel-choice table.
+"""The complex64 Fourier / Walsh-Hadamard pass with bulk-copy (TMA) tiles (bulk stores, or
+thread stores with the next tile's load issued early) against the FP64 oracle, and against the
+thread-load kernel, each selected through the kernel-choice table.
 
 Shapes the bulk-copy kernel takes: a contiguous field of 9 or 10 qubits starting at qubit 3 or
 above (the lanes are qubits 0..2), with the twiddle before or after the transform or none,
@@ -43,7 +44,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("tma", [1, 0])
+@pytest.mark.parametrize("tma", [4, 3, 2, 1, 0])
 @pytest.mark.parametrize("case", list(range(len(CASES))))
 def test_pass_matches_oracle_with_either_kernel(qs, tma, case):
     n, field, src, sign, pre, walsh = CASES[case]
@@ -77,17 +78,18 @@ def test_both_kernels_agree_on_a_large_pass(qs):
     st0 = synth.gaussian_state_torch(5, n, C64, "cuda", normalize=True)
     c = qs.Circuit(n).add_dft(list(range(14, 24)), -1, list(range(4, 14)))
     outs = []
-    for tma in (1, 0):
+    for tma in (4, 3, 2, 1, 0):
         qs.qsim_tune_set(qs.QSIM_C64, qs.QSIM_TUNE_DFT_TMA, tma)
         st = st0.clone()
         qs.qsim_apply(st, c)
         torch.cuda.synchronize()
         outs.append(st)
     qs.qsim_tune_reset()
-    assert float((outs[0] - outs[1]).abs().max()) <= 1e-6
+    for o in outs[1:]:
+        assert float((outs[0] - o).abs().max()) <= 1e-6
 
 
-@pytest.mark.parametrize("tma", [1, 0])
+@pytest.mark.parametrize("tma", [4, 3, 2, 1, 0])
 def test_hhl_with_ten_qubit_clock_fields_matches_oracle(qs, tma):
     """A solve whose clock register splits into two 9-qubit fields (m = 18, qubits 3..11 and
     12..20): the passes with the structured phase on their inputs / outputs and the inversion

@@ -2,6 +2,7 @@
 memory-budget admission; failures injected on the host (poisoned systems, a request larger
 than the pool, a wait that times out, an unknown ticket).  No test faults or hangs a GPU."""
 import math
+import time
 
 import numpy as np
 import pytest
@@ -149,3 +150,66 @@ def test_pool_completion_queue_hands_out_each_ticket_once(qs):
     for t in seen:
         assert pool.poll(t) is not None
     pool.close()
+
+
+def test_pool_launches_overlap_on_the_device(qs):
+    """Continuous batching, not a queue: launches on different stream slots run at the same time
+    (their device-time intervals, from CUDA events on each slot's stream, intersect), and both
+    batched and full-GPU launches take part."""
+    items = stream_items(60, max_n=20, seed=31)
+    pool = qs.Pool(1 << 30, n_builders=4, n_streams=4)
+    res = run_all(pool, items, qs.QSIM_C64)
+    log = pool.launch_log()
+    pool.close()
+    assert all(r is not None for r in res)
+    assert {e["batched"] for e in log} == {0, 1}
+    assert sum(e["n_requests"] for e in log) == len(items)
+    ok = [e for e in log if e["t_start"] >= 0]
+    overlaps = 0
+    for i, a in enumerate(ok):
+        for b in ok[i + 1:]:
+            if a["slot"] != b["slot"] and a["t_start"] < b["t_end"] and b["t_start"] < a["t_end"]:
+                overlaps += 1
+    assert overlaps >= 1, "no two launches on different streams overlapped"
+
+
+def test_pool_admits_new_work_while_earlier_work_runs(qs):
+    """Mid-run admission under a tight memory budget: the arena holds two 20-qubit complex64
+    states (8 MiB each) at a time; a first wave of four requests is on the GPU when a second
+    wave of four arrives.  Second-wave requests are admitted as first-wave memory frees up
+    (a second-wave launch starts before the last first-wave launch has ended), the arena's peak
+    stays within its size, and every result is correct (same as alone)."""
+    rng = np.random.default_rng(13)
+    probs = []
+    for _ in range(8):
+        A, b = synth.contingency_system(rng, 2 ** 3 + 1)
+        probs.append(dict(A=A, b=b, m=16))                    # 3 + 16 + 1 = 20 qubits
+    pool = qs.Pool(20 << 20, n_builders=2, n_streams=4)
+    wave1 = [pool.submit(p["A"], p["b"], p["m"]) for p in probs[:4]]
+    # the second wave arrives once the first is on the GPU
+    for _ in range(2000):
+        if pool.info()["running"] > 0:
+            break
+        time.sleep(0.001)
+    assert pool.info()["running"] > 0
+    wave2 = [pool.submit(p["A"], p["b"], p["m"]) for p in probs[4:]]
+    out = {}
+    for t in wave1 + wave2:
+        pool.wait(t, 120.0)
+        out[t] = pool.poll(t)
+    info = pool.info()
+    log = pool.launch_log()
+    # each request alone, for the comparison
+    alone = []
+    for p in probs:
+        t = pool.submit(p["A"], p["b"], p["m"])
+        pool.wait(t, 120.0)
+        alone.append(pool.poll(t))
+    pool.close()
+    assert info["bytes_peak"] <= 20 << 20 and info["done"] == 8
+    end1 = max(e["t_end"] for e in log if e["first_ticket"] in wave1)
+    start2 = min(e["t_start"] for e in log if e["first_ticket"] in wave2)
+    assert start2 < end1, "the second wave waited for the whole first wave"
+    for a, t in zip(alone, wave1 + wave2):
+        b = out[t]
+        assert np.max(np.abs(a["x"] - b["x"])) <= 1e-12 * max(1.0, np.max(np.abs(b["x"])))
