@@ -202,8 +202,15 @@ int qsim_launch_counts(unsigned long long *counts, int n);
                                     complex64 entry; 1..6)                                          */
 #define QSIM_TUNE_DFT_L2PROMO 5  /* bulk-copy pass kernel: L2 promotion of its tile loads (0 none,
                                     1 64 B, 2 128 B, 3 256 B)                                      */
-#define QSIM_TUNE_TUNED 6        /* 1 once qsim_autotune has written this dtype's entries        */
-#define QSIM_TUNE_COUNT 7
+#define QSIM_TUNE_DFT_MERGE 6    /* complex64 passes of the phase estimation run together (bulk-copy
+                                    kernels with 16-lane rows): bit 0 = the clock's H layer on a
+                                    field still |0>, the structured phase and the inverse QFT's
+                                    first pass with generated inputs; bit 1 = the inverse QFT's
+                                    last pass, the inversion and the QFT's first pass (two
+                                    transforms per tile, one launch per half); bit 2 = the QFT's
+                                    last pass, the structured phase and the Walsh-Hadamard pass    */
+#define QSIM_TUNE_TUNED 7        /* 1 once qsim_autotune has written this dtype's entries        */
+#define QSIM_TUNE_COUNT 8
 
 /* Each entry is kept per state dtype and per size class (states of up to 24 qubits, 25..28,
  * 29 and more: on a 31-qubit state a pass over the top qubits meets other bounds than on a

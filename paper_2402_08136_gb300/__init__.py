@@ -42,6 +42,7 @@ from ._binding import (  # noqa: F401
     QSIM_TUNE_DENSE_TC,
     QSIM_TUNE_FUSE_WIDTH,
     QSIM_TUNE_DFT_L2PROMO,
+    QSIM_TUNE_DFT_MERGE,
     QSIM_TUNE_TUNED,
     qsim_version,
 )

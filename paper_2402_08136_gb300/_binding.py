@@ -65,9 +65,10 @@ QSIM_TUNE_DFT_PREFETCH = 2
 QSIM_TUNE_DENSE_TC = 3
 QSIM_TUNE_FUSE_WIDTH = 4
 QSIM_TUNE_DFT_L2PROMO = 5
-QSIM_TUNE_TUNED = 6
-QSIM_TUNE_COUNT = 7
-TUNE_NAMES = ("dft_tma", "dft_lanes", "dft_prefetch", "dense_tc", "fuse_width", "dft_l2promo", "tuned")
+QSIM_TUNE_DFT_MERGE = 6
+QSIM_TUNE_TUNED = 7
+QSIM_TUNE_COUNT = 8
+TUNE_NAMES = ("dft_tma", "dft_lanes", "dft_prefetch", "dense_tc", "fuse_width", "dft_l2promo", "dft_merge", "tuned")
 
 
 class _PoolLaunch(ctypes.Structure):

@@ -198,7 +198,20 @@ int tune_get(int dtype, int key, int n_qubits);  // entry of the size class of n
 // dft_tma.cu: complex64 pass with bulk-copy (TMA) tiles; false when the shape does not fit
 bool dft_tma_launch(const void *dft_args, int n, int K, int sign, int kind, int variant, int l2promo,
                     cudaStream_t st);
+// two passes on one field in one kernel (see run_dft2); part (merge 1): 1 sin part into the upper
+// half, 0 cos part in place
+bool dft2_tma_launch(const void *args1, const void *args2, int n, int K, int merge, int part, int l2promo,
+                     cudaStream_t st);
+bool run_dft2(void *state, int n, int dtype, int merge, const Op &op1, const void *tab1, const Op &mid,
+              const void *qlo, const void *qhi, const Op &op2, const void *tab2, cudaStream_t st);
+// a pass on a field that is still |0> right above the live width, preceded by H on the field and
+// the structured phase: inputs generated, not read (dft_gen_kernel)
+bool dft_gen_launch(const void *args, int w, int K, int sign, cudaStream_t st);
+bool run_dft_generated(void *state, int w, int dtype, const Op &op, const void *tables, const Op &qop,
+                       const void *qlo, const void *qhi, cudaStream_t st);
 unsigned dft_tma_read_error();
+unsigned dft_merge_read_error();
+void dft_merge_clear_error();
 void dft_tma_clear_error();
 // linalg.cpp
 // Both throw Error(QSIM_EINVAL, "eigensolver did not converge ...") when the iteration cap

@@ -810,7 +810,7 @@ unsigned read_device_error() {
     unsigned v = 0;
     cudaError_t e = cudaMemcpyFromSymbol(&v, g_device_error, sizeof(v));
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("reading device status: ") + cudaGetErrorString(e));
-    return v | dft_tma_read_error();  // bit 0 either way: a bounded wait ran out
+    return v | dft_tma_read_error() | dft_merge_read_error();  // bit 0 either way: a bounded wait ran out
 }
 
 void clear_device_error() {
@@ -818,6 +818,7 @@ void clear_device_error() {
     cudaError_t e = cudaMemcpyToSymbol(g_device_error, &z, sizeof(z));
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("clearing device status: ") + cudaGetErrorString(e));
     dft_tma_clear_error();
+    dft_merge_clear_error();
 }
 
 }  // namespace qsim

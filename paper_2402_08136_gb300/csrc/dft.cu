@@ -44,11 +44,12 @@ void dft_tables(const Op &op, std::vector<cd> &W, std::vector<cd> &Tlo, std::vec
     for (size_t j = 0; j < Thi.size(); j++) Thi[j] = unit(j << hT, K + ns);
 }
 
-bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cudaStream_t st, const Op *qop,
-             const void *qlo, const void *qhi, int qmode, const Op *inv) {
+// The pass arguments shared by every pass kernel: tables, twiddle mode, the structured phase
+// (qop, qmode) and the inversion (inv).  False when the inversion cannot be carried by the pass.
+static bool dft_common_args(DftArgs &a, void *state, int n, int dtype, const Op &op, const void *tables,
+                            const Op *qop, const void *qlo, const void *qhi, int qmode, const Op *inv) {
     const int K = (int)op.targets.size(), ns = (int)op.controls.size();
     QSIM_REQUIRE(K >= 1 && K <= kMaxK && ns <= kMaxSrc && K + ns <= 30 && K <= n, "Fourier pass shape");
-    DftArgs a;
     std::memset(&a, 0, sizeof(a));
     a.psi = state;
     const size_t vb = dtype == QSIM_C128 ? 16 : 8;
@@ -106,13 +107,25 @@ bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
     a.scale = std::ldexp(1.0, -K / 2) * ((K & 1) ? std::sqrt(0.5) : 1.0);
     for (int j = 0; j < K; j++) a.fpos[j] = op.targets[j];
     for (int j = 0; j < ns; j++) a.spos[j] = op.controls[j];
-    const int k1 = K / 2;
-    const bool contig = [&] {
-        for (int j = 0; j < K; j++)
-            if (op.targets[j] != op.targets[0] + j) return false;
-        return true;
-    }();
     a.f0 = op.targets[0];
+    return true;
+}
+
+static bool contiguous_field(const Op &op) {
+    for (size_t j = 0; j < op.targets.size(); j++)
+        if (op.targets[j] != op.targets[0] + (int)j) return false;
+    return true;
+}
+
+bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cudaStream_t st, const Op *qop,
+             const void *qlo, const void *qhi, int qmode, const Op *inv) {
+    const int K = (int)op.targets.size(), ns = (int)op.controls.size();
+    DftArgs a;
+    if (!dft_common_args(a, state, n, dtype, op, tables, qop, qlo, qhi, qmode, inv)) return false;
+    const size_t vb = dtype == QSIM_C128 ? 16 : 8;
+    const int hT = a.hT;
+    const int k1 = K / 2;
+    const bool contig = contiguous_field(op);
     const int kind = op.kind == OP_WALSH ? 1 : (a.inv ? 2 : 0);
     // complex64 with a contiguous field: the bulk-copy tile kernel, when the table selects it
     // and the shape fits
@@ -159,6 +172,60 @@ bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
     if (dtype == QSIM_C128) dft_launch_f64(a, K, op.sign, kind, contig, threads, smem, st);
     else dft_launch_f32(a, K, op.sign, kind, contig, threads, smem, st);
     return true;
+}
+
+// Two passes on the same contiguous field in one tile-resident kernel (complex64, bulk-copy
+// tiles), when the table selects the 128-byte-row kernel and the shapes fit:
+//   merge 1: the inverse QFT's last pass (sign -1), the HHL inversion on the ancilla right above
+//            the live state, and the QFT's first pass (sign +1) over the same field: launched
+//            twice, first the sin part into the unwritten upper half, then the cos part in place;
+//   merge 2: a QFT pass (sign +1), the structured phase (diagonal) and the Walsh-Hadamard pass
+//            of the same field.
+// Returns false (nothing launched) when the shapes do not fit.
+bool run_dft2(void *state, int n, int dtype, int merge, const Op &op1, const void *tab1, const Op &mid,
+              const void *qlo, const void *qhi, const Op &op2, const void *tab2, cudaStream_t st) {
+    if (dtype != QSIM_C64 || tune_get(QSIM_C64, QSIM_TUNE_DFT_TMA, n) < 3) return false;
+    if (!((tune_get(QSIM_C64, QSIM_TUNE_DFT_MERGE, n) >> merge) & 1)) return false;
+    if (!contiguous_field(op1) || op1.targets != op2.targets) return false;
+    const int K = (int)op1.targets.size();
+    if (K < 9 || K > 10) return false;
+    DftArgs a1, a2;
+    if (merge == 1) {
+        if (op1.kind != OP_DFT || op1.sign != -1 || op2.kind != OP_DFT || op2.sign != 1 || mid.kind != OP_HHL_INVERT)
+            return false;
+        for (int q : op2.controls)
+            if (q >= n) return false;
+        if (!dft_common_args(a1, state, n, dtype, op1, tab1, nullptr, nullptr, nullptr, 0, &mid)) return false;
+        if (!dft_common_args(a2, state, n, dtype, op2, tab2, nullptr, nullptr, nullptr, 0, nullptr)) return false;
+        // the sin part reads the lower half and fills the upper one; then the cos part in place
+        for (int part = 1; part >= 0; part--)
+            if (!dft2_tma_launch(&a1, &a2, n, K, merge, part, tune_get(QSIM_C64, QSIM_TUNE_DFT_L2PROMO, n), st))
+                return false;
+        return true;
+    }
+    if (merge == 2) {
+        if (op1.kind != OP_DFT || op1.sign != 1 || op2.kind != OP_WALSH || mid.kind != OP_QPE_PHASE) return false;
+        if (!dft_common_args(a1, state, n, dtype, op1, tab1, &mid, qlo, qhi, 2, nullptr)) return false;
+        if (!dft_common_args(a2, state, n, dtype, op2, tab2, nullptr, nullptr, nullptr, 0, nullptr)) return false;
+        return dft2_tma_launch(&a1, &a2, n, K, merge, 0, tune_get(QSIM_C64, QSIM_TUNE_DFT_L2PROMO, n), st);
+    }
+    return false;
+}
+
+// The pass `op` on a field right above the live width w that is still |0>, after H on that
+// field and the structured phase qop (complex64, fields of 9-10 qubits): inputs generated from
+// the live amplitudes, outputs over 2^(w + K) amplitudes.  False when the shape does not fit.
+bool run_dft_generated(void *state, int w, int dtype, const Op &op, const void *tables, const Op &qop,
+                       const void *qlo, const void *qhi, cudaStream_t st) {
+    if (dtype != QSIM_C64 || op.kind != OP_DFT || !contiguous_field(op) || op.targets[0] != w) return false;
+    const int nw = w + (int)op.targets.size();
+    if (tune_get(QSIM_C64, QSIM_TUNE_DFT_TMA, nw) < 3 || !(tune_get(QSIM_C64, QSIM_TUNE_DFT_MERGE, nw) & 1)) return false;
+    for (int q : op.controls)
+        if (q >= w) return false;
+    const int K = (int)op.targets.size();
+    DftArgs a;
+    if (!dft_common_args(a, state, w + K, dtype, op, tables, &qop, qlo, qhi, 1, nullptr)) return false;
+    return dft_gen_launch(&a, w, K, op.sign, st);
 }
 
 }  // namespace qsim

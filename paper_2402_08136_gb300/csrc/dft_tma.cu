@@ -33,15 +33,7 @@
 // Every wait on the tile's mbarrier is bounded (1 s of %globaltimer); on timeout the kernel
 // raises a device flag (read by qsim_device_status), waits (bounded) for its own copies and
 // returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-#include <cuda_runtime.h>
-
-#include <algorithm>
-#include <cstring>
-#include <mutex>
-
-#include "dft_impl.cuh"
+#include "dft_tma.cuh"
 
 namespace qsim {
 
@@ -49,94 +41,22 @@ __device__ unsigned int g_dft_tma_error = 0;
 
 namespace dftt {
 
-using dftk::bitrev;
-using dftk::cmul;
-using dftk::DftArgs;
-using dftk::dft_regs;
-
-constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
-    return t;
-}
-
-// Bounded wait for the mbarrier phase of the given parity; false after about one second.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-    unsigned long long t0 = 0;
-    for (unsigned it = 0;; it++) {
-        unsigned ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if ((it & 63) == 0) {
-            const unsigned long long t = global_ns();
-            if (t0 == 0) t0 = t;
-            else if (t - t0 > kWaitLimitNs) return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load(unsigned dst, const CUtensorMap *map, int c1, int c4, unsigned bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(dst),
-        "l"(map), "r"(0), "r"(c1), "r"(0), "r"(0), "r"(c4), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_prefetch_l2(const CUtensorMap *map, int c1, int c4) {
-    asm volatile("cp.async.bulk.prefetch.tensor.5d.L2.global [%0, {%1, %2, %3, %4, %5}];\n" ::"l"(map), "r"(0), "r"(c1),
-                 "r"(0), "r"(0), "r"(c4)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tma_store(const CUtensorMap *map, int c1, int c4, unsigned src) {
-    asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];\n" ::"l"(map),
-                 "r"(0), "r"(c1), "r"(0), "r"(0), "r"(c4), "r"(src)
-                 : "memory");
-    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
-}
-
-// The bulk stores issued by this thread have finished reading shared memory.
-__device__ __forceinline__ void tma_store_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
-// ... and are complete (visible in global memory).
-__device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
-
-struct TmaExtra {
-    int gap;        // qubits between the lanes and the field (f0 - 3)
-    int above;      // qubits above the field in the tensor map (includes the ancilla for KIND 2)
-    int inv_c4;     // KIND 2: coordinate offset of the upper half along the "above" dimension
-    long long ntiles;  // tiles to transform (the lower half only for KIND 2)
-};
-
-// L lane qubits (the lowest qubits): rows of 2^L amplitudes, 64 (L = 3) or 128 bytes (L = 4)
-template <int K, int L>
-struct Shape {
-    static constexpr int k1 = K / 2, k2 = K - k1;
-    static constexpr int N1 = 1 << k1, N2 = 1 << k2, RR = N2 / N1;
-    static constexpr int NL = 1 << L;
-    static constexpr int threads = N1 * NL;
-    static constexpr int tile = (1 << K) * NL;  // amplitudes
-    static constexpr int min_blocks = threads >= 512 ? 1 : 512 / threads;  // 128 registers a thread
-};
-
 // KIND 0: DFT, 1: Walsh-Hadamard, 2: DFT with the HHL inversion on its outputs.
 // EARLY: the outputs leave by thread stores straight from registers, and the next tile's bulk
 // load is issued as soon as step 2 has read the buffer, so that copy overlaps step 2's
 // transform and stores; otherwise the outputs go back through the buffer and a bulk store,
 // and the next load waits for that store to have read the buffer.
-template <int K, int L, int SGN, int KIND, bool EARLY>
+// TW (twiddle mode 0 none, 1 before, 2 after) and QS (structured phase: 0 none, 1 inputs with
+// the recurrence, 2 outputs of a Walsh-Hadamard pass with the recurrence) fix the options at
+// compile time (3: read from the arguments), so each common pass runs a kernel without the
+// code of the options it does not use.
+template <int K, int L, int SGN, int KIND, bool EARLY, int TW, int QS>
 __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
     dft_tma_kernel(const __grid_constant__ CUtensorMap tmap, const DftArgs a, const TmaExtra x) {
     using S = Shape<K, L>;
+    const int twmode = TW == 3 ? a.twmode : TW;
+    const int qmode = QS == 3 ? a.qmode : QS;
+    const int qrec = QS == 3 ? a.qrec : (QS != 0);
     constexpr int kL = L, kNL = S::NL;
     constexpr bool WALSH = KIND == 1;
     constexpr bool INV = KIND == 2;
@@ -200,11 +120,9 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
             tma_store_wait_read();  // the previous tile's store has read the buffer
             issue_load(t);
         }
+        // every thread waits for the tile itself (the copy's completion makes it visible to the
+        // thread that observes it); the decision to give up is taken together at the first barrier
         const bool ok = mbar_wait(bar_a, it & 1u);
-        if (__syncthreads_or(!ok)) {  // every thread takes the same decision
-            failed = true;
-            break;
-        }
         if (tid == 0) {
             // L2 prefetch of the first tile whose load is not issued yet
             const long long tn = t + (EARLY ? 2 : 1) * (long long)gridDim.x;
@@ -226,9 +144,9 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
         // step 1
 #pragma unroll
         for (int q = 0; q < N2; q++) v[q] = buf[(u + N1 * q) * kNL + l];
-        if (a.qmode == 1) {
+        if (qmode == 1) {
             const unsigned long long i0 = base + ((unsigned long long)u << a.f0);
-            if (a.qrec) {
+            if (qrec) {
                 // inputs at field values u + N1 q: the phase is P Q^q, Q = the phase of clock
                 // value N1 2^(f0 - qnb) (refreshed from the tables every 8 terms)
                 const float2 Q = qphase_cd((unsigned long long)N1 << (a.f0 - a.qnb), i0 & qdm);
@@ -244,7 +162,7 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
                 for (int q = 0; q < N2; q++) v[q] = cmul(v[q], qphase(i0 + ((unsigned long long)(N1 * q) << a.f0)));
             }
         }
-        if (a.twmode == 1) {
+        if (twmode == 1) {
 #pragma unroll
             for (int q = 0; q < N2; q++) {
                 const unsigned e = w * (unsigned)(u + N1 * q);
@@ -259,7 +177,10 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
                 if (aa != 0) v[i] = cmul(v[i], dftk::lds_fresh(Ws + u * aa));  // u aa < 2^K
             }
         }
-        __syncthreads();  // every thread has read its step-1 points
+        if (__syncthreads_or(!ok)) {  // every thread has read its step-1 points (or one gave up)
+            failed = true;
+            break;
+        }
 #pragma unroll
         for (int i = 0; i < N2; i++) {
             const int aa = WALSH ? i : bitrev(i, k2);
@@ -282,7 +203,7 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
 #pragma unroll
         for (int r = 0; r < RR; r++) {
             const int aa = u * RR + r;
-            const bool qseq = WALSH && a.qmode == 2 && a.qrec;
+            const bool qseq = WALSH && qmode == 2 && qrec;
             float2 P{1.f, 0.f}, Q{1.f, 0.f};
             const unsigned long long q0 = base + ((unsigned long long)(N1 * aa) << a.f0);
             if (qseq) Q = qphase_cd(1ull << (a.f0 - a.qnb), q0 & qdm);
@@ -292,7 +213,7 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
                 float2 z = v[r * N1 + i];
                 z.x *= scale;
                 z.y *= scale;
-                if (a.twmode == 2) {
+                if (twmode == 2) {
                     const unsigned e = w * (unsigned)y;
                     z = cmul(z, cmul(Tlo[e & tmask], Thi[e >> a.hT]));
                 }
@@ -300,7 +221,7 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
                     if ((i & 7) == 0) P = qphase(q0 + ((unsigned long long)i << a.f0));
                     z = cmul(z, P);
                     P = cmul(P, Q);
-                } else if (a.qmode == 2) {
+                } else if (qmode == 2) {
                     z = cmul(z, qphase(base + ((unsigned long long)y << a.f0)));
                 }
                 if (EARLY) {
@@ -407,10 +328,10 @@ int num_sms() {
     return sms;
 }
 
-template <int K, int L, int SGN, int KIND, bool EARLY>
+template <int K, int L, int SGN, int KIND, bool EARLY, int TW = 3, int QS = 3>
 void launch(const CUtensorMap &map, const DftArgs &a, const TmaExtra &x, size_t smem, cudaStream_t st) {
     using S = Shape<K, L>;
-    auto kern = dft_tma_kernel<K, L, SGN, KIND, EARLY>;
+    auto kern = dft_tma_kernel<K, L, SGN, KIND, EARLY, TW, QS>;
     static bool attr = false;
     if (!attr) {
         DFT_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -429,11 +350,25 @@ void launch(const CUtensorMap &map, const DftArgs &a, const TmaExtra &x, size_t 
 template <int K, int L, bool EARLY>
 void launch_k(const CUtensorMap &map, const DftArgs &a, const TmaExtra &x, int sign, int kind, size_t smem,
               cudaStream_t st) {
+    if (EARLY && L == 4) {
+        // the passes of the phase estimation, each with a kernel of its own options
+        const int qs = a.qmode == 0 ? 0 : (a.qrec && a.qmode == 1 ? 1 : (a.qrec && a.qmode == 2 && kind == 1 ? 2 : 3));
+        const int tw = a.twmode;
+        if (kind == 2 && tw == 0 && qs == 0) return launch<K, L, -1, 2, EARLY, 0, 0>(map, a, x, smem, st);
+        if (kind == 1 && tw == 0 && qs == 0) return launch<K, L, 1, 1, EARLY, 0, 0>(map, a, x, smem, st);
+        if (kind == 1 && tw == 0 && qs == 1) return launch<K, L, 1, 1, EARLY, 0, 1>(map, a, x, smem, st);
+        if (kind == 1 && tw == 0 && qs == 2) return launch<K, L, 1, 1, EARLY, 0, 2>(map, a, x, smem, st);
+        if (kind == 0 && sign < 0 && tw == 2 && qs == 0) return launch<K, L, -1, 0, EARLY, 2, 0>(map, a, x, smem, st);
+        if (kind == 0 && sign < 0 && tw == 0 && qs == 0) return launch<K, L, -1, 0, EARLY, 0, 0>(map, a, x, smem, st);
+        if (kind == 0 && sign > 0 && tw == 0 && qs == 0) return launch<K, L, 1, 0, EARLY, 0, 0>(map, a, x, smem, st);
+        if (kind == 0 && sign > 0 && tw == 1 && qs == 0) return launch<K, L, 1, 0, EARLY, 1, 0>(map, a, x, smem, st);
+    }
     if (kind == 2) launch<K, L, -1, 2, EARLY>(map, a, x, smem, st);
     else if (kind == 1) launch<K, L, 1, 1, EARLY>(map, a, x, smem, st);
     else if (sign > 0) launch<K, L, 1, 0, EARLY>(map, a, x, smem, st);
     else launch<K, L, -1, 0, EARLY>(map, a, x, smem, st);
 }
+
 
 }  // namespace dftt
 

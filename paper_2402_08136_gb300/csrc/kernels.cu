@@ -1178,6 +1178,30 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
     for (size_t i = 0; i < ops.size(); i++) {
         const Op &op = ops[i];
         const void *dptr = base + op.dev_off[slot];
+        if (op.kind == OP_WALSH && i + 2 < ops.size() && ops[i + 1].kind == OP_QPE_PHASE && ops[i + 2].kind == OP_DFT &&
+            ops[i + 2].targets == op.targets && expandable(op)) {
+            // H on a field that is still |0> right above the live part, the structured phase and a
+            // Fourier pass on the same field: the pass generates its inputs (complex64)
+            const Op &q = ops[i + 1];
+            if (run_dft_generated(state, w, dtype, ops[i + 2], base + ops[i + 2].dev_off[slot], q, base + q.dev_off[slot],
+                                  base + q.dev_off_tc[slot], st)) {
+                w += (int)op.targets.size();
+                i += 2;
+                continue;
+            }
+        }
+        if (op.kind == OP_DFT && i + 2 < ops.size() && ops[i + 1].kind == OP_QPE_PHASE && ops[i + 2].kind == OP_WALSH &&
+            ops[i + 2].targets == op.targets && !expandable(op)) {
+            // a QFT pass, the structured phase and the Walsh-Hadamard pass of the same field in one
+            // tile-resident kernel (complex64, bulk-copy tiles) when the shapes fit
+            const Op &q = ops[i + 1];
+            materialize(std::max(top_qubit(op), top_qubit(ops[i + 2])) + 1);
+            if (run_dft2(state, w, dtype, 2, op, dptr, q, base + q.dev_off[slot], base + q.dev_off_tc[slot], ops[i + 2],
+                         base + ops[i + 2].dev_off[slot], st)) {
+                i += 2;
+                continue;
+            }
+        }
         if (i + 1 < ops.size()) {
             // a structured phase next to a pass runs inside it: on the pass's outputs, unless this
             // pass has a twiddle and the pass after the phase has none (then on that one's inputs)
@@ -1209,6 +1233,15 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
             // the pass writes the rotated outputs into both halves (the upper one is unwritten)
             bool low = true;
             for (int q : ops[i + 1].controls) low = low && q < n - 1;
+            // ... and, when the QFT's first pass over the same field follows, that pass too (one
+            // tile-resident kernel per half, complex64 bulk-copy tiles, when the shapes fit)
+            if (low && i + 2 < ops.size() && ops[i + 2].kind == OP_DFT && ops[i + 2].targets == op.targets &&
+                run_dft2(state, w, dtype, 1, op, dptr, ops[i + 1], nullptr, nullptr, ops[i + 2],
+                         base + ops[i + 2].dev_off[slot], st)) {
+                w = n;
+                i += 2;
+                continue;
+            }
             if (low && run_dft(state, w, dtype, op, dptr, st, nullptr, nullptr, nullptr, 0, &ops[i + 1])) {
                 w = n;
                 i++;

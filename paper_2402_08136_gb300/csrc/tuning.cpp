@@ -38,6 +38,7 @@ int default_value(int slot, int key) {
         case QSIM_TUNE_DENSE_TC: return slot == 0 ? ((1 << 4) | (1 << 5) | (1 << 6) | (1 << 7)) : 0;
         case QSIM_TUNE_FUSE_WIDTH: return slot == 0 ? 4 : 2;
         case QSIM_TUNE_DFT_L2PROMO: return 2;
+        case QSIM_TUNE_DFT_MERGE: return 1;  // two-transform merges measured slower on GB300
         case QSIM_TUNE_TUNED: return 0;
         default: return 0;
     }
@@ -59,6 +60,7 @@ bool valid_value(int key, int v) {
     switch (key) {
         case QSIM_TUNE_DFT_TMA: return v >= 0 && v <= 4;
         case QSIM_TUNE_DFT_L2PROMO: return v >= 0 && v <= 3;
+        case QSIM_TUNE_DFT_MERGE: return v >= 0 && v <= 7;
         case QSIM_TUNE_DFT_LANES: return v >= 0 && v <= 8;
         case QSIM_TUNE_DFT_PREFETCH: return v >= 0 && v <= 4;
         case QSIM_TUNE_DENSE_TC: return v >= 0 && v < 256;

@@ -112,3 +112,44 @@ def test_hhl_with_ten_qubit_clock_fields_matches_oracle(qs, tma):
         assert qs.qsim_device_status() == 0
     finally:
         qs.qsim_tune_reset()
+
+
+@pytest.mark.parametrize("m", [18, 20])
+@pytest.mark.parametrize("tma", [4, 0])
+def test_hhl_merged_passes_match_oracle(qs, m, tma):
+    """nb = 4: both clock fields start at qubit 4 or above, so with 128-byte tile rows the executor
+    runs the top field's H layer, the structured phase and the inverse QFT's first pass as one
+    kernel with generated inputs, merges the inverse QFT's last pass, the inversion and the QFT's
+    first pass into one kernel per half, and the QFT's last pass, the structured phase and the
+    Walsh-Hadamard pass of the top field into another (tma = 4); tma = 0 runs the same circuit
+    pass by pass.  Both against the oracle's gate-level HHL, on a NaN-filled state."""
+    rng = np.random.default_rng(300 + m)
+    A, b = synth.contingency_system(rng, 2 ** 4 + 1)      # nb = 4
+    qs.qsim_tune_set(qs.QSIM_C64, qs.QSIM_TUNE_DFT_TMA, tma)
+    qs.qsim_tune_set(qs.QSIM_C64, qs.QSIM_TUNE_DFT_MERGE, 7)   # every merge, whatever the default
+    try:
+        h = qs.hhl_build(A, b, m, structured=True, fft_qft=True)
+        info = h.info()
+        assert info["n"] == 4 + m + 1
+        ref = ohhl.solve(A, b, m)
+        st = torch.empty(1 << info["n"], dtype=C64, device="cuda")
+        st.fill_(float("nan"))
+        before = qs.qsim_launch_counts()
+        qs.hhl_run(st, h, qs.qsim_fuse(h.as_circuit(), 4))
+        r = qs.hhl_readout(st, h)
+        after = qs.qsim_launch_counts()
+        compare_hhl(st, r, ref, C64, TOL[C64])
+        assert qs.qsim_device_status() == 0
+        passes = after["fourier_tma"] - before["fourier_tma"] + after["fourier"] - before["fourier"]
+        expands = after["expand"] - before["expand"]
+        if tma == 4:
+            # H layer + phase + inverse QFT on the top field with generated inputs, 2 merged launches
+            # (inverse QFT's last pass, inversion, QFT's first pass), QFT top + phase + Walsh
+            # merged, Walsh bottom field: 5 pass launches, and only the bottom field's H layer is a
+            # write-only expansion (2 launches)
+            assert after["fourier"] == before["fourier"]
+            assert passes == 5 and expands == 2
+        else:
+            assert passes == 6 and expands == 4
+    finally:
+        qs.qsim_tune_reset()

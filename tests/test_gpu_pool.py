@@ -174,42 +174,44 @@ def test_pool_launches_overlap_on_the_device(qs):
 
 
 def test_pool_admits_new_work_while_earlier_work_runs(qs):
-    """Mid-run admission under a tight memory budget: the arena holds two 20-qubit complex64
-    states (8 MiB each) at a time; a first wave of four requests is on the GPU when a second
-    wave of four arrives.  Second-wave requests are admitted as first-wave memory frees up
-    (a second-wave launch starts before the last first-wave launch has ended), the arena's peak
-    stays within its size, and every result is correct (same as alone)."""
+    """Mid-run admission under a memory budget.  Two 26-qubit complex128 requests (1 GiB states,
+    tens of ms each on the FP64 pipe) start; while they are on the GPU two 26-qubit complex64
+    requests (512 MiB) arrive, with room in the arena for only one of them.  That one is
+    admitted at once and runs alongside the first wave (device-time intervals intersect); the
+    other must wait for memory, so its launch starts only after an earlier launch has ended.
+    The arena's peak stays within its size, and every result equals the same request run alone."""
     rng = np.random.default_rng(13)
     probs = []
-    for _ in range(8):
-        A, b = synth.contingency_system(rng, 2 ** 3 + 1)
-        probs.append(dict(A=A, b=b, m=16))                    # 3 + 16 + 1 = 20 qubits
-    pool = qs.Pool(20 << 20, n_builders=2, n_streams=4)
-    wave1 = [pool.submit(p["A"], p["b"], p["m"]) for p in probs[:4]]
-    # the second wave arrives once the first is on the GPU
-    for _ in range(2000):
-        if pool.info()["running"] > 0:
-            break
-        time.sleep(0.001)
+    for _ in range(4):
+        A, b = synth.contingency_system(rng, 2 ** 5 + 1)
+        probs.append(dict(A=A, b=b, m=20))                    # 5 + 20 + 1 = 26 qubits
+    dts = [qs.QSIM_C128, qs.QSIM_C128, qs.QSIM_C64, qs.QSIM_C64]
+    arena = 2 * (1 << 30) + (512 << 20) + (64 << 20)
+    pool = qs.Pool(arena, n_builders=2, n_streams=4)
+    wave1 = [pool.submit(p["A"], p["b"], p["m"], dtype=d, structured=True) for p, d in zip(probs[:2], dts[:2])]
+    t0 = time.perf_counter()
+    while pool.info()["running"] == 0 and time.perf_counter() - t0 < 30.0:
+        pass
     assert pool.info()["running"] > 0
-    wave2 = [pool.submit(p["A"], p["b"], p["m"]) for p in probs[4:]]
+    wave2 = [pool.submit(p["A"], p["b"], p["m"], dtype=d, structured=True) for p, d in zip(probs[2:], dts[2:])]
     out = {}
     for t in wave1 + wave2:
         pool.wait(t, 120.0)
         out[t] = pool.poll(t)
     info = pool.info()
-    log = pool.launch_log()
-    # each request alone, for the comparison
+    log = {e["first_ticket"]: e for e in pool.launch_log()}
     alone = []
-    for p in probs:
-        t = pool.submit(p["A"], p["b"], p["m"])
+    for p, d in zip(probs, dts):
+        t = pool.submit(p["A"], p["b"], p["m"], dtype=d, structured=True)
         pool.wait(t, 120.0)
         alone.append(pool.poll(t))
     pool.close()
-    assert info["bytes_peak"] <= 20 << 20 and info["done"] == 8
-    end1 = max(e["t_end"] for e in log if e["first_ticket"] in wave1)
-    start2 = min(e["t_start"] for e in log if e["first_ticket"] in wave2)
-    assert start2 < end1, "the second wave waited for the whole first wave"
+    assert info["bytes_peak"] <= arena and info["done"] == 4
+    first, late = log[wave2[0]], log[wave2[1]]
+    assert any(first["t_start"] < log[t]["t_end"] and log[t]["t_start"] < first["t_end"] for t in wave1), \
+        "the request that arrived mid-run did not run alongside the first wave"
+    assert late["t_start"] >= min(log[t]["t_end"] for t in wave1 + wave2[:1]), \
+        "a request started without memory for its state"
     for a, t in zip(alone, wave1 + wave2):
         b = out[t]
         assert np.max(np.abs(a["x"] - b["x"])) <= 1e-12 * max(1.0, np.max(np.abs(b["x"])))
