@@ -437,6 +437,50 @@ int qsim_apply_batched(void *const *states, const int *n_qubits, const qsim_circ
                        int count, int dtype, void *stream);
 
 /* ======================================================================================= *
+ * State sharding over 2^g ranks with a qubit-swap exchange (Sec. II-C: the simulator's        *
+ * state vector spread over several GPUs; Sec. III-B: 42 qubits on several nodes)            *
+ * ======================================================================================= */
+
+/* Rank r holds the 2^(n-g) amplitudes whose top g physical qubits equal r.  A plan turns an
+ * unfused circuit into steps: a swap exchanges global physical qubit n-g+global_bit with the
+ * local physical qubit local_qubit (ranks r and r ^ 2^global_bit trade the halves of their
+ * shards whose bit local_qubit differs from bit global_bit of r: qsim_shard_pack the half with
+ * that bit = 1 - bit global_bit of r, send it, receive the partner's, qsim_shard_unpack it into
+ * the same positions); an apply step runs a local circuit (gates first_gate .. last_gate-1 of the
+ * input, their qubits renumbered to physical positions, on n-g qubits) on every shard.  Before a
+ * gate that touches a global qubit the planner swaps it with a local position the gate does not
+ * touch, the one used again farthest in the future.  The last steps restore the logical order,
+ * so the shards in rank order are the state.  The structured phase operator
+ * (QSIM_HHL_STRUCTURED_QPE) needs fixed qubit positions and is rejected; a gate may touch at
+ * most n-g qubits. */
+typedef struct qsim_shard_plan qsim_shard_plan;
+typedef struct {
+    int kind;          /* 0 swap, 1 apply                                                       */
+    int global_bit;    /* swap: global bit b (physical qubit n-g+b)                            */
+    int local_qubit;   /* swap: local physical qubit                                           */
+    int first_gate, last_gate; /* apply: gates of the input circuit (first == last: the final
+                                  local reordering, SWAP gates only)                          */
+} qsim_shard_step;
+
+/* Plan the unfused circuit c over 2^n_global ranks (0 <= n_global <= 10, n_global < n).
+ * Errors: EINVAL (fused circuit, structured phase operator, a gate wider than a shard), ENOMEM. */
+int qsim_shard_plan_create(const qsim_circuit *c, int n_global, qsim_shard_plan **out);
+int qsim_shard_plan_num_steps(const qsim_shard_plan *p);
+/* Step i; perm (may be NULL) receives the n-entry logical -> physical qubit map that holds
+ * during step i (after the swap, for a swap step).  Errors: EINVAL. */
+int qsim_shard_plan_get_step(const qsim_shard_plan *p, int i, qsim_shard_step *s, int *perm);
+/* The local circuit of apply step i (owned by the plan; NULL for a swap step).  It can be fused
+ * (qsim_fuse) and applied with qsim_apply on each n-g qubit shard. */
+const qsim_circuit *qsim_shard_plan_local_circuit(const qsim_shard_plan *p, int i);
+void qsim_shard_plan_free(qsim_shard_plan *p);
+
+/* Copy the half of a shard (device, 2^n_local amplitudes of dtype) whose bit `qubit` equals
+ * `value` into out (device, 2^(n_local-1) amplitudes, in index order), or back (unpack), async
+ * on `stream`.  Errors: EINVAL, ECUDA. */
+int qsim_shard_pack(const void *shard, int n_local, int dtype, int qubit, int value, void *out, void *stream);
+int qsim_shard_unpack(void *shard, int n_local, int dtype, int qubit, int value, const void *in, void *stream);
+
+/* ======================================================================================= *
  * Serving pool: HHL solves admitted as they arrive, states resident in one device arena     *
  * ======================================================================================= */
 

@@ -77,6 +77,11 @@ class _PoolLaunch(ctypes.Structure):
                 ("t_start", ctypes.c_double), ("t_end", ctypes.c_double)]
 
 
+class _ShardStep(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("global_bit", ctypes.c_int), ("local_qubit", ctypes.c_int),
+                ("first_gate", ctypes.c_int), ("last_gate", ctypes.c_int)]
+
+
 class _TuneReport(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int), ("values", ctypes.c_int * QSIM_TUNE_COUNT),
                 ("dft_ms", ctypes.c_double), ("dense_ms", ctypes.c_double * 3),
@@ -142,6 +147,13 @@ _SIGS = {
     "qsim_pool_take_completed": ([_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, _IP, ctypes.c_double],
                                  ctypes.c_int),
     "qsim_pool_destroy": ([_VP], None),
+    "qsim_shard_plan_create": ([_VP, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
+    "qsim_shard_plan_num_steps": ([_VP], ctypes.c_int),
+    "qsim_shard_plan_get_step": ([_VP, ctypes.c_int, ctypes.POINTER(_ShardStep), _IP], ctypes.c_int),
+    "qsim_shard_plan_local_circuit": ([_VP, ctypes.c_int], _VP),
+    "qsim_shard_plan_free": ([_VP], None),
+    "qsim_shard_pack": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP], ctypes.c_int),
+    "qsim_shard_unpack": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP], ctypes.c_int),
     "qsim_pool_launch_log": ([_VP, ctypes.POINTER(_PoolLaunch), ctypes.c_int, _IP], ctypes.c_int),
     "hhl_readout": ([_VP, ctypes.c_int, _VP, _VP, _DP, _DP, ctypes.POINTER(_ReadoutStats)],
                     ctypes.c_int),
@@ -665,3 +677,51 @@ class Pool:
             self.close()
         except Exception:
             pass
+
+
+class ShardPlan:
+    """qsim_shard_plan: the steps that run an unfused circuit on 2^n_global shards.  steps is a
+    list of dicts: {"kind": "swap", "global_bit", "local_qubit", "perm"} or {"kind": "apply",
+    "first_gate", "last_gate", "perm", "circuit"} (the local circuit, owned by the plan)."""
+
+    def __init__(self, circuit: Circuit, n_global: int):
+        p = _VP()
+        _check(library().qsim_shard_plan_create(circuit.ptr, int(n_global), ctypes.byref(p)))
+        self._ptr = p
+        self.n = circuit.n_qubits
+        self.n_global = int(n_global)
+        self.n_local = self.n - self.n_global
+        self.steps = []
+        for i in range(library().qsim_shard_plan_num_steps(p)):
+            st = _ShardStep()
+            perm = np.zeros(self.n, dtype=np.int32)
+            _check(library().qsim_shard_plan_get_step(p, i, ctypes.byref(st), perm.ctypes.data_as(_IP)))
+            if st.kind == 0:
+                self.steps.append({"kind": "swap", "global_bit": st.global_bit, "local_qubit": st.local_qubit,
+                                   "perm": perm.tolist()})
+            else:
+                c = Circuit(_ptr=_VP(library().qsim_shard_plan_local_circuit(p, i)), _owner=self)
+                self.steps.append({"kind": "apply", "first_gate": st.first_gate, "last_gate": st.last_gate,
+                                   "perm": perm.tolist(), "circuit": c})
+
+    def __del__(self):
+        if getattr(self, "_ptr", None):
+            try:
+                library().qsim_shard_plan_free(self._ptr)
+            except Exception:
+                pass
+            self._ptr = None
+
+
+def qsim_shard_pack(shard, qubit: int, value: int, out, stream=None):
+    n = shard.numel().bit_length() - 1
+    _check(library().qsim_shard_pack(ctypes.c_void_p(shard.data_ptr()), n, _dtype_of(shard), int(qubit), int(value),
+                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def qsim_shard_unpack(shard, qubit: int, value: int, src, stream=None):
+    n = shard.numel().bit_length() - 1
+    _check(library().qsim_shard_unpack(ctypes.c_void_p(shard.data_ptr()), n, _dtype_of(shard), int(qubit), int(value),
+                                       ctypes.c_void_p(src.data_ptr()), _stream_ptr(stream)))
+    return shard

@@ -320,3 +320,25 @@ def test_hhl_batch_with_qft_passes_matches_oracle(qs, dtype, cuda_device):
         assert np.max(np.abs(out - ref["psi"])) <= tol
         assert abs(r["p_success"] - ref["P"]) <= 10 * tol
         assert abs(r["p_clock0"] - ref["P0"]) <= 10 * tol
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_batch_autotune_returns_its_fastest_candidate_and_every_width_is_correct(qs, dtype, cuda_device):
+    """hhl_batch_autotune: the width it returns is the one with the smallest measured time, and the
+    batch fused at every candidate width reproduces the oracle (the state within the dtype's
+    bound, the readout within the bounds that implies)."""
+    probs = synth.batched_problems(seed=23, count=16)
+    hs = [qs.hhl_build(p["A"], p["b"], p["m"], structured=True, fft_qft=True) for p in probs]
+    states = [torch.empty(1 << h.info()["n"], dtype=dtype, device="cuda") for h in hs]
+    cands = (1, 2, 3, 4, 5)
+    k, tmap = qs.hhl_batch_autotune(hs, states, cands)
+    assert set(tmap) == set(cands) and all(v > 0 for v in tmap.values())
+    assert k == min(tmap, key=tmap.get)
+    refs = [ref_solve(p) for p in probs]
+    for kk in cands:
+        fused = [qs.qsim_fuse(h.as_circuit(), kk) for h in hs]
+        b = qs.hhl_batch_create(hs, states, fused)
+        b.run()
+        for p, st, r, ref in zip(probs, states, b.results(), refs):
+            check_hhl_result(st, r, ref, p["m"], dtype)

@@ -153,3 +153,36 @@ def test_hhl_merged_passes_match_oracle(qs, m, tma):
             assert passes == 6 and expands == 4
     finally:
         qs.qsim_tune_reset()
+
+
+def test_autotune_writes_its_size_class_and_results_stay_correct(qs):
+    """qsim_autotune on a 22-qubit complex64 buffer: it writes the table entries of that size
+    class only (marked tuned), reports positive timings, and a Fourier pass and a dense 5-qubit
+    gate run with the tuned entries still match the oracle."""
+    n = 22
+    buf = torch.empty(1 << n, dtype=C64, device="cuda")
+    try:
+        rep = qs.qsim_autotune(buf)
+        assert rep["n_qubits"] == n and rep["table"]["tuned"] == 1
+        assert rep["dft_ms"] > 0 and all(v > 0 for v in rep["fuse_ms"].values())
+        assert qs.qsim_tune_get(qs.QSIM_C64, qs.QSIM_TUNE_TUNED, n) == 1
+        assert qs.qsim_tune_get(qs.QSIM_C64, qs.QSIM_TUNE_TUNED, 27) == 0      # another size class
+        for k in ("dft_tma", "dft_lanes", "dft_prefetch", "dense_tc", "fuse_width"):
+            key = getattr(qs, "QSIM_TUNE_" + k.upper())
+            assert qs.qsim_tune_get(qs.QSIM_C64, key, n) == rep["table"][k]
+        psi = host_input(synth.gaussian_state_np(71, n), C64)
+        ref = psi.copy()
+        field, src = list(range(12, 22)), list(range(2, 12))
+        ohhl.dft_pass(ref, field, -1, src, False)
+        rng = np.random.default_rng(72)
+        U = synth.haar_unitary(rng, 32)
+        t = synth.random_targets(rng, n, 5)
+        from oracle import core as ocore
+        ocore.apply_gate(ref, t, U)
+        c = qs.Circuit(n).add_dft(field, -1, src).add_gate(t, U)
+        st = dev_state(psi, C64)
+        qs.qsim_apply(st, c)
+        torch.cuda.synchronize()
+        check(st, ref, C64)
+    finally:
+        qs.qsim_tune_reset()
