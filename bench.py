@@ -272,7 +272,7 @@ def run_gates(args, ws, rank, dtype_name):
     # overwrites the contents), then the benchmark's input is written
     st = torch.empty(1 << n, dtype=dtype, device="cuda")
     t0 = time.perf_counter()
-    tune = qs.qsim_autotune(st, stream)
+    tune = {} if args.no_autotune else qs.qsim_autotune(st, stream)
     tune["seconds"] = round(time.perf_counter() - t0, 2)
     st.copy_(synth.gaussian_state_torch(seed, n, dtype, "cuda", normalize=True))
     bytes_per_gate = 2.0 * S * (1 << n)
@@ -569,7 +569,8 @@ def sub_hhl27(args, ws, rank):
         fuse_ms = 1e3 * (time.perf_counter() - tf)
         ci = circ.info()
         st = torch.empty(1 << n, dtype=dt, device="cuda")
-        if not qs.qsim_tune_get(qs.QSIM_C64 if name == "c64" else qs.QSIM_C128, qs.QSIM_TUNE_TUNED):
+        if not args.no_autotune and not qs.qsim_tune_get(qs.QSIM_C64 if name == "c64" else qs.QSIM_C128,
+                                                         qs.QSIM_TUNE_TUNED):
             tune[name] = qs.qsim_autotune(st, stream)
         for _ in range(3):
             qs.hhl_run(st, h, circ, stream)
@@ -595,6 +596,36 @@ def sub_hhl27(args, ws, rank):
                        "leakage": r["leakage"], "max_k": max_k, "fused_ops": ci["n_gates"],
                        "launches_per_solve": nl / reps[name], "host_fuse_ms": round(fuse_ms, 3),
                        "solves_timed": reps[name], "clocks": clk.summary()}
+        # the same solve with hhl_run replayed from a CUDA graph (captured once; every launch of
+        # the solve's circuit in one replay), the readout eager: no per-operation host work
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream()
+        cs.wait_stream(stream)
+        with torch.cuda.stream(cs):
+            qs.hhl_run(st, h, circ, cs)
+        cs.synchronize()
+        with torch.cuda.graph(g, stream=cs):
+            qs.hhl_run(st, h, circ, cs)
+        for _ in range(3):
+            g.replay()
+            qs.hhl_readout(st, h, stream)
+        torch.cuda.synchronize()
+        glat = []
+        l0 = qs.qsim_launch_count()
+        t0 = time.perf_counter()
+        for _ in range(reps[name]):
+            a = time.perf_counter()
+            g.replay()
+            rg = qs.hhl_readout(st, h, stream)
+            glat.append(time.perf_counter() - a)
+        gdt = max_over_ranks(ws, time.perf_counter() - t0)
+        paths[name]["graph"] = {"solves_per_s": round(ws * reps[name] / gdt, 2),
+                                "ms_per_solve": round(1e3 * gdt / reps[name], 3),
+                                "p50_ms": round(1e3 * float(np.percentile(glat, 50)), 3),
+                                "p99_ms": round(1e3 * float(np.percentile(glat, 99)), 3),
+                                "readout_rel_err_vs_classical": float(np.linalg.norm(rg["x"] - xt) / np.linalg.norm(xt)),
+                                "library_launches_outside_graph": qs.qsim_launch_count() - l0}
+        del g
         keep[name] = (st.cpu().numpy(), r)
         del st
         torch.cuda.empty_cache()
@@ -608,14 +639,17 @@ def sub_hhl27(args, ws, rank):
             "note": "mean of the three pass shapes of the solve, each timed alone on a 27-qubit complex64 state"}
     oracle_p = dict(p)
     oracle_p["m"] = 12
+    best = paths["c64"]["graph"] if paths["c64"]["graph"]["solves_per_s"] > paths["c64"]["solves_per_s"] else paths["c64"]
     rec = {
-        "metric": "HHL solves/s (27 qubits, complex64 precision form)", "value": paths["c64"]["solves_per_s"],
-        "unit": "solves/s", "ms_per_solve": paths["c64"]["ms_per_solve"], "dtype": "c64",
+        "metric": "HHL solves/s (27 qubits, complex64 precision form)", "value": best["solves_per_s"],
+        "unit": "solves/s", "ms_per_solve": best["ms_per_solve"], "dtype": "c64",
+        "solve_path": "hhl_run replayed from a CUDA graph + hhl_readout" if best is not paths["c64"]
+                      else "hhl_run + hhl_readout (eager)",
         "config": {"workload": "27-qubit HHL: 64x64 reduced Laplacian of a random 65-bus grid (98 lines), "
                                "nb=6, m=20, structured phase estimation, QFTs as Fourier passes",
                    "n_qubits": n, "nb": info["nb"], "m": info["m"], "host_build_ms": round(build_ms, 3),
                    "l2": "state 1 GiB (c64) / 2 GiB (c128), larger than L2"},
-        "latency_ms": {"p50": paths["c64"]["p50_ms"], "p99": paths["c64"]["p99_ms"]},
+        "latency_ms": {"p50": best["p50_ms"], "p99": best["p99_ms"]},
         "paths": paths, "roofline": roof, "tuning": qs.qsim_tune_table(), "autotune": tune,
         "speedup_c64_vs_c128": round(paths["c64"]["solves_per_s"] / paths["c128"]["solves_per_s"], 2),
         "gpu_launches": int(paths["c64"]["launches_per_solve"] * reps["c64"]),
@@ -976,6 +1010,8 @@ def main():
     ap.add_argument("--e2e-from-host-gen", action="store_true")
     ap.add_argument("--no-subrecords", action="store_true",
                     help="default workload only: skip the configs 1, 3, 4, 5 sub-records")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the kernel-choice table's defaults (for profiling runs with a fixed launch sequence)")
     ap.add_argument("--no-oracle27", action="store_true",
                     help="skip the full-size 27-qubit oracle comparison (about 2 minutes of host time)")
     args = ap.parse_args()

@@ -194,7 +194,8 @@ int qsim_launch_counts(unsigned long long *counts, int n);
                                     rows of 16 amplitudes (128 B)                                 */
 #define QSIM_TUNE_DFT_LANES 1    /* thread-load pass kernel: lane qubits per tile (0 = 128-byte
                                     runs: 4 for complex64, 3 for complex128)                       */
-#define QSIM_TUNE_DFT_PREFETCH 2 /* thread-load pass kernel: L2 prefetch distance in tiles (0 off) */
+#define QSIM_TUNE_DFT_PREFETCH 2 /* pass kernels: L2 prefetch distance in tiles (0 off; bulk-copy
+                                    kernels prefetch with a bulk tensor prefetch)                  */
 #define QSIM_TUNE_DENSE_TC 3     /* complex64 dense gates: bit k set = gates of k targets (4..6)
                                     on the tensor cores; bit 7 = real 7-target gates (and real
                                     6-target gates on qubits 0 and 1) on the tensor cores          */

@@ -144,6 +144,10 @@ void circuit_info(const qsim_circuit *c, qsim_circuit_info *out);
 void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int live = -1);
 // every kernel launch site reports its launches (qsim_launch_count)
 void note_launches(int k, int family);
+// resident blocks per SM of `kernel` (a __global__ function) for this launch shape on the current
+// device, queried once per (kernel, threads, smem, device) and then served from a cache (the
+// query runs on every launch otherwise, and the host time adds up for short solves)
+int occupancy_cached(const void *kernel, int threads, size_t smem);
 void ensure_device_blob(qsim_circuit *c, int dtype);
 std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype);   // sets op offsets
 void attach_external_blob(qsim_circuit *c, int dtype, void *dev, size_t bytes);
@@ -196,7 +200,7 @@ bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
 // tuning.cpp: the kernel-choice table (QSIM_TUNE_* keys of qsim.h)
 int tune_get(int dtype, int key, int n_qubits);  // entry of the size class of n_qubits
 // dft_tma.cu: complex64 pass with bulk-copy (TMA) tiles; false when the shape does not fit
-bool dft_tma_launch(const void *dft_args, int n, int K, int sign, int kind, int variant, int l2promo,
+bool dft_tma_launch(const void *dft_args, int n, int K, int sign, int kind, int variant, int l2promo, int prefetch,
                     cudaStream_t st);
 // two passes on one field in one kernel (see run_dft2); part (merge 1): 1 sin part into the upper
 // half, 0 cos part in place

@@ -133,7 +133,8 @@ bool run_dft(void *state, int n, int dtype, const Op &op, const void *tables, cu
         DftArgs t = a;
         t.hT = hT;
         t.tw_smem = 0;
-        if (dft_tma_launch(&t, n, K, op.sign, kind, variant, tune_get(QSIM_C64, QSIM_TUNE_DFT_L2PROMO, n), st))
+        if (dft_tma_launch(&t, n, K, op.sign, kind, variant, tune_get(QSIM_C64, QSIM_TUNE_DFT_L2PROMO, n),
+                           tune_get(QSIM_C64, QSIM_TUNE_DFT_PREFETCH, n), st))
             return true;
     }
     int L = std::min(lane_bits_default(dtype, k1), n - K);

@@ -458,7 +458,7 @@ void launch_kind(const DftArgs &a, bool contig, int threads, size_t smem, cudaSt
         QSIM_REQUIRE(contig, "fused inversion needs a contiguous field");
     }
     int per_sm = 0;
-    DFT_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    per_sm = occupancy_cached(reinterpret_cast<const void *>(kern), threads, smem);
     QSIM_REQUIRE(per_sm > 0, "Fourier pass does not fit on an SM");
     const long long grid = std::min<long long>(a.ntiles, (long long)num_sms_dft() * per_sm);
     kern<<<(int)grid, threads, smem, st>>>(a);

@@ -349,7 +349,7 @@ void launch2(const CUtensorMap &map, const DftArgs &a1, const DftArgs &a2, const
         attr = true;
     }
     int per_sm = 0;
-    DFT_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::threads, smem));
+    per_sm = occupancy_cached(reinterpret_cast<const void *>(kern), S::threads, smem);
     QSIM_REQUIRE(per_sm > 0, "merged Fourier passes do not fit on an SM");
     const long long grid = std::min<long long>(x.ntiles, (long long)num_sms() * per_sm);
     kern<<<(int)grid, S::threads, smem, st>>>(map, a1, a2, x);
@@ -368,7 +368,7 @@ void launch_gen(const DftArgs &a, long long ntiles, size_t smem, cudaStream_t st
         attr = true;
     }
     int per_sm = 0;
-    DFT_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::threads, smem));
+    per_sm = occupancy_cached(reinterpret_cast<const void *>(kern), S::threads, smem);
     QSIM_REQUIRE(per_sm > 0, "generated-input Fourier pass does not fit on an SM");
     const long long grid = std::min<long long>(ntiles, (long long)num_sms() * per_sm);
     kern<<<(int)grid, S::threads, smem, st>>>(a, ntiles);
@@ -432,6 +432,7 @@ bool dft2_tma_launch(const void *args1, const void *args2, int n, int K, int mer
     x.above = above;
     x.inv_c4 = 0;
     x.ntiles = 1ll << (n - K - kL);
+    x.pf = 1;
     size_t smem = (((size_t)1 << K) << kL) * 8 + 2 * ((size_t)1 << K) * 8;
     const int ntw = a1.ns > 0 ? (1 << a1.hT) + (1 << (K + a1.ns - a1.hT)) : 0;
     a1.tw_smem = 0;

@@ -122,19 +122,29 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
         }
         // every thread waits for the tile itself (the copy's completion makes it visible to the
         // thread that observes it); the decision to give up is taken together at the first barrier
+        // index of this thread's amplitude at field value 0
+        const unsigned long long base = (unsigned long long)l | ((unsigned long long)c1 << kL) |
+                                        ((unsigned long long)c4 << (a.f0 + K));
+        // the structured phase on the inputs (QS 1): the table reads do not depend on the tile's
+        // data, so they are issued before the wait for it and their latency overlaps the copy
+        constexpr int NR = (N2 + 7) / 8;
+        float2 Qp{1.f, 0.f}, Pr[NR];
+        if (QS == 1) {
+            const unsigned long long i0 = base + ((unsigned long long)u << a.f0);
+            Qp = qphase_cd((unsigned long long)N1 << (a.f0 - a.qnb), i0 & qdm);
+#pragma unroll
+            for (int j = 0; j < NR; j++) Pr[j] = qphase(i0 + ((unsigned long long)(N1 * 8 * j) << a.f0));
+        }
         const bool ok = mbar_wait(bar_a, it & 1u);
-        if (tid == 0) {
-            // L2 prefetch of the first tile whose load is not issued yet
-            const long long tn = t + (EARLY ? 2 : 1) * (long long)gridDim.x;
+        if (tid == 0 && x.pf > 0) {
+            // L2 prefetch of a tile whose load is not issued yet (pf tiles of this CTA ahead)
+            const long long tn = t + (EARLY ? x.pf + 1 : x.pf) * (long long)gridDim.x;
             if (tn < x.ntiles) {
                 int n1, n4;
                 coords(tn, n1, n4);
                 tma_prefetch_l2(&tmap, n1, n4);
             }
         }
-        // index of this thread's amplitude at field value 0
-        const unsigned long long base = (unsigned long long)l | ((unsigned long long)c1 << kL) |
-                                        ((unsigned long long)c4 << (a.f0 + K));
         unsigned long long kb = 0;  // clock value bits outside the field (inversion)
         if (INV)
             for (int sg = 0; sg < a.inv_nseg; sg++)
@@ -144,7 +154,15 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
         // step 1
 #pragma unroll
         for (int q = 0; q < N2; q++) v[q] = buf[(u + N1 * q) * kNL + l];
-        if (qmode == 1) {
+        if (QS == 1) {
+            float2 P{1.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < N2; q++) {
+                if ((q & 7) == 0) P = Pr[q / 8];
+                v[q] = cmul(v[q], P);
+                P = cmul(P, Qp);
+            }
+        } else if (qmode == 1) {
             const unsigned long long i0 = base + ((unsigned long long)u << a.f0);
             if (qrec) {
                 // inputs at field values u + N1 q: the phase is P Q^q, Q = the phase of clock
@@ -338,7 +356,7 @@ void launch(const CUtensorMap &map, const DftArgs &a, const TmaExtra &x, size_t 
         attr = true;
     }
     int per_sm = 0;
-    DFT_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::threads, smem));
+    per_sm = occupancy_cached(reinterpret_cast<const void *>(kern), S::threads, smem);
     QSIM_REQUIRE(per_sm > 0, "Fourier pass (bulk-copy tiles) does not fit on an SM");
     const long long grid = std::min<long long>(x.ntiles, (long long)num_sms() * per_sm);
     kern<<<(int)grid, S::threads, smem, st>>>(map, a, x);
@@ -392,7 +410,8 @@ void dft_tma_clear_error() {
 // above, the lanes on qubits 0..2.  kind: 0 DFT, 1 Walsh-Hadamard, 2 DFT with the inversion
 // (inv_bit = n, the ancilla right above the state).  Returns false when the shape does not
 // fit (the caller then runs dft_kernel).
-bool dft_tma_launch(const void *args, int n, int K, int sign, int kind, int variant, int promo, cudaStream_t st) {
+bool dft_tma_launch(const void *args, int n, int K, int sign, int kind, int variant, int promo, int prefetch,
+                    cudaStream_t st) {
     using namespace dftt;
     const DftArgs &a0 = *static_cast<const DftArgs *>(args);
     if (K < 9 || K > 10 || variant < 1 || variant > 4) return false;
@@ -430,6 +449,7 @@ bool dft_tma_launch(const void *args, int n, int K, int sign, int kind, int vari
     x.above = above;
     x.inv_c4 = kind == 2 ? 1 << (n - f0 - K) : 0;
     x.ntiles = 1ll << (n - K - kL);
+    x.pf = prefetch;
     const size_t tile_bytes = ((size_t)1 << K) * kNL * 8;
     const int ntw = a.ns > 0 ? (1 << a.hT) + (1 << (K + a.ns - a.hT)) : 0;
     size_t smem = tile_bytes + ((size_t)1 << K) * 8;

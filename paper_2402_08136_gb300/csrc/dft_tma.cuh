@@ -82,6 +82,7 @@ struct TmaExtra {
     int above;      // qubits above the field in the tensor map (includes the ancilla for KIND 2)
     int inv_c4;     // KIND 2: coordinate offset of the upper half along the "above" dimension
     long long ntiles;  // tiles to transform (the lower half only for KIND 2)
+    int pf;            // > 0: L2 prefetch of the tile pf loads ahead of the next one issued
 };
 
 // L lane qubits (the lowest qubits): rows of 2^L amplitudes, 64 (L = 3) or 128 bytes (L = 4)

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
@@ -45,6 +47,24 @@ void note_launches(int k, int family) {
     g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed);
     if (family >= 0 && family < QSIM_KERNEL_FAMILIES)
         g_family[family].fetch_add((unsigned long long)k, std::memory_order_relaxed);
+}
+
+int occupancy_cached(const void *kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, size_t, int>, int> cache;
+    int dev = 0;
+    CUDA_OK(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(kernel, threads, smem, dev);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    int per_sm = 0;
+    CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = per_sm;
+    return per_sm;
 }
 
 static void check_launch(const char *what, int launches, int family) {
@@ -782,7 +802,7 @@ void launch_dense_t(const DenseArgs &a, size_t smem, bool pipe, cudaStream_t st)
         attr[pipe] = true;
     }
     int per_sm = 0;
-    CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    per_sm = occupancy_cached(reinterpret_cast<const void *>(kern), kThreads, smem);
     QSIM_REQUIRE(per_sm > 0, "dense kernel does not fit on an SM");
     const long long grid = std::min<long long>(a.ntiles, (long long)num_sms() * per_sm);
     kern<<<(int)grid, kThreads, smem, st>>>(a);

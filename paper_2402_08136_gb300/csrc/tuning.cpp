@@ -202,8 +202,10 @@ extern "C" int qsim_autotune(void *state, int n_qubits, int dtype, void *stream,
                 int tma, lanes, pf;
             };
             std::vector<Cand> cands;
-            if (dtype == QSIM_C64)
-                for (int v : {4, 3, 2, 1}) cands.push_back({v, 0, 1});
+            if (dtype == QSIM_C64) {
+                for (int pf : {1, 0, 2}) cands.push_back({4, 0, pf});
+                for (int v : {3, 2, 1}) cands.push_back({v, 0, 1});
+            }
             for (int lanes : {0, 3, 5})
                 for (int pf : {0, 1}) cands.push_back({0, lanes, pf});
             double best = 1e300;

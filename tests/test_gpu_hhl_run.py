@@ -192,3 +192,31 @@ def test_launch_counter_counts_kernels(qs, cuda_device):
     l1 = qs.qsim_launch_count()
     qs.hhl_readout(s2, h)
     assert qs.qsim_launch_count() - l1 == 2
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_hhl_run_replays_from_a_cuda_graph(qs, dtype, cuda_device):
+    """hhl_run only enqueues stream work after its first call (which uploads the circuit's
+    tables), so it can be captured into a CUDA graph: a replay gives the same bits as the eager
+    call, solve after solve (the graph rewrites every amplitude it reads)."""
+    import synth as _s
+    rng = np.random.default_rng(61)
+    A, b = _s.contingency_system(rng, 2 ** 4 + 1)
+    h = qs.hhl_build(A, b, 18, structured=True, fft_qft=True)
+    c = qs.qsim_fuse(h.as_circuit(), 6 if dtype == torch.complex64 else 2)
+    n = h.info()["n"]
+    st = torch.empty(1 << n, dtype=dtype, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        qs.hhl_run(st, h, c, s)
+    s.synchronize()
+    eager = st.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        qs.hhl_run(st, h, c, s)
+    for _ in range(2):
+        st.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(st, eager)
