@@ -34,7 +34,7 @@ int default_value(int slot, int key) {
     switch (key) {
         case QSIM_TUNE_DFT_TMA: return slot == 0 ? 4 : 0;  // complex64 only
         case QSIM_TUNE_DFT_LANES: return 0;                // 0: 128-byte lane runs
-        case QSIM_TUNE_DFT_PREFETCH: return 1;
+        case QSIM_TUNE_DFT_PREFETCH: return slot == 0 ? 0 : 1;  // bulk-copy passes: no L2 prefetch
         case QSIM_TUNE_DENSE_TC: return slot == 0 ? ((1 << 4) | (1 << 5) | (1 << 6) | (1 << 7)) : 0;
         case QSIM_TUNE_FUSE_WIDTH: return slot == 0 ? 4 : 2;
         case QSIM_TUNE_DFT_L2PROMO: return 2;
