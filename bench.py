@@ -720,6 +720,11 @@ def sub_records(args, ws, rank):
         rs["cpu_baseline"] = oracle_hhl_both([it["problem"] for it in items[:16]],
                                              "16 requests of the stream (qubits capped at 16)")
     out["serving"] = rs
+    # the full qubit range 8..30 (7.5 % of the requests need 28-30 qubits, 2-8 GiB states): a
+    # shorter stream at the same offered rate, to show the service rate and latency the box
+    # reaches when the offered load exceeds it
+    rf = run_serving(with_args(args, count=1000, rate=2000.0, max_n=30, pool_gb=150.0), ws, rank)
+    out["serving_full_range"] = rf
     if rank == 0 and not args.no_oracle27:
         oracle_hhl27_compare(r27, keep, p27)
     del keep

@@ -62,13 +62,18 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
     constexpr bool INV = KIND == 2;
     constexpr int k1 = S::k1, k2 = S::k2, N1 = S::N1, N2 = S::N2, RR = S::RR, KN = 1 << K;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // [tile (1024-aligned)] [W] [twiddle tables] [mbarrier]
+    // [tile (1024-aligned)] [W] [twiddle tables] [phase steps (QS 1)] [mbarrier]
+    constexpr int NR = (S::N2 + 7) / 8;  // refresh points of the phase recurrence along a column
     const unsigned pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
     float2 *buf = reinterpret_cast<float2 *>(smem_raw + pad);
     float2 *Ws = buf + S::tile;
     float2 *Tsm = Ws + KN;
     const int ntlo = 1 << a.hT, nthi = 1 << (K + a.ns - a.hT);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(Tsm + (a.tw_smem ? ntlo + nthi : 0));
+    // QS 1: for every data index d, the phase of the clock step between consecutive inputs of a
+    // column ([d][0]) and of the steps to its refresh points ([d][j], j >= 1): the recurrence
+    // then needs one table read per column instead of one per refresh point
+    float2 *Psm = Tsm + (a.tw_smem ? ntlo + nthi : 0);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Psm + (QS == 1 ? (NR << a.qnb) : 0));
     const unsigned bar_a = smem_u32(bar), buf_a = smem_u32(buf);
     const int tid = threadIdx.x;
     const int l = tid & (kNL - 1);
@@ -80,6 +85,15 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
         const float2 *tg = reinterpret_cast<const float2 *>(a.Tlo), *th = reinterpret_cast<const float2 *>(a.Thi);
         for (int i = tid; i < ntlo; i += S::threads) Tsm[i] = tg[i];
         for (int i = tid; i < nthi; i += S::threads) Tsm[ntlo + i] = th[i];
+    }
+    if (QS == 1) {
+        const float2 *ql = reinterpret_cast<const float2 *>(a.qlo), *qh = reinterpret_cast<const float2 *>(a.qhi);
+        const unsigned long long hm = (1ull << a.qh) - 1ull;
+        for (int i = tid; i < (NR << a.qnb); i += S::threads) {
+            const int d = i / NR, j = i % NR;
+            const unsigned long long cv = (unsigned long long)(j == 0 ? S::N1 : S::N1 * 8 * j) << (a.f0 - a.qnb);
+            Psm[i] = cmul(ql[((cv & hm) << a.qnb) + d], qh[((cv >> a.qh) << a.qnb) + d]);
+        }
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_a) : "memory");
@@ -127,13 +141,12 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
                                         ((unsigned long long)c4 << (a.f0 + K));
         // the structured phase on the inputs (QS 1): the table reads do not depend on the tile's
         // data, so they are issued before the wait for it and their latency overlaps the copy
-        constexpr int NR = (N2 + 7) / 8;
-        float2 Qp{1.f, 0.f}, Pr[NR];
+        float2 Qp{1.f, 0.f}, P0{1.f, 0.f};
+        const float2 *ps = Psm;
         if (QS == 1) {
             const unsigned long long i0 = base + ((unsigned long long)u << a.f0);
-            Qp = qphase_cd((unsigned long long)N1 << (a.f0 - a.qnb), i0 & qdm);
-#pragma unroll
-            for (int j = 0; j < NR; j++) Pr[j] = qphase(i0 + ((unsigned long long)(N1 * 8 * j) << a.f0));
+            P0 = qphase(i0);
+            ps = Psm + (i0 & qdm) * NR;
         }
         const bool ok = mbar_wait(bar_a, it & 1u);
         if (tid == 0 && x.pf > 0) {
@@ -155,10 +168,13 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
 #pragma unroll
         for (int q = 0; q < N2; q++) v[q] = buf[(u + N1 * q) * kNL + l];
         if (QS == 1) {
+            // inputs at field values u + N1 q: phase P0 Q^q, restarted every 8 terms from P0 times
+            // the step to the refresh point (at most 8 FP32 products from an exact table value)
+            Qp = ps[0];
             float2 P{1.f, 0.f};
 #pragma unroll
             for (int q = 0; q < N2; q++) {
-                if ((q & 7) == 0) P = Pr[q / 8];
+                if ((q & 7) == 0) P = q == 0 ? P0 : cmul(P0, ps[q / 8]);
                 v[q] = cmul(v[q], P);
                 P = cmul(P, Qp);
             }
@@ -180,7 +196,22 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
                 for (int q = 0; q < N2; q++) v[q] = cmul(v[q], qphase(i0 + ((unsigned long long)(N1 * q) << a.f0)));
             }
         }
-        if (twmode == 1) {
+        if (TW == 1) {
+            // the input twiddle exp(s 2 pi i w (u + N1 q) / 2^(K+ns)) is geometric in q: one
+            // complex product per input, restarted from the tables every 8 terms
+            const unsigned e1 = w * (unsigned)N1;
+            const float2 Qt = cmul(Tlo[e1 & tmask], Thi[e1 >> a.hT]);
+            float2 P{1.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < N2; q++) {
+                if ((q & 7) == 0) {
+                    const unsigned e = w * (unsigned)(u + N1 * q);
+                    P = cmul(Tlo[e & tmask], Thi[e >> a.hT]);
+                }
+                v[q] = cmul(v[q], P);
+                P = cmul(P, Qt);
+            }
+        } else if (twmode == 1) {
 #pragma unroll
             for (int q = 0; q < N2; q++) {
                 const unsigned e = w * (unsigned)(u + N1 * q);
@@ -457,6 +488,10 @@ bool dft_tma_launch(const void *args, int n, int K, int sign, int kind, int vari
     if (ntw > 0 && smem + (size_t)ntw * 8 + 16 <= (kL == 3 ? 110 : 200) * 1024) {
         a.tw_smem = 1;
         smem += (size_t)ntw * 8;
+    }
+    if (kL == 4 && early && a.qmode == 1 && a.qrec) {
+        if (a.qnb > 10) return false;
+        smem += (size_t)8 * 4 << a.qnb;  // phase steps of the recurrence (QS 1: N2 / 8 = 4 per data index)
     }
     smem += 16 + 1024;  // mbarrier, alignment slack
     if (kL == 3) {
