@@ -62,18 +62,22 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
     constexpr bool INV = KIND == 2;
     constexpr int k1 = S::k1, k2 = S::k2, N1 = S::N1, N2 = S::N2, RR = S::RR, KN = 1 << K;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // [tile (1024-aligned)] [W] [twiddle tables] [phase steps (QS 1)] [mbarrier]
-    constexpr int NR = (S::N2 + 7) / 8;  // refresh points of the phase recurrence along a column
+    // [tile (1024-aligned)] [W] [twiddle tables] [phase steps] [mbarrier]
+    // phase recurrence through a step table: QS 1 along the inputs u + N1 q of a column, QS 2 on a
+    // transform along the outputs aa + N2 j of a thread (stride PST, PCNT terms, NR refresh points)
+    constexpr bool PT = QS == 1 || (QS == 2 && KIND == 0);
+    constexpr int PST = QS == 1 ? S::N1 : S::N2, PCNT = QS == 1 ? S::N2 : S::N1;
+    constexpr int NR = (PCNT + 7) / 8;
     const unsigned pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
     float2 *buf = reinterpret_cast<float2 *>(smem_raw + pad);
     float2 *Ws = buf + S::tile;
     float2 *Tsm = Ws + KN;
     const int ntlo = 1 << a.hT, nthi = 1 << (K + a.ns - a.hT);
-    // QS 1: for every data index d, the phase of the clock step between consecutive inputs of a
-    // column ([d][0]) and of the steps to its refresh points ([d][j], j >= 1): the recurrence
-    // then needs one table read per column instead of one per refresh point
+    // for every data index d, the phase of the clock step between consecutive terms ([d][0]) and
+    // of the steps to the refresh points ([d][j], j >= 1): the recurrence then needs one table
+    // read per sequence instead of one per refresh point
     float2 *Psm = Tsm + (a.tw_smem ? ntlo + nthi : 0);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(Psm + (QS == 1 ? (NR << a.qnb) : 0));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Psm + (PT ? (NR << a.qnb) : 0));
     const unsigned bar_a = smem_u32(bar), buf_a = smem_u32(buf);
     const int tid = threadIdx.x;
     const int l = tid & (kNL - 1);
@@ -86,12 +90,12 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
         for (int i = tid; i < ntlo; i += S::threads) Tsm[i] = tg[i];
         for (int i = tid; i < nthi; i += S::threads) Tsm[ntlo + i] = th[i];
     }
-    if (QS == 1) {
+    if (PT) {
         const float2 *ql = reinterpret_cast<const float2 *>(a.qlo), *qh = reinterpret_cast<const float2 *>(a.qhi);
         const unsigned long long hm = (1ull << a.qh) - 1ull;
         for (int i = tid; i < (NR << a.qnb); i += S::threads) {
             const int d = i / NR, j = i % NR;
-            const unsigned long long cv = (unsigned long long)(j == 0 ? S::N1 : S::N1 * 8 * j) << (a.f0 - a.qnb);
+            const unsigned long long cv = (unsigned long long)(j == 0 ? PST : PST * 8 * j) << (a.f0 - a.qnb);
             Psm[i] = cmul(ql[((cv & hm) << a.qnb) + d], qh[((cv >> a.qh) << a.qnb) + d]);
         }
     }
@@ -247,6 +251,15 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
         }
         __syncthreads();  // every thread has read its step-2 points: the buffer is free
         if (EARLY && tid == 0 && t + gridDim.x < x.ntiles) issue_load(t + gridDim.x);
+        // the structured phase on a transform's outputs (QS 2): outputs aa + N2 j of group aa
+        // take P(aa) R^j; P(aa) is read from the tables before the transform, whose arithmetic
+        // covers the latency
+        constexpr bool DSEQ = QS == 2 && KIND == 0;
+        float2 Pa[RR];
+        if (DSEQ) {
+#pragma unroll
+            for (int r = 0; r < RR; r++) Pa[r] = qphase(base + ((unsigned long long)(u * RR + r) << a.f0));
+        }
 #pragma unroll
         for (int r = 0; r < RR; r++) dft_regs<N1, SGN, WALSH>(v + r * N1);
 #pragma unroll
@@ -256,8 +269,12 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
             float2 P{1.f, 0.f}, Q{1.f, 0.f};
             const unsigned long long q0 = base + ((unsigned long long)(N1 * aa) << a.f0);
             if (qseq) Q = qphase_cd(1ull << (a.f0 - a.qnb), q0 & qdm);
+            const float2 *pd = Psm + (base & qdm) * NR;
+            if (DSEQ) Q = pd[0];
 #pragma unroll
-            for (int i = 0; i < N1; i++) {
+            for (int jj = 0; jj < N1; jj++) {
+                // DSEQ visits the outputs in the order of j (output aa + N2 j sits in v[bitrev(j)])
+                const int i = DSEQ ? bitrev(jj, k1) : jj;
                 const int y = WALSH ? i + N1 * aa : aa + N2 * bitrev(i, k1);
                 float2 z = v[r * N1 + i];
                 z.x *= scale;
@@ -266,7 +283,11 @@ __global__ void __launch_bounds__(Shape<K, L>::threads, Shape<K, L>::min_blocks)
                     const unsigned e = w * (unsigned)y;
                     z = cmul(z, cmul(Tlo[e & tmask], Thi[e >> a.hT]));
                 }
-                if (qseq) {
+                if (DSEQ) {
+                    if ((jj & 7) == 0) P = jj == 0 ? Pa[r] : cmul(Pa[r], pd[jj / 8]);
+                    z = cmul(z, P);
+                    P = cmul(P, Q);
+                } else if (qseq) {
                     if ((i & 7) == 0) P = qphase(q0 + ((unsigned long long)i << a.f0));
                     z = cmul(z, P);
                     P = cmul(P, Q);
@@ -399,9 +420,9 @@ void launch(const CUtensorMap &map, const DftArgs &a, const TmaExtra &x, size_t 
 template <int K, int L, bool EARLY>
 void launch_k(const CUtensorMap &map, const DftArgs &a, const TmaExtra &x, int sign, int kind, size_t smem,
               cudaStream_t st) {
-    if (EARLY && L == 4) {
+    if constexpr (EARLY && L == 4) {
         // the passes of the phase estimation, each with a kernel of its own options
-        const int qs = a.qmode == 0 ? 0 : (a.qrec && a.qmode == 1 ? 1 : (a.qrec && a.qmode == 2 && kind == 1 ? 2 : 3));
+        const int qs = a.qmode == 0 ? 0 : (a.qrec && a.qmode == 1 ? 1 : (a.qrec && a.qmode == 2 && kind != 2 ? 2 : 3));
         const int tw = a.twmode;
         if (kind == 2 && tw == 0 && qs == 0) return launch<K, L, -1, 2, EARLY, 0, 0>(map, a, x, smem, st);
         if (kind == 1 && tw == 0 && qs == 0) return launch<K, L, 1, 1, EARLY, 0, 0>(map, a, x, smem, st);
@@ -411,6 +432,8 @@ void launch_k(const CUtensorMap &map, const DftArgs &a, const TmaExtra &x, int s
         if (kind == 0 && sign < 0 && tw == 0 && qs == 0) return launch<K, L, -1, 0, EARLY, 0, 0>(map, a, x, smem, st);
         if (kind == 0 && sign > 0 && tw == 0 && qs == 0) return launch<K, L, 1, 0, EARLY, 0, 0>(map, a, x, smem, st);
         if (kind == 0 && sign > 0 && tw == 1 && qs == 0) return launch<K, L, 1, 0, EARLY, 1, 0>(map, a, x, smem, st);
+        if (kind == 0 && sign > 0 && tw == 2 && qs == 0) return launch<K, L, 1, 0, EARLY, 2, 0>(map, a, x, smem, st);
+        if (kind == 0 && sign > 0 && tw == 0 && qs == 2) return launch<K, L, 1, 0, EARLY, 0, 2>(map, a, x, smem, st);
     }
     if (kind == 2) launch<K, L, -1, 2, EARLY>(map, a, x, smem, st);
     else if (kind == 1) launch<K, L, 1, 1, EARLY>(map, a, x, smem, st);
@@ -489,9 +512,9 @@ bool dft_tma_launch(const void *args, int n, int K, int sign, int kind, int vari
         a.tw_smem = 1;
         smem += (size_t)ntw * 8;
     }
-    if (kL == 4 && early && a.qmode == 1 && a.qrec) {
+    if (kL == 4 && early && a.qrec && (a.qmode == 1 || (a.qmode == 2 && kind == 0))) {
         if (a.qnb > 10) return false;
-        smem += (size_t)8 * 4 << a.qnb;  // phase steps of the recurrence (QS 1: N2 / 8 = 4 per data index)
+        smem += (size_t)8 * 4 << a.qnb;  // phase steps of the recurrence (at most 32 / 8 = 4 per data index)
     }
     smem += 16 + 1024;  // mbarrier, alignment slack
     if (kL == 3) {

@@ -252,7 +252,22 @@ hhl_circuit *build_from_spectrum(int N, const std::vector<double> &lamA, const s
     }
     // uncompute: inverse of the phase estimation
     if (flags & QSIM_HHL_STRUCTURED_QPE) {
+        const size_t qft_begin = c.gates.size();
         for (size_t i = qpe_end; i-- > iqft_begin;) c.gates.push_back(inverse_gate(c.gates[i]));  // QFT
+        if (passes && c.gates.size() >= qft_begin + 2) {
+            // the twiddle between the QFT's first two passes depends on the first pass's output
+            // digit and the second pass's input digit: it moves onto the first pass's outputs (the
+            // same diagonal between the same two transforms), so that the second pass, which
+            // carries the phase operator on its outputs, has no twiddle of its own
+            Gate &p1 = c.gates[qft_begin], &p2 = c.gates[qft_begin + 1];
+            if (p1.kind == GATE_DFT && p2.kind == GATE_DFT && p1.controls.empty() && p2.pre == 1 &&
+                p2.controls == p1.targets) {
+                p1.controls = p2.targets;
+                p1.pre = 0;
+                p2.controls.clear();
+                p2.pre = 0;
+            }
+        }
         Gate g = c.gates[phase_idx];  // the phase operator, inverted
         g.sign = -1;
         c.gates.push_back(g);
