@@ -428,6 +428,241 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Group-major form with the X operand in tensor memory (any targets the transposed form does not
+// take).  The same GEMM Y[128 x 2D] = X[128 x 2D] * B^T, but the MMA reads X (the A operand) from
+// tensor memory instead of shared memory: producer thread (warp w, lane l) owns group row
+// m = 32 (w mod 4) + l, which is exactly the TMEM lane its warp may write, and stores its hi and
+// lo TF32 parts of each chunk with tcgen05.st into a ring of TMEM slots (64 columns: 32 hi, 32
+// lo).  Shared memory then serves only B, which halves the shared-memory operand traffic of
+// every MMA (a 128 x 2D x 8 MMA read 8 KB of shared memory per issue, more than the SM's shared
+// memory delivers in the MMA's own time for 2D = 128), and the producers no longer write
+// shared memory at all.  Tensor memory: two accumulators of 2D columns and (512 - 4D) / 64
+// chunk slots (4 for 6 targets).  Same roles, barriers and bounded waits as dense_tc_kernel;
+// 21 warps (the register file is split over the SM's four sub-partitions, so the sub-partition
+// holding 6 warps caps a thread at 80 registers: the producers keep 6 chunks of loads in flight
+// within that).
+template <int K>
+struct GmCfg {
+    static constexpr int D = 1 << K, N = 2 * D, KK = 2 * D, NCH = KK / kCH;
+    static constexpr int BBYTES = N * KK * 4;
+    static constexpr int NB = (512 - 2 * N) / 64;  // tensor-memory chunk slots
+    static constexpr int NBAR = 2 * NB + 5;        // full/empty per slot, accfull/accempty x2, drain
+    static constexpr int SMEM = 2 * BBYTES + 8 * NBAR + 16 + 8 * D;
+    static constexpr unsigned IDESC = Cfg<K>::IDESC;
+};
+
+// MMA with the A operand in tensor memory
+__device__ __forceinline__ void mma_tf32_ta(unsigned d_tmem, unsigned a_tmem, uint64_t bdesc, unsigned idesc,
+                                            unsigned accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(unsigned taddr, const unsigned (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a) {
+    using C = GmCfg<K>;
+    constexpr int D = C::D, N = C::N, KK = C::KK, NCH = C::NCH, NB = C::NB;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float *Bs = reinterpret_cast<float *>(sm);  // [2][N*KK]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * C::BBYTES);
+    uint64_t *full = bars;                       // [NB] producer warps -> MMA (count 16)
+    uint64_t *empty = bars + NB;                 // [NB] MMA completion -> producers (commit)
+    uint64_t *accfull = bars + 2 * NB;           // [2] MMA completion -> epilogue (commit)
+    uint64_t *accempty = accfull + 2;            // [2] epilogue warps -> MMA (count 4)
+    uint64_t *drain = accfull + 4;               // MMA completion before tensor memory is freed
+    unsigned *tslot = reinterpret_cast<unsigned *>(bars + C::NBAR);
+    long long *toff = reinterpret_cast<long long *>(tslot + 4);  // D entries
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(a.Bg);
+        float4 *dst = reinterpret_cast<float4 *>(Bs);
+        for (int i = tid; i < 2 * C::BBYTES / 16; i += kThreadsWS) dst[i] = src[i];
+        for (int c = tid; c < D; c += kThreadsWS) {
+            long long o = 0;
+            for (int b = 0; b < K; b++)
+                if ((c >> b) & 1) o |= 1ll << a.targets[b];
+            toff[c] = o;
+        }
+        if (tid == 0) {
+            for (int i = 0; i < NB; i++) {
+                mbar_init(&full[i], kProducers / 32);
+                mbar_init(&empty[i], 1);
+            }
+            for (int i = 0; i < 2; i++) {
+                mbar_init(&accfull[i], 1);
+                mbar_init(&accempty[i], 4);
+            }
+            mbar_init(drain, 1);
+        }
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                         "r"(512u)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    }
+    const unsigned tmem = *tslot;
+    float2 *psi = reinterpret_cast<float2 *>(a.psi);
+    const long long first = blockIdx.x, stride = gridDim.x;
+    const long long ntl = first < a.ntiles ? (a.ntiles - first + stride - 1) / stride : 0;
+    const long long total = ntl * NCH;
+    bool failed = false;
+    auto group_base = [&](long long tile_i, int m) -> unsigned long long {
+        const unsigned long long gidx = (unsigned long long)(first + tile_i * stride) * kM + m;
+        return insert_zeros(gidx, a.fix, a.nfix) | a.cmask;
+    };
+
+    if (warp < kEpiWarp0) {
+        // ------------------------------------------------------------------ producers
+        // thread: group row m (its TMEM lane), amplitudes 4h .. 4h+3 of every chunk (K-columns
+        // 8h .. 8h+7 of the slot's hi and lo halves)
+        const int q = warp & 3, h = warp >> 2, m = 32 * q + lane;
+        float2 r[kPrefetch][kAmpsPT];
+        long long gb_tile = -1;
+        unsigned long long gb_row = 0;
+        auto load = [&](long long qq, float2(&rr)[kAmpsPT]) {
+            if (qq < total) {
+                if (qq / NCH != gb_tile) {
+                    gb_tile = qq / NCH;
+                    gb_row = group_base(gb_tile, m);
+                }
+                const int c0 = (int)(qq % NCH) * 16 + kAmpsPT * h;
+#pragma unroll
+                for (int e = 0; e < kAmpsPT; e++) rr[e] = __ldcs(psi + gb_row + toff[c0 + e]);
+            }
+        };
+#pragma unroll
+        for (int p = 0; p < kPrefetch; p++) load(p, r[p]);
+        for (long long q0 = 0; q0 < total && !failed; q0 += kPrefetch) {
+#pragma unroll
+            for (int p = 0; p < kPrefetch; p++) {
+                const long long qq = q0 + p;
+                if (qq >= total) break;
+                const int b = (int)(qq % NB);
+                if (qq >= NB) {  // the slot's previous chunk has been consumed by its MMAs
+                    bool ok = mbar_wait(&empty[b], (unsigned)(((qq / NB) - 1) & 1));
+                    ok = __all_sync(0xffffffffu, ok);  // the warp leaves together
+                    if (!ok) {
+                        failed = true;
+                        break;
+                    }
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(2 * N + b * 64 + 8 * h);
+                unsigned v[8];
+#pragma unroll
+                for (int e = 0; e < kAmpsPT; e++) {
+                    v[2 * e] = to_tf32(r[p][e].x);
+                    v[2 * e + 1] = to_tf32(r[p][e].y);
+                }
+                tmem_st8(ta, v);
+#pragma unroll
+                for (int e = 0; e < kAmpsPT; e++) {
+                    v[2 * e] = to_tf32(r[p][e].x - __uint_as_float(to_tf32(r[p][e].x)));
+                    v[2 * e + 1] = to_tf32(r[p][e].y - __uint_as_float(to_tf32(r[p][e].y)));
+                }
+                tmem_st8(ta + 32u, v);
+                load(qq + kPrefetch, r[p]);
+                asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[b]);
+            }
+        }
+    } else if (warp < kMmaWarp) {
+        // ------------------------------------------------------------------ epilogue
+        const int sub = warp - kEpiWarp0;  // TMEM lane subpartition
+        const int m = sub * 32 + lane;     // group row == TMEM lane
+        for (long long t = 0; t < ntl && !failed; t++) {
+            const int ab = (int)(t & 1);
+            bool ok = mbar_wait(&accfull[ab], (unsigned)((t >> 1) & 1));
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned long long gb = group_base(t, m);
+            const unsigned acc = tmem + (unsigned)(ab * N) + ((unsigned)(sub * 32) << 16);
+#pragma unroll
+            for (int col = 0; col < N; col += 16) {
+                unsigned v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                      "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                    : "r"(acc + (unsigned)col));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                for (int i = 0; i < 8; i++)
+                    __stcs(psi + gb + toff[col / 2 + i], make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])));
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty[ab]);
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------------------ MMA issuer
+        const unsigned b_hi = smem_u32(Bs), b_lo = b_hi + C::BBYTES;
+        for (long long qq = 0; qq < total && !failed; qq++) {
+            const int b = (int)(qq % NB);
+            const int j = (int)(qq % NCH);
+            const long long t = qq / NCH;
+            const int ab = (int)(t & 1);
+            if (j == 0 && t >= 2 && !mbar_wait(&accempty[ab], (unsigned)(((t >> 1) - 1) & 1))) {
+                failed = true;
+                break;
+            }
+            if (!mbar_wait(&full[b], (unsigned)((qq / NB) & 1))) {
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned acc = tmem + (unsigned)(ab * N);
+            const unsigned x_hi = tmem + (unsigned)(2 * N + b * 64), x_lo = x_hi + 32u;
+#pragma unroll
+            for (int kk = 0; kk < kCH / 8; kk++) {
+                const unsigned boff = (j * (kCH / 4) + kk * 2) * 128;  // 2 core matrices along K
+                const uint64_t dBh = make_desc(b_hi + boff, 128, KK * 32);
+                const uint64_t dBl = make_desc(b_lo + boff, 128, KK * 32);
+                mma_tf32_ta(acc, x_hi + 8u * kk, dBh, C::IDESC, (j == 0 && kk == 0) ? 0u : 1u);
+                mma_tf32_ta(acc, x_hi + 8u * kk, dBl, C::IDESC, 1u);
+                mma_tf32_ta(acc, x_lo + 8u * kk, dBh, C::IDESC, 1u);
+            }
+            commit_to(&empty[b]);
+            if (j == NCH - 1) commit_to(&accfull[ab]);
+        }
+        // every MMA issued has completed (or the bounded wait ran out) before tensor memory is
+        // released
+        commit_to(drain);
+        if (!mbar_wait(drain, 0u)) failed = true;
+    }
+    if (failed) atomicOr(&g_device_error, 1u);
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512u) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // Real 7-target gates (a real U, e.g. the eigenvector matrix of a real symmetric system) on the
 // lowest qubits, complex64.  For real U the complex product splits into two real ones,
 // Y_re = U X_re and Y_im = U X_im, so one real GEMM does both:
@@ -750,6 +985,23 @@ void dense_tc_pack(int k, const std::vector<cd> &U, unsigned char *out) {
         }
 }
 
+template <int K>
+static void launch_tc_gm(const tc::Args &a, int sms, cudaStream_t st) {
+    using C = tc::GmCfg<K>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc::dense_tc_gm_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_gm_kernel attribute: ") + cudaGetErrorString(e));
+        attr = true;
+    }
+    // one CTA per SM: it holds all 512 tensor-memory columns
+    const long long grid = std::min<long long>(a.ntiles, (long long)sms);
+    tc::dense_tc_gm_kernel<K><<<(int)grid, tc::kThreadsWS, C::SMEM, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_gm_kernel: ") + cudaGetErrorString(e));
+    note_launches(1, QSIM_KERNEL_DENSE_TC);
+}
+
 template <int K, bool TR>
 static void launch_tc_t(const tc::Args &a, int sms, cudaStream_t st) {
     using C = tc::Cfg<K>;
@@ -798,9 +1050,9 @@ bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const 
     // targets ascending (canonical order); qubits 0 and 1 among them: transposed form
     const bool tr = K == 6 && targets[0] == 0 && targets[1] == 1;
     switch (K) {
-        case 4: launch_tc_t<4, false>(a, sms, st); break;
-        case 5: launch_tc_t<5, false>(a, sms, st); break;
-        case 6: tr ? launch_tc_t<6, true>(a, sms, st) : launch_tc_t<6, false>(a, sms, st); break;
+        case 4: launch_tc_gm<4>(a, sms, st); break;
+        case 5: launch_tc_gm<5>(a, sms, st); break;
+        case 6: tr ? launch_tc_t<6, true>(a, sms, st) : launch_tc_gm<6>(a, sms, st); break;
         default: return false;
     }
     return true;
