@@ -11,31 +11,29 @@
 // which keeps ~22 significant bits per product (Markidis et al., "NVIDIA Tensor Core
 // Programmability, Performance & Precision", 2018, for the split scheme).
 //
-// CTA (persistent, as many per SM as shared and tensor memory allow): 21 warps in three roles
-// coupled only through mbarriers.  B (hi and lo, host-split, canonical K-major layout) stays in
-// shared memory.  X is produced in chunks of 16 amplitudes (32 K-columns) per group by 16
-// producer warps: every producer thread owns one group row m and a quarter of each chunk, keeps
-// six chunks of loads in flight in registers, splits them into hi/lo, writes them into a ring
-// of shared-memory chunk buffers and arrives on the buffer's "full" barrier.  One lane of the
-// MMA warp waits for full buffers, issues the 3 x 4 MMAs of a chunk and commits them to the
-// buffer's "empty" barrier (and, after a tile's last chunk, to the accumulator's barrier).  Two
-// accumulators alternate between tiles; 4 epilogue warps (one per TMEM lane subpartition, lane
-// = group row) read a finished accumulator, store its 128 x D outputs straight to HBM and hand
-// it back, so the MMAs of one tile overlap the epilogue of the previous one.
+// CTA (persistent, one per SM: it allocates all 512 tensor-memory columns): 21 warps in three
+// roles coupled only through mbarriers.  16 producer warps load chunks of 16 amplitudes
+// (32 K-columns) per group row, keeping six chunks of loads in flight in registers, and split
+// them into TF32 hi/lo; one lane of the MMA warp waits for full chunks, issues the 3 x 4 MMAs of
+// a chunk and commits them to the chunk's "empty" barrier (and, after a tile's last chunk, to
+// the accumulator's barrier); 4 epilogue warps (one per TMEM lane subpartition) read a finished
+// accumulator, store its outputs straight to HBM and hand it back.  Two accumulators alternate
+// between tiles, so the MMAs of one tile overlap the epilogue of the previous one.
+//
+// The operand the MMA reads once per issue from shared memory is the bound: a 128 x 128 x 8
+// TF32 MMA with both operands in shared memory reads 8 KB, more than shared memory delivers in
+// the MMA's own time.  So one operand always lives in tensor memory:
+//   - group-major form (dense_tc_gm_kernel, any targets but the transposed case): X in tensor
+//     memory, written by the producers with tcgen05.st into a ring of chunk slots, U (B
+//     operand) in shared memory;
+//   - transposed form (dense_tc_tr_kernel, 6 targets including qubits 0 and 1) and real
+//     7-target gates (dense_tc_real7_kernel): U is the A operand and sits in tensor memory, X
+//     chunks (B operand) in a six-deep shared-memory ring.
 //
 // Shared-memory operand layout (no swizzle, K-major): 8-row x 16-byte core matrices; core
 // matrices adjacent along K are 128 bytes apart (leading byte offset), adjacent along M/N
-// (K/4) * 128 bytes apart (stride byte offset).
-//
-// Transposed form (TR, 6 targets including qubits 0 and 1): when the targets are the lowest
-// qubits, a group's amplitudes are contiguous but consecutive groups are 2^k amplitudes apart,
-// and the group-major form above reads and writes 8-byte pieces at that stride.  TR computes
-//     Y^T[2D x 128] = B[2D x 2D] * X^T,
-// with B (the real form of U) as the MMA's A operand (M = 2D = 128) and the tile's 128 groups
-// as its B operand (N = 128), chunk by chunk along K as above.  Producers load each group's 16
-// amplitudes of a chunk as 16-byte vectors (a warp reads 8 groups x 64 contiguous bytes), and
-// the accumulator's TMEM lanes are output reals, so the epilogue's warp stores write 32
-// consecutive floats of one group.
+// (K/4) * 128 bytes apart (stride byte offset).  The host packs U in that layout; u_to_tmem
+// reads it from there into tensor memory.
 //
 // Every wait on an mbarrier is bounded; on timeout the kernel raises a flag in device memory
 // (read by qsim_device_status), skips the remaining work, releases its tensor memory and exits.
@@ -54,7 +52,6 @@ namespace tc {
 
 constexpr int kM = 128;      // groups per tile (MMA M)
 constexpr int kCH = 32;      // K-columns per chunk (16 complex amplitudes)
-constexpr int kNBuf = 3;     // chunk ring
 constexpr int kMaxFix = 40;
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
 
@@ -153,15 +150,10 @@ __device__ __forceinline__ unsigned long long insert_zeros(unsigned long long x,
 template <int K>
 struct Cfg {
     static constexpr int D = 1 << K;
-    static constexpr int N = 2 * D;       // MMA N (output reals per group)
+    static constexpr int N = 2 * D;       // output reals per group
     static constexpr int KK = 2 * D;      // reduction length
     static constexpr int NCH = KK / kCH;  // chunks per tile
     static constexpr int BBYTES = N * KK * 4;
-    static constexpr int ABYTES = kM * kCH * 4;
-    static constexpr int NBAR = 2 * kNBuf + 4;  // full/empty per buffer, accfull/accempty x2
-    static constexpr int SMEM = 2 * BBYTES + kNBuf * 2 * ABYTES + 8 * NBAR + 16 + 8 * D + 8 * kM;
-    static constexpr int TMEM_COLS = 2 * N;  // two accumulators: the MMAs of a tile overlap
-                                             // the previous tile's epilogue
     static constexpr unsigned IDESC = (1u << 4)          // D format F32
                                       | (2u << 7)        // A format TF32
                                       | (2u << 10)       // B format TF32
@@ -179,254 +171,6 @@ constexpr int kMmaWarp = kEpiWarp0 + 4;
 constexpr int kThreadsWS = (kMmaWarp + 1) * 32;
 constexpr int kPrefetch = 6;  // chunks of loads in flight per producer thread
 
-template <int K, bool TR>
-__global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
-    using C = Cfg<K>;
-    constexpr int D = C::D, N = C::N, KK = C::KK, NCH = C::NCH;
-    static_assert(!TR || N == kM, "the transposed form needs 2D = 128 output reals (6 targets)");
-    extern __shared__ __align__(1024) unsigned char sm[];
-    float *Bs = reinterpret_cast<float *>(sm);                               // [2][N*KK]
-    unsigned char *Aring = sm + 2 * C::BBYTES;                               // [kNBuf][2][ABYTES]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(Aring + kNBuf * 2 * C::ABYTES);
-    uint64_t *full = bars;                    // [kNBuf] producers -> MMA (count 256)
-    uint64_t *empty = bars + kNBuf;           // [kNBuf] MMA completion -> producers (commit)
-    uint64_t *accfull = bars + 2 * kNBuf;     // [2] MMA completion -> epilogue (commit)
-    uint64_t *accempty = bars + 2 * kNBuf + 2;  // [2] epilogue -> MMA (count 128)
-    unsigned *tslot = reinterpret_cast<unsigned *>(bars + C::NBAR);
-    long long *toff = reinterpret_cast<long long *>(tslot + 4);              // D entries
-    long long *goff = toff + D;  // kM entries: offset of group m of a tile from the tile's group 0
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // ---- set-up: B into shared memory, target offsets, barriers, tensor memory
-    {
-        const float4 *src = reinterpret_cast<const float4 *>(a.Bg);
-        float4 *dst = reinterpret_cast<float4 *>(Bs);
-        for (int i = tid; i < 2 * C::BBYTES / 16; i += kThreadsWS) dst[i] = src[i];
-        for (int c = tid; c < D; c += kThreadsWS) {
-            long long o = 0;
-            for (int b = 0; b < K; b++)
-                if ((c >> b) & 1) o |= 1ll << a.targets[b];
-            toff[c] = o;
-        }
-        // TR epilogue: group index = tile * 128 + m, whose zero-inserted offset splits into the
-        // tile's part and m's part (disjoint bits)
-        if (TR)
-            for (int mm = tid; mm < kM; mm += kThreadsWS)
-                goff[mm] = (long long)insert_zeros((unsigned long long)mm, a.fix, a.nfix);
-        if (tid == 0) {
-            for (int i = 0; i < kNBuf; i++) {
-                mbar_init(&full[i], kProducers);
-                mbar_init(&empty[i], 1);
-            }
-            for (int i = 0; i < 2; i++) {
-                mbar_init(&accfull[i], 1);
-                mbar_init(&accempty[i], 128);
-            }
-        }
-        if (warp == 0) {
-            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
-                         "r"((unsigned)C::TMEM_COLS)
-                         : "memory");
-            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    }
-    const unsigned tmem = *tslot;
-    float2 *psi = reinterpret_cast<float2 *>(a.psi);
-    const long long first = blockIdx.x, stride = gridDim.x;
-    const long long ntl = first < a.ntiles ? (a.ntiles - first + stride - 1) / stride : 0;
-    const long long total = ntl * NCH;
-    bool failed = false;
-
-    auto tile_base = [&](long long tile_i) -> unsigned long long {
-        const unsigned long long gidx = (unsigned long long)(first + tile_i * stride) * kM;
-        return insert_zeros(gidx, a.fix, a.nfix) | a.cmask;
-    };
-    auto group_base = [&](long long tile_i, int m) -> unsigned long long {
-        const unsigned long long gidx = (unsigned long long)(first + tile_i * stride) * kM + m;
-        return insert_zeros(gidx, a.fix, a.nfix) | a.cmask;
-    };
-
-    if (warp < kEpiWarp0) {
-        // ------------------------------------------------------------------ producers
-        // Group-major form: thread t owns group row m = t % 128 and quarter h = t / 128 of every
-        // chunk (amplitudes 4h .. 4h+3); rows m and m+8 share banks: every other row block
-        // swaps its amplitude pairs.
-        // TR: thread t owns group row m and amplitude pairs h and h + 4 of every chunk
-        // (amplitudes 2h, 2h+1, 2h+8, 2h+9 of its 16).  A warp is 8 rows x 4 consecutive pairs
-        // (8 runs of 64 bytes per vector load), a quarter-warp 8 rows x 1 pair (16-byte
-        // shared-memory stores into 8 distinct bank slots).
-        const int m = TR ? 8 * (tid >> 5) + (tid & 7) : tid & (kM - 1);
-        const int h = TR ? (tid >> 3) & 3 : tid >> 7;
-        const int sw = TR ? 0 : (m >> 3) & 1;
-        unsigned soff[kAmpsPT];  // canonical-layout byte offset of this thread's amplitude e
-#pragma unroll
-        for (int e = 0; e < kAmpsPT; e++) {
-            const int k = 2 * kAmpsPT * h + 2 * (e ^ sw);
-            soff[e] = (m >> 3) * 1024 + (k >> 2) * 128 + (m & 7) * 16 + (k & 3) * 4;
-        }
-        float2 r[kPrefetch][kAmpsPT];
-        // the row's group base changes once per tile: computed when a tile's first chunk loads
-        long long gb_tile = -1;
-        unsigned long long gb_row = 0;
-        auto load = [&](long long qq, float2(&rr)[kAmpsPT]) {
-            if (qq < total) {
-                if (qq / NCH != gb_tile) {
-                    gb_tile = qq / NCH;
-                    gb_row = group_base(gb_tile, m);
-                }
-                const unsigned long long gb = gb_row;
-                if (TR) {  // qubit 0 is a target: each pair is contiguous
-                    const int c0 = (int)(qq % NCH) * 16 + 2 * h;
-                    const float4 u0 = __ldcs(reinterpret_cast<const float4 *>(psi + gb + toff[c0]));
-                    const float4 u1 = __ldcs(reinterpret_cast<const float4 *>(psi + gb + toff[c0 + 8]));
-                    rr[0] = make_float2(u0.x, u0.y);
-                    rr[1] = make_float2(u0.z, u0.w);
-                    rr[2] = make_float2(u1.x, u1.y);
-                    rr[3] = make_float2(u1.z, u1.w);
-                } else {
-                    const int c0 = (int)(qq % NCH) * 16 + kAmpsPT * h;
-#pragma unroll
-                    for (int e = 0; e < kAmpsPT; e++) rr[e] = __ldcs(psi + gb + toff[c0 + e]);
-                }
-            }
-        };
-#pragma unroll
-        for (int p = 0; p < kPrefetch; p++) load(p, r[p]);
-        for (long long q0 = 0; q0 < total && !failed; q0 += kPrefetch) {
-#pragma unroll
-            for (int p = 0; p < kPrefetch; p++) {
-                const long long qq = q0 + p;
-                if (qq >= total || failed) break;
-                const int b = (int)(qq % kNBuf);
-                const long long use = qq / kNBuf;
-                if (use > 0 && !mbar_wait(&empty[b], (unsigned)((use - 1) & 1))) {
-                    failed = true;
-                    break;
-                }
-                unsigned char *ahi = Aring + b * 2 * C::ABYTES;
-                unsigned char *alo = ahi + C::ABYTES;
-                if (TR) {
-#pragma unroll
-                    for (int pi = 0; pi < 2; pi++) {  // pair h + 4 pi: chunk reals 4h + 16 pi .. +3
-                        const float2 x0 = r[p][2 * pi], x1 = r[p][2 * pi + 1];
-                        const unsigned off = (m >> 3) * 1024 + (h + 4 * pi) * 128 + (m & 7) * 16;
-                        const unsigned h0 = to_tf32(x0.x), h1 = to_tf32(x0.y);
-                        const unsigned h2 = to_tf32(x1.x), h3 = to_tf32(x1.y);
-                        *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(h0, h1, h2, h3);
-                        *reinterpret_cast<uint4 *>(alo + off) =
-                            make_uint4(to_tf32(x0.x - __uint_as_float(h0)), to_tf32(x0.y - __uint_as_float(h1)),
-                                       to_tf32(x1.x - __uint_as_float(h2)), to_tf32(x1.y - __uint_as_float(h3)));
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < kAmpsPT; e++) {
-                        const float2 x = sw ? r[p][e ^ 1] : r[p][e];
-                        const unsigned off = soff[e];
-                        const unsigned hx = to_tf32(x.x), hy = to_tf32(x.y);
-                        const unsigned lx = to_tf32(x.x - __uint_as_float(hx));
-                        const unsigned ly = to_tf32(x.y - __uint_as_float(hy));
-                        *reinterpret_cast<uint2 *>(ahi + off) = make_uint2(hx, hy);
-                        *reinterpret_cast<uint2 *>(alo + off) = make_uint2(lx, ly);
-                    }
-                }
-                load(qq + kPrefetch, r[p]);
-                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                mbar_arrive(&full[b]);
-            }
-        }
-    } else if (warp < kMmaWarp) {
-        // ------------------------------------------------------------------ epilogue
-        const int sub = warp - kEpiWarp0;         // TMEM lane subpartition
-        const int m = sub * 32 + lane;            // group row == TMEM lane (TR: output real)
-        const long long ta = TR ? toff[m >> 1] : 0;  // TR: amplitude of output real m
-        float *psif = reinterpret_cast<float *>(a.psi);
-        for (long long t = 0; t < ntl && !failed; t++) {
-            const int ab = (int)(t & 1);
-            if (!mbar_wait(&accfull[ab], (unsigned)((t >> 1) & 1))) {
-                failed = true;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const unsigned long long gb = TR ? tile_base(t) : group_base(t, m);
-            const unsigned acc = tmem + (unsigned)(ab * N) + ((unsigned)(sub * 32) << 16);
-#pragma unroll
-            for (int col = 0; col < N; col += 16) {
-                unsigned v[16];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-                      "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                    : "r"(acc + (unsigned)col));
-                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-                if (TR) {  // v[i] = output real m of tile group col + i
-#pragma unroll
-                    for (int i = 0; i < 16; i++)
-                        __stcs(psif + 2 * (long long)(gb + goff[col + i] + ta) + (m & 1), __uint_as_float(v[i]));
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 8; i++)
-                        __stcs(psi + gb + toff[col / 2 + i],
-                               make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])));
-                }
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-            mbar_arrive(&accempty[ab]);
-        }
-    } else if (lane == 0) {
-        // ------------------------------------------------------------------ MMA issuer
-        const unsigned aring_u32 = smem_u32(Aring);
-        const unsigned b_hi = smem_u32(Bs), b_lo = b_hi + C::BBYTES;
-        for (long long qq = 0; qq < total && !failed; qq++) {
-            const int b = (int)(qq % kNBuf);
-            const int j = (int)(qq % NCH);
-            const long long t = qq / NCH;
-            const int ab = (int)(t & 1);
-            if (j == 0 && t >= 2 && !mbar_wait(&accempty[ab], (unsigned)(((t >> 1) - 1) & 1))) {
-                failed = true;
-                break;
-            }
-            if (!mbar_wait(&full[b], (unsigned)((qq / kNBuf) & 1))) {
-                failed = true;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const unsigned a_hi = aring_u32 + b * 2 * C::ABYTES, a_lo = a_hi + C::ABYTES;
-            const unsigned acc = tmem + (unsigned)(ab * N);
-#pragma unroll
-            for (int kk = 0; kk < kCH / 8; kk++) {
-                const unsigned aoff = kk * 256;                       // 2 core matrices along K
-                const unsigned boff = (j * (kCH / 4) + kk * 2) * 128;
-                const uint64_t dAh = make_desc(a_hi + aoff, 128, 1024);
-                const uint64_t dAl = make_desc(a_lo + aoff, 128, 1024);
-                const uint64_t dBh = make_desc(b_hi + boff, 128, KK * 32);
-                const uint64_t dBl = make_desc(b_lo + boff, 128, KK * 32);
-                // group-major: D[group][real] = X U^T; TR: D[real][group] = U X^T (M = N = 128)
-                mma_tf32(acc, TR ? dBh : dAh, TR ? dAh : dBh, C::IDESC, (j == 0 && kk == 0) ? 0u : 1u);
-                mma_tf32(acc, TR ? dBl : dAh, TR ? dAh : dBl, C::IDESC, 1u);
-                mma_tf32(acc, TR ? dBh : dAl, TR ? dAl : dBh, C::IDESC, 1u);
-            }
-            commit_to(&empty[b]);
-            if (j == NCH - 1) commit_to(&accfull[ab]);
-        }
-    }
-    if (failed) atomicOr(&g_device_error, 1u);
-    __syncwarp();
-    // every MMA has completed once the epilogue warps consumed the last accumulator (or gave
-    // up after a bounded wait); only then is tensor memory released
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((unsigned)C::TMEM_COLS)
-                     : "memory");
-    }
-}
-
 // ---------------------------------------------------------------------------------------
 // Group-major form with the X operand in tensor memory (any targets the transposed form does not
 // take).  The same GEMM Y[128 x 2D] = X[128 x 2D] * B^T, but the MMA reads X (the A operand) from
@@ -437,8 +181,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_kernel(const Args a) {
 // every MMA (a 128 x 2D x 8 MMA read 8 KB of shared memory per issue, more than the SM's shared
 // memory delivers in the MMA's own time for 2D = 128), and the producers no longer write
 // shared memory at all.  Tensor memory: two accumulators of 2D columns and (512 - 4D) / 64
-// chunk slots (4 for 6 targets).  Same roles, barriers and bounded waits as dense_tc_kernel;
-// 21 warps (the register file is split over the SM's four sub-partitions, so the sub-partition
+// chunk slots (4 for 6 targets).  21 warps (the register file is split over the SM's four sub-partitions, so the sub-partition
 // holding 6 warps caps a thread at 80 registers: the producers keep 6 chunks of loads in flight
 // within that).
 template <int K>
@@ -662,54 +405,89 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// Real 7-target gates (a real U, e.g. the eigenvector matrix of a real symmetric system) on the
-// lowest qubits, complex64.  For real U the complex product splits into two real ones,
-// Y_re = U X_re and Y_im = U X_im, so one real GEMM does both:
-//     Y^T[128 out amps x 128 rows] = U[128 x 128] * X^T,   row = (group, re or im),
-// U (TF32 hi/lo, 128 KB) is the MMA's A operand, a chunk of 32 input amplitudes of 64 groups
-// (128 rows) its B operand, and the accumulator's TMEM lanes are output amplitudes, so each
-// epilogue warp stores 32 consecutive complex amplitudes of one group.  Same roles, barriers
-// and bounded waits as dense_tc_kernel.
-namespace tcr {
-constexpr int D = 128;           // amplitudes per group (7 targets)
-constexpr int KK = 128;          // reduction length: input amplitudes
-constexpr int MG = 64;           // groups per tile (128 rows: re and im of each)
-constexpr int NCH = KK / kCH;    // chunks of 32 input amplitudes
-constexpr int BBYTES = D * KK * 4;
-constexpr int ABYTES = 2 * MG * kCH * 4;
-constexpr int NBAR = 2 * kNBuf + 4;
-constexpr int SMEM = 2 * BBYTES + kNBuf * 2 * ABYTES + 8 * NBAR + 16 + 8 * D + 8 * MG;
-constexpr int TMEM_COLS = 2 * 2 * MG;
-constexpr unsigned IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)((2 * MG) >> 3) << 17) |
-                           ((unsigned)(D >> 4) << 24);
-}  // namespace tcr
+// U as an MMA A operand in tensor memory.  Ug holds U's hi part and then its lo part, each 128
+// rows n x 128 columns k in the canonical shared-memory layout (8-row x 16-byte core matrices,
+// K-major).  Row n goes to TMEM lane n, column k to columns col0 + k (hi) and col0 + 128 + k (lo).
+// Called by the 16 producer warps: warp w writes lanes 32 (w mod 4) .. +31 (the lanes its warp
+// may access) and columns 32 (w / 4) .. +31 of each half.
+__device__ __forceinline__ void u_to_tmem(const float *Ug, unsigned tmem, unsigned col0, int warp, int lane) {
+    constexpr int KK = 128;
+    const int q = warp & 3, part = warp >> 2, n = 32 * q + lane;
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+        const char *src = reinterpret_cast<const char *>(Ug + (size_t)half * 128 * KK);
+        unsigned v[32];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int k = 32 * part + 4 * i;
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(src + (size_t)(n >> 3) * (KK * 32) + (size_t)(k >> 2) * 128 +
+                                                                    (size_t)(n & 7) * 16));
+            v[4 * i] = __float_as_uint(f.x);
+            v[4 * i + 1] = __float_as_uint(f.y);
+            v[4 * i + 2] = __float_as_uint(f.z);
+            v[4 * i + 3] = __float_as_uint(f.w);
+        }
+        const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + col0 + (unsigned)(half * KK + 32 * part);
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+            "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(ta),
+            "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+            "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+            "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+            "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+            : "memory");
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
 
-__global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Args a) {
-    using namespace tcr;
+// ---------------------------------------------------------------------------------------
+// Transposed form (6 targets including qubits 0 and 1).  When the targets are the lowest qubits,
+// a group's amplitudes are contiguous but consecutive groups are 2^k amplitudes apart, and the
+// group-major form would read and write 8-byte pieces at that stride.  This form computes
+//     Y^T[2D x 128] = B[2D x 2D] * X^T,
+// with B (the real form of U, hi and lo) as the MMA's A operand, held in tensor memory next to
+// the two accumulators (U columns 256..511), and the tile's 128 groups as its B operand (N =
+// 128), a ring of six shared-memory chunks of 32 K-columns.  Producers load each group's 16
+// amplitudes of a chunk as 16-byte vectors (a warp reads 8 groups x 64 contiguous bytes), and
+// the accumulator's TMEM lanes are output reals, so the epilogue's warp stores write 32
+// consecutive floats of one group.  Roles, barriers and bounded waits as in the group-major
+// kernels.
+namespace tct {
+constexpr int K = 6, D = 64, N = 128, KK = 128, NCH = KK / kCH;
+constexpr int ABYTES = kM * kCH * 4;  // one chunk (hi or lo)
+constexpr int NBUF = 6;
+constexpr int NBAR = 2 * NBUF + 5;
+constexpr int SMEM = NBUF * 2 * ABYTES + 8 * NBAR + 16 + 8 * D + 8 * kM;
+constexpr int UCOL = 2 * N;  // tensor memory: two accumulators, then U hi and U lo
+}  // namespace tct
+
+__global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_tr_kernel(const Args a) {
+    using namespace tct;
     extern __shared__ __align__(1024) unsigned char sm[];
-    float *Bs = reinterpret_cast<float *>(sm);  // U hi, U lo
-    unsigned char *Aring = sm + 2 * BBYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(Aring + kNBuf * 2 * ABYTES);
-    uint64_t *full = bars, *empty = bars + kNBuf, *accfull = bars + 2 * kNBuf, *accempty = bars + 2 * kNBuf + 2;
+    unsigned char *Aring = sm;  // [NBUF][2][ABYTES]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(Aring + NBUF * 2 * ABYTES);
+    uint64_t *full = bars;                 // [NBUF] producers -> MMA (count 512)
+    uint64_t *empty = bars + NBUF;         // [NBUF] MMA completion -> producers (commit)
+    uint64_t *accfull = bars + 2 * NBUF;   // [2] MMA completion -> epilogue (commit)
+    uint64_t *accempty = accfull + 2;      // [2] epilogue -> MMA (count 128)
+    uint64_t *drain = accfull + 4;         // MMA completion before tensor memory is freed
     unsigned *tslot = reinterpret_cast<unsigned *>(bars + NBAR);
     long long *toff = reinterpret_cast<long long *>(tslot + 4);  // D entries
-    long long *goff = toff + D;                                  // MG entries
+    long long *goff = toff + D;  // kM entries: offset of group m of a tile from the tile's group 0
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     {
-        const float4 *src = reinterpret_cast<const float4 *>(a.Bg);
-        float4 *dst = reinterpret_cast<float4 *>(Bs);
-        for (int i = tid; i < 2 * BBYTES / 16; i += kThreadsWS) dst[i] = src[i];
         for (int c = tid; c < D; c += kThreadsWS) {
             long long o = 0;
-            for (int b = 0; b < 7; b++)
+            for (int b = 0; b < K; b++)
                 if ((c >> b) & 1) o |= 1ll << a.targets[b];
             toff[c] = o;
         }
-        for (int g = tid; g < MG; g += kThreadsWS) goff[g] = (long long)insert_zeros((unsigned long long)g, a.fix, a.nfix);
+        // group index = tile * 128 + m, whose zero-inserted offset splits into the tile's part and
+        // m's part (disjoint bits)
+        for (int mm = tid; mm < kM; mm += kThreadsWS) goff[mm] = (long long)insert_zeros((unsigned long long)mm, a.fix, a.nfix);
         if (tid == 0) {
-            for (int i = 0; i < kNBuf; i++) {
+            for (int i = 0; i < NBUF; i++) {
                 mbar_init(&full[i], kProducers);
                 mbar_init(&empty[i], 1);
             }
@@ -717,10 +495,11 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Arg
                 mbar_init(&accfull[i], 1);
                 mbar_init(&accempty[i], 128);
             }
+            mbar_init(drain, 1);
         }
         if (warp == 0) {
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
-                         "r"((unsigned)TMEM_COLS)
+                         "r"(512u)
                          : "memory");
             asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -730,6 +509,229 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Arg
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     }
     const unsigned tmem = *tslot;
+    if (warp < kEpiWarp0) u_to_tmem(a.Bg, tmem, (unsigned)UCOL, warp, lane);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    float2 *psi = reinterpret_cast<float2 *>(a.psi);
+    const long long first = blockIdx.x, stride = gridDim.x;
+    const long long ntl = first < a.ntiles ? (a.ntiles - first + stride - 1) / stride : 0;
+    const long long total = ntl * NCH;
+    bool failed = false;
+    auto tile_base = [&](long long tile_i) -> unsigned long long {
+        const unsigned long long gidx = (unsigned long long)(first + tile_i * stride) * kM;
+        return insert_zeros(gidx, a.fix, a.nfix) | a.cmask;
+    };
+
+    if (warp < kEpiWarp0) {
+        // ------------------------------------------------------------------ producers
+        // thread t owns group row m and amplitude pairs h and h + 4 of every chunk (amplitudes
+        // 2h, 2h+1, 2h+8, 2h+9 of its 16).  A warp is 8 rows x 4 consecutive pairs (8 runs of
+        // 64 bytes per vector load), a quarter-warp 8 rows x 1 pair (16-byte shared-memory
+        // stores into 8 distinct bank slots).
+        const int m = 8 * (tid >> 5) + (tid & 7);
+        const int h = (tid >> 3) & 3;
+        float2 r[kPrefetch][kAmpsPT];
+        long long gb_tile = -1;
+        unsigned long long gb_row = 0;
+        auto load = [&](long long qq, float2(&rr)[kAmpsPT]) {
+            if (qq < total) {
+                if (qq / NCH != gb_tile) {
+                    gb_tile = qq / NCH;
+                    gb_row = tile_base(gb_tile) + (unsigned long long)goff[m];
+                }
+                // qubit 0 is a target: each pair is contiguous
+                const int c0 = (int)(qq % NCH) * 16 + 2 * h;
+                const float4 u0 = __ldcs(reinterpret_cast<const float4 *>(psi + gb_row + toff[c0]));
+                const float4 u1 = __ldcs(reinterpret_cast<const float4 *>(psi + gb_row + toff[c0 + 8]));
+                rr[0] = make_float2(u0.x, u0.y);
+                rr[1] = make_float2(u0.z, u0.w);
+                rr[2] = make_float2(u1.x, u1.y);
+                rr[3] = make_float2(u1.z, u1.w);
+            }
+        };
+#pragma unroll
+        for (int p = 0; p < kPrefetch; p++) load(p, r[p]);
+        for (long long q0 = 0; q0 < total && !failed; q0 += kPrefetch) {
+#pragma unroll
+            for (int p = 0; p < kPrefetch; p++) {
+                const long long qq = q0 + p;
+                if (qq >= total || failed) break;
+                const int b = (int)(qq % NBUF);
+                const long long use = qq / NBUF;
+                if (use > 0 && !mbar_wait(&empty[b], (unsigned)((use - 1) & 1))) {
+                    failed = true;
+                    break;
+                }
+                unsigned char *ahi = Aring + b * 2 * ABYTES;
+                unsigned char *alo = ahi + ABYTES;
+#pragma unroll
+                for (int pi = 0; pi < 2; pi++) {  // pair h + 4 pi: chunk reals 4h + 16 pi .. +3
+                    const float2 x0 = r[p][2 * pi], x1 = r[p][2 * pi + 1];
+                    const unsigned off = (m >> 3) * 1024 + (h + 4 * pi) * 128 + (m & 7) * 16;
+                    const unsigned h0 = to_tf32(x0.x), h1 = to_tf32(x0.y);
+                    const unsigned h2 = to_tf32(x1.x), h3 = to_tf32(x1.y);
+                    *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(h0, h1, h2, h3);
+                    *reinterpret_cast<uint4 *>(alo + off) =
+                        make_uint4(to_tf32(x0.x - __uint_as_float(h0)), to_tf32(x0.y - __uint_as_float(h1)),
+                                   to_tf32(x1.x - __uint_as_float(h2)), to_tf32(x1.y - __uint_as_float(h3)));
+                }
+                load(qq + kPrefetch, r[p]);
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive(&full[b]);
+            }
+        }
+    } else if (warp < kMmaWarp) {
+        // ------------------------------------------------------------------ epilogue
+        const int sub = warp - kEpiWarp0;          // TMEM lane subpartition
+        const int m = sub * 32 + lane;             // output real
+        const long long ta = toff[m >> 1];         // its amplitude
+        float *psif = reinterpret_cast<float *>(a.psi);
+        for (long long t = 0; t < ntl && !failed; t++) {
+            const int ab = (int)(t & 1);
+            if (!mbar_wait(&accfull[ab], (unsigned)((t >> 1) & 1))) {
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned long long gb = tile_base(t);
+            const unsigned acc = tmem + (unsigned)(ab * N) + ((unsigned)(sub * 32) << 16);
+#pragma unroll
+            for (int col = 0; col < N; col += 16) {
+                unsigned v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                      "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                    : "r"(acc + (unsigned)col));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                // v[i] = output real m of tile group col + i
+#pragma unroll
+                for (int i = 0; i < 16; i++)
+                    __stcs(psif + 2 * (long long)(gb + goff[col + i] + ta) + (m & 1), __uint_as_float(v[i]));
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            mbar_arrive(&accempty[ab]);
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------------------ MMA issuer
+        const unsigned aring_u32 = smem_u32(Aring);
+        const unsigned u_hi = tmem + (unsigned)UCOL, u_lo = u_hi + (unsigned)KK;
+        for (long long qq = 0; qq < total && !failed; qq++) {
+            const int b = (int)(qq % NBUF);
+            const int j = (int)(qq % NCH);
+            const long long t = qq / NCH;
+            const int ab = (int)(t & 1);
+            if (j == 0 && t >= 2 && !mbar_wait(&accempty[ab], (unsigned)(((t >> 1) - 1) & 1))) {
+                failed = true;
+                break;
+            }
+            if (!mbar_wait(&full[b], (unsigned)((qq / NBUF) & 1))) {
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const unsigned acc = tmem + (unsigned)(ab * N);
+            const unsigned x_hi = aring_u32 + b * 2 * ABYTES, x_lo = x_hi + ABYTES;
+#pragma unroll
+            for (int kk = 0; kk < kCH / 8; kk++) {
+                const unsigned uc = (unsigned)(j * kCH + kk * 8);  // U columns of this K-step
+                const uint64_t dXh = make_desc(x_hi + kk * 256, 128, 1024);  // 2 core matrices along K
+                const uint64_t dXl = make_desc(x_lo + kk * 256, 128, 1024);
+                // Y^T = U X^T in 3xTF32: Uhi Xhi + Ulo Xhi + Uhi Xlo
+                mma_tf32_ta(acc, u_hi + uc, dXh, Cfg<K>::IDESC, (j == 0 && kk == 0) ? 0u : 1u);
+                mma_tf32_ta(acc, u_lo + uc, dXh, Cfg<K>::IDESC, 1u);
+                mma_tf32_ta(acc, u_hi + uc, dXl, Cfg<K>::IDESC, 1u);
+            }
+            commit_to(&empty[b]);
+            if (j == NCH - 1) commit_to(&accfull[ab]);
+        }
+        commit_to(drain);  // tensor memory is released only after every MMA has completed
+        if (!mbar_wait(drain, 0u)) failed = true;
+    }
+    if (failed) atomicOr(&g_device_error, 1u);
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512u) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Real 7-target gates (a real U, e.g. the eigenvector matrix of a real symmetric system) on the
+// lowest qubits, complex64.  For real U the complex product splits into two real ones,
+// Y_re = U X_re and Y_im = U X_im, so one real GEMM does both:
+//     Y^T[128 out amps x 128 rows] = U[128 x 128] * X^T,   row = (group, re or im),
+// U (TF32 hi/lo) is the MMA's A operand, held in tensor memory next to the two accumulators, a
+// chunk of 32 input amplitudes of 64 groups (128 rows) its B operand, in a six-deep shared-memory
+// ring, and the accumulator's TMEM lanes are output amplitudes, so each epilogue warp stores 32
+// consecutive complex amplitudes of one group.  Roles, barriers and bounded waits as in the
+// other tensor-core kernels.
+namespace tcr {
+constexpr int D = 128;           // amplitudes per group (7 targets)
+constexpr int KK = 128;          // reduction length: input amplitudes
+constexpr int MG = 64;           // groups per tile (128 rows: re and im of each)
+constexpr int NCH = KK / kCH;    // chunks of 32 input amplitudes
+constexpr int BBYTES = D * KK * 4;
+constexpr int ABYTES = 2 * MG * kCH * 4;
+constexpr int NBUF = 6;         // chunk ring (U lives in tensor memory, so shared memory holds X only)
+constexpr int NBAR = 2 * NBUF + 5;
+constexpr int SMEM = NBUF * 2 * ABYTES + 8 * NBAR + 16 + 8 * D + 8 * MG;
+constexpr int UCOL = 2 * 2 * MG;  // tensor memory: two accumulators, then U hi and U lo (512 columns)
+constexpr unsigned IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)((2 * MG) >> 3) << 17) |
+                           ((unsigned)(D >> 4) << 24);
+}  // namespace tcr
+
+__global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Args a) {
+    using namespace tcr;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *Aring = sm;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(Aring + NBUF * 2 * ABYTES);
+    uint64_t *full = bars, *empty = bars + NBUF, *accfull = bars + 2 * NBUF, *accempty = bars + 2 * NBUF + 2;
+    uint64_t *drain = bars + 2 * NBUF + 4;
+    unsigned *tslot = reinterpret_cast<unsigned *>(bars + NBAR);
+    long long *toff = reinterpret_cast<long long *>(tslot + 4);  // D entries
+    long long *goff = toff + D;                                  // MG entries
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    {
+        for (int c = tid; c < D; c += kThreadsWS) {
+            long long o = 0;
+            for (int b = 0; b < 7; b++)
+                if ((c >> b) & 1) o |= 1ll << a.targets[b];
+            toff[c] = o;
+        }
+        for (int g = tid; g < MG; g += kThreadsWS) goff[g] = (long long)insert_zeros((unsigned long long)g, a.fix, a.nfix);
+        if (tid == 0) {
+            for (int i = 0; i < NBUF; i++) {
+                mbar_init(&full[i], kProducers);
+                mbar_init(&empty[i], 1);
+            }
+            for (int i = 0; i < 2; i++) {
+                mbar_init(&accfull[i], 1);
+                mbar_init(&accempty[i], 128);
+            }
+            mbar_init(drain, 1);
+        }
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                         "r"(512u)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    }
+    const unsigned tmem = *tslot;
+    if (warp < kEpiWarp0) u_to_tmem(a.Bg, tmem, (unsigned)UCOL, warp, lane);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     float2 *psi = reinterpret_cast<float2 *>(a.psi);
     const long long first = blockIdx.x, stride = gridDim.x;
     const long long ntl = first < a.ntiles ? (a.ntiles - first + stride - 1) / stride : 0;
@@ -778,8 +780,8 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Arg
             for (int p = 0; p < kPrefetch; p++) {
                 const long long qq = q0 + p;
                 if (qq >= total || failed) break;
-                const int b = (int)(qq % kNBuf);
-                const long long use = qq / kNBuf;
+                const int b = (int)(qq % NBUF);
+                const long long use = qq / NBUF;
                 if (use > 0 && !mbar_wait(&empty[b], (unsigned)((use - 1) & 1))) {
                     failed = true;
                     break;
@@ -838,9 +840,9 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Arg
     } else if (lane == 0) {
         // ------------------------------------------------------------------ MMA issuer
         const unsigned aring_u32 = smem_u32(Aring);
-        const unsigned u_hi = smem_u32(Bs), u_lo = u_hi + BBYTES;
+        const unsigned u_hi = tmem + (unsigned)UCOL, u_lo = u_hi + (unsigned)KK;
         for (long long qq = 0; qq < total && !failed; qq++) {
-            const int b = (int)(qq % kNBuf);
+            const int b = (int)(qq % NBUF);
             const int j = (int)(qq % NCH);
             const long long t = qq / NCH;
             const int ab = (int)(t & 1);
@@ -848,7 +850,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Arg
                 failed = true;
                 break;
             }
-            if (!mbar_wait(&full[b], (unsigned)((qq / kNBuf) & 1))) {
+            if (!mbar_wait(&full[b], (unsigned)((qq / NBUF) & 1))) {
                 failed = true;
                 break;
             }
@@ -857,18 +859,18 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Arg
             const unsigned x_hi = aring_u32 + b * 2 * ABYTES, x_lo = x_hi + ABYTES;
 #pragma unroll
             for (int kk = 0; kk < kCH / 8; kk++) {
-                const unsigned uoff = (j * (kCH / 4) + kk * 2) * 128;
-                const uint64_t dUh = make_desc(u_hi + uoff, 128, KK * 32);
-                const uint64_t dUl = make_desc(u_lo + uoff, 128, KK * 32);
+                const unsigned uc = (unsigned)(j * kCH + kk * 8);  // U columns of this K-step
                 const uint64_t dXh = make_desc(x_hi + kk * 256, 128, 1024);
                 const uint64_t dXl = make_desc(x_lo + kk * 256, 128, 1024);
-                mma_tf32(acc, dUh, dXh, IDESC, (j == 0 && kk == 0) ? 0u : 1u);
-                mma_tf32(acc, dUl, dXh, IDESC, 1u);
-                mma_tf32(acc, dUh, dXl, IDESC, 1u);
+                mma_tf32_ta(acc, u_hi + uc, dXh, IDESC, (j == 0 && kk == 0) ? 0u : 1u);
+                mma_tf32_ta(acc, u_lo + uc, dXh, IDESC, 1u);
+                mma_tf32_ta(acc, u_hi + uc, dXl, IDESC, 1u);
             }
             commit_to(&empty[b]);
             if (j == NCH - 1) commit_to(&accfull[ab]);
         }
+        commit_to(drain);  // tensor memory is released only after every MMA has completed
+        if (!mbar_wait(drain, 0u)) failed = true;
     }
     if (failed) atomicOr(&g_device_error, 1u);
     __syncwarp();
@@ -876,8 +878,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Arg
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((unsigned)TMEM_COLS)
-                     : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512u) : "memory");
     }
 }
 
@@ -1002,26 +1003,18 @@ static void launch_tc_gm(const tc::Args &a, int sms, cudaStream_t st) {
     note_launches(1, QSIM_KERNEL_DENSE_TC);
 }
 
-template <int K, bool TR>
-static void launch_tc_t(const tc::Args &a, int sms, cudaStream_t st) {
-    using C = tc::Cfg<K>;
+static void launch_tc_tr(const tc::Args &a, int sms, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc::dense_tc_kernel<K, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-        if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_kernel attribute: ") + cudaGetErrorString(e));
+        cudaError_t e = cudaFuncSetAttribute(tc::dense_tc_tr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::tct::SMEM);
+        if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_tr_kernel attribute: ") + cudaGetErrorString(e));
         attr = true;
     }
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc::dense_tc_kernel<K, TR>, tc::kThreadsWS, C::SMEM);
-        if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-        // tensor memory: every resident CTA holds TMEM_COLS of the SM's 512 columns
-        per_sm = std::min(per_sm, 512 / C::TMEM_COLS);
-    }
-    const long long grid = std::min<long long>(a.ntiles, (long long)sms * per_sm);
-    tc::dense_tc_kernel<K, TR><<<(int)grid, tc::kThreadsWS, C::SMEM, st>>>(a);
+    // one CTA per SM: it holds all 512 tensor-memory columns
+    const long long grid = std::min<long long>(a.ntiles, (long long)sms);
+    tc::dense_tc_tr_kernel<<<(int)grid, tc::kThreadsWS, tc::tct::SMEM, st>>>(a);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_kernel: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_tr_kernel: ") + cudaGetErrorString(e));
     note_launches(1, QSIM_KERNEL_DENSE_TC);
 }
 
@@ -1052,7 +1045,7 @@ bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const 
     switch (K) {
         case 4: launch_tc_gm<4>(a, sms, st); break;
         case 5: launch_tc_gm<5>(a, sms, st); break;
-        case 6: tr ? launch_tc_t<6, true>(a, sms, st) : launch_tc_gm<6>(a, sms, st); break;
+        case 6: tr ? launch_tc_tr(a, sms, st) : launch_tc_gm<6>(a, sms, st); break;
         default: return false;
     }
     return true;
