@@ -196,7 +196,7 @@ int qsim_launch_counts(unsigned long long *counts, int n);
                                     runs: 4 for complex64, 3 for complex128)                       */
 #define QSIM_TUNE_DFT_PREFETCH 2 /* pass kernels: L2 prefetch distance in tiles (0 off; bulk-copy
                                     kernels prefetch with a bulk tensor prefetch)                  */
-#define QSIM_TUNE_DENSE_TC 3     /* complex64 dense gates: bit k set = gates of k targets (4..6)
+#define QSIM_TUNE_DENSE_TC 3     /* complex64 dense gates: bit k set = gates of k targets (3..6)
                                     on the tensor cores; bit 7 = real 7-target gates (and real
                                     6-target gates on qubits 0 and 1) on the tensor cores          */
 #define QSIM_TUNE_FUSE_WIDTH 4   /* width qsim_fuse uses when called with max_k = 0 (the
@@ -228,7 +228,7 @@ typedef struct {
     int n_qubits;           /* state size the measurements were taken on                       */
     int values[QSIM_TUNE_COUNT]; /* the table after tuning                                      */
     double dft_ms;          /* fastest Fourier-pass variant, ms per pass                        */
-    double dense_ms[3];     /* complex64 dense gates of 4, 5, 6 targets: faster kernel, ms/gate */
+    double dense_ms[4];     /* complex64 dense gates of 3, 4, 5, 6 targets: faster kernel, ms/gate */
     double fuse_ms[5];      /* fused gate-level test circuit at widths 2..6, ms per application */
 } qsim_tune_report;
 
@@ -398,14 +398,16 @@ int qsim_batch_create(const qsim_circuit *const *cs, void *const *states, int co
 int hhl_batch_create(const hhl_circuit *const *hs, const qsim_circuit *const *fused,
                      void *const *states, int count, int dtype, qsim_batch **out);
 
-/* Run the batch: one persistent kernel on `stream`, nothing else (no allocation, no copy, no
- * synchronization; the kernel resets its own work counter when it ends), so the call can be
- * captured into a CUDA graph.  Runs of one batch must not overlap (same stream, or ordered).
- * Each CTA takes whole circuits (most expensive first); a state of up to 2^13 (complex128) or
- * 2^14 (complex64) amplitudes stays in shared memory for the whole circuit, larger ones are
- * updated in place.  One CTA runs one circuit in a fixed order, so a
- * circuit's result is bit-identical whatever else is in the batch; it equals qsim_apply of
- * the same circuit up to rounding (different kernels).  Errors: EINVAL, ECUDA. */
+/* Run the batch: at most two persistent kernels on `stream`, nothing else (no allocation, no
+ * copy, no synchronization; each kernel resets its own work counter when it ends), so the call
+ * can be captured into a CUDA graph.  Runs of one batch must not overlap (same stream, or
+ * ordered).  Circuits whose state exceeds 2^13 (complex128) or 2^14 (complex64) amplitudes
+ * run first, each on a team of 4 CTAs (a thread-block cluster) that splits every operation
+ * and updates the state in place; then every other circuit runs on one CTA with its state in
+ * shared memory.  Within each launch circuits go most expensive first.  A circuit always runs
+ * on the same kind of team in a fixed order, so its result is bit-identical whatever else is
+ * in the batch; it equals qsim_apply of the same circuit up to rounding (different kernels).
+ * Errors: EINVAL, ECUDA. */
 int qsim_batch_run(qsim_batch *b, void *stream);
 
 /* After an HHL batch ran on `stream`: wait for `stream` and write, for batch entry i in order,

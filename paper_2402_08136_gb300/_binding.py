@@ -84,7 +84,7 @@ class _ShardStep(ctypes.Structure):
 
 class _TuneReport(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int), ("values", ctypes.c_int * QSIM_TUNE_COUNT),
-                ("dft_ms", ctypes.c_double), ("dense_ms", ctypes.c_double * 3),
+                ("dft_ms", ctypes.c_double), ("dense_ms", ctypes.c_double * 4),
                 ("fuse_ms", ctypes.c_double * 5)]
 
 
@@ -431,7 +431,7 @@ def qsim_autotune(state, stream=None) -> dict:
     _check(library().qsim_autotune(ctypes.c_void_p(state.data_ptr()), n, _dtype_of(state), _stream_ptr(stream),
                                    ctypes.byref(r)))
     return {"n_qubits": r.n_qubits, "table": {TUNE_NAMES[k]: r.values[k] for k in range(QSIM_TUNE_COUNT)},
-            "dft_ms": r.dft_ms, "dense_ms": {str(4 + i): r.dense_ms[i] for i in range(3)},
+            "dft_ms": r.dft_ms, "dense_ms": {str(3 + i): r.dense_ms[i] for i in range(4)},
             "fuse_ms": {str(2 + i): r.fuse_ms[i] for i in range(5)}}
 
 

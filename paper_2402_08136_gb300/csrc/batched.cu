@@ -74,10 +74,43 @@ __device__ __forceinline__ unsigned expand(unsigned g, unsigned fixmask) {
     return g;
 }
 
-template <typename V, int K, bool REAL>
-__device__ void op_dense(V *psi, int n, const BOp &op, const V *U, int tid) {
+// A circuit runs on a team: one CTA (CS = 1), or the CS CTAs of a thread-block cluster for a
+// state too large for one CTA's shared memory (it stays in global memory, L2-resident).  vt is
+// the thread's index in the team, team_sync<CS> the barrier between steps of an operation.
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+
+template <int CS>
+__device__ __forceinline__ void team_sync() {
+    if (CS == 1) {
+        __syncthreads();
+    } else {
+        // every thread of every CTA of the cluster; release / acquire order the global-memory
+        // updates of one step before the next step's reads in the other CTAs
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+    }
+}
+
+// store a 32-bit / 64-bit value into the shared memory of CTA `rank` of the cluster, at the
+// address that `local` has in this CTA
+__device__ __forceinline__ void st_cluster(const void *local, unsigned rank, unsigned v) {
+    unsigned a = (unsigned)__cvta_generic_to_shared(local), ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("st.shared::cluster.u32 [%0], %1;\n" ::"r"(ra), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster(const void *local, unsigned rank, double v) {
+    unsigned a = (unsigned)__cvta_generic_to_shared(local), ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("st.shared::cluster.f64 [%0], %1;\n" ::"r"(ra), "d"(v) : "memory");
+}
+
+template <typename V, int K, bool REAL, int CS>
+__device__ void op_dense(V *psi, int n, const BOp &op, const V *U, unsigned vt) {
     constexpr int D = 1 << K;
-    constexpr int NT = Threads<V>::n;
+    constexpr int NT = CS * Threads<V>::n;
     // independent groups per iteration (their loads overlap); complex128 keeps the register
     // count of the 3..5-target gates in check with one group
     constexpr int ILP = (K <= 2 || (K <= 4 && sizeof(V) == 8)) ? 2 : 1;
@@ -99,14 +132,14 @@ __device__ void op_dense(V *psi, int n, const BOp &op, const V *U, int tid) {
         // from its stores.  ngroups and NT are powers of two.  complex64 keeps the loop: its
         // arithmetic is cheap and the loop's two interleaved groups pay more than the split.
         const int S = min(D, NT / (int)ngroups);
-        const unsigned gi = (unsigned)tid / (unsigned)S;
-        const int s = tid & (S - 1);
+        const unsigned gi = vt / (unsigned)S;
+        const int s = (int)(vt & (unsigned)(S - 1));
         const bool live = gi < ngroups;
         const unsigned base = live ? (expand(gi, op.fixmask) | op.cmask) : 0u;
         V x[D];
 #pragma unroll
         for (int c = 0; c < D; c++) x[c] = live ? psi[base + offs[c]] : V{0, 0};
-        __syncthreads();
+        team_sync<CS>();
         if (!live) return;
 #pragma unroll 1
         for (int r = s; r < D; r += S) {
@@ -130,7 +163,7 @@ __device__ void op_dense(V *psi, int n, const BOp &op, const V *U, int tid) {
         }
         return;
     }
-    for (unsigned g0 = tid; g0 < ngroups; g0 += ILP * NT) {
+    for (unsigned g0 = vt; g0 < ngroups; g0 += ILP * NT) {
         unsigned base[ILP];
         bool live[ILP];
         V x[ILP][D];
@@ -177,9 +210,9 @@ __device__ __forceinline__ V cmulb(V a, V b) {
 // bits below j, from the table W[e] = exp(s 2 pi i e / 2^K), e = r 2^(K-1-j)), a barrier after
 // each, then one pass that undoes the digit reversal of the DFT, scales by 2^(-K/2) and
 // applies the output twiddle.  The input twiddle, if any, is a pass of its own first.
-template <typename V>
-__device__ void op_fourier(V *psi, int n, const BOp &op, const V *data, int tid, bool walsh) {
-    constexpr int NT = Threads<V>::n;
+template <typename V, int CS>
+__device__ void op_fourier(V *psi, int n, const BOp &op, const V *data, unsigned vt, bool walsh) {
+    constexpr int NT = CS * Threads<V>::n;
     using Rr = decltype(V{}.x);
     const int K = op.k, f0 = op.c0;
     const unsigned N = 1u << n, fmask = ((1u << K) - 1u) << f0;
@@ -193,8 +226,8 @@ __device__ void op_fourier(V *psi, int n, const BOp &op, const V *data, int tid,
         return cmulb(Tlo[q & tmask], Thi[q >> hT]);
     };
     if (twmode == 1) {
-        for (unsigned i = tid; i < N; i += NT) psi[i] = cmulb(psi[i], tw(i, (i & fmask) >> f0));
-        __syncthreads();
+        for (unsigned i = vt; i < N; i += NT) psi[i] = cmulb(psi[i], tw(i, (i & fmask) >> f0));
+        team_sync<CS>();
     }
     for (int j = K - 1; j >= 0; j--) {
         const int p = f0 + j;
@@ -202,7 +235,7 @@ __device__ void op_fourier(V *psi, int n, const BOp &op, const V *data, int tid,
         // two independent pairs per iteration: their loads are in flight together (states
         // updated in place in L2 would otherwise wait for one round trip per pair)
         constexpr int U4 = 2;
-        for (unsigned g0 = tid; g0 < N / 2; g0 += U4 * NT) {
+        for (unsigned g0 = vt; g0 < N / 2; g0 += U4 * NT) {
             V a[U4], b[U4];
             unsigned i0[U4];
 #pragma unroll
@@ -228,10 +261,10 @@ __device__ void op_fourier(V *psi, int n, const BOp &op, const V *data, int tid,
                 psi[i0[e] | bit] = d;
             }
         }
-        __syncthreads();
+        team_sync<CS>();
     }
     const Rr scale = (K & 1) ? (Rr)(0.70710678118654752440 / (double)(1u << (K / 2))) : (Rr)(1.0 / (double)(1u << (K / 2)));
-    for (unsigned i = tid; i < N; i += NT) {
+    for (unsigned i = vt; i < N; i += NT) {
         const unsigned y = (i & fmask) >> f0;
         const unsigned yr = walsh ? y : (__brev(y) >> (32 - K));
         if (yr < y) continue;  // the pair (y, yr) belongs to the thread that holds the smaller one
@@ -254,9 +287,10 @@ __device__ void op_fourier(V *psi, int n, const BOp &op, const V *data, int tid,
 // the field); it is read once, all K stages run on it in shared memory, and the write-back
 // undoes the digit reversal and applies the scaling and the output twiddle.  One L2 read and
 // write per amplitude instead of one per stage.
-template <typename V>
-__device__ void op_fourier_tiled(V *g, int n, const BOp &op, const V *data, int tid, bool walsh, V *sm, int L) {
-    constexpr int NT = Threads<V>::n;
+template <typename V, int CS>
+__device__ void op_fourier_tiled(V *g, int n, const BOp &op, const V *data, int tid, unsigned rank, bool walsh, V *sm,
+                                 int L) {
+    constexpr int NT = Threads<V>::n;  // the CTA's threads: a tile belongs to one CTA of the team
     using Rr = decltype(V{}.x);
     const int K = op.k, f0 = op.c0;
     const unsigned TN = 1u << (K + L), lmask = (1u << L) - 1u;
@@ -276,7 +310,7 @@ __device__ void op_fourier_tiled(V *g, int n, const BOp &op, const V *data, int 
         return (j & lmask) | (olo << L) | ((j >> L) << f0) | (ohi << (f0 + K));
     };
     const Rr scale = (K & 1) ? (Rr)(0.70710678118654752440 / (double)(1u << (K / 2))) : (Rr)(1.0 / (double)(1u << (K / 2)));
-    for (unsigned o = 0; o < ntile; o++) {
+    for (unsigned o = rank; o < ntile; o += CS) {
         for (unsigned j = tid; j < TN; j += NT) {
             const unsigned gi = gidx(o, j);
             V x = g[gi];
@@ -316,37 +350,37 @@ __device__ void op_fourier_tiled(V *g, int n, const BOp &op, const V *data, int 
     }
 }
 
-template <typename R>
-__device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typename C2<R>::T *data, int tid,
-                       typename C2<R>::T *sm, int smem_log) {
+template <typename R, int CS>
+__device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typename C2<R>::T *data, unsigned vt,
+                       int tid, unsigned rank, typename C2<R>::T *sm, int smem_log) {
     using V = typename C2<R>::T;
-    constexpr int kThreads = Threads<V>::n;
+    constexpr int kThreads = CS * Threads<V>::n;  // the team's threads
     const V *d = data + op.data;
     switch (op.kind) {
         case B_DENSE:
             if (op.c0)  // real U (flag set by the encoder)
                 switch (op.k) {
-                    case 1: op_dense<V, 1, true>(psi, n, op, d, tid); break;
-                    case 2: op_dense<V, 2, true>(psi, n, op, d, tid); break;
-                    case 3: op_dense<V, 3, true>(psi, n, op, d, tid); break;
-                    case 4: op_dense<V, 4, true>(psi, n, op, d, tid); break;
-                    case 5: op_dense<V, 5, true>(psi, n, op, d, tid); break;
+                    case 1: op_dense<V, 1, true, CS>(psi, n, op, d, vt); break;
+                    case 2: op_dense<V, 2, true, CS>(psi, n, op, d, vt); break;
+                    case 3: op_dense<V, 3, true, CS>(psi, n, op, d, vt); break;
+                    case 4: op_dense<V, 4, true, CS>(psi, n, op, d, vt); break;
+                    case 5: op_dense<V, 5, true, CS>(psi, n, op, d, vt); break;
                     default: break;
                 }
             else
                 switch (op.k) {
-                    case 1: op_dense<V, 1, false>(psi, n, op, d, tid); break;
-                    case 2: op_dense<V, 2, false>(psi, n, op, d, tid); break;
-                    case 3: op_dense<V, 3, false>(psi, n, op, d, tid); break;
-                    case 4: op_dense<V, 4, false>(psi, n, op, d, tid); break;
-                    case 5: op_dense<V, 5, false>(psi, n, op, d, tid); break;
+                    case 1: op_dense<V, 1, false, CS>(psi, n, op, d, vt); break;
+                    case 2: op_dense<V, 2, false, CS>(psi, n, op, d, vt); break;
+                    case 3: op_dense<V, 3, false, CS>(psi, n, op, d, vt); break;
+                    case 4: op_dense<V, 4, false, CS>(psi, n, op, d, vt); break;
+                    case 5: op_dense<V, 5, false, CS>(psi, n, op, d, vt); break;
                     default: break;
                 }
             break;
         case B_PHASE: {
             const unsigned cnt = 1u << (n - __popc(op.fixmask));
             const V ph = d[0];
-            for (unsigned g = tid; g < cnt; g += kThreads) {
+            for (unsigned g = vt; g < cnt; g += kThreads) {
                 const unsigned i = expand(g, op.fixmask) | op.cmask;
                 psi[i] = cmulb(psi[i], ph);
             }
@@ -354,7 +388,7 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
         }
         case B_DIAG: {
             const unsigned cnt = 1u << (n - __popc(op.cmask));  // every index with the controls set
-            for (unsigned g = tid; g < cnt; g += kThreads) {
+            for (unsigned g = vt; g < cnt; g += kThreads) {
                 const unsigned i = expand(g, op.cmask) | op.cmask;  // enumerate all but controls
                 unsigned p = 0;
                 for (int b = 0; b < op.k; b++) p |= ((i >> op.t[b]) & 1u) << b;
@@ -365,7 +399,7 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
         case B_SWAP: {
             const unsigned cnt = 1u << (n - __popc(op.fixmask));
             const unsigned ma = 1u << op.t[0], mb = 1u << op.t[1];
-            for (unsigned g = tid; g < cnt; g += kThreads) {
+            for (unsigned g = vt; g < cnt; g += kThreads) {
                 const unsigned i = expand(g, op.fixmask) | op.cmask;
                 const V x = psi[i | ma], y = psi[i | mb];
                 psi[i | ma] = y;
@@ -377,7 +411,7 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
             const unsigned cnt = 1u << (n - 1);
             const int tq = op.t[0];
             const unsigned tb = 1u << tq, vmask = (1u << op.nreg) - 1u;
-            for (unsigned g = tid; g < cnt; g += kThreads) {
+            for (unsigned g = vt; g < cnt; g += kThreads) {
                 const unsigned i0 = ((g >> tq) << (tq + 1)) | (g & (tb - 1u));
                 const V cs = d[(i0 >> op.c0) & vmask];
                 const V x0 = psi[i0], x1 = psi[i0 | tb];
@@ -399,7 +433,7 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
             const unsigned tb = 1u << tq, vmask = (1u << op.nreg) - 1u;
             using Rr = decltype(V{}.x);
             const Rr Cs = d[0].x;
-            for (unsigned g = tid; g < cnt; g += kThreads) {
+            for (unsigned g = vt; g < cnt; g += kThreads) {
                 const unsigned i0 = ((g >> tq) << (tq + 1)) | (g & (tb - 1u));
                 const unsigned raw = (i0 >> op.c0) & vmask;
                 const unsigned k = rot ? ((raw >> rot) | ((raw & ((1u << rot) - 1u)) << (op.nreg - rot))) : raw;
@@ -427,8 +461,8 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
         case B_WALSH: {
             const bool walsh = op.kind == B_WALSH;
             const int L = min((int)op.c0, smem_log - (int)op.k);  // lanes below the field
-            if (psi != sm && L >= 0) op_fourier_tiled<V>(psi, n, op, data, tid, walsh, sm, L);
-            else op_fourier<V>(psi, n, op, data, tid, walsh);
+            if (psi != sm && L >= 0) op_fourier_tiled<V, CS>(psi, n, op, data, tid, rank, walsh, sm, L);
+            else op_fourier<V, CS>(psi, n, op, data, vt, walsh);
             break;
         }
         case B_QPE: {  // data qubits 0..k-1, clock register k..k+nreg-1, split at c0 bits
@@ -436,7 +470,7 @@ __device__ void run_op(typename C2<R>::T *psi, int n, const BOp &op, const typen
             const unsigned N = 1u << n, dmask = (1u << op.k) - 1u, cm = (1u << op.nreg) - 1u;
             const unsigned hm = (1u << op.c0) - 1u;
             constexpr int U4 = 2;  // independent amplitudes per iteration (loads in flight together)
-            for (unsigned i0 = tid; i0 < N; i0 += U4 * kThreads) {
+            for (unsigned i0 = vt; i0 < N; i0 += U4 * kThreads) {
                 V x[U4], ph[U4];
 #pragma unroll
                 for (int e = 0; e < U4; e++) {
@@ -487,12 +521,18 @@ __device__ __forceinline__ void block_sum3(double &a, double &b, double &c, doub
     __syncthreads();
 }
 
-template <typename R>
+// CS = 1: each CTA runs whole circuits by itself.  CS > 1 (launched as clusters of CS CTAs):
+// the cluster is one team that runs each of its circuits together, the state in global memory,
+// every operation's work split over the team's threads (a Fourier pass: its tiles over the
+// team's CTAs) and a cluster barrier between steps; readout partial sums are added in rank
+// order, so results do not depend on the rest of the batch either.
+template <typename R, int CS>
 __global__ void __launch_bounds__(Threads<typename C2<R>::T>::n) batched_kernel(const BCirc *circs, const int *order,
                                                                               int count, unsigned *counter,
                                                                               int smem_amps, int stage_bytes) {
     using V = typename C2<R>::T;
-    constexpr int kThreads = Threads<V>::n;
+    constexpr int kThreads = Threads<V>::n;  // per CTA
+    constexpr int kTeam = CS * kThreads;
     extern __shared__ __align__(16) unsigned char smraw[];
     V *sm = reinterpret_cast<V *>(smraw);
     // after the state area: the running circuit's data (matrices, tables) and op list when they
@@ -501,31 +541,43 @@ __global__ void __launch_bounds__(Threads<typename C2<R>::T>::n) batched_kernel(
     unsigned char *stage = smraw + (((size_t)smem_amps * sizeof(V) + 15) & ~(size_t)15);
     __shared__ int cur;
     __shared__ double red[3 * (Threads<V>::n >> 5)];
+    __shared__ double part[3 * CS];  // team: each CTA's readout sums, gathered in rank 0
     const int tid = threadIdx.x;
+    const unsigned rank = CS == 1 ? 0u : cluster_rank();
+    const unsigned vt = rank * (unsigned)kThreads + (unsigned)tid;
+    const int nteams = (int)gridDim.x / CS;
     const int smem_log = 31 - __clz(smem_amps);
+    team_sync<CS>();  // a cluster's CTAs have all started before one writes another's shared memory
     for (;;) {
-        if (tid == 0) cur = (int)atomicAdd(counter, 1u);
-        __syncthreads();
+        if (rank == 0 && tid == 0) {
+            const int v = (int)atomicAdd(counter, 1u);
+            if (CS == 1) cur = v;
+            else
+                for (unsigned r = 0; r < (unsigned)CS; r++) st_cluster(&cur, r, (unsigned)v);
+        }
+        team_sync<CS>();
         const int ci = cur;
-        __syncthreads();
+        team_sync<CS>();
         if (ci >= count) {
-            // Every CTA ends with one increment that returns count or more; the one that
-            // returns count + gridDim.x - 1 is the launch's last, so it puts the counter back to
+            // Every team ends with one increment that returns count or more; the one that
+            // returns count + nteams - 1 is the launch's last, so it puts the counter back to
             // zero for the next launch (no separate reset before each run).
-            if (tid == 0 && ci == count + (int)gridDim.x - 1) *counter = 0u;
+            if (rank == 0 && tid == 0 && ci == count + nteams - 1) *counter = 0u;
             break;
         }
         const BCirc c = circs[order[ci]];
         const unsigned N = 1u << c.n;
         V *g = reinterpret_cast<V *>(c.state);
-        V *psi = (int)N <= smem_amps ? sm : g;  // larger states stay in global memory (L2); the
-                                                 // passes then tile through shared memory
+        // a state that fits stays in shared memory for the whole circuit (one CTA); larger ones
+        // stay in global memory (L2), where the passes tile through shared memory
+        V *psi = (CS == 1 && (int)N <= smem_amps) ? sm : g;
         const V *gdata = reinterpret_cast<const V *>(c.data);
         const V *data = gdata;
         const BOp *ops = c.ops;
         {
             // data (8-byte units: its size is a multiple of 8 and it starts 256-byte aligned)
-            // first, then the ops (32-byte records, 16-byte units)
+            // first, then the ops (32-byte records, 16-byte units); every CTA of a team keeps
+            // its own copy
             const unsigned ob = (unsigned)c.nops * (unsigned)sizeof(BOp);
             const unsigned db = (c.data_bytes + 15u) & ~15u;
             const bool with_data = db + ob <= (unsigned)stage_bytes;
@@ -545,19 +597,19 @@ __global__ void __launch_bounds__(Threads<typename C2<R>::T>::n) batched_kernel(
         }
         if (c.flags & 1) {
             const unsigned Db = 1u << c.nb;
-            for (unsigned i = tid; i < N; i += kThreads) psi[i] = i < Db ? gdata[c.b_off + i] : V{0, 0};
+            for (unsigned i = vt; i < N; i += kTeam) psi[i] = i < Db ? gdata[c.b_off + i] : V{0, 0};
         } else if (psi == sm) {
             for (unsigned i = tid; i < N; i += kThreads) psi[i] = g[i];
         }
-        __syncthreads();
+        team_sync<CS>();
         for (int o = 0; o < c.nops; o++) {
-            run_op<R>(psi, c.n, ops[o], data, tid, sm, smem_log);
-            __syncthreads();
+            run_op<R, CS>(psi, c.n, ops[o], data, vt, tid, rank, sm, smem_log);
+            team_sync<CS>();
         }
         if (c.flags & 2) {
             // FP64 sums in a fixed order: ||psi||^2, P(top qubit = 1), P(slice)
             double s_all = 0.0, s_hi = 0.0;
-            for (unsigned i = tid; i < N; i += kThreads) {
+            for (unsigned i = vt; i < N; i += kTeam) {
                 const V z = psi[i];
                 const double q = (double)z.x * (double)z.x + (double)z.y * (double)z.y;
                 s_all += q;
@@ -565,22 +617,42 @@ __global__ void __launch_bounds__(Threads<typename C2<R>::T>::n) batched_kernel(
             }
             const unsigned Db = 1u << c.nb;
             double s_sl = 0.0;
-            for (unsigned i = tid; i < Db; i += kThreads) {
+            for (unsigned i = vt; i < Db; i += kTeam) {
                 const V z = psi[N / 2 + i];
                 s_sl += (double)z.x * (double)z.x + (double)z.y * (double)z.y;
                 c.result[4 + 2 * i] = (double)z.x;
                 c.result[4 + 2 * i + 1] = (double)z.y;
             }
             block_sum3<kThreads>(s_all, s_hi, s_sl, red);
-            if (tid == 0) {
-                c.result[0] = s_all;
-                c.result[1] = s_hi;
-                c.result[2] = s_sl;
+            if (CS == 1) {
+                if (tid == 0) {
+                    c.result[0] = s_all;
+                    c.result[1] = s_hi;
+                    c.result[2] = s_sl;
+                }
+            } else {
+                if (tid == 0) {
+                    st_cluster(&part[3 * rank], 0u, s_all);
+                    st_cluster(&part[3 * rank + 1], 0u, s_hi);
+                    st_cluster(&part[3 * rank + 2], 0u, s_sl);
+                }
+                team_sync<CS>();
+                if (rank == 0 && tid == 0) {
+                    double a = 0.0, b = 0.0, d = 0.0;
+                    for (int r = 0; r < CS; r++) {
+                        a += part[3 * r];
+                        b += part[3 * r + 1];
+                        d += part[3 * r + 2];
+                    }
+                    c.result[0] = a;
+                    c.result[1] = b;
+                    c.result[2] = d;
+                }
             }
         }
         if (psi == sm)
             for (unsigned i = tid; i < N; i += kThreads) g[i] = psi[i];
-        __syncthreads();
+        team_sync<CS>();
     }
 }
 
@@ -590,6 +662,7 @@ __global__ void __launch_bounds__(Threads<typename C2<R>::T>::n) batched_kernel(
 // ------------------------------------------------------------------------------- host side
 struct qsim_batch {
     int count = 0, dtype = 0, smem_amps = 0, stage_bytes = 0, grid = 1;
+    int nbig = 0, grid_big = 0;  // circuits run by cluster teams (the first nbig of the order)
     size_t smem_bytes = 0;
     bool hhl = false;
     void *dev = nullptr;  // one allocation: circs | order | counter | ops | data | results
@@ -777,6 +850,9 @@ bool encode(const Op &op, int dtype, std::vector<unsigned char> &data, BOp &b) {
     return false;
 }
 
+// log2 of the amplitudes a CTA keeps in shared memory
+int batch_smem_log(int dtype) { return dtype == QSIM_C128 ? 13 : 14; }
+
 double circuit_cost(const qsim_circuit *c) {
     double s = 0;
     for (const Op &op : c->ops) s += (op.kind == OP_DENSE ? (double)(1 << op.targets.size()) : 1.0);
@@ -794,6 +870,7 @@ struct BatchImage {
     size_t results = 0;
     std::vector<qsim_batch::Meta> meta;
     int count = 0, dtype = 0, max_n = 0;
+    int nbig = 0;  // circuits whose state exceeds one CTA's shared memory (first in the order)
     size_t stage_bytes = 0;  // shared memory for the largest circuit's data and op list (capped)
     bool hhl = false;
 };
@@ -861,7 +938,15 @@ BatchImage batch_image(const std::vector<const qsim_circuit *> &cs, const std::v
     std::iota(order.begin(), order.end(), 0);
     std::vector<double> cost(count);
     for (int i = 0; i < count; i++) cost[i] = circuit_cost(cs[i]);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    // states larger than one CTA's shared memory go to the cluster teams (a launch of their
+    // own): they come first; each part in order of decreasing cost
+    const int cap_log = batch_smem_log(dtype);
+    auto big = [&](int i) { return cs[i]->n > cap_log; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (big(a) != big(b)) return big(a);
+        return cost[a] > cost[b];
+    });
+    for (int i = 0; i < count; i++) im.nbig += big(i) ? 1 : 0;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     im.o_circs = 0;
     im.o_order = al(im.o_circs + sizeof(batch::BCirc) * count);
@@ -927,8 +1012,9 @@ qsim_batch *batch_from_image(BatchImage &im, void *dev, double *pinned_results, 
     B->d_results = reinterpret_cast<double *>(base + im.o_res);
     B->results_doubles = im.results;
     if (im.results && external) B->h_results = pinned_results;
-    const int cap_amps = im.dtype == QSIM_C128 ? (1 << 13) : (1 << 14);
+    const int cap_amps = 1 << batch_smem_log(im.dtype);
     B->smem_amps = std::min(cap_amps, 1 << im.max_n);
+    B->nbig = im.nbig;
     B->stage_bytes = (int)im.stage_bytes;
     if (im.dtype == QSIM_C128) configure_batch<double>(B.get());
     else configure_batch<float>(B.get());
@@ -983,30 +1069,82 @@ namespace {
 
 // Kernel attributes and the grid are fixed when the batch is created, so that a run is only a
 // launch (capturable into a CUDA graph).
+constexpr int kTeamCTAs = 4;  // CTAs of a cluster team (a 16-qubit complex64 state is 4 tiles of 2^14)
+
 template <typename R>
 void configure_batch(qsim_batch *B) {
     const size_t smem = (((size_t)B->smem_amps * vbytes(B->dtype) + 15) & ~(size_t)15) + (size_t)B->stage_bytes;
-    auto kern = batch::batched_kernel<R>;
+    constexpr int kThreads = batch::Threads<typename batch::C2<R>::T>::n;
+    auto kern = batch::batched_kernel<R, 1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel attribute: ") + cudaGetErrorString(e));
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, batch::Threads<typename batch::C2<R>::T>::n, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    B->grid = std::max(1, std::min(B->count, sms * per_sm));
+    B->grid = std::max(1, std::min(B->count - B->nbig, sms * per_sm));
     B->smem_bytes = smem;
+    B->grid_big = 0;
+    if (B->nbig > 0) {
+        auto kc = batch::batched_kernel<R, kTeamCTAs>;
+        e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel attribute: ") + cudaGetErrorString(e));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = kTeamCTAs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(kTeamCTAs * std::max(1, sms / kTeamCTAs)));
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        e = cudaOccupancyMaxActiveClusters(&clusters, kc, &cfg);
+        if (e != cudaSuccess || clusters < 1) {
+            cudaGetLastError();
+            throw Error(QSIM_ECUDA, "batched kernel: no cluster of 4 CTAs fits on the device");
+        }
+        B->grid_big = kTeamCTAs * std::min(B->nbig, clusters);
+    }
 }
 
-// The work counter is zero when the batch is uploaded and the kernel leaves it at zero.
+// The work counters are zero when the batch is uploaded and the kernels leave them at zero:
+// the cluster teams take the first nbig circuits of the order (counter 0), single CTAs the rest
+// (counter 32, its own cache line).
 template <typename R>
 void launch_batch(qsim_batch *B, cudaStream_t st) {
-    batch::batched_kernel<R><<<B->grid, batch::Threads<typename batch::C2<R>::T>::n, B->smem_bytes, st>>>(B->d_circs, B->d_order, B->count,
-                                                                              B->d_counter, B->smem_amps, B->stage_bytes);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel: ") + cudaGetErrorString(e));
-    note_launches(1, QSIM_KERNEL_BATCHED);
+    constexpr int kThreads = batch::Threads<typename batch::C2<R>::T>::n;
+    if (B->nbig > 0) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = kTeamCTAs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)B->grid_big);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = B->smem_bytes;
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const batch::BCirc *circs = B->d_circs;
+        const int *order = B->d_order;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, batch::batched_kernel<R, kTeamCTAs>, circs, order, B->nbig, B->d_counter,
+                                           B->smem_amps, B->stage_bytes);
+        if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel (teams): ") + cudaGetErrorString(e));
+        note_launches(1, QSIM_KERNEL_BATCHED);
+    }
+    if (B->count > B->nbig) {
+        batch::batched_kernel<R, 1><<<B->grid, kThreads, B->smem_bytes, st>>>(B->d_circs, B->d_order + B->nbig, B->count - B->nbig,
+                                                                             B->d_counter + 32, B->smem_amps, B->stage_bytes);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel: ") + cudaGetErrorString(e));
+        note_launches(1, QSIM_KERNEL_BATCHED);
+    }
 }
 
 void run_batch(qsim_batch *B, void *stream) {

@@ -152,7 +152,6 @@ struct Cfg {
     static constexpr int D = 1 << K;
     static constexpr int N = 2 * D;       // output reals per group
     static constexpr int KK = 2 * D;      // reduction length
-    static constexpr int NCH = KK / kCH;  // chunks per tile
     static constexpr int BBYTES = N * KK * 4;
     static constexpr unsigned IDESC = (1u << 4)          // D format F32
                                       | (2u << 7)        // A format TF32
@@ -186,10 +185,16 @@ constexpr int kPrefetch = 6;  // chunks of loads in flight per producer thread
 // within that).
 template <int K>
 struct GmCfg {
-    static constexpr int D = 1 << K, N = 2 * D, KK = 2 * D, NCH = KK / kCH;
+    static constexpr int D = 1 << K, N = 2 * D, KK = 2 * D;
+    static constexpr int CA = D < 16 ? D : 16;         // amplitudes per chunk and group
+    static constexpr int CK = 2 * CA;                  // K-columns per chunk
+    static constexpr int NCH = KK / CK;                // chunks per tile
+    static constexpr int APT = CA * kM / kProducers;   // amplitudes per chunk and producer thread
+    static constexpr int PF = kPrefetch * 4 / APT;     // chunks of loads in flight per thread
     static constexpr int BBYTES = N * KK * 4;
-    static constexpr int NB = (512 - 2 * N) / 64;  // tensor-memory chunk slots
-    static constexpr int NBAR = 2 * NB + 5;        // full/empty per slot, accfull/accempty x2, drain
+    static constexpr int SLOT = 2 * CK;                // tensor-memory columns per chunk (hi, lo)
+    static constexpr int NB = (512 - 2 * N) / SLOT;    // tensor-memory chunk slots
+    static constexpr int NBAR = 2 * NB + 5;            // full/empty per slot, accfull/accempty x2, drain
     static constexpr int SMEM = 2 * BBYTES + 8 * NBAR + 16 + 8 * D;
     static constexpr unsigned IDESC = Cfg<K>::IDESC;
 };
@@ -204,16 +209,21 @@ __device__ __forceinline__ void mma_tf32_ta(unsigned d_tmem, unsigned a_tmem, ui
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_st8(unsigned taddr, const unsigned (&v)[8]) {
+__device__ __forceinline__ void tmem_st(unsigned taddr, const unsigned (&v)[8]) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr), "r"(v[0]),
                  "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st(unsigned taddr, const unsigned (&v)[4]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3])
                  : "memory");
 }
 
 template <int K>
 __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a) {
     using C = GmCfg<K>;
-    constexpr int D = C::D, N = C::N, KK = C::KK, NCH = C::NCH, NB = C::NB;
+    constexpr int D = C::D, N = C::N, KK = C::KK, NCH = C::NCH, NB = C::NB, APT = C::APT, PF = C::PF;
     extern __shared__ __align__(1024) unsigned char sm[];
     float *Bs = reinterpret_cast<float *>(sm);  // [2][N*KK]
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * C::BBYTES);
@@ -271,28 +281,28 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a
 
     if (warp < kEpiWarp0) {
         // ------------------------------------------------------------------ producers
-        // thread: group row m (its TMEM lane), amplitudes 4h .. 4h+3 of every chunk (K-columns
-        // 8h .. 8h+7 of the slot's hi and lo halves)
+        // thread: group row m (its TMEM lane), amplitudes APT h .. APT h + APT-1 of every chunk
+        // (K-columns 2 APT h .. of the slot's hi and lo halves)
         const int q = warp & 3, h = warp >> 2, m = 32 * q + lane;
-        float2 r[kPrefetch][kAmpsPT];
+        float2 r[PF][APT];
         long long gb_tile = -1;
         unsigned long long gb_row = 0;
-        auto load = [&](long long qq, float2(&rr)[kAmpsPT]) {
+        auto load = [&](long long qq, float2(&rr)[APT]) {
             if (qq < total) {
                 if (qq / NCH != gb_tile) {
                     gb_tile = qq / NCH;
                     gb_row = group_base(gb_tile, m);
                 }
-                const int c0 = (int)(qq % NCH) * 16 + kAmpsPT * h;
+                const int c0 = (int)(qq % NCH) * C::CA + APT * h;
 #pragma unroll
-                for (int e = 0; e < kAmpsPT; e++) rr[e] = __ldcs(psi + gb_row + toff[c0 + e]);
+                for (int e = 0; e < APT; e++) rr[e] = __ldcs(psi + gb_row + toff[c0 + e]);
             }
         };
 #pragma unroll
-        for (int p = 0; p < kPrefetch; p++) load(p, r[p]);
-        for (long long q0 = 0; q0 < total && !failed; q0 += kPrefetch) {
+        for (int p = 0; p < PF; p++) load(p, r[p]);
+        for (long long q0 = 0; q0 < total && !failed; q0 += PF) {
 #pragma unroll
-            for (int p = 0; p < kPrefetch; p++) {
+            for (int p = 0; p < PF; p++) {
                 const long long qq = q0 + p;
                 if (qq >= total) break;
                 const int b = (int)(qq % NB);
@@ -305,21 +315,21 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a
                     }
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(2 * N + b * 64 + 8 * h);
-                unsigned v[8];
+                const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(2 * N + b * C::SLOT + 2 * APT * h);
+                unsigned v[2 * APT];
 #pragma unroll
-                for (int e = 0; e < kAmpsPT; e++) {
+                for (int e = 0; e < APT; e++) {
                     v[2 * e] = to_tf32(r[p][e].x);
                     v[2 * e + 1] = to_tf32(r[p][e].y);
                 }
-                tmem_st8(ta, v);
+                tmem_st(ta, v);
 #pragma unroll
-                for (int e = 0; e < kAmpsPT; e++) {
+                for (int e = 0; e < APT; e++) {
                     v[2 * e] = to_tf32(r[p][e].x - __uint_as_float(to_tf32(r[p][e].x)));
                     v[2 * e + 1] = to_tf32(r[p][e].y - __uint_as_float(to_tf32(r[p][e].y)));
                 }
-                tmem_st8(ta + 32u, v);
-                load(qq + kPrefetch, r[p]);
+                tmem_st(ta + (unsigned)C::CK, v);
+                load(qq + PF, r[p]);
                 asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                 __syncwarp();
@@ -377,10 +387,10 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const unsigned acc = tmem + (unsigned)(ab * N);
-            const unsigned x_hi = tmem + (unsigned)(2 * N + b * 64), x_lo = x_hi + 32u;
+            const unsigned x_hi = tmem + (unsigned)(2 * N + b * C::SLOT), x_lo = x_hi + (unsigned)C::CK;
 #pragma unroll
-            for (int kk = 0; kk < kCH / 8; kk++) {
-                const unsigned boff = (j * (kCH / 4) + kk * 2) * 128;  // 2 core matrices along K
+            for (int kk = 0; kk < C::CK / 8; kk++) {
+                const unsigned boff = (j * (C::CK / 4) + kk * 2) * 128;  // 2 core matrices along K
                 const uint64_t dBh = make_desc(b_hi + boff, 128, KK * 32);
                 const uint64_t dBl = make_desc(b_lo + boff, 128, KK * 32);
                 mma_tf32_ta(acc, x_hi + 8u * kk, dBh, C::IDESC, (j == 0 && kk == 0) ? 0u : 1u);
@@ -899,7 +909,7 @@ size_t dense_tc_blob_bytes(int k) {
     return 2 * (2 * D) * (2 * D) * 4;
 }
 
-bool dense_tc_supported(int k) { return k >= 4 && k <= 6; }
+bool dense_tc_supported(int k) { return k >= 3 && k <= 6; }
 
 bool dense_tc_real7_applies(const Op &op) {
     return op.real_u && op.targets.size() == 7 && op.targets[0] == 0 && op.targets[1] == 1;
@@ -1043,6 +1053,7 @@ bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const 
     // targets ascending (canonical order); qubits 0 and 1 among them: transposed form
     const bool tr = K == 6 && targets[0] == 0 && targets[1] == 1;
     switch (K) {
+        case 3: launch_tc_gm<3>(a, sms, st); break;
         case 4: launch_tc_gm<4>(a, sms, st); break;
         case 5: launch_tc_gm<5>(a, sms, st); break;
         case 6: tr ? launch_tc_tr(a, sms, st) : launch_tc_gm<6>(a, sms, st); break;

@@ -222,11 +222,11 @@ extern "C" int qsim_autotune(void *state, int n_qubits, int dtype, void *stream,
             T[QSIM_TUNE_DFT_PREFETCH].store(bc.pf);
             rep.dft_ms = best / 3.0;
         }
-        // 2. dense gates of 4..6 targets (complex64): tensor cores or SIMT, per width (bit 7, the
+        // 2. dense gates of 3..6 targets (complex64): tensor cores or SIMT, per width (bit 7, the
         //    real 7-target tensor-core kernel, keeps its value)
         if (dtype == QSIM_C64) {
             int mask = T[QSIM_TUNE_DENSE_TC].load() & (1 << 7);
-            for (int k = 4; k <= 6; k++) {
+            for (int k = 3; k <= 6; k++) {
                 CircuitHolder ch(n);
                 for (int g = 0; g < 3; g++) {
                     std::vector<int> perm(n);
@@ -244,7 +244,7 @@ extern "C" int qsim_autotune(void *state, int n_qubits, int dtype, void *stream,
                     t[use] = time_apply(state, n, dtype, ch.c, st, 2);
                 }
                 if (t[1] < t[0]) mask |= 1 << k;
-                rep.dense_ms[k - 4] = std::min(t[0], t[1]) / 3.0;
+                rep.dense_ms[k - 3] = std::min(t[0], t[1]) / 3.0;
             }
             T[QSIM_TUNE_DENSE_TC].store(mask);
         }

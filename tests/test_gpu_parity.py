@@ -82,10 +82,23 @@ def test_dense_gate_parity(qs, dtype, k):
     check(st, ref, dtype)
 
 
-@pytest.mark.parametrize("k", [4, 5, 6])
-def test_tensor_core_dense_parity_complex64(qs, k):
-    """complex64 gates with 4..6 targets and at least 128 groups run on the tcgen05 3xTF32
+@pytest.fixture
+def tc_on(qs):
+    """Select the tensor-core kernel for dense gates of k targets (every size class); the
+    kernel-choice table is put back afterwards."""
+    def on(k):
+        mask = qs.qsim_tune_get(qs.QSIM_C64, qs.QSIM_TUNE_DENSE_TC, 17)
+        qs.qsim_tune_set(qs.QSIM_C64, qs.QSIM_TUNE_DENSE_TC, mask | (1 << k))
+    yield on
+    qs.qsim_tune_reset()
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_tensor_core_dense_parity_complex64(qs, k, tc_on):
+    """complex64 gates with 3..6 targets and at least 128 groups run on the tcgen05 3xTF32
     kernel: low, high and random targets, with and without controls, vs the FP64 oracle."""
+    tc_on(k)
+    before = qs.qsim_launch_counts()["dense_tc"]
     rng = np.random.default_rng(500 + k)
     n = 17
     psi = host_input(synth.gaussian_state_np(500 + k, n), torch.complex64)
@@ -104,6 +117,7 @@ def test_tensor_core_dense_parity_complex64(qs, k):
     qs.qsim_apply(st, c)
     torch.cuda.synchronize()
     assert qs.qsim_device_status() == 0
+    assert qs.qsim_launch_counts()["dense_tc"] - before == len(cases)
     check(st, ref, torch.complex64)
 
 
@@ -162,11 +176,12 @@ def test_real_matrix_gates(qs, dtype):
     check(st, ref, dtype)
 
 
-@pytest.mark.parametrize("k", [4, 5, 6])
-def test_tensor_core_low_target_layouts(qs, k):
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_tensor_core_low_target_layouts(qs, k, tc_on):
     """Gates whose targets include qubits 0 and 1 (vector loads across a group's amplitudes,
     shuffle-transposed stores), in any given order, with scattered upper targets and controls;
     and gates with qubit 0 but not qubit 1 (the group-major layout)."""
+    tc_on(k)
     rng = np.random.default_rng(900 + k)
     n = 19
     psi = host_input(synth.gaussian_state_np(900 + k, n), torch.complex64)
