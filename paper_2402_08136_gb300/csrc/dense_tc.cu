@@ -179,8 +179,8 @@ constexpr int kPrefetch = 6;  // chunks of loads in flight per producer thread
 // lo).  Shared memory then serves only B, which halves the shared-memory operand traffic of
 // every MMA (a 128 x 2D x 8 MMA read 8 KB of shared memory per issue, more than the SM's shared
 // memory delivers in the MMA's own time for 2D = 128), and the producers no longer write
-// shared memory at all.  Tensor memory: two accumulators of 2D columns and (512 - 4D) / 64
-// chunk slots (4 for 6 targets).  21 warps (the register file is split over the SM's four sub-partitions, so the sub-partition
+// shared memory at all.  Tensor memory: NACC accumulators of 2D columns (two for 6 targets, four
+// for 4 and 5, eight for 3) and chunk slots in the rest of the 512 columns.  21 warps (the register file is split over the SM's four sub-partitions, so the sub-partition
 // holding 6 warps caps a thread at 80 registers: the producers keep 6 chunks of loads in flight
 // within that).
 template <int K>
@@ -193,8 +193,11 @@ struct GmCfg {
     static constexpr int PF = kPrefetch * 4 / APT;     // chunks of loads in flight per thread
     static constexpr int BBYTES = N * KK * 4;
     static constexpr int SLOT = 2 * CK;                // tensor-memory columns per chunk (hi, lo)
-    static constexpr int NB = (512 - 2 * N) / SLOT;    // tensor-memory chunk slots
-    static constexpr int NBAR = 2 * NB + 5;            // full/empty per slot, accfull/accempty x2, drain
+    // accumulators in flight: narrow gates finish a tile every few hundred cycles, so more of
+    // them keep the MMA -> epilogue hand-off off the critical path
+    static constexpr int NACC = K == 3 ? 8 : (K == 6 ? 2 : 4);
+    static constexpr int NB = (512 - NACC * N) / SLOT;  // tensor-memory chunk slots
+    static constexpr int NBAR = 2 * NB + 2 * NACC + 1;   // full/empty per slot, accfull/accempty, drain
     static constexpr int SMEM = 2 * BBYTES + 8 * NBAR + 16 + 8 * D;
     static constexpr unsigned IDESC = Cfg<K>::IDESC;
 };
@@ -229,9 +232,9 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * C::BBYTES);
     uint64_t *full = bars;                       // [NB] producer warps -> MMA (count 16)
     uint64_t *empty = bars + NB;                 // [NB] MMA completion -> producers (commit)
-    uint64_t *accfull = bars + 2 * NB;           // [2] MMA completion -> epilogue (commit)
-    uint64_t *accempty = accfull + 2;            // [2] epilogue warps -> MMA (count 4)
-    uint64_t *drain = accfull + 4;               // MMA completion before tensor memory is freed
+    uint64_t *accfull = bars + 2 * NB;           // [NACC] MMA completion -> epilogue (commit)
+    uint64_t *accempty = accfull + C::NACC;      // [NACC] epilogue warps -> MMA (count 4)
+    uint64_t *drain = accempty + C::NACC;        // MMA completion before tensor memory is freed
     unsigned *tslot = reinterpret_cast<unsigned *>(bars + C::NBAR);
     long long *toff = reinterpret_cast<long long *>(tslot + 4);  // D entries
 
@@ -251,7 +254,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a
                 mbar_init(&full[i], kProducers / 32);
                 mbar_init(&empty[i], 1);
             }
-            for (int i = 0; i < 2; i++) {
+            for (int i = 0; i < C::NACC; i++) {
                 mbar_init(&accfull[i], 1);
                 mbar_init(&accempty[i], 4);
             }
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a
                     }
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(2 * N + b * C::SLOT + 2 * APT * h);
+                const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(C::NACC * N + b * C::SLOT + 2 * APT * h);
                 unsigned v[2 * APT];
 #pragma unroll
                 for (int e = 0; e < APT; e++) {
@@ -341,8 +344,8 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a
         const int sub = warp - kEpiWarp0;  // TMEM lane subpartition
         const int m = sub * 32 + lane;     // group row == TMEM lane
         for (long long t = 0; t < ntl && !failed; t++) {
-            const int ab = (int)(t & 1);
-            bool ok = mbar_wait(&accfull[ab], (unsigned)((t >> 1) & 1));
+            const int ab = (int)(t % C::NACC);
+            bool ok = mbar_wait(&accfull[ab], (unsigned)((t / C::NACC) & 1));
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
                 failed = true;
@@ -376,8 +379,8 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a
             const int b = (int)(qq % NB);
             const int j = (int)(qq % NCH);
             const long long t = qq / NCH;
-            const int ab = (int)(t & 1);
-            if (j == 0 && t >= 2 && !mbar_wait(&accempty[ab], (unsigned)(((t >> 1) - 1) & 1))) {
+            const int ab = (int)(t % C::NACC);
+            if (j == 0 && t >= C::NACC && !mbar_wait(&accempty[ab], (unsigned)(((t / C::NACC) - 1) & 1))) {
                 failed = true;
                 break;
             }
@@ -387,7 +390,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const unsigned acc = tmem + (unsigned)(ab * N);
-            const unsigned x_hi = tmem + (unsigned)(2 * N + b * C::SLOT), x_lo = x_hi + (unsigned)C::CK;
+            const unsigned x_hi = tmem + (unsigned)(C::NACC * N + b * C::SLOT), x_lo = x_hi + (unsigned)C::CK;
 #pragma unroll
             for (int kk = 0; kk < C::CK / 8; kk++) {
                 const unsigned boff = (j * (C::CK / 4) + kk * 2) * 128;  // 2 core matrices along K
