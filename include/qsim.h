@@ -143,6 +143,22 @@ int qsim_circuit_get_info(const qsim_circuit *c, qsim_circuit_info *out);
  * FP64 rounding.  Errors: EINVAL, ENOMEM. */
 int qsim_fuse(const qsim_circuit *in, int max_k, qsim_circuit **out);
 
+/* The paper's gate fusion (Sec. II-C, Fig. 4) on gates of at most two qubits: its four
+ * strategies in their priority order, each one pass over the whole circuit: one-qubit gates on
+ * the same qubit first; then a one-qubit gate into the two-qubit gate that follows it on its
+ * qubit, then into the one that precedes it; finally two-qubit gates on the same pair.  A gate
+ * with one control and one target counts as a two-qubit gate; every other gate stays in place
+ * and blocks merges across it on its qubits.  Products are formed on the host in FP64; the
+ * result equals the input up to rounding.  `in` must be unfused.  Errors: EINVAL, ENOMEM. */
+int qsim_fuse_paper(const qsim_circuit *in, qsim_circuit **out);
+
+/* Gate i of a circuit (as built, or as fused): its kind (0 dense gate, 1 uniformly controlled
+ * RY, other values: the structured operators), k targets and n_controls controls (each array,
+ * when not NULL, must hold that many ints) and, for a dense gate when U is not NULL, its
+ * 2^k x 2^k matrix (interleaved doubles, row-major, 2 * 4^k of them).  Errors: EINVAL. */
+int qsim_circuit_get_gate(const qsim_circuit *c, int i, int *kind, int *k, int *targets, int *n_controls,
+                          int *controls, double *U);
+
 /* ======================================================================================= *
  * Application (the hot loop)                                                               *
  * ======================================================================================= */

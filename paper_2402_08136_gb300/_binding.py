@@ -105,6 +105,10 @@ _SIGS = {
     "qsim_circuit_free": ([_VP], None),
     "qsim_circuit_get_info": ([_VP, ctypes.POINTER(_CircuitInfo)], ctypes.c_int),
     "qsim_fuse": ([_VP, ctypes.c_int, ctypes.POINTER(_VP)], ctypes.c_int),
+    "qsim_fuse_paper": ([_VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "qsim_circuit_get_gate": ([_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "qsim_apply": ([_VP, ctypes.c_int, ctypes.c_int, _VP, _VP], ctypes.c_int),
     "hhl_build": ([_DP, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                    ctypes.POINTER(_VP)], ctypes.c_int),
@@ -315,6 +319,34 @@ def qsim_fuse(circuit: Circuit, max_k: int = 0) -> Circuit:
     p = _VP()
     _check(library().qsim_fuse(circuit.ptr, int(max_k), ctypes.byref(p)))
     return Circuit(_ptr=p)
+
+
+def qsim_fuse_paper(circuit: Circuit) -> Circuit:
+    """The paper's priority-ordered fusion of gates on at most two qubits (Sec. II-C, Fig. 4)."""
+    p = _VP()
+    _check(library().qsim_fuse_paper(circuit.ptr, ctypes.byref(p)))
+    return Circuit(_ptr=p)
+
+
+def qsim_circuit_gates(circuit: Circuit) -> list:
+    """The circuit's gates as dicts: kind, targets, controls and, for dense gates, U (numpy)."""
+    import numpy as np
+    out = []
+    for i in range(circuit.info()["n_gates"]):
+        kind, k, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(library().qsim_circuit_get_gate(circuit.ptr, i, ctypes.byref(kind), ctypes.byref(k), None,
+                                               ctypes.byref(nc), None, None))
+        t = (ctypes.c_int * max(1, k.value))()
+        c = (ctypes.c_int * max(1, nc.value))()
+        U = (ctypes.c_double * (2 * 4 ** k.value))() if kind.value == 0 else None
+        _check(library().qsim_circuit_get_gate(circuit.ptr, i, ctypes.byref(kind), ctypes.byref(k), t, ctypes.byref(nc),
+                                               c, U))
+        g = {"kind": kind.value, "targets": list(t)[:k.value], "controls": list(c)[:nc.value]}
+        if U is not None:
+            a = np.frombuffer(U, dtype=np.float64)
+            g["U"] = (a[0::2] + 1j * a[1::2]).reshape(1 << k.value, 1 << k.value).copy()
+        out.append(g)
+    return out
 
 
 def qsim_apply(state, circuit: Circuit, stream=None, n_qubits: int | None = None):

@@ -252,6 +252,109 @@ static qsim_circuit *fuse_impl(const qsim_circuit *in, int max_k) {
     return out.release();
 }
 
+// The paper's gate fusion (Sec. II-C, Fig. 4) on gates of at most two qubits, its four
+// strategies applied in their priority order, each as one pass over the whole circuit:
+//   1. consecutive one-qubit gates on the same qubit are multiplied together;
+//   2. a one-qubit gate is multiplied into the two-qubit gate that follows it on its qubit;
+//   3. a one-qubit gate is multiplied into the two-qubit gate that precedes it on its qubit;
+//   4. consecutive two-qubit gates on the same pair of qubits are multiplied together.
+// "Consecutive on a qubit" means that no gate in between touches that qubit (strategy 4: either
+// qubit), so every merge moves a gate past gates it commutes with.  A gate with one control and
+// one target is a two-qubit gate here (its dense 4 x 4 form once it takes part in a merge);
+// every other gate stays where it is and is never merged across on its qubits.
+namespace {
+struct FGate {
+    Gate g;
+    bool alive = true;
+    int nq = 0;  // 1 or 2: mergeable one- or two-qubit gate; 0: anything else
+    std::vector<int> q;
+};
+
+// the dense two-qubit form (targets {t, c}) of a gate with one control c and one target t
+void densify(FGate &f) {
+    if (f.g.controls.empty()) return;
+    const int t = f.g.targets[0], c = f.g.controls[0];
+    std::vector<cd> U(16, cd(0.0, 0.0));
+    for (int r = 0; r < 4; r++)
+        for (int k = 0; k < 4; k++) {
+            if ((r >> 1) != (k >> 1)) continue;  // bit 1 <-> c (untouched)
+            if ((r >> 1) == 0) U[(size_t)r * 4 + k] = (r & 1) == (k & 1) ? cd(1.0, 0.0) : cd(0.0, 0.0);
+            else U[(size_t)r * 4 + k] = f.g.U[(size_t)(r & 1) * 2 + (k & 1)];
+        }
+    f.g.targets = {t, c};
+    f.g.controls.clear();
+    f.g.U.swap(U);
+}
+}  // namespace
+
+static qsim_circuit *fuse_paper_impl(const qsim_circuit *in) {
+    std::vector<FGate> fs(in->gates.size());
+    for (size_t i = 0; i < fs.size(); i++) {
+        FGate &f = fs[i];
+        f.g = in->gates[i];
+        f.q = f.g.targets;
+        f.q.insert(f.q.end(), f.g.controls.begin(), f.g.controls.end());
+        if (f.g.kind == GATE_U && f.g.targets.size() == 1 && f.g.controls.empty()) f.nq = 1;
+        else if (f.g.kind == GATE_U && f.q.size() == 2 && f.g.controls.size() <= 1) f.nq = 2;
+    }
+    auto touches = [&](size_t j, int q) { return std::find(fs[j].q.begin(), fs[j].q.end(), q) != fs[j].q.end(); };
+    auto next_on = [&](size_t i, int q) -> long {
+        for (size_t j = i + 1; j < fs.size(); j++)
+            if (fs[j].alive && touches(j, q)) return (long)j;
+        return -1;
+    };
+    auto prev_on = [&](size_t i, int q) -> long {
+        for (size_t j = i; j-- > 0;)
+            if (fs[j].alive && touches(j, q)) return (long)j;
+        return -1;
+    };
+    // merge A into B (A's qubits are among B's): A acts before B (a_first: U_B U_A) or after it
+    // (U_A U_B); B keeps its place in the list
+    auto merge = [&](FGate &A, FGate &B, bool a_first) {
+        densify(A);
+        densify(B);
+        const int K = (int)B.g.targets.size(), D = 1 << K;
+        std::vector<cd> E = expand_to(B.g.targets, A.g.targets, A.g.U), out;
+        if (a_first) matmul_into(out, B.g.U, E, D);  // A acts first: U_B U_A
+        else matmul_into(out, E, B.g.U, D);          // A acts after: U_A U_B
+        B.g.U.swap(out);
+        B.q = B.g.targets;
+        A.alive = false;
+    };
+    // 1. one-qubit + one-qubit
+    for (size_t i = 0; i < fs.size(); i++) {
+        if (!fs[i].alive || fs[i].nq != 1) continue;
+        const long j = next_on(i, fs[i].q[0]);
+        if (j >= 0 && fs[j].nq == 1) merge(fs[i], fs[j], true);
+    }
+    // 2. one-qubit into the following two-qubit gate
+    for (size_t i = 0; i < fs.size(); i++) {
+        if (!fs[i].alive || fs[i].nq != 1) continue;
+        const long j = next_on(i, fs[i].q[0]);
+        if (j >= 0 && fs[j].nq == 2) merge(fs[i], fs[j], true);
+    }
+    // 3. one-qubit into the preceding two-qubit gate
+    for (size_t i = 0; i < fs.size(); i++) {
+        if (!fs[i].alive || fs[i].nq != 1) continue;
+        const long j = prev_on(i, fs[i].q[0]);
+        if (j >= 0 && fs[j].nq == 2) merge(fs[i], fs[j], false);
+    }
+    // 4. two-qubit + two-qubit on the same pair
+    for (size_t i = 0; i < fs.size(); i++) {
+        if (!fs[i].alive || fs[i].nq != 2) continue;
+        const long j = next_on(i, fs[i].q[0]);
+        if (j < 0 || fs[j].nq != 2 || j != next_on(i, fs[i].q[1])) continue;
+        if (!touches((size_t)j, fs[i].q[0]) || !touches((size_t)j, fs[i].q[1])) continue;
+        merge(fs[i], fs[j], true);
+    }
+    std::unique_ptr<qsim_circuit> out(new qsim_circuit());
+    out->n = in->n;
+    out->fused = true;
+    for (FGate &f : fs)
+        if (f.alive) out->gates.push_back(std::move(f.g));
+    return out.release();
+}
+
 namespace {
 // exp(i x c) for a double x and an integer c, |c| < 2^27, to a few ulps however large x c is.
 // The product is formed exactly as p + e (e = fma(x, c, -p)), reduced by 2 pi split into three
@@ -467,6 +570,37 @@ int qsim_circuit_get_info(const qsim_circuit *c, qsim_circuit_info *out) {
         qsim_circuit *cc = const_cast<qsim_circuit *>(c);
         build_ops(cc);
         circuit_info(cc, out);
+    });
+}
+
+int qsim_fuse_paper(const qsim_circuit *in, qsim_circuit **out) {
+    return guarded([&] {
+        QSIM_REQUIRE(in != nullptr && out != nullptr, "NULL argument");
+        QSIM_REQUIRE(!in->fused, "fuse the unfused gate list");
+        qsim_circuit *f = fuse_paper_impl(in);
+        build_ops(f);
+        *out = f;
+    });
+}
+
+int qsim_circuit_get_gate(const qsim_circuit *c, int i, int *kind, int *k, int *targets, int *n_controls,
+                          int *controls, double *U) {
+    return guarded([&] {
+        QSIM_REQUIRE(c != nullptr && kind != nullptr && k != nullptr && n_controls != nullptr, "NULL argument");
+        QSIM_REQUIRE(i >= 0 && i < (int)c->gates.size(), "gate index out of range");
+        const Gate &g = c->gates[i];
+        *kind = (int)g.kind;
+        *k = (int)g.targets.size();
+        *n_controls = (int)g.controls.size();
+        if (targets)
+            for (size_t b = 0; b < g.targets.size(); b++) targets[b] = g.targets[b];
+        if (controls)
+            for (size_t b = 0; b < g.controls.size(); b++) controls[b] = g.controls[b];
+        if (U && g.kind == GATE_U)
+            for (size_t e = 0; e < g.U.size(); e++) {
+                U[2 * e] = g.U[e].real();
+                U[2 * e + 1] = g.U[e].imag();
+            }
     });
 }
 
