@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <numeric>
 
@@ -1071,25 +1072,50 @@ namespace {
 // launch (capturable into a CUDA graph).
 constexpr int kTeamCTAs = 4;  // CTAs of a cluster team (a 16-qubit complex64 state is 4 tiles of 2^14)
 
+// Occupancy of the two batched kernels for a dynamic shared-memory size, queried once per
+// (device, type, size): batches are created on the serving pool's hot path.
+struct BatchOcc {
+    int per_sm = 1, clusters = 0;
+};
+
 template <typename R>
-void configure_batch(qsim_batch *B) {
-    const size_t smem = (((size_t)B->smem_amps * vbytes(B->dtype) + 15) & ~(size_t)15) + (size_t)B->stage_bytes;
-    constexpr int kThreads = batch::Threads<typename batch::C2<R>::T>::n;
-    auto kern = batch::batched_kernel<R, 1>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel attribute: ") + cudaGetErrorString(e));
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-    int dev = 0, sms = 0;
+BatchOcc batch_occupancy(size_t smem, bool need_clusters) {
+    static std::mutex mu;
+    static std::map<std::pair<int, size_t>, BatchOcc> cache;
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    B->grid = std::max(1, std::min(B->count - B->nbig, sms * per_sm));
-    B->smem_bytes = smem;
-    B->grid_big = 0;
-    if (B->nbig > 0) {
+    const std::pair<int, size_t> key(dev, smem);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end() && (!need_clusters || it->second.clusters > 0)) return it->second;
+    }
+    constexpr int kThreads = batch::Threads<typename batch::C2<R>::T>::n;
+    BatchOcc o;
+    // the kernels' dynamic shared-memory limit is set once to the device's opt-in maximum, so
+    // that a launch of any batch size is covered whatever size was configured last
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // (less the kernel's own static shared memory)
+    auto dyn_max = [&](const void *k) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) throw Error(QSIM_ECUDA, "batched kernel attributes");
+        const int m = optin - (int)fa.sharedSizeBytes;
+        QSIM_REQUIRE((size_t)m >= smem, "batched kernel: shared memory per CTA exceeds the device limit");
+        return m;
+    };
+    auto kern = batch::batched_kernel<R, 1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         dyn_max(reinterpret_cast<const void *>(kern)));
+    if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel attribute: ") + cudaGetErrorString(e));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, kern, kThreads, smem);
+    if (e != cudaSuccess || o.per_sm < 1) o.per_sm = 1;
+    if (need_clusters) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         auto kc = batch::batched_kernel<R, kTeamCTAs>;
-        e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dyn_max(reinterpret_cast<const void *>(kc)));
         if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("batched kernel attribute: ") + cudaGetErrorString(e));
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute at[1];
@@ -1102,14 +1128,27 @@ void configure_batch(qsim_batch *B) {
         cfg.dynamicSmemBytes = smem;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        int clusters = 0;
-        e = cudaOccupancyMaxActiveClusters(&clusters, kc, &cfg);
-        if (e != cudaSuccess || clusters < 1) {
+        e = cudaOccupancyMaxActiveClusters(&o.clusters, kc, &cfg);
+        if (e != cudaSuccess || o.clusters < 1) {
             cudaGetLastError();
             throw Error(QSIM_ECUDA, "batched kernel: no cluster of 4 CTAs fits on the device");
         }
-        B->grid_big = kTeamCTAs * std::min(B->nbig, clusters);
     }
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = o;
+    return o;
+}
+
+template <typename R>
+void configure_batch(qsim_batch *B) {
+    const size_t smem = (((size_t)B->smem_amps * vbytes(B->dtype) + 15) & ~(size_t)15) + (size_t)B->stage_bytes;
+    const BatchOcc o = batch_occupancy<R>(smem, B->nbig > 0);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    B->grid = std::max(1, std::min(B->count - B->nbig, sms * o.per_sm));
+    B->smem_bytes = smem;
+    B->grid_big = B->nbig > 0 ? kTeamCTAs * std::min(B->nbig, o.clusters) : 0;
 }
 
 // The work counters are zero when the batch is uploaded and the kernels leave them at zero:

@@ -189,10 +189,14 @@ struct GmCfg {
     static constexpr int CA = D < 16 ? D : 16;         // amplitudes per chunk and group
     static constexpr int CK = 2 * CA;                  // K-columns per chunk
     static constexpr int NCH = KK / CK;                // chunks per tile
-    static constexpr int APT = CA * kM / kProducers;   // amplitudes per chunk and producer thread
-    static constexpr int PF = kPrefetch * 4 / APT;     // chunks of loads in flight per thread
+    // tiles per chunk: a 3-target tile is only 8 KB, so a chunk carries four of them (producer
+    // warp h loads all 8 amplitudes of its row of tile h) and the hand-offs per chunk are paid
+    // once per 32 KB
+    static constexpr int TPC = K == 3 ? 4 : 1;
+    static constexpr int APT = TPC > 1 ? CA : CA * kM / kProducers;  // amplitudes per chunk and thread
+    static constexpr int PF = TPC > 1 ? 3 : kPrefetch * 4 / APT;     // chunks of loads in flight
     static constexpr int BBYTES = N * KK * 4;
-    static constexpr int SLOT = 2 * CK;                // tensor-memory columns per chunk (hi, lo)
+    static constexpr int SLOT = TPC * 2 * CK;          // tensor-memory columns per chunk (hi, lo per tile)
     // accumulators in flight: narrow gates finish a tile every few hundred cycles, so more of
     // them keep the MMA -> epilogue hand-off off the critical path
     static constexpr int NACC = K == 3 ? 8 : (K == 6 ? 2 : 4);
@@ -217,6 +221,12 @@ __device__ __forceinline__ void tmem_st(unsigned taddr, const unsigned (&v)[8]) 
                  "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
                  : "memory");
 }
+__device__ __forceinline__ void tmem_st(unsigned taddr, const unsigned (&v)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+                 "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+                 : "memory");
+}
 __device__ __forceinline__ void tmem_st(unsigned taddr, const unsigned (&v)[4]) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
                  "r"(v[2]), "r"(v[3])
@@ -227,6 +237,8 @@ template <int K>
 __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a) {
     using C = GmCfg<K>;
     constexpr int D = C::D, N = C::N, KK = C::KK, NCH = C::NCH, NB = C::NB, APT = C::APT, PF = C::PF;
+    constexpr int TPC = C::TPC;
+    static_assert(TPC == 1 || NCH == 1, "several tiles per chunk only when a tile is one chunk");
     extern __shared__ __align__(1024) unsigned char sm[];
     float *Bs = reinterpret_cast<float *>(sm);  // [2][N*KK]
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * C::BBYTES);
@@ -275,7 +287,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a
     float2 *psi = reinterpret_cast<float2 *>(a.psi);
     const long long first = blockIdx.x, stride = gridDim.x;
     const long long ntl = first < a.ntiles ? (a.ntiles - first + stride - 1) / stride : 0;
-    const long long total = ntl * NCH;
+    const long long total = (ntl + TPC - 1) / TPC * NCH;  // chunks
     bool failed = false;
     auto group_base = [&](long long tile_i, int m) -> unsigned long long {
         const unsigned long long gidx = (unsigned long long)(first + tile_i * stride) * kM + m;
@@ -285,18 +297,21 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a
     if (warp < kEpiWarp0) {
         // ------------------------------------------------------------------ producers
         // thread: group row m (its TMEM lane), amplitudes APT h .. APT h + APT-1 of every chunk
-        // (K-columns 2 APT h .. of the slot's hi and lo halves)
+        // (K-columns 2 APT h .. of the slot's hi and lo halves); with several tiles per chunk,
+        // every amplitude of its row of the chunk's tile h
         const int q = warp & 3, h = warp >> 2, m = 32 * q + lane;
         float2 r[PF][APT];
         long long gb_tile = -1;
         unsigned long long gb_row = 0;
         auto load = [&](long long qq, float2(&rr)[APT]) {
             if (qq < total) {
-                if (qq / NCH != gb_tile) {
-                    gb_tile = qq / NCH;
-                    gb_row = group_base(gb_tile, m);
+                const long long t = TPC > 1 ? (qq / NCH) * TPC + h : qq / NCH;
+                if (t >= ntl) return;  // past the CTA's last tile: the MMAs skip it
+                if (t != gb_tile) {
+                    gb_tile = t;
+                    gb_row = group_base(t, m);
                 }
-                const int c0 = (int)(qq % NCH) * C::CA + APT * h;
+                const int c0 = (int)(qq % NCH) * C::CA + (TPC > 1 ? 0 : APT * h);
 #pragma unroll
                 for (int e = 0; e < APT; e++) rr[e] = __ldcs(psi + gb_row + toff[c0 + e]);
             }
@@ -318,7 +333,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a
                     }
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(C::NACC * N + b * C::SLOT + 2 * APT * h);
+                const unsigned ta = tmem + ((unsigned)(32 * q) << 16) + (unsigned)(C::NACC * N + b * C::SLOT + (TPC > 1 ? h * 2 * C::CK : 2 * APT * h));
                 unsigned v[2 * APT];
 #pragma unroll
                 for (int e = 0; e < APT; e++) {
@@ -377,31 +392,40 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_gm_kernel(const Args a
         const unsigned b_hi = smem_u32(Bs), b_lo = b_hi + C::BBYTES;
         for (long long qq = 0; qq < total && !failed; qq++) {
             const int b = (int)(qq % NB);
-            const int j = (int)(qq % NCH);
-            const long long t = qq / NCH;
-            const int ab = (int)(t % C::NACC);
-            if (j == 0 && t >= C::NACC && !mbar_wait(&accempty[ab], (unsigned)(((t / C::NACC) - 1) & 1))) {
-                failed = true;
-                break;
-            }
-            if (!mbar_wait(&full[b], (unsigned)((qq / NB) & 1))) {
+            const int j = (int)(qq % NCH);         // chunk within its tile
+            const long long t0 = (qq / NCH) * TPC;  // the chunk's first tile
+            // before a tile's first chunk: its accumulator has been read out by the epilogue
+            if (j == 0)
+                for (int i = 0; i < TPC && !failed; i++) {
+                    const long long t = t0 + i;
+                    if (t < ntl && t >= C::NACC &&
+                        !mbar_wait(&accempty[t % C::NACC], (unsigned)(((t / C::NACC) - 1) & 1)))
+                        failed = true;
+                }
+            if (failed || !mbar_wait(&full[b], (unsigned)((qq / NB) & 1))) {
                 failed = true;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const unsigned acc = tmem + (unsigned)(ab * N);
-            const unsigned x_hi = tmem + (unsigned)(C::NACC * N + b * C::SLOT), x_lo = x_hi + (unsigned)C::CK;
+            for (int i = 0; i < TPC; i++) {
+                const long long t = t0 + i;
+                if (t >= ntl) break;
+                const int ab = (int)(t % C::NACC);
+                const unsigned acc = tmem + (unsigned)(ab * N);
+                const unsigned x_hi = tmem + (unsigned)(C::NACC * N + b * C::SLOT + i * 2 * C::CK),
+                               x_lo = x_hi + (unsigned)C::CK;
 #pragma unroll
-            for (int kk = 0; kk < C::CK / 8; kk++) {
-                const unsigned boff = (j * (C::CK / 4) + kk * 2) * 128;  // 2 core matrices along K
-                const uint64_t dBh = make_desc(b_hi + boff, 128, KK * 32);
-                const uint64_t dBl = make_desc(b_lo + boff, 128, KK * 32);
-                mma_tf32_ta(acc, x_hi + 8u * kk, dBh, C::IDESC, (j == 0 && kk == 0) ? 0u : 1u);
-                mma_tf32_ta(acc, x_hi + 8u * kk, dBl, C::IDESC, 1u);
-                mma_tf32_ta(acc, x_lo + 8u * kk, dBh, C::IDESC, 1u);
+                for (int kk = 0; kk < C::CK / 8; kk++) {
+                    const unsigned boff = (j * (C::CK / 4) + kk * 2) * 128;  // 2 core matrices along K
+                    const uint64_t dBh = make_desc(b_hi + boff, 128, KK * 32);
+                    const uint64_t dBl = make_desc(b_lo + boff, 128, KK * 32);
+                    mma_tf32_ta(acc, x_hi + 8u * kk, dBh, C::IDESC, (j == 0 && kk == 0) ? 0u : 1u);
+                    mma_tf32_ta(acc, x_hi + 8u * kk, dBl, C::IDESC, 1u);
+                    mma_tf32_ta(acc, x_lo + 8u * kk, dBh, C::IDESC, 1u);
+                }
+                if (j == NCH - 1) commit_to(&accfull[ab]);
             }
             commit_to(&empty[b]);
-            if (j == NCH - 1) commit_to(&accfull[ab]);
         }
         // every MMA issued has completed (or the bounded wait ran out) before tensor memory is
         // released
