@@ -572,9 +572,11 @@ def sub_hhl27(args, ws, rank):
         if not args.no_autotune and not qs.qsim_tune_get(qs.QSIM_C64 if name == "c64" else qs.QSIM_C128,
                                                          qs.QSIM_TUNE_TUNED):
             tune[name] = qs.qsim_autotune(st, stream)
+        # the readout's partial sums come out of the circuit's last kernel (hhl_run_sums)
+        sums = torch.zeros(qs.QSIM_READOUT_SUMS_DOUBLES, dtype=torch.float64, device="cuda")
         for _ in range(3):
-            qs.hhl_run(st, h, circ, stream)
-            qs.hhl_readout(st, h, stream)
+            qs.hhl_run_sums(st, h, sums, circ, stream)
+            qs.hhl_readout_sums(st, h, sums, stream)
         torch.cuda.synchronize()
         lat = []
         with ClockSampler(torch.cuda.current_device()) as clk:
@@ -582,8 +584,8 @@ def sub_hhl27(args, ws, rank):
             t0 = time.perf_counter()
             for _ in range(reps[name]):
                 a = time.perf_counter()
-                qs.hhl_run(st, h, circ, stream)
-                r = qs.hhl_readout(st, h, stream)
+                qs.hhl_run_sums(st, h, sums, circ, stream)
+                r = qs.hhl_readout_sums(st, h, sums, stream)
                 lat.append(time.perf_counter() - a)
             dt_s = time.perf_counter() - t0
             nl = qs.qsim_launch_count() - l0
@@ -602,13 +604,13 @@ def sub_hhl27(args, ws, rank):
         cs = torch.cuda.Stream()
         cs.wait_stream(stream)
         with torch.cuda.stream(cs):
-            qs.hhl_run(st, h, circ, cs)
+            qs.hhl_run_sums(st, h, sums, circ, cs)
         cs.synchronize()
         with torch.cuda.graph(g, stream=cs):
-            qs.hhl_run(st, h, circ, cs)
+            qs.hhl_run_sums(st, h, sums, circ, cs)
         for _ in range(3):
             g.replay()
-            qs.hhl_readout(st, h, stream)
+            qs.hhl_readout_sums(st, h, sums, stream)
         torch.cuda.synchronize()
         glat = []
         l0 = qs.qsim_launch_count()
@@ -616,7 +618,7 @@ def sub_hhl27(args, ws, rank):
         for _ in range(reps[name]):
             a = time.perf_counter()
             g.replay()
-            rg = qs.hhl_readout(st, h, stream)
+            rg = qs.hhl_readout_sums(st, h, sums, stream)
             glat.append(time.perf_counter() - a)
         gdt = max_over_ranks(ws, time.perf_counter() - t0)
         paths[name]["graph"] = {"solves_per_s": round(ws * reps[name] / gdt, 2),
@@ -643,8 +645,8 @@ def sub_hhl27(args, ws, rank):
     rec = {
         "metric": "HHL solves/s (27 qubits, complex64 precision form)", "value": best["solves_per_s"],
         "unit": "solves/s", "ms_per_solve": best["ms_per_solve"], "dtype": "c64",
-        "solve_path": "hhl_run replayed from a CUDA graph + hhl_readout" if best is not paths["c64"]
-                      else "hhl_run + hhl_readout (eager)",
+        "solve_path": "hhl_run_sums replayed from a CUDA graph + hhl_readout_sums (readout partial sums from the circuit's last kernel)" if best is not paths["c64"]
+                      else "hhl_run_sums + hhl_readout_sums (eager)",
         "config": {"workload": "27-qubit HHL: 64x64 reduced Laplacian of a random 65-bus grid (98 lines), "
                                "nb=6, m=20, structured phase estimation, QFTs as Fourier passes",
                    "n_qubits": n, "nb": info["nb"], "m": info["m"], "host_build_ms": round(build_ms, 3),

@@ -392,6 +392,20 @@ typedef struct {
 int hhl_readout(const void *state, int dtype, const hhl_circuit *h, void *stream, double *x_out,
                 double *x_state_out, hhl_readout_stats *stats);
 
+/* Readout sums computed inside the run.  hhl_run_sums is hhl_run that also leaves, in
+ * sums_device (device memory of QSIM_READOUT_SUMS_DOUBLES doubles, caller-owned), the FP64
+ * partial sums of |psi|^2 over the final state that the readout needs: written by the circuit's
+ * last kernel while it stores the state when that is the complex64 real 7-target tensor-core
+ * gate (the eigenvector rotation V that ends the structured HHL circuit), else by a reduction
+ * pass after it.  Device-only, so it can be captured into a CUDA graph.  hhl_readout_sums is
+ * hhl_readout taking those partials instead of reducing the state again; the state must not
+ * have changed since the hhl_run_sums that wrote sums_device.  Errors: EINVAL, ENOMEM, ECUDA. */
+#define QSIM_READOUT_SUMS_DOUBLES 4096
+int hhl_run_sums(void *state, int dtype, const hhl_circuit *h, const qsim_circuit *c, void *stream,
+                 double *sums_device);
+int hhl_readout_sums(const void *state, int dtype, const hhl_circuit *h, const double *sums_device, void *stream,
+                     double *x_out, double *x_state_out, hhl_readout_stats *stats);
+
 /* ======================================================================================= *
  * Batched execution: many small circuits in one persistent launch                          *
  * ======================================================================================= */

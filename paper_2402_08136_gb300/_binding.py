@@ -129,6 +129,8 @@ _SIGS = {
     "hhl_get_info": ([_VP, ctypes.POINTER(_HHLInfo)], ctypes.c_int),
     "hhl_prepare_state": ([_VP, ctypes.c_int, _VP, _VP], ctypes.c_int),
     "hhl_run": ([_VP, ctypes.c_int, _VP, _VP, _VP], ctypes.c_int),
+    "hhl_run_sums": ([_VP, ctypes.c_int, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "hhl_readout_sums": ([_VP, ctypes.c_int, _VP, _VP, _VP, _DP, _DP, ctypes.POINTER(_ReadoutStats)], ctypes.c_int),
     "qsim_launch_count": ([], ctypes.c_ulonglong),
     "qsim_device_status": ([ctypes.POINTER(ctypes.c_uint), ctypes.c_int], ctypes.c_int),
     "qsim_batch_create": ([ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int,
@@ -507,6 +509,40 @@ def hhl_readout(state, h: HHLCircuit, stream=None) -> dict:
     _check(library().hhl_readout(ctypes.c_void_p(state.data_ptr()), _dtype_of(state), h.ptr,
                                  _stream_ptr(stream), x.view(np.float64).ctypes.data_as(_DP),
                                  xs.view(np.float64).ctypes.data_as(_DP), ctypes.byref(st)))
+    out = {f: getattr(st, f) for f, _ in st._fields_}
+    out["x"] = x
+    out["x_state"] = xs
+    return out
+
+
+QSIM_READOUT_SUMS_DOUBLES = 4096
+
+
+def hhl_run_sums(state, h: HHLCircuit, sums, circuit=None, stream=None):
+    """hhl_run that also writes the final state's readout partial sums into `sums` (a CUDA
+    float64 tensor of QSIM_READOUT_SUMS_DOUBLES entries), in the circuit's last kernel when it
+    can.  Device-only (graph-capturable)."""
+    import torch
+    _check_state(state, h.info()["n"])
+    if not (sums.is_cuda and sums.dtype == torch.float64 and sums.numel() >= QSIM_READOUT_SUMS_DOUBLES):
+        raise QsimError(-1, "sums must be a CUDA float64 tensor of QSIM_READOUT_SUMS_DOUBLES entries")
+    _check(library().hhl_run_sums(ctypes.c_void_p(state.data_ptr()), _dtype_of(state), h.ptr,
+                                  circuit.ptr if circuit is not None else None, _stream_ptr(stream),
+                                  ctypes.c_void_p(sums.data_ptr())))
+    return state
+
+
+def hhl_readout_sums(state, h: HHLCircuit, sums, stream=None) -> dict:
+    """hhl_readout from the partial sums hhl_run_sums left in `sums` (synchronizes the stream)."""
+    info = h.info()
+    _check_state(state, info["n"])
+    x = np.zeros(info["N"], dtype=np.complex128)
+    xs = np.zeros(1 << info["nb"], dtype=np.complex128)
+    st = _ReadoutStats()
+    _check(library().hhl_readout_sums(ctypes.c_void_p(state.data_ptr()), _dtype_of(state), h.ptr,
+                                      ctypes.c_void_p(sums.data_ptr()), _stream_ptr(stream),
+                                      x.view(np.float64).ctypes.data_as(_DP), xs.view(np.float64).ctypes.data_as(_DP),
+                                      ctypes.byref(st)))
     out = {f: getattr(st, f) for f, _ in st._fields_}
     out["x"] = x
     out["x_state"] = xs

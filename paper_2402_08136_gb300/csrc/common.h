@@ -141,7 +141,13 @@ void circuit_info(const qsim_circuit *c, qsim_circuit_info *out);
 // kernels.cu
 // live < n: the caller guarantees that the input is zero at every index >= 2^live and that only
 // the first 2^live amplitudes have been written (see hhl_run); the result is the full state.
-void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int live = -1);
+// sums (optional, QSIM_READOUT_SUMS_DOUBLES doubles of device memory): the readout partial sums
+// of the final state (buf[0] = P, then P partials, the first half over the lower half of the
+// state): written by the last operation's kernel when it can, else by a reduction after it
+void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int live = -1, double *sums = nullptr);
+// final readout from such a buffer: sums[3] and the (ancilla = 1, clock = 0) slice on the host
+void readout_device_sums(const void *state, int dtype, int n, int nb, void *stream, const double *buf,
+                         double sums[3], cd *slice);
 // every kernel launch site reports its launches (qsim_launch_count)
 void note_launches(int k, int family);
 // resident blocks per SM of `kernel` (a __global__ function) for this launch shape on the current
@@ -172,8 +178,11 @@ bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const 
 bool dense_tc_real7_applies(const Op &op);
 size_t dense_tc_real7_blob_bytes();
 void dense_tc_pack_real7(const std::vector<cd> &U, unsigned char *out);
+// sums (optional): readout partial sums of the result, split by bit hi_bit of the index (see
+// tc::Args); only for a gate without controls
 bool launch_dense_tc_real7(void *state, int n, const std::vector<int> &targets, const std::vector<int> &controls,
-                           const void *Bdev, int sms, cudaStream_t st);
+                           const void *Bdev, int sms, cudaStream_t st, double *sums = nullptr, int hi_bit = 0,
+                           bool *sums_written = nullptr);
 // batched.cu: plan (host image) / instantiate (device tables) / launch / results, for the pool
 struct BatchImage;
 bool batch_supported(const qsim_circuit *c);  // every op runs in the batched executor

@@ -63,6 +63,11 @@ struct Args {
     int nfix;
     int fix[kMaxFix];         // ascending: targets and controls
     int targets[8];
+    // readout sums of the result (real 7-target kernel, when not NULL): sums[0] = 2 G (G = the
+    // grid), sums[1 + c] = sum of |y|^2 over CTA c's outputs whose bit `hi_bit` is 0, sums[1 + G + c]
+    // over those where it is 1
+    double *sums;
+    int hi_bit;
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -847,6 +852,8 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Arg
         const int sub = warp - kEpiWarp0;
         const int n = sub * 32 + lane;  // output amplitude == TMEM lane
         const long long ta = toff[n];
+        double s_lo = 0.0, s_hi = 0.0;  // readout sums of this thread's outputs
+        const bool sums = a.sums != nullptr;
         for (long long t = 0; t < ntl && !failed; t++) {
             const int ab = (int)(t & 1);
             if (!mbar_wait(&accfull[ab], (unsigned)((t >> 1) & 1))) {
@@ -866,13 +873,45 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Arg
                       "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                     : "r"(acc + (unsigned)col));
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                float q8 = 0.f;  // the chunk's 8 squared magnitudes (one ancilla value per tile)
 #pragma unroll
-                for (int i = 0; i < 8; i++)
-                    __stcs(psi + tb + goff[col / 2 + i] + ta,
-                           make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])));
+                for (int i = 0; i < 8; i++) {
+                    const unsigned long long idx = tb + goff[col / 2 + i] + ta;
+                    const float yr = __uint_as_float(v[2 * i]), yi = __uint_as_float(v[2 * i + 1]);
+                    __stcs(psi + idx, make_float2(yr, yi));
+                    if (sums) q8 = __fmaf_rn(yi, yi, __fmaf_rn(yr, yr, q8));
+                }
+                if (sums) {
+                    if ((tb >> a.hi_bit) & 1ull) s_hi += (double)q8;
+                    else s_lo += (double)q8;
+                }
             }
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             mbar_arrive(&accempty[ab]);
+        }
+        if (sums) {
+            // the CTA's sums in a fixed order: warp shuffles, then the 4 epilogue warps in order
+            // (named barrier 1 holds only them)
+            __shared__ double red[8];
+            for (int o = 16; o > 0; o >>= 1) {
+                s_lo += __shfl_down_sync(0xffffffffu, s_lo, o);
+                s_hi += __shfl_down_sync(0xffffffffu, s_hi, o);
+            }
+            if (lane == 0) {
+                red[2 * sub] = s_lo;
+                red[2 * sub + 1] = s_hi;
+            }
+            asm volatile("bar.sync 1, 128;\n" ::: "memory");
+            if (sub == 0 && lane == 0) {
+                double lo = 0.0, hi = 0.0;
+                for (int w = 0; w < 4; w++) {
+                    lo += red[2 * w];
+                    hi += red[2 * w + 1];
+                }
+                a.sums[1 + blockIdx.x] = lo;
+                a.sums[1 + gridDim.x + blockIdx.x] = hi;
+                if (blockIdx.x == 0) a.sums[0] = 2.0 * (double)gridDim.x;
+            }
         }
     } else if (lane == 0) {
         // ------------------------------------------------------------------ MMA issuer
@@ -966,7 +1005,7 @@ void dense_tc_pack_real7(const std::vector<cd> &U, unsigned char *out) {
 }
 
 bool launch_dense_tc_real7(void *state, int n, const std::vector<int> &targets, const std::vector<int> &controls,
-                           const void *Bdev, int sms, cudaStream_t st) {
+                           const void *Bdev, int sms, cudaStream_t st, double *sums, int hi_bit, bool *sums_written) {
     const int free_bits = n - 7 - (int)controls.size();
     if (free_bits < 6) return false;  // fewer than 64 groups
     tc::Args a;
@@ -984,6 +1023,20 @@ bool launch_dense_tc_real7(void *state, int n, const std::vector<int> &targets, 
     a.nfix = (int)fix.size();
     for (int i = 0; i < a.nfix; i++) a.fix[i] = fix[i];
     for (int b = 0; b < 7; b++) a.targets[b] = targets[b];
+    QSIM_REQUIRE(sums == nullptr || controls.empty(), "readout sums need every amplitude written");
+    // the epilogue classifies a whole tile (64 groups) by bit hi_bit of its base: valid when that
+    // bit is above the state or a group bit with at least 6 group bits below it
+    if (sums && hi_bit < n) {
+        int below = 0;
+        bool target = false;
+        for (int q : targets) target = target || q == hi_bit;
+        for (int q = 0; q < hi_bit; q++)
+            if (std::find(targets.begin(), targets.end(), q) == targets.end()) below++;
+        if (target || below < 6) sums = nullptr;
+    }
+    if (sums_written) *sums_written = sums != nullptr;
+    a.sums = sums;
+    a.hi_bit = hi_bit;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(tc::dense_tc_real7_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -298,6 +298,34 @@ std::vector<cd> read_complex(const double *p, size_t n) {
 
 using namespace qsim;
 
+// The host side of a readout: x, |x> and the statistics from the sums and the slice.
+static void readout_finish(const hhl_circuit *h, const double sums[3], const std::vector<cd> &slice, double *x_out,
+                           double *x_state_out, hhl_readout_stats *stats) {
+    const double P = sums[1], P0 = sums[2];  // P(anc = 1), P(anc = 1, clock = 0)
+    const double inv = P0 > 0.0 ? 1.0 / std::sqrt(P0) : 0.0;
+    const double norm_x = std::sqrt(P) / h->C;
+    if (x_state_out)
+        for (size_t i = 0; i < slice.size(); i++) {
+            x_state_out[2 * i] = slice[i].real() * inv;
+            x_state_out[2 * i + 1] = slice[i].imag() * inv;
+        }
+    if (x_out)
+        for (int i = 0; i < h->N; i++) {
+            const cd x = slice[h->x_off + i] * (inv * norm_x * h->norm_b);
+            x_out[2 * i] = x.real();
+            x_out[2 * i + 1] = x.imag();
+        }
+    if (stats) {
+        stats->p_success = P;
+        stats->p_clock0 = P0;
+        stats->leakage = P - P0;
+        stats->norm2 = sums[0];
+        stats->norm_x = norm_x;
+        stats->norm_b = h->norm_b;
+    }
+}
+
+
 extern "C" {
 
 int hhl_build_ex(const double *A, const double *b, int N, int n_clock, double t, double C, int flags,
@@ -491,6 +519,30 @@ int hhl_run(void *state, int dtype, const hhl_circuit *h, const qsim_circuit *c,
     });
 }
 
+int hhl_run_sums(void *state, int dtype, const hhl_circuit *h, const qsim_circuit *c, void *stream,
+                 double *sums_device) {
+    return guarded([&] {
+        QSIM_REQUIRE(state != nullptr && h != nullptr && sums_device != nullptr, "NULL argument");
+        QSIM_REQUIRE(dtype == QSIM_C64 || dtype == QSIM_C128, "dtype must be QSIM_C64 or QSIM_C128");
+        const qsim_circuit *g = c ? c : &h->circ;
+        QSIM_REQUIRE(g->n == h->n, "circuit and HHL problem disagree on the qubit count");
+        launch_prepare_state(state, h->n, dtype, h->b_pad.data(), h->nb, stream, h->nb);
+        apply_ops(state, h->n, dtype, const_cast<qsim_circuit *>(g), stream, h->nb, sums_device);
+    });
+}
+
+int hhl_readout_sums(const void *state, int dtype, const hhl_circuit *h, const double *sums_device, void *stream,
+                     double *x_out, double *x_state_out, hhl_readout_stats *stats) {
+    return guarded([&] {
+        QSIM_REQUIRE(state != nullptr && h != nullptr && sums_device != nullptr, "NULL argument");
+        QSIM_REQUIRE(dtype == QSIM_C64 || dtype == QSIM_C128, "dtype must be QSIM_C64 or QSIM_C128");
+        double sums[3];
+        std::vector<cd> slice((size_t)1 << h->nb);
+        readout_device_sums(state, dtype, h->n, h->nb, stream, sums_device, sums, slice.data());
+        readout_finish(h, sums, slice, x_out, x_state_out, stats);
+    });
+}
+
 int hhl_readout(const void *state, int dtype, const hhl_circuit *h, void *stream, double *x_out,
                 double *x_state_out, hhl_readout_stats *stats) {
     return guarded([&] {
@@ -499,28 +551,7 @@ int hhl_readout(const void *state, int dtype, const hhl_circuit *h, void *stream
         double sums[3];  // ||psi||^2, P(anc = 1), P(anc = 1, clock = 0)
         std::vector<cd> slice((size_t)1 << h->nb);
         readout_device(state, dtype, h->n, h->nb, h->m, stream, sums, slice.data());
-        const double P = sums[1], P0 = sums[2];
-        const double inv = P0 > 0.0 ? 1.0 / std::sqrt(P0) : 0.0;
-        const double norm_x = std::sqrt(P) / h->C;
-        if (x_state_out)
-            for (size_t i = 0; i < slice.size(); i++) {
-                x_state_out[2 * i] = slice[i].real() * inv;
-                x_state_out[2 * i + 1] = slice[i].imag() * inv;
-            }
-        if (x_out)
-            for (int i = 0; i < h->N; i++) {
-                const cd x = slice[h->x_off + i] * (inv * norm_x * h->norm_b);
-                x_out[2 * i] = x.real();
-                x_out[2 * i + 1] = x.imag();
-            }
-        if (stats) {
-            stats->p_success = P;
-            stats->p_clock0 = P0;
-            stats->leakage = P - P0;
-            stats->norm2 = sums[0];
-            stats->norm_x = norm_x;
-            stats->norm_b = h->norm_b;
-        }
+        readout_finish(h, sums, slice, x_out, x_state_out, stats);
     });
 }
 

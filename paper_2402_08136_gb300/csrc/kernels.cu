@@ -686,7 +686,7 @@ __device__ __forceinline__ void ds_add_square(float x, float &hi, float &lo) {
 constexpr int kNormGroup = 16;
 
 template <typename R>
-__global__ void norm_partials_kernel(const void *state, long long chunk, double *partials) {
+__global__ void norm_partials_kernel(const void *state, long long chunk, double *partials, double *count = nullptr) {
     using V = typename C2<R>::T;
     __shared__ double sh[32];
     const V *psi = reinterpret_cast<const V *>(state) + (long long)blockIdx.x * chunk;
@@ -717,13 +717,21 @@ __global__ void norm_partials_kernel(const void *state, long long chunk, double 
     }
     const double t = block_sum(s, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    if (count && blockIdx.x == 0 && threadIdx.x == 0) *count = (double)gridDim.x;
 }
+
+// The same sums from a readout-sums buffer: buf[0] = P, the count of partial sums, then P
+// partials whose first half covers the state's lower half (ancilla = 0) and second half its
+// upper half, each half in a fixed order (written by the last pass of a run, or by
+// norm_partials_kernel).
+template <typename R>
+__global__ void norm_final_buf_kernel(const double *buf, const void *state, long long off, int len, double *out);
 
 // out[0] = sum of all partials, out[1] = sum of the upper half (ancilla = 1),
 // out[2] = sum over the slice psi[off .. off + len) (ancilla = 1, clock = 0).
 template <typename R>
-__global__ void norm_final_kernel(const double *partials, int nblk, const void *state,
-                                  long long off, int len, double *out) {
+__device__ void norm_final_body(const double *partials, int nblk, const void *state, long long off, int len,
+                                double *out) {
     using V = typename C2<R>::T;
     __shared__ double sh[32];
     double lo = 0.0, hi = 0.0, sl = 0.0;
@@ -746,6 +754,17 @@ __global__ void norm_final_kernel(const double *partials, int nblk, const void *
         out[1] = thi;
         out[2] = tsl;
     }
+}
+
+template <typename R>
+__global__ void norm_final_kernel(const double *partials, int nblk, const void *state, long long off, int len,
+                                  double *out) {
+    norm_final_body<R>(partials, nblk, state, off, len, out);
+}
+
+template <typename R>
+__global__ void norm_final_buf_kernel(const double *buf, const void *state, long long off, int len, double *out) {
+    norm_final_body<R>(buf + 1, (int)buf[0], state, off, len, out);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1167,7 +1186,9 @@ static int top_qubit(const Op &op) {
     return q;
 }
 
-void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int live) {
+static int readout_blocks(int n);
+
+void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int live, double *sums) {
     ensure_device_blob(c, dtype);
     const int slot = dtype == QSIM_C128 ? 1 : 0;
     const unsigned char *base = static_cast<const unsigned char *>(c->blob[slot].ptr);
@@ -1180,6 +1201,7 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
     // writes the upper half without reading it (inside the preceding pass when that pass runs
     // right below it); any other op first zero-fills up to its top qubit.
     int w = (live >= 0 && live < n) ? live : n;
+    bool sums_done = false;  // the last operation's kernel wrote the readout sums
     const size_t vb = 2 * real_size(dtype);
     auto materialize = [&](int to) {
         if (to <= w) return;
@@ -1297,14 +1319,19 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
                     std::vector<int> t7(op.targets);
                     t7.push_back(op.tc_pad);
                     std::sort(t7.begin(), t7.end());
+                    double *s7 = (sums && i + 1 == ops.size() && op.controls.empty()) ? sums : nullptr;
                     if (op.tc_pad < w &&
-                        launch_dense_tc_real7(state, w, t7, op.controls, base + op.dev_off_tc[slot], num_sms(), st))
+                        launch_dense_tc_real7(state, w, t7, op.controls, base + op.dev_off_tc[slot], num_sms(), st, s7,
+                                              n - 1, &sums_done))
                         break;
-                } else if (dtype == QSIM_C64 && op.has_tc && tc_enabled((int)op.targets.size(), w) &&
-                           (op.targets.size() == 7
-                                ? launch_dense_tc_real7(state, w, op.targets, op.controls, base + op.dev_off_tc[slot], num_sms(), st)
-                                : launch_dense_tc(state, w, op.targets, op.controls, base + op.dev_off_tc[slot], num_sms(), st))) {
-                    break;
+                } else if (dtype == QSIM_C64 && op.has_tc && tc_enabled((int)op.targets.size(), w)) {
+                    double *s7 = (sums && i + 1 == ops.size() && op.controls.empty() && op.targets.size() == 7) ? sums
+                                                                                                                : nullptr;
+                    if (op.targets.size() == 7
+                            ? launch_dense_tc_real7(state, w, op.targets, op.controls, base + op.dev_off_tc[slot], num_sms(),
+                                                    st, s7, n - 1, &sums_done)
+                            : launch_dense_tc(state, w, op.targets, op.controls, base + op.dev_off_tc[slot], num_sms(), st))
+                        break;
                 }
                 run_dense(state, w, dtype, op, dptr, st);
                 break;
@@ -1319,6 +1346,13 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
         }
     }
     materialize(n);
+    if (sums && !sums_done) {  // the readout sums by a reduction pass of their own
+        const int nblk = readout_blocks(n);
+        const long long chunk = (1ll << n) / nblk;
+        if (dtype == QSIM_C128) norm_partials_kernel<double><<<nblk, 256, 0, st>>>(state, chunk, sums + 1, sums);
+        else norm_partials_kernel<float><<<nblk, 256, 0, st>>>(state, chunk, sums + 1, sums);
+        check_launch("norm_partials_kernel", 1, QSIM_KERNEL_READOUT);
+    }
 }
 
 void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb, void *stream, int live) {
@@ -1429,6 +1463,48 @@ void readout_device(const void *state, int dtype, int n, int nb, int m, void *st
             } else {
                 const float *p = reinterpret_cast<const float *>(hs.data()) + 2 * i;
                 slice[i] = cd(p[0], p[1]);
+            }
+        }
+    } catch (...) {
+        if (scratch) cudaFreeAsync(scratch, st);
+        throw;
+    }
+}
+
+void readout_device_sums(const void *state, int dtype, int n, int nb, void *stream, const double *buf,
+                         double sums[3], cd *slice) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long N = 1ll << n;
+    const size_t vb = 2 * real_size(dtype);
+    const size_t slice_len = (size_t)1 << nb;
+    const long long off = N / 2;  // ancilla = 1 (the top qubit), clock = 0
+    void *scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, 64, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(QSIM_ENOMEM, std::string("cudaMallocAsync readout scratch: ") + cudaGetErrorString(e));
+    }
+    double *out = static_cast<double *>(scratch);
+    try {
+        if (dtype == QSIM_C128) norm_final_buf_kernel<double><<<1, 256, 0, st>>>(buf, state, off, (int)slice_len, out);
+        else norm_final_buf_kernel<float><<<1, 256, 0, st>>>(buf, state, off, (int)slice_len, out);
+        check_launch("norm_final_buf_kernel", 1, QSIM_KERNEL_READOUT);
+        std::vector<unsigned char> hs(slice_len * vb);
+        double hsum[3];
+        CUDA_OK(cudaMemcpyAsync(hsum, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_OK(cudaMemcpyAsync(hs.data(), static_cast<const unsigned char *>(state) + off * vb, slice_len * vb,
+                                cudaMemcpyDeviceToHost, st));
+        CUDA_OK(cudaFreeAsync(scratch, st));
+        scratch = nullptr;
+        CUDA_OK(cudaStreamSynchronize(st));
+        for (int k = 0; k < 3; k++) sums[k] = hsum[k];
+        for (size_t k = 0; k < slice_len; k++) {
+            if (dtype == QSIM_C128) {
+                const double *p = reinterpret_cast<const double *>(hs.data()) + 2 * k;
+                slice[k] = cd(p[0], p[1]);
+            } else {
+                const float *p = reinterpret_cast<const float *>(hs.data()) + 2 * k;
+                slice[k] = cd(p[0], p[1]);
             }
         }
     } catch (...) {

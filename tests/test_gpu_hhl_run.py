@@ -220,3 +220,72 @@ def test_hhl_run_replays_from_a_cuda_graph(qs, dtype, cuda_device):
         g.replay()
         torch.cuda.synchronize()
         assert torch.equal(st, eager)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_readout_sums_inside_the_run(qs, dtype, cuda_device):
+    """hhl_run_sums + hhl_readout_sums against hhl_run + hhl_readout on a 64 x 64 system with
+    12 clock qubits (19 qubits): complex64 ends with the real 7-target tensor-core V, whose
+    epilogue writes the readout partial sums (no reduction pass of its own: one readout launch
+    instead of two); complex128 takes the reduction pass and gives the same sums bit for bit.
+    The kernel adds the squares of 8 amplitudes in FP32 (16 roundings: at most 2^-20 of the
+    group's sum) and the groups in FP64, so the complex64 sums agree to 2e-6 relative with the
+    reduction pass (far inside what the state's own 1e-5 per amplitude allows), the solutions
+    likewise; both match the FP64 oracle's P and P0."""
+    p = synth.hhl27_problem()
+    m = 12
+    h = qs.hhl_build(p["A"], p["b"], m, structured=True, fft_qft=True)
+    circ = qs.qsim_fuse(h.as_circuit(), 4)
+    n = h.info()["n"]
+    a = torch.empty(1 << n, dtype=dtype, device="cuda")
+    b = torch.empty(1 << n, dtype=dtype, device="cuda")
+    sums = torch.full((qs.QSIM_READOUT_SUMS_DOUBLES,), float("nan"), dtype=torch.float64, device="cuda")
+    qs.hhl_run(a, h, circ)
+    r0 = qs.hhl_readout(a, h)
+    c0 = qs.qsim_launch_counts()
+    qs.hhl_run_sums(b, h, sums, circ)
+    c1 = qs.qsim_launch_counts()
+    r1 = qs.hhl_readout_sums(b, h, sums)
+    c2 = qs.qsim_launch_counts()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)  # the same state either way
+    fused = dtype == torch.complex64
+    assert c1["readout"] - c0["readout"] == (0 if fused else 1)
+    assert c2["readout"] - c1["readout"] == 1
+    for key in ("p_success", "p_clock0", "norm2"):
+        if fused:
+            assert abs(r1[key] - r0[key]) <= 2e-6 * abs(r0[key])
+        else:
+            assert r1[key] == r0[key]
+    assert np.max(np.abs(r1["x"] - r0["x"])) <= 2e-6 * np.max(np.abs(r0["x"]))
+    ref = ohhl.solve(p["A"], p["b"], m)
+    tol = 1e-5 if fused else max(1e-12, 2.0 ** m * 2 * math.pi * 8 * np.finfo(float).eps)
+    bound = 2 * tol * np.sum(np.abs(ref["psi"])) + (1 << n) * tol * tol
+    assert abs(r1["p_success"] - ref["P"]) <= bound
+    assert abs(r1["p_clock0"] - ref["P0"]) <= bound
+
+
+@pytest.mark.gpu
+def test_readout_sums_replay_from_a_cuda_graph(qs, cuda_device):
+    """hhl_run_sums is device-only after its first call: captured once, replayed, read out."""
+    p = synth.hhl27_problem()
+    h = qs.hhl_build(p["A"], p["b"], 12, structured=True, fft_qft=True)
+    circ = qs.qsim_fuse(h.as_circuit(), 4)
+    n = h.info()["n"]
+    st = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    sums = torch.zeros(qs.QSIM_READOUT_SUMS_DOUBLES, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        qs.hhl_run_sums(st, h, sums, circ, stream=s)
+    s.synchronize()
+    r0 = qs.hhl_readout_sums(st, h, sums, stream=s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        qs.hhl_run_sums(st, h, sums, circ, stream=s)
+    sums.zero_()
+    g.replay()
+    r1 = qs.hhl_readout_sums(st, h, sums, stream=s)
+    assert r1["p_success"] == r0["p_success"] and r1["p_clock0"] == r0["p_clock0"]
+    assert np.array_equal(r1["x"], r0["x"])
