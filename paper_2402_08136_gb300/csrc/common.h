@@ -158,10 +158,12 @@ void ensure_device_blob(qsim_circuit *c, int dtype);
 std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype);   // sets op offsets
 void attach_external_blob(qsim_circuit *c, int dtype, void *dev, size_t bytes);
 // launches the readout reductions and async copies of the sums (3 doubles) and of the raw
-// 2^nb-amplitude slice into pinned host memory; scratch holds >= readout_scratch_doubles(n)
+// 2^nb-amplitude slice into pinned host memory; scratch holds >= readout_scratch_doubles(n),
+// its first QSIM_READOUT_SUMS_DOUBLES entries a readout-sums buffer (already written by
+// apply_ops when sums_ready)
 size_t readout_scratch_doubles(int n);
 void readout_launch_async(const void *state, int dtype, int n, int nb, cudaStream_t st, double *scratch,
-                          double *pinned_sums, void *pinned_slice);
+                          double *pinned_sums, void *pinned_slice, bool sums_ready = false);
 // live in [nb, n): zero and write only the first 2^live amplitudes (apply_ops with the same
 // live width treats the rest as zero)
 void launch_prepare_state(void *state, int n, int dtype, const cd *b_pad, int nb, void *stream,

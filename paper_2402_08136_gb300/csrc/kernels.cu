@@ -1392,25 +1392,30 @@ static int readout_blocks(int n) {
     return 1 << lg;
 }
 
-size_t readout_scratch_doubles(int n) { return (size_t)readout_blocks(n) + 8; }
+// scratch of readout_launch_async: a readout-sums buffer (count, then up to 4095 partials) and
+// the 3 final sums
+size_t readout_scratch_doubles(int n) {
+    (void)n;
+    return (size_t)QSIM_READOUT_SUMS_DOUBLES + 8;
+}
 
 void readout_launch_async(const void *state, int dtype, int n, int nb, cudaStream_t st, double *scratch,
-                          double *pinned_sums, void *pinned_slice) {
+                          double *pinned_sums, void *pinned_slice, bool sums_ready) {
     const long long N = 1ll << n;
-    const int nblk = readout_blocks(n);
-    const long long chunk = N / nblk;
     const size_t vb = 2 * real_size(dtype);
     const size_t slice_len = (size_t)1 << nb;
-    double *partials = scratch, *out = scratch + nblk;
+    double *out = scratch + QSIM_READOUT_SUMS_DOUBLES;
     const long long off = N / 2;
-    if (dtype == QSIM_C128) {
-        norm_partials_kernel<double><<<nblk, 256, 0, st>>>(state, chunk, partials);
-        norm_final_kernel<double><<<1, 256, 0, st>>>(partials, nblk, state, off, (int)slice_len, out);
-    } else {
-        norm_partials_kernel<float><<<nblk, 256, 0, st>>>(state, chunk, partials);
-        norm_final_kernel<float><<<1, 256, 0, st>>>(partials, nblk, state, off, (int)slice_len, out);
+    if (!sums_ready) {  // the partial sums by a reduction pass (else apply_ops left them)
+        const int nblk = readout_blocks(n);
+        const long long chunk = N / nblk;
+        if (dtype == QSIM_C128) norm_partials_kernel<double><<<nblk, 256, 0, st>>>(state, chunk, scratch + 1, scratch);
+        else norm_partials_kernel<float><<<nblk, 256, 0, st>>>(state, chunk, scratch + 1, scratch);
+        check_launch("norm_partials_kernel", 1, QSIM_KERNEL_READOUT);
     }
-    check_launch("readout kernels", 2, QSIM_KERNEL_READOUT);
+    if (dtype == QSIM_C128) norm_final_buf_kernel<double><<<1, 256, 0, st>>>(scratch, state, off, (int)slice_len, out);
+    else norm_final_buf_kernel<float><<<1, 256, 0, st>>>(scratch, state, off, (int)slice_len, out);
+    check_launch("norm_final_buf_kernel", 1, QSIM_KERNEL_READOUT);
     CUDA_OK(cudaMemcpyAsync(pinned_sums, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_OK(cudaMemcpyAsync(pinned_slice, static_cast<const unsigned char *>(state) + off * vb, slice_len * vb,
                             cudaMemcpyDeviceToHost, st));

@@ -327,9 +327,10 @@ void launch_large(qsim_pool *p, Slot &s, PoolReq *r) {
     // only the data register is populated after the preparation (clock and ancilla |0>): the
     // executor widens the live part as the circuit fills it (as hhl_run does)
     launch_prepare_state(r->state, r->n, dtype, r->h->b_pad.data(), r->h->nb, s.st, r->h->nb);
-    apply_ops(r->state, r->n, dtype, r->fused, s.st, r->h->nb);
-    readout_launch_async(r->state, dtype, r->n, r->h->nb, s.st, static_cast<double *>(addr(p, sb)), s.pinned,
-                         s.pinned + 4);
+    // the readout partial sums come from the circuit's last kernel when it can write them
+    double *scratch = static_cast<double *>(addr(p, sb));
+    apply_ops(r->state, r->n, dtype, r->fused, s.st, r->h->nb, scratch);
+    readout_launch_async(r->state, dtype, r->n, r->h->nb, s.st, scratch, s.pinned, s.pinned + 4, true);
     e = cudaEventRecord(s.ev_end, s.st);
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, cudaGetErrorString(e));
     e = cudaEventRecord(s.ev, s.st);
