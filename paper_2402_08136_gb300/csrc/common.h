@@ -97,9 +97,12 @@ struct Op {
     // the real form (tensor cores); OP_QPE_PHASE, the high half of its two-table split
     size_t dev_off_tc[2] = {0, 0};
     bool has_tc = false;
-    // complex64 real 6-target op on qubits 0 and 1 run by the real 7-target tensor-core kernel
-    // as I (x) U: the added qubit (-1: none), the lowest one that is neither target nor control
-    int tc_pad = -1;
+    // complex64 op on qubits 0 and 1 widened with identity qubits for a tensor-core form whose
+    // loads and stores run along the low qubits: a real U of 4..6 targets to 7 (the real 7-target
+    // kernel), a complex U of 4..5 targets to 6 (the transposed form).  tc_pads: the added
+    // qubits (empty: none), the lowest that are neither target nor control; tc_pad_k: 7 or 6
+    std::vector<int> tc_pads;
+    int tc_pad_k = 0;
     bool real_u = false;        // OP_DENSE: every entry of U is real (SIMT kernels use 2 FMAs per entry)
 };
 

@@ -1070,33 +1070,74 @@ std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype) {
             const int D = 1 << (int)op.targets.size();
             for (int col = 0; col < D; col++)
                 for (int r = 0; r < D; r++) put_complex(blob, dtype, op.U[(size_t)r * D + col]);
-            int pad = -1;
-            if (dtype == QSIM_C64 && op.real_u && op.targets.size() == 6 && op.targets[0] == 0 && op.targets[1] == 1)
-                for (int q = 2; q < c->n && pad < 0; q++) {
-                    bool used = false;
-                    for (int x : op.targets) used = used || x == q;
-                    for (int x : op.controls) used = used || x == q;
-                    if (!used) pad = q;
+            // Gates of 4..6 targets on qubit 0 or 1 (the other one a target or free) are widened
+            // with identity qubits to the tensor-core forms that run along the low qubits: the
+            // transposed 6-target form (any U) and the real 7-target form (real U).  The
+            // group-major form's warp loads touch 32 / 2^f lines of 128 B, f = free qubits among
+            // 0..3; at 28 qubits it takes 0.72-0.75 ms with f >= 2, 1.1 ms with f = 1, 2.1 ms with
+            // f = 0.  The transposed form takes 0.74 ms with qubit 2 or 3 free, else 0.88 ms; the
+            // real 7-target form 0.78 ms.
+            const int k = (int)op.targets.size();
+            auto used = [&](int q) {
+                for (int x : op.targets) if (x == q) return true;
+                for (int x : op.controls) if (x == q) return true;
+                return false;
+            };
+            const bool t0 = op.targets[0] == 0, t1 = std::find(op.targets.begin(), op.targets.end(), 1) != op.targets.end();
+            const int miss = !t0 + !t1;
+            const bool low23 = c->n > 3 && (!used(2) || !used(3));
+            int f = 0;
+            for (int q = 0; q < 4 && q < c->n; q++) f += !used(q);
+            int padk = 0;
+            bool keep23 = false;  // take the added qubits from 4 up, keeping qubit 2 or 3 free
+            if (dtype == QSIM_C64 && k >= 4 && k <= 6 && (t0 || t1) && (t0 || !used(0)) && (t1 || !used(1))) {
+                if (k == 6 && miss == 0) {
+                    if (op.real_u && !low23) padk = 7;  // the transposed form itself is slow here
+                } else if (f <= 1) {
+                    if (k + miss <= 6 && (low23 || !op.real_u)) {
+                        padk = 6;
+                        keep23 = low23;
+                    } else if (op.real_u && k + miss <= 7) {
+                        padk = 7;
+                    }
                 }
-            if (pad >= 0) {
-                // real U on the lowest qubits: the real 7-target kernel (U as the MMA's A operand,
-                // 128-byte output runs) with I (x) U on the lowest free qubit beats the
-                // transposed complex form (449 against 505 us at 27 qubits)
-                std::vector<int> t7(op.targets);
-                t7.push_back(pad);
-                std::sort(t7.begin(), t7.end());
-                const int pbit = (int)(std::find(t7.begin(), t7.end(), pad) - t7.begin());
-                auto drop = [&](int x) { return ((x >> (pbit + 1)) << pbit) | (x & ((1 << pbit) - 1)); };
-                std::vector<cd> U7((size_t)128 * 128, cd(0.0, 0.0));
-                for (int r = 0; r < 128; r++)
-                    for (int cc = 0; cc < 128; cc++)
-                        if (((r >> pbit) & 1) == ((cc >> pbit) & 1)) U7[(size_t)r * 128 + cc] = op.U[(size_t)drop(r) * 64 + drop(cc)];
+            }
+            std::vector<int> pads;  // qubits 0 and 1 when missing, then the lowest free ones
+            if (padk) {
+                if (!t0) pads.push_back(0);
+                if (!t1) pads.push_back(1);
+                for (int q = keep23 ? 4 : 2; q < c->n && (int)pads.size() < padk - k; q++)
+                    if (!used(q)) pads.push_back(q);
+            }
+            if (padk && (int)pads.size() == padk - k) {
+                std::vector<int> tw(op.targets);
+                tw.insert(tw.end(), pads.begin(), pads.end());
+                std::sort(tw.begin(), tw.end());
+                int pmask = 0;  // bit positions of the added qubits in the widened index
+                for (int q : pads) pmask |= 1 << (int)(std::find(tw.begin(), tw.end(), q) - tw.begin());
+                auto drop = [&](int x) {  // the widened index without the added bits
+                    int v = 0, b = 0;
+                    for (int i = 0; i < padk; i++)
+                        if (!((pmask >> i) & 1)) v |= ((x >> i) & 1) << b++;
+                    return v;
+                };
+                const int DW = 1 << padk;
+                std::vector<cd> UW((size_t)DW * DW, cd(0.0, 0.0));
+                for (int r = 0; r < DW; r++)
+                    for (int cc = 0; cc < DW; cc++)
+                        if ((r & pmask) == (cc & pmask)) UW[(size_t)r * DW + cc] = op.U[(size_t)drop(r) * D + drop(cc)];
                 align_blob(blob);
                 op.dev_off_tc[slot] = blob.size();
                 op.has_tc = true;
-                op.tc_pad = pad;
-                blob.resize(blob.size() + dense_tc_real7_blob_bytes());
-                dense_tc_pack_real7(U7, blob.data() + op.dev_off_tc[slot]);
+                op.tc_pads = pads;
+                op.tc_pad_k = padk;
+                if (padk == 7) {
+                    blob.resize(blob.size() + dense_tc_real7_blob_bytes());
+                    dense_tc_pack_real7(UW, blob.data() + op.dev_off_tc[slot]);
+                } else {
+                    blob.resize(blob.size() + dense_tc_blob_bytes(6));
+                    dense_tc_pack(6, UW, blob.data() + op.dev_off_tc[slot]);
+                }
             } else if (dtype == QSIM_C64 && dense_tc_supported((int)op.targets.size())) {
                 align_blob(blob);
                 op.dev_off_tc[slot] = blob.size();
@@ -1314,16 +1355,21 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
         materialize(top_qubit(op) + 1);
         switch (op.kind) {
             case OP_DENSE:
-                if (dtype == QSIM_C64 && op.has_tc && tc_enabled(7, w) && op.tc_pad >= 0) {
-                    // real 6-target gate padded to 7 targets (the pad must lie inside the live width)
-                    std::vector<int> t7(op.targets);
-                    t7.push_back(op.tc_pad);
-                    std::sort(t7.begin(), t7.end());
-                    double *s7 = (sums && i + 1 == ops.size() && op.controls.empty()) ? sums : nullptr;
-                    if (op.tc_pad < w &&
-                        launch_dense_tc_real7(state, w, t7, op.controls, base + op.dev_off_tc[slot], num_sms(), st, s7,
-                                              n - 1, &sums_done))
-                        break;
+                if (dtype == QSIM_C64 && op.has_tc && !op.tc_pads.empty()) {
+                    // widened with identity qubits; all of them must lie inside the live width
+                    bool inside = tc_enabled(op.tc_pad_k, w);
+                    for (int q : op.tc_pads) inside = inside && q < w;
+                    if (inside) {
+                        std::vector<int> tw(op.targets);
+                        tw.insert(tw.end(), op.tc_pads.begin(), op.tc_pads.end());
+                        std::sort(tw.begin(), tw.end());
+                        double *s7 = (sums && i + 1 == ops.size() && op.controls.empty()) ? sums : nullptr;
+                        if (op.tc_pad_k == 7
+                                ? launch_dense_tc_real7(state, w, tw, op.controls, base + op.dev_off_tc[slot], num_sms(),
+                                                        st, s7, n - 1, &sums_done)
+                                : launch_dense_tc(state, w, tw, op.controls, base + op.dev_off_tc[slot], num_sms(), st))
+                            break;
+                    }
                 } else if (dtype == QSIM_C64 && op.has_tc && tc_enabled((int)op.targets.size(), w)) {
                     double *s7 = (sums && i + 1 == ops.size() && op.controls.empty() && op.targets.size() == 7) ? sums
                                                                                                                 : nullptr;

@@ -86,9 +86,11 @@ def test_dense_gate_parity(qs, dtype, k):
 def tc_on(qs):
     """Select the tensor-core kernel for dense gates of k targets (every size class); the
     kernel-choice table is put back afterwards."""
-    def on(k):
+    def on(*ks):
         mask = qs.qsim_tune_get(qs.QSIM_C64, qs.QSIM_TUNE_DENSE_TC, 17)
-        qs.qsim_tune_set(qs.QSIM_C64, qs.QSIM_TUNE_DENSE_TC, mask | (1 << k))
+        for k in ks:
+            mask |= 1 << k
+        qs.qsim_tune_set(qs.QSIM_C64, qs.QSIM_TUNE_DENSE_TC, mask)
     yield on
     qs.qsim_tune_reset()
 
@@ -96,8 +98,9 @@ def tc_on(qs):
 @pytest.mark.parametrize("k", [3, 4, 5, 6])
 def test_tensor_core_dense_parity_complex64(qs, k, tc_on):
     """complex64 gates with 3..6 targets and at least 128 groups run on the tcgen05 3xTF32
-    kernel: low, high and random targets, with and without controls, vs the FP64 oracle."""
-    tc_on(k)
+    kernel: low, high and random targets, with and without controls, vs the FP64 oracle.  4 and
+    5 targets on qubits 0 and 1 run widened to the 6-target transposed form."""
+    tc_on(k, 6)
     before = qs.qsim_launch_counts()["dense_tc"]
     rng = np.random.default_rng(500 + k)
     n = 17
@@ -143,6 +146,55 @@ def test_real_six_target_gates_on_low_qubits(qs):
         st = dev_state(psi, dtype)
         qs.qsim_apply(st, qs.Circuit(n).add_gate(t, U, ctl))
         torch.cuda.synchronize()
+        check(st, ref, dtype)
+    st = dev_state(psi, dtype)
+    qs.qsim_apply(st, c_all)
+    torch.cuda.synchronize()
+    check(st, ref_all, dtype)
+
+
+@pytest.mark.parametrize("real", [False, True])
+def test_widened_low_qubit_gates(qs, real, tc_on):
+    """complex64 gates of 4..6 targets on qubit 0 or 1, widened with identity qubits to the
+    6-target transposed form or (real U) the real 7-target form where the group-major form's
+    loads are poor (at most one free qubit among 0..3).  The added qubits are qubits 0 and 1
+    when free, then the lowest that are neither target nor control (from qubit 4 up when qubit
+    2 or 3 is free and the transposed form is taken): above the targets, between them, moved up
+    by controls.  Gates with qubit 0 or 1 a control, or with free low qubits, stay in the
+    group-major form.  Each gate alone (one tensor-core launch) and all in one circuit."""
+    tc_on(6, 7)
+    dtype = torch.complex64
+    rng = np.random.default_rng(77 + real)
+    n = 16
+    psi = host_input(synth.gaussian_state_np(78, n), dtype)
+    cases = [([0, 1, 2, 3], []), ([0, 1, 3, 6], []), ([0, 1, 2, 3], [4, 5]), ([1, 0, 5, 2, 9], [3]),
+             ([0, 1, 2, 3, 4], []), ([0, 1, 4, 7, 8], [2, 15]),
+             ([1, 2, 3, 4], []), ([0, 2, 3, 9], [12]), ([0, 1, 2, 9], []), ([0, 1, 3, 7, 9], [4]),
+             ([0, 5, 9, 13], [2]), ([1, 3, 6, 8, 10], []),
+             ([1, 3, 6, 8], [0]), ([0, 3, 4, 6, 7], [1])]  # the last two: qubit 0 or 1 a control
+    if real:
+        cases += [([0, 1, 2, 3, 4, 5], [6]), ([0, 1, 3, 5, 7, 9], [2, 4]), ([1, 2, 3, 4, 5, 6], []),
+                  ([0, 1, 2, 3, 9, 13], []), ([0, 1, 2, 9, 13, 15], []),
+                  ([0, 2, 4, 6, 8, 10], [1]), ([6, 5, 4, 3, 2, 0], [13, 14])]
+    c_all = qs.Circuit(n)
+    ref_all = psi.copy()
+    for t, ctl in cases:
+        D = 1 << len(t)
+        if real:
+            Q, _ = np.linalg.qr(rng.standard_normal((D, D)))
+            U = Q.astype(np.complex128)
+        else:
+            U = synth.haar_unitary(rng, D)
+        c_all.add_gate(t, U, ctl)
+        ocore.apply_gate(ref_all, t, U, ctl)
+        ref = psi.copy()
+        ocore.apply_gate(ref, t, U, ctl)
+        st = dev_state(psi, dtype)
+        before = qs.qsim_launch_counts()["dense_tc"]
+        qs.qsim_apply(st, qs.Circuit(n).add_gate(t, U, ctl))
+        torch.cuda.synchronize()
+        assert qs.qsim_device_status() == 0
+        assert qs.qsim_launch_counts()["dense_tc"] - before == 1, (t, ctl)
         check(st, ref, dtype)
     st = dev_state(psi, dtype)
     qs.qsim_apply(st, c_all)
