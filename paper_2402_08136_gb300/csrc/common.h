@@ -97,12 +97,14 @@ struct Op {
     // the real form (tensor cores); OP_QPE_PHASE, the high half of its two-table split
     size_t dev_off_tc[2] = {0, 0};
     bool has_tc = false;
-    // complex64 op on qubits 0 and 1 widened with identity qubits for a tensor-core form whose
-    // loads and stores run along the low qubits: a real U of 4..6 targets to 7 (the real 7-target
-    // kernel), a complex U of 4..5 targets to 6 (the transposed form).  tc_pads: the added
-    // qubits (empty: none), the lowest that are neither target nor control; tc_pad_k: 7 or 6
+    // complex64 dense op on qubit 0 or 1 widened with identity qubits to a tensor-core form whose
+    // loads and stores run along the low qubits: the transposed 6-target form (1..5 targets) or
+    // the real 7-target kernel (a real U of 6 targets without qubit 0 or 1).  tc_pads: the added
+    // qubits (empty: not widened), qubits 0 and 1 among them when not targets; tc_pad_k: 6 or 7;
+    // dev_off_tcw: the widened form's blob (complex64 device data)
     std::vector<int> tc_pads;
     int tc_pad_k = 0;
+    size_t dev_off_tcw = 0;
     bool real_u = false;        // OP_DENSE: every entry of U is real (SIMT kernels use 2 FMAs per entry)
 };
 
@@ -177,8 +179,11 @@ void readout_device(const void *state, int dtype, int n, int nb, int m, void *st
 bool dense_tc_supported(int k);
 size_t dense_tc_blob_bytes(int k);
 void dense_tc_pack(int k, const std::vector<cd> &U, unsigned char *out);
+// sums (may be NULL): readout partial sums of the result, written by the transposed form only
+// (6 targets with qubits 0 and 1, no controls); *sums_written says whether they were
 bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const std::vector<int> &controls,
-                     const void *Bdev, int sms, cudaStream_t st);
+                     const void *Bdev, int sms, cudaStream_t st, double *sums = nullptr, int hi_bit = 0,
+                     bool *sums_written = nullptr);
 // complex64, real U on 7 targets including qubits 0 and 1 (ascending)
 bool dense_tc_real7_applies(const Op &op);
 size_t dense_tc_real7_blob_bytes();

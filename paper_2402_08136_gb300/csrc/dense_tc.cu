@@ -482,6 +482,32 @@ __device__ __forceinline__ void u_to_tmem(const float *Ug, unsigned tmem, unsign
     asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
 }
 
+// The CTA's readout sums (see Args::sums) from its 4 epilogue warps, in a fixed order: warp
+// shuffles, then the warps in order (named barrier 1 holds only them).  Every epilogue thread
+// calls it, also after a failed wait.
+__device__ __forceinline__ void epi_store_sums(double s_lo, double s_hi, int sub, int lane, const Args &a) {
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) {
+        s_lo += __shfl_down_sync(0xffffffffu, s_lo, o);
+        s_hi += __shfl_down_sync(0xffffffffu, s_hi, o);
+    }
+    if (lane == 0) {
+        red[2 * sub] = s_lo;
+        red[2 * sub + 1] = s_hi;
+    }
+    asm volatile("bar.sync 1, 128;\n" ::: "memory");
+    if (sub == 0 && lane == 0) {
+        double lo = 0.0, hi = 0.0;
+        for (int w = 0; w < 4; w++) {
+            lo += red[2 * w];
+            hi += red[2 * w + 1];
+        }
+        a.sums[1 + blockIdx.x] = lo;
+        a.sums[1 + gridDim.x + blockIdx.x] = hi;
+        if (blockIdx.x == 0) a.sums[0] = 2.0 * (double)gridDim.x;
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Transposed form (6 targets including qubits 0 and 1).  When the targets are the lowest qubits,
 // a group's amplitudes are contiguous but consecutive groups are 2^k amplitudes apart, and the
@@ -490,7 +516,7 @@ __device__ __forceinline__ void u_to_tmem(const float *Ug, unsigned tmem, unsign
 // with B (the real form of U, hi and lo) as the MMA's A operand, held in tensor memory next to
 // the two accumulators (U columns 256..511), and the tile's 128 groups as its B operand (N =
 // 128), a ring of six shared-memory chunks of 32 K-columns.  Producers load each group's 16
-// amplitudes of a chunk as 16-byte vectors (a warp reads 8 groups x 64 contiguous bytes), and
+// amplitudes of a chunk as 16-byte vectors (a warp reads 4 groups x 128 contiguous bytes), and
 // the accumulator's TMEM lanes are output reals, so the epilogue's warp stores write 32
 // consecutive floats of one group.  Roles, barriers and bounded waits as in the group-major
 // kernels.
@@ -567,25 +593,27 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_tr_kernel(const Args a
 
     if (warp < kEpiWarp0) {
         // ------------------------------------------------------------------ producers
-        // thread t owns group row m and amplitude pairs h and h + 4 of every chunk (amplitudes
-        // 2h, 2h+1, 2h+8, 2h+9 of its 16).  A warp is 8 rows x 4 consecutive pairs (8 runs of
-        // 64 bytes per vector load), a quarter-warp 8 rows x 1 pair (16-byte shared-memory
-        // stores into 8 distinct bank slots).
-        const int m = 8 * (tid >> 5) + (tid & 7);
-        const int h = (tid >> 3) & 3;
+        // thread (warp w, lane l): amplitude pair h = l / 4 (amplitudes 2h, 2h+1 of the chunk's
+        // 16) of group rows 8w + (l mod 4) and 8w + 4 + (l mod 4).  A warp's vector load reads 4
+        // rows x 16 amplitudes, which are 4 whole 128-byte lines whether qubits 2 and 3 are
+        // targets or free (one free: its two rows share a line).  The 16-byte shared-memory
+        // stores alternate the rows between lanes of odd and even h, so a quarter-warp covers all
+        // 8 row slots of a core matrix (no bank conflict).
+        const int rw = lane & 3, h = lane >> 2;
         float2 r[kPrefetch][kAmpsPT];
         long long gb_tile = -1;
-        unsigned long long gb_row = 0;
+        unsigned long long gb_base = 0;
+        const long long gA = goff[8 * warp + rw], gB = goff[8 * warp + 4 + rw];
         auto load = [&](long long qq, float2(&rr)[kAmpsPT]) {
             if (qq < total) {
                 if (qq / NCH != gb_tile) {
                     gb_tile = qq / NCH;
-                    gb_row = tile_base(gb_tile) + (unsigned long long)goff[m];
+                    gb_base = tile_base(gb_tile);
                 }
                 // qubit 0 is a target: each pair is contiguous
-                const int c0 = (int)(qq % NCH) * 16 + 2 * h;
-                const float4 u0 = __ldcs(reinterpret_cast<const float4 *>(psi + gb_row + toff[c0]));
-                const float4 u1 = __ldcs(reinterpret_cast<const float4 *>(psi + gb_row + toff[c0 + 8]));
+                const long long t0 = toff[(int)(qq % NCH) * 16 + 2 * h];
+                const float4 u0 = __ldcs(reinterpret_cast<const float4 *>(psi + gb_base + gA + t0));
+                const float4 u1 = __ldcs(reinterpret_cast<const float4 *>(psi + gb_base + gB + t0));
                 rr[0] = make_float2(u0.x, u0.y);
                 rr[1] = make_float2(u0.z, u0.w);
                 rr[2] = make_float2(u1.x, u1.y);
@@ -608,9 +636,10 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_tr_kernel(const Args a
                 unsigned char *ahi = Aring + b * 2 * ABYTES;
                 unsigned char *alo = ahi + ABYTES;
 #pragma unroll
-                for (int pi = 0; pi < 2; pi++) {  // pair h + 4 pi: chunk reals 4h + 16 pi .. +3
-                    const float2 x0 = r[p][2 * pi], x1 = r[p][2 * pi + 1];
-                    const unsigned off = (m >> 3) * 1024 + (h + 4 * pi) * 128 + (m & 7) * 16;
+                for (int pi = 0; pi < 2; pi++) {  // row 8w + rw (pi = h mod 2) or 8w + 4 + rw
+                    const int rowB = pi ^ (h & 1);
+                    const float2 x0 = rowB ? r[p][2] : r[p][0], x1 = rowB ? r[p][3] : r[p][1];
+                    const unsigned off = warp * 1024 + h * 128 + (4 * rowB + rw) * 16;
                     const unsigned h0 = to_tf32(x0.x), h1 = to_tf32(x0.y);
                     const unsigned h2 = to_tf32(x1.x), h3 = to_tf32(x1.y);
                     *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(h0, h1, h2, h3);
@@ -629,6 +658,8 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_tr_kernel(const Args a
         const int m = sub * 32 + lane;             // output real
         const long long ta = toff[m >> 1];         // its amplitude
         float *psif = reinterpret_cast<float *>(a.psi);
+        double s_lo = 0.0, s_hi = 0.0;  // readout sums of this thread's outputs
+        const bool sums = a.sums != nullptr;
         for (long long t = 0; t < ntl && !failed; t++) {
             const int ab = (int)(t & 1);
             if (!mbar_wait(&accfull[ab], (unsigned)((t >> 1) & 1))) {
@@ -649,13 +680,22 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_tr_kernel(const Args a
                     : "r"(acc + (unsigned)col));
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                 // v[i] = output real m of tile group col + i
+                float q16 = 0.f;  // their 16 squares (one ancilla value per tile)
 #pragma unroll
-                for (int i = 0; i < 16; i++)
-                    __stcs(psif + 2 * (long long)(gb + goff[col + i] + ta) + (m & 1), __uint_as_float(v[i]));
+                for (int i = 0; i < 16; i++) {
+                    const float y = __uint_as_float(v[i]);
+                    __stcs(psif + 2 * (long long)(gb + goff[col + i] + ta) + (m & 1), y);
+                    if (sums) q16 = __fmaf_rn(y, y, q16);
+                }
+                if (sums) {
+                    if ((gb >> a.hi_bit) & 1ull) s_hi += (double)q16;
+                    else s_lo += (double)q16;
+                }
             }
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             mbar_arrive(&accempty[ab]);
         }
+        if (sums) epi_store_sums(s_lo, s_hi, sub, lane, a);
     } else if (lane == 0) {
         // ------------------------------------------------------------------ MMA issuer
         const unsigned aring_u32 = smem_u32(Aring);
@@ -889,30 +929,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Arg
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             mbar_arrive(&accempty[ab]);
         }
-        if (sums) {
-            // the CTA's sums in a fixed order: warp shuffles, then the 4 epilogue warps in order
-            // (named barrier 1 holds only them)
-            __shared__ double red[8];
-            for (int o = 16; o > 0; o >>= 1) {
-                s_lo += __shfl_down_sync(0xffffffffu, s_lo, o);
-                s_hi += __shfl_down_sync(0xffffffffu, s_hi, o);
-            }
-            if (lane == 0) {
-                red[2 * sub] = s_lo;
-                red[2 * sub + 1] = s_hi;
-            }
-            asm volatile("bar.sync 1, 128;\n" ::: "memory");
-            if (sub == 0 && lane == 0) {
-                double lo = 0.0, hi = 0.0;
-                for (int w = 0; w < 4; w++) {
-                    lo += red[2 * w];
-                    hi += red[2 * w + 1];
-                }
-                a.sums[1 + blockIdx.x] = lo;
-                a.sums[1 + gridDim.x + blockIdx.x] = hi;
-                if (blockIdx.x == 0) a.sums[0] = 2.0 * (double)gridDim.x;
-            }
-        }
+        if (sums) epi_store_sums(s_lo, s_hi, sub, lane, a);
     } else if (lane == 0) {
         // ------------------------------------------------------------------ MMA issuer
         const unsigned aring_u32 = smem_u32(Aring);
@@ -1004,6 +1021,18 @@ void dense_tc_pack_real7(const std::vector<cd> &U, unsigned char *out) {
         }
 }
 
+// The readout-sum epilogues classify a whole tile (2^tile_bits groups) by bit hi_bit of its base:
+// valid when that bit is above the state, or a group bit with at least tile_bits group bits below.
+static bool tile_classifies(int n, const std::vector<int> &targets, int hi_bit, int tile_bits) {
+    if (hi_bit >= n) return true;
+    int below = 0;
+    for (int q : targets)
+        if (q == hi_bit) return false;
+    for (int q = 0; q < hi_bit; q++)
+        if (std::find(targets.begin(), targets.end(), q) == targets.end()) below++;
+    return below >= tile_bits;
+}
+
 bool launch_dense_tc_real7(void *state, int n, const std::vector<int> &targets, const std::vector<int> &controls,
                            const void *Bdev, int sms, cudaStream_t st, double *sums, int hi_bit, bool *sums_written) {
     const int free_bits = n - 7 - (int)controls.size();
@@ -1024,16 +1053,7 @@ bool launch_dense_tc_real7(void *state, int n, const std::vector<int> &targets, 
     for (int i = 0; i < a.nfix; i++) a.fix[i] = fix[i];
     for (int b = 0; b < 7; b++) a.targets[b] = targets[b];
     QSIM_REQUIRE(sums == nullptr || controls.empty(), "readout sums need every amplitude written");
-    // the epilogue classifies a whole tile (64 groups) by bit hi_bit of its base: valid when that
-    // bit is above the state or a group bit with at least 6 group bits below it
-    if (sums && hi_bit < n) {
-        int below = 0;
-        bool target = false;
-        for (int q : targets) target = target || q == hi_bit;
-        for (int q = 0; q < hi_bit; q++)
-            if (std::find(targets.begin(), targets.end(), q) == targets.end()) below++;
-        if (target || below < 6) sums = nullptr;
-    }
+    if (sums && !tile_classifies(n, targets, hi_bit, 6)) sums = nullptr;
     if (sums_written) *sums_written = sums != nullptr;
     a.sums = sums;
     a.hi_bit = hi_bit;
@@ -1110,7 +1130,7 @@ static void launch_tc_tr(const tc::Args &a, int sms, cudaStream_t st) {
 
 // Returns false if this gate shape is not handled by the tensor-core kernel.
 bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const std::vector<int> &controls,
-                     const void *Bdev, int sms, cudaStream_t st) {
+                     const void *Bdev, int sms, cudaStream_t st, double *sums, int hi_bit, bool *sums_written) {
     const int K = (int)targets.size();
     if (!dense_tc_supported(K)) return false;
     const int free_bits = n - K - (int)controls.size();
@@ -1130,8 +1150,14 @@ bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const 
     a.nfix = (int)fix.size();
     for (int i = 0; i < a.nfix; i++) a.fix[i] = fix[i];
     for (int b = 0; b < K; b++) a.targets[b] = targets[b];
-    // targets ascending (canonical order); qubits 0 and 1 among them: transposed form
+    // targets ascending (canonical order); qubits 0 and 1 among them: transposed form, the only
+    // one that also writes readout sums
     const bool tr = K == 6 && targets[0] == 0 && targets[1] == 1;
+    QSIM_REQUIRE(sums == nullptr || controls.empty(), "readout sums need every amplitude written");
+    if (sums && (!tr || !tile_classifies(n, targets, hi_bit, 7))) sums = nullptr;
+    if (sums_written) *sums_written = sums != nullptr;
+    a.sums = sums;
+    a.hi_bit = hi_bit;
     switch (K) {
         case 3: launch_tc_gm<3>(a, sms, st); break;
         case 4: launch_tc_gm<4>(a, sms, st); break;

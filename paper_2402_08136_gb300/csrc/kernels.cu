@@ -1070,43 +1070,52 @@ std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype) {
             const int D = 1 << (int)op.targets.size();
             for (int col = 0; col < D; col++)
                 for (int r = 0; r < D; r++) put_complex(blob, dtype, op.U[(size_t)r * D + col]);
-            // Gates of 4..6 targets on qubit 0 or 1 (the other one a target or free) are widened
-            // with identity qubits to the tensor-core forms that run along the low qubits: the
-            // transposed 6-target form (any U) and the real 7-target form (real U).  The
-            // group-major form's warp loads touch 32 / 2^f lines of 128 B, f = free qubits among
-            // 0..3; at 28 qubits it takes 0.72-0.75 ms with f >= 2, 1.1 ms with f = 1, 2.1 ms with
-            // f = 0.  The transposed form takes 0.74 ms with qubit 2 or 3 free, else 0.88 ms; the
-            // real 7-target form 0.78 ms.
+            // Gates on qubit 0 or 1 (the other one a target or free) may be widened with identity
+            // qubits to the tensor-core forms that run along the low qubits: the transposed
+            // 6-target form (any U) and the real 7-target form (real U).  Measured at 28 qubits:
+            // the group-major form's warp loads touch 32 / 2^f lines of 128 B, f = free qubits
+            // among 0..3, and it takes 0.73 ms with f >= 2, 1.12 ms with f = 1, 2.1 ms with f = 0;
+            // the SIMT kernels take 0.68-1.42 ms for 1..3 targets on qubit 0 or 1 (1.05 for
+            // targets {0, 1}, 1.42 for {0, 1, 2}); the transposed form 0.67 ms with one of qubits
+            // 2 and 3 free, 0.71 with none, 0.73 with both; the real 7-target form 0.79 ms.  The
+            // widened form is taken where it is estimated 5% faster, and always for 1..3 targets
+            // (never slower in the measurements).
             const int k = (int)op.targets.size();
             auto used = [&](int q) {
                 for (int x : op.targets) if (x == q) return true;
                 for (int x : op.controls) if (x == q) return true;
                 return false;
             };
+            if (dtype == QSIM_C64) {
+                op.has_tc = false;
+                op.tc_pads.clear();
+                op.tc_pad_k = 0;
+            }
             const bool t0 = op.targets[0] == 0, t1 = std::find(op.targets.begin(), op.targets.end(), 1) != op.targets.end();
             const int miss = !t0 + !t1;
-            const bool low23 = c->n > 3 && (!used(2) || !used(3));
             int f = 0;
             for (int q = 0; q < 4 && q < c->n; q++) f += !used(q);
+            const int f23 = c->n > 3 ? (int)!used(2) + (int)!used(3) : 0;
             int padk = 0;
-            bool keep23 = false;  // take the added qubits from 4 up, keeping qubit 2 or 3 free
-            if (dtype == QSIM_C64 && k >= 4 && k <= 6 && (t0 || t1) && (t0 || !used(0)) && (t1 || !used(1))) {
-                if (k == 6 && miss == 0) {
-                    if (op.real_u && !low23) padk = 7;  // the transposed form itself is slow here
-                } else if (f <= 1) {
-                    if (k + miss <= 6 && (low23 || !op.real_u)) {
-                        padk = 6;
-                        keep23 = low23;
-                    } else if (op.real_u && k + miss <= 7) {
-                        padk = 7;
-                    }
+            bool pad2 = false;  // widen over qubit 2 as well, leaving qubit 3 the only free one of the two
+            if (dtype == QSIM_C64 && (t0 || t1) && (t0 || !used(0)) && (t1 || !used(1)) && k <= 6) {
+                const double now = k >= 4 ? (f == 0 ? 2.1 : f == 1 ? 1.12 : 0.73) : 1e30;
+                const int need = 6 - k - miss;  // qubits added above 0 and 1 for the transposed form
+                if (need >= 0 && k < 6) {
+                    pad2 = f23 == 2 && need >= 1;
+                    const int fw = f23 - (int)pad2;
+                    const double tr = fw == 1 ? 0.67 : fw == 0 ? 0.71 : 0.73;
+                    if (tr < 0.95 * now) padk = 6;
+                } else if (k == 6 && miss == 1 && op.real_u && 0.79 < 0.95 * now) {
+                    padk = 7;
                 }
             }
-            std::vector<int> pads;  // qubits 0 and 1 when missing, then the lowest free ones
+            std::vector<int> pads;  // qubits 0 and 1 when missing, (2), then free ones from 4 up
             if (padk) {
                 if (!t0) pads.push_back(0);
                 if (!t1) pads.push_back(1);
-                for (int q = keep23 ? 4 : 2; q < c->n && (int)pads.size() < padk - k; q++)
+                if (pad2) pads.push_back(2);
+                for (int q = padk == 7 ? 2 : 4; q < c->n && (int)pads.size() < padk - k; q++)
                     if (!used(q)) pads.push_back(q);
             }
             if (padk && (int)pads.size() == padk - k) {
@@ -1127,18 +1136,19 @@ std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype) {
                     for (int cc = 0; cc < DW; cc++)
                         if ((r & pmask) == (cc & pmask)) UW[(size_t)r * DW + cc] = op.U[(size_t)drop(r) * D + drop(cc)];
                 align_blob(blob);
-                op.dev_off_tc[slot] = blob.size();
-                op.has_tc = true;
+                op.dev_off_tcw = blob.size();
                 op.tc_pads = pads;
                 op.tc_pad_k = padk;
                 if (padk == 7) {
                     blob.resize(blob.size() + dense_tc_real7_blob_bytes());
-                    dense_tc_pack_real7(UW, blob.data() + op.dev_off_tc[slot]);
+                    dense_tc_pack_real7(UW, blob.data() + op.dev_off_tcw);
                 } else {
                     blob.resize(blob.size() + dense_tc_blob_bytes(6));
-                    dense_tc_pack(6, UW, blob.data() + op.dev_off_tc[slot]);
+                    dense_tc_pack(6, UW, blob.data() + op.dev_off_tcw);
                 }
-            } else if (dtype == QSIM_C64 && dense_tc_supported((int)op.targets.size())) {
+            }
+            // the gate's own tensor-core form (also where the widened one is not taken)
+            if (dtype == QSIM_C64 && dense_tc_supported((int)op.targets.size())) {
                 align_blob(blob);
                 op.dev_off_tc[slot] = blob.size();
                 op.has_tc = true;
@@ -1355,9 +1365,11 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
         materialize(top_qubit(op) + 1);
         switch (op.kind) {
             case OP_DENSE:
-                if (dtype == QSIM_C64 && op.has_tc && !op.tc_pads.empty()) {
-                    // widened with identity qubits; all of them must lie inside the live width
-                    bool inside = tc_enabled(op.tc_pad_k, w);
+                if (dtype == QSIM_C64 && !op.tc_pads.empty()) {
+                    // widened with identity qubits; all of them must lie inside the live width.  Gates
+                    // of 1..3 targets are widened only on states larger than L2 (2^24 amplitudes),
+                    // where the SIMT kernels' low-qubit loads were measured slower; below, they stay.
+                    bool inside = tc_enabled(op.tc_pad_k, w) && (op.targets.size() >= 4 || w >= 24);
                     for (int q : op.tc_pads) inside = inside && q < w;
                     if (inside) {
                         std::vector<int> tw(op.targets);
@@ -1365,18 +1377,20 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
                         std::sort(tw.begin(), tw.end());
                         double *s7 = (sums && i + 1 == ops.size() && op.controls.empty()) ? sums : nullptr;
                         if (op.tc_pad_k == 7
-                                ? launch_dense_tc_real7(state, w, tw, op.controls, base + op.dev_off_tc[slot], num_sms(),
-                                                        st, s7, n - 1, &sums_done)
-                                : launch_dense_tc(state, w, tw, op.controls, base + op.dev_off_tc[slot], num_sms(), st))
+                                ? launch_dense_tc_real7(state, w, tw, op.controls, base + op.dev_off_tcw, num_sms(), st,
+                                                        s7, n - 1, &sums_done)
+                                : launch_dense_tc(state, w, tw, op.controls, base + op.dev_off_tcw, num_sms(), st, s7,
+                                                  n - 1, &sums_done))
                             break;
                     }
-                } else if (dtype == QSIM_C64 && op.has_tc && tc_enabled((int)op.targets.size(), w)) {
-                    double *s7 = (sums && i + 1 == ops.size() && op.controls.empty() && op.targets.size() == 7) ? sums
-                                                                                                                : nullptr;
+                }
+                if (dtype == QSIM_C64 && op.has_tc && tc_enabled((int)op.targets.size(), w)) {
+                    double *s7 = (sums && i + 1 == ops.size() && op.controls.empty()) ? sums : nullptr;
                     if (op.targets.size() == 7
                             ? launch_dense_tc_real7(state, w, op.targets, op.controls, base + op.dev_off_tc[slot], num_sms(),
                                                     st, s7, n - 1, &sums_done)
-                            : launch_dense_tc(state, w, op.targets, op.controls, base + op.dev_off_tc[slot], num_sms(), st))
+                            : launch_dense_tc(state, w, op.targets, op.controls, base + op.dev_off_tc[slot], num_sms(), st,
+                                              s7, n - 1, &sums_done))
                         break;
                 }
                 run_dense(state, w, dtype, op, dptr, st);

@@ -226,11 +226,11 @@ def test_hhl_run_replays_from_a_cuda_graph(qs, dtype, cuda_device):
 @pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
 def test_readout_sums_inside_the_run(qs, dtype, cuda_device):
     """hhl_run_sums + hhl_readout_sums against hhl_run + hhl_readout on a 64 x 64 system with
-    12 clock qubits (19 qubits): complex64 ends with the real 7-target tensor-core V, whose
-    epilogue writes the readout partial sums (no reduction pass of its own: one readout launch
-    instead of two); complex128 takes the reduction pass and gives the same sums bit for bit.
-    The kernel adds the squares of 8 amplitudes in FP32 (16 roundings: at most 2^-20 of the
-    group's sum) and the groups in FP64, so the complex64 sums agree to 2e-6 relative with the
+    12 clock qubits (19 qubits): complex64 ends with V on the 6 data qubits in the transposed
+    tensor-core form, whose epilogue writes the readout partial sums (no reduction pass of its
+    own: one readout launch instead of two); complex128 takes the reduction pass and gives the
+    same sums bit for bit.  The kernel adds 16 squared reals in FP32 (16 roundings: at most
+    2^-20 of their sum) and those sums in FP64, so the complex64 sums agree to 2e-6 relative with the
     reduction pass (far inside what the state's own 1e-5 per amplitude allows), the solutions
     likewise; both match the FP64 oracle's P and P0."""
     p = synth.hhl27_problem()

@@ -202,6 +202,30 @@ def test_widened_low_qubit_gates(qs, real, tc_on):
     check(st, ref_all, dtype)
 
 
+def test_widened_small_gates_on_low_qubits(qs, tc_on):
+    """complex64 gates of 1..3 targets on qubit 0 or 1 run widened to the 6-target transposed
+    tensor-core form on states of at least 2^24 amplitudes (one tensor-core launch each), and stay
+    in the SIMT kernels with qubit 0 or 1 a control or on smaller states."""
+    tc_on(6)
+    dtype = torch.complex64
+    rng = np.random.default_rng(79)
+    cases = [(24, [0], [], 1), (24, [1], [7], 1), (24, [1, 0], [], 1), (24, [0, 2], [3], 1),
+             (24, [1, 5], [], 1), (24, [0, 1, 2], [], 1), (24, [3, 1, 2], [23], 1),
+             (24, [0, 3, 7], [1], 0), (24, [4, 9], [], 0), (20, [0, 1], [], 0)]
+    for n, t, ctl, expect_tc in cases:
+        psi = host_input(synth.gaussian_state_np(80 + n, n), dtype)
+        U = synth.haar_unitary(rng, 1 << len(t))
+        ref = psi.copy()
+        ocore.apply_gate(ref, t, U, ctl)
+        st = dev_state(psi, dtype)
+        before = qs.qsim_launch_counts()["dense_tc"]
+        qs.qsim_apply(st, qs.Circuit(n).add_gate(t, U, ctl))
+        torch.cuda.synchronize()
+        assert qs.qsim_device_status() == 0
+        assert qs.qsim_launch_counts()["dense_tc"] - before == expect_tc, (n, t, ctl)
+        check(st, ref, dtype)
+
+
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_real_matrix_gates(qs, dtype):
     """Real orthogonal gates (the eigenvector matrices of real symmetric systems) run the SIMT
