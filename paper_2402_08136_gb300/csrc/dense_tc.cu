@@ -482,6 +482,15 @@ __device__ __forceinline__ void u_to_tmem(const float *Ug, unsigned tmem, unsign
     asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
 }
 
+// A tile's share of an epilogue thread's readout sums: 8 FP32 sums of 16 squares each, added in
+// FP32 (at most 24 roundings: within 1.5e-6 of the exact sum of the 128 squares), then into the
+// FP64 total of the tile's ancilla half.  One FP64 conversion and add per tile: FP64 runs at 1/64
+// of the FP32 rate, and per 16 columns it held up the epilogue's stores.
+__device__ __forceinline__ void tile_sum_into(float t, bool hi, double &s_lo, double &s_hi) {
+    if (hi) s_hi += (double)t;
+    else s_lo += (double)t;
+}
+
 // The CTA's readout sums (see Args::sums) from its 4 epilogue warps, in a fixed order: warp
 // shuffles, then the warps in order (named barrier 1 holds only them).  Every epilogue thread
 // calls it, also after a failed wait.
@@ -669,7 +678,8 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_tr_kernel(const Args a
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const unsigned long long gb = tile_base(t);
             const unsigned acc = tmem + (unsigned)(ab * N) + ((unsigned)(sub * 32) << 16);
-#pragma unroll
+            float tsum = 0.f;  // the squares of the thread's outputs in this tile
+#pragma unroll 1
             for (int col = 0; col < N; col += 16) {
                 unsigned v[16];
                 asm volatile(
@@ -680,18 +690,16 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_tr_kernel(const Args a
                     : "r"(acc + (unsigned)col));
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                 // v[i] = output real m of tile group col + i
-                float q16 = 0.f;  // their 16 squares (one ancilla value per tile)
+                float q16 = 0.f;
 #pragma unroll
                 for (int i = 0; i < 16; i++) {
                     const float y = __uint_as_float(v[i]);
                     __stcs(psif + 2 * (long long)(gb + goff[col + i] + ta) + (m & 1), y);
                     if (sums) q16 = __fmaf_rn(y, y, q16);
                 }
-                if (sums) {
-                    if ((gb >> a.hi_bit) & 1ull) s_hi += (double)q16;
-                    else s_lo += (double)q16;
-                }
+                tsum += q16;
             }
+            if (sums) tile_sum_into(tsum, (gb >> a.hi_bit) & 1ull, s_lo, s_hi);
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             mbar_arrive(&accempty[ab]);
         }
@@ -903,7 +911,8 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Arg
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const unsigned long long tb = tile_base(t);
             const unsigned acc = tmem + (unsigned)(ab * 2 * MG) + ((unsigned)(sub * 32) << 16);
-#pragma unroll
+            float tsum = 0.f;  // the squared magnitudes of the thread's outputs in this tile
+#pragma unroll 1
             for (int col = 0; col < 2 * MG; col += 16) {  // 16 columns = re, im of 8 groups
                 unsigned v[16];
                 asm volatile(
@@ -913,7 +922,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Arg
                       "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                     : "r"(acc + (unsigned)col));
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-                float q8 = 0.f;  // the chunk's 8 squared magnitudes (one ancilla value per tile)
+                float q8 = 0.f;
 #pragma unroll
                 for (int i = 0; i < 8; i++) {
                     const unsigned long long idx = tb + goff[col / 2 + i] + ta;
@@ -921,11 +930,9 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_real7_kernel(const Arg
                     __stcs(psi + idx, make_float2(yr, yi));
                     if (sums) q8 = __fmaf_rn(yi, yi, __fmaf_rn(yr, yr, q8));
                 }
-                if (sums) {
-                    if ((tb >> a.hi_bit) & 1ull) s_hi += (double)q8;
-                    else s_lo += (double)q8;
-                }
+                tsum += q8;
             }
+            if (sums) tile_sum_into(tsum, (tb >> a.hi_bit) & 1ull, s_lo, s_hi);
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             mbar_arrive(&accempty[ab]);
         }
