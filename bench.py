@@ -148,9 +148,11 @@ def rank_seed(base: int, rank: int) -> int:
 # capture of the current kernel on a 27-qubit state (the full-size launch is linear in 2^n).
 # An entry is removed whenever its kernel changes, until it is captured again.
 TRAFFIC = {
-    ("dense_tc_gm_kernel", "c64"): {"bytes_per_amp": 2.0865e9 / 2 ** 27,
-                                    "source": "profiles/dense_gate_kernels_c64_27q.md (k=4..6 mean, "
-                                              "27-qubit capture scaled by 2^n)"},
+    ("dense_tc_gm_kernel+dense_tc_tr_kernel", "c64"): {
+        "bytes_per_amp": 2.0865e9 / 2 ** 27,
+        "source": "profiles/dense_gate_kernels_c64_27q.md (group-major form, k=4..6 mean) and "
+                  "profiles/dense_tc_tr_kernel_c64_27q.md (transposed form, 2.087e9), 27-qubit "
+                  "captures scaled by 2^n"},
     ("dense_pipe_kernel", "c64"): {"bytes_per_amp": 2.0874e9 / 2 ** 27,
                                    "source": "profiles/dense_gate_kernels_c64_27q.md (k=1..3 mean, "
                                              "27-qubit capture scaled by 2^n)"},
@@ -160,7 +162,9 @@ TRAFFIC = {
 FP64_PEAK_TFLOPS = 1.25
 
 
-FAMILY_KERNEL = {"dense_simt": "dense_pipe_kernel", "dense_tc": "dense_tc_gm_kernel",
+# the library counts launches per family; the tensor-core family is the group-major and the
+# transposed form (gates on qubit 0 or 1)
+FAMILY_KERNEL = {"dense_simt": "dense_pipe_kernel", "dense_tc": "dense_tc_gm_kernel+dense_tc_tr_kernel",
                  "fourier": "dft_kernel", "fourier_tma": "dft_tma_kernel"}
 
 

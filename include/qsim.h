@@ -213,8 +213,9 @@ int qsim_launch_counts(unsigned long long *counts, int n);
 #define QSIM_TUNE_DFT_PREFETCH 2 /* pass kernels: L2 prefetch distance in tiles (0 off; bulk-copy
                                     kernels prefetch with a bulk tensor prefetch)                  */
 #define QSIM_TUNE_DENSE_TC 3     /* complex64 dense gates: bit k set = gates of k targets (3..6)
-                                    on the tensor cores; bit 7 = real 7-target gates (and real
-                                    6-target gates on qubits 0 and 1) on the tensor cores          */
+                                    on the tensor cores; bit 7 = real 7-target gates on the
+                                    tensor cores.  Gates on qubit 0 or 1 widened with identity
+                                    qubits take bit 6 (transposed form) or 7 (real form)          */
 #define QSIM_TUNE_FUSE_WIDTH 4   /* width qsim_fuse uses when called with max_k = 0 (the
                                     complex64 entry; 1..6)                                          */
 #define QSIM_TUNE_DFT_L2PROMO 5  /* bulk-copy pass kernel: L2 promotion of its tile loads (0 none,
@@ -395,9 +396,9 @@ int hhl_readout(const void *state, int dtype, const hhl_circuit *h, void *stream
 /* Readout sums computed inside the run.  hhl_run_sums is hhl_run that also leaves, in
  * sums_device (device memory of QSIM_READOUT_SUMS_DOUBLES doubles, caller-owned), the FP64
  * partial sums of |psi|^2 over the final state that the readout needs: written by the circuit's
- * last kernel while it stores the state when that is the complex64 real 7-target tensor-core
- * gate (the eigenvector rotation V that ends the structured HHL circuit), else by a reduction
- * pass after it.  Device-only, so it can be captured into a CUDA graph.  hhl_readout_sums is
+ * last kernel while it stores the state when that is a complex64 tensor-core gate without
+ * controls in the transposed 6-target or the real 7-target form (the eigenvector rotation V that
+ * ends the structured HHL circuit), else by a reduction pass after it.  Device-only, so it can be captured into a CUDA graph.  hhl_readout_sums is
  * hhl_readout taking those partials instead of reducing the state again; the state must not
  * have changed since the hhl_run_sums that wrote sums_device.  Errors: EINVAL, ENOMEM, ECUDA. */
 #define QSIM_READOUT_SUMS_DOUBLES 4096

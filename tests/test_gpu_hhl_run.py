@@ -229,8 +229,8 @@ def test_readout_sums_inside_the_run(qs, dtype, cuda_device):
     12 clock qubits (19 qubits): complex64 ends with V on the 6 data qubits in the transposed
     tensor-core form, whose epilogue writes the readout partial sums (no reduction pass of its
     own: one readout launch instead of two); complex128 takes the reduction pass and gives the
-    same sums bit for bit.  The kernel adds 16 squared reals in FP32 (16 roundings: at most
-    2^-20 of their sum) and those sums in FP64, so the complex64 sums agree to 2e-6 relative with the
+    same sums bit for bit.  The kernel adds a tile's 128 squares per thread in FP32 (at most 24
+    roundings: within 1.5e-6 of their sum) and the tiles in FP64, so the complex64 sums agree to 2e-6 relative with the
     reduction pass (far inside what the state's own 1e-5 per amplitude allows), the solutions
     likewise; both match the FP64 oracle's P and P0."""
     p = synth.hhl27_problem()
