@@ -1157,9 +1157,14 @@ bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const 
     a.nfix = (int)fix.size();
     for (int i = 0; i < a.nfix; i++) a.fix[i] = fix[i];
     for (int b = 0; b < K; b++) a.targets[b] = targets[b];
-    // targets ascending (canonical order); qubits 0 and 1 among them: transposed form, the only
-    // one that also writes readout sums
-    const bool tr = K == 6 && targets[0] == 0 && targets[1] == 1;
+    // targets ascending (canonical order).  6 targets with qubit 0 (its amplitude pairs are the
+    // transposed form's 16-byte loads): the transposed form when qubit 1 is a target too, or when
+    // at most one of qubits 0..3 is free, where the group-major form's warp loads touch 16-32
+    // lines; it is the only form that also writes readout sums
+    int free_low = 0;
+    for (int q = 0; q < 4 && q < n; q++)
+        free_low += std::find(fix.begin(), fix.end(), q) == fix.end();
+    const bool tr = K == 6 && targets[0] == 0 && (targets[1] == 1 || free_low <= 1);
     QSIM_REQUIRE(sums == nullptr || controls.empty(), "readout sums need every amplitude written");
     if (sums && (!tr || !tile_classifies(n, targets, hi_bit, 7))) sums = nullptr;
     if (sums_written) *sums_written = sums != nullptr;
