@@ -125,9 +125,10 @@ def test_tensor_core_dense_parity_complex64(qs, k, tc_on):
 
 
 def test_real_six_target_gates_on_low_qubits(qs):
-    """complex64 real 6-target gates whose targets include qubits 0 and 1 run in the real
-    7-target tensor-core kernel as I (x) U on the lowest free qubit (at the top of the target
-    list, in its middle, and moved up by a control); applied alone and in one circuit."""
+    """complex64 real 6-target gates whose targets include qubits 0 and 1 (the eigenvector
+    rotation of a 64 x 64 system on the data register) run in the transposed tensor-core form:
+    targets contiguous, with gaps, with controls above and between them; applied alone and in one
+    circuit."""
     dtype = torch.complex64
     rng = np.random.default_rng(66)
     n = 14
