@@ -525,10 +525,13 @@ __device__ __forceinline__ void epi_store_sums(double s_lo, double s_hi, int sub
 // with B (the real form of U, hi and lo) as the MMA's A operand, held in tensor memory next to
 // the two accumulators (U columns 256..511), and the tile's 128 groups as its B operand (N =
 // 128), a ring of six shared-memory chunks of 32 K-columns.  Producers load each group's 16
-// amplitudes of a chunk as 16-byte vectors (a warp reads 4 groups x 128 contiguous bytes), and
-// the accumulator's TMEM lanes are output reals, so the epilogue's warp stores write 32
-// consecutive floats of one group.  Roles, barriers and bounded waits as in the group-major
-// kernels.
+// amplitudes of a chunk as 16-byte vectors (a warp reads 4 groups x 128 contiguous bytes).  With
+// PAIRG (qubit 1 a target, qubit 0 free: a group bit) a 16-byte load is one amplitude of two
+// sibling groups instead, and a warp reads 4 group pairs x 8 amplitudes.  The accumulator's TMEM
+// lanes are output reals, so the epilogue's warp stores write 32 consecutive floats of one group;
+// with PAIRG, lanes 2j and 2j+1 (re and im of output amplitude j) swap one value per pair of tile
+// columns (sibling groups) and each writes one whole amplitude of one of the two: 256 contiguous
+// bytes per warp store.  Roles, barriers and bounded waits as in the group-major kernels.
 namespace tct {
 constexpr int K = 6, D = 64, N = 128, KK = 128, NCH = KK / kCH;
 constexpr int ABYTES = kM * kCH * 4;  // one chunk (hi or lo)
@@ -538,6 +541,7 @@ constexpr int SMEM = NBUF * 2 * ABYTES + 8 * NBAR + 16 + 8 * D + 8 * kM;
 constexpr int UCOL = 2 * N;  // tensor memory: two accumulators, then U hi and U lo
 }  // namespace tct
 
+template <bool PAIRG>
 __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_tr_kernel(const Args a) {
     using namespace tct;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -602,27 +606,36 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_tr_kernel(const Args a
 
     if (warp < kEpiWarp0) {
         // ------------------------------------------------------------------ producers
-        // thread (warp w, lane l): amplitude pair h = l / 4 (amplitudes 2h, 2h+1 of the chunk's
-        // 16) of group rows 8w + (l mod 4) and 8w + 4 + (l mod 4).  A warp's vector load reads 4
-        // rows x 16 amplitudes, which are 4 whole 128-byte lines whether qubits 2 and 3 are
-        // targets or free (one free: its two rows share a line).  The 16-byte shared-memory
+        // Without PAIRG, thread (warp w, lane l): amplitude pair h = l / 4 (amplitudes 2h, 2h+1 of
+        // the chunk's 16) of group rows 8w + (l mod 4) and 8w + 4 + (l mod 4).  A warp's vector
+        // load reads 4 rows x 16 amplitudes, which are 4 whole 128-byte lines whether qubits 2 and
+        // 3 are targets or free (one free: its two rows share a line).  The 16-byte shared-memory
         // stores alternate the rows between lanes of odd and even h, so a quarter-warp covers all
         // 8 row slots of a core matrix (no bank conflict).
+        // With PAIRG, thread (w, l): amplitudes c = l / 4 and c + 8 of the chunk for the sibling
+        // rows 8w + 2(l mod 4) and 8w + 2(l mod 4) + 1; a vector load reads 4 row pairs x 8
+        // amplitudes.  Its 8-byte stores (one amplitude of one row) take the even or the odd row
+        // first by bit 1 of c, so a half-warp covers the 16 distinct 8-byte slots of a 128-byte
+        // core-matrix row group (no bank conflict).
         const int rw = lane & 3, h = lane >> 2;
         float2 r[kPrefetch][kAmpsPT];
         long long gb_tile = -1;
         unsigned long long gb_base = 0;
-        const long long gA = goff[8 * warp + rw], gB = goff[8 * warp + 4 + rw];
+        const long long gA = PAIRG ? goff[8 * warp + 2 * rw] : goff[8 * warp + rw];
+        const long long gB = PAIRG ? gA : goff[8 * warp + 4 + rw];
         auto load = [&](long long qq, float2(&rr)[kAmpsPT]) {
             if (qq < total) {
                 if (qq / NCH != gb_tile) {
                     gb_tile = qq / NCH;
                     gb_base = tile_base(gb_tile);
                 }
-                // qubit 0 is a target: each pair is contiguous
-                const long long t0 = toff[(int)(qq % NCH) * 16 + 2 * h];
-                const float4 u0 = __ldcs(reinterpret_cast<const float4 *>(psi + gb_base + gA + t0));
-                const float4 u1 = __ldcs(reinterpret_cast<const float4 *>(psi + gb_base + gB + t0));
+                const int c0 = (int)(qq % NCH) * 16;
+                // without PAIRG qubit 0 is a target (amplitudes 2h, 2h+1 adjacent); with it the two
+                // rows are siblings in qubit 0 (amplitude c of both adjacent)
+                const long long ta0 = toff[c0 + (PAIRG ? h : 2 * h)];
+                const long long ta1 = PAIRG ? toff[c0 + h + 8] : ta0;
+                const float4 u0 = __ldcs(reinterpret_cast<const float4 *>(psi + gb_base + gA + ta0));
+                const float4 u1 = __ldcs(reinterpret_cast<const float4 *>(psi + gb_base + gB + ta1));
                 rr[0] = make_float2(u0.x, u0.y);
                 rr[1] = make_float2(u0.z, u0.w);
                 rr[2] = make_float2(u1.x, u1.y);
@@ -644,17 +657,36 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_tr_kernel(const Args a
                 }
                 unsigned char *ahi = Aring + b * 2 * ABYTES;
                 unsigned char *alo = ahi + ABYTES;
+                if constexpr (PAIRG) {
+                    // r[0], r[1]: amplitude h of the even and odd row; r[2], r[3]: amplitude h + 8
 #pragma unroll
-                for (int pi = 0; pi < 2; pi++) {  // row 8w + rw (pi = h mod 2) or 8w + 4 + rw
-                    const int rowB = pi ^ (h & 1);
-                    const float2 x0 = rowB ? r[p][2] : r[p][0], x1 = rowB ? r[p][3] : r[p][1];
-                    const unsigned off = warp * 1024 + h * 128 + (4 * rowB + rw) * 16;
-                    const unsigned h0 = to_tf32(x0.x), h1 = to_tf32(x0.y);
-                    const unsigned h2 = to_tf32(x1.x), h3 = to_tf32(x1.y);
-                    *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(h0, h1, h2, h3);
-                    *reinterpret_cast<uint4 *>(alo + off) =
-                        make_uint4(to_tf32(x0.x - __uint_as_float(h0)), to_tf32(x0.y - __uint_as_float(h1)),
-                                   to_tf32(x1.x - __uint_as_float(h2)), to_tf32(x1.y - __uint_as_float(h3)));
+                    for (int hv = 0; hv < 2; hv++) {
+                        const int c = h + 8 * hv;  // amplitude of the chunk: K columns 2c, 2c + 1
+#pragma unroll
+                        for (int pi = 0; pi < 2; pi++) {
+                            const int odd = pi ^ ((h >> 1) & 1);
+                            const float2 x = odd ? r[p][2 * hv + 1] : r[p][2 * hv];
+                            const unsigned off =
+                                warp * 1024 + (c >> 1) * 128 + (2 * rw + odd) * 16 + (c & 1) * 8;
+                            const unsigned h0 = to_tf32(x.x), h1 = to_tf32(x.y);
+                            *reinterpret_cast<uint2 *>(ahi + off) = make_uint2(h0, h1);
+                            *reinterpret_cast<uint2 *>(alo + off) =
+                                make_uint2(to_tf32(x.x - __uint_as_float(h0)), to_tf32(x.y - __uint_as_float(h1)));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int pi = 0; pi < 2; pi++) {  // row 8w + rw (pi = h mod 2) or 8w + 4 + rw
+                        const int rowB = pi ^ (h & 1);
+                        const float2 x0 = rowB ? r[p][2] : r[p][0], x1 = rowB ? r[p][3] : r[p][1];
+                        const unsigned off = warp * 1024 + h * 128 + (4 * rowB + rw) * 16;
+                        const unsigned h0 = to_tf32(x0.x), h1 = to_tf32(x0.y);
+                        const unsigned h2 = to_tf32(x1.x), h3 = to_tf32(x1.y);
+                        *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(h0, h1, h2, h3);
+                        *reinterpret_cast<uint4 *>(alo + off) =
+                            make_uint4(to_tf32(x0.x - __uint_as_float(h0)), to_tf32(x0.y - __uint_as_float(h1)),
+                                       to_tf32(x1.x - __uint_as_float(h2)), to_tf32(x1.y - __uint_as_float(h3)));
+                    }
                 }
                 load(qq + kPrefetch, r[p]);
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -666,6 +698,7 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_tr_kernel(const Args a
         const int sub = warp - kEpiWarp0;          // TMEM lane subpartition
         const int m = sub * 32 + lane;             // output real
         const long long ta = toff[m >> 1];         // its amplitude
+        const int odd = m & 1;                     // im lane: with PAIRG, writes the odd column of each pair
         float *psif = reinterpret_cast<float *>(a.psi);
         double s_lo = 0.0, s_hi = 0.0;  // readout sums of this thread's outputs
         const bool sums = a.sums != nullptr;
@@ -691,11 +724,24 @@ __global__ void __launch_bounds__(kThreadsWS, 1) dense_tc_tr_kernel(const Args a
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                 // v[i] = output real m of tile group col + i
                 float q16 = 0.f;
+                if constexpr (PAIRG) {
+                    // columns i, i+1 are sibling groups (adjacent amplitudes): per pair the re lane
+                    // gives its value of column i+1 for the im lane's value of column i, so the re
+                    // lane holds amplitude m/2 of group col + i, the im lane that of group col + i + 1
 #pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const float y = __uint_as_float(v[i]);
-                    __stcs(psif + 2 * (long long)(gb + goff[col + i] + ta) + (m & 1), y);
-                    if (sums) q16 = __fmaf_rn(y, y, q16);
+                    for (int i = 0; i < 16; i += 2) {
+                        const float y0 = __uint_as_float(v[i]), y1 = __uint_as_float(v[i + 1]);
+                        const float got = __shfl_xor_sync(0xffffffffu, odd ? y0 : y1, 1);
+                        __stcs(psi + gb + goff[col + i + odd] + ta, odd ? make_float2(got, y1) : make_float2(y0, got));
+                        if (sums) q16 = __fmaf_rn(y1, y1, __fmaf_rn(y0, y0, q16));
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        const float y = __uint_as_float(v[i]);
+                        __stcs(psif + 2 * (long long)(gb + goff[col + i] + ta) + (m & 1), y);
+                        if (sums) q16 = __fmaf_rn(y, y, q16);
+                    }
                 }
                 tsum += q16;
             }
@@ -1120,16 +1166,18 @@ static void launch_tc_gm(const tc::Args &a, int sms, cudaStream_t st) {
     note_launches(1, QSIM_KERNEL_DENSE_TC);
 }
 
+template <bool PAIRG>
 static void launch_tc_tr(const tc::Args &a, int sms, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc::dense_tc_tr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::tct::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(tc::dense_tc_tr_kernel<PAIRG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             tc::tct::SMEM);
         if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_tr_kernel attribute: ") + cudaGetErrorString(e));
         attr = true;
     }
     // one CTA per SM: it holds all 512 tensor-memory columns
     const long long grid = std::min<long long>(a.ntiles, (long long)sms);
-    tc::dense_tc_tr_kernel<<<(int)grid, tc::kThreadsWS, tc::tct::SMEM, st>>>(a);
+    tc::dense_tc_tr_kernel<PAIRG><<<(int)grid, tc::kThreadsWS, tc::tct::SMEM, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) throw Error(QSIM_ECUDA, std::string("dense_tc_tr_kernel: ") + cudaGetErrorString(e));
     note_launches(1, QSIM_KERNEL_DENSE_TC);
@@ -1160,11 +1208,15 @@ bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const 
     // targets ascending (canonical order).  6 targets with qubit 0 (its amplitude pairs are the
     // transposed form's 16-byte loads): the transposed form when qubit 1 is a target too, or when
     // at most one of qubits 0..3 is free, where the group-major form's warp loads touch 16-32
-    // lines; it is the only form that also writes readout sums
+    // lines.  6 targets with qubit 1 and a free qubit 0 (sibling groups in each 16-byte load):
+    // the transposed form's PAIRG variant when qubit 0 is the only free one of qubits 0..3.  The
+    // transposed form is the only one that also writes readout sums
     int free_low = 0;
     for (int q = 0; q < 4 && q < n; q++)
         free_low += std::find(fix.begin(), fix.end(), q) == fix.end();
-    const bool tr = K == 6 && targets[0] == 0 && (targets[1] == 1 || free_low <= 1);
+    const bool q0_free = std::find(fix.begin(), fix.end(), 0) == fix.end();
+    const bool trp = K == 6 && targets[0] == 1 && q0_free && free_low == 1;
+    const bool tr = trp || (K == 6 && targets[0] == 0 && (targets[1] == 1 || free_low <= 1));
     QSIM_REQUIRE(sums == nullptr || controls.empty(), "readout sums need every amplitude written");
     if (sums && (!tr || !tile_classifies(n, targets, hi_bit, 7))) sums = nullptr;
     if (sums_written) *sums_written = sums != nullptr;
@@ -1174,7 +1226,11 @@ bool launch_dense_tc(void *state, int n, const std::vector<int> &targets, const 
         case 3: launch_tc_gm<3>(a, sms, st); break;
         case 4: launch_tc_gm<4>(a, sms, st); break;
         case 5: launch_tc_gm<5>(a, sms, st); break;
-        case 6: tr ? launch_tc_tr(a, sms, st) : launch_tc_gm<6>(a, sms, st); break;
+        case 6:
+            if (trp) launch_tc_tr<true>(a, sms, st);
+            else if (tr) launch_tc_tr<false>(a, sms, st);
+            else launch_tc_gm<6>(a, sms, st);
+            break;
         default: return false;
     }
     return true;

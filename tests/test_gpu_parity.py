@@ -162,7 +162,8 @@ def test_widened_low_qubit_gates(qs, real, tc_on):
     when free, then the lowest that are neither target nor control (from qubit 4 up when qubit
     2 or 3 is free and the transposed form is taken): above the targets, between them, moved up
     by controls.  Complex 6-target gates with qubit 0 but at most one free qubit among 0..3 run
-    in the transposed form unwidened (qubit 1 a group bit).  Gates with qubit 0 or 1 a control,
+    in the transposed form unwidened (qubit 1 a group bit); with qubit 1 and qubit 0 the only
+    free one, in its sibling-group variant (each 16-byte load one amplitude of two groups).  Gates with qubit 0 or 1 a control,
     or with free low qubits, stay in the group-major form.  Each gate alone (one tensor-core
     launch) and all in one circuit."""
     tc_on(6, 7)
@@ -175,6 +176,7 @@ def test_widened_low_qubit_gates(qs, real, tc_on):
              ([1, 2, 3, 4], []), ([0, 2, 3, 9], [12]), ([0, 1, 2, 9], []), ([0, 1, 3, 7, 9], [4]),
              ([0, 5, 9, 13], [2]), ([1, 3, 6, 8, 10], []),
              ([0, 2, 3, 4, 5, 6], []), ([0, 2, 3, 7, 9, 11], [13]),  # complex: transposed, qubit 1 free
+             ([1, 2, 3, 4, 5, 6], []), ([1, 2, 5, 7, 9, 11], [3]),  # complex: sibling-group loads
              ([1, 3, 6, 8], [0]), ([0, 3, 4, 6, 7], [1])]  # the last two: qubit 0 or 1 a control
     if real:
         cases += [([0, 1, 2, 3, 4, 5], [6]), ([0, 1, 3, 5, 7, 9], [2, 4]), ([1, 2, 3, 4, 5, 6], []),
