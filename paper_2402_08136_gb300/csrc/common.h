@@ -97,13 +97,11 @@ struct Op {
     // the real form (tensor cores); OP_QPE_PHASE, the high half of its two-table split
     size_t dev_off_tc[2] = {0, 0};
     bool has_tc = false;
-    // complex64 dense op on qubit 0 or 1 widened with identity qubits to a tensor-core form whose
-    // loads and stores run along the low qubits: the transposed 6-target form (1..5 targets) or
-    // the real 7-target kernel (a real U of 6 targets without qubit 0 or 1).  tc_pads: the added
-    // qubits (empty: not widened), qubits 0 and 1 among them when not targets; tc_pad_k: 6 or 7;
+    // complex64 dense op of 1..5 targets on qubit 0 or 1 widened with identity qubits to the
+    // transposed 6-target tensor-core form, whose loads and stores run along the low qubits.
+    // tc_pads: the added qubits (empty: not widened), qubits 0 and 1 among them when not targets;
     // dev_off_tcw: the widened form's blob (complex64 device data)
     std::vector<int> tc_pads;
-    int tc_pad_k = 0;
     size_t dev_off_tcw = 0;
     bool real_u = false;        // OP_DENSE: every entry of U is real (SIMT kernels use 2 FMAs per entry)
 };

@@ -26,9 +26,11 @@
 //   - group-major form (dense_tc_gm_kernel, any targets but the transposed case): X in tensor
 //     memory, written by the producers with tcgen05.st into a ring of chunk slots, U (B
 //     operand) in shared memory;
-//   - transposed form (dense_tc_tr_kernel, 6 targets including qubits 0 and 1) and real
-//     7-target gates (dense_tc_real7_kernel): U is the A operand and sits in tensor memory, X
-//     chunks (B operand) in a six-deep shared-memory ring.
+//   - transposed form (dense_tc_tr_kernel, 6 targets on the low qubits: qubits 0 and 1, or
+//     qubit 0 or qubit 1 with the other free and few free qubits below 4; gates of 1..5
+//     targets there are widened to it by the host) and real 7-target gates
+//     (dense_tc_real7_kernel): U is the A operand and sits in tensor memory, X chunks (B
+//     operand) in a six-deep shared-memory ring.
 //
 // Shared-memory operand layout (no swizzle, K-major): 8-row x 16-byte core matrices; core
 // matrices adjacent along K are 128 bytes apart (leading byte offset), adjacent along M/N
@@ -518,7 +520,7 @@ __device__ __forceinline__ void epi_store_sums(double s_lo, double s_hi, int sub
 }
 
 // ---------------------------------------------------------------------------------------
-// Transposed form (6 targets including qubits 0 and 1).  When the targets are the lowest qubits,
+// Transposed form (6 targets on the low qubits, see launch_dense_tc).  When the targets are the lowest qubits,
 // a group's amplitudes are contiguous but consecutive groups are 2^k amplitudes apart, and the
 // group-major form would read and write 8-byte pieces at that stride.  This form computes
 //     Y^T[2D x 128] = B[2D x 2D] * X^T,

@@ -1070,17 +1070,16 @@ std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype) {
             const int D = 1 << (int)op.targets.size();
             for (int col = 0; col < D; col++)
                 for (int r = 0; r < D; r++) put_complex(blob, dtype, op.U[(size_t)r * D + col]);
-            // Gates on qubit 0 or 1 (the other one a target or free) may be widened with identity
-            // qubits to the tensor-core forms that run along the low qubits: the transposed
-            // 6-target form (any U) and the real 7-target form (real U).  Measured at 28 qubits:
-            // the group-major form's warp loads touch 32 / 2^f lines of 128 B, f = free qubits
-            // among 0..3, and it takes 0.73 ms with f >= 2, 1.12 ms with f = 1, 2.1 ms with f = 0;
-            // the SIMT kernels take 0.68-1.42 ms for 1..3 targets on qubit 0 or 1 (1.05 for
-            // targets {0, 1}, 1.42 for {0, 1, 2}); the transposed form 0.67 ms with one of qubits
-            // 2 and 3 free, 0.71 with none, 0.73 with both; the real 7-target form 0.79 ms.  The
-            // widened form is taken where it is estimated 5% faster, and always for 1..3 targets
-            // (never slower in the measurements).  6 targets with qubit 0 need no widening: the
-            // transposed form takes them directly (0.70 ms; launch_dense_tc).
+            // Gates of 1..5 targets on qubit 0 or 1 (the other one a target or free) may be widened
+            // with identity qubits to the transposed 6-target tensor-core form, which runs along
+            // the low qubits.  Measured at 28 qubits: the group-major form's warp loads touch
+            // 32 / 2^f lines of 128 B, f = free qubits among 0..3, and it takes 0.73 ms with f >= 2,
+            // 1.12 ms with f = 1, 2.1 ms with f = 0; the SIMT kernels take 0.68-1.42 ms for 1..3
+            // targets on qubit 0 or 1 (1.05 for targets {0, 1}, 1.42 for {0, 1, 2}); the
+            // transposed form 0.67 ms with one of qubits 2 and 3 free, 0.71 with none, 0.73 with
+            // both.  The widened form is taken where it is estimated 5% faster, and always for
+            // 1..3 targets (never slower in the measurements).  6 targets need no widening: the
+            // transposed form takes those on qubit 0 or 1 directly (0.70-0.73 ms; launch_dense_tc).
             const int k = (int)op.targets.size();
             auto used = [&](int q) {
                 for (int x : op.targets) if (x == q) return true;
@@ -1090,37 +1089,31 @@ std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype) {
             if (dtype == QSIM_C64) {
                 op.has_tc = false;
                 op.tc_pads.clear();
-                op.tc_pad_k = 0;
             }
             const bool t0 = op.targets[0] == 0, t1 = std::find(op.targets.begin(), op.targets.end(), 1) != op.targets.end();
             const int miss = !t0 + !t1;
             int f = 0;
             for (int q = 0; q < 4 && q < c->n; q++) f += !used(q);
             const int f23 = c->n > 3 ? (int)!used(2) + (int)!used(3) : 0;
-            int padk = 0;
+            const int need = 6 - k - miss;  // qubits added above 0 and 1
+            bool widen = false;
             bool pad2 = false;  // widen over qubit 2 as well, leaving qubit 3 the only free one of the two
-            if (dtype == QSIM_C64 && (t0 || t1) && (t0 || !used(0)) && (t1 || !used(1)) && k <= 6) {
+            if (dtype == QSIM_C64 && (t0 || t1) && (t0 || !used(0)) && (t1 || !used(1)) && k < 6 && need >= 0) {
                 const double now = k >= 4 ? (f == 0 ? 2.1 : f == 1 ? 1.12 : 0.73) : 1e30;
-                const int need = 6 - k - miss;  // qubits added above 0 and 1 for the transposed form
-                if (need >= 0 && k < 6) {
-                    pad2 = f23 == 2 && need >= 1;
-                    const int fw = f23 - (int)pad2;
-                    const double tr = fw == 1 ? 0.67 : fw == 0 ? 0.71 : 0.73;
-                    if (tr < 0.95 * now) padk = 6;
-                } else if (k == 6 && !t0 && op.real_u && 0.79 < 0.95 * now) {
-                    // qubit 1 without qubit 0 (with qubit 0 the transposed form takes it as it is)
-                    padk = 7;
-                }
+                pad2 = f23 == 2 && need >= 1;
+                const int fw = f23 - (int)pad2;
+                const double tr = fw == 1 ? 0.67 : fw == 0 ? 0.71 : 0.73;
+                widen = tr < 0.95 * now;
             }
             std::vector<int> pads;  // qubits 0 and 1 when missing, (2), then free ones from 4 up
-            if (padk) {
+            if (widen) {
                 if (!t0) pads.push_back(0);
                 if (!t1) pads.push_back(1);
                 if (pad2) pads.push_back(2);
-                for (int q = padk == 7 ? 2 : 4; q < c->n && (int)pads.size() < padk - k; q++)
+                for (int q = 4; q < c->n && (int)pads.size() < 6 - k; q++)
                     if (!used(q)) pads.push_back(q);
             }
-            if (padk && (int)pads.size() == padk - k) {
+            if (widen && (int)pads.size() == 6 - k) {
                 std::vector<int> tw(op.targets);
                 tw.insert(tw.end(), pads.begin(), pads.end());
                 std::sort(tw.begin(), tw.end());
@@ -1128,11 +1121,11 @@ std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype) {
                 for (int q : pads) pmask |= 1 << (int)(std::find(tw.begin(), tw.end(), q) - tw.begin());
                 auto drop = [&](int x) {  // the widened index without the added bits
                     int v = 0, b = 0;
-                    for (int i = 0; i < padk; i++)
+                    for (int i = 0; i < 6; i++)
                         if (!((pmask >> i) & 1)) v |= ((x >> i) & 1) << b++;
                     return v;
                 };
-                const int DW = 1 << padk;
+                const int DW = 64;
                 std::vector<cd> UW((size_t)DW * DW, cd(0.0, 0.0));
                 for (int r = 0; r < DW; r++)
                     for (int cc = 0; cc < DW; cc++)
@@ -1140,14 +1133,8 @@ std::vector<unsigned char> pack_device_blob(qsim_circuit *c, int dtype) {
                 align_blob(blob);
                 op.dev_off_tcw = blob.size();
                 op.tc_pads = pads;
-                op.tc_pad_k = padk;
-                if (padk == 7) {
-                    blob.resize(blob.size() + dense_tc_real7_blob_bytes());
-                    dense_tc_pack_real7(UW, blob.data() + op.dev_off_tcw);
-                } else {
-                    blob.resize(blob.size() + dense_tc_blob_bytes(6));
-                    dense_tc_pack(6, UW, blob.data() + op.dev_off_tcw);
-                }
+                blob.resize(blob.size() + dense_tc_blob_bytes(6));
+                dense_tc_pack(6, UW, blob.data() + op.dev_off_tcw);
             }
             // the gate's own tensor-core form (also where the widened one is not taken)
             if (dtype == QSIM_C64 && dense_tc_supported((int)op.targets.size())) {
@@ -1371,18 +1358,15 @@ void apply_ops(void *state, int n, int dtype, qsim_circuit *c, void *stream, int
                     // widened with identity qubits; all of them must lie inside the live width.  Gates
                     // of 1..3 targets are widened only on states larger than L2 (2^24 amplitudes),
                     // where the SIMT kernels' low-qubit loads were measured slower; below, they stay.
-                    bool inside = tc_enabled(op.tc_pad_k, w) && (op.targets.size() >= 4 || w >= 24);
+                    bool inside = tc_enabled(6, w) && (op.targets.size() >= 4 || w >= 24);
                     for (int q : op.tc_pads) inside = inside && q < w;
                     if (inside) {
                         std::vector<int> tw(op.targets);
                         tw.insert(tw.end(), op.tc_pads.begin(), op.tc_pads.end());
                         std::sort(tw.begin(), tw.end());
                         double *s7 = (sums && i + 1 == ops.size() && op.controls.empty()) ? sums : nullptr;
-                        if (op.tc_pad_k == 7
-                                ? launch_dense_tc_real7(state, w, tw, op.controls, base + op.dev_off_tcw, num_sms(), st,
-                                                        s7, n - 1, &sums_done)
-                                : launch_dense_tc(state, w, tw, op.controls, base + op.dev_off_tcw, num_sms(), st, s7,
-                                                  n - 1, &sums_done))
+                        if (launch_dense_tc(state, w, tw, op.controls, base + op.dev_off_tcw, num_sms(), st, s7, n - 1,
+                                            &sums_done))
                             break;
                     }
                 }

@@ -156,16 +156,16 @@ def test_real_six_target_gates_on_low_qubits(qs):
 
 @pytest.mark.parametrize("real", [False, True])
 def test_widened_low_qubit_gates(qs, real, tc_on):
-    """complex64 gates of 4..6 targets on qubit 0 or 1, widened with identity qubits to the
-    6-target transposed form or (real U) the real 7-target form where the group-major form's
-    loads are poor (at most one free qubit among 0..3).  The added qubits are qubits 0 and 1
-    when free, then the lowest that are neither target nor control (from qubit 4 up when qubit
-    2 or 3 is free and the transposed form is taken): above the targets, between them, moved up
-    by controls.  Complex 6-target gates with qubit 0 but at most one free qubit among 0..3 run
-    in the transposed form unwidened (qubit 1 a group bit); with qubit 1 and qubit 0 the only
-    free one, in its sibling-group variant (each 16-byte load one amplitude of two groups).  Gates with qubit 0 or 1 a control,
-    or with free low qubits, stay in the group-major form.  Each gate alone (one tensor-core
-    launch) and all in one circuit."""
+    """complex64 gates of 4..5 targets on qubit 0 or 1, widened with identity qubits to the
+    6-target transposed form where the group-major form's loads are poor, and 6-target gates on
+    the low qubits in the transposed form itself.  The added qubits are qubits 0 and 1 when
+    free, qubit 2 when that leaves exactly one of qubits 2 and 3 free, then free qubits from 4
+    up: above the targets, between them, moved up by controls.  6-target gates with qubit 0 and
+    at most one free qubit among 0..3 run in the transposed form unwidened (qubit 1 a group
+    bit); with qubit 1 and qubit 0 the only free one, in its sibling-group variant (each 16-byte
+    load one amplitude of two groups).  Gates with qubit 0 or 1 a control, or with free low
+    qubits, stay in the group-major form.  Each gate alone (one tensor-core launch) and all in
+    one circuit."""
     tc_on(6, 7)
     dtype = torch.complex64
     rng = np.random.default_rng(77 + real)
